@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the coagulation step on synthetic discs.
+
+One step = rebuild the collision kernel from the gas arrays (a2, a3) and
+integrate every cell of the 128 R x 64 Z x 100-bin grid over 1e4 yr with
+BS3 3(2) and the paper's tolerances (a4-a7).  The metric is accepted
+cell-substeps per second over the timed steps.
+
+    python bench.py [--gpus N --steps K --warmup W] [--precision mixed|fp64]
+    python bench.py --impl reference ...   # the FP64 CPU oracle arm
+
+Under torchrun each rank integrates its own copy of the workload (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2402_18471_b300 import synth  # noqa: E402
+
+WORKLOADS = {
+    "grid_128x64_N100": synth.grid_128x64,
+    "column_1x32_N50": synth.column_1x32,
+    "adjoint_64x32_N80": synth.adjoint_64x32,
+    "grid_512x256_N150": synth.grid_512x256,
+}
+METRIC = "cell-substeps/s, 128x64 cells x 100 bins: mixed vs FP64 GPU, rel err<=1e-5"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
+TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 rate ratio
+
+
+def peaks():
+    if os.path.exists(PEAKS_FILE):
+        p = json.load(open(PEAKS_FILE))
+        return dict(hbm_gbs=p["hbm_gbs"], bf16=p["bf16_tflops"], bf16_sus=p["bf16_tflops_sustained"],
+                    src="measured")
+    return dict(hbm_gbs=6400.0, bf16=1800.0, bf16_sus=1400.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smax.append(float(f[2])); pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(busy)), "sm_max_mhz": max(smax),
+                "power_w_max": max(pw), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(disc, budget_s=20.0, t_span=None):
+    """The FP64 oracle on a bounded sample of cells of the same workload."""
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    t_span = disc.t_span if t_span is None else t_span
+    # a deterministic sample spread over the grid; grown until the budget is used
+    n = 4
+    total_sub, total_t, used = 0, 0.0, []
+    rng_cells = np.linspace(0, disc.n_cells - 1, 4096).astype(int)
+    while total_t < budget_s and n <= len(rng_cells):
+        cells = np.unique(rng_cells[np.linspace(0, len(rng_cells) - 1, n).astype(int)])
+        cells = np.setdiff1d(cells, used)
+        if len(cells) == 0:
+            break
+        sub = disc.subset(cells)
+        o = O.Oracle(sub, n_threads=cores)
+        t0 = time.perf_counter()
+        r = o.step(sub.rho0, t_span)
+        dt = time.perf_counter() - t0
+        total_sub += int(r["n_acc"].sum())
+        total_t += dt
+        used = np.concatenate([used, cells]).astype(int)
+        n *= 2
+    return {"value": total_sub / total_t, "unit": "cell-substeps/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{len(used)} of {disc.n_cells} cells spread over the grid, full "
+                      f"{t_span / synth.CONST['yr']:.0f} yr, {total_sub} accepted substeps in "
+                      f"{total_t:.1f} s, OpenMP over cells"}
+
+
+def run_reference(args, disc, rank, world):
+    if rank != 0:
+        return
+    cb = None
+    vals = []
+    for s in range(args.warmup + args.steps):
+        r = cpu_baseline(disc, budget_s=args.ref_budget)
+        if s >= args.warmup:
+            vals.append(r["value"])
+            cb = r
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cell-substeps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_cells": disc.n_cells, "n_bins": disc.n_bins,
+                       "t_span_yr": disc.t_span / synth.CONST["yr"],
+                       "note": "FP64 CPU oracle on a bounded cell sample per step"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "cell-substeps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="grid_128x64_N100", choices=list(WORKLOADS))
+    ap.add_argument("--t-span-yr", type=float, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-leg", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=10.0)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    disc = WORKLOADS[args.workload]()
+    if args.t_span_yr:
+        disc.t_span = args.t_span_yr * synth.CONST["yr"]
+
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, disc, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import torch
+    from paper_2402_18471_b300 import coag
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    stream = torch.cuda.current_stream()
+
+    def measure(precision, steps, warmup, with_e2e):
+        g = coag.Coag(disc, precision, stream=stream)
+        rho0 = g.state(disc.rho0)
+        rho = torch.empty_like(rho0)
+        dt = torch.zeros(disc.n_cells, dtype=torch.float64, device="cuda")
+
+        def one_step():
+            rho.copy_(rho0)
+            dt.zero_()
+            g.build_kernel()
+            return g.step(rho, disc.t_span, dt)
+
+        for _ in range(warmup):
+            one_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sub = 0
+        kern_ms = 0.0
+        launches = 0
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0.record(stream)
+            for _ in range(steps):
+                st = one_step()
+                sub += st["accepted"]
+                kern_ms += st["elapsed_ms"]
+                launches += 3 + 2 * ((disc.n_cells - 1) // 65535)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        res = dict(ms=ms, sub=sub, kern_ms=kern_ms, launches=launches, clocks=clk.summary(),
+                   last=st, g=g)
+        if with_e2e:
+            host_in = torch.from_numpy(np.ascontiguousarray(disc.rho0)).pin_memory()
+            host_out = torch.empty_like(host_in).pin_memory()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            esub = 0
+            for _ in range(steps):
+                rho.copy_(host_in, non_blocking=True)
+                dt.zero_()
+                g.build_kernel()
+                st = g.step(rho, disc.t_span, dt)
+                esub += st["accepted"]
+                host_out.copy_(rho, non_blocking=True)
+                torch.cuda.synchronize()
+            res["e2e_s"] = time.perf_counter() - t0
+            res["e2e_sub"] = esub
+            res["bytes"] = host_in.numel() * 8
+            res["check"] = host_out.numpy().copy()
+        return res
+
+    main_res = measure(args.precision, args.steps, args.warmup, True)
+    fp64_res = None
+    if args.precision == "mixed" and not args.no_fp64_leg:
+        fp64_res = measure("fp64", 1, 1, False)
+
+    # max over ranks of the timed region; units summed over ranks
+    ms = main_res["ms"]
+    sub = main_res["sub"]
+    if dist:
+        t = torch.tensor([ms, main_res.get("e2e_s", 0.0)], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_s = float(t[0]), float(t[1])
+        u = torch.tensor([float(sub), float(main_res.get("e2e_sub", 0))], device="cuda")
+        dist.all_reduce(u)
+        sub, e2e_sub = int(u[0]), int(u[1])
+    else:
+        e2e_s, e2e_sub = main_res["e2e_s"], main_res["e2e_sub"]
+
+    if rank == 0:
+        pk = peaks()
+        value = sub / (ms / 1e3)
+        N = disc.n_bins
+        Np = N * (N + 1) // 2
+        cell_sub_per_launch = main_res["last"]["accepted"]
+        kern_s = main_res["last"]["elapsed_ms"] / 1e3
+        if args.precision == "fp64":
+            # algorithmic FP64 flops per cell-substep: 3 right-hand sides of
+            # 2 flops x (3 products + 6 two-term entries) per pair + N^2 fragment spread
+            flops = 3 * (2 * 15 * Np + N * N)
+            achieved = cell_sub_per_launch * flops / kern_s / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
+                    "traffic": None, "kernel": "step64_kernel",
+                    "peak_src": "nominal FP64 rate of B300 (no measured FP64 peak)"}
+        else:
+            # tensor flops of the TF32 split contraction: 3 products x 2 x N x 2Np per RHS
+            flops = 3 * 3 * 2 * N * 2 * Np
+            achieved = cell_sub_per_launch * flops / kern_s / 1e12
+            peak_tf32 = pk["bf16_sus"] * TF32_OVER_BF16
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tf32, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tf32, "traffic": None, "kernel": "step_mixed_kernel",
+                    "peak_src": f"{pk['src']} sustained bf16 x nominal tf32/bf16 ratio"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-substeps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "tf32x3+f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_cells": disc.n_cells, "n_bins": N,
+                       "t_span_yr": disc.t_span / synth.CONST["yr"],
+                       "precision": args.precision, "rtol": disc.rtol, "atol_rel": disc.atol_rel,
+                       "l2": "K tables larger than L2 (FP32 331 MB / FP64 404 MB) are rebuilt every step",
+                       "step": "kernel build + BS3 integration of all cells over t_span"},
+            "ms_kernel_per_step": main_res["kern_ms"] / args.steps,
+            "accepted_per_step": main_res["last"]["accepted"],
+            "rejected_per_step": main_res["last"]["rejected"],
+            "mass_err_max": main_res["last"]["mass_err_max"],
+            "roofline": roof,
+            "clocks": main_res["clocks"],
+            "gpu_launches": main_res["launches"],
+            "e2e": {"value": e2e_sub / e2e_s, "unit": "cell-substeps/s",
+                    "h2d_bytes_per_step": main_res["bytes"], "d2h_bytes_per_step": main_res["bytes"]},
+        }
+        if fp64_res is not None:
+            v64 = fp64_res["sub"] / (fp64_res["ms"] / 1e3)
+            line["fp64_gpu"] = {"value": v64, "unit": "cell-substeps/s", "speedup_mixed_over_fp64": value / v64}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(disc, budget_s=args.cpu_budget)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * cudisc_coag.h -- C ABI of the B300 coagulation-fragmentation step.
+ *
+ * The library integrates, for every cell of an (R, Z) grid independently, the
+ * Smoluchowski equation in mass-density form (Sec. 5, Eq. smol of Robinson,
+ * Booth & Owen, "Introducing cuDisc", arXiv 2402.18471):
+ *
+ *   d rho_k / dt = sum_i sum_{j<=i} gain_ijk - sum_i m_k n_i n_k K_ik,
+ *
+ * with the collision kernel K_ij = pi (a_i + a_j)^2 dv_ij (Eq. kernel), the
+ * relative velocity dv^2 = v_BM^2 + v_turb^2 + dv_lam^2 (Brownian, Eq. vbrown;
+ * turbulent after Ormel & Cuzzi 2007, Eq. OCVrel; laminar drift/settling),
+ * the fragmentation probability of Eq. (p_frag), the two-bin split of
+ * coagulation products and remnants (Eqs. Cijk, Rijk, fragrem) and the
+ * power-law fragment distribution (Eqs. fragdist, Nijk), gathered per
+ * largest-fragment bin and then distributed.  Time integration is the
+ * Bogacki-Shampine 3(2) embedded pair with per-cell adaptive steps and the
+ * paper's tolerances (rtol 1e-2, atol 1e-10 x sum_k rho_k; Sec. 5, last
+ * paragraph).
+ *
+ * Conventions
+ *   - CGS units.  Cell c, bin k: dust densities are rho[c * N + k] (bins
+ *     contiguous).  N = n_bins, Np = N (N + 1) / 2 pairs.
+ *   - "device" arrays are CUDA global-memory pointers on the current device;
+ *     "host" arrays are ordinary CPU memory.  Every array passed in stays
+ *     owned by the caller; the library never frees it.  The context owns its
+ *     own device buffers (kernel tables, mapping tensors, workspace).
+ *   - Every call returns a cudisc_status; no call aborts or throws.  On an
+ *     error cudisc_coag_last_error(ctx) returns a message (NULL ctx: the last
+ *     error of the calling thread).
+ *   - Work is issued on params.stream (NULL: the legacy default stream).
+ *     cudisc_coag_rhs is asynchronous.  cudisc_coag_step,
+ *     cudisc_coag_build_kernel and cudisc_coag_vjp synchronise that stream
+ *     before returning so they can report per-cell failures.
+ */
+#ifndef CUDISC_COAG_H
+#define CUDISC_COAG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cudisc_coag_ctx cudisc_coag_ctx;   /* opaque, owned by the library */
+
+typedef enum {
+    CUDISC_OK = 0,
+    CUDISC_EINVAL = 1,      /* bad argument: the message names it */
+    CUDISC_ENOMEM = 2,      /* a device or host allocation failed */
+    CUDISC_ECUDA = 3,       /* a CUDA runtime error (message has the CUDA text) */
+    CUDISC_EMAXSTEPS = 4,   /* some cell hit max_substeps before t_span */
+    CUDISC_ENONFINITE = 5,  /* some cell produced a non-finite state */
+    CUDISC_ENOTSUP = 6,     /* size or mode outside what this build supports */
+    CUDISC_EDTMIN = 7       /* some cell's step shrank below 1e-14 t_span */
+} cudisc_status;
+
+typedef enum {
+    CUDISC_FP64 = 0,        /* FP64 everywhere: sparse gather on CUDA cores */
+    CUDISC_MIXED_TF32 = 1   /* gain/loss contraction on tcgen05 tensor cores with
+                               TF32 hi+lo split operands (3 products), FP32
+                               accumulation in TMEM, FP64 state, mass budget
+                               and step control */
+} cudisc_precision;
+
+typedef enum {
+    CUDISC_KERNEL_PHYSICAL = 0,  /* K = pi (a_i + a_j)^2 dv (Eq. kernel) */
+    CUDISC_KERNEL_CONSTANT = 1,  /* K = kernel_const (closed-form tests) */
+    CUDISC_KERNEL_ADDITIVE = 2   /* K = kernel_const (m_i + m_j) */
+} cudisc_kernel_mode;
+
+typedef enum {
+    CUDISC_FRAG_PHYSICAL = 0,    /* p_frag from Eq. (p_frag) */
+    CUDISC_FRAG_NONE = 1,        /* p_frag = 0 */
+    CUDISC_FRAG_ALL = 2          /* p_frag = 1 */
+} cudisc_frag_mode;
+
+typedef enum {
+    CUDISC_SPLIT_MASS = 0,       /* C_ijk, R_ijk = eps, 1 - eps as mass fractions */
+    CUDISC_SPLIT_NUMBER = 1      /* eps as the number fraction (conserves number) */
+} cudisc_split_mode;
+
+typedef struct {
+    int n_cells;                 /* >= 1 */
+    int n_bins;                  /* N, 2 <= N <= 160 */
+    const double *mass_centres;  /* host [N], strictly increasing, g */
+    const double *mass_edges;    /* host [N+1], strictly increasing,
+                                    edge k < centre k < edge k+1, g */
+    const double *rho_gas;       /* device [n_cells], g cm^-3 */
+    const double *T;             /* device [n_cells], K */
+    const double *alpha;         /* device [n_cells], turbulence parameter */
+    const double *R;             /* device [n_cells], cylindrical radius, cm */
+    const double *Z;             /* device [n_cells], height, cm */
+    const double *eta;           /* device [n_cells] drift parameter, or NULL:
+                                    no radial/azimuthal drift */
+    const double *v_dust;        /* device [3][n_cells][N] (v_R, v_phi, v_Z) dust
+                                    velocities, or NULL: terminal velocities from
+                                    St, eta and Z */
+    double v_frag;               /* fragmentation velocity, cm/s */
+    double eta_frag;             /* fragment power law n(m) ~ m^-eta (11/6) */
+    double chi_im;               /* impactor excavation factor (1) */
+    double rho_m;                /* grain material density (1.6) */
+    double mu;                   /* mean molecular weight (2.4) */
+    double Mstar;                /* stellar mass, g */
+    double k_B, m_H, G, sigma_H2;/* constants; sigma_H2 sets nu_mol */
+    double kernel_const;         /* for CONSTANT / ADDITIVE kernels */
+    int kernel_mode;             /* cudisc_kernel_mode */
+    int frag_mode;               /* cudisc_frag_mode */
+    int split_mode;              /* cudisc_split_mode */
+    int precision;               /* cudisc_precision */
+    double rtol;                 /* relative tolerance (1e-2) */
+    double atol_rel;             /* absolute tolerance / sum_k rho_k (1e-10) */
+    long long max_substeps;      /* per cell, accepted + rejected attempts */
+    void *stream;                /* cudaStream_t, NULL = legacy default stream */
+} cudisc_coag_params;
+
+typedef struct {
+    long long accepted;          /* accepted substeps summed over cells */
+    long long rejected;          /* rejected attempts summed over cells */
+    long long max_accepted;      /* largest per-cell accepted count */
+    int n_failed;                /* cells whose status is not CUDISC_OK */
+    int worst_status;            /* largest per-cell status code */
+    double mass_err_max;         /* max_c |sum_k rho'_ck / sum_k rho_ck - 1| */
+    double elapsed_ms;           /* device time of the integration kernel */
+} cudisc_step_stats;
+
+/* Create a context: validates params (EINVAL on any inconsistency, naming the
+ * field), builds the mapping tensors of Eqs. (Cijk), (Rijk), (fragrem) and
+ * (Nijk) on the host in FP64, uploads them, allocates the workspace, and
+ * builds K and p_frag from the gas arrays (as cudisc_coag_build_kernel).
+ * The device pointers in params must stay valid for the context's life. */
+cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx **out);
+
+/* Rebuild the per-cell collision kernel K_ij and K_ij p_frag,ij (Sec. 5,
+ * Eqs. kernel, vbrown, OCVrel, p_frag) from the current contents of the gas
+ * arrays named at init (call after the caller changes them). */
+cudisc_status cudisc_coag_build_kernel(cudisc_coag_ctx *ctx);
+
+/* Copy the kernel tables out for inspection: K_out and KF_out are device
+ * [n_cells][Np] FP64, pair p = i (i + 1) / 2 + j for j <= i, holding K_ij and
+ * K_ij p_frag,ij as stored by the context (FP32 values widened in the mixed
+ * precision). */
+cudisc_status cudisc_coag_get_kernel(cudisc_coag_ctx *ctx, double *K_out, double *KF_out);
+
+/* Right-hand side of Eq. (smol): drho_dt[c][k] for the state rho[c][k]
+ * (device, [n_cells][N], FP64 in and out).  Asynchronous on the stream. */
+cudisc_status cudisc_coag_rhs(cudisc_coag_ctx *ctx, const double *rho, double *drho_dt);
+
+/* Integrate every cell over t_span seconds with BS3 3(2) (Sec. 5).
+ * rho (device [n_cells][N]) is read and overwritten with the result.
+ * dt_cell (device [n_cells], FP64, may be NULL): on entry the first step per
+ * cell (<= 0: automatic), on exit the last proposed step.  stats (host, may
+ * be NULL) receives totals.  Returns the worst per-cell status. */
+cudisc_status cudisc_coag_step(cudisc_coag_ctx *ctx, double *rho, double t_span,
+                               double *dt_cell, cudisc_step_stats *stats);
+
+/* Optional per-cell records for later cudisc_coag_step calls (all device
+ * pointers; pass NULLs to stop recording):
+ *   dt_log [n_cells][log_cap] accepted step sizes in order,
+ *   n_log  [n_cells] int64 number of accepted steps (may exceed log_cap:
+ *          only the first log_cap are stored),
+ *   status [n_cells] int32 per-cell status. */
+cudisc_status cudisc_coag_set_records(cudisc_coag_ctx *ctx, double *dt_log,
+                                      long long log_cap, long long *n_log,
+                                      int *status);
+
+/* Fixed-step replay: apply per-cell sequences of BS3 steps without error
+ * control (hs [n_cells][stride] device FP64, n_h [n_cells] device int64).
+ * Used to compare precisions on one step sequence. */
+cudisc_status cudisc_coag_replay(cudisc_coag_ctx *ctx, double *rho, const double *hs,
+                                 const long long *n_h, long long stride);
+
+void cudisc_coag_destroy(cudisc_coag_ctx *ctx);
+
+/* Message of the last failed call on ctx (or of this thread when ctx is
+ * NULL); never NULL, "" when there was no error. */
+const char *cudisc_coag_last_error(const cudisc_coag_ctx *ctx);
+
+/* Library version string. */
+const char *cudisc_coag_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUDISC_COAG_H */

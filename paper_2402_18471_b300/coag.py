@@ -1,0 +1,242 @@
+"""Thin Python binding of the C ABI in include/cudisc_coag.h.
+
+Argument marshalling only: every step of the coagulation update runs in the
+CUDA library libcudisc_coag.so.  PyTorch provides device memory and streams.
+If the library cannot be loaded the binding raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+OK, EINVAL, ENOMEM, ECUDA, EMAXSTEPS, ENONFINITE, ENOTSUP, EDTMIN = range(8)
+FP64, MIXED_TF32 = 0, 1
+PRECISIONS = {"fp64": FP64, "mixed": MIXED_TF32, "mixed_tf32": MIXED_TF32}
+
+
+class CoagError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cudisc status {status}: {msg}")
+        self.status = status
+
+
+class cudisc_coag_params(C.Structure):
+    _fields_ = [
+        ("n_cells", C.c_int), ("n_bins", C.c_int),
+        ("mass_centres", C.c_void_p), ("mass_edges", C.c_void_p),
+        ("rho_gas", C.c_void_p), ("T", C.c_void_p), ("alpha", C.c_void_p),
+        ("R", C.c_void_p), ("Z", C.c_void_p), ("eta", C.c_void_p), ("v_dust", C.c_void_p),
+        ("v_frag", C.c_double), ("eta_frag", C.c_double), ("chi_im", C.c_double),
+        ("rho_m", C.c_double), ("mu", C.c_double), ("Mstar", C.c_double),
+        ("k_B", C.c_double), ("m_H", C.c_double), ("G", C.c_double), ("sigma_H2", C.c_double),
+        ("kernel_const", C.c_double),
+        ("kernel_mode", C.c_int), ("frag_mode", C.c_int), ("split_mode", C.c_int),
+        ("precision", C.c_int),
+        ("rtol", C.c_double), ("atol_rel", C.c_double),
+        ("max_substeps", C.c_longlong),
+        ("stream", C.c_void_p),
+    ]
+
+
+class cudisc_step_stats(C.Structure):
+    _fields_ = [
+        ("accepted", C.c_longlong), ("rejected", C.c_longlong),
+        ("max_accepted", C.c_longlong), ("n_failed", C.c_int), ("worst_status", C.c_int),
+        ("mass_err_max", C.c_double), ("elapsed_ms", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libcudisc_coag.so (building it with nvcc when missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libcudisc_coag.so is missing and could not be built")
+        L = C.CDLL(path)
+        v, d = C.c_void_p, C.c_double
+        L.cudisc_coag_init.argtypes = [C.POINTER(cudisc_coag_params), C.POINTER(v)]
+        L.cudisc_coag_build_kernel.argtypes = [v]
+        L.cudisc_coag_get_kernel.argtypes = [v, v, v]
+        L.cudisc_coag_rhs.argtypes = [v, v, v]
+        L.cudisc_coag_step.argtypes = [v, v, d, v, C.POINTER(cudisc_step_stats)]
+        L.cudisc_coag_set_records.argtypes = [v, v, C.c_longlong, v, v]
+        L.cudisc_coag_replay.argtypes = [v, v, v, v, C.c_longlong]
+        L.cudisc_coag_destroy.argtypes = [v]
+        L.cudisc_coag_destroy.restype = None
+        L.cudisc_coag_last_error.argtypes = [v]
+        L.cudisc_coag_last_error.restype = C.c_char_p
+        L.cudisc_coag_version.restype = C.c_char_p
+        for fn in ("cudisc_coag_init", "cudisc_coag_build_kernel", "cudisc_coag_get_kernel",
+                   "cudisc_coag_rhs", "cudisc_coag_step", "cudisc_coag_set_records",
+                   "cudisc_coag_replay"):
+            getattr(L, fn).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st: int, ctx=None):
+    if st != OK:
+        msg = lib().cudisc_coag_last_error(ctx).decode()
+        raise CoagError(st, msg)
+
+
+# ---- the ABI calls, same names -------------------------------------------
+
+def cudisc_coag_init(params: cudisc_coag_params):
+    h = C.c_void_p()
+    _check(lib().cudisc_coag_init(C.byref(params), C.byref(h)))
+    return h
+
+
+def cudisc_coag_build_kernel(ctx):
+    _check(lib().cudisc_coag_build_kernel(ctx), ctx)
+
+
+def cudisc_coag_get_kernel(ctx, K_ptr, KF_ptr):
+    _check(lib().cudisc_coag_get_kernel(ctx, K_ptr, KF_ptr), ctx)
+
+
+def cudisc_coag_rhs(ctx, rho_ptr, drho_ptr):
+    _check(lib().cudisc_coag_rhs(ctx, rho_ptr, drho_ptr), ctx)
+
+
+def cudisc_coag_step(ctx, rho_ptr, t_span, dt_ptr, check=True):
+    s = cudisc_step_stats()
+    st = lib().cudisc_coag_step(ctx, rho_ptr, float(t_span), dt_ptr, C.byref(s))
+    if check:
+        _check(st, ctx)
+    return st, s
+
+
+def cudisc_coag_set_records(ctx, dt_ptr, cap, n_ptr, status_ptr):
+    _check(lib().cudisc_coag_set_records(ctx, dt_ptr, int(cap), n_ptr, status_ptr), ctx)
+
+
+def cudisc_coag_replay(ctx, rho_ptr, hs_ptr, n_ptr, stride):
+    _check(lib().cudisc_coag_replay(ctx, rho_ptr, hs_ptr, n_ptr, int(stride)), ctx)
+
+
+def cudisc_coag_destroy(ctx):
+    lib().cudisc_coag_destroy(ctx)
+
+
+def cudisc_coag_version() -> str:
+    return lib().cudisc_coag_version().decode()
+
+
+# ---- convenience wrapper over one synthetic disc ---------------------------
+
+class Coag:
+    """A context bound to one disc.  Gas arrays are copied to the device once;
+    dust states are torch float64 CUDA tensors of shape [n_cells, N]."""
+
+    def __init__(self, disc, precision: str = "fp64", device: str = "cuda", stream=None,
+                 use_v_dust: bool = True, **over):
+        import torch
+        self.torch = torch
+        self.disc = disc
+        self.device = torch.device(device)
+        self.N = disc.n_bins
+        self.n_cells = disc.n_cells
+        self.Np = self.N * (self.N + 1) // 2
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        s = disc.scalars()
+        s.update(over)
+        dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=self.device)
+        self._keep = {k: dev(getattr(disc, k)) for k in ("rho_gas", "T", "alpha", "R", "Z", "eta")}
+        if use_v_dust and disc.v_dust is not None:
+            self._keep["v_dust"] = dev(disc.v_dust)
+        self._m = np.ascontiguousarray(disc.m, dtype=np.float64)
+        self._me = np.ascontiguousarray(disc.me, dtype=np.float64)
+        p = cudisc_coag_params()
+        p.n_cells, p.n_bins = self.n_cells, self.N
+        p.mass_centres = self._m.ctypes.data
+        p.mass_edges = self._me.ctypes.data
+        for k in ("rho_gas", "T", "alpha", "R", "Z", "eta"):
+            setattr(p, k, self._keep[k].data_ptr())
+        p.v_dust = self._keep["v_dust"].data_ptr() if "v_dust" in self._keep else None
+        for k in ("v_frag", "eta_frag", "chi_im", "rho_m", "mu", "Mstar", "k_B", "m_H", "G",
+                  "sigma_H2", "kernel_const", "rtol", "atol_rel"):
+            setattr(p, k, float(s[k]))
+        for k in ("kernel_mode", "frag_mode", "split_mode"):
+            setattr(p, k, int(s[k]))
+        p.precision = self.precision
+        p.max_substeps = int(s["max_substeps"])
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        p.stream = self.stream.cuda_stream
+        self.params = p
+        self.ctx = cudisc_coag_init(p)
+        self._rec = None
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            cudisc_coag_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def state(self, rho):
+        return self.torch.as_tensor(np.ascontiguousarray(rho, dtype=np.float64), device=self.device)
+
+    def build_kernel(self):
+        cudisc_coag_build_kernel(self.ctx)
+
+    def get_kernel(self):
+        t = self.torch
+        K = t.empty((self.n_cells, self.Np), dtype=t.float64, device=self.device)
+        KF = t.empty_like(K)
+        cudisc_coag_get_kernel(self.ctx, K.data_ptr(), KF.data_ptr())
+        return K, KF
+
+    def rhs(self, rho):
+        rho = rho.contiguous()
+        out = self.torch.empty_like(rho)
+        cudisc_coag_rhs(self.ctx, rho.data_ptr(), out.data_ptr())
+        return out
+
+    def set_records(self, log_cap: int):
+        t = self.torch
+        if log_cap <= 0:
+            cudisc_coag_set_records(self.ctx, None, 0, None, None)
+            self._rec = None
+            return None
+        self._rec = dict(
+            dt=t.zeros((self.n_cells, log_cap), dtype=t.float64, device=self.device),
+            n=t.zeros(self.n_cells, dtype=t.int64, device=self.device),
+            status=t.zeros(self.n_cells, dtype=t.int32, device=self.device))
+        cudisc_coag_set_records(self.ctx, self._rec["dt"].data_ptr(), log_cap,
+                                self._rec["n"].data_ptr(), self._rec["status"].data_ptr())
+        return self._rec
+
+    def step(self, rho, t_span, dt=None, check=True):
+        """Integrate rho (in place) over t_span; returns the stats dict."""
+        assert rho.is_contiguous() and rho.dtype == self.torch.float64
+        st, s = cudisc_coag_step(self.ctx, rho.data_ptr(), t_span,
+                                 dt.data_ptr() if dt is not None else None, check=check)
+        d = s.as_dict()
+        d["status"] = st
+        return d
+
+    def replay(self, rho, hs, n_h):
+        assert rho.is_contiguous()
+        hs = hs.contiguous()
+        n_h = n_h.contiguous().to(self.torch.int64)
+        cudisc_coag_replay(self.ctx, rho.data_ptr(), hs.data_ptr(), n_h.data_ptr(), hs.shape[1])

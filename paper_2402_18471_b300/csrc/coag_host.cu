@@ -1,0 +1,480 @@
+// Host side of the C ABI: validation, the FP64 mapping-tensor builder
+// (Sec. 5, Eqs. Cijk, Rijk, fragrem, fragdist, Nijk), device tables and the
+// dispatch to the FP64 and mixed-precision kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "coag_internal.h"
+
+using cdc::CellOut;
+
+namespace {
+
+thread_local std::string g_thread_err;
+
+cudisc_status fail(cudisc_coag_ctx *c, cudisc_status st, const std::string &msg)
+{
+    if (c) c->err = msg;
+    g_thread_err = msg;
+    return st;
+}
+
+cudisc_status cuda_fail(cudisc_coag_ctx *c, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    cudisc_status st = (e == cudaErrorMemoryAllocation) ? CUDISC_ENOMEM : CUDISC_ECUDA;
+    return fail(c, st, m);
+}
+
+#define CUDA_TRY(ctx, expr)                                   \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
+    } while (0)
+
+template <class T>
+cudaError_t upload(T **dst, const std::vector<T> &src, cudaStream_t s)
+{
+    size_t n = src.size() ? src.size() : 1;
+    cudaError_t e = cudaMalloc((void **)dst, n * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (src.empty()) return cudaSuccess;
+    e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+// Two-bin split of a product mass: lower bin l = max{k : m_k <= mass},
+// u = l + 1, eps = (m_u - mass) / (m_u - m_l); an exact hit is all in l;
+// outside the grid the whole mass goes to the end bin.  Returns mass
+// fractions (mode 0: eps, 1 - eps; mode 1: eps and 1 - eps as number
+// fractions, converted to mass fractions).
+void two_bin(const std::vector<double> &m, double mass, int mode, int &kl, int &ku,
+             double &fl, double &fu)
+{
+    const int N = (int)m.size();
+    if (mass >= m[N - 1]) { kl = ku = N - 1; fl = 1.0; fu = 0.0; return; }
+    if (mass <= m[0]) { kl = ku = 0; fl = 1.0; fu = 0.0; return; }
+    int lo = 0, hi = N - 1;               // m[lo] <= mass < m[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (m[mid] <= mass) lo = mid; else hi = mid;
+    }
+    kl = lo; ku = lo + 1;
+    double eps = (m[ku] - mass) / (m[ku] - m[kl]);
+    if (mode == CUDISC_SPLIT_NUMBER) {
+        fl = eps * m[kl] / mass;
+        fu = (1.0 - eps) * m[ku] / mass;
+    } else {
+        fl = eps;
+        fu = 1.0 - eps;
+    }
+}
+
+// Mass fraction of fragments in bin k when the largest fragment fills bin l:
+// integral of m n(m) dm with n ~ m^-eta over bin k, normalised over bins 0..l.
+double frag_share(const std::vector<double> &me, double eta, int k, int l)
+{
+    double s = 2.0 - eta;
+    if (std::fabs(s) < 1e-12)
+        return std::log(me[k + 1] / me[k]) / std::log(me[l + 1] / me[0]);
+    double lo = std::pow(me[0], s);
+    return (std::pow(me[k + 1], s) - std::pow(me[k], s)) / (std::pow(me[l + 1], s) - lo);
+}
+
+uint32_t tf32_trunc_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return u & 0xFFFFE000u;
+}
+
+float bits_f(uint32_t u) { float f; std::memcpy(&f, &u, 4); return f; }
+
+} // namespace
+
+cdc::DevTables cudisc_coag_ctx::tables() const
+{
+    cdc::DevTables t;
+    t.N = N; t.Np = Np; t.n_cells = n_cells;
+    t.m = d_m; t.minv = d_minv; t.a = d_a; t.me = d_me;
+    t.pair_ij = d_pair_ij;
+    t.row = d_row; t.ent_p = d_ent_p; t.ent_ab = d_ent_ab;
+    t.frow = d_frow; t.fent_p = d_fent_p; t.fent_m = d_fent_m;
+    t.Ntab = d_Ntab;
+    t.n_blk = n_blk; t.blk_i = d_blk_i; t.blk_j0 = d_blk_j0;
+    t.Btiles = d_Btiles;
+    return t;
+}
+
+static cudisc_status validate(const cudisc_coag_params *p, std::string &why)
+{
+    if (!p) { why = "params is NULL"; return CUDISC_EINVAL; }
+    if (p->n_cells < 1) { why = "n_cells must be >= 1"; return CUDISC_EINVAL; }
+    if (p->n_bins < 2) { why = "n_bins must be >= 2"; return CUDISC_EINVAL; }
+    if (p->n_bins > cdc::kMaxBins) {
+        why = "n_bins > 160 is not supported by this build";
+        return CUDISC_ENOTSUP;
+    }
+    if (p->precision == CUDISC_MIXED_TF32 && p->n_bins > cdc::kMBins) {
+        why = "the mixed precision path supports n_bins <= 128";
+        return CUDISC_ENOTSUP;
+    }
+    if (p->precision != CUDISC_FP64 && p->precision != CUDISC_MIXED_TF32) {
+        why = "precision must be CUDISC_FP64 or CUDISC_MIXED_TF32";
+        return CUDISC_EINVAL;
+    }
+    if (!p->mass_centres || !p->mass_edges) { why = "mass_centres / mass_edges are NULL"; return CUDISC_EINVAL; }
+    if (!p->rho_gas || !p->T || !p->alpha || !p->R || !p->Z) {
+        why = "rho_gas, T, alpha, R and Z must be device arrays";
+        return CUDISC_EINVAL;
+    }
+    const int N = p->n_bins;
+    for (int k = 0; k < N; k++) {
+        double c = p->mass_centres[k];
+        if (!(c > 0.0) || !std::isfinite(c)) { why = "mass_centres must be positive and finite"; return CUDISC_EINVAL; }
+        if (k && !(c > p->mass_centres[k - 1])) { why = "mass_centres must be strictly increasing"; return CUDISC_EINVAL; }
+        if (!(p->mass_edges[k] < c && c < p->mass_edges[k + 1])) {
+            why = "mass_edges must bracket every centre: edge k < centre k < edge k+1";
+            return CUDISC_EINVAL;
+        }
+    }
+    if (!(p->mass_edges[0] > 0.0)) { why = "mass_edges[0] must be positive"; return CUDISC_EINVAL; }
+    if (p->kernel_mode < 0 || p->kernel_mode > 2) { why = "kernel_mode out of range"; return CUDISC_EINVAL; }
+    if (p->frag_mode < 0 || p->frag_mode > 2) { why = "frag_mode out of range"; return CUDISC_EINVAL; }
+    if (p->split_mode < 0 || p->split_mode > 1) { why = "split_mode out of range"; return CUDISC_EINVAL; }
+    if (!(p->rtol > 0.0) || !(p->atol_rel >= 0.0)) { why = "rtol must be > 0 and atol_rel >= 0"; return CUDISC_EINVAL; }
+    if (p->max_substeps < 1) { why = "max_substeps must be >= 1"; return CUDISC_EINVAL; }
+    if (!(p->rho_m > 0) || !(p->mu > 0) || !(p->Mstar > 0) || !(p->k_B > 0) || !(p->m_H > 0) ||
+        !(p->G > 0) || !(p->sigma_H2 > 0)) {
+        why = "rho_m, mu, Mstar, k_B, m_H, G and sigma_H2 must be positive";
+        return CUDISC_EINVAL;
+    }
+    if (p->frag_mode == CUDISC_FRAG_PHYSICAL && !(p->v_frag > 0)) { why = "v_frag must be positive"; return CUDISC_EINVAL; }
+    if (!(p->chi_im > 0)) { why = "chi_im must be positive"; return CUDISC_EINVAL; }
+    return CUDISC_OK;
+}
+
+// Build every per-grid table on the host (FP64) and upload it.
+static cudisc_status build_tables(cudisc_coag_ctx *c)
+{
+    const cudisc_coag_params &p = c->p;
+    const int N = c->N;
+    const std::vector<double> &m = c->h_m, &me = c->h_me;
+    std::vector<double> minv(N), a(N);
+    for (int k = 0; k < N; k++) {
+        minv[k] = 1.0 / m[k];
+        a[k] = std::cbrt(3.0 * m[k] / (4.0 * M_PI * p.rho_m));
+    }
+    // packed pairs p = i (i + 1) / 2 + j
+    std::vector<unsigned int> pij(c->Np);
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j <= i; j++) pij[i * (i + 1) / 2 + j] = ((unsigned)i << 16) | (unsigned)j;
+
+    // fragment distribution table N_k(m^e_{l+1})
+    std::vector<double> Ntab((size_t)N * N, 0.0);
+    for (int l = 0; l < N; l++)
+        for (int k = 0; k <= l; k++) Ntab[(size_t)l * N + k] = frag_share(me, p.eta_frag, k, l);
+
+    // per-pair row of the redistribution, per unit n_i n_j K (1/2 at i = j):
+    //   alpha_k: coagulation gain minus the loss of both grains,
+    //   beta_k : remnant gain minus the coagulation gain (the part p_frag moves),
+    //   Mf at l: fragment mass gathered per largest-fragment bin.
+    // All coefficients are divided by m_i m_j so that they multiply rho_i rho_j K.
+    std::vector<std::vector<std::pair<int, double2>>> rows(N);
+    std::vector<std::vector<std::pair<int, double>>> frows(N);
+    // mixed path dense tile image: per block b, hi then lo, 128 rows x 32 floats
+    c->n_blk = 0;
+    std::vector<int> blk_i, blk_j0;
+    for (int i = 0; i < N; i++)
+        for (int j0 = 0; j0 <= i; j0 += cdc::kBlkPairs) { blk_i.push_back(i); blk_j0.push_back(j0); }
+    c->n_blk = (int)blk_i.size();
+    const bool mixed = p.precision == CUDISC_MIXED_TF32;
+    std::vector<float> tiles;
+    if (mixed) tiles.assign((size_t)c->n_blk * 2 * cdc::kMBins * cdc::kBlkElems, 0.0f);
+
+    std::vector<double> colA(N), colB(N);
+    int blk = 0;
+    for (int i = 0; i < N; i++) {
+        for (int j = 0; j <= i; j++) {
+            const int pp = i * (i + 1) / 2 + j;
+            const double h = (i == j) ? 0.5 : 1.0;
+            const double w = h / (m[i] * m[j]);
+            const double M = m[i] + m[j];
+            std::fill(colA.begin(), colA.end(), 0.0);
+            std::fill(colB.begin(), colB.end(), 0.0);
+            int kl, ku; double fl, fu;
+            two_bin(m, M, p.split_mode, kl, ku, fl, fu);
+            colA[kl] += M * fl; colA[ku] += M * fu;
+            colB[kl] -= M * fl; colB[ku] -= M * fu;
+            colA[i] -= m[i]; colA[j] -= m[j];
+            const double mtar = m[i] >= m[j] ? m[i] : m[j];
+            const double mim = m[i] >= m[j] ? m[j] : m[i];
+            const double cm = p.chi_im * mim;
+            const double mrem = (cm < mtar) ? (mtar - cm) : 0.0;
+            const double mx = (cm < mtar) ? cm : mtar;
+            if (mrem > 0.0) {
+                two_bin(m, mrem, p.split_mode, kl, ku, fl, fu);
+                colB[kl] += mrem * fl; colB[ku] += mrem * fu;
+            }
+            const double Mf = M - mrem;
+            // largest-fragment bin: smallest l with me[l+1] > mx
+            int l = N - 1;
+            {
+                int lo = 0, hi = N - 1;
+                if (me[N] > mx) {
+                    while (lo < hi) {
+                        int mid = (lo + hi) / 2;
+                        if (me[mid + 1] > mx) hi = mid; else lo = mid + 1;
+                    }
+                    l = lo;
+                }
+            }
+            for (int k = 0; k < N; k++) {
+                if (colA[k] != 0.0 || colB[k] != 0.0)
+                    rows[k].push_back({pp, make_double2(colA[k] * w, colB[k] * w)});
+            }
+            frows[l].push_back({pp, Mf * w});
+            if (mixed) {
+                // dense column of the contraction: fragments folded in directly
+                const int jb = j / cdc::kBlkPairs;
+                const int b = blk + jb;
+                const int t = j - jb * cdc::kBlkPairs;
+                for (int k = 0; k < N; k++) {
+                    double va = colA[k] * w;
+                    double vb = colB[k] * w + (k <= l ? Mf * w * Ntab[(size_t)l * N + k] : 0.0);
+                    for (int s = 0; s < 2; s++) {
+                        double v = s == 0 ? va : vb;
+                        int e = 2 * t + s;                       // element in the row
+                        float f = (float)v;
+                        uint32_t hb = tf32_trunc_bits(f);
+                        float hi = bits_f(hb);
+                        float lo = (float)(v - (double)hi);
+                        int chunk = e >> 2;
+                        size_t off = (size_t)k * 32 + (size_t)(((chunk ^ (k & 7)) << 2) | (e & 3));
+                        size_t base = (size_t)b * 2 * cdc::kMBins * 32;
+                        tiles[base + off] = hi;
+                        tiles[base + (size_t)cdc::kMBins * 32 + off] = lo;
+                    }
+                }
+            }
+        }
+        blk += (i + cdc::kBlkPairs) / cdc::kBlkPairs;
+    }
+    // CSR
+    std::vector<int> row(N + 1, 0), ent_p, frow(N + 1, 0), fent_p;
+    std::vector<double2> ent_ab;
+    std::vector<double> fent_m;
+    for (int k = 0; k < N; k++) {
+        row[k] = (int)ent_p.size();
+        for (auto &e : rows[k]) { ent_p.push_back(e.first); ent_ab.push_back(e.second); }
+        frow[k] = (int)fent_p.size();
+        for (auto &e : frows[k]) { fent_p.push_back(e.first); fent_m.push_back(e.second); }
+    }
+    row[N] = (int)ent_p.size();
+    frow[N] = (int)fent_p.size();
+
+    cudaStream_t s = c->stream;
+    CUDA_TRY(c, upload(&c->d_m, m, s));
+    CUDA_TRY(c, upload(&c->d_minv, minv, s));
+    CUDA_TRY(c, upload(&c->d_a, a, s));
+    CUDA_TRY(c, upload(&c->d_me, me, s));
+    CUDA_TRY(c, upload(&c->d_pair_ij, pij, s));
+    CUDA_TRY(c, upload(&c->d_row, row, s));
+    CUDA_TRY(c, upload(&c->d_ent_p, ent_p, s));
+    CUDA_TRY(c, upload(&c->d_ent_ab, ent_ab, s));
+    CUDA_TRY(c, upload(&c->d_frow, frow, s));
+    CUDA_TRY(c, upload(&c->d_fent_p, fent_p, s));
+    CUDA_TRY(c, upload(&c->d_fent_m, fent_m, s));
+    CUDA_TRY(c, upload(&c->d_Ntab, Ntab, s));
+    CUDA_TRY(c, upload(&c->d_blk_i, blk_i, s));
+    CUDA_TRY(c, upload(&c->d_blk_j0, blk_j0, s));
+    if (mixed) {
+        std::vector<float4> t4(tiles.size() / 4);
+        std::memcpy(t4.data(), tiles.data(), tiles.size() * sizeof(float));
+        CUDA_TRY(c, upload(&c->d_Btiles, t4, s));
+    }
+    return CUDISC_OK;
+}
+
+static void free_ctx(cudisc_coag_ctx *c)
+{
+    if (!c) return;
+    void *ptrs[] = {c->d_m, c->d_minv, c->d_a, c->d_me, c->d_pair_ij, c->d_row, c->d_ent_p,
+                    c->d_ent_ab, c->d_frow, c->d_fent_p, c->d_fent_m, c->d_Ntab, c->d_blk_i,
+                    c->d_blk_j0, c->d_Btiles, c->d_prep, c->d_prep32, c->d_scal, c->d_K64,
+                    c->d_K32, c->d_out, c->d_work, c->d_counter};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+}
+
+extern "C" {
+
+const char *cudisc_coag_version(void) { return "cudisc-coag-b300 0.1 (sm_103a)"; }
+
+const char *cudisc_coag_last_error(const cudisc_coag_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_thread_err.c_str();
+}
+
+cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx **out)
+{
+    g_thread_err.clear();
+    if (!out) return fail(nullptr, CUDISC_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    cudisc_status st = validate(params, why);
+    if (st != CUDISC_OK) return fail(nullptr, st, why);
+    cudisc_coag_ctx *c = new cudisc_coag_ctx();
+    c->p = *params;
+    c->stream = (cudaStream_t)params->stream;
+    c->N = params->n_bins;
+    c->Np = c->N * (c->N + 1) / 2;
+    c->n_cells = params->n_cells;
+    c->h_m.assign(params->mass_centres, params->mass_centres + c->N);
+    c->h_me.assign(params->mass_edges, params->mass_edges + c->N + 1);
+    // the stored pointers to host mass arrays are not kept
+    c->p.mass_centres = nullptr;
+    c->p.mass_edges = nullptr;
+    st = build_tables(c);
+    if (st != CUDISC_OK) { g_thread_err = c->err; free_ctx(c); return st; }
+    const size_t nc = (size_t)c->n_cells, N = (size_t)c->N;
+    cudaError_t e;
+    e = cudaMalloc(&c->d_prep, nc * cdc::PF_COUNT * N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_prep32, nc * cdc::PF_COUNT * N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_scal, nc * sizeof(cdc::CellScal));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_out, nc * sizeof(CellOut));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, 64 * sizeof(int));
+    if (e == cudaSuccess) {
+        if (params->precision == CUDISC_FP64)
+            e = cudaMalloc(&c->d_K64, nc * (size_t)c->Np * sizeof(double2));
+        else
+            e = cudaMalloc(&c->d_K32, nc * (size_t)c->n_blk * cdc::kBlkPairs * sizeof(float2));
+    }
+    if (e == cudaSuccess && params->precision == CUDISC_MIXED_TF32) {
+        c->work_bytes = cdc::mixed_workspace_bytes(c->n_cells, c->N);
+        e = cudaMalloc(&c->d_work, c->work_bytes);
+    }
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e != cudaSuccess) {
+        cuda_fail(c, e, "cudisc_coag_init: workspace allocation");
+        st = (e == cudaErrorMemoryAllocation) ? CUDISC_ENOMEM : CUDISC_ECUDA;
+        free_ctx(c);
+        return st;
+    }
+    st = cudisc_coag_build_kernel(c);
+    if (st != CUDISC_OK) { g_thread_err = c->err; free_ctx(c); return st; }
+    *out = c;
+    return CUDISC_OK;
+}
+
+void cudisc_coag_destroy(cudisc_coag_ctx *ctx) { free_ctx(ctx); }
+
+cudisc_status cudisc_coag_build_kernel(cudisc_coag_ctx *c)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    CUDA_TRY(c, cdc::launch_prep(c));
+    CUDA_TRY(c, cdc::launch_kbuild(c));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_coag_get_kernel(cudisc_coag_ctx *c, double *K_out, double *KF_out)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!K_out || !KF_out) return fail(c, CUDISC_EINVAL, "K_out / KF_out are NULL");
+    CUDA_TRY(c, cdc::launch_get_kernel(c, K_out, KF_out));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_coag_rhs(cudisc_coag_ctx *c, const double *rho, double *drho)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!rho || !drho) return fail(c, CUDISC_EINVAL, "rho / drho_dt are NULL");
+    if (c->p.precision == CUDISC_FP64) CUDA_TRY(c, cdc::launch_rhs_fp64(c, rho, drho));
+    else CUDA_TRY(c, cdc::launch_rhs_mixed(c, rho, drho));
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_coag_set_records(cudisc_coag_ctx *c, double *dt_log, long long log_cap,
+                                      long long *n_log, int *status)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (dt_log && log_cap < 1) return fail(c, CUDISC_EINVAL, "log_cap must be >= 1 with dt_log");
+    c->rec_dt = dt_log;
+    c->rec_cap = dt_log ? log_cap : 0;
+    c->rec_n = n_log;
+    c->rec_status = status;
+    return CUDISC_OK;
+}
+
+static cudisc_status finish_step(cudisc_coag_ctx *c, cudisc_step_stats *stats)
+{
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    std::vector<CellOut> h(c->n_cells);
+    CUDA_TRY(c, cudaMemcpy(h.data(), c->d_out, h.size() * sizeof(CellOut), cudaMemcpyDeviceToHost));
+    cudisc_step_stats s;
+    std::memset(&s, 0, sizeof(s));
+    for (const CellOut &o : h) {
+        s.accepted += o.n_acc;
+        s.rejected += o.n_rej;
+        if (o.n_acc > s.max_accepted) s.max_accepted = o.n_acc;
+        if (o.status != 0) s.n_failed++;
+        if (o.status > s.worst_status) s.worst_status = o.status;
+        if (o.mass_err > s.mass_err_max) s.mass_err_max = o.mass_err;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    s.elapsed_ms = ms;
+    if (stats) *stats = s;
+    if (s.worst_status != 0) {
+        char buf[160];
+        std::snprintf(buf, sizeof(buf), "%d of %d cells failed; worst per-cell status %d",
+                      s.n_failed, c->n_cells, s.worst_status);
+        c->err = buf;
+        return (cudisc_status)s.worst_status;
+    }
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_coag_step(cudisc_coag_ctx *c, double *rho, double t_span, double *dt_cell,
+                               cudisc_step_stats *stats)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!rho) return fail(c, CUDISC_EINVAL, "rho is NULL");
+    if (!(t_span > 0.0) || !std::isfinite(t_span)) return fail(c, CUDISC_EINVAL, "t_span must be positive and finite");
+    CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
+    if (c->p.precision == CUDISC_FP64)
+        CUDA_TRY(c, cdc::launch_step_fp64(c, rho, t_span, dt_cell, nullptr, nullptr, 0));
+    else
+        CUDA_TRY(c, cdc::launch_step_mixed(c, rho, t_span, dt_cell, nullptr, nullptr, 0));
+    CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
+    return finish_step(c, stats);
+}
+
+cudisc_status cudisc_coag_replay(cudisc_coag_ctx *c, double *rho, const double *hs,
+                                 const long long *n_h, long long stride)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!rho || !hs || !n_h) return fail(c, CUDISC_EINVAL, "rho, hs and n_h must be device arrays");
+    if (stride < 1) return fail(c, CUDISC_EINVAL, "stride must be >= 1");
+    CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
+    if (c->p.precision == CUDISC_FP64)
+        CUDA_TRY(c, cdc::launch_step_fp64(c, rho, 1.0, nullptr, hs, n_h, stride));
+    else
+        CUDA_TRY(c, cdc::launch_step_mixed(c, rho, 1.0, nullptr, hs, n_h, stride));
+    CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
+    return finish_step(c, nullptr);
+}
+
+} // extern "C"

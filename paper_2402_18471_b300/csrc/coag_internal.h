@@ -1,0 +1,107 @@
+// Internal declarations of the B300 coagulation library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cudisc_coag.h"
+
+namespace cdc {
+
+constexpr int kMaxBins = 160;         // FP64 path keeps the pair weights of one cell in smem
+constexpr int kBlkPairs = 16;         // pairs per K-block of the mixed contraction
+constexpr int kBlkElems = 32;         // TF32 elements per K-block row (a and b per pair)
+constexpr int kMBins = 128;           // MMA M: bins padded to 128 rows (N <= 128 here)
+constexpr int kMaxGridY = 65535;      // launches over cells are chunked to this
+
+// Per-cell scalars produced by the prep kernel (FP64).
+struct CellScal {
+    double kT8pi;   // 8 k_B T / pi  (Eq. vbrown numerator per unit mass sum)
+    double Vg2;     // alpha c_s^2   (eddy velocity squared)
+    double delta;   // Re^-1/2       (Kolmogorov Stokes number)
+    double pad;
+};
+
+// Per-cell, per-bin fields of the prep kernel, stored [cell][field][N].
+enum PrepField { PF_ST = 0, PF_VR, PF_VPHI, PF_VZ, PF_G1, PF_G2, PF_COUNT };
+
+// Per-cell integration scalars written back by the step kernels.
+struct CellOut {
+    long long n_acc, n_rej;
+    double h_last;
+    double mass_err;
+    int status;
+    int pad;
+};
+
+// Launch-time view of the tables the kernels read (all device pointers).
+struct DevTables {
+    int N, Np, n_cells;
+    const double *m, *minv, *a, *me;          // [N], me [N+1]
+    const unsigned int *pair_ij;              // [Np] (i << 16) | j
+    // FP64 gather form of Eq. (smol): per output bin k, entries (p, alpha, beta)
+    const int *row;                           // [N+1]
+    const int *ent_p;                         // [nnz]
+    const double2 *ent_ab;                    // [nnz]
+    const int *frow;                          // [N+1] fragment gather per bin l
+    const int *fent_p;                        // [fnnz]
+    const double *fent_m;                     // [fnnz]
+    const double *Ntab;                       // [N][N] row l, col k: N_k(m^e_{l+1})
+    // mixed path
+    int n_blk;
+    const int *blk_i, *blk_j0;                // [n_blk]
+    const float4 *Btiles;                     // [n_blk][2][128][32] swizzled TF32 hi/lo
+};
+
+} // namespace cdc
+
+struct cudisc_coag_ctx {
+    cudisc_coag_params p;
+    cudaStream_t stream = nullptr;
+    int N = 0, Np = 0, n_cells = 0, n_blk = 0;
+    std::string err;
+    // host copies
+    std::vector<double> h_m, h_me;
+    // device tables
+    double *d_m = nullptr, *d_minv = nullptr, *d_a = nullptr, *d_me = nullptr;
+    unsigned int *d_pair_ij = nullptr;
+    int *d_row = nullptr, *d_ent_p = nullptr, *d_frow = nullptr, *d_fent_p = nullptr;
+    double2 *d_ent_ab = nullptr;
+    double *d_fent_m = nullptr, *d_Ntab = nullptr;
+    int *d_blk_i = nullptr, *d_blk_j0 = nullptr;
+    float4 *d_Btiles = nullptr;
+    // per-cell prep and kernel tables
+    double *d_prep = nullptr;          // [n_cells][PF_COUNT][N]
+    float *d_prep32 = nullptr;         // same, FP32
+    cdc::CellScal *d_scal = nullptr;   // [n_cells]
+    double2 *d_K64 = nullptr;          // [n_cells][Np]      {K, K p_frag}
+    float2 *d_K32 = nullptr;           // [n_cells][n_blk*16] {K, K p_frag}
+    // integration workspace
+    cdc::CellOut *d_out = nullptr;     // [n_cells]
+    double *d_work = nullptr;          // mixed path slot state
+    size_t work_bytes = 0;
+    int *d_counter = nullptr;          // work queue head
+    // optional records
+    double *rec_dt = nullptr; long long rec_cap = 0; long long *rec_n = nullptr;
+    int *rec_status = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    cdc::DevTables tables() const;
+};
+
+namespace cdc {
+// kernel launchers (defined in the .cu files)
+cudaError_t launch_prep(const cudisc_coag_ctx *c);
+cudaError_t launch_kbuild(const cudisc_coag_ctx *c);
+cudaError_t launch_get_kernel(const cudisc_coag_ctx *c, double *K, double *KF);
+cudaError_t launch_rhs_fp64(const cudisc_coag_ctx *c, const double *rho, double *drho);
+cudaError_t launch_step_fp64(const cudisc_coag_ctx *c, double *rho, double t_span,
+                             double *dt_cell, const double *replay_h,
+                             const long long *replay_n, long long replay_stride);
+cudaError_t launch_rhs_mixed(const cudisc_coag_ctx *c, const double *rho, double *drho);
+cudaError_t launch_step_mixed(const cudisc_coag_ctx *c, double *rho, double t_span,
+                              double *dt_cell, const double *replay_h,
+                              const long long *replay_n, long long replay_stride);
+size_t mixed_workspace_bytes(int n_cells, int N);
+} // namespace cdc
