@@ -49,33 +49,6 @@ cudaError_t upload(T **dst, const std::vector<T> &src, cudaStream_t s)
     return cudaStreamSynchronize(s);
 }
 
-// Two-bin split of a product mass: lower bin l = max{k : m_k <= mass},
-// u = l + 1, eps = (m_u - mass) / (m_u - m_l); an exact hit is all in l;
-// outside the grid the whole mass goes to the end bin.  Returns mass
-// fractions (mode 0: eps, 1 - eps; mode 1: eps and 1 - eps as number
-// fractions, converted to mass fractions).
-void two_bin(const std::vector<double> &m, double mass, int mode, int &kl, int &ku,
-             double &fl, double &fu)
-{
-    const int N = (int)m.size();
-    if (mass >= m[N - 1]) { kl = ku = N - 1; fl = 1.0; fu = 0.0; return; }
-    if (mass <= m[0]) { kl = ku = 0; fl = 1.0; fu = 0.0; return; }
-    int lo = 0, hi = N - 1;               // m[lo] <= mass < m[hi]
-    while (hi - lo > 1) {
-        int mid = (lo + hi) / 2;
-        if (m[mid] <= mass) lo = mid; else hi = mid;
-    }
-    kl = lo; ku = lo + 1;
-    double eps = (m[ku] - mass) / (m[ku] - m[kl]);
-    if (mode == CUDISC_SPLIT_NUMBER) {
-        fl = eps * m[kl] / mass;
-        fu = (1.0 - eps) * m[ku] / mass;
-    } else {
-        fl = eps;
-        fu = 1.0 - eps;
-    }
-}
-
 // Mass fraction of fragments in bin k when the largest fragment fills bin l:
 // integral of m n(m) dm with n ~ m^-eta over bin k, normalised over bins 0..l.
 double frag_share(const std::vector<double> &me, double eta, int k, int l)
@@ -95,6 +68,73 @@ uint32_t tf32_trunc_bits(float f)
 }
 
 float bits_f(uint32_t u) { float f; std::memcpy(&f, &u, 4); return f; }
+
+// Double-double arithmetic (error-free transforms: Knuth's TwoSum and the
+// FMA form of Dekker's TwoProduct).  A pair whose grains differ in mass by
+// up to 1e21 adds and removes m_i-sized masses at bin i while moving only
+// an m_j-sized mass; summing those terms in plain FP64 leaves an error of
+// ~1e-16 m_i, which can exceed the transfer itself.  Accumulating each net
+// coefficient in double-double makes every pair conserve mass to the
+// rounding of its own transfer.
+struct dd { double hi, lo; };
+dd dd_of(double a) { return {a, 0.0}; }
+dd two_sum(double a, double b)
+{
+    double s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+dd fast_two_sum(double a, double b) { double s = a + b; return {s, b - (s - a)}; }
+dd operator+(dd a, dd b)
+{
+    dd s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+dd operator-(dd a) { return {-a.hi, -a.lo}; }
+dd operator-(dd a, dd b) { return a + (-b); }
+dd operator*(dd a, dd b)
+{
+    double p = a.hi * b.hi;
+    double e = std::fma(a.hi, b.hi, -p);
+    e += a.hi * b.lo + a.lo * b.hi;
+    return fast_two_sum(p, e);
+}
+dd operator/(dd a, dd b)
+{
+    double q1 = a.hi / b.hi;
+    dd r = a - b * dd_of(q1);
+    double q2 = r.hi / b.hi;
+    r = r - b * dd_of(q2);
+    double q3 = r.hi / b.hi;
+    return fast_two_sum(q1, q2) + dd_of(q3);
+}
+double dd_val(dd a) { return a.hi + a.lo; }
+
+// two_bin in double-double: the mass fractions of the lower and upper bin.
+void two_bin_dd(const std::vector<double> &m, dd mass, int mode, int &kl, int &ku, dd &fl, dd &fu)
+{
+    const int N = (int)m.size();
+    if (dd_val(mass - dd_of(m[N - 1])) >= 0.0) { kl = ku = N - 1; fl = dd_of(1.0); fu = dd_of(0.0); return; }
+    if (dd_val(mass - dd_of(m[0])) <= 0.0) { kl = ku = 0; fl = dd_of(1.0); fu = dd_of(0.0); return; }
+    int lo = 0, hi = N - 1;               // m[lo] <= mass < m[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (dd_val(mass - dd_of(m[mid])) >= 0.0) lo = mid; else hi = mid;
+    }
+    kl = lo; ku = lo + 1;
+    const dd span = dd_of(m[ku]) - dd_of(m[kl]);
+    const dd up = (mass - dd_of(m[kl])) / span;          // 1 - eps
+    const dd eps = (dd_of(m[ku]) - mass) / span;
+    if (mode == CUDISC_SPLIT_NUMBER) {
+        fl = eps * dd_of(m[kl]) / mass;
+        fu = up * dd_of(m[ku]) / mass;
+    } else {
+        fl = eps;
+        fu = up;
+    }
+}
 
 } // namespace
 
@@ -198,46 +238,50 @@ static cudisc_status build_tables(cudisc_coag_ctx *c)
     std::vector<float> tiles;
     if (mixed) tiles.assign((size_t)c->n_blk * 2 * cdc::kMBins * cdc::kBlkElems, 0.0f);
 
-    std::vector<double> colA(N), colB(N);
+    std::vector<dd> colA(N), colB(N);
     int blk = 0;
     for (int i = 0; i < N; i++) {
         for (int j = 0; j <= i; j++) {
             const int pp = i * (i + 1) / 2 + j;
             const double h = (i == j) ? 0.5 : 1.0;
             const double w = h / (m[i] * m[j]);
-            const double M = m[i] + m[j];
-            std::fill(colA.begin(), colA.end(), 0.0);
-            std::fill(colB.begin(), colB.end(), 0.0);
-            int kl, ku; double fl, fu;
-            two_bin(m, M, p.split_mode, kl, ku, fl, fu);
-            colA[kl] += M * fl; colA[ku] += M * fu;
-            colB[kl] -= M * fl; colB[ku] -= M * fu;
-            colA[i] -= m[i]; colA[j] -= m[j];
+            const dd M = two_sum(m[i], m[j]);               // exact
+            std::fill(colA.begin(), colA.end(), dd_of(0.0));
+            std::fill(colB.begin(), colB.end(), dd_of(0.0));
+            int kl, ku; dd fl, fu;
+            two_bin_dd(m, M, p.split_mode, kl, ku, fl, fu);
+            const dd cl = M * fl, cu = M * fu;
+            colA[kl] = colA[kl] + cl; colA[ku] = colA[ku] + cu;
+            colB[kl] = colB[kl] - cl; colB[ku] = colB[ku] - cu;
+            colA[i] = colA[i] - dd_of(m[i]);
+            colA[j] = colA[j] - dd_of(m[j]);
             const double mtar = m[i] >= m[j] ? m[i] : m[j];
             const double mim = m[i] >= m[j] ? m[j] : m[i];
-            const double cm = p.chi_im * mim;
-            const double mrem = (cm < mtar) ? (mtar - cm) : 0.0;
-            const double mx = (cm < mtar) ? cm : mtar;
-            if (mrem > 0.0) {
-                two_bin(m, mrem, p.split_mode, kl, ku, fl, fu);
-                colB[kl] += mrem * fl; colB[ku] += mrem * fu;
+            const dd cm = dd_of(p.chi_im) * dd_of(mim);
+            const bool has_rem = dd_val(cm - dd_of(mtar)) < 0.0;
+            const dd mrem = has_rem ? dd_of(mtar) - cm : dd_of(0.0);
+            const double mx = has_rem ? dd_val(cm) : mtar;
+            if (has_rem) {
+                dd rl, ru;
+                two_bin_dd(m, mrem, p.split_mode, kl, ku, rl, ru);
+                colB[kl] = colB[kl] + mrem * rl;
+                colB[ku] = colB[ku] + mrem * ru;
             }
-            const double Mf = M - mrem;
+            const double Mf = dd_val(M - mrem);
             // largest-fragment bin: smallest l with me[l+1] > mx
             int l = N - 1;
-            {
+            if (me[N] > mx) {
                 int lo = 0, hi = N - 1;
-                if (me[N] > mx) {
-                    while (lo < hi) {
-                        int mid = (lo + hi) / 2;
-                        if (me[mid + 1] > mx) hi = mid; else lo = mid + 1;
-                    }
-                    l = lo;
+                while (lo < hi) {
+                    int mid = (lo + hi) / 2;
+                    if (me[mid + 1] > mx) hi = mid; else lo = mid + 1;
                 }
+                l = lo;
             }
             for (int k = 0; k < N; k++) {
-                if (colA[k] != 0.0 || colB[k] != 0.0)
-                    rows[k].push_back({pp, make_double2(colA[k] * w, colB[k] * w)});
+                const double a_k = dd_val(colA[k]), b_k = dd_val(colB[k]);
+                if (a_k != 0.0 || b_k != 0.0)
+                    rows[k].push_back({pp, make_double2(a_k * w, b_k * w)});
             }
             frows[l].push_back({pp, Mf * w});
             if (mixed) {
@@ -246,8 +290,10 @@ static cudisc_status build_tables(cudisc_coag_ctx *c)
                 const int b = blk + jb;
                 const int t = j - jb * cdc::kBlkPairs;
                 for (int k = 0; k < N; k++) {
-                    double va = colA[k] * w;
-                    double vb = colB[k] * w + (k <= l ? Mf * w * Ntab[(size_t)l * N + k] : 0.0);
+                    double va = dd_val(colA[k]) * w;
+                    dd vbd = colB[k];
+                    if (k <= l) vbd = vbd + dd_of(Mf) * dd_of(Ntab[(size_t)l * N + k]);
+                    double vb = dd_val(vbd) * w;
                     for (int s = 0; s < 2; s++) {
                         double v = s == 0 ? va : vb;
                         int e = 2 * t + s;                       // element in the row
@@ -353,6 +399,7 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
     if (e == cudaSuccess) e = cudaMalloc(&c->d_scal, nc * sizeof(cdc::CellScal));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_out, nc * sizeof(CellOut));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, 64 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_counter, 0, 64 * sizeof(int));
     if (e == cudaSuccess) {
         if (params->precision == CUDISC_FP64)
             e = cudaMalloc(&c->d_K64, nc * (size_t)c->Np * sizeof(double2));
@@ -421,6 +468,13 @@ cudisc_status cudisc_coag_set_records(cudisc_coag_ctx *c, double *dt_log, long l
 static cudisc_status finish_step(cudisc_coag_ctx *c, cudisc_step_stats *stats)
 {
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int dev_err = 0;
+    CUDA_TRY(c, cudaMemcpy(&dev_err, c->d_counter + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (dev_err != 0) {
+        char buf[128];
+        std::snprintf(buf, sizeof(buf), "a bounded device wait ran out (code %d); results are invalid", dev_err);
+        return fail(c, CUDISC_ECUDA, buf);
+    }
     std::vector<CellOut> h(c->n_cells);
     CUDA_TRY(c, cudaMemcpy(h.data(), c->d_out, h.size() * sizeof(CellOut), cudaMemcpyDeviceToHost));
     cudisc_step_stats s;

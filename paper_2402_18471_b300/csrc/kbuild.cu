@@ -3,10 +3,10 @@
 // dv^2 = v_BM^2 + v_turb^2 + dv_lam^2 (Eqs. vbrown, OCVrel) and the
 // fragmentation probability of Eq. (p_frag).  Output per pair: {K, K p_frag}.
 //
-// The FP32 builder feeds the mixed-precision contraction and is bound by the
-// HBM writes of its output (8 B per pair); it keeps the special-function
-// count at three per pair (one reciprocal shared by the three Ormel & Cuzzi
-// denominators, one reciprocal square root for dv and 1/dv^2, one exp).
+// The FP32 builder feeds the mixed-precision contraction and is meant to be
+// bound by the HBM writes of its output (8 B per pair): one correctly
+// rounded reciprocal serves the three Ormel & Cuzzi denominators, plus one
+// square root, one division and one exp per pair.
 #include <algorithm>
 #include <cmath>
 
@@ -165,10 +165,10 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
         int i1 = i, i2 = j;
         if (S2 > S1) { float t = S1; S1 = S2; S2 = t; i1 = j; i2 = i; }
         const float Ss = fminf(fmaxf(1.6f * S1, d), 1.0f);
-        // one reciprocal for 1/(S1+S2), 1/(Ss+S1), 1/(Ss+S2)
+        // one correctly rounded reciprocal for 1/(S1+S2), 1/(Ss+S1), 1/(Ss+S2)
         const float A = S1 + S2, B = Ss + S1, C = Ss + S2;
         const float BC = B * C;
-        const float r = __fdividef(1.0f, A * BC);
+        const float r = 1.0f / (A * BC);
         const float rA = r * BC, rB = r * A * C, rC = r * A * B;
         const float S1s = S1 * S1, S2s = S2 * S2;
         const float g11 = pr[PF_G1 * N + i1], g12 = pr[PF_G1 * N + i2];
@@ -181,8 +181,7 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
         const float dP = pr[PF_VPHI * N + i] - pr[PF_VPHI * N + j];
         const float dZ = pr[PF_VZ * N + i] - pr[PF_VZ * N + j];
         const float dv2 = vbm2 + (float)s.Vg2 * V + (dR * dR + dP * dP + dZ * dZ);
-        const float rs = rsqrtf(dv2);                 // 1 / dv
-        const float dv = dv2 * rs;
+        const float dv = sqrtf(dv2);
         float K;
         if (kernel_mode == CUDISC_KERNEL_CONSTANT) K = kc;
         else if (kernel_mode == CUDISC_KERNEL_ADDITIVE) K = (float)(kc * (m[i] + m[j]));
@@ -191,8 +190,8 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
         if (frag_mode == CUDISC_FRAG_NONE) pf = 0.0f;
         else if (frag_mode == CUDISC_FRAG_ALL) pf = 1.0f;
         else {
-            const float x = 1.5f * v_frag * v_frag * rs * rs;
-            pf = (x + 1.0f) * __expf(-x);
+            const float x = 1.5f * v_frag * v_frag / dv2;
+            pf = (x + 1.0f) * expf(-x);
         }
         out = make_float2(K, K * pf);
     }

@@ -1,16 +1,748 @@
-// Mixed-precision path (tcgen05 tensor-core contraction): placeholder until
-// the kernel lands; init rejects CUDISC_MIXED_TF32 with ENOTSUP meanwhile.
+// Mixed-precision coagulation step on the 5th-generation tensor cores.
+//
+// The gain/loss redistribution of Eq. (smol) is a contraction over pairs:
+//   d rho_k / dt = S^2 sum_q Bt[k][q] A[c][q],
+// with S = sum_k |rho_k| per cell, x = rho / S, and per pair p = (i, j <= i)
+// two columns q: A = x_i x_j K_ij and A = x_i x_j K_ij p_frag,ij.  Bt holds
+// the fixed net redistribution coefficients per unit n_i n_j K (coagulation
+// into the two bins of Eq. Cijk, remnant into those of Eq. Rijk, fragments
+// by N_k of Eq. Nijk, minus the two colliding grains; 1/2 at i = j), divided
+// by m_i m_j.  It is built once on the host in double-double.
+//
+// Layout on chip (one CTA per SM, persistent over all right-hand sides):
+//   MMA M = 128 bins (Bt, streamed as swizzled 32 KB TF32 hi/lo tiles by the
+//   bulk-copy engine), MMA N = NS cell slots (generated operand), K = 32
+//   TF32 elements (16 pairs) per block; D [128 lanes x NS columns] FP32 in
+//   TMEM.  Each block issues three products: Bt_hi A_hi + Bt_hi A_lo +
+//   Bt_lo A_hi, with hi = the TF32 truncation and lo = the FP32 remainder.
+// Warp roles: warp 0 bulk-copy producer, warp 1 MMA issuer and TMEM owner,
+// warps 2..9 generate A (x_i x_j K split into hi/lo in the SW128 K-major
+// layout) and, between right-hand sides, run the per-slot FP64 logic: the
+// mass budget (sum_k f_k = 0 restored in FP64), the Bogacki-Shampine 3(2)
+// stages, the error norm, step control and refilling a slot with the next
+// cell when one finishes.
+//
+// Every mbarrier wait is bounded by a clock limit; a wait that runs out
+// records an error code in the status word and the kernel winds down.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
 #include "coag_internal.h"
 
 namespace cdc {
-size_t mixed_workspace_bytes(int, int) { return 256; }
-cudaError_t launch_rhs_mixed(const cudisc_coag_ctx *, const double *, double *)
+namespace {
+
+constexpr int kGenWarps = 8;
+constexpr int kThreads = 64 + 32 * kGenWarps;
+constexpr int kTileBytes = kMBins * 128;          // one 128-row x 128 B TF32 tile
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+constexpr double A21 = 0.5, A32 = 0.75;
+constexpr double B1 = 2.0 / 9.0, B2 = 1.0 / 3.0, B3 = 4.0 / 9.0;
+constexpr double E1 = -5.0 / 72.0, E2 = 1.0 / 12.0, E3 = 1.0 / 9.0, E4 = -1.0 / 8.0;
+
+enum Mode { MODE_STEP = 0, MODE_RHS = 1, MODE_REPLAY = 2 };
+enum ErrCode { ERR_WAIT_PRODUCER = 1, ERR_WAIT_MMA = 2, ERR_WAIT_GEN = 3, ERR_WAIT_EPI = 4 };
+
+struct MixedArgs {
+    DevTables t;
+    const float2 *K32;          // [n_cells][n_blk*16]
+    double *rho;                // state in/out (STEP, REPLAY) or input (RHS)
+    double *drho;               // output (RHS)
+    double t_span;
+    double *dt_cell;
+    double rtol, atol_rel;
+    long long max_steps;
+    const double *replay_h;
+    const long long *replay_n;
+    long long replay_stride;
+    CellOut *out;
+    int *err;                   // device status word
+    double *work;               // [grid][NS][5][N] FP64 slot state
+    double *rec_dt;
+    long long rec_cap;
+    long long *rec_n;
+    int *rec_status;
+    int NS, S, XS, mode;
+};
+
+struct __align__(16) Slot {
+    double t, h, hs, S, Sx, atol;
+    long long nacc, nrej, nrep;
+    int cell, phase, last, status;
+};
+
+// ---- PTX wrappers ----------------------------------------------------------
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t n)
 {
-    return cudaErrorNotSupported;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
 }
-cudaError_t launch_step_mixed(const cudisc_coag_ctx *, double *, double, double *,
-                              const double *, const long long *, long long)
+__device__ __forceinline__ void mbar_arrive(uint64_t *b)
 {
-    return cudaErrorNotSupported;
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded wait: false when the clock limit runs out or another role failed.
+__device__ __noinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *s_err, int code)
+{
+    const long long t0 = clock64();
+    for (int it = 0;; ++it) {
+        if (mbar_test(b, parity)) return true;
+        if ((it & 63) == 63) {
+            if (*s_err) return false;
+            if (clock64() - t0 > kWaitCycles) { atomicCAS((int *)s_err, 0, code); return false; }
+        }
+    }
+}
+// The same wait, with one answer for the whole warp (all 32 lanes call it).
+__device__ __forceinline__ bool wwait(uint64_t *b, uint32_t parity, volatile int *s_err, int code)
+{
+    return __all_sync(0xffffffffu, mbar_wait(b, parity, s_err, code));
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(su32(dst)), "l"(src), "r"(bytes), "r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle: 8-row groups
+// 1024 B apart (SBO), descriptor version 1, layout code 2.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+// Instruction descriptor, kind::tf32: D F32, A and B TF32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                 ::"r"(dt), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 8; q++) v[q] = __uint_as_float(r[q]);
+}
+// Generator-group barrier on an mbarrier (256 arrivals), with a bounded wait
+// so that a group member that gave up cannot hang the others.
+__device__ __forceinline__ bool gen_sync(uint64_t *gbar, uint32_t &phase, volatile int *s_err)
+{
+    mbar_arrive(gbar);
+    const bool ok = wwait(gbar, phase & 1, s_err, ERR_WAIT_EPI);
+    phase++;
+    return ok;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// TF32 split: hi keeps the top 19 bits (exact TF32), lo is the exact remainder.
+__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+
+// ---- per-slot logic (one warp per slot, lanes over bins) ------------------
+
+struct SlotBufs { double *y, *k1, *k2, *k3, *Y; };
+
+__device__ __forceinline__ SlotBufs slot_bufs(const MixedArgs &a, int slot)
+{
+    const int N = a.t.N;
+    double *base = a.work + ((size_t)blockIdx.x * a.NS + slot) * 5 * (size_t)N;
+    return {base, base + N, base + 2 * N, base + 3 * N, base + 4 * N};
+}
+
+// Load cell c into slot: state, scales, phase 0 (or mark the slot empty).
+__device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, int c)
+{
+    const int N = a.t.N, lane = threadIdx.x & 31;
+    if (c < 0) {
+        for (int k = lane; k < a.XS; k += 32) xrow[k] = 0.f;
+        if (lane == 0) sl.cell = -1;
+        return;
+    }
+    SlotBufs B = slot_bufs(a, slot);
+    const double *rc = a.rho + (size_t)c * N;
+    double s = 0.0, sa = 0.0;
+    for (int k = lane; k < N; k += 32) {
+        const double v = rc[k];
+        B.y[k] = v;
+        s += v;
+        sa += fabs(v);
+    }
+    s = warp_sum(s);
+    sa = warp_sum(sa);
+    const double Sx = sa > 0.0 ? sa : 1.0;
+    for (int k = lane; k < a.XS; k += 32) xrow[k] = (k < N) ? (float)(B.y[k] / Sx) : 0.f;
+    if (lane == 0) {
+        sl.cell = c;
+        sl.phase = 0;
+        sl.S = s;
+        sl.Sx = Sx;
+        sl.atol = a.atol_rel * s;
+        sl.t = 0.0;
+        sl.h = (a.mode == MODE_STEP && a.dt_cell) ? a.dt_cell[c] : 0.0;
+        sl.hs = 0.0;
+        sl.nacc = sl.nrej = sl.nrep = 0;
+        sl.last = 0;
+        sl.status = CUDISC_OK;
+    }
+}
+
+__device__ void slot_finish(const MixedArgs &a, Slot &sl, int slot)
+{
+    const int N = a.t.N, lane = threadIdx.x & 31;
+    const int c = sl.cell;
+    if (a.mode != MODE_RHS) {
+        SlotBufs B = slot_bufs(a, slot);
+        double *rc = a.rho + (size_t)c * N;
+        double s1 = 0.0;
+        for (int k = lane; k < N; k += 32) { rc[k] = B.y[k]; s1 += B.y[k]; }
+        s1 = warp_sum(s1);
+        if (lane == 0) {
+            CellOut o;
+            o.n_acc = sl.nacc; o.n_rej = sl.nrej; o.h_last = sl.h;
+            o.mass_err = sl.S > 0.0 ? fabs(s1 / sl.S - 1.0) : 0.0;
+            o.status = sl.status; o.pad = 0;
+            a.out[c] = o;
+            if (a.dt_cell && a.mode == MODE_STEP) a.dt_cell[c] = sl.h;
+            if (a.rec_n) a.rec_n[c] = sl.nacc;
+            if (a.rec_status) a.rec_status[c] = sl.status;
+        }
+    }
+}
+
+// Stage input x = Y / Sx for the next right-hand side.
+__device__ __forceinline__ void set_x(const MixedArgs &a, const Slot &sl, float *xrow, const double *Y)
+{
+    const int N = a.t.N, lane = threadIdx.x & 31;
+    const double r = 1.0 / sl.Sx;
+    for (int k = lane; k < N; k += 32) xrow[k] = (float)(Y[k] * r);
+}
+
+// Y = y + hs * A21 * k1 after choosing the step (shared by the first step
+// and every step after an accept or reject).
+__device__ bool begin_step(const MixedArgs &a, Slot &sl, float *xrow, SlotBufs B)
+{
+    const int N = a.t.N, lane = threadIdx.x & 31;
+    if (sl.nacc + sl.nrej >= a.max_steps) { sl.status = CUDISC_EMAXSTEPS; return false; }
+    sl.last = (sl.h >= a.t_span - sl.t);
+    sl.hs = sl.last ? (a.t_span - sl.t) : sl.h;
+    for (int k = lane; k < N; k += 32) B.Y[k] = B.y[k] + sl.hs * A21 * B.k1[k];
+    __syncwarp();
+    set_x(a, sl, xrow, B.Y);
+    sl.phase = 1;
+    return true;
+}
+
+// Process one right-hand side result f = S^2 D for this slot.  Returns true
+// when the slot finished its cell.
+__device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const float *Drow, int slot)
+{
+    const int N = a.t.N, lane = threadIdx.x & 31;
+    SlotBufs B = slot_bufs(a, slot);
+    const double S2 = sl.Sx * sl.Sx;
+    // FP64 mass budget: restore sum_k f_k = 0 by moving the residual in
+    // proportion to |f_k| (the redistribution conserves mass exactly).
+    double fv[(kMBins + 31) / 32];
+    double s = 0.0, sa = 0.0;
+#pragma unroll
+    for (int m = 0; m < (kMBins + 31) / 32; m++) {
+        const int k = lane + 32 * m;
+        fv[m] = (k < N) ? S2 * (double)Drow[k] : 0.0;
+        s += fv[m];
+        sa += fabs(fv[m]);
+    }
+    s = warp_sum(s);
+    sa = warp_sum(sa);
+    if (sa > 0.0) {
+        const double r = s / sa;
+#pragma unroll
+        for (int m = 0; m < (kMBins + 31) / 32; m++) fv[m] -= r * fabs(fv[m]);
+    }
+    if (a.mode == MODE_RHS) {
+#pragma unroll
+        for (int m = 0; m < (kMBins + 31) / 32; m++) {
+            const int k = lane + 32 * m;
+            if (k < N) a.drho[(size_t)sl.cell * N + k] = fv[m];
+        }
+        return true;
+    }
+    double *dst = sl.phase == 0 ? B.k1 : sl.phase == 1 ? B.k2 : sl.phase == 2 ? B.k3 : nullptr;
+    if (dst) {
+#pragma unroll
+        for (int m = 0; m < (kMBins + 31) / 32; m++) {
+            const int k = lane + 32 * m;
+            if (k < N) dst[k] = fv[m];
+        }
+        __syncwarp();
+    }
+    if (a.mode == MODE_REPLAY) {
+        const long long nh = a.replay_n[sl.cell];
+        const double hh = nh > 0 ? a.replay_h[(size_t)sl.cell * a.replay_stride + sl.nrep] : 0.0;
+        if (sl.phase == 0) {
+            if (nh == 0) return true;
+            for (int k = lane; k < N; k += 32) B.Y[k] = B.y[k] + hh * A21 * B.k1[k];
+            __syncwarp();
+            set_x(a, sl, xrow, B.Y);
+            sl.phase = 1;
+        } else if (sl.phase == 1) {
+            for (int k = lane; k < N; k += 32) B.Y[k] = B.y[k] + hh * A32 * B.k2[k];
+            __syncwarp();
+            set_x(a, sl, xrow, B.Y);
+            sl.phase = 2;
+        } else {
+            for (int k = lane; k < N; k += 32)
+                B.y[k] = B.y[k] + hh * (B1 * B.k1[k] + B2 * B.k2[k] + B3 * B.k3[k]);
+            __syncwarp();
+            sl.nrep++;
+            sl.nacc = sl.nrep;
+            if (sl.nrep >= nh) return true;
+            set_x(a, sl, xrow, B.y);
+            sl.phase = 0;
+        }
+        return false;
+    }
+    // adaptive Bogacki-Shampine 3(2)
+    switch (sl.phase) {
+    case 0: {
+        if (!(sl.h > 0.0)) {
+            double q = INFINITY;
+            for (int k = lane; k < N; k += 32)
+                if (B.k1[k] != 0.0) q = fmin(q, (fabs(B.y[k]) + sl.atol) / fabs(B.k1[k]));
+            q = warp_min(q);
+            sl.h = isfinite(q) ? 0.1 * q : a.t_span;
+            if (sl.h > a.t_span) sl.h = a.t_span;
+        }
+        return !begin_step(a, sl, xrow, B);
+    }
+    case 1:
+        for (int k = lane; k < N; k += 32) B.Y[k] = B.y[k] + sl.hs * A32 * B.k2[k];
+        __syncwarp();
+        set_x(a, sl, xrow, B.Y);
+        sl.phase = 2;
+        return false;
+    case 2:
+        for (int k = lane; k < N; k += 32)
+            B.Y[k] = B.y[k] + sl.hs * (B1 * B.k1[k] + B2 * B.k2[k] + B3 * B.k3[k]);
+        __syncwarp();
+        set_x(a, sl, xrow, B.Y);
+        sl.phase = 3;
+        return false;
+    default: {
+        // phase 3: fv holds k4 = f(y1), y1 is in B.Y
+        double E = 0.0, ymin = INFINITY, fin = 1.0;
+#pragma unroll
+        for (int m = 0; m < (kMBins + 31) / 32; m++) {
+            const int k = lane + 32 * m;
+            if (k < N) {
+                const double e = sl.hs * (E1 * B.k1[k] + E2 * B.k2[k] + E3 * B.k3[k] + E4 * fv[m]);
+                const double sc = sl.atol + a.rtol * fmax(fabs(B.y[k]), fabs(B.Y[k]));
+                const double r = fabs(e) / sc;
+                if (!isfinite(r) || !isfinite(B.Y[k])) fin = 0.0;
+                if (r > E) E = r;
+                if (B.Y[k] < ymin) ymin = B.Y[k];
+            }
+        }
+        E = warp_max(E);
+        ymin = warp_min(ymin);
+        const bool finite = warp_min(fin) > 0.5;
+        if (finite && E <= 1.0 && ymin >= -sl.atol) {
+            sl.t = sl.last ? a.t_span : sl.t + sl.hs;
+#pragma unroll
+            for (int m = 0; m < (kMBins + 31) / 32; m++) {
+                const int k = lane + 32 * m;
+                if (k < N) { B.y[k] = B.Y[k]; B.k1[k] = fv[m]; }
+            }
+            __syncwarp();
+            if (lane == 0 && a.rec_dt && sl.nacc < a.rec_cap)
+                a.rec_dt[(size_t)sl.cell * a.rec_cap + sl.nacc] = sl.hs;
+            sl.nacc++;
+            double fac = (E > 0.0) ? 0.9 * pow(E, -1.0 / 3.0) : 5.0;
+            fac = fmin(fmax(fac, 0.2), 5.0);
+            if (!(sl.last && sl.hs < sl.h)) sl.h = sl.hs * fac;
+            if (sl.t >= a.t_span) return true;
+        } else {
+            sl.nrej++;
+            double fac;
+            if (!finite) fac = 0.2;
+            else if (E > 1.0) fac = fmax(0.9 * pow(E, -1.0 / 3.0), 0.2);
+            else fac = 0.5;
+            sl.h = sl.hs * fac;
+            if (sl.h < 1e-14 * a.t_span) { sl.status = finite ? CUDISC_EDTMIN : CUDISC_ENONFINITE; return true; }
+        }
+        return !begin_step(a, sl, xrow, B);
+    }
+    }
+}
+
+// ---- the kernel --------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int NS = a.NS, S = a.S, XS = a.XS, N = a.t.N, n_blk = a.t.n_blk;
+    const int stage_bytes = 2 * kTileBytes + 2 * NS * 128;
+    uint8_t *stages = sm;
+    float *xrows = (float *)(sm + (size_t)S * stage_bytes);
+    Slot *slots = (Slot *)(xrows + (size_t)NS * XS);
+    uint64_t *bars = (uint64_t *)(slots + NS);
+    uint64_t *full_tma = bars, *gen_full = bars + S, *empty = bars + 2 * S;
+    uint64_t *done = bars + 3 * S, *go = bars + 3 * S + 1, *gbar = bars + 3 * S + 2;
+    uint64_t *fin = bars + 3 * S + 3;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_err, s_continue, s_next;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t ncols = NS <= 32 ? 32 : (NS <= 64 ? 64 : 128);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(&full_tma[s], 1);
+            mbar_init(&gen_full[s], kGenWarps);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        mbar_init(go, 1);
+        mbar_init(gbar, 32 * kGenWarps);
+        mbar_init(fin, 1);
+        s_err = 0;
+        s_continue = 1;
+        s_next = NS;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(su32(&s_tmem)), "r"(ncols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // initial slot fill: slot s takes cell blockIdx.x + s * gridDim.x
+    if (warp >= 2) {
+        for (int s = warp - 2; s < NS; s += kGenWarps) {
+            const int c = blockIdx.x + s * gridDim.x;
+            slot_load(a, slots[s], xrows + (size_t)s * XS, s, c < a.t.n_cells ? c : -1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 0) {
+        // ---- producer: Bt hi/lo tiles by the bulk-copy engine ----
+        long long g = 0;
+        for (int r = 0;; r++) {
+            if (r > 0) {
+                if (!wwait(go, (r - 1) & 1, &s_err, ERR_WAIT_PRODUCER)) break;
+                if (!s_continue) break;
+            }
+            bool ok = true;
+            for (int b = 0; b < n_blk; b++, g++) {
+                const int s = (int)(g % S);
+                const uint32_t u = (uint32_t)(g / S);
+                if (g >= S && !wwait(&empty[s], (u + 1) & 1, &s_err, ERR_WAIT_PRODUCER)) { ok = false; break; }
+                if (lane == 0) {
+                    uint8_t *dst = stages + (size_t)s * stage_bytes;
+                    mbar_expect_tx(&full_tma[s], 2 * kTileBytes);
+                    bulk_g2s(dst, a.t.Btiles + (size_t)b * (2 * kTileBytes / 16), 2 * kTileBytes, &full_tma[s]);
+                }
+                __syncwarp();
+            }
+            if (!ok) break;
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ----
+        const uint32_t idesc = idesc_tf32(kMBins, NS);
+        long long g = 0;
+        for (int r = 0;; r++) {
+            if (r > 0) {
+                if (!wwait(go, (r - 1) & 1, &s_err, ERR_WAIT_MMA)) break;
+                if (!s_continue) break;
+            }
+            bool ok = true;
+            for (int b = 0; b < n_blk; b++, g++) {
+                const int s = (int)(g % S);
+                const uint32_t u = (uint32_t)(g / S);
+                if (!wwait(&full_tma[s], u & 1, &s_err, ERR_WAIT_MMA) ||
+                    !wwait(&gen_full[s], u & 1, &s_err, ERR_WAIT_MMA)) { ok = false; break; }
+                tc_fence_after();
+                if (lane == 0) {
+                    uint8_t *st = stages + (size_t)s * stage_bytes;
+                    const uint32_t bt_hi = su32(st), bt_lo = bt_hi + kTileBytes;
+                    const uint32_t c_hi = bt_hi + 2 * kTileBytes, c_lo = c_hi + NS * 128;
+                    const uint64_t dbh = sw128_desc(bt_hi), dbl = sw128_desc(bt_lo);
+                    const uint64_t dch = sw128_desc(c_hi), dcl = sw128_desc(c_lo);
+#pragma unroll
+                    for (int kk = 0; kk < 4; kk++) {
+                        const uint64_t adv = (uint64_t)(kk * 2);   // 32 bytes per K step
+                        mma_tf32(tmem, dbh + adv, dch + adv, idesc, (b > 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32(tmem, dbh + adv, dcl + adv, idesc, 1u);
+                        mma_tf32(tmem, dbl + adv, dch + adv, idesc, 1u);
+                    }
+                    mma_commit(&empty[s]);
+                    if (b == n_blk - 1) mma_commit(done);
+                }
+                __syncwarp();
+            }
+            if (!ok) break;
+        }
+    } else {
+        // ---- generators / per-slot epilogue ----
+        const int gt = threadIdx.x - 64;              // 0 .. 255
+        const int P = NS / 16;                        // pairs per thread per block
+        const int row = gt % NS;
+        const int t0 = (gt / NS) * P;
+        uint32_t gphase = 0;
+        long long g = 0;
+        for (int r = 0;; r++) {
+            bool ok = true;
+            for (int b = 0; b < n_blk; b++, g++) {
+                const int s = (int)(g % S);
+                const uint32_t u = (uint32_t)(g / S);
+                if (g >= S && !wwait(&empty[s], (u + 1) & 1, &s_err, ERR_WAIT_GEN)) { ok = false; break; }
+                uint8_t *st = stages + (size_t)s * stage_bytes;
+                float *chi = (float *)(st + 2 * kTileBytes);
+                float *clo = (float *)(st + 2 * kTileBytes + NS * 128);
+                const int cell = slots[row].cell;
+                const int bi = __ldg(a.t.blk_i + b), bj0 = __ldg(a.t.blk_j0 + b);
+                const float *xr = xrows + (size_t)row * XS;
+                const float xi = xr[bi];
+                const float2 *kp = a.K32 + ((size_t)(cell < 0 ? 0 : cell) * n_blk + b) * kBlkPairs + t0;
+                for (int u2 = 0; u2 < P; u2 += 2) {
+                    float vh[4], vl[4];
+#pragma unroll
+                    for (int w = 0; w < 2; w++) {
+                        float va = 0.f, vb = 0.f;
+                        if (u2 + w < P && cell >= 0) {
+                            const float2 kv = __ldg(kp + u2 + w);
+                            const float xx = xi * xr[bj0 + t0 + u2 + w];
+                            va = xx * kv.x;
+                            vb = xx * kv.y;
+                        }
+                        const float ha = tf32_hi(va), hb = tf32_hi(vb);
+                        vh[2 * w] = ha; vh[2 * w + 1] = hb;
+                        vl[2 * w] = va - ha; vl[2 * w + 1] = vb - hb;
+                    }
+                    const int e = 2 * (t0 + u2);              // first element
+                    const int off = row * 32 + ((((e >> 2) ^ (row & 7)) << 2) | (e & 3));
+                    if (P >= 2) {
+                        *(float4 *)(chi + off) = make_float4(vh[0], vh[1], vh[2], vh[3]);
+                        *(float4 *)(clo + off) = make_float4(vl[0], vl[1], vl[2], vl[3]);
+                    } else {
+                        *(float2 *)(chi + off) = make_float2(vh[0], vh[1]);
+                        *(float2 *)(clo + off) = make_float2(vl[0], vl[1]);
+                    }
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&gen_full[s]);
+            }
+            if (!ok) break;
+            // ---- epilogue: D (TMEM) -> smem [slot][bin] ----
+            if (!wwait(done, r & 1, &s_err, ERR_WAIT_EPI)) break;
+            tc_fence_after();
+            float *Dsm = (float *)stages;                 // stages are idle now
+            const int DS = N + 1;
+            {
+                const int q = warp & 3;                   // TMEM lane quadrant of this warp
+                const int half = (warp - 2) >> 2;         // which half of the columns
+                const int c0 = half * (NS / 2), c1 = c0 + NS / 2;
+                const int bin = 32 * q + lane;
+                for (int cc = c0; cc < c1; cc += 8) {
+                    float v[8];
+                    tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cc, v);
+                    if (bin < N) {
+#pragma unroll
+                        for (int z = 0; z < 8; z++)
+                            if (cc + z < c1) Dsm[(size_t)(cc + z) * DS + bin] = v[z];
+                    }
+                }
+            }
+            tc_fence_before();
+            if (!gen_sync(gbar, gphase, &s_err)) break;
+            // ---- per-slot FP64 logic ----
+            for (int sidx = warp - 2; sidx < NS; sidx += kGenWarps) {
+                Slot &sl = slots[sidx];
+                if (sl.cell < 0) continue;
+                Slot loc = sl;
+                __syncwarp();
+                bool fin = slot_advance(a, loc, xrows + (size_t)sidx * XS, Dsm + (size_t)sidx * DS, sidx);
+                __syncwarp();
+                if (fin) {
+                    slot_finish(a, loc, sidx);
+                    int k = 0;
+                    if (lane == 0) k = atomicAdd(&s_next, 1);
+                    k = __shfl_sync(0xffffffffu, k, 0);
+                    const int c = blockIdx.x + k * gridDim.x;
+                    __syncwarp();
+                    if (lane == 0) sl = loc;
+                    __syncwarp();
+                    slot_load(a, sl, xrows + (size_t)sidx * XS, sidx, c < a.t.n_cells ? c : -1);
+                } else if (lane == 0) {
+                    sl = loc;
+                }
+                __syncwarp();
+            }
+            // generic-proxy writes to the stage memory (D staging) must be
+            // ordered before the bulk copies of the next pass overwrite it
+            fence_async_smem();
+            if (!gen_sync(gbar, gphase, &s_err)) break;
+            if (gt == 0) {
+                int any = 0;
+                for (int s2 = 0; s2 < NS; s2++) any |= (slots[s2].cell >= 0);
+                s_continue = any;
+                mbar_arrive(go);
+            }
+            if (!gen_sync(gbar, gphase, &s_err)) break;
+            if (!s_continue) break;
+        }
+    }
+    if (warp == 1 && lane == 0) {
+        // every MMA this thread issued has completed before TMEM is freed
+        mma_commit(fin);
+        mbar_wait(fin, 0, &s_err, ERR_WAIT_MMA);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+    if (threadIdx.x == 0 && s_err) atomicCAS(a.err, 0, s_err);
+}
+
+struct Config { int grid, NS, S, XS; size_t smem; };
+
+Config mixed_config(int n_cells, int N)
+{
+    int dev = 0, n_sm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    Config c;
+    int per = (n_cells + n_sm - 1) / n_sm;
+    int NS = ((per + 15) / 16) * 16;
+    NS = std::max(16, std::min(128, NS));
+    if (NS > 64) NS = 128; else if (NS > 32) NS = 64;
+    c.NS = NS;
+    c.grid = std::min(n_sm, (n_cells + NS - 1) / NS);
+    if (c.grid < 1) c.grid = 1;
+    // when cells exceed the slots, spread them over every SM
+    if ((long long)c.grid * NS < n_cells) c.grid = n_sm;
+    c.S = NS >= 128 ? 2 : 3;
+    const int n16 = ((N + 15) / 16) * 16;
+    c.XS = n16 + 1;
+    const size_t stage = 2 * (size_t)kTileBytes + 2 * (size_t)NS * 128;
+    c.smem = 1024 + c.S * stage + (size_t)NS * c.XS * 4 + (size_t)NS * sizeof(Slot) + 8 * (3 * c.S + 4);
+    return c;
+}
+
+cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double *drho, double t_span,
+                         double *dt_cell, const double *replay_h, const long long *replay_n,
+                         long long replay_stride)
+{
+    Config cf = mixed_config(c->n_cells, c->N);
+    const size_t need = (size_t)cf.grid * cf.NS * 5 * (size_t)c->N * sizeof(double);
+    if (need > c->work_bytes) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(c->d_counter + 1, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    MixedArgs a;
+    a.t = c->tables();
+    a.K32 = c->d_K32;
+    a.rho = rho;
+    a.drho = drho;
+    a.t_span = t_span;
+    a.dt_cell = dt_cell;
+    a.rtol = c->p.rtol;
+    a.atol_rel = c->p.atol_rel;
+    a.max_steps = c->p.max_substeps;
+    a.replay_h = replay_h;
+    a.replay_n = replay_n;
+    a.replay_stride = replay_stride;
+    a.out = c->d_out;
+    a.err = c->d_counter + 1;
+    a.work = c->d_work;
+    a.rec_dt = mode == MODE_STEP ? c->rec_dt : nullptr;
+    a.rec_cap = c->rec_cap;
+    a.rec_n = mode == MODE_RHS ? nullptr : c->rec_n;
+    a.rec_status = mode == MODE_RHS ? nullptr : c->rec_status;
+    a.NS = cf.NS;
+    a.S = cf.S;
+    a.XS = cf.XS;
+    a.mode = mode;
+    step_mixed_kernel<<<cf.grid, kThreads, cf.smem, c->stream>>>(a);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+size_t mixed_workspace_bytes(int n_cells, int N)
+{
+    Config cf = mixed_config(n_cells, N);
+    return (size_t)cf.grid * cf.NS * 5 * (size_t)N * sizeof(double);
+}
+
+cudaError_t launch_rhs_mixed(const cudisc_coag_ctx *c, const double *rho, double *drho)
+{
+    return launch_mixed(c, MODE_RHS, const_cast<double *>(rho), drho, 1.0, nullptr, nullptr, nullptr, 0);
+}
+
+cudaError_t launch_step_mixed(const cudisc_coag_ctx *c, double *rho, double t_span, double *dt_cell,
+                              const double *replay_h, const long long *replay_n, long long replay_stride)
+{
+    return launch_mixed(c, replay_h ? MODE_REPLAY : MODE_STEP, rho, nullptr, t_span, dt_cell, replay_h,
+                        replay_n, replay_stride);
+}
+
 } // namespace cdc

@@ -1,0 +1,163 @@
+"""GPU parity of the mixed-precision (tcgen05 TF32 split) path against the
+FP64 CPU oracle, through the C ABI.
+
+Tolerances, derived from the arithmetic: each contraction term carries the
+FP32 rounding of x_i x_j K (a few 1e-7) plus the TF32 split's 2^-20, so a
+right-hand side agrees with the oracle to ~3e-6 of the cell's gross
+collision flux; integrated states must agree to 1e-5 relative per bin (floor:
+the paper's absolute tolerance 1e-10 sum_k rho_k) and conserve mass to 1e-9.
+"""
+import numpy as np
+import pytest
+
+from paper_2402_18471_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def coag_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_18471_b300 import coag
+    return coag
+
+
+def packed(full):
+    N = full.shape[1]
+    ii, jj = np.tril_indices(N)
+    order = np.argsort(ii * (ii + 1) // 2 + jj)
+    return full[:, ii[order], jj[order]]
+
+
+def gross(o, d, rho):
+    K, _, _ = o.kernel()
+    n = rho / d.m
+    return (d.m * n * np.einsum("cik,ci->ck", K, n)).sum(1)
+
+
+def state_err(out, ref, S):
+    return np.abs(out - ref) / (np.abs(ref) + 1e-10 * S[:, None])
+
+
+CASES = {
+    # slot counts per CTA of 16, 32, 64, 128 and the refill path
+    "N2_one_cell": lambda: synth.make_disc(1, 1, 2, 1e-5, 1e-3, 10.0, 10.0, 50.0),
+    "N17_37_cells": lambda: synth.make_disc(1, 37, 17, 1e-5, 0.1, 10.0, 10.0, 50.0, seed=9),
+    "column_1x32_N50": lambda: synth.column_1x32(),
+    "N40_4736_cells": lambda: synth.make_disc(74, 64, 40, 1e-5, 1.0, 5.0, 100.0, 50.0, seed=5),
+    "N24_9000_cells": lambda: synth.make_disc(100, 90, 24, 1e-5, 0.1, 5.0, 100.0, 20.0, seed=6),
+    "N20_20000_cells_refill": lambda: synth.make_disc(200, 100, 20, 1e-5, 0.1, 5.0, 100.0, 20.0, seed=7),
+    "N128_5_cells": lambda: synth.make_disc(1, 5, 128, 1e-5, 10.0, 10.0, 10.0, 20.0),
+}
+SMALL = ["N2_one_cell", "N17_37_cells", "column_1x32_N50", "N128_5_cells"]
+
+
+def sample_of(d, k=24):
+    return np.unique(np.linspace(0, d.n_cells - 1, min(k, d.n_cells)).astype(int))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_rhs_mixed_matches_oracle(coag_mod, oracle_mod, case):
+    d = CASES[case]()
+    rho = synth.random_state(d, seed=21)
+    g = coag_mod.Coag(d, "mixed")
+    out = g.rhs(g.state(rho)).cpu().numpy()
+    cells = sample_of(d)
+    ds = d.subset(cells)
+    o = oracle_mod.Oracle(ds)
+    ref = o.rhs(rho[cells])
+    G = gross(o, ds, rho[cells])
+    err = np.abs(out[cells] - ref) / G[:, None]
+    assert err.max() < 3e-6, err.max()
+    # the FP64 mass budget makes every right-hand side conserve mass
+    assert np.all(np.abs(out.sum(1)) <= 1e-13 * np.abs(out).sum(1) + 1e-300)
+
+
+@pytest.mark.parametrize("case", SMALL)
+def test_kernel_build_fp32_matches_oracle(coag_mod, oracle_mod, case):
+    d = CASES[case]()
+    o = oracle_mod.Oracle(d)
+    K, pf, _ = o.kernel()
+    g = coag_mod.Coag(d, "mixed")
+    Kg, KFg = (x.cpu().numpy() for x in g.get_kernel())
+    Ko, KFo = packed(K), packed(K * pf)
+    assert np.allclose(Kg, Ko, rtol=2e-6, atol=0)
+    assert np.all(np.abs(KFg - KFo) <= 2e-5 * np.abs(KFo) + 2e-6 * Ko)
+
+
+@pytest.mark.parametrize("case", ["N17_37_cells", "column_1x32_N50", "N128_5_cells"])
+def test_replay_mixed_matches_oracle(coag_mod, oracle_mod, case):
+    """The oracle's own accepted step sequence replayed by both sides."""
+    d = CASES[case]()
+    o = oracle_mod.Oracle(d)
+    ref = o.step(d.rho0, d.t_span, log_cap=4000)
+    want = o.replay(d.rho0, ref["log"], ref["n_log"])
+    g = coag_mod.Coag(d, "mixed")
+    y = g.state(d.rho0)
+    g.replay(y, torch.as_tensor(ref["log"], device="cuda"), torch.as_tensor(ref["n_log"], device="cuda"))
+    S = d.rho0.sum(1)
+    e = state_err(y.cpu().numpy(), want, S)
+    assert e.max() < 1e-5, e.max()
+    assert np.abs(y.cpu().numpy().sum(1) / S - 1).max() < 1e-9
+
+
+@pytest.mark.parametrize("case", ["column_1x32_N50", "N40_4736_cells", "N20_20000_cells_refill"])
+def test_free_running_mixed_step(coag_mod, oracle_mod, case):
+    """Free-running adaptive step: the oracle replays the GPU's own accepted
+    step sequence (decisions near E = 1 may differ between precisions)."""
+    d = CASES[case]()
+    g = coag_mod.Coag(d, "mixed")
+    rec = g.set_records(3000)
+    y = g.state(d.rho0)
+    dt = torch.zeros(d.n_cells, dtype=torch.float64, device="cuda")
+    st = g.step(y, d.t_span, dt)
+    assert st["status"] == 0 and st["n_failed"] == 0
+    assert st["mass_err_max"] < 1e-9
+    n = rec["n"].cpu().numpy()
+    assert n.max() <= 3000 and n.min() >= 1
+    assert st["accepted"] == n.sum()
+    cells = sample_of(d, 16)
+    ds = d.subset(cells)
+    want = oracle_mod.Oracle(ds).replay(d.rho0[cells], rec["dt"].cpu().numpy()[cells], n[cells])
+    S = d.rho0[cells].sum(1)
+    e = state_err(y.cpu().numpy()[cells], want, S)
+    assert e.max() < 1e-5, e.max()
+    # every cell ran to t_span: its accepted steps add up to it
+    assert np.allclose(rec["dt"].cpu().numpy().sum(1), d.t_span, rtol=1e-12)
+
+
+def test_mixed_maxsteps_status(coag_mod):
+    d = CASES["N17_37_cells"]()
+    d.max_substeps = 4
+    g = coag_mod.Coag(d, "mixed")
+    st = g.step(g.state(d.rho0), d.t_span, check=False)
+    assert st["status"] == coag_mod.EMAXSTEPS and st["n_failed"] == d.n_cells
+
+
+def test_full_size_grid_mixed_rhs_sampled(coag_mod, oracle_mod):
+    """128 x 64 cells x 100 bins in the launch configuration the benchmark
+    uses; sampled cells against the oracle."""
+    d = synth.grid_128x64()
+    rho = synth.random_state(d, seed=5)
+    g = coag_mod.Coag(d, "mixed")
+    out = g.rhs(g.state(rho)).cpu().numpy()
+    cells = np.arange(0, d.n_cells, 331)
+    ds = d.subset(cells)
+    o = oracle_mod.Oracle(ds)
+    ref = o.rhs(rho[cells])
+    err = np.abs(out[cells] - ref) / gross(o, ds, rho[cells])[:, None]
+    assert err.max() < 3e-6, err.max()
+
+
+def test_full_size_fp64_step_conserves_mass(coag_mod):
+    """With the double-double mapping coefficients the FP64 path conserves
+    total mass to ~1e-13 over 1e4 yr of the 128 x 64 x 100 workload."""
+    d = synth.grid_128x64()
+    g = coag_mod.Coag(d, "fp64")
+    y = g.state(d.rho0)
+    st = g.step(y, d.t_span)
+    assert st["status"] == 0
+    assert st["mass_err_max"] < 1e-12, st["mass_err_max"]
