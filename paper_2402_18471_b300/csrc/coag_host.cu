@@ -60,10 +60,13 @@ double frag_share(const std::vector<double> &me, double eta, int k, int l)
     return (std::pow(me[k + 1], s) - std::pow(me[k], s)) / (std::pow(me[l + 1], s) - lo);
 }
 
-uint32_t tf32_trunc_bits(float f)
+// Round an FP32 value to the nearest TF32 value (ties to even).
+uint32_t tf32_rn_bits(float f)
 {
     uint32_t u;
     std::memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return u & 0xFFFFE000u;
+    u += 0xFFFu + ((u >> 13) & 1u);
     return u & 0xFFFFE000u;
 }
 
@@ -297,10 +300,8 @@ static cudisc_status build_tables(cudisc_coag_ctx *c)
                     for (int s = 0; s < 2; s++) {
                         double v = s == 0 ? va : vb;
                         int e = 2 * t + s;                       // element in the row
-                        float f = (float)v;
-                        uint32_t hb = tf32_trunc_bits(f);
-                        float hi = bits_f(hb);
-                        float lo = (float)(v - (double)hi);
+                        float hi = bits_f(tf32_rn_bits((float)v));
+                        float lo = bits_f(tf32_rn_bits((float)(v - (double)hi)));
                         int chunk = e >> 2;
                         size_t off = (size_t)k * 32 + (size_t)(((chunk ^ (k & 7)) << 2) | (e & 3));
                         size_t base = (size_t)b * 2 * cdc::kMBins * 32;
@@ -395,7 +396,7 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
     const size_t nc = (size_t)c->n_cells, N = (size_t)c->N;
     cudaError_t e;
     e = cudaMalloc(&c->d_prep, nc * cdc::PF_COUNT * N * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_prep32, nc * cdc::PF_COUNT * N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_prep32, nc * cdc::P3_COUNT * N * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_scal, nc * sizeof(cdc::CellScal));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_out, nc * sizeof(CellOut));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, 64 * sizeof(int));

@@ -20,11 +20,20 @@ struct CellScal {
     double kT8pi;   // 8 k_B T / pi  (Eq. vbrown numerator per unit mass sum)
     double Vg2;     // alpha c_s^2   (eddy velocity squared)
     double delta;   // Re^-1/2       (Kolmogorov Stokes number)
+    double etavK;   // eta Omega R   (drift velocity scale)
+    double ZOm;     // Z Omega       (settling velocity scale)
     double pad;
 };
 
 // Per-cell, per-bin fields of the prep kernel, stored [cell][field][N].
 enum PrepField { PF_ST = 0, PF_VR, PF_VPHI, PF_VZ, PF_G1, PF_G2, PF_COUNT };
+// FP32 copy: St and each input velocity as an FP32 hi/lo pair, so that
+// differences of nearly equal velocities keep their precision.
+// P3_SS, P3_SSMD, P3_OMSS: St* = clamp(1.6 St, Re^-1/2, 1), St* - Re^-1/2 and
+// 1 - St* of the bin when it is the larger of a pair, formed in FP64 (both
+// differences can be tiny next to their operands).
+enum Prep32Field { P3_ST = 0, P3_VRH, P3_VRL, P3_VPH, P3_VPL, P3_VZH, P3_VZL,
+                   P3_SS, P3_SSMD, P3_OMSS, P3_COUNT };
 
 // Per-cell integration scalars written back by the step kernels.
 struct CellOut {

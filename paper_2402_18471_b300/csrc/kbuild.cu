@@ -4,9 +4,8 @@
 // fragmentation probability of Eq. (p_frag).  Output per pair: {K, K p_frag}.
 //
 // The FP32 builder feeds the mixed-precision contraction and is meant to be
-// bound by the HBM writes of its output (8 B per pair): one correctly
-// rounded reciprocal serves the three Ormel & Cuzzi denominators, plus one
-// square root, one division and one exp per pair.
+// bound by the HBM writes of its output (8 B per pair).  It evaluates the
+// Ormel & Cuzzi terms in a cancellation-free arrangement (see below).
 #include <algorithm>
 #include <cmath>
 
@@ -70,18 +69,24 @@ __global__ void __launch_bounds__(128) prep_kernel(
     const double g1 = St * St / (1.0 + St);      // St^2 / (t_L + St), t_L = 1
     const double g2 = St * St / (St + delta);    // St^2 / (t_eta + St)
     double *pr = prep + (size_t)c * PF_COUNT * N;
-    float *pf = prep32 + (size_t)c * PF_COUNT * N;
+    float *pf = prep32 + (size_t)c * P3_COUNT * N;
     const double v[PF_COUNT] = {St, vR, vphi, vZ, g1, g2};
 #pragma unroll
-    for (int f = 0; f < PF_COUNT; f++) {
-        pr[f * N + k] = v[f];
-        pf[f * N + k] = (float)v[f];
-    }
+    for (int f = 0; f < PF_COUNT; f++) pr[f * N + k] = v[f];
+    const float vRh = (float)vR, vPh = (float)vphi, vZh = (float)vZ;
+    const double Ss = fmin(fmax(1.6 * St, delta), 1.0);
+    const float v32[P3_COUNT] = {(float)St, vRh, (float)(vR - vRh), vPh, (float)(vphi - vPh),
+                                 vZh, (float)(vZ - vZh), (float)Ss, (float)(Ss - delta),
+                                 (float)(1.0 - Ss)};
+#pragma unroll
+    for (int f = 0; f < P3_COUNT; f++) pf[f * N + k] = v32[f];
     if (k == 0) {
         CellScal s;
         s.kT8pi = 8.0 * kp.k_B * Tc / M_PI;
         s.Vg2 = al * cs * cs;
         s.delta = delta;
+        s.etavK = (eta ? eta[c] : 0.0) * Om * Rc;
+        s.ZOm = Zc * Om;
         s.pad = 0.0;
         scal[c] = s;
     }
@@ -144,7 +149,8 @@ __global__ void __launch_bounds__(256) kbuild64_kernel(
 // q = 16 b + t is pair (blk_i[b], blk_j0[b] + t); slots past the diagonal
 // hold zeros.
 __global__ void __launch_bounds__(256) kbuild32_kernel(
-    int c0, float kc, float v_frag, int kernel_mode, int frag_mode, int n_cells, int N, int n_slots,
+    int c0, float kc, float v_frag, int kernel_mode, int frag_mode, int has_vdust, int n_cells,
+    int N, int n_slots,
     const int *__restrict__ blk_i, const int *__restrict__ blk_j0,
     const double *__restrict__ a, const double *__restrict__ minv,
     const double *__restrict__ m, const float *__restrict__ prep32,
@@ -158,28 +164,52 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
     const int j = blk_j0[b] + (q & 15);
     float2 out = make_float2(0.f, 0.f);
     if (j <= i) {
-        const float *pr = prep32 + (size_t)c * PF_COUNT * N;
+        const float *pr = prep32 + (size_t)c * P3_COUNT * N;
         const CellScal s = scal[c];
         const float d = (float)s.delta;
-        float S1 = pr[PF_ST * N + i], S2 = pr[PF_ST * N + j];
-        int i1 = i, i2 = j;
-        if (S2 > S1) { float t = S1; S1 = S2; S2 = t; i1 = j; i2 = i; }
-        const float Ss = fminf(fmaxf(1.6f * S1, d), 1.0f);
-        // one correctly rounded reciprocal for 1/(S1+S2), 1/(Ss+S1), 1/(Ss+S2)
-        const float A = S1 + S2, B = Ss + S1, C = Ss + S2;
-        const float BC = B * C;
-        const float r = 1.0f / (A * BC);
-        const float rA = r * BC, rB = r * A * C, rC = r * A * B;
-        const float S1s = S1 * S1, S2s = S2 * S2;
-        const float g11 = pr[PF_G1 * N + i1], g12 = pr[PF_G1 * N + i2];
-        const float g21 = pr[PF_G2 * N + i1], g22 = pr[PF_G2 * N + i2];
-        const float dVI = (S1 - S2) * rA * (S1s * rB - g11 - S2s * rC + g12);
-        const float dVII = 2.0f * (Ss - d) + S1s * rB - g21 + S2s * rC - g22;
-        const float V = fmaxf(dVI + dVII, 0.0f);
+        const float Si = pr[P3_ST * N + i], Sj = pr[P3_ST * N + j];
+        float S1 = Si, S2 = Sj;
+        int i1 = i;
+        if (S2 > S1) { float t = S1; S1 = S2; S2 = t; i1 = j; }
+        const float Ss = pr[P3_SS * N + i1];
+        const float Ssmd = pr[P3_SSMD * N + i1], omSs = pr[P3_OMSS * N + i1];
+        // Ormel & Cuzzi class I and II terms rearranged into sums and
+        // products of non-negative factors (algebraically identical to the
+        // closed forms).  In FP32 the literal forms cancel: with St* clamped
+        // to Re^-1/2 and St1 = St2 class II is exactly zero but leaves a
+        // residue ~1e-7 St^2/Re^-1/2, and for St >> 1 both forms reduce to
+        // small differences of numbers near one.
+        //   dVI  = (S1-S2)^2 (1-St*) [St*(S1+S2) + S1 S2 (1+St*)]
+        //          / [(S1+S2)(St*+S1)(1+S1)(St*+S2)(1+S2)]
+        //   dVII = (St*-d) sum_{s=S1,S2} [s (St*+d) + St* d] / [(s+St*)(s+d)]
+        const float A = S1 + S2, P1 = S1 + Ss, P2 = S2 + Ss;
+        const float Q1 = 1.0f + S1, Q2 = 1.0f + S2, R1 = S1 + d, R2 = S2 + d;
+        const float dS = S1 - S2;
+        const float nI = dS * dS * omSs * (Ss * A + S1 * S2 * (1.0f + Ss));
+        const float dI = A * (P1 * Q1) * (P2 * Q2);
+        const float sd = Ss + d, Sd = Ss * d;
+        const float nII = Ssmd * ((S1 * sd + Sd) * (P2 * R2) + (S2 * sd + Sd) * (P1 * R1));
+        const float dII = (P1 * R1) * (P2 * R2);
+        const float V = fmaxf(nI / dI + nII / dII, 0.0f);
         const float vbm2 = (float)(s.kT8pi * (minv[i] + minv[j]));
-        const float dR = pr[PF_VR * N + i] - pr[PF_VR * N + j];
-        const float dP = pr[PF_VPHI * N + i] - pr[PF_VPHI * N + j];
-        const float dZ = pr[PF_VZ * N + i] - pr[PF_VZ * N + j];
+        float dR, dP, dZ;
+        if (has_vdust) {
+            // input velocities: difference of FP32 hi/lo pairs
+            dR = (pr[P3_VRH * N + i] - pr[P3_VRH * N + j]) + (pr[P3_VRL * N + i] - pr[P3_VRL * N + j]);
+            dP = (pr[P3_VPH * N + i] - pr[P3_VPH * N + j]) + (pr[P3_VPL * N + i] - pr[P3_VPL * N + j]);
+            dZ = (pr[P3_VZH * N + i] - pr[P3_VZH * N + j]) + (pr[P3_VZL * N + i] - pr[P3_VZL * N + j]);
+        } else {
+            // terminal velocities: differences factored through St_i - St_j
+            //   v_R   = -2 eta v_K St/(1+St^2), v_phi = -eta v_K/(1+St^2),
+            //   v_Z   = -Z Omega St/(1+St)
+            const float dS = Si - Sj;
+            const float ai = 1.0f + Si * Si, aj = 1.0f + Sj * Sj;
+            const float rij = 1.0f / (ai * aj);
+            const float ev = (float)s.etavK;
+            dR = -2.0f * ev * dS * (1.0f - Si * Sj) * rij;
+            dP = ev * dS * (Si + Sj) * rij;
+            dZ = -(float)s.ZOm * dS / ((1.0f + Si) * (1.0f + Sj));
+        }
         const float dv2 = vbm2 + (float)s.Vg2 * V + (dR * dR + dP * dP + dZ * dZ);
         const float dv = sqrtf(dv2);
         float K;
@@ -253,7 +283,8 @@ cudaError_t launch_kbuild(const cudisc_coag_ctx *c)
         for (int c0 = 0; c0 < c->n_cells; c0 += kMaxGridY) {
         dim3 grid((n_slots + 255) / 256, std::min(kMaxGridY, c->n_cells - c0));
         kbuild32_kernel<<<grid, 256, 0, c->stream>>>(
-            c0, (float)p.kernel_const, (float)p.v_frag, p.kernel_mode, p.frag_mode, c->n_cells, c->N,
+            c0, (float)p.kernel_const, (float)p.v_frag, p.kernel_mode, p.frag_mode, p.v_dust != nullptr,
+            c->n_cells, c->N,
             n_slots, c->d_blk_i, c->d_blk_j0, c->d_a, c->d_minv, c->d_m, c->d_prep32, c->d_scal,
             c->d_K32);
         }

@@ -12,9 +12,11 @@
 // Layout on chip (one CTA per SM, persistent over all right-hand sides):
 //   MMA M = 128 bins (Bt, streamed as swizzled 32 KB TF32 hi/lo tiles by the
 //   bulk-copy engine), MMA N = NS cell slots (generated operand), K = 32
-//   TF32 elements (16 pairs) per block; D [128 lanes x NS columns] FP32 in
-//   TMEM.  Each block issues three products: Bt_hi A_hi + Bt_hi A_lo +
-//   Bt_lo A_hi, with hi = the TF32 truncation and lo = the FP32 remainder.
+//   TF32 elements (16 pairs) per block.  Each block issues the four products
+//   of (Bt_hi + Bt_lo)(A_hi + A_lo), hi and lo rounded to nearest TF32: the
+//   hi x hi product into one of several FP32 accumulators [128 lanes x NS
+//   columns] in TMEM (a contiguous share of the blocks each), the three
+//   correction products into one more; the epilogue sums them in FP64.
 // Warp roles: warp 0 bulk-copy producer, warp 1 MMA issuer and TMEM owner,
 // warps 2..9 generate A (x_i x_j K split into hi/lo in the SW128 K-major
 // layout) and, between right-hand sides, run the per-slot FP64 logic: the
@@ -34,6 +36,7 @@ namespace cdc {
 namespace {
 
 constexpr int kGenWarps = 8;
+constexpr int kMaxMain = 8;                       // TMEM accumulators for the hi x hi products
 constexpr int kThreads = 64 + 32 * kGenWarps;
 constexpr int kTileBytes = kMBins * 128;          // one 128-row x 128 B TF32 tile
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
@@ -188,8 +191,15 @@ __device__ __forceinline__ double warp_min(double v)
     return v;
 }
 
-// TF32 split: hi keeps the top 19 bits (exact TF32), lo is the exact remainder.
-__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+// TF32 split, both parts rounded to nearest: hi = rn_tf32(v), lo =
+// rn_tf32(v - hi).  The tensor core then sees exact TF32 values and
+// hi + lo matches v to 2^-22 relative, without the bias of truncation.
+__device__ __forceinline__ float tf32_rn(float v)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
 
 // ---- per-slot logic (one warp per slot, lanes over bins) ------------------
 
@@ -287,7 +297,7 @@ __device__ bool begin_step(const MixedArgs &a, Slot &sl, float *xrow, SlotBufs B
 
 // Process one right-hand side result f = S^2 D for this slot.  Returns true
 // when the slot finished its cell.
-__device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const float *Drow, int slot)
+__device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const double *Drow, int slot)
 {
     const int N = a.t.N, lane = threadIdx.x & 31;
     SlotBufs B = slot_bufs(a, slot);
@@ -299,7 +309,7 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
 #pragma unroll
     for (int m = 0; m < (kMBins + 31) / 32; m++) {
         const int k = lane + 32 * m;
-        fv[m] = (k < N) ? S2 * (double)Drow[k] : 0.0;
+        fv[m] = (k < N) ? S2 * Drow[k] : 0.0;
         s += fv[m];
         sa += fabs(fv[m]);
     }
@@ -444,7 +454,16 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     __shared__ uint32_t s_tmem;
     __shared__ int s_err, s_continue, s_next;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t ncols = NS <= 32 ? 32 : (NS <= 64 ? 64 : 128);
+    // TMEM: nacc accumulators for the hi x hi products, each taking a
+    // contiguous share of the blocks (every one gets at least one), plus one
+    // for the three 2^-11-smaller correction products of every block.  FP32
+    // accumulation error grows with the additions per accumulator; the
+    // epilogue sums them all in FP64.
+    int nmain = 512 / NS - 1;
+    if (nmain > kMaxMain) nmain = kMaxMain;
+    const int nacc = n_blk < nmain ? n_blk : nmain;
+    const int tcols = (nacc + 1) * NS;
+    const uint32_t ncols = tcols <= 32 ? 32 : tcols <= 64 ? 64 : tcols <= 128 ? 128 : tcols <= 256 ? 256 : 512;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; s++) {
@@ -523,11 +542,18 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     const uint64_t dbh = sw128_desc(bt_hi), dbl = sw128_desc(bt_lo);
                     const uint64_t dch = sw128_desc(c_hi), dcl = sw128_desc(c_lo);
 #pragma unroll
+                    // accumulator chunk of this block: the pass over all blocks is
+                    // split across NACC TMEM accumulators summed later in FP64
+                    const int ch = (int)(((long long)b * nacc) / n_blk);
+                    const bool first = (b == 0) || ((int)(((long long)(b - 1) * nacc) / n_blk) != ch);
+                    const uint32_t dt = tmem + (uint32_t)(ch * NS);
+                    const uint32_t dc = tmem + (uint32_t)(nacc * NS);
                     for (int kk = 0; kk < 4; kk++) {
                         const uint64_t adv = (uint64_t)(kk * 2);   // 32 bytes per K step
-                        mma_tf32(tmem, dbh + adv, dch + adv, idesc, (b > 0 || kk > 0) ? 1u : 0u);
-                        mma_tf32(tmem, dbh + adv, dcl + adv, idesc, 1u);
-                        mma_tf32(tmem, dbl + adv, dch + adv, idesc, 1u);
+                        mma_tf32(dt, dbh + adv, dch + adv, idesc, (!first || kk > 0) ? 1u : 0u);
+                        mma_tf32(dc, dbh + adv, dcl + adv, idesc, (b > 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32(dc, dbl + adv, dch + adv, idesc, 1u);
+                        mma_tf32(dc, dbl + adv, dcl + adv, idesc, 1u);
                     }
                     mma_commit(&empty[s]);
                     if (b == n_blk - 1) mma_commit(done);
@@ -569,9 +595,9 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                             va = xx * kv.x;
                             vb = xx * kv.y;
                         }
-                        const float ha = tf32_hi(va), hb = tf32_hi(vb);
+                        const float ha = tf32_rn(va), hb = tf32_rn(vb);
                         vh[2 * w] = ha; vh[2 * w + 1] = hb;
-                        vl[2 * w] = va - ha; vl[2 * w + 1] = vb - hb;
+                        vl[2 * w] = tf32_rn(va - ha); vl[2 * w + 1] = tf32_rn(vb - hb);
                     }
                     const int e = 2 * (t0 + u2);              // first element
                     const int off = row * 32 + ((((e >> 2) ^ (row & 7)) << 2) | (e & 3));
@@ -591,20 +617,27 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             // ---- epilogue: D (TMEM) -> smem [slot][bin] ----
             if (!wwait(done, r & 1, &s_err, ERR_WAIT_EPI)) break;
             tc_fence_after();
-            float *Dsm = (float *)stages;                 // stages are idle now
-            const int DS = N + 1;
+            double *Dsm = (double *)stages;               // stages are idle now
+            const int DS = N;
             {
                 const int q = warp & 3;                   // TMEM lane quadrant of this warp
                 const int half = (warp - 2) >> 2;         // which half of the columns
                 const int c0 = half * (NS / 2), c1 = c0 + NS / 2;
                 const int bin = 32 * q + lane;
                 for (int cc = c0; cc < c1; cc += 8) {
-                    float v[8];
-                    tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cc, v);
+                    double acc[8];
+#pragma unroll
+                    for (int z = 0; z < 8; z++) acc[z] = 0.0;
+                    for (int ch = 0; ch <= nacc; ch++) {
+                        float v[8];
+                        tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ch * NS + cc), v);
+#pragma unroll
+                        for (int z = 0; z < 8; z++) acc[z] += (double)v[z];
+                    }
                     if (bin < N) {
 #pragma unroll
                         for (int z = 0; z < 8; z++)
-                            if (cc + z < c1) Dsm[(size_t)(cc + z) * DS + bin] = v[z];
+                            if (cc + z < c1) Dsm[(size_t)(cc + z) * DS + bin] = acc[z];
                     }
                 }
             }
