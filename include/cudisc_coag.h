@@ -168,6 +168,29 @@ cudisc_status cudisc_coag_set_records(cudisc_coag_ctx *ctx, double *dt_log,
 cudisc_status cudisc_coag_replay(cudisc_coag_ctx *ctx, double *rho, const double *hs,
                                  const long long *n_h, long long stride);
 
+/* Same integration as cudisc_coag_step on a CUDISC_MIXED_TF32 context, but
+ * the per-cell-slot integrator state lives in a fixed 16 MiB device array
+ * compiled into the library instead of the context's workspace.  The paper
+ * has no counterpart: this is for callers that cannot allocate device memory
+ * at the point where they integrate, for example a code whose device memory
+ * is wholly owned by its own pool allocator, or a time loop that must not take
+ * cudaMalloc's implicit device synchronisation.  This call itself allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine); the caller
+ * passes rho and dt_cell exactly as for cudisc_coag_step.
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - Every GPU that loads the library holds the 16 MiB until the process
+ *     exits, whether or not this entry point is used.
+ *   - All calls share the one array (it keeps the last call's contents, and
+ *     every slot is written before it is read): calls that overlap on the GPU,
+ *     from any context, race and give wrong results.
+ *   - Problems whose slot state exceeds 16 MiB (148 CTAs x slots x 5 x N x
+ *     8 bytes) are rejected with CUDISC_ENOTSUP and a message; use
+ *     cudisc_coag_step for them.
+ *   - Returns CUDISC_EINVAL for a context of another precision. */
+cudisc_status cudisc_coag_step_static_scratch(cudisc_coag_ctx *ctx, double *rho, double t_span,
+                                              double *dt_cell, cudisc_step_stats *stats);
+
 void cudisc_coag_destroy(cudisc_coag_ctx *ctx);
 
 /* Message of the last failed call on ctx (or of this thread when ctx is

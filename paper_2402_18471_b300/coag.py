@@ -75,6 +75,7 @@ def lib():
         L.cudisc_coag_step.argtypes = [v, v, d, v, C.POINTER(cudisc_step_stats)]
         L.cudisc_coag_set_records.argtypes = [v, v, C.c_longlong, v, v]
         L.cudisc_coag_replay.argtypes = [v, v, v, v, C.c_longlong]
+        L.cudisc_coag_step_static_scratch.argtypes = [v, v, d, v, C.POINTER(cudisc_step_stats)]
         L.cudisc_coag_destroy.argtypes = [v]
         L.cudisc_coag_destroy.restype = None
         L.cudisc_coag_last_error.argtypes = [v]
@@ -82,7 +83,7 @@ def lib():
         L.cudisc_coag_version.restype = C.c_char_p
         for fn in ("cudisc_coag_init", "cudisc_coag_build_kernel", "cudisc_coag_get_kernel",
                    "cudisc_coag_rhs", "cudisc_coag_step", "cudisc_coag_set_records",
-                   "cudisc_coag_replay"):
+                   "cudisc_coag_replay", "cudisc_coag_step_static_scratch"):
             getattr(L, fn).restype = C.c_int
         _lib = L
     return _lib
@@ -117,6 +118,16 @@ def cudisc_coag_rhs(ctx, rho_ptr, drho_ptr):
 def cudisc_coag_step(ctx, rho_ptr, t_span, dt_ptr, check=True):
     s = cudisc_step_stats()
     st = lib().cudisc_coag_step(ctx, rho_ptr, float(t_span), dt_ptr, C.byref(s))
+    if check:
+        _check(st, ctx)
+    return st, s
+
+
+def cudisc_coag_step_static_scratch(ctx, rho_ptr, t_span, dt_ptr, check=True):
+    """The integration of cudisc_coag_step, with the integrator's scratch in a
+    fixed device array inside the library: allocates no device memory."""
+    s = cudisc_step_stats()
+    st = lib().cudisc_coag_step_static_scratch(ctx, rho_ptr, float(t_span), dt_ptr, C.byref(s))
     if check:
         _check(st, ctx)
     return st, s

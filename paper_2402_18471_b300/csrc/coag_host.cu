@@ -517,6 +517,28 @@ cudisc_status cudisc_coag_step(cudisc_coag_ctx *c, double *rho, double t_span, d
     return finish_step(c, stats);
 }
 
+cudisc_status cudisc_coag_step_static_scratch(cudisc_coag_ctx *c, double *rho, double t_span,
+                                              double *dt_cell, cudisc_step_stats *stats)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!rho) return fail(c, CUDISC_EINVAL, "rho is NULL");
+    if (c->p.precision != CUDISC_MIXED_TF32)
+        return fail(c, CUDISC_EINVAL, "cudisc_coag_step_static_scratch needs a CUDISC_MIXED_TF32 context");
+    if (!(t_span > 0.0) || !std::isfinite(t_span)) return fail(c, CUDISC_EINVAL, "t_span must be positive and finite");
+    bool too_big = false;
+    CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
+    CUDA_TRY(c, cdc::launch_step_mixed_static(c, rho, t_span, dt_cell, &too_big));
+    if (too_big) {
+        char buf[200];
+        std::snprintf(buf, sizeof(buf),
+                      "problem needs more integrator scratch than the fixed %zu MiB static array; "
+                      "use cudisc_coag_step", cdc::static_scratch_bytes() >> 20);
+        return fail(c, CUDISC_ENOTSUP, buf);
+    }
+    CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
+    return finish_step(c, stats);
+}
+
 cudisc_status cudisc_coag_replay(cudisc_coag_ctx *c, double *rho, const double *hs,
                                  const long long *n_h, long long stride)
 {

@@ -113,4 +113,8 @@ cudaError_t launch_step_mixed(const cudisc_coag_ctx *c, double *rho, double t_sp
                               double *dt_cell, const double *replay_h,
                               const long long *replay_n, long long replay_stride);
 size_t mixed_workspace_bytes(int n_cells, int N);
+// fixed-scratch variant of the mixed step (see cudisc_coag_step_static_scratch)
+size_t static_scratch_bytes();
+cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, double t_span,
+                                     double *dt_cell, bool *too_big);
 } // namespace cdc

@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "coag_internal.h"
 
@@ -759,6 +760,79 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
 }
 
 } // namespace
+
+// ---- fixed-scratch variant -------------------------------------------------
+// Scratch for cudisc_coag_step_static_scratch: the per-slot FP64 integrator
+// state that the regular entry point keeps in the context's workspace.  It is
+// a file-scope device array of fixed size, so every GPU that loads this
+// library holds these 16 MiB until the process exits.  Host code must not
+// pass the symbol itself to a kernel (on the host it only names a stand-in);
+// the device address comes from cudaGetSymbolAddress, taken once per device.
+namespace {
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_ptr[kMaxDevices] = {};
+} // namespace
+
+size_t static_scratch_bytes() { return kStaticScratchBytes; }
+
+cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, double t_span,
+                                     double *dt_cell, bool *too_big)
+{
+    *too_big = false;
+    Config cf = mixed_config(c->n_cells, c->N);
+    const size_t need = (size_t)cf.grid * cf.NS * 5 * (size_t)c->N * sizeof(double);
+    if (need > kStaticScratchBytes) { *too_big = true; return cudaSuccess; }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    void *scratch = nullptr;
+    {
+        // set-up, once per device, with that device current
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        if (!g_scratch_ptr[dev]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+            if (e != cudaSuccess) return e;
+            g_scratch_ptr[dev] = ptr;
+        }
+        scratch = g_scratch_ptr[dev];
+    }
+    e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(c->d_counter + 1, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    MixedArgs a;
+    a.t = c->tables();
+    a.K32 = c->d_K32;
+    a.rho = rho;
+    a.drho = nullptr;
+    a.t_span = t_span;
+    a.dt_cell = dt_cell;
+    a.rtol = c->p.rtol;
+    a.atol_rel = c->p.atol_rel;
+    a.max_steps = c->p.max_substeps;
+    a.replay_h = nullptr;
+    a.replay_n = nullptr;
+    a.replay_stride = 0;
+    a.out = c->d_out;
+    a.err = c->d_counter + 1;
+    a.work = (double *)scratch;     // every slot is written before it is read
+    a.rec_dt = c->rec_dt;
+    a.rec_cap = c->rec_cap;
+    a.rec_n = c->rec_n;
+    a.rec_status = c->rec_status;
+    a.NS = cf.NS;
+    a.S = cf.S;
+    a.XS = cf.XS;
+    a.mode = MODE_STEP;
+    step_mixed_kernel<<<cf.grid, kThreads, cf.smem, c->stream>>>(a);
+    return cudaGetLastError();
+}
 
 size_t mixed_workspace_bytes(int n_cells, int N)
 {
