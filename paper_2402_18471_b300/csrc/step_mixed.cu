@@ -45,6 +45,13 @@ constexpr double A21 = 0.5, A32 = 0.75;
 constexpr double B1 = 2.0 / 9.0, B2 = 1.0 / 3.0, B3 = 4.0 / 9.0;
 constexpr double E1 = -5.0 / 72.0, E2 = 1.0 / 12.0, E3 = 1.0 / 9.0, E4 = -1.0 / 8.0;
 
+// Bytes of one pipeline stage: Bt hi/lo tiles and the generated hi/lo tiles,
+// rounded up to keep every stage 1024-byte aligned.
+__host__ __device__ constexpr int stage_size(int NS)
+{
+    return ((2 * kTileBytes + 2 * NS * 128 + 1023) / 1024) * 1024;
+}
+
 enum Mode { MODE_STEP = 0, MODE_RHS = 1, MODE_REPLAY = 2 };
 enum ErrCode { ERR_WAIT_PRODUCER = 1, ERR_WAIT_MMA = 2, ERR_WAIT_GEN = 3, ERR_WAIT_EPI = 4 };
 
@@ -62,6 +69,7 @@ struct MixedArgs {
     long long replay_stride;
     CellOut *out;
     int *err;                   // device status word
+    int *queue;                 // global work-queue head (cells past the initial fill)
     double *work;               // [grid][NS][5][N] FP64 slot state
     double *rec_dt;
     long long rec_cap;
@@ -437,6 +445,118 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const do
     }
 }
 
+// Generate one thread's share (P pairs of one cell row) of a block's operand
+// tile: a = x_i x_j K, b = x_i x_j K p_frag, each split into TF32 hi and lo
+// and stored at its place in the SW128 K-major tiles.  K comes from the
+// stage's staged rows (bulk-copied by the producer), x from the slot's row.
+template <int P>
+struct KRegs { float v[2 * P]; };
+
+// Load one thread's K share of block b (P pairs, {K, K p_frag} each).
+template <int P>
+__device__ __forceinline__ void load_k(KRegs<P> &k, const float2 *kbase, int b)
+{
+    const float *src = (const float *)(kbase + (size_t)b * kBlkPairs);
+    if constexpr (P == 4) {
+        const float4 a0 = __ldg((const float4 *)src), a1 = __ldg((const float4 *)src + 1);
+        k.v[0] = a0.x; k.v[1] = a0.y; k.v[2] = a0.z; k.v[3] = a0.w;
+        k.v[4] = a1.x; k.v[5] = a1.y; k.v[6] = a1.z; k.v[7] = a1.w;
+    } else if constexpr (P == 2) {
+        const float4 a0 = __ldg((const float4 *)src);
+        k.v[0] = a0.x; k.v[1] = a0.y; k.v[2] = a0.z; k.v[3] = a0.w;
+    } else {
+        const float2 a0 = __ldg((const float2 *)src);
+        k.v[0] = a0.x; k.v[1] = a0.y;
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void gen_block(float *chi, float *clo, const KRegs<P> &kr, const float *xr,
+                                          int bi, int bj0, int t0, int row, bool active)
+{
+    float va[2 * P];
+    if (active) {
+        const float xi = xr[bi];
+        float xj[P];
+        const float *kv = kr.v;
+        if constexpr (P == 4) {
+            const float4 v = *(const float4 *)(xr + bj0 + t0);
+            xj[0] = v.x; xj[1] = v.y; xj[2] = v.z; xj[3] = v.w;
+        } else if constexpr (P == 2) {
+            const float2 v = *(const float2 *)(xr + bj0 + t0);
+            xj[0] = v.x; xj[1] = v.y;
+        } else {
+            xj[0] = xr[bj0 + t0];
+        }
+#pragma unroll
+        for (int u = 0; u < P; u++) {
+            const float xx = xi * xj[u];
+            va[2 * u] = xx * kv[2 * u];
+            va[2 * u + 1] = xx * kv[2 * u + 1];
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 2 * P; u++) va[u] = 0.f;
+    }
+    float vh[2 * P], vl[2 * P];
+#pragma unroll
+    for (int u = 0; u < 2 * P; u++) {
+        vh[u] = tf32_rn(va[u]);
+        vl[u] = tf32_rn(va[u] - vh[u]);
+    }
+    const int e0 = 2 * t0;                                // first element of the share
+#pragma unroll
+    for (int q = 0; q < (2 * P + 3) / 4; q++) {
+        const int e = e0 + 4 * q;
+        const int off = row * 32 + ((((e >> 2) ^ (row & 7)) << 2) | (e & 3));
+        if constexpr (P >= 2) {
+            *(float4 *)(chi + off) = make_float4(vh[4 * q], vh[4 * q + 1], vh[4 * q + 2], vh[4 * q + 3]);
+            *(float4 *)(clo + off) = make_float4(vl[4 * q], vl[4 * q + 1], vl[4 * q + 2], vl[4 * q + 3]);
+        } else {
+            *(float2 *)(chi + off) = make_float2(vh[0], vh[1]);
+            *(float2 *)(clo + off) = make_float2(vl[0], vl[1]);
+        }
+    }
+}
+
+// One pass of a generator thread over all blocks: K loads run two blocks
+// ahead in registers; a row without a cell writes its zeros once per stage
+// in the pass and is skipped afterwards.
+template <int P>
+__device__ __forceinline__ bool gen_pass(const MixedArgs &a, uint8_t *stages, int stage_bytes,
+                                         const float2 *kbase, const float *xr, uint64_t *empty,
+                                         uint64_t *full_tma, uint64_t *gen_full, volatile int *s_err,
+                                         long long g0, int n_blk, int S, int NS, int row, int t0,
+                                         bool active, int lane)
+{
+    (void)full_tma;
+    KRegs<P> k0, k1, k2;
+    if (active) {
+        load_k<P>(k0, kbase, 0);
+        if (n_blk > 1) load_k<P>(k1, kbase, 1);
+    }
+    long long g = g0;
+    for (int b = 0; b < n_blk; b++, g++) {
+        if (active && b + 2 < n_blk) load_k<P>(k2, kbase, b + 2);
+        const int s = (int)(g % S);
+        const uint32_t u = (uint32_t)(g / S);
+        if (g >= S && !wwait(&empty[s], (u + 1) & 1, s_err, ERR_WAIT_GEN)) return false;
+        if (active || b < S) {
+            uint8_t *st = stages + (size_t)s * stage_bytes;
+            float *chi = (float *)(st + 2 * kTileBytes);
+            float *clo = (float *)(st + 2 * kTileBytes + NS * 128);
+            const int bi = __ldg(a.t.blk_i + b), bj0 = __ldg(a.t.blk_j0 + b);
+            gen_block<P>(chi, clo, k0, xr, bi, bj0, t0, row, active);
+            fence_async_smem();
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&gen_full[s]);
+        k0 = k1;
+        k1 = k2;
+    }
+    return true;
+}
+
 // ---- the kernel --------------------------------------------------------------
 
 __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
@@ -444,7 +564,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int NS = a.NS, S = a.S, XS = a.XS, N = a.t.N, n_blk = a.t.n_blk;
-    const int stage_bytes = 2 * kTileBytes + 2 * NS * 128;
+    const int stage_bytes = stage_size(NS);
     uint8_t *stages = sm;
     float *xrows = (float *)(sm + (size_t)S * stage_bytes);
     Slot *slots = (Slot *)(xrows + (size_t)NS * XS);
@@ -542,7 +662,6 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     const uint32_t c_hi = bt_hi + 2 * kTileBytes, c_lo = c_hi + NS * 128;
                     const uint64_t dbh = sw128_desc(bt_hi), dbl = sw128_desc(bt_lo);
                     const uint64_t dch = sw128_desc(c_hi), dcl = sw128_desc(c_lo);
-#pragma unroll
                     // accumulator chunk of this block: the pass over all blocks is
                     // split across NACC TMEM accumulators summed later in FP64
                     const int ch = (int)(((long long)b * nacc) / n_blk);
@@ -569,51 +688,22 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         const int P = NS / 16;                        // pairs per thread per block
         const int row = gt % NS;
         const int t0 = (gt / NS) * P;
+        const float *xr = xrows + (size_t)row * XS;
+        const int n_slots_k = n_blk * kBlkPairs;
         uint32_t gphase = 0;
         long long g = 0;
         for (int r = 0;; r++) {
             bool ok = true;
-            for (int b = 0; b < n_blk; b++, g++) {
-                const int s = (int)(g % S);
-                const uint32_t u = (uint32_t)(g / S);
-                if (g >= S && !wwait(&empty[s], (u + 1) & 1, &s_err, ERR_WAIT_GEN)) { ok = false; break; }
-                uint8_t *st = stages + (size_t)s * stage_bytes;
-                float *chi = (float *)(st + 2 * kTileBytes);
-                float *clo = (float *)(st + 2 * kTileBytes + NS * 128);
-                const int cell = slots[row].cell;
-                const int bi = __ldg(a.t.blk_i + b), bj0 = __ldg(a.t.blk_j0 + b);
-                const float *xr = xrows + (size_t)row * XS;
-                const float xi = xr[bi];
-                const float2 *kp = a.K32 + ((size_t)(cell < 0 ? 0 : cell) * n_blk + b) * kBlkPairs + t0;
-                for (int u2 = 0; u2 < P; u2 += 2) {
-                    float vh[4], vl[4];
-#pragma unroll
-                    for (int w = 0; w < 2; w++) {
-                        float va = 0.f, vb = 0.f;
-                        if (u2 + w < P && cell >= 0) {
-                            const float2 kv = __ldg(kp + u2 + w);
-                            const float xx = xi * xr[bj0 + t0 + u2 + w];
-                            va = xx * kv.x;
-                            vb = xx * kv.y;
-                        }
-                        const float ha = tf32_rn(va), hb = tf32_rn(vb);
-                        vh[2 * w] = ha; vh[2 * w + 1] = hb;
-                        vl[2 * w] = tf32_rn(va - ha); vl[2 * w + 1] = tf32_rn(vb - hb);
-                    }
-                    const int e = 2 * (t0 + u2);              // first element
-                    const int off = row * 32 + ((((e >> 2) ^ (row & 7)) << 2) | (e & 3));
-                    if (P >= 2) {
-                        *(float4 *)(chi + off) = make_float4(vh[0], vh[1], vh[2], vh[3]);
-                        *(float4 *)(clo + off) = make_float4(vl[0], vl[1], vl[2], vl[3]);
-                    } else {
-                        *(float2 *)(chi + off) = make_float2(vh[0], vh[1]);
-                        *(float2 *)(clo + off) = make_float2(vl[0], vl[1]);
-                    }
-                }
-                fence_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&gen_full[s]);
-            }
+            const int cell = slots[row].cell;             // fixed for the whole pass
+            const bool active = cell >= 0;
+            const float2 *kbase = a.K32 + (size_t)(active ? cell : 0) * n_slots_k + t0;
+            if (P == 4) ok = gen_pass<4>(a, stages, stage_bytes, kbase, xr, empty, full_tma, gen_full,
+                                         &s_err, g, n_blk, S, NS, row, t0, active, lane);
+            else if (P == 2) ok = gen_pass<2>(a, stages, stage_bytes, kbase, xr, empty, full_tma, gen_full,
+                                              &s_err, g, n_blk, S, NS, row, t0, active, lane);
+            else ok = gen_pass<1>(a, stages, stage_bytes, kbase, xr, empty, full_tma, gen_full,
+                                  &s_err, g, n_blk, S, NS, row, t0, active, lane);
+            g += n_blk;
             if (!ok) break;
             // ---- epilogue: D (TMEM) -> smem [slot][bin] ----
             if (!wwait(done, r & 1, &s_err, ERR_WAIT_EPI)) break;
@@ -654,10 +744,11 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                 __syncwarp();
                 if (fin) {
                     slot_finish(a, loc, sidx);
-                    int k = 0;
-                    if (lane == 0) k = atomicAdd(&s_next, 1);
-                    k = __shfl_sync(0xffffffffu, k, 0);
-                    const int c = blockIdx.x + k * gridDim.x;
+                    // refill from the global queue: cells 0 .. grid*NS-1 were the
+                    // initial fill, later ones go to whichever slot frees first
+                    int c = 0;
+                    if (lane == 0) c = (int)gridDim.x * NS + atomicAdd(a.queue, 1);
+                    c = __shfl_sync(0xffffffffu, c, 0);
                     __syncwarp();
                     if (lane == 0) sl = loc;
                     __syncwarp();
@@ -697,25 +788,25 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
 
 struct Config { int grid, NS, S, XS; size_t smem; };
 
+
 Config mixed_config(int n_cells, int N)
 {
     int dev = 0, n_sm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     Config c;
-    int per = (n_cells + n_sm - 1) / n_sm;
+    // every SM gets a CTA once there are 16 cells per SM; slots per CTA are
+    // a multiple of 16 (the MMA N), at most 64
+    c.grid = std::max(1, std::min(n_sm, (n_cells + 15) / 16));
+    const int per = (n_cells + c.grid - 1) / c.grid;
     int NS = ((per + 15) / 16) * 16;
-    NS = std::max(16, std::min(128, NS));
-    if (NS > 64) NS = 128; else if (NS > 32) NS = 64;
+    NS = std::min(NS, 64);
+    if (NS > 32) NS = 64;
     c.NS = NS;
-    c.grid = std::min(n_sm, (n_cells + NS - 1) / NS);
-    if (c.grid < 1) c.grid = 1;
-    // when cells exceed the slots, spread them over every SM
-    if ((long long)c.grid * NS < n_cells) c.grid = n_sm;
-    c.S = NS >= 128 ? 2 : 3;
+    c.S = 3;
     const int n16 = ((N + 15) / 16) * 16;
-    c.XS = n16 + 1;
-    const size_t stage = 2 * (size_t)kTileBytes + 2 * (size_t)NS * 128;
+    c.XS = n16 + 4;                              // rows 16 B aligned, 4 words off the bank period
+    const size_t stage = (size_t)stage_size(NS);
     c.smem = 1024 + c.S * stage + (size_t)NS * c.XS * 4 + (size_t)NS * sizeof(Slot) + 8 * (3 * c.S + 4);
     return c;
 }
@@ -729,7 +820,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     if (need > c->work_bytes) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(c->d_counter + 1, 0, sizeof(int), c->stream);
+    e = cudaMemsetAsync(c->d_counter + 1, 0, 2 * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
     MixedArgs a;
     a.t = c->tables();
@@ -746,6 +837,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.replay_stride = replay_stride;
     a.out = c->d_out;
     a.err = c->d_counter + 1;
+    a.queue = c->d_counter + 2;
     a.work = c->d_work;
     a.rec_dt = mode == MODE_STEP ? c->rec_dt : nullptr;
     a.rec_cap = c->rec_cap;
@@ -804,7 +896,7 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     }
     e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(c->d_counter + 1, 0, sizeof(int), c->stream);
+    e = cudaMemsetAsync(c->d_counter + 1, 0, 2 * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
     MixedArgs a;
     a.t = c->tables();
@@ -821,6 +913,7 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     a.replay_stride = 0;
     a.out = c->d_out;
     a.err = c->d_counter + 1;
+    a.queue = c->d_counter + 2;
     a.work = (double *)scratch;     // every slot is written before it is read
     a.rec_dt = c->rec_dt;
     a.rec_cap = c->rec_cap;
