@@ -13,10 +13,10 @@
 //   MMA M = 128 bins (Bt, streamed as swizzled 32 KB TF32 hi/lo tiles by the
 //   bulk-copy engine), MMA N = NS cell slots (generated operand), K = 32
 //   TF32 elements (16 pairs) per block.  Each block issues the four products
-//   of (Bt_hi + Bt_lo)(A_hi + A_lo), hi and lo rounded to nearest TF32: the
-//   hi x hi product into one of several FP32 accumulators [128 lanes x NS
-//   columns] in TMEM (a contiguous share of the blocks each), the three
-//   correction products into one more; the epilogue sums them in FP64.
+//   of (Bt_hi + Bt_lo)(A_hi + A_lo), hi and lo rounded to nearest TF32: hi x
+//   hi into one of several FP32 accumulators [128 lanes x NS columns] in TMEM
+//   (a contiguous share of the blocks each), the three corrections into one
+//   more; the epilogue sums them in FP64.
 // Warp roles: warp 0 bulk-copy producer, warp 1 MMA issuer and TMEM owner,
 // warps 2..9 generate A (x_i x_j K split into hi/lo in the SW128 K-major
 // layout) and, between right-hand sides, run the per-slot FP64 logic: the
@@ -38,6 +38,8 @@ namespace {
 
 constexpr int kGenWarps = 8;
 constexpr int kMaxMain = 8;                       // TMEM accumulators for the hi x hi products
+constexpr int kCStages = 4;                       // generated-tile ring depth
+constexpr int kMaxSB = 8;                         // mapping-tile ring depth, at most
 constexpr int kThreads = 64 + 32 * kGenWarps;
 constexpr int kTileBytes = kMBins * 128;          // one 128-row x 128 B TF32 tile
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
@@ -76,6 +78,7 @@ struct MixedArgs {
     long long *rec_n;
     int *rec_status;
     int NS, S, XS, mode;
+    int SB, NB8;                // mapping-tile ring depth, tile rows copied (bins rounded to 8)
 };
 
 struct __align__(16) Slot {
@@ -122,6 +125,8 @@ __device__ __noinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile in
 // The same wait, with one answer for the whole warp (all 32 lanes call it).
 __device__ __forceinline__ bool wwait(uint64_t *b, uint32_t parity, volatile int *s_err, int code)
 {
+    // fast path: the phase is usually complete already
+    if (__all_sync(0xffffffffu, mbar_test(b, parity))) return true;
     return __all_sync(0xffffffffu, mbar_wait(b, parity, s_err, code));
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
@@ -523,34 +528,32 @@ __device__ __forceinline__ void gen_block(float *chi, float *clo, const KRegs<P>
 // ahead in registers; a row without a cell writes its zeros once per stage
 // in the pass and is skipped afterwards.
 template <int P>
-__device__ __forceinline__ bool gen_pass(const MixedArgs &a, uint8_t *stages, int stage_bytes,
-                                         const float2 *kbase, const float *xr, uint64_t *empty,
-                                         uint64_t *full_tma, uint64_t *gen_full, volatile int *s_err,
-                                         long long g0, int n_blk, int S, int NS, int row, int t0,
-                                         bool active, int lane)
+__device__ __forceinline__ bool gen_pass(const MixedArgs &a, uint8_t *cring, int cstride,
+                                         const float2 *kbase, const float *xr, uint64_t *c_empty,
+                                         uint64_t *c_full, volatile int *s_err, long long g0, int n_blk,
+                                         int SC, int NS, int row, int t0, bool active, int lane)
 {
-    (void)full_tma;
     KRegs<P> k0, k1, k2;
     if (active) {
         load_k<P>(k0, kbase, 0);
         if (n_blk > 1) load_k<P>(k1, kbase, 1);
     }
     long long g = g0;
+    int s = (int)(g0 % SC);
+    uint32_t u = (uint32_t)(g0 / SC);
     for (int b = 0; b < n_blk; b++, g++) {
         if (active && b + 2 < n_blk) load_k<P>(k2, kbase, b + 2);
-        const int s = (int)(g % S);
-        const uint32_t u = (uint32_t)(g / S);
-        if (g >= S && !wwait(&empty[s], (u + 1) & 1, s_err, ERR_WAIT_GEN)) return false;
-        if (active || b < S) {
-            uint8_t *st = stages + (size_t)s * stage_bytes;
-            float *chi = (float *)(st + 2 * kTileBytes);
-            float *clo = (float *)(st + 2 * kTileBytes + NS * 128);
+        if (g >= SC && !wwait(&c_empty[s], (u + 1) & 1, s_err, ERR_WAIT_GEN)) return false;
+        if (active || b < SC) {
+            float *chi = (float *)(cring + (size_t)s * cstride);
+            float *clo = chi + NS * 32;
             const int bi = __ldg(a.t.blk_i + b), bj0 = __ldg(a.t.blk_j0 + b);
             gen_block<P>(chi, clo, k0, xr, bi, bj0, t0, row, active);
             fence_async_smem();
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&gen_full[s]);
+        if (lane == 0) mbar_arrive(&c_full[s]);
+        if (++s == SC) { s = 0; u++; }
         k0 = k1;
         k1 = k2;
     }
@@ -563,17 +566,21 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int NS = a.NS, S = a.S, XS = a.XS, N = a.t.N, n_blk = a.t.n_blk;
-    const int stage_bytes = stage_size(NS);
-    uint8_t *stages = sm;
-    float *xrows = (float *)(sm + (size_t)S * stage_bytes);
+    const int NS = a.NS, XS = a.XS, N = a.t.N, n_blk = a.t.n_blk;
+    const int SB = a.SB, SC = kCStages;
+    const int half_bytes = a.NB8 * 128;                 // rows of one Bt tile copied
+    const int bstride = 2 * half_bytes;                 // hi then lo, both 1024-aligned
+    const int cstride = 2 * NS * 128;
+    uint8_t *bring = sm;                                // mapping tiles (also the D staging area)
+    uint8_t *cring = bring + (size_t)SB * bstride;      // generated tiles
+    float *xrows = (float *)(cring + (size_t)SC * cstride);
     Slot *slots = (Slot *)(xrows + (size_t)NS * XS);
     uint64_t *bars = (uint64_t *)(slots + NS);
-    uint64_t *full_tma = bars, *gen_full = bars + S, *empty = bars + 2 * S;
-    uint64_t *done = bars + 3 * S, *go = bars + 3 * S + 1, *gbar = bars + 3 * S + 2;
-    uint64_t *fin = bars + 3 * S + 3;
+    uint64_t *bt_full = bars, *bt_empty = bars + SB;
+    uint64_t *c_full = bars + 2 * SB, *c_empty = bars + 2 * SB + SC;
+    uint64_t *done = bars + 2 * SB + 2 * SC, *go = done + 1, *gbar = done + 2, *fin = done + 3;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_err, s_continue, s_next;
+    __shared__ int s_err, s_continue;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // TMEM: nacc accumulators for the hi x hi products, each taking a
     // contiguous share of the blocks (every one gets at least one), plus one
@@ -587,10 +594,13 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     const uint32_t ncols = tcols <= 32 ? 32 : tcols <= 64 ? 64 : tcols <= 128 ? 128 : tcols <= 256 ? 256 : 512;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < S; s++) {
-            mbar_init(&full_tma[s], 1);
-            mbar_init(&gen_full[s], kGenWarps);
-            mbar_init(&empty[s], 1);
+        for (int s = 0; s < SB; s++) {
+            mbar_init(&bt_full[s], 1);
+            mbar_init(&bt_empty[s], 1);
+        }
+        for (int s = 0; s < SC; s++) {
+            mbar_init(&c_full[s], kGenWarps);
+            mbar_init(&c_empty[s], 1);
         }
         mbar_init(done, 1);
         mbar_init(go, 1);
@@ -598,7 +608,6 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         mbar_init(fin, 1);
         s_err = 0;
         s_continue = 1;
-        s_next = NS;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -619,8 +628,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     const uint32_t tmem = s_tmem;
 
     if (warp == 0) {
-        // ---- producer: Bt hi/lo tiles by the bulk-copy engine ----
+        // ---- producer: mapping tiles (rows 0..NB8-1 of hi and lo) by the bulk-copy engine ----
         long long g = 0;
+        int ps = 0;
+        uint32_t pu = 0;
         for (int r = 0;; r++) {
             if (r > 0) {
                 if (!wwait(go, (r - 1) & 1, &s_err, ERR_WAIT_PRODUCER)) break;
@@ -628,13 +639,16 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             }
             bool ok = true;
             for (int b = 0; b < n_blk; b++, g++) {
-                const int s = (int)(g % S);
-                const uint32_t u = (uint32_t)(g / S);
-                if (g >= S && !wwait(&empty[s], (u + 1) & 1, &s_err, ERR_WAIT_PRODUCER)) { ok = false; break; }
+                const int s = ps;
+                const uint32_t u = pu;
+                if (++ps == SB) { ps = 0; pu++; }      // ring position without divisions
+                if (g >= SB && !wwait(&bt_empty[s], (u + 1) & 1, &s_err, ERR_WAIT_PRODUCER)) { ok = false; break; }
                 if (lane == 0) {
-                    uint8_t *dst = stages + (size_t)s * stage_bytes;
-                    mbar_expect_tx(&full_tma[s], 2 * kTileBytes);
-                    bulk_g2s(dst, a.t.Btiles + (size_t)b * (2 * kTileBytes / 16), 2 * kTileBytes, &full_tma[s]);
+                    uint8_t *dst = bring + (size_t)s * bstride;
+                    const uint8_t *src = (const uint8_t *)(a.t.Btiles + (size_t)b * (2 * kTileBytes / 16));
+                    mbar_expect_tx(&bt_full[s], 2 * half_bytes);
+                    bulk_g2s(dst, src, half_bytes, &bt_full[s]);
+                    bulk_g2s(dst + half_bytes, src + kTileBytes, half_bytes, &bt_full[s]);
                 }
                 __syncwarp();
             }
@@ -644,40 +658,53 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         // ---- MMA issuer ----
         const uint32_t idesc = idesc_tf32(kMBins, NS);
         long long g = 0;
+        int ms = 0, mc = 0;
+        uint32_t mu = 0, mv = 0;
         for (int r = 0;; r++) {
             if (r > 0) {
                 if (!wwait(go, (r - 1) & 1, &s_err, ERR_WAIT_MMA)) break;
                 if (!s_continue) break;
             }
             bool ok = true;
+            int ch = 0, ch_next = (n_blk + nacc - 1) / nacc;   // hi x hi accumulator of the block
+            bool first = true;
             for (int b = 0; b < n_blk; b++, g++) {
-                const int s = (int)(g % S);
-                const uint32_t u = (uint32_t)(g / S);
-                if (!wwait(&full_tma[s], u & 1, &s_err, ERR_WAIT_MMA) ||
-                    !wwait(&gen_full[s], u & 1, &s_err, ERR_WAIT_MMA)) { ok = false; break; }
+                const int sb = ms, sc = mc;
+                const uint32_t ub = mu, uc = mv;
+                if (++ms == SB) { ms = 0; mu++; }
+                if (++mc == SC) { mc = 0; mv++; }
+                if (b == ch_next) { ch++; ch_next = (int)(((long long)(ch + 1) * n_blk + nacc - 1) / nacc); first = true; }
+                if (!wwait(&bt_full[sb], ub & 1, &s_err, ERR_WAIT_MMA) ||
+                    !wwait(&c_full[sc], uc & 1, &s_err, ERR_WAIT_MMA)) { ok = false; break; }
                 tc_fence_after();
                 if (lane == 0) {
-                    uint8_t *st = stages + (size_t)s * stage_bytes;
-                    const uint32_t bt_hi = su32(st), bt_lo = bt_hi + kTileBytes;
-                    const uint32_t c_hi = bt_hi + 2 * kTileBytes, c_lo = c_hi + NS * 128;
+                    const uint32_t bt_hi = su32(bring + (size_t)sb * bstride), bt_lo = bt_hi + half_bytes;
+                    const uint32_t c_hi = su32(cring + (size_t)sc * cstride), c_lo = c_hi + NS * 128;
                     const uint64_t dbh = sw128_desc(bt_hi), dbl = sw128_desc(bt_lo);
                     const uint64_t dch = sw128_desc(c_hi), dcl = sw128_desc(c_lo);
-                    // accumulator chunk of this block: the pass over all blocks is
-                    // split across NACC TMEM accumulators summed later in FP64
-                    const int ch = (int)(((long long)b * nacc) / n_blk);
-                    const bool first = (b == 0) || ((int)(((long long)(b - 1) * nacc) / n_blk) != ch);
+                    // the pass over all blocks is split across nacc TMEM
+                    // accumulators (contiguous block ranges) summed later in FP64
                     const uint32_t dt = tmem + (uint32_t)(ch * NS);
                     const uint32_t dc = tmem + (uint32_t)(nacc * NS);
-                    for (int kk = 0; kk < 4; kk++) {
+                    // hi x hi into the block's accumulator; hi x lo, lo x hi and
+                    // lo x lo into the correction accumulator
+                    mma_tf32(dt, dbh, dch, idesc, first ? 0u : 1u);
+                    mma_tf32(dc, dbh, dcl, idesc, b > 0 ? 1u : 0u);
+                    mma_tf32(dc, dbl, dch, idesc, 1u);
+                    mma_tf32(dc, dbl, dcl, idesc, 1u);
+#pragma unroll
+                    for (int kk = 1; kk < 4; kk++) {
                         const uint64_t adv = (uint64_t)(kk * 2);   // 32 bytes per K step
-                        mma_tf32(dt, dbh + adv, dch + adv, idesc, (!first || kk > 0) ? 1u : 0u);
-                        mma_tf32(dc, dbh + adv, dcl + adv, idesc, (b > 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32(dt, dbh + adv, dch + adv, idesc, 1u);
+                        mma_tf32(dc, dbh + adv, dcl + adv, idesc, 1u);
                         mma_tf32(dc, dbl + adv, dch + adv, idesc, 1u);
                         mma_tf32(dc, dbl + adv, dcl + adv, idesc, 1u);
                     }
-                    mma_commit(&empty[s]);
+                    mma_commit(&bt_empty[sb]);
+                    mma_commit(&c_empty[sc]);
                     if (b == n_blk - 1) mma_commit(done);
                 }
+                first = false;
                 __syncwarp();
             }
             if (!ok) break;
@@ -697,18 +724,18 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             const int cell = slots[row].cell;             // fixed for the whole pass
             const bool active = cell >= 0;
             const float2 *kbase = a.K32 + (size_t)(active ? cell : 0) * n_slots_k + t0;
-            if (P == 4) ok = gen_pass<4>(a, stages, stage_bytes, kbase, xr, empty, full_tma, gen_full,
-                                         &s_err, g, n_blk, S, NS, row, t0, active, lane);
-            else if (P == 2) ok = gen_pass<2>(a, stages, stage_bytes, kbase, xr, empty, full_tma, gen_full,
-                                              &s_err, g, n_blk, S, NS, row, t0, active, lane);
-            else ok = gen_pass<1>(a, stages, stage_bytes, kbase, xr, empty, full_tma, gen_full,
-                                  &s_err, g, n_blk, S, NS, row, t0, active, lane);
+            if (P == 4) ok = gen_pass<4>(a, cring, cstride, kbase, xr, c_empty, c_full, &s_err, g, n_blk,
+                                         SC, NS, row, t0, active, lane);
+            else if (P == 2) ok = gen_pass<2>(a, cring, cstride, kbase, xr, c_empty, c_full, &s_err, g,
+                                              n_blk, SC, NS, row, t0, active, lane);
+            else ok = gen_pass<1>(a, cring, cstride, kbase, xr, c_empty, c_full, &s_err, g, n_blk, SC,
+                                  NS, row, t0, active, lane);
             g += n_blk;
             if (!ok) break;
             // ---- epilogue: D (TMEM) -> smem [slot][bin] ----
             if (!wwait(done, r & 1, &s_err, ERR_WAIT_EPI)) break;
             tc_fence_after();
-            double *Dsm = (double *)stages;               // stages are idle now
+            double *Dsm = (double *)bring;                // the mapping-tile ring is idle now
             const int DS = N;
             {
                 const int q = warp & 3;                   // TMEM lane quadrant of this warp
@@ -786,7 +813,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     if (threadIdx.x == 0 && s_err) atomicCAS(a.err, 0, s_err);
 }
 
-struct Config { int grid, NS, S, XS; size_t smem; };
+struct Config { int grid, NS, S, XS, SB, NB8; size_t smem; };
 
 
 Config mixed_config(int n_cells, int N)
@@ -803,11 +830,24 @@ Config mixed_config(int n_cells, int N)
     NS = std::min(NS, 64);
     if (NS > 32) NS = 64;
     c.NS = NS;
-    c.S = 3;
+    c.S = kCStages;
     const int n16 = ((N + 15) / 16) * 16;
     c.XS = n16 + 4;                              // rows 16 B aligned, 4 words off the bank period
-    const size_t stage = (size_t)stage_size(NS);
-    c.smem = 1024 + c.S * stage + (size_t)NS * c.XS * 4 + (size_t)NS * sizeof(Slot) + 8 * (3 * c.S + 4);
+    c.NB8 = ((N + 7) / 8) * 8;
+    const size_t bstride = 2 * (size_t)c.NB8 * 128;
+    const size_t cring = (size_t)kCStages * 2 * NS * 128;
+    const size_t tail = (size_t)NS * c.XS * 4 + (size_t)NS * sizeof(Slot) + 8 * (2 * kMaxSB + 2 * kCStages + 4);
+    const size_t budget = 232448 - 1024 - 2048;  // opt-in shared memory, alignment, static
+    int SB = (int)((budget - cring - tail) / bstride);
+    SB = std::min(SB, kMaxSB);
+    // the D staging area (NS x N doubles) aliases the mapping-tile ring
+    while ((size_t)SB * bstride < (size_t)NS * N * 8 && SB < kMaxSB) SB++;
+    c.SB = SB;
+    // the MMA reads all 128 tile rows: rows past NB8 of the last tile fall in
+    // the bytes after the ring, which must stay inside the allocation
+    const size_t ring_end = (size_t)SB * bstride;
+    const size_t layout_end = ring_end + cring + tail;
+    c.smem = 1024 + std::max(layout_end, ring_end + (size_t)kTileBytes);
     return c;
 }
 
@@ -846,6 +886,8 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.NS = cf.NS;
     a.S = cf.S;
     a.XS = cf.XS;
+    a.SB = cf.SB;
+    a.NB8 = cf.NB8;
     a.mode = mode;
     step_mixed_kernel<<<cf.grid, kThreads, cf.smem, c->stream>>>(a);
     return cudaGetLastError();
@@ -922,6 +964,8 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     a.NS = cf.NS;
     a.S = cf.S;
     a.XS = cf.XS;
+    a.SB = cf.SB;
+    a.NB8 = cf.NB8;
     a.mode = MODE_STEP;
     step_mixed_kernel<<<cf.grid, kThreads, cf.smem, c->stream>>>(a);
     return cudaGetLastError();
