@@ -355,7 +355,7 @@ static void free_ctx(cudisc_coag_ctx *c)
     void *ptrs[] = {c->d_m, c->d_minv, c->d_a, c->d_me, c->d_pair_ij, c->d_row, c->d_ent_p,
                     c->d_ent_ab, c->d_frow, c->d_fent_p, c->d_fent_m, c->d_Ntab, c->d_blk_i,
                     c->d_blk_j0, c->d_Btiles, c->d_prep, c->d_prep32, c->d_scal, c->d_K64,
-                    c->d_K32, c->d_out, c->d_work, c->d_counter};
+                    c->d_K32, c->d_out, c->d_work, c->d_counter, c->d_scal32};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -398,6 +398,7 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
     e = cudaMalloc(&c->d_prep, nc * cdc::PF_COUNT * N * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_prep32, nc * cdc::P3_COUNT * N * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_scal, nc * sizeof(cdc::CellScal));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_scal32, nc * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_out, nc * sizeof(CellOut));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, 64 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_counter, 0, 64 * sizeof(int));

@@ -32,8 +32,10 @@ enum PrepField { PF_ST = 0, PF_VR, PF_VPHI, PF_VZ, PF_G1, PF_G2, PF_COUNT };
 // P3_SS, P3_SSMD, P3_OMSS: St* = clamp(1.6 St, Re^-1/2, 1), St* - Re^-1/2 and
 // 1 - St* of the bin when it is the larger of a pair, formed in FP64 (both
 // differences can be tiny next to their operands).
+// P3_U = 8 k_B T / (pi m_k) (so v_BM^2 = U_i + U_j), P3_A = a_k, P3_M = m_k:
+// the pair loop of the FP32 builder then needs no FP64 arithmetic.
 enum Prep32Field { P3_ST = 0, P3_VRH, P3_VRL, P3_VPH, P3_VPL, P3_VZH, P3_VZL,
-                   P3_SS, P3_SSMD, P3_OMSS, P3_COUNT };
+                   P3_SS, P3_SSMD, P3_OMSS, P3_U, P3_A, P3_M, P3_COUNT };
 
 // Per-cell integration scalars written back by the step kernels.
 struct CellOut {
@@ -84,6 +86,7 @@ struct cudisc_coag_ctx {
     double *d_prep = nullptr;          // [n_cells][PF_COUNT][N]
     float *d_prep32 = nullptr;         // same, FP32
     cdc::CellScal *d_scal = nullptr;   // [n_cells]
+    float4 *d_scal32 = nullptr;        // [n_cells] {delta, Vg2, etavK, ZOm} in FP32
     double2 *d_K64 = nullptr;          // [n_cells][Np]      {K, K p_frag}
     float2 *d_K32 = nullptr;           // [n_cells][n_blk*16] {K, K p_frag}
     // integration workspace

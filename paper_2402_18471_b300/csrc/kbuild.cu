@@ -32,12 +32,12 @@ KParams kparams(const cudisc_coag_params &p)
 // Omega), dust velocities (input or terminal drift and settling), and the
 // per-bin parts of the Ormel & Cuzzi closed forms.
 __global__ void __launch_bounds__(128) prep_kernel(
-    int c0, KParams kp, int n_cells, int N, const double *__restrict__ a,
+    int c0, KParams kp, int n_cells, int N, const double *__restrict__ a, const double *__restrict__ m,
     const double *__restrict__ rho_gas, const double *__restrict__ T,
     const double *__restrict__ alpha, const double *__restrict__ R,
     const double *__restrict__ Z, const double *__restrict__ eta,
     const double *__restrict__ v_dust, double *__restrict__ prep,
-    float *__restrict__ prep32, CellScal *__restrict__ scal)
+    float *__restrict__ prep32, CellScal *__restrict__ scal, float4 *__restrict__ scal32)
 {
     const int c = c0 + blockIdx.y;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(128) prep_kernel(
     const double Ss = fmin(fmax(1.6 * St, delta), 1.0);
     const float v32[P3_COUNT] = {(float)St, vRh, (float)(vR - vRh), vPh, (float)(vphi - vPh),
                                  vZh, (float)(vZ - vZh), (float)Ss, (float)(Ss - delta),
-                                 (float)(1.0 - Ss)};
+                                 (float)(1.0 - Ss), (float)(8.0 * kp.k_B * Tc / (M_PI * m[k])),
+                                 (float)a[k], (float)m[k]};
 #pragma unroll
     for (int f = 0; f < P3_COUNT; f++) pf[f * N + k] = v32[f];
     if (k == 0) {
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(128) prep_kernel(
         s.ZOm = Zc * Om;
         s.pad = 0.0;
         scal[c] = s;
+        scal32[c] = make_float4((float)s.delta, (float)s.Vg2, (float)s.etavK, (float)s.ZOm);
     }
 }
 
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
     const int *__restrict__ blk_i, const int *__restrict__ blk_j0,
     const double *__restrict__ a, const double *__restrict__ minv,
     const double *__restrict__ m, const float *__restrict__ prep32,
-    const CellScal *__restrict__ scal, float2 *__restrict__ Kout)
+    const float4 *__restrict__ scal32, float2 *__restrict__ Kout)
 {
     const int c = c0 + blockIdx.y;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -165,8 +167,8 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
     float2 out = make_float2(0.f, 0.f);
     if (j <= i) {
         const float *pr = prep32 + (size_t)c * P3_COUNT * N;
-        const CellScal s = scal[c];
-        const float d = (float)s.delta;
+        const float4 s4 = scal32[c];
+        const float d = s4.x, Vg2 = s4.y;
         const float Si = pr[P3_ST * N + i], Sj = pr[P3_ST * N + j];
         float S1 = Si, S2 = Sj;
         int i1 = i;
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
         const float nII = Ssmd * ((S1 * sd + Sd) * (P2 * R2) + (S2 * sd + Sd) * (P1 * R1));
         const float dII = (P1 * R1) * (P2 * R2);
         const float V = fmaxf(nI / dI + nII / dII, 0.0f);
-        const float vbm2 = (float)(s.kT8pi * (minv[i] + minv[j]));
+        const float vbm2 = pr[P3_U * N + i] + pr[P3_U * N + j];
         float dR, dP, dZ;
         if (has_vdust) {
             // input velocities: difference of FP32 hi/lo pairs
@@ -205,17 +207,17 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
             const float dS = Si - Sj;
             const float ai = 1.0f + Si * Si, aj = 1.0f + Sj * Sj;
             const float rij = 1.0f / (ai * aj);
-            const float ev = (float)s.etavK;
+            const float ev = s4.z;
             dR = -2.0f * ev * dS * (1.0f - Si * Sj) * rij;
             dP = ev * dS * (Si + Sj) * rij;
-            dZ = -(float)s.ZOm * dS / ((1.0f + Si) * (1.0f + Sj));
+            dZ = -s4.w * dS / ((1.0f + Si) * (1.0f + Sj));
         }
-        const float dv2 = vbm2 + (float)s.Vg2 * V + (dR * dR + dP * dP + dZ * dZ);
+        const float dv2 = vbm2 + Vg2 * V + (dR * dR + dP * dP + dZ * dZ);
         const float dv = sqrtf(dv2);
         float K;
         if (kernel_mode == CUDISC_KERNEL_CONSTANT) K = kc;
-        else if (kernel_mode == CUDISC_KERNEL_ADDITIVE) K = (float)(kc * (m[i] + m[j]));
-        else { const float sa = (float)(a[i] + a[j]); K = 3.14159265358979f * sa * sa * dv; }
+        else if (kernel_mode == CUDISC_KERNEL_ADDITIVE) K = kc * (pr[P3_M * N + i] + pr[P3_M * N + j]);
+        else { const float sa = pr[P3_A * N + i] + pr[P3_A * N + j]; K = 3.14159265358979f * sa * sa * dv; }
         float pf;
         if (frag_mode == CUDISC_FRAG_NONE) pf = 0.0f;
         else if (frag_mode == CUDISC_FRAG_ALL) pf = 1.0f;
@@ -261,9 +263,9 @@ cudaError_t launch_prep(const cudisc_coag_ctx *c)
     const cudisc_coag_params &p = c->p;
     for (int c0 = 0; c0 < c->n_cells; c0 += kMaxGridY) {
     dim3 grid((c->N + 127) / 128, std::min(kMaxGridY, c->n_cells - c0));
-    prep_kernel<<<grid, 128, 0, c->stream>>>(c0, kparams(p), c->n_cells, c->N, c->d_a, p.rho_gas, p.T,
+    prep_kernel<<<grid, 128, 0, c->stream>>>(c0, kparams(p), c->n_cells, c->N, c->d_a, c->d_m, p.rho_gas, p.T,
                                              p.alpha, p.R, p.Z, p.eta, p.v_dust, c->d_prep,
-                                             c->d_prep32, c->d_scal);
+                                             c->d_prep32, c->d_scal, c->d_scal32);
     }
     return cudaGetLastError();
 }
@@ -285,7 +287,7 @@ cudaError_t launch_kbuild(const cudisc_coag_ctx *c)
         kbuild32_kernel<<<grid, 256, 0, c->stream>>>(
             c0, (float)p.kernel_const, (float)p.v_frag, p.kernel_mode, p.frag_mode, p.v_dust != nullptr,
             c->n_cells, c->N,
-            n_slots, c->d_blk_i, c->d_blk_j0, c->d_a, c->d_minv, c->d_m, c->d_prep32, c->d_scal,
+            n_slots, c->d_blk_i, c->d_blk_j0, c->d_a, c->d_minv, c->d_m, c->d_prep32, c->d_scal32,
             c->d_K32);
         }
     }

@@ -217,13 +217,20 @@ __device__ __forceinline__ float tf32_rn(float v)
 
 // ---- per-slot logic (one warp per slot, lanes over bins) ------------------
 
-struct SlotBufs { double *y, *k1, *k2, *k3, *Y; };
+// Slot state in global scratch (per slot 5 N doubles are reserved): the state
+// y in FP64, its scaled copy yx = y / Sx and the stage right-hand sides in the
+// same scaled units (kx = f / Sx = Sx D) in FP32.  The stage inputs, the error
+// norm and the step controller work in FP32 (their rounding sits below the
+// contraction's own ~3e-7); FP64 holds the state and the mass budget of every
+// accepted increment, so total mass is conserved to FP64 rounding.
+struct SlotBufs { double *y; float *yx, *k1, *k2, *k3; };
 
 __device__ __forceinline__ SlotBufs slot_bufs(const MixedArgs &a, int slot)
 {
     const int N = a.t.N;
     double *base = a.work + ((size_t)blockIdx.x * a.NS + slot) * 5 * (size_t)N;
-    return {base, base + N, base + 2 * N, base + 3 * N, base + 4 * N};
+    float *f = (float *)(base + N);
+    return {base, f, f + N, f + 2 * N, f + 3 * N};
 }
 
 // Load cell c into slot: state, scales, phase 0 (or mark the slot empty).
@@ -247,7 +254,12 @@ __device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, i
     s = warp_sum(s);
     sa = warp_sum(sa);
     const double Sx = sa > 0.0 ? sa : 1.0;
-    for (int k = lane; k < a.XS; k += 32) xrow[k] = (k < N) ? (float)(B.y[k] / Sx) : 0.f;
+    const double r = 1.0 / Sx;
+    for (int k = lane; k < a.XS; k += 32) {
+        const float v = (k < N) ? (float)(B.y[k] * r) : 0.f;
+        if (k < N) B.yx[k] = v;
+        xrow[k] = v;
+    }
     if (lane == 0) {
         sl.cell = c;
         sl.phase = 0;
@@ -286,68 +298,92 @@ __device__ void slot_finish(const MixedArgs &a, Slot &sl, int slot)
     }
 }
 
-// Stage input x = Y / Sx for the next right-hand side.
-__device__ __forceinline__ void set_x(const MixedArgs &a, const Slot &sl, float *xrow, const double *Y)
+// Accept an increment dx (scaled units, FP32) into the FP64 state: the
+// residual of sum_k dx_k is moved in proportion to |dx_k| (mass budget),
+// then y += Sx dx and yx = y / Sx.
+__device__ void commit_increment(const Slot &sl, SlotBufs B, int N, const float *dx)
 {
-    const int N = a.t.N, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
+    double d[(kMBins + 31) / 32];
+    double s = 0.0, sa = 0.0;
+#pragma unroll
+    for (int m = 0; m < (kMBins + 31) / 32; m++) {
+        const int k = lane + 32 * m;
+        d[m] = (k < N) ? (double)dx[m] * sl.Sx : 0.0;
+        s += d[m];
+        sa += fabs(d[m]);
+    }
+    s = warp_sum(s);
+    sa = warp_sum(sa);
+    const double q = sa > 0.0 ? s / sa : 0.0;
     const double r = 1.0 / sl.Sx;
-    for (int k = lane; k < N; k += 32) xrow[k] = (float)(Y[k] * r);
+#pragma unroll
+    for (int m = 0; m < (kMBins + 31) / 32; m++) {
+        const int k = lane + 32 * m;
+        if (k < N) {
+            const double y = B.y[k] + (d[m] - q * fabs(d[m]));
+            B.y[k] = y;
+            B.yx[k] = (float)(y * r);
+        }
+    }
+    __syncwarp();
 }
 
-// Y = y + hs * A21 * k1 after choosing the step (shared by the first step
-// and every step after an accept or reject).
+// First stage input x = yx + hs A21 k1 after choosing the step (shared by
+// the first step and every step after an accept or reject).
 __device__ bool begin_step(const MixedArgs &a, Slot &sl, float *xrow, SlotBufs B)
 {
     const int N = a.t.N, lane = threadIdx.x & 31;
     if (sl.nacc + sl.nrej >= a.max_steps) { sl.status = CUDISC_EMAXSTEPS; return false; }
     sl.last = (sl.h >= a.t_span - sl.t);
     sl.hs = sl.last ? (a.t_span - sl.t) : sl.h;
-    for (int k = lane; k < N; k += 32) B.Y[k] = B.y[k] + sl.hs * A21 * B.k1[k];
-    __syncwarp();
-    set_x(a, sl, xrow, B.Y);
+    const float c1 = (float)(sl.hs * A21);
+    for (int k = lane; k < N; k += 32) xrow[k] = B.yx[k] + c1 * B.k1[k];
     sl.phase = 1;
     return true;
 }
 
-// Process one right-hand side result f = S^2 D for this slot.  Returns true
-// when the slot finished its cell.
-__device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const double *Drow, int slot)
+// Process one right-hand side result, D = sum of the TMEM accumulators for
+// this slot (kx = Sx D in scaled units).  Returns true when the slot
+// finished its cell.
+__device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const float *Drow, int slot)
 {
     const int N = a.t.N, lane = threadIdx.x & 31;
+    constexpr int MB = (kMBins + 31) / 32;
     SlotBufs B = slot_bufs(a, slot);
-    const double S2 = sl.Sx * sl.Sx;
-    // FP64 mass budget: restore sum_k f_k = 0 by moving the residual in
-    // proportion to |f_k| (the redistribution conserves mass exactly).
-    double fv[(kMBins + 31) / 32];
-    double s = 0.0, sa = 0.0;
+    const float sx = (float)sl.Sx;
+    float kv[MB];
 #pragma unroll
-    for (int m = 0; m < (kMBins + 31) / 32; m++) {
+    for (int m = 0; m < MB; m++) {
         const int k = lane + 32 * m;
-        fv[m] = (k < N) ? S2 * Drow[k] : 0.0;
-        s += fv[m];
-        sa += fabs(fv[m]);
-    }
-    s = warp_sum(s);
-    sa = warp_sum(sa);
-    if (sa > 0.0) {
-        const double r = s / sa;
-#pragma unroll
-        for (int m = 0; m < (kMBins + 31) / 32; m++) fv[m] -= r * fabs(fv[m]);
+        kv[m] = (k < N) ? sx * Drow[k] : 0.f;
     }
     if (a.mode == MODE_RHS) {
+        // d rho / dt = Sx^2 D with the FP64 mass budget
+        double fv[MB], s = 0.0, sa = 0.0;
 #pragma unroll
-        for (int m = 0; m < (kMBins + 31) / 32; m++) {
+        for (int m = 0; m < MB; m++) {
             const int k = lane + 32 * m;
-            if (k < N) a.drho[(size_t)sl.cell * N + k] = fv[m];
+            fv[m] = (k < N) ? sl.Sx * sl.Sx * (double)Drow[k] : 0.0;
+            s += fv[m];
+            sa += fabs(fv[m]);
+        }
+        s = warp_sum(s);
+        sa = warp_sum(sa);
+        const double q = sa > 0.0 ? s / sa : 0.0;
+#pragma unroll
+        for (int m = 0; m < MB; m++) {
+            const int k = lane + 32 * m;
+            if (k < N) a.drho[(size_t)sl.cell * N + k] = fv[m] - q * fabs(fv[m]);
         }
         return true;
     }
-    double *dst = sl.phase == 0 ? B.k1 : sl.phase == 1 ? B.k2 : sl.phase == 2 ? B.k3 : nullptr;
+    float *dst = sl.phase == 0 ? B.k1 : sl.phase == 1 ? B.k2 : sl.phase == 2 ? B.k3 : nullptr;
     if (dst) {
 #pragma unroll
-        for (int m = 0; m < (kMBins + 31) / 32; m++) {
+        for (int m = 0; m < MB; m++) {
             const int k = lane + 32 * m;
-            if (k < N) dst[k] = fv[m];
+            if (k < N) dst[k] = kv[m];
         }
         __syncwarp();
     }
@@ -356,23 +392,26 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const do
         const double hh = nh > 0 ? a.replay_h[(size_t)sl.cell * a.replay_stride + sl.nrep] : 0.0;
         if (sl.phase == 0) {
             if (nh == 0) return true;
-            for (int k = lane; k < N; k += 32) B.Y[k] = B.y[k] + hh * A21 * B.k1[k];
-            __syncwarp();
-            set_x(a, sl, xrow, B.Y);
+            const float c1 = (float)(hh * A21);
+            for (int k = lane; k < N; k += 32) xrow[k] = B.yx[k] + c1 * B.k1[k];
             sl.phase = 1;
         } else if (sl.phase == 1) {
-            for (int k = lane; k < N; k += 32) B.Y[k] = B.y[k] + hh * A32 * B.k2[k];
-            __syncwarp();
-            set_x(a, sl, xrow, B.Y);
+            const float c2 = (float)(hh * A32);
+            for (int k = lane; k < N; k += 32) xrow[k] = B.yx[k] + c2 * B.k2[k];
             sl.phase = 2;
         } else {
-            for (int k = lane; k < N; k += 32)
-                B.y[k] = B.y[k] + hh * (B1 * B.k1[k] + B2 * B.k2[k] + B3 * B.k3[k]);
-            __syncwarp();
+            const float b1 = (float)(hh * B1), b2 = (float)(hh * B2), b3 = (float)(hh * B3);
+            float dx[MB];
+#pragma unroll
+            for (int m = 0; m < MB; m++) {
+                const int k = lane + 32 * m;
+                dx[m] = (k < N) ? b1 * B.k1[k] + b2 * B.k2[k] + b3 * B.k3[k] : 0.f;
+            }
+            commit_increment(sl, B, N, dx);
             sl.nrep++;
             sl.nacc = sl.nrep;
             if (sl.nrep >= nh) return true;
-            set_x(a, sl, xrow, B.y);
+            for (int k = lane; k < N; k += 32) xrow[k] = B.yx[k];
             sl.phase = 0;
         }
         return false;
@@ -381,58 +420,74 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const do
     switch (sl.phase) {
     case 0: {
         if (!(sl.h > 0.0)) {
-            double q = INFINITY;
+            const float atolx = (float)(sl.atol / sl.Sx);
+            float q = INFINITY;
             for (int k = lane; k < N; k += 32)
-                if (B.k1[k] != 0.0) q = fmin(q, (fabs(B.y[k]) + sl.atol) / fabs(B.k1[k]));
-            q = warp_min(q);
-            sl.h = isfinite(q) ? 0.1 * q : a.t_span;
+                if (B.k1[k] != 0.f) q = fminf(q, (fabsf(B.yx[k]) + atolx) / fabsf(B.k1[k]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) q = fminf(q, __shfl_xor_sync(0xffffffffu, q, o));
+            sl.h = isfinite(q) ? 0.1 * (double)q : a.t_span;
             if (sl.h > a.t_span) sl.h = a.t_span;
         }
         return !begin_step(a, sl, xrow, B);
     }
-    case 1:
-        for (int k = lane; k < N; k += 32) B.Y[k] = B.y[k] + sl.hs * A32 * B.k2[k];
-        __syncwarp();
-        set_x(a, sl, xrow, B.Y);
+    case 1: {
+        const float c2 = (float)(sl.hs * A32);
+        for (int k = lane; k < N; k += 32) xrow[k] = B.yx[k] + c2 * B.k2[k];
         sl.phase = 2;
         return false;
-    case 2:
+    }
+    case 2: {
+        const float b1 = (float)(sl.hs * B1), b2 = (float)(sl.hs * B2), b3 = (float)(sl.hs * B3);
         for (int k = lane; k < N; k += 32)
-            B.Y[k] = B.y[k] + sl.hs * (B1 * B.k1[k] + B2 * B.k2[k] + B3 * B.k3[k]);
-        __syncwarp();
-        set_x(a, sl, xrow, B.Y);
+            xrow[k] = B.yx[k] + (b1 * B.k1[k] + b2 * B.k2[k] + b3 * B.k3[k]);
         sl.phase = 3;
         return false;
+    }
     default: {
-        // phase 3: fv holds k4 = f(y1), y1 is in B.Y
-        double E = 0.0, ymin = INFINITY, fin = 1.0;
+        // phase 3: kv holds k4 = f(y1); y1 = yx + dx is the stage input
+        const float b1 = (float)(sl.hs * B1), b2 = (float)(sl.hs * B2), b3 = (float)(sl.hs * B3);
+        const float e1 = (float)(sl.hs * E1), e2 = (float)(sl.hs * E2), e3 = (float)(sl.hs * E3),
+                    e4 = (float)(sl.hs * E4);
+        const float atolx = (float)(sl.atol / sl.Sx), rtol = (float)a.rtol;
+        float dx[MB];
+        float E = 0.f, ymin = INFINITY, fin = 1.f;
 #pragma unroll
-        for (int m = 0; m < (kMBins + 31) / 32; m++) {
+        for (int m = 0; m < MB; m++) {
             const int k = lane + 32 * m;
+            dx[m] = 0.f;
             if (k < N) {
-                const double e = sl.hs * (E1 * B.k1[k] + E2 * B.k2[k] + E3 * B.k3[k] + E4 * fv[m]);
-                const double sc = sl.atol + a.rtol * fmax(fabs(B.y[k]), fabs(B.Y[k]));
-                const double r = fabs(e) / sc;
-                if (!isfinite(r) || !isfinite(B.Y[k])) fin = 0.0;
+                const float k1 = B.k1[k], k2 = B.k2[k], k3 = B.k3[k], yx = B.yx[k];
+                dx[m] = b1 * k1 + b2 * k2 + b3 * k3;
+                const float y1 = yx + dx[m];
+                const float e = e1 * k1 + e2 * k2 + e3 * k3 + e4 * kv[m];
+                const float sc = atolx + rtol * fmaxf(fabsf(yx), fabsf(y1));
+                const float r = fabsf(e) / sc;
+                if (!isfinite(r) || !isfinite(y1)) fin = 0.f;
                 if (r > E) E = r;
-                if (B.Y[k] < ymin) ymin = B.Y[k];
+                if (y1 < ymin) ymin = y1;
             }
         }
-        E = warp_max(E);
-        ymin = warp_min(ymin);
-        const bool finite = warp_min(fin) > 0.5;
-        if (finite && E <= 1.0 && ymin >= -sl.atol) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            E = fmaxf(E, __shfl_xor_sync(0xffffffffu, E, o));
+            ymin = fminf(ymin, __shfl_xor_sync(0xffffffffu, ymin, o));
+            fin = fminf(fin, __shfl_xor_sync(0xffffffffu, fin, o));
+        }
+        const bool finite = fin > 0.5f;
+        if (finite && E <= 1.f && ymin >= -atolx) {
+            commit_increment(sl, B, N, dx);
             sl.t = sl.last ? a.t_span : sl.t + sl.hs;
 #pragma unroll
-            for (int m = 0; m < (kMBins + 31) / 32; m++) {
+            for (int m = 0; m < MB; m++) {
                 const int k = lane + 32 * m;
-                if (k < N) { B.y[k] = B.Y[k]; B.k1[k] = fv[m]; }
+                if (k < N) B.k1[k] = kv[m];                 // FSAL
             }
             __syncwarp();
             if (lane == 0 && a.rec_dt && sl.nacc < a.rec_cap)
                 a.rec_dt[(size_t)sl.cell * a.rec_cap + sl.nacc] = sl.hs;
             sl.nacc++;
-            double fac = (E > 0.0) ? 0.9 * pow(E, -1.0 / 3.0) : 5.0;
+            double fac = (E > 0.f) ? 0.9 * pow((double)E, -1.0 / 3.0) : 5.0;
             fac = fmin(fmax(fac, 0.2), 5.0);
             if (!(sl.last && sl.hs < sl.h)) sl.h = sl.hs * fac;
             if (sl.t >= a.t_span) return true;
@@ -440,7 +495,7 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const do
             sl.nrej++;
             double fac;
             if (!finite) fac = 0.2;
-            else if (E > 1.0) fac = fmax(0.9 * pow(E, -1.0 / 3.0), 0.2);
+            else if (E > 1.f) fac = fmax(0.9 * pow((double)E, -1.0 / 3.0), 0.2);
             else fac = 0.5;
             sl.h = sl.hs * fac;
             if (sl.h < 1e-14 * a.t_span) { sl.status = finite ? CUDISC_EDTMIN : CUDISC_ENONFINITE; return true; }
@@ -735,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             // ---- epilogue: D (TMEM) -> smem [slot][bin] ----
             if (!wwait(done, r & 1, &s_err, ERR_WAIT_EPI)) break;
             tc_fence_after();
-            double *Dsm = (double *)bring;                // the mapping-tile ring is idle now
+            float *Dsm = (float *)bring;                  // the mapping-tile ring is idle now
             const int DS = N;
             {
                 const int q = warp & 3;                   // TMEM lane quadrant of this warp
@@ -743,25 +798,30 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                 const int c0 = half * (NS / 2), c1 = c0 + NS / 2;
                 const int bin = 32 * q + lane;
                 for (int cc = c0; cc < c1; cc += 8) {
-                    double acc[8];
+                    // compensated (Neumaier) FP32 sum of the accumulators
+                    float sum[8], cmp[8];
 #pragma unroll
-                    for (int z = 0; z < 8; z++) acc[z] = 0.0;
+                    for (int z = 0; z < 8; z++) { sum[z] = 0.f; cmp[z] = 0.f; }
                     for (int ch = 0; ch <= nacc; ch++) {
                         float v[8];
                         tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ch * NS + cc), v);
 #pragma unroll
-                        for (int z = 0; z < 8; z++) acc[z] += (double)v[z];
+                        for (int z = 0; z < 8; z++) {
+                            const float t = sum[z] + v[z];
+                            cmp[z] += (fabsf(sum[z]) >= fabsf(v[z])) ? (sum[z] - t) + v[z] : (v[z] - t) + sum[z];
+                            sum[z] = t;
+                        }
                     }
                     if (bin < N) {
 #pragma unroll
                         for (int z = 0; z < 8; z++)
-                            if (cc + z < c1) Dsm[(size_t)(cc + z) * DS + bin] = acc[z];
+                            if (cc + z < c1) Dsm[(size_t)(cc + z) * DS + bin] = sum[z] + cmp[z];
                     }
                 }
             }
             tc_fence_before();
             if (!gen_sync(gbar, gphase, &s_err)) break;
-            // ---- per-slot FP64 logic ----
+            // ---- per-slot integrator logic ----
             for (int sidx = warp - 2; sidx < NS; sidx += kGenWarps) {
                 Slot &sl = slots[sidx];
                 if (sl.cell < 0) continue;
