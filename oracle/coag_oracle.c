@@ -25,6 +25,9 @@
  *   Sec. 5 last paragraph Bogacki-Shampine 3(2), rtol 1e-2, atol 1e-10 sum rho
  *   Eq. (t_stop)          Epstein stopping time, v_th = sqrt(8/pi) c_s
  *   Sec. 3.3              nu = alpha c_s H; Re = nu_t / nu_mol (Sec. 7.2)
+ *   adjoint               the paper has none: the discrete adjoint of the
+ *                         replayed BS3 map (step sizes frozen), written out
+ *                         stage by stage from the forward formulas above
  *
  * Readings where the paper is silent or ambiguous (each is listed with its
  * reason in the design notes):
@@ -662,4 +665,169 @@ int oracle_bs3_scalar(double lam, double y0, double t_span, double h0, double rt
     bs3_integrate(lin_rhs, &cx, 1, &y, t_span, h0, rtol, atol, 100000000L, NULL, 0, NULL, &st);
     out[0] = y; out[1] = (double)st.n_acc; out[2] = (double)st.n_rej;
     return st.status;
+}
+
+/* ======================================================================== */
+/* Discrete adjoint of the replayed step sequence                           */
+/* ======================================================================== */
+
+/* Derivatives of K_ij and p_frag,ij with respect to alpha (turbulent term,
+ * including Re = nu_t / nu_mol proportional to alpha in delta = Re^-1/2 and
+ * in the St* clamp) and of p_frag with respect to v_frag. */
+static void pair_kernel_deriv(const oracle_params *P, const cellphys *cp, int c, int i, int j,
+                              double *dK_da, double *dpf_da, double *dpf_dvf)
+{
+    const double *m = P->m;
+    double alpha = P->alpha[c];
+    double K, pf, dv;
+    pair_kernel(P, cp, i, j, &K, &pf, &dv);
+    double S1 = cp->St[i] > cp->St[j] ? cp->St[i] : cp->St[j];
+    double S2 = cp->St[i] > cp->St[j] ? cp->St[j] : cp->St[i];
+    double d = 1.0 / sqrt(cp->Re);
+    double a16 = 1.6 * S1;
+    double Ss = a16 < d ? d : a16;
+    int clamp_d = (a16 < d) && (d < 1.0);
+    if (Ss > 1.0) Ss = 1.0;
+    double V = oracle_vrel2(cp->St[i], cp->St[j], cp->Re);
+    double dVI_dSs = 0.0;
+    if (S1 + S2 > 0.0)
+        dVI_dSs = (S1 - S2) / (S1 + S2) *
+                  (-S1 * S1 / ((Ss + S1) * (Ss + S1)) + S2 * S2 / ((Ss + S2) * (Ss + S2)));
+    double dVII_dSs = 2.0 - S1 * S1 / ((S1 + Ss) * (S1 + Ss)) - S2 * S2 / ((S2 + Ss) * (S2 + Ss));
+    double dVII_dd = -2.0 + S1 * S1 / ((S1 + d) * (S1 + d)) + S2 * S2 / ((S2 + d) * (S2 + d));
+    double dV_dd = (dVI_dSs + dVII_dSs) * (clamp_d ? 1.0 : 0.0) + dVII_dd;
+    if (!(V > 0.0)) dV_dd = 0.0;
+    double cs2 = cp->cs * cp->cs;
+    double dd_da = -0.5 * d / alpha;                 /* delta ~ alpha^-1/2 */
+    double dvt2_da = cs2 * V + alpha * cs2 * dV_dd * dd_da;
+    double ddv_da = dv > 0.0 ? dvt2_da / (2.0 * dv) : 0.0;
+    double s = cp->a[i] + cp->a[j];
+    *dK_da = (P->kernel_mode == 0) ? M_PI * s * s * ddv_da : 0.0;
+    double dpf_ddv = 0.0, dpfdvf = 0.0;
+    if (P->frag_mode == 0 && dv > 0.0) {
+        double x = 1.5 * (P->v_frag / dv) * (P->v_frag / dv);
+        dpf_ddv = 2.0 * x * x * exp(-x) / dv;
+        dpfdvf = -2.0 * x * x * exp(-x) / P->v_frag;
+    }
+    *dpf_da = dpf_ddv * ddv_da;
+    *dpf_dvf = dpfdvf;
+    (void)m; (void)K; (void)pf;
+}
+
+/* ybar += J(rho)^T v and the per-pair cotangents of K (Kbar) and p_frag
+ * (pfbar), for the right-hand side of rhs_cell written pair by pair. */
+static void rhs_vjp_cell(cellctx *cx, const double *rho, const double *v, double *ybar,
+                         double *Kbar, double *pfbar, double *Fv)
+{
+    const oracle_params *P = cx->P;
+    const int N = P->n_bins;
+    const double *m = P->m;
+    for (int l = 0; l < N; l++) {
+        double t = 0.0;
+        for (int k = 0; k <= l; k++) t += v[k] * cx->Ntab[l * N + k];
+        Fv[l] = t;
+    }
+    for (int i = 0; i < N; i++) {
+        double ni = rho[i] / m[i];
+        for (int j = 0; j <= i; j++) {
+            double nj = rho[j] / m[j];
+            double h = (i == j) ? 0.5 : 1.0;
+            double K = cx->K[i * N + j];
+            double pf = cx->pf[i * N + j];
+            const pairmap *q = &cx->map[i * N + j];
+            double mc = m[i] + m[j];
+            double Gc = mc * (q->cfl * v[q->ckl] + q->cfu * v[q->cku]);
+            double Gr = (q->mrem > 0.0) ? q->mrem * (q->rfl * v[q->rkl] + q->rfu * v[q->rku]) : 0.0;
+            double Gf = q->mfr * Fv[q->l];
+            double Gl = -(m[i] * v[i] + m[j] * v[j]);
+            double G = (1.0 - pf) * Gc + pf * (Gr + Gf) + Gl;
+            double W = ni * nj * K * h;
+            ybar[i] += G * nj * K * h / m[i];
+            ybar[j] += G * ni * K * h / m[j];
+            Kbar[i * N + j] += G * ni * nj * h;
+            pfbar[i * N + j] += W * (Gr + Gf - Gc);
+        }
+    }
+}
+
+/* Gradient of L = sum_{c,k} w[c][k] rho_ck(T), where rho(T) is reached from
+ * rho0 by the given accepted BS3 steps (hs[c*stride + s], s < n_h[c]; the
+ * step sequence is held fixed), with respect to rho0 (g_rho0 [c][k]), the
+ * per-cell alpha (g_alpha [c], may be NULL) and v_frag (*g_vfrag, summed
+ * over cells, may be NULL).  Parity: pinned (central finite differences of
+ * oracle_step_replay, dot-product identity). */
+int oracle_vjp(const oracle_params *P, const double *rho0, const double *hs, const long *n_h,
+               long stride, const double *w, double *g_rho0, double *g_alpha, double *g_vfrag)
+{
+    const int N = P->n_bins;
+    double vf_total = 0.0;
+    #pragma omp parallel for schedule(dynamic) num_threads(nthreads_of(P)) reduction(+:vf_total)
+    for (int c = 0; c < P->n_cells; c++) {
+        cellctx cx;
+        cell_alloc(P, c, &cx);
+        long nh = n_h[c];
+        const double *hc = hs + (size_t)c * stride;
+        double *Ys = xmalloc(sizeof(double) * N * (nh + 1));
+        double *k1 = xmalloc(sizeof(double) * N), *k2 = xmalloc(sizeof(double) * N);
+        double *Y2 = xmalloc(sizeof(double) * N), *Y3 = xmalloc(sizeof(double) * N);
+        double *lam = xmalloc(sizeof(double) * N), *yb = xmalloc(sizeof(double) * N);
+        double *kb1 = xmalloc(sizeof(double) * N), *kb2 = xmalloc(sizeof(double) * N);
+        double *kb3 = xmalloc(sizeof(double) * N), *Fv = xmalloc(sizeof(double) * N);
+        double *Kbar = xmalloc(sizeof(double) * N * N), *pfbar = xmalloc(sizeof(double) * N * N);
+        memcpy(Ys, rho0 + (size_t)c * N, sizeof(double) * N);
+        for (long s = 0; s < nh; s++) {           /* forward: store every state */
+            memcpy(Ys + (s + 1) * N, Ys + s * N, sizeof(double) * N);
+            bs3_fixed(rhs_cell, &cx, N, Ys + (s + 1) * N, hc + s, 1);
+        }
+        memcpy(lam, w + (size_t)c * N, sizeof(double) * N);
+        for (long s = nh - 1; s >= 0; s--) {
+            const double *y = Ys + s * N;
+            double h = hc[s];
+            rhs_cell(&cx, y, k1);
+            for (int k = 0; k < N; k++) Y2[k] = y[k] + h * BS_A21 * k1[k];
+            rhs_cell(&cx, Y2, k2);
+            for (int k = 0; k < N; k++) Y3[k] = y[k] + h * BS_A32 * k2[k];
+            /* y' = y + h (b1 k1 + b2 k2 + b3 k3(Y3)) */
+            for (int k = 0; k < N; k++) {
+                yb[k] = lam[k];
+                kb1[k] = h * BS_B1 * lam[k];
+                kb2[k] = h * BS_B2 * lam[k];
+                kb3[k] = h * BS_B3 * lam[k];
+            }
+            /* k3 = f(Y3), Y3 = y + h A32 k2 */
+            double *Yb = xmalloc(sizeof(double) * N);
+            for (int k = 0; k < N; k++) Yb[k] = 0.0;
+            rhs_vjp_cell(&cx, Y3, kb3, Yb, Kbar, pfbar, Fv);
+            for (int k = 0; k < N; k++) { yb[k] += Yb[k]; kb2[k] += h * BS_A32 * Yb[k]; Yb[k] = 0.0; }
+            /* k2 = f(Y2), Y2 = y + h A21 k1 */
+            rhs_vjp_cell(&cx, Y2, kb2, Yb, Kbar, pfbar, Fv);
+            for (int k = 0; k < N; k++) { yb[k] += Yb[k]; kb1[k] += h * BS_A21 * Yb[k]; Yb[k] = 0.0; }
+            /* k1 = f(y) */
+            rhs_vjp_cell(&cx, y, kb1, Yb, Kbar, pfbar, Fv);
+            for (int k = 0; k < N; k++) lam[k] = yb[k] + Yb[k];
+            free(Yb);
+        }
+        memcpy(g_rho0 + (size_t)c * N, lam, sizeof(double) * N);
+        /* parameters: chain the accumulated pair cotangents */
+        cellphys cp;
+        double *buf = xmalloc(sizeof(double) * 5 * N);
+        cp.a = buf; cp.St = buf + N; cp.vR = buf + 2 * N; cp.vphi = buf + 3 * N; cp.vZ = buf + 4 * N;
+        cell_physics(P, c, &cp);
+        double ga = 0.0, gv = 0.0;
+        for (int i = 0; i < N; i++)
+            for (int j = 0; j <= i; j++) {
+                double dK, dpa, dpv;
+                pair_kernel_deriv(P, &cp, c, i, j, &dK, &dpa, &dpv);
+                ga += Kbar[i * N + j] * dK + pfbar[i * N + j] * dpa;
+                gv += pfbar[i * N + j] * dpv;
+            }
+        if (g_alpha) g_alpha[c] = ga;
+        vf_total += gv;
+        free(buf);
+        free(Ys); free(k1); free(k2); free(Y2); free(Y3); free(lam); free(yb);
+        free(kb1); free(kb2); free(kb3); free(Fv); free(Kbar); free(pfbar);
+        cell_free(&cx);
+    }
+    if (g_vfrag) *g_vfrag = vf_total;
+    return 0;
 }

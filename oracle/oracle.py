@@ -64,9 +64,10 @@ def lib():
         _lib.oracle_step.argtypes = [P, d, C.c_double, d, d, d, d, d, C.c_long, d]
         _lib.oracle_step_replay.argtypes = [P, d, d, d, C.c_long]
         _lib.oracle_bs3_scalar.argtypes = [C.c_double] * 6 + [C.c_int, C.c_long, d]
+        _lib.oracle_vjp.argtypes = [P, d, d, d, C.c_long, d, d, d, d]
         for fn in ("oracle_cell_physics", "oracle_kernel", "oracle_pair_map",
                    "oracle_frag_table", "oracle_rhs", "oracle_rhs_bruteforce",
-                   "oracle_step", "oracle_step_replay", "oracle_bs3_scalar"):
+                   "oracle_step", "oracle_step_replay", "oracle_bs3_scalar", "oracle_vjp"):
             getattr(_lib, fn).restype = C.c_int
     return _lib
 
@@ -159,6 +160,15 @@ class Oracle:
                                int(log_cap), _ptr(nl))
         return dict(rho=y, dt=dtv, n_acc=na, n_rej=nr, status=stt, rc=rc,
                     log=log[:, :log_cap] if log_cap else None, n_log=nl)
+
+    def vjp(self, rho0, hs, n_h, w):
+        """Gradient of sum(w * rho(T)) after replaying hs w.r.t. rho0, alpha, v_frag."""
+        rho0 = _f64(rho0); hs = _f64(hs); w = _f64(w)
+        n_h = np.ascontiguousarray(n_h, dtype=np.int64)
+        g_rho0 = np.zeros_like(rho0); g_alpha = np.zeros(self.n_cells); g_vf = np.zeros(1)
+        lib().oracle_vjp(C.byref(self.p), _ptr(rho0), _ptr(hs), _ptr(n_h), hs.shape[1], _ptr(w),
+                         _ptr(g_rho0), _ptr(g_alpha), _ptr(g_vf))
+        return g_rho0, g_alpha, float(g_vf[0])
 
     def replay(self, rho, hs, n_h):
         y = _f64(rho).copy()
