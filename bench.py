@@ -211,7 +211,9 @@ def main():
             rho.copy_(rho0)
             dt.zero_()
             g.build_kernel()
-            return g.step(rho, disc.t_span, dt)
+            st = g.step(rho, disc.t_span, dt)
+            st["kbuild_ms"] = g.timings()["kbuild_ms"]
+            return st
 
         for _ in range(warmup):
             one_step()
@@ -220,22 +222,26 @@ def main():
             dist.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         sub = 0
+        rej = 0
         kern_ms = 0.0
+        kb_ms = 0.0
         launches = 0
         with ClockSampler(torch.cuda.current_device()) as clk:
             e0.record(stream)
             for _ in range(steps):
                 st = one_step()
                 sub += st["accepted"]
+                rej += st["rejected"]
                 kern_ms += st["elapsed_ms"]
+                kb_ms += st["kbuild_ms"]
                 launches += 3 + 2 * ((disc.n_cells - 1) // 65535)
             e1.record(stream)
             torch.cuda.synchronize()
         if dist:
             dist.barrier()
         ms = e0.elapsed_time(e1)
-        res = dict(ms=ms, sub=sub, kern_ms=kern_ms, launches=launches, clocks=clk.summary(),
-                   last=st, g=g)
+        res = dict(ms=ms, sub=sub, rej=rej, kern_ms=kern_ms, kb_ms=kb_ms, launches=launches,
+                   clocks=clk.summary(), last=st, g=g)
         if with_e2e:
             host_in = torch.from_numpy(np.ascontiguousarray(disc.rho0)).pin_memory()
             host_out = torch.empty_like(host_in).pin_memory()
@@ -279,30 +285,48 @@ def main():
         value = sub / (ms / 1e3)
         N = disc.n_bins
         Np = N * (N + 1) // 2
-        cell_sub_per_launch = main_res["last"]["accepted"]
-        kern_s = main_res["last"]["elapsed_ms"] / 1e3
+        n_steps = args.steps
+        kern_s = main_res["kern_ms"] / n_steps / 1e3          # integration kernel, per launch
+        # right-hand-side evaluations per launch: 3 per attempted substep
+        # (FSAL) plus the initial f(y0) of every cell
+        evals = (3 * (main_res["sub"] + main_res["rej"]) / n_steps + disc.n_cells)
         if args.precision == "fp64":
-            # algorithmic FP64 flops per cell-substep: 3 right-hand sides of
-            # 2 flops x (3 products + 6 two-term entries) per pair + N^2 fragment spread
-            flops = 3 * (2 * 15 * Np + N * N)
-            achieved = cell_sub_per_launch * flops / kern_s / 1e12
+            # algorithmic FP64 flops per RHS of one cell: per pair the product
+            # n_i n_j K (3), the two loss terms (4) and the coagulation /
+            # remnant / fragment-mass scatter (2 x 5 two-bin entries), then
+            # the N(N+1)/2 fragment spread (2 each)
+            flops = 2 * 13 * Np + N * (N + 1)
+            achieved = evals * flops / kern_s / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
                     "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
                     "traffic": None, "kernel": "step64_kernel",
                     "peak_src": "nominal FP64 rate of B300 (no measured FP64 peak)"}
         else:
-            # tensor flops of the TF32 split contraction: 3 products x 2 x N x 2Np per RHS
-            flops = 3 * 3 * 2 * N * 2 * Np
-            achieved = cell_sub_per_launch * flops / kern_s / 1e12
+            # tensor flops of the TF32 split contraction per RHS of one cell:
+            # A[1 x 2Np] x B[2Np x N] for each of the 4 products hi.hi, hi.lo,
+            # lo.hi, lo.lo (unpadded pairs)
+            flops = 4 * 2 * (2 * Np) * N
+            achieved = evals * flops / kern_s / 1e12
             peak_tf32 = pk["bf16_sus"] * TF32_OVER_BF16
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tf32, "unit": "TFLOP/s",
                     "frac": achieved / peak_tf32, "traffic": None, "kernel": "step_mixed_kernel",
-                    "peak_src": f"{pk['src']} sustained bf16 x nominal tf32/bf16 ratio"}
+                    "peak_src": f"{pk['src']} sustained bf16 {pk['bf16_sus']} TFLOP/s x nominal "
+                                f"tf32/bf16 ratio 1.1/2.25",
+                    "rhs_evals_per_launch": evals, "flops_per_rhs": flops}
+        # kernel-table build: HBM-bound writes of {K, K p_frag} per pair per cell
+        kb_s = main_res["kb_ms"] / n_steps / 1e3
+        kb_bytes = disc.n_cells * Np * (8 if args.precision == "mixed" else 16)
+        kb_gbs = kb_bytes / kb_s / 1e9
+        roof_kb = {"bound": "hbm", "achieved": kb_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                   "frac": kb_gbs / pk["hbm_gbs"], "traffic": None,
+                   "kernel": "kbuild32_kernel" if args.precision == "mixed" else "kbuild64_kernel",
+                   "ms_per_launch": kb_s * 1e3, "bytes_per_launch": kb_bytes,
+                   "peak_src": f"{pk['src']} copy bandwidth"}
         line = {
             "metric": METRIC, "value": value, "unit": "cell-substeps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "tf32x3+f64" if args.precision == "mixed" else "f64",
+            "dtype": "tf32x4+f32+f64" if args.precision == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "n_cells": disc.n_cells, "n_bins": N,
                        "t_span_yr": disc.t_span / synth.CONST["yr"],
@@ -314,6 +338,7 @@ def main():
             "rejected_per_step": main_res["last"]["rejected"],
             "mass_err_max": main_res["last"]["mass_err_max"],
             "roofline": roof,
+            "roofline_kbuild": roof_kb,
             "clocks": main_res["clocks"],
             "gpu_launches": main_res["launches"],
             "e2e": {"value": e2e_sub / e2e_s, "unit": "cell-substeps/s",

@@ -56,9 +56,10 @@ typedef enum {
 typedef enum {
     CUDISC_FP64 = 0,        /* FP64 everywhere: sparse gather on CUDA cores */
     CUDISC_MIXED_TF32 = 1   /* gain/loss contraction on tcgen05 tensor cores with
-                               TF32 hi+lo split operands (3 products), FP32
-                               accumulation in TMEM, FP64 state, mass budget
-                               and step control */
+                               TF32 hi+lo split operands (4 products: hi.hi,
+                               hi.lo, lo.hi, lo.lo), FP32 accumulation in TMEM
+                               with compensated chunk sums, FP32 stage
+                               arithmetic, FP64 state and mass budget */
 } cudisc_precision;
 
 typedef enum {
@@ -134,6 +135,10 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
  * arrays named at init (call after the caller changes them). */
 cudisc_status cudisc_coag_build_kernel(cudisc_coag_ctx *ctx);
 
+/* Set the fragmentation velocity v_frag (cm/s, > 0 and finite, else
+ * CUDISC_EINVAL).  Takes effect at the next cudisc_coag_build_kernel. */
+cudisc_status cudisc_coag_set_v_frag(cudisc_coag_ctx *ctx, double v_frag);
+
 /* Copy the kernel tables out for inspection: K_out and KF_out are device
  * [n_cells][Np] FP64, pair p = i (i + 1) / 2 + j for j <= i, holding K_ij and
  * K_ij p_frag,ij as stored by the context (FP32 values widened in the mixed
@@ -190,6 +195,53 @@ cudisc_status cudisc_coag_replay(cudisc_coag_ctx *ctx, double *rho, const double
  *   - Returns CUDISC_EINVAL for a context of another precision. */
 cudisc_status cudisc_coag_step_static_scratch(cudisc_coag_ctx *ctx, double *rho, double t_span,
                                               double *dt_cell, cudisc_step_stats *stats);
+
+/* Device times (CUDA events on params.stream) of the last call of each kind:
+ * the per-cell prep and the kernel-table build of cudisc_coag_build_kernel,
+ * the integration kernel of cudisc_coag_step (also in stats.elapsed_ms) and
+ * the whole of cudisc_coag_vjp.  0 for a kind not yet called.  Host only. */
+typedef struct {
+    double prep_ms;
+    double kbuild_ms;
+    double step_ms;
+    double vjp_ms;
+} cudisc_timings;
+cudisc_status cudisc_coag_get_timings(const cudisc_coag_ctx *ctx, cudisc_timings *out);
+
+/* Vector-Jacobian product of the integration (the paper has no adjoint; this
+ * is the discrete adjoint of the BS3 map of Sec. 5 with the step sizes held
+ * fixed).  For L = sum_{c,k} grad_rhoT[c][k] rho_ck(T), where rho(T) is
+ * reached from rho0 by a per-cell sequence of accepted BS3 steps, it writes
+ *   grad_rho0  [n_cells][N] device FP64: dL / d rho0,
+ *   grad_alpha [n_cells]    device FP64: dL / d alpha_c (through v_turb,
+ *                           Re = nu_t / nu_mol and St*), or NULL,
+ *   grad_vfrag [1]          device FP64: dL / d v_frag summed over cells
+ *                           (through p_frag), or NULL.
+ * The step sequence is either given (hs [n_cells][stride] device FP64,
+ * n_h [n_cells] device int64, 0 <= n_h[c] <= stride: e.g. the records of a
+ * cudisc_coag_step call, see cudisc_coag_set_records; t_span is ignored) or,
+ * with hs == NULL, taken from a fresh adaptive integration of rho0 over
+ * t_span with an automatic first step (n_h and stride ignored).  rho0 and
+ * grad_rhoT are device [n_cells][N] FP64 and are not modified.
+ * The adjoint runs one CTA per cell: a forward pass keeps the state every 16
+ * substeps, and each 16-substep segment is recomputed before its reverse
+ * sweep.  Arithmetic is FP64 for contexts of either precision (FP32 loses
+ * the gradient with respect to large grains, a small difference of
+ * sweep-up sums); K and K p_frag are the context's current tables
+ * (cudisc_coag_build_kernel), so a CUDISC_MIXED_TF32 context differentiates
+ * its own map with FP32 kernel tables.  The context's
+ * adjoint tables are built on the first call and its checkpoint storage
+ * (n_cells x ceil(max n_h / 16) x N values) grows when a longer sequence
+ * arrives; later calls of the same size allocate nothing.
+ * Errors: CUDISC_EINVAL (NULL arrays, n_h outside [0, stride]),
+ * CUDISC_ENOTSUP (N too large for the per-cell shared memory; every
+ * N <= 160 fits), the forward's per-cell status when
+ * hs == NULL and that integration fails, CUDISC_ENONFINITE when a cell's
+ * gradient is not finite.  Synchronises the stream. */
+cudisc_status cudisc_coag_vjp(cudisc_coag_ctx *ctx, const double *rho0, double t_span,
+                              const double *hs, const long long *n_h, long long stride,
+                              const double *grad_rhoT, double *grad_rho0, double *grad_alpha,
+                              double *grad_vfrag);
 
 void cudisc_coag_destroy(cudisc_coag_ctx *ctx);
 

@@ -44,6 +44,14 @@ class cudisc_coag_params(C.Structure):
     ]
 
 
+class cudisc_timings(C.Structure):
+    _fields_ = [("prep_ms", C.c_double), ("kbuild_ms", C.c_double),
+                ("step_ms", C.c_double), ("vjp_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class cudisc_step_stats(C.Structure):
     _fields_ = [
         ("accepted", C.c_longlong), ("rejected", C.c_longlong),
@@ -76,6 +84,9 @@ def lib():
         L.cudisc_coag_set_records.argtypes = [v, v, C.c_longlong, v, v]
         L.cudisc_coag_replay.argtypes = [v, v, v, v, C.c_longlong]
         L.cudisc_coag_step_static_scratch.argtypes = [v, v, d, v, C.POINTER(cudisc_step_stats)]
+        L.cudisc_coag_get_timings.argtypes = [v, C.POINTER(cudisc_timings)]
+        L.cudisc_coag_set_v_frag.argtypes = [v, d]
+        L.cudisc_coag_vjp.argtypes = [v, v, d, v, v, C.c_longlong, v, v, v, v]
         L.cudisc_coag_destroy.argtypes = [v]
         L.cudisc_coag_destroy.restype = None
         L.cudisc_coag_last_error.argtypes = [v]
@@ -83,7 +94,8 @@ def lib():
         L.cudisc_coag_version.restype = C.c_char_p
         for fn in ("cudisc_coag_init", "cudisc_coag_build_kernel", "cudisc_coag_get_kernel",
                    "cudisc_coag_rhs", "cudisc_coag_step", "cudisc_coag_set_records",
-                   "cudisc_coag_replay", "cudisc_coag_step_static_scratch"):
+                   "cudisc_coag_replay", "cudisc_coag_step_static_scratch",
+                   "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp"):
             getattr(L, fn).restype = C.c_int
         _lib = L
     return _lib
@@ -139,6 +151,22 @@ def cudisc_coag_set_records(ctx, dt_ptr, cap, n_ptr, status_ptr):
 
 def cudisc_coag_replay(ctx, rho_ptr, hs_ptr, n_ptr, stride):
     _check(lib().cudisc_coag_replay(ctx, rho_ptr, hs_ptr, n_ptr, int(stride)), ctx)
+
+
+def cudisc_coag_set_v_frag(ctx, v_frag: float):
+    _check(lib().cudisc_coag_set_v_frag(ctx, float(v_frag)), ctx)
+
+
+def cudisc_coag_vjp(ctx, rho0_ptr, t_span, hs_ptr, n_ptr, stride, grad_rhoT_ptr, grad_rho0_ptr,
+                    grad_alpha_ptr, grad_vfrag_ptr):
+    _check(lib().cudisc_coag_vjp(ctx, rho0_ptr, float(t_span), hs_ptr, n_ptr, int(stride),
+                                 grad_rhoT_ptr, grad_rho0_ptr, grad_alpha_ptr, grad_vfrag_ptr), ctx)
+
+
+def cudisc_coag_get_timings(ctx) -> dict:
+    t = cudisc_timings()
+    _check(lib().cudisc_coag_get_timings(ctx, C.byref(t)), ctx)
+    return t.as_dict()
 
 
 def cudisc_coag_destroy(ctx):
@@ -210,6 +238,9 @@ class Coag:
     def build_kernel(self):
         cudisc_coag_build_kernel(self.ctx)
 
+    def timings(self) -> dict:
+        return cudisc_coag_get_timings(self.ctx)
+
     def get_kernel(self):
         t = self.torch
         K = t.empty((self.n_cells, self.Np), dtype=t.float64, device=self.device)
@@ -251,3 +282,90 @@ class Coag:
         hs = hs.contiguous()
         n_h = n_h.contiguous().to(self.torch.int64)
         cudisc_coag_replay(self.ctx, rho.data_ptr(), hs.data_ptr(), n_h.data_ptr(), hs.shape[1])
+
+    # -- parameters the adjoint differentiates ------------------------------
+    def set_alpha(self, alpha):
+        """Copy new per-cell alpha values into the array the context reads
+        (call build_kernel afterwards)."""
+        self._keep["alpha"].copy_(self.torch.as_tensor(alpha, dtype=self.torch.float64,
+                                                       device=self.device).reshape(-1))
+
+    def set_v_frag(self, v_frag: float):
+        cudisc_coag_set_v_frag(self.ctx, float(v_frag))
+
+    def vjp(self, rho0, grad_rhoT, hs=None, n_h=None, t_span=0.0):
+        """Gradients of sum(grad_rhoT * rho(T)) with respect to rho0, the
+        per-cell alpha and v_frag, for the given step sequence (hs, n_h) or,
+        without one, for a fresh adaptive integration over t_span."""
+        t = self.torch
+        rho0 = rho0.contiguous()
+        grad_rhoT = grad_rhoT.contiguous().to(t.float64)
+        g0 = t.empty_like(rho0)
+        ga = t.empty(self.n_cells, dtype=t.float64, device=self.device)
+        gv = t.empty(1, dtype=t.float64, device=self.device)
+        if hs is None:
+            cudisc_coag_vjp(self.ctx, rho0.data_ptr(), t_span, None, None, 0, grad_rhoT.data_ptr(),
+                            g0.data_ptr(), ga.data_ptr(), gv.data_ptr())
+        else:
+            hs = hs.contiguous()
+            n_h = n_h.contiguous().to(t.int64)
+            cudisc_coag_vjp(self.ctx, rho0.data_ptr(), 0.0, hs.data_ptr(), n_h.data_ptr(),
+                            hs.shape[1], grad_rhoT.data_ptr(), g0.data_ptr(), ga.data_ptr(),
+                            gv.data_ptr())
+        return g0, ga, gv
+
+
+def _coag_step_function():
+    import torch
+
+    class CoagStep(torch.autograd.Function):
+        """rho(T) = step(rho0; alpha, v_frag) as a differentiable function.
+
+        forward: sets alpha and v_frag on the context, rebuilds K and runs the
+        adaptive integration over t_span with step records; backward: the
+        library's adjoint over the recorded step sequence (the step sizes are
+        held fixed, as in the discrete adjoint)."""
+
+        @staticmethod
+        def forward(ctx, rho0, alpha, v_frag, coag, t_span, log_cap):
+            coag.set_alpha(alpha.detach())
+            coag.set_v_frag(float(v_frag))
+            coag.build_kernel()
+            rec = coag.set_records(log_cap)
+            y = rho0.detach().to(torch.float64).contiguous().clone()
+            st = coag.step(y, t_span)
+            coag.set_records(0)
+            if int(rec["n"].max()) > log_cap:
+                raise CoagError(ENOTSUP, f"more than log_cap={log_cap} accepted substeps in a cell")
+            ctx.save_for_backward(rho0.detach(), alpha.detach())
+            ctx.coag, ctx.v_frag = coag, float(v_frag)
+            ctx.vf_shape = v_frag.shape if torch.is_tensor(v_frag) else None
+            ctx.hs, ctx.n_h = rec["dt"], rec["n"]
+            ctx.stats = st
+            return y
+
+        @staticmethod
+        def backward(ctx, g):
+            rho0, alpha = ctx.saved_tensors
+            coag = ctx.coag
+            coag.set_alpha(alpha)
+            coag.set_v_frag(ctx.v_frag)
+            coag.build_kernel()
+            g0, ga, gv = coag.vjp(rho0.to(torch.float64), g, ctx.hs, ctx.n_h)
+            g_vf = gv.reshape(ctx.vf_shape) if ctx.vf_shape is not None else None
+            return g0.to(rho0.dtype), ga.reshape(alpha.shape).to(alpha.dtype), g_vf, None, None, None
+
+    return CoagStep
+
+
+_CoagStep = None
+
+
+def coag_step(rho0, alpha, v_frag, coag: "Coag", t_span: float, log_cap: int = 4096):
+    """Differentiable coagulation step: rho(T) from rho0 [n_cells, N] (CUDA
+    float64), alpha [n_cells] and a scalar v_frag tensor; gradients flow to
+    all three through cudisc_coag_vjp."""
+    global _CoagStep
+    if _CoagStep is None:
+        _CoagStep = _coag_step_function()
+    return _CoagStep.apply(rho0, alpha, v_frag, coag, t_span, log_cap)

@@ -1,6 +1,7 @@
 // Host side of the C ABI: validation, the FP64 mapping-tensor builder
 // (Sec. 5, Eqs. Cijk, Rijk, fragrem, fragdist, Nijk), device tables and the
 // dispatch to the FP64 and mixed-precision kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -360,6 +361,9 @@ static void free_ctx(cudisc_coag_ctx *c)
         if (q) cudaFree(q);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    for (cudaEvent_t &ev : c->evb)
+        if (ev) cudaEventDestroy(ev);
+    cdc::vjp_free(c);
     delete c;
 }
 
@@ -414,6 +418,8 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
     }
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    for (cudaEvent_t &ev : c->evb)
+        if (e == cudaSuccess) e = cudaEventCreate(&ev);
     if (e != cudaSuccess) {
         cuda_fail(c, e, "cudisc_coag_init: workspace allocation");
         st = (e == cudaErrorMemoryAllocation) ? CUDISC_ENOMEM : CUDISC_ECUDA;
@@ -428,12 +434,40 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
 
 void cudisc_coag_destroy(cudisc_coag_ctx *ctx) { free_ctx(ctx); }
 
+cudisc_status cudisc_coag_get_timings(const cudisc_coag_ctx *c, cudisc_timings *out)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!out) return CUDISC_EINVAL;
+    out->prep_ms = c->t_prep;
+    out->kbuild_ms = c->t_kbuild;
+    out->step_ms = c->t_step;
+    out->vjp_ms = c->t_vjp;
+    return CUDISC_OK;
+}
+
 cudisc_status cudisc_coag_build_kernel(cudisc_coag_ctx *c)
 {
     if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    CUDA_TRY(c, cudaEventRecord(c->evb[0], c->stream));
     CUDA_TRY(c, cdc::launch_prep(c));
+    CUDA_TRY(c, cudaEventRecord(c->evb[1], c->stream));
     CUDA_TRY(c, cdc::launch_kbuild(c));
+    CUDA_TRY(c, cudaEventRecord(c->evb[2], c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, c->evb[0], c->evb[1]);
+    cudaEventElapsedTime(&b, c->evb[1], c->evb[2]);
+    c->t_prep = a;
+    c->t_kbuild = b;
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_coag_set_v_frag(cudisc_coag_ctx *c, double v_frag)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!(v_frag > 0.0) || !std::isfinite(v_frag))
+        return fail(c, CUDISC_EINVAL, "v_frag must be positive and finite");
+    c->p.v_frag = v_frag;
     return CUDISC_OK;
 }
 
@@ -492,6 +526,7 @@ static cudisc_status finish_step(cudisc_coag_ctx *c, cudisc_step_stats *stats)
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
     s.elapsed_ms = ms;
+    c->t_step = ms;
     if (stats) *stats = s;
     if (s.worst_status != 0) {
         char buf[160];
@@ -553,6 +588,77 @@ cudisc_status cudisc_coag_replay(cudisc_coag_ctx *c, double *rho, const double *
         CUDA_TRY(c, cdc::launch_step_mixed(c, rho, 1.0, nullptr, hs, n_h, stride));
     CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
     return finish_step(c, nullptr);
+}
+
+cudisc_status cudisc_coag_vjp(cudisc_coag_ctx *c, const double *rho0, double t_span,
+                              const double *hs, const long long *n_h, long long stride,
+                              const double *grad_rhoT, double *grad_rho0, double *grad_alpha,
+                              double *grad_vfrag)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!rho0 || !grad_rhoT || !grad_rho0)
+        return fail(c, CUDISC_EINVAL, "rho0, grad_rhoT and grad_rho0 must be device arrays");
+    if (!cdc::vjp_fits(c))
+        return fail(c, CUDISC_ENOTSUP, "n_bins too large for the adjoint's per-cell shared memory");
+    const size_t nc = (size_t)c->n_cells;
+    const double *H = hs;
+    const long long *NH = n_h;
+    long long str = stride;
+    std::vector<long long> hn(nc);
+    if (!hs) {
+        // the step sequence of a fresh adaptive integration from rho0
+        if (!(t_span > 0.0) || !std::isfinite(t_span))
+            return fail(c, CUDISC_EINVAL, "t_span must be positive and finite");
+        long long cap = std::max<long long>(1, std::min<long long>(c->p.max_substeps, 4096));
+        for (int attempt = 0; attempt < 2; attempt++) {
+            double *dt = nullptr, *tmp = nullptr;
+            long long *nn = nullptr;
+            int *sts = nullptr;
+            CUDA_TRY(c, cdc::vjp_records(c, cap, &dt, &nn, &sts, &tmp));
+            CUDA_TRY(c, cudaMemcpyAsync(tmp, rho0, nc * c->N * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, c->stream));
+            double *u_dt = c->rec_dt;
+            long long u_cap = c->rec_cap, *u_n = c->rec_n;
+            int *u_st = c->rec_status;
+            c->rec_dt = dt; c->rec_cap = cap; c->rec_n = nn; c->rec_status = sts;
+            cudaError_t e = cudaEventRecord(c->ev0, c->stream);
+            if (e == cudaSuccess)
+                e = c->p.precision == CUDISC_FP64
+                        ? cdc::launch_step_fp64(c, tmp, t_span, nullptr, nullptr, nullptr, 0)
+                        : cdc::launch_step_mixed(c, tmp, t_span, nullptr, nullptr, nullptr, 0);
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev1, c->stream);
+            c->rec_dt = u_dt; c->rec_cap = u_cap; c->rec_n = u_n; c->rec_status = u_st;
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudisc_coag_vjp: forward integration");
+            cudisc_status st = finish_step(c, nullptr);
+            if (st != CUDISC_OK) return st;
+            CUDA_TRY(c, cudaMemcpy(hn.data(), nn, nc * sizeof(long long), cudaMemcpyDeviceToHost));
+            const long long mx = *std::max_element(hn.begin(), hn.end());
+            H = dt; NH = nn; str = cap;
+            if (mx <= cap) break;
+            cap = mx;
+        }
+    } else {
+        if (!n_h) return fail(c, CUDISC_EINVAL, "n_h must be a device array with hs");
+        if (stride < 1) return fail(c, CUDISC_EINVAL, "stride must be >= 1");
+    }
+    CUDA_TRY(c, cudaMemcpy(hn.data(), NH, nc * sizeof(long long), cudaMemcpyDeviceToHost));
+    long long mx = 0;
+    for (long long v : hn) {
+        if (v < 0 || v > str) return fail(c, CUDISC_EINVAL, "n_h entries must lie in [0, stride]");
+        mx = std::max(mx, v);
+    }
+    CUDA_TRY(c, cdc::vjp_prepare(c, mx));
+    CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
+    CUDA_TRY(c, cdc::launch_vjp(c, rho0, H, NH, str, grad_rhoT, grad_rho0, grad_alpha, grad_vfrag));
+    CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    c->t_vjp = ms;
+    int worst = 0;
+    CUDA_TRY(c, cdc::vjp_worst_status(c, &worst));
+    if (worst != 0) return fail(c, (cudisc_status)worst, "non-finite adjoint in some cell");
+    return CUDISC_OK;
 }
 
 } // extern "C"

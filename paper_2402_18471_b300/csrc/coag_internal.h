@@ -9,6 +9,8 @@
 
 namespace cdc {
 
+struct VjpState;                      // adjoint tables and workspace (vjp.cu)
+
 constexpr int kMaxBins = 160;         // FP64 path keeps the pair weights of one cell in smem
 constexpr int kBlkPairs = 16;         // pairs per K-block of the mixed contraction
 constexpr int kBlkElems = 32;         // TF32 elements per K-block row (a and b per pair)
@@ -98,6 +100,9 @@ struct cudisc_coag_ctx {
     double *rec_dt = nullptr; long long rec_cap = 0; long long *rec_n = nullptr;
     int *rec_status = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t evb[3] = {nullptr, nullptr, nullptr};   // prep | kbuild | end
+    double t_prep = 0.0, t_kbuild = 0.0, t_step = 0.0, t_vjp = 0.0;   // ms, last call
+    cdc::VjpState *vjp = nullptr;      // built on the first cudisc_coag_vjp
 
     cdc::DevTables tables() const;
 };
@@ -116,6 +121,16 @@ cudaError_t launch_step_mixed(const cudisc_coag_ctx *c, double *rho, double t_sp
                               double *dt_cell, const double *replay_h,
                               const long long *replay_n, long long replay_stride);
 size_t mixed_workspace_bytes(int n_cells, int N);
+// adjoint (vjp.cu)
+bool vjp_fits(const cudisc_coag_ctx *c);
+cudaError_t vjp_prepare(cudisc_coag_ctx *c, long long max_steps);
+cudaError_t vjp_records(cudisc_coag_ctx *c, long long cap, double **dt, long long **n, int **status,
+                        double **rho_tmp);
+cudaError_t launch_vjp(cudisc_coag_ctx *c, const double *rho0, const double *hs,
+                       const long long *n_h, long long stride, const double *w, double *g_rho0,
+                       double *g_alpha, double *g_vf);
+cudaError_t vjp_worst_status(const cudisc_coag_ctx *c, int *worst);
+void vjp_free(cudisc_coag_ctx *c);
 // fixed-scratch variant of the mixed step (see cudisc_coag_step_static_scratch)
 size_t static_scratch_bytes();
 cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, double t_span,

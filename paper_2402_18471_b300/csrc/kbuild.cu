@@ -10,6 +10,7 @@
 #include <cmath>
 
 #include "coag_internal.h"
+#include "oc07.cuh"
 
 namespace cdc {
 namespace {
@@ -92,21 +93,6 @@ __global__ void __launch_bounds__(128) prep_kernel(
         scal[c] = s;
         scal32[c] = make_float4((float)s.delta, (float)s.Vg2, (float)s.etavK, (float)s.ZOm);
     }
-}
-
-// Ormel & Cuzzi (2007) V_rel^2 / V_g^2 from the larger (1) and smaller (2)
-// Stokes numbers: class I over slow eddies between t* and t_L and class II
-// over fast eddies between t_eta and t*, both particles responding.
-__device__ __forceinline__ double vrel2_f64(double S1, double S2, double g1_1, double g1_2,
-                                            double g2_1, double g2_2, double d)
-{
-    double Ss = fmin(fmax(1.6 * S1, d), 1.0);
-    double dVI = 0.0;
-    if (S1 + S2 > 0.0)
-        dVI = (S1 - S2) / (S1 + S2) *
-              (S1 * S1 / (Ss + S1) - g1_1 - S2 * S2 / (Ss + S2) + g1_2);
-    double dVII = 2.0 * (Ss - d) + S1 * S1 / (S1 + Ss) - g2_1 + S2 * S2 / (S2 + Ss) - g2_2;
-    return fmax(dVI + dVII, 0.0);
 }
 
 __global__ void __launch_bounds__(256) kbuild64_kernel(

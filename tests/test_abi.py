@@ -89,4 +89,8 @@ def test_null_context_is_an_error_not_a_crash():
     assert L.cudisc_coag_build_kernel(None) == coag.EINVAL
     assert L.cudisc_coag_rhs(None, None, None) == coag.EINVAL
     assert L.cudisc_coag_step(None, None, 1.0, None, None) == coag.EINVAL
+    assert L.cudisc_coag_vjp(None, None, 1.0, None, None, 0, None, None, None, None) == coag.EINVAL
+    assert L.cudisc_coag_set_v_frag(None, 1.0) == coag.EINVAL
+    t = coag.cudisc_timings()
+    assert L.cudisc_coag_get_timings(None, C.byref(t)) == coag.EINVAL
     L.cudisc_coag_destroy(None)
