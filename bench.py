@@ -37,6 +37,14 @@ WORKLOADS = {
 METRIC = "cell-substeps/s, 128x64 cells x 100 bins: mixed vs FP64 GPU, rel err<=1e-5"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work
+# from one ncu capture of the named kernel (summaries under profiles/), valid
+# only for the kernel source they were taken on: a changed source reports null.
+MEASURED_TRAFFIC = {
+    "step_mixed_kernel": {"bytes_per_rhs_eval": 29.219291e9 / 635531,
+                          "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
+                          "sha256": "ef739ba4ddf640ff14c01ab9605242ae84573605d70c9fb5c5a096a817bc3ed7"},
+}
 TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 rate ratio
 
 
@@ -46,6 +54,19 @@ def peaks():
         return dict(hbm_gbs=p["hbm_gbs"], bf16=p["bf16_tflops"], bf16_sus=p["bf16_tflops_sustained"],
                     src="measured")
     return dict(hbm_gbs=6400.0, bf16=1800.0, bf16_sus=1400.0, src="fallback")
+
+
+def measured_traffic(kernel: str, units: float):
+    """Traffic per launch scaled from the profiled per-unit bytes, or None
+    when no capture exists for the kernel's current source."""
+    import hashlib
+    m = MEASURED_TRAFFIC.get(kernel)
+    if not m:
+        return None
+    src = os.path.join(ROOT, m["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != m["sha256"]:
+        return None
+    return m["bytes_per_rhs_eval"] * units
 
 
 class ClockSampler:
@@ -126,7 +147,7 @@ def cpu_baseline(disc, budget_s=20.0, t_span=None):
         used = np.concatenate([used, cells]).astype(int)
         n *= 2
     return {"value": total_sub / total_t, "unit": "cell-substeps/s", "cores": cores,
-            "kind": "oracle",
+            "kind": "oracle", "seconds": total_t,
             "sample": f"{len(used)} of {disc.n_cells} cells spread over the grid, full "
                       f"{t_span / synth.CONST['yr']:.0f} yr, {total_sub} accepted substeps in "
                       f"{total_t:.1f} s, OpenMP over cells"}
@@ -136,16 +157,17 @@ def run_reference(args, disc, rank, world):
     if rank != 0:
         return
     cb = None
-    vals = []
+    vals, secs = [], []
     for s in range(args.warmup + args.steps):
         r = cpu_baseline(disc, budget_s=args.ref_budget)
         if s >= args.warmup:
             vals.append(r["value"])
+            secs.append(r["seconds"])
             cb = r
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cell-substeps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "n_cells": disc.n_cells, "n_bins": disc.n_bins,
                        "t_span_yr": disc.t_span / synth.CONST["yr"],
@@ -309,7 +331,11 @@ def main():
             achieved = evals * flops / kern_s / 1e12
             peak_tf32 = pk["bf16_sus"] * TF32_OVER_BF16
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tf32, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tf32, "traffic": None, "kernel": "step_mixed_kernel",
+                    "frac": achieved / peak_tf32,
+                    "traffic": measured_traffic("step_mixed_kernel", evals),
+                    "traffic_note": "DRAM bytes per RHS evaluation from an ncu capture of a "
+                                    "300-yr launch of the same grid, scaled to this launch's "
+                                    "evaluations", "kernel": "step_mixed_kernel",
                     "peak_src": f"{pk['src']} sustained bf16 {pk['bf16_sus']} TFLOP/s x nominal "
                                 f"tf32/bf16 ratio 1.1/2.25",
                     "rhs_evals_per_launch": evals, "flops_per_rhs": flops}

@@ -16,7 +16,7 @@
 //   of (Bt_hi + Bt_lo)(A_hi + A_lo), hi and lo rounded to nearest TF32: hi x
 //   hi into one of several FP32 accumulators [128 lanes x NS columns] in TMEM
 //   (a contiguous share of the blocks each), the three corrections into one
-//   more; the epilogue sums them in FP64.
+//   more; the epilogue adds them with a compensated (Neumaier) FP32 sum.
 // Warp roles: warp 0 bulk-copy producer, warp 1 MMA issuer and TMEM owner,
 // warps 2..9 generate A (x_i x_j K split into hi/lo in the SW128 K-major
 // layout) and, between right-hand sides, run the per-slot FP64 logic: the
@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     // contiguous share of the blocks (every one gets at least one), plus one
     // for the three 2^-11-smaller correction products of every block.  FP32
     // accumulation error grows with the additions per accumulator; the
-    // epilogue sums them all in FP64.
+    // epilogue adds them with a compensated (Neumaier) FP32 sum.
     int nmain = 512 / NS - 1;
     if (nmain > kMaxMain) nmain = kMaxMain;
     const int nacc = n_blk < nmain ? n_blk : nmain;
