@@ -141,8 +141,8 @@ cudisc_status cudisc_coag_set_v_frag(cudisc_coag_ctx *ctx, double v_frag);
 
 /* Copy the kernel tables out for inspection: K_out and KF_out are device
  * [n_cells][Np] FP64, pair p = i (i + 1) / 2 + j for j <= i, holding K_ij and
- * K_ij p_frag,ij as stored by the context (FP32 values widened in the mixed
- * precision). */
+ * K_ij p_frag,ij as stored by the context (mixed precision: the FP32
+ * tables {K p_coag, K p_frag} widened, K = K p_coag + K p_frag in FP64). */
 cudisc_status cudisc_coag_get_kernel(cudisc_coag_ctx *ctx, double *K_out, double *KF_out);
 
 /* Right-hand side of Eq. (smol): drho_dt[c][k] for the state rho[c][k]

@@ -289,13 +289,16 @@ static cudisc_status build_tables(cudisc_coag_ctx *c)
             }
             frows[l].push_back({pp, Mf * w});
             if (mixed) {
-                // dense column of the contraction: fragments folded in directly
+                // dense columns of the contraction, against {K p_c, K p_f}:
+                //   a: coagulation gain minus the loss of both grains,
+                //   b: remnant and fragment gain (fragments folded in
+                //      directly) minus the loss of both grains
                 const int jb = j / cdc::kBlkPairs;
                 const int b = blk + jb;
                 const int t = j - jb * cdc::kBlkPairs;
                 for (int k = 0; k < N; k++) {
                     double va = dd_val(colA[k]) * w;
-                    dd vbd = colB[k];
+                    dd vbd = colB[k] + colA[k];
                     if (k <= l) vbd = vbd + dd_of(Mf) * dd_of(Ntab[(size_t)l * N + k]);
                     double vb = dd_val(vbd) * w;
                     for (int s = 0; s < 2; s++) {

@@ -133,87 +133,192 @@ __global__ void __launch_bounds__(256) kbuild64_kernel(
     Kout[(size_t)c * Np + p] = make_double2(K, K * pf);
 }
 
-// FP32 builder in the blocked pair layout of the mixed contraction: slot
-// q = 16 b + t is pair (blk_i[b], blk_j0[b] + t); slots past the diagonal
-// hold zeros.
-__global__ void __launch_bounds__(256) kbuild32_kernel(
-    int c0, float kc, float v_frag, int kernel_mode, int frag_mode, int has_vdust, int n_cells,
-    int N, int n_slots,
-    const int *__restrict__ blk_i, const int *__restrict__ blk_j0,
-    const double *__restrict__ a, const double *__restrict__ minv,
-    const double *__restrict__ m, const float *__restrict__ prep32,
-    const float4 *__restrict__ scal32, float2 *__restrict__ Kout)
+// Hardware approximations (flush-to-zero; a few ulp) for the FP32 builder.
+__device__ __forceinline__ float rcp_ftz(float x)
 {
-    const int c = c0 + blockIdx.y;
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n_cells || q >= n_slots) return;
-    const int b = q >> 4;
-    const int i = blk_i[b];
-    const int j = blk_j0[b] + (q & 15);
-    float2 out = make_float2(0.f, 0.f);
-    if (j <= i) {
-        const float *pr = prep32 + (size_t)c * P3_COUNT * N;
-        const float4 s4 = scal32[c];
-        const float d = s4.x, Vg2 = s4.y;
-        const float Si = pr[P3_ST * N + i], Sj = pr[P3_ST * N + j];
-        float S1 = Si, S2 = Sj;
-        int i1 = i;
-        if (S2 > S1) { float t = S1; S1 = S2; S2 = t; i1 = j; }
-        const float Ss = pr[P3_SS * N + i1];
-        const float Ssmd = pr[P3_SSMD * N + i1], omSs = pr[P3_OMSS * N + i1];
-        // Ormel & Cuzzi class I and II terms rearranged into sums and
-        // products of non-negative factors (algebraically identical to the
-        // closed forms).  In FP32 the literal forms cancel: with St* clamped
-        // to Re^-1/2 and St1 = St2 class II is exactly zero but leaves a
-        // residue ~1e-7 St^2/Re^-1/2, and for St >> 1 both forms reduce to
-        // small differences of numbers near one.
-        //   dVI  = (S1-S2)^2 (1-St*) [St*(S1+S2) + S1 S2 (1+St*)]
-        //          / [(S1+S2)(St*+S1)(1+S1)(St*+S2)(1+S2)]
-        //   dVII = (St*-d) sum_{s=S1,S2} [s (St*+d) + St* d] / [(s+St*)(s+d)]
-        const float A = S1 + S2, P1 = S1 + Ss, P2 = S2 + Ss;
-        const float Q1 = 1.0f + S1, Q2 = 1.0f + S2, R1 = S1 + d, R2 = S2 + d;
-        const float dS = S1 - S2;
-        const float nI = dS * dS * omSs * (Ss * A + S1 * S2 * (1.0f + Ss));
-        const float dI = A * (P1 * Q1) * (P2 * Q2);
-        const float sd = Ss + d, Sd = Ss * d;
-        const float nII = Ssmd * ((S1 * sd + Sd) * (P2 * R2) + (S2 * sd + Sd) * (P1 * R1));
-        const float dII = (P1 * R1) * (P2 * R2);
-        const float V = fmaxf(nI / dI + nII / dII, 0.0f);
-        const float vbm2 = pr[P3_U * N + i] + pr[P3_U * N + j];
-        float dR, dP, dZ;
-        if (has_vdust) {
-            // input velocities: difference of FP32 hi/lo pairs
-            dR = (pr[P3_VRH * N + i] - pr[P3_VRH * N + j]) + (pr[P3_VRL * N + i] - pr[P3_VRL * N + j]);
-            dP = (pr[P3_VPH * N + i] - pr[P3_VPH * N + j]) + (pr[P3_VPL * N + i] - pr[P3_VPL * N + j]);
-            dZ = (pr[P3_VZH * N + i] - pr[P3_VZH * N + j]) + (pr[P3_VZL * N + i] - pr[P3_VZL * N + j]);
-        } else {
-            // terminal velocities: differences factored through St_i - St_j
-            //   v_R   = -2 eta v_K St/(1+St^2), v_phi = -eta v_K/(1+St^2),
-            //   v_Z   = -Z Omega St/(1+St)
-            const float dS = Si - Sj;
-            const float ai = 1.0f + Si * Si, aj = 1.0f + Sj * Sj;
-            const float rij = 1.0f / (ai * aj);
-            const float ev = s4.z;
-            dR = -2.0f * ev * dS * (1.0f - Si * Sj) * rij;
-            dP = ev * dS * (Si + Sj) * rij;
-            dZ = -s4.w * dS / ((1.0f + Si) * (1.0f + Sj));
-        }
-        const float dv2 = vbm2 + Vg2 * V + (dR * dR + dP * dP + dZ * dZ);
-        const float dv = sqrtf(dv2);
-        float K;
-        if (kernel_mode == CUDISC_KERNEL_CONSTANT) K = kc;
-        else if (kernel_mode == CUDISC_KERNEL_ADDITIVE) K = kc * (pr[P3_M * N + i] + pr[P3_M * N + j]);
-        else { const float sa = pr[P3_A * N + i] + pr[P3_A * N + j]; K = 3.14159265358979f * sa * sa * dv; }
-        float pf;
-        if (frag_mode == CUDISC_FRAG_NONE) pf = 0.0f;
-        else if (frag_mode == CUDISC_FRAG_ALL) pf = 1.0f;
-        else {
-            const float x = 1.5f * v_frag * v_frag / dv2;
-            pf = (x + 1.0f) * expf(-x);
-        }
-        out = make_float2(K, K * pf);
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// e^-x = 2^(-x log2 e)
+__device__ __forceinline__ float exp_neg_ftz(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x * -1.4426950408889634f));
+    return r;
+}
+
+// Coagulation probability p_c = 1 - (1 + x) e^-x of Eq. (p_frag), accurate in
+// FP32 also where p_frag rounds to 1: for x < 1 from its Taylor series
+//   1 - (1 + x) e^-x = sum_{n>=2} (-1)^n (n - 1) x^n / n!
+//                    = x^2 sum_{m>=0} (-1)^m (m + 1) x^m / (m + 2)!,
+// 13 terms (truncation < 3e-9 at x = 1), evaluated by Horner; for x >= 1 from
+// the closed form (p_c >= 0.26 there, no cancellation).  Given e = e^-x.
+__device__ __forceinline__ float pcoag_f32(float x, float e)
+{
+    if (x >= 1.0f) return 1.0f - (1.0f + x) * e;
+    constexpr double f2 = 2, f3 = 6, f4 = 24, f5 = 120, f6 = 720, f7 = 5040, f8 = 40320,
+                     f9 = 362880, f10 = 3628800, f11 = 39916800, f12 = 479001600,
+                     f13 = 6227020800.0, f14 = 87178291200.0;
+    float s = (float)(13 / f14);
+    s = s * x + (float)(-12 / f13);
+    s = s * x + (float)(11 / f12);
+    s = s * x + (float)(-10 / f11);
+    s = s * x + (float)(9 / f10);
+    s = s * x + (float)(-8 / f9);
+    s = s * x + (float)(7 / f8);
+    s = s * x + (float)(-6 / f7);
+    s = s * x + (float)(5 / f6);
+    s = s * x + (float)(-4 / f5);
+    s = s * x + (float)(3 / f4);
+    s = s * x + (float)(-2 / f3);
+    s = s * x + (float)(1 / f2);
+    return x * x * s;
+}
+
+// Shared-memory fields of the FP32 builder, each [NR] (NR = N rounded up to
+// 16, zero-padded so that four consecutive bins load as one 16-byte word):
+// the prep fields P3_*, then 1/(1+St^2) and 1/(1+St).
+enum { KB_INVA = P3_COUNT, KB_INVQ, KB_COUNT };
+
+// FP32 builder in the blocked pair layout of the mixed contraction: slot
+// q = 16 b + t is pair (blk_i[b], blk_j0[b] + t) and holds {K p_c, K p_f}
+// (p_c = 1 - p_f, each accurate to a few ulp of itself, so that neither
+// coagulation in a fragmentation-dominated cell nor fragmentation in a
+// coagulation-dominated one is lost to rounding); slots past the diagonal
+// hold zeros.  One CTA per cell: the cell's per-bin fields are staged in
+// shared memory once; each thread then produces four consecutive slots of a
+// block (same i, j .. j+3) and writes them as two 16-byte stores.  The
+// larger Stokes number of a pair (i, j <= i) is always St_i: St = rho_m a
+// Omega / (rho_g v_th) rises with the bin's size.  Divisions, the square
+// root and the exponential use the hardware approximations: K stays within
+// 1e-6 and K p_frag within 1e-5 of FP64.
+//   Physical = physical kernel and fragmentation probability (the other
+//   modes are the closed-form test kernels); HasVdust = input velocities.
+template <bool Physical, bool HasVdust>
+__global__ void __launch_bounds__(256) kbuild32_kernel(
+    float kc, float v_frag, int kernel_mode, int frag_mode, int n_cells, int N, int NR,
+    int n_slots, const int *__restrict__ blk_i, const int *__restrict__ blk_j0,
+    const float *__restrict__ prep32, const float4 *__restrict__ scal32,
+    float2 *__restrict__ Kout)
+{
+    extern __shared__ __align__(16) float f32s[];       // [KB_COUNT][NR]
+    const int c = blockIdx.x;
+    if (c >= n_cells) return;
+    const float *src = prep32 + (size_t)c * P3_COUNT * N;
+    for (int t = threadIdx.x; t < P3_COUNT * NR; t += blockDim.x) {
+        const int f = t / NR, k = t - f * NR;
+        f32s[t] = k < N ? src[f * N + k] : 0.0f;
     }
-    Kout[(size_t)c * n_slots + q] = out;
+    for (int k = threadIdx.x; k < NR; k += blockDim.x) {
+        const float S = f32s[P3_ST * NR + k];
+        f32s[KB_INVA * NR + k] = 1.0f / (1.0f + S * S);
+        f32s[KB_INVQ * NR + k] = 1.0f / (1.0f + S);
+    }
+    __syncthreads();
+    const float4 s4 = scal32[c];
+    const float d = s4.x, Vg2 = s4.y, ev = s4.z, zo = s4.w;
+    const float vf2 = 1.5f * v_frag * v_frag;
+    const float *St = f32s + P3_ST * NR, *U = f32s + P3_U * NR, *Aa = f32s + P3_A * NR;
+    const float *IA = f32s + KB_INVA * NR, *IQ = f32s + KB_INVQ * NR;
+    float4 *dst = reinterpret_cast<float4 *>(Kout + (size_t)c * n_slots);
+    for (int g = threadIdx.x; 4 * g < n_slots; g += blockDim.x) {
+        const int q0 = 4 * g;
+        const int b = q0 >> 4;
+        const int i = __ldg(blk_i + b);
+        const int j0 = __ldg(blk_j0 + b) + (q0 & 15);
+        // bin i (the larger Stokes number)
+        const float S1 = St[i], Ss = f32s[P3_SS * NR + i], Ssmd = f32s[P3_SSMD * NR + i];
+        const float omSs = f32s[P3_OMSS * NR + i], Ui = U[i], ai = Aa[i], ia1 = IA[i], iq1 = IQ[i];
+        const float P1 = S1 + Ss, Q1 = 1.0f + S1, R1 = S1 + d;
+        const float sd = Ss + d, Sd = Ss * d, opSs = 1.0f + Ss;
+        const float c1 = S1 * sd + Sd, PQ1 = P1 * Q1, PR1 = P1 * R1;
+        // bins j0 .. j0+3
+        const float4 S2v = *reinterpret_cast<const float4 *>(St + j0);
+        const float4 Ujv = *reinterpret_cast<const float4 *>(U + j0);
+        const float4 ajv = *reinterpret_cast<const float4 *>(Aa + j0);
+        const float4 iav = *reinterpret_cast<const float4 *>(IA + j0);
+        const float4 iqv = *reinterpret_cast<const float4 *>(IQ + j0);
+        const float S2a[4] = {S2v.x, S2v.y, S2v.z, S2v.w};
+        const float Uja[4] = {Ujv.x, Ujv.y, Ujv.z, Ujv.w};
+        const float aja[4] = {ajv.x, ajv.y, ajv.z, ajv.w};
+        const float iaa[4] = {iav.x, iav.y, iav.z, iav.w};
+        const float iqa[4] = {iqv.x, iqv.y, iqv.z, iqv.w};
+        float o[8];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int j = j0 + u;
+            const float S2 = S2a[u];
+            // Ormel & Cuzzi class I and II terms rearranged into sums and
+            // products of non-negative factors (algebraically identical to
+            // the closed forms).  In FP32 the literal forms cancel: with St*
+            // clamped to Re^-1/2 and St1 = St2 class II is exactly zero but
+            // leaves a residue ~1e-7 St^2/Re^-1/2, and for St >> 1 both
+            // forms reduce to small differences of numbers near one.
+            //   dVI  = (S1-S2)^2 (1-St*) [St*(S1+S2) + S1 S2 (1+St*)]
+            //          / [(S1+S2)(St*+S1)(1+S1)(St*+S2)(1+S2)]
+            //   dVII = (St*-d) sum_{s=S1,S2} [s (St*+d) + St* d] / [(s+St*)(s+d)]
+            const float A = S1 + S2, P2 = S2 + Ss, Q2 = 1.0f + S2, R2 = S2 + d;
+            const float dS = S1 - S2;
+            const float nI = dS * dS * omSs * (Ss * A + S1 * S2 * opSs);
+            const float dI = A * PQ1 * (P2 * Q2);
+            const float PR2 = P2 * R2;
+            const float nII = Ssmd * (c1 * PR2 + (S2 * sd + Sd) * PR1);
+            const float dII = PR1 * PR2;
+            const float V = fmaxf(nI * rcp_ftz(dI) + nII * rcp_ftz(dII), 0.0f);
+            float dR, dP, dZ;
+            if (HasVdust) {
+                // input velocities: difference of FP32 hi/lo pairs
+                const float *f = f32s;
+                dR = (f[P3_VRH * NR + i] - f[P3_VRH * NR + j]) + (f[P3_VRL * NR + i] - f[P3_VRL * NR + j]);
+                dP = (f[P3_VPH * NR + i] - f[P3_VPH * NR + j]) + (f[P3_VPL * NR + i] - f[P3_VPL * NR + j]);
+                dZ = (f[P3_VZH * NR + i] - f[P3_VZH * NR + j]) + (f[P3_VZL * NR + i] - f[P3_VZL * NR + j]);
+            } else {
+                // terminal velocities: differences factored through St_i - St_j
+                //   v_R   = -2 eta v_K St/(1+St^2), v_phi = -eta v_K/(1+St^2),
+                //   v_Z   = -Z Omega St/(1+St)
+                const float rij = ia1 * iaa[u];
+                dR = -2.0f * ev * dS * (1.0f - S1 * S2) * rij;
+                dP = ev * dS * A * rij;
+                dZ = -zo * dS * (iq1 * iqa[u]);
+            }
+            const float dv2 = (Ui + Uja[u]) + Vg2 * V + (dR * dR + dP * dP + dZ * dZ);
+            const float rs = rsqrt_ftz(dv2);
+            float K, pc, pf;
+            if (Physical) {
+                const float sa = ai + aja[u];
+                K = 3.14159265358979f * sa * sa * (dv2 * rs);
+                const float x = vf2 * (rs * rs);
+                const float e = exp_neg_ftz(x);
+                pf = (x + 1.0f) * e;
+                pc = pcoag_f32(x, e);
+            } else {
+                const float *Mm = f32s + P3_M * NR;
+                if (kernel_mode == CUDISC_KERNEL_CONSTANT) K = kc;
+                else if (kernel_mode == CUDISC_KERNEL_ADDITIVE) K = kc * (Mm[i] + Mm[j]);
+                else { const float sa = ai + aja[u]; K = 3.14159265358979f * sa * sa * (dv2 * rs); }
+                if (frag_mode == CUDISC_FRAG_NONE) { pf = 0.0f; pc = 1.0f; }
+                else if (frag_mode == CUDISC_FRAG_ALL) { pf = 1.0f; pc = 0.0f; }
+                else {
+                    const float x = vf2 * (rs * rs);
+                    const float e = exp_neg_ftz(x);
+                    pf = (x + 1.0f) * e;
+                    pc = pcoag_f32(x, e);
+                }
+            }
+            const bool live = j <= i;
+            o[2 * u] = live ? K * pc : 0.0f;
+            o[2 * u + 1] = live ? K * pf : 0.0f;
+        }
+        dst[2 * g] = make_float4(o[0], o[1], o[2], o[3]);
+        dst[2 * g + 1] = make_float4(o[4], o[5], o[6], o[7]);
+    }
 }
 
 __global__ void get_kernel_kernel(int c0, int n_cells, int Np, int precision, int n_slots,
@@ -235,8 +340,8 @@ __global__ void get_kernel_kernel(int c0, int n_cells, int Np, int precision, in
         int row0 = 0;
         for (int r = 0; r < i; r++) row0 += (r + 16) >> 4;
         const int q = (row0 + (j >> 4)) * 16 + (j & 15);
-        float2 v = K32[(size_t)c * n_slots + q];
-        k = v.x; kf = v.y;
+        float2 v = K32[(size_t)c * n_slots + q];          // {K p_c, K p_f}
+        k = (double)v.x + (double)v.y; kf = v.y;
     }
     K[(size_t)c * Np + p] = k;
     KF[(size_t)c * Np + p] = kf;
@@ -268,14 +373,15 @@ cudaError_t launch_kbuild(const cudisc_coag_ctx *c)
         }
     } else {
         const int n_slots = c->n_blk * kBlkPairs;
-        for (int c0 = 0; c0 < c->n_cells; c0 += kMaxGridY) {
-        dim3 grid((n_slots + 255) / 256, std::min(kMaxGridY, c->n_cells - c0));
-        kbuild32_kernel<<<grid, 256, 0, c->stream>>>(
-            c0, (float)p.kernel_const, (float)p.v_frag, p.kernel_mode, p.frag_mode, p.v_dust != nullptr,
-            c->n_cells, c->N,
-            n_slots, c->d_blk_i, c->d_blk_j0, c->d_a, c->d_minv, c->d_m, c->d_prep32, c->d_scal32,
-            c->d_K32);
-        }
+        const int NR = (c->N + 15) / 16 * 16;
+        const size_t smem = (size_t)KB_COUNT * NR * sizeof(float);
+        const bool phys = p.kernel_mode == CUDISC_KERNEL_PHYSICAL && p.frag_mode == CUDISC_FRAG_PHYSICAL;
+        const bool vd = p.v_dust != nullptr;
+        auto kern = phys ? (vd ? kbuild32_kernel<true, true> : kbuild32_kernel<true, false>)
+                         : (vd ? kbuild32_kernel<false, true> : kbuild32_kernel<false, false>);
+        kern<<<c->n_cells, 256, smem, c->stream>>>(
+            (float)p.kernel_const, (float)p.v_frag, p.kernel_mode, p.frag_mode, c->n_cells, c->N, NR,
+            n_slots, c->d_blk_i, c->d_blk_j0, c->d_prep32, c->d_scal32, c->d_K32);
     }
     return cudaGetLastError();
 }

@@ -3,11 +3,13 @@
 // The gain/loss redistribution of Eq. (smol) is a contraction over pairs:
 //   d rho_k / dt = S^2 sum_q Bt[k][q] A[c][q],
 // with S = sum_k |rho_k| per cell, x = rho / S, and per pair p = (i, j <= i)
-// two columns q: A = x_i x_j K_ij and A = x_i x_j K_ij p_frag,ij.  Bt holds
-// the fixed net redistribution coefficients per unit n_i n_j K (coagulation
-// into the two bins of Eq. Cijk, remnant into those of Eq. Rijk, fragments
-// by N_k of Eq. Nijk, minus the two colliding grains; 1/2 at i = j), divided
-// by m_i m_j.  It is built once on the host in double-double.
+// two columns q: A = x_i x_j K_ij p_coag,ij and A = x_i x_j K_ij p_frag,ij.
+// Bt holds the fixed net redistribution coefficients per unit n_i n_j K and
+// outcome: coagulation into the two bins of Eq. Cijk minus the two colliding
+// grains, and remnant into those of Eq. Rijk plus fragments by N_k of
+// Eq. Nijk minus the two colliding grains (1/2 at i = j), divided by m_i m_j.
+// It is built once on the host in double-double.  Carrying p_coag and p_frag
+// each in its own column keeps both accurate in FP32 whichever dominates.
 //
 // Layout on chip (one CTA per SM, persistent over all right-hand sides):
 //   MMA M = 128 bins (Bt, streamed as swizzled 32 KB TF32 hi/lo tiles by the

@@ -382,7 +382,11 @@ __global__ void __launch_bounds__(256) kderiv_kernel(
     const int i = ij >> 16, j = ij & 0xffff;
     double K, KF;
     if (K64) { const double2 v = K64[(size_t)c * Np + p]; K = v.x; KF = v.y; }
-    else { const float2 v = K32[(size_t)c * n_slots + pair_q[p]]; K = v.x; KF = v.y; }
+    else {   // mixed tables hold {K p_c, K p_f}
+        const float2 v = K32[(size_t)c * n_slots + pair_q[p]];
+        K = (double)v.x + (double)v.y;
+        KF = v.y;
+    }
     const double *pr = prep + (size_t)c * PF_COUNT * N;
     const CellScal s = scal[c];
     const double Si = pr[PF_ST * N + i], Sj = pr[PF_ST * N + j];
