@@ -12,16 +12,21 @@
 // each in its own column keeps both accurate in FP32 whichever dominates.
 //
 // Layout on chip (one CTA per SM, persistent over all right-hand sides):
-//   MMA M = 128 bins (Bt, streamed as swizzled 32 KB TF32 hi/lo tiles by the
-//   bulk-copy engine), MMA N = NS cell slots (generated operand), K = 32
-//   TF32 elements (16 pairs) per block.  Each block issues the four products
-//   of (Bt_hi + Bt_lo)(A_hi + A_lo), hi and lo rounded to nearest TF32: hi x
-//   hi into one of several FP32 accumulators [128 lanes x NS columns] in TMEM
-//   (a contiguous share of the blocks each), the three corrections into one
-//   more; the epilogue adds them with a compensated (Neumaier) FP32 sum.
+//   MMA M = 128 rows = 64 cell slots x {A_hi, A_lo}: the generated operand
+//   A (x_i x_j K p, split into TF32 hi and lo, both rounded to nearest) is
+//   written by the generator warps straight into tensor memory, rows 0..63
+//   the hi parts and rows 64..127 the lo parts of the same 64 slots.
+//   MMA N = the bins padded to 16 (Bt, streamed as swizzled TF32 hi and lo
+//   tiles by the bulk-copy engine into shared memory, the B operand).
+//   K = 32 TF32 elements (16 pairs) per block, 8 per instruction.  Per K
+//   step two MMAs: [A_hi; A_lo] x Bt_hi into one of several FP32
+//   accumulators (a contiguous share of the blocks each) and [A_hi; A_lo] x
+//   Bt_lo into one more; the four split products hi.hi, lo.hi, hi.lo and
+//   lo.lo are the four row-halves of the two accumulators.  Only the Bt
+//   tiles pass through shared memory, once each way.
 // Warp roles: warp 0 bulk-copy producer, warp 1 MMA issuer and TMEM owner,
-// warps 2..9 generate A (x_i x_j K split into hi/lo in the SW128 K-major
-// layout) and, between right-hand sides, run the per-slot FP64 logic: the
+// warps 2..9 generate A (two warps per TMEM lane quadrant, one per half of a
+// block's pairs) and, between right-hand sides, run the per-slot logic: the
 // mass budget (sum_k f_k = 0 restored in FP64), the Bogacki-Shampine 3(2)
 // stages, the error norm, step control and refilling a slot with the next
 // cell when one finishes.
@@ -39,22 +44,16 @@ namespace cdc {
 namespace {
 
 constexpr int kGenWarps = 8;
-constexpr int kMaxMain = 8;                       // TMEM accumulators for the hi x hi products
-constexpr int kCStages = 4;                       // generated-tile ring depth
-constexpr int kMaxSB = 8;                         // mapping-tile ring depth, at most
+constexpr int kSlots = 64;                        // cell slots per CTA (TMEM rows / 2)
+constexpr int kAStages = 2;                       // generated-operand stages in TMEM (two blocks, 64 columns each)
+constexpr int kMaxMain = 8;                       // TMEM accumulators for the products with Bt_hi
+constexpr int kMaxSB = 4;                         // mapping-tile ring depth (stages of two blocks), at most
 constexpr int kThreads = 64 + 32 * kGenWarps;
-constexpr int kTileBytes = kMBins * 128;          // one 128-row x 128 B TF32 tile
+constexpr int kTileBytes = kMBins * 128;          // one 128-row x 128 B TF32 tile in global memory
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 constexpr double A21 = 0.5, A32 = 0.75;
 constexpr double B1 = 2.0 / 9.0, B2 = 1.0 / 3.0, B3 = 4.0 / 9.0;
 constexpr double E1 = -5.0 / 72.0, E2 = 1.0 / 12.0, E3 = 1.0 / 9.0, E4 = -1.0 / 8.0;
-
-// Bytes of one pipeline stage: Bt hi/lo tiles and the generated hi/lo tiles,
-// rounded up to keep every stage 1024-byte aligned.
-__host__ __device__ constexpr int stage_size(int NS)
-{
-    return ((2 * kTileBytes + 2 * NS * 128 + 1023) / 1024) * 1024;
-}
 
 enum Mode { MODE_STEP = 0, MODE_RHS = 1, MODE_REPLAY = 2 };
 enum ErrCode { ERR_WAIT_PRODUCER = 1, ERR_WAIT_MMA = 2, ERR_WAIT_GEN = 3, ERR_WAIT_EPI = 4 };
@@ -79,8 +78,9 @@ struct MixedArgs {
     long long rec_cap;
     long long *rec_n;
     int *rec_status;
-    int NS, S, XS, mode;
-    int SB, NB8;                // mapping-tile ring depth, tile rows copied (bins rounded to 8)
+    int NS, XS, mode;
+    int SB, NBP;                // mapping-tile ring depth; bins padded to 16 (MMA N, tile rows copied)
+    int nacc;                   // TMEM accumulators for the products with Bt_hi
 };
 
 struct __align__(16) Slot {
@@ -156,12 +156,28 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
 {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-__device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+// tcgen05.mma kind::tf32 with the A operand in tensor memory (M rows =
+// lanes, K columns) and B in shared memory (descriptor).
+__device__ __forceinline__ void mma_tf32_ts(uint32_t dt, uint32_t at, uint64_t b, uint32_t idesc, uint32_t acc)
 {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                 ::"r"(dt), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+                 ::"r"(dt), "r"(at), "l"(b), "r"(idesc), "r"(acc) : "memory");
 }
+// Store 16 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,"
+                 "%9,%10,%11,%12,%13,%14,%15,%16};"
+                 ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+                   "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])),
+                   "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+                   "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+                   "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+                   "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -194,27 +210,16 @@ __device__ __forceinline__ double warp_sum(double v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ double warp_max(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-__device__ __forceinline__ double warp_min(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
 // TF32 split, both parts rounded to nearest: hi = rn_tf32(v), lo =
 // rn_tf32(v - hi).  The tensor core then sees exact TF32 values and
 // hi + lo matches v to 2^-22 relative, without the bias of truncation.
+// Rounding to the 10-bit TF32 mantissa, ties away from zero, is integer
+// arithmetic on the bits of a finite float: add half a TF32 ulp (bit 12) to
+// the magnitude bits and clear the 13 dropped bits (a carry into the
+// exponent is the correct rounding up to the next binade).
 __device__ __forceinline__ float tf32_rn(float v)
 {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
 }
 
 // ---- per-slot logic (one warp per slot, lanes over bins) ------------------
@@ -507,112 +512,114 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
     }
 }
 
-// Generate one thread's share (P pairs of one cell row) of a block's operand
-// tile: a = x_i x_j K, b = x_i x_j K p_frag, each split into TF32 hi and lo
-// and stored at its place in the SW128 K-major tiles.  K comes from the
-// stage's staged rows (bulk-copied by the producer), x from the slot's row.
-template <int P>
-struct KRegs { float v[2 * P]; };
+// Generator thread: one TMEM row (a slot's hi or lo part) and eight pairs of
+// every block (half of its 16).  a = x_i x_j K p_coag, b = x_i x_j K p_frag,
+// split hi = rn_tf32(v), lo = rn_tf32(v - hi); the thread keeps the half its
+// row holds and writes the 16 values into the stage's TMEM columns.
+struct KRegs { float4 v[4]; };           // {K p_coag, K p_frag} of 8 pairs
 
-// Load one thread's K share of block b (P pairs, {K, K p_frag} each).
-template <int P>
-__device__ __forceinline__ void load_k(KRegs<P> &k, const float2 *kbase, int b)
+__device__ __forceinline__ void load_k(KRegs &k, const float2 *kbase, int b)
 {
-    const float *src = (const float *)(kbase + (size_t)b * kBlkPairs);
-    if constexpr (P == 4) {
-        const float4 a0 = __ldg((const float4 *)src), a1 = __ldg((const float4 *)src + 1);
-        k.v[0] = a0.x; k.v[1] = a0.y; k.v[2] = a0.z; k.v[3] = a0.w;
-        k.v[4] = a1.x; k.v[5] = a1.y; k.v[6] = a1.z; k.v[7] = a1.w;
-    } else if constexpr (P == 2) {
-        const float4 a0 = __ldg((const float4 *)src);
-        k.v[0] = a0.x; k.v[1] = a0.y; k.v[2] = a0.z; k.v[3] = a0.w;
-    } else {
-        const float2 a0 = __ldg((const float2 *)src);
-        k.v[0] = a0.x; k.v[1] = a0.y;
-    }
+    const float4 *src = (const float4 *)(kbase + (size_t)b * kBlkPairs);
+#pragma unroll
+    for (int q = 0; q < 4; q++) k.v[q] = __ldg(src + q);
 }
 
-template <int P>
-__device__ __forceinline__ void gen_block(float *chi, float *clo, const KRegs<P> &kr, const float *xr,
-                                          int bi, int bj0, int t0, int row, bool active)
+__device__ __forceinline__ void gen_block(uint32_t taddr, const KRegs &kr, const float *xr, int bi,
+                                          int jfirst, bool lo_half)
 {
-    float va[2 * P];
-    if (active) {
-        const float xi = xr[bi];
-        float xj[P];
-        const float *kv = kr.v;
-        if constexpr (P == 4) {
-            const float4 v = *(const float4 *)(xr + bj0 + t0);
-            xj[0] = v.x; xj[1] = v.y; xj[2] = v.z; xj[3] = v.w;
-        } else if constexpr (P == 2) {
-            const float2 v = *(const float2 *)(xr + bj0 + t0);
-            xj[0] = v.x; xj[1] = v.y;
-        } else {
-            xj[0] = xr[bj0 + t0];
-        }
+    const float xi = xr[bi];
+    const float4 xa = *(const float4 *)(xr + jfirst), xb = *(const float4 *)(xr + jfirst + 4);
+    const float xj[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+    const float *kv = (const float *)kr.v;
+    float out[16];
+    if (lo_half) {
 #pragma unroll
-        for (int u = 0; u < P; u++) {
+        for (int u = 0; u < 8; u++) {
             const float xx = xi * xj[u];
-            va[2 * u] = xx * kv[2 * u];
-            va[2 * u + 1] = xx * kv[2 * u + 1];
+#pragma unroll
+            for (int w = 0; w < 2; w++) {
+                const float v = xx * kv[2 * u + w];
+                out[2 * u + w] = tf32_rn(v - tf32_rn(v));
+            }
         }
     } else {
 #pragma unroll
-        for (int u = 0; u < 2 * P; u++) va[u] = 0.f;
-    }
-    float vh[2 * P], vl[2 * P];
+        for (int u = 0; u < 8; u++) {
+            const float xx = xi * xj[u];
 #pragma unroll
-    for (int u = 0; u < 2 * P; u++) {
-        vh[u] = tf32_rn(va[u]);
-        vl[u] = tf32_rn(va[u] - vh[u]);
-    }
-    const int e0 = 2 * t0;                                // first element of the share
-#pragma unroll
-    for (int q = 0; q < (2 * P + 3) / 4; q++) {
-        const int e = e0 + 4 * q;
-        const int off = row * 32 + ((((e >> 2) ^ (row & 7)) << 2) | (e & 3));
-        if constexpr (P >= 2) {
-            *(float4 *)(chi + off) = make_float4(vh[4 * q], vh[4 * q + 1], vh[4 * q + 2], vh[4 * q + 3]);
-            *(float4 *)(clo + off) = make_float4(vl[4 * q], vl[4 * q + 1], vl[4 * q + 2], vl[4 * q + 3]);
-        } else {
-            *(float2 *)(chi + off) = make_float2(vh[0], vh[1]);
-            *(float2 *)(clo + off) = make_float2(vl[0], vl[1]);
+            for (int w = 0; w < 2; w++) out[2 * u + w] = tf32_rn(xx * kv[2 * u + w]);
         }
     }
+    tmem_st16(taddr, out);
 }
 
-// One pass of a generator thread over all blocks: K loads run two blocks
-// ahead in registers; a row without a cell writes its zeros once per stage
-// in the pass and is skipped afterwards.
-template <int P>
-__device__ __forceinline__ bool gen_pass(const MixedArgs &a, uint8_t *cring, int cstride,
-                                         const float2 *kbase, const float *xr, uint64_t *c_empty,
-                                         uint64_t *c_full, volatile int *s_err, long long g0, int n_blk,
-                                         int SC, int NS, int row, int t0, bool active, int lane)
+// One pass of a generator warp over all blocks, a stage of two a step.  K loads
+// run four blocks ahead in four register sets used in rotation by an unrolled
+// loop (no copies of registers whose loads are still in flight); a warp whose
+// rows have no cell only takes part in the stage hand-over (its TMEM rows
+// feed accumulator rows nobody reads).
+struct GenCtx {
+    const MixedArgs *a;
+    uint32_t tmem, lane_base;
+    const float2 *kbase;
+    const float *xr;
+    uint64_t *c_empty, *c_full;
+    volatile int *s_err;
+    int n_blk, half, lane;
+    bool lo_half, active;
+    int bi, bj0;                         // pair row and first column of the next block
+};
+
+// One pipeline stage = two blocks (b = 2 st, 2 st + 1; the last stage of a
+// pass may hold one): one wait, two independent products-and-splits into
+// the stage's 64 TMEM columns, one store wait, one arrival.
+__device__ __forceinline__ bool gen_stage(GenCtx &G, KRegs &ka, KRegs &kb, int st, long long g, int &s,
+                                          uint32_t &u)
 {
-    KRegs<P> k0, k1, k2;
-    if (active) {
-        load_k<P>(k0, kbase, 0);
-        if (n_blk > 1) load_k<P>(k1, kbase, 1);
+    const int b = 2 * st;
+    if (b >= G.n_blk) return true;
+    const bool two = b + 1 < G.n_blk;
+    if (g >= kAStages && !wwait(&G.c_empty[s], (u + 1) & 1, G.s_err, ERR_WAIT_GEN)) return false;
+    int bi1 = G.bi, bj1 = G.bj0 + kBlkPairs;               // the second block's (i, j0)
+    if (bj1 > bi1) { bi1++; bj1 = 0; }
+    if (G.active) {
+        tc_fence_after();
+        const uint32_t base = G.tmem + G.lane_base + (uint32_t)(s * 64 + 16 * G.half);
+        gen_block(base, ka, G.xr, G.bi, G.bj0 + 8 * G.half, G.lo_half);
+        if (two) gen_block(base + 32, kb, G.xr, bi1, bj1 + 8 * G.half, G.lo_half);
+        tmem_st_wait();
+        tc_fence_before();
+        if (b + 4 < G.n_blk) load_k(ka, G.kbase, b + 4);
+        if (b + 5 < G.n_blk) load_k(kb, G.kbase, b + 5);
     }
-    long long g = g0;
-    int s = (int)(g0 % SC);
-    uint32_t u = (uint32_t)(g0 / SC);
-    for (int b = 0; b < n_blk; b++, g++) {
-        if (active && b + 2 < n_blk) load_k<P>(k2, kbase, b + 2);
-        if (g >= SC && !wwait(&c_empty[s], (u + 1) & 1, s_err, ERR_WAIT_GEN)) return false;
-        if (active || b < SC) {
-            float *chi = (float *)(cring + (size_t)s * cstride);
-            float *clo = chi + NS * 32;
-            const int bi = __ldg(a.t.blk_i + b), bj0 = __ldg(a.t.blk_j0 + b);
-            gen_block<P>(chi, clo, k0, xr, bi, bj0, t0, row, active);
-            fence_async_smem();
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&c_full[s]);
-        if (++s == SC) { s = 0; u++; }
-        k0 = k1;
-        k1 = k2;
+    __syncwarp();
+    if (G.lane == 0) mbar_arrive(&G.c_full[s]);
+    // blocks run along rows: (i, 0), (i, 16), .. while j0 <= i, then (i + 1, 0)
+    G.bi = bi1;
+    G.bj0 = bj1 + kBlkPairs;
+    if (G.bj0 > G.bi) { G.bi++; G.bj0 = 0; }
+    if (++s == kAStages) { s = 0; u++; }
+    return true;
+}
+
+__device__ __forceinline__ bool gen_pass(GenCtx &G, long long g0)
+{
+    G.bi = 0;
+    G.bj0 = 0;
+    KRegs k0, k1, k2, k3;
+    if (G.active) {
+        load_k(k0, G.kbase, 0);
+        if (G.n_blk > 1) load_k(k1, G.kbase, 1);
+        if (G.n_blk > 2) load_k(k2, G.kbase, 2);
+        if (G.n_blk > 3) load_k(k3, G.kbase, 3);
+    }
+    const int n_st = (G.n_blk + 1) / 2;
+    int s = (int)(g0 % kAStages);
+    uint32_t u = (uint32_t)(g0 / kAStages);
+    for (int st = 0; st < n_st; st += 2) {
+        const long long g = g0 + st;
+        if (!gen_stage(G, k0, k1, st, g, s, u) || !gen_stage(G, k2, k3, st + 1, g + 1, s, u)) return false;
     }
     return true;
 }
@@ -623,31 +630,29 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int NS = a.NS, XS = a.XS, N = a.t.N, n_blk = a.t.n_blk;
-    const int SB = a.SB, SC = kCStages;
-    const int half_bytes = a.NB8 * 128;                 // rows of one Bt tile copied
-    const int bstride = 2 * half_bytes;                 // hi then lo, both 1024-aligned
-    const int cstride = 2 * NS * 128;
+    const int NS = a.NS, XS = a.XS, N = a.t.N, n_blk = a.t.n_blk, NBP = a.NBP;
+    const int SB = a.SB;
+    const int half_bytes = NBP * 128;                   // rows of one Bt tile copied
+    const int bstride = ((2 * half_bytes + 1023) / 1024) * 1024;   // hi then lo, 1024-aligned
+    const int sstride = 2 * bstride;                    // one stage: two blocks
+    const int n_st = (n_blk + 1) / 2;                   // stages per pass
     uint8_t *bring = sm;                                // mapping tiles (also the D staging area)
-    uint8_t *cring = bring + (size_t)SB * bstride;      // generated tiles
-    float *xrows = (float *)(cring + (size_t)SC * cstride);
+    float *xrows = (float *)(bring + (size_t)SB * sstride);
     Slot *slots = (Slot *)(xrows + (size_t)NS * XS);
     uint64_t *bars = (uint64_t *)(slots + NS);
     uint64_t *bt_full = bars, *bt_empty = bars + SB;
-    uint64_t *c_full = bars + 2 * SB, *c_empty = bars + 2 * SB + SC;
-    uint64_t *done = bars + 2 * SB + 2 * SC, *go = done + 1, *gbar = done + 2, *fin = done + 3;
+    uint64_t *c_full = bars + 2 * SB, *c_empty = bars + 2 * SB + kAStages;
+    uint64_t *done = bars + 2 * SB + 2 * kAStages, *go = done + 1, *gbar = done + 2, *fin = done + 3;
     __shared__ uint32_t s_tmem;
     __shared__ int s_err, s_continue;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // TMEM: nacc accumulators for the hi x hi products, each taking a
-    // contiguous share of the blocks (every one gets at least one), plus one
-    // for the three 2^-11-smaller correction products of every block.  FP32
-    // accumulation error grows with the additions per accumulator; the
-    // epilogue adds them with a compensated (Neumaier) FP32 sum.
-    int nmain = 512 / NS - 1;
-    if (nmain > kMaxMain) nmain = kMaxMain;
-    const int nacc = n_blk < nmain ? n_blk : nmain;
-    const int tcols = (nacc + 1) * NS;
+    // TMEM columns: kAStages x 64 for the generated operand, then nacc
+    // accumulators for [A_hi; A_lo] x Bt_hi (each a contiguous share of the
+    // blocks, summed in the epilogue with a compensated FP32 sum) and one for
+    // [A_hi; A_lo] x Bt_lo, NBP columns each.
+    const int nacc = a.nacc < n_blk ? a.nacc : n_blk;   // every accumulator gets a block
+    const uint32_t acol = kAStages * 64;
+    const int tcols = (int)acol + (nacc + 1) * NBP;
     const uint32_t ncols = tcols <= 32 ? 32 : tcols <= 64 ? 64 : tcols <= 128 ? 128 : tcols <= 256 ? 256 : 512;
 
     if (threadIdx.x == 0) {
@@ -655,7 +660,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             mbar_init(&bt_full[s], 1);
             mbar_init(&bt_empty[s], 1);
         }
-        for (int s = 0; s < SC; s++) {
+        for (int s = 0; s < kAStages; s++) {
             mbar_init(&c_full[s], kGenWarps);
             mbar_init(&c_empty[s], 1);
         }
@@ -685,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     const uint32_t tmem = s_tmem;
 
     if (warp == 0) {
-        // ---- producer: mapping tiles (rows 0..NB8-1 of hi and lo) by the bulk-copy engine ----
+        // ---- producer: mapping tiles (rows 0..NBP-1 of hi and lo) by the bulk-copy engine ----
         long long g = 0;
         int ps = 0;
         uint32_t pu = 0;
@@ -695,17 +700,20 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                 if (!s_continue) break;
             }
             bool ok = true;
-            for (int b = 0; b < n_blk; b++, g++) {
+            for (int st = 0; st < n_st; st++, g++) {
                 const int s = ps;
                 const uint32_t u = pu;
                 if (++ps == SB) { ps = 0; pu++; }      // ring position without divisions
                 if (g >= SB && !wwait(&bt_empty[s], (u + 1) & 1, &s_err, ERR_WAIT_PRODUCER)) { ok = false; break; }
                 if (lane == 0) {
-                    uint8_t *dst = bring + (size_t)s * bstride;
-                    const uint8_t *src = (const uint8_t *)(a.t.Btiles + (size_t)b * (2 * kTileBytes / 16));
-                    mbar_expect_tx(&bt_full[s], 2 * half_bytes);
-                    bulk_g2s(dst, src, half_bytes, &bt_full[s]);
-                    bulk_g2s(dst + half_bytes, src + kTileBytes, half_bytes, &bt_full[s]);
+                    const int nb = 2 * st + 1 < n_blk ? 2 : 1;
+                    mbar_expect_tx(&bt_full[s], (uint32_t)(nb * 2 * half_bytes));
+                    for (int q = 0; q < nb; q++) {
+                        uint8_t *dst = bring + (size_t)s * sstride + (size_t)q * bstride;
+                        const uint8_t *src = (const uint8_t *)(a.t.Btiles + (size_t)(2 * st + q) * (2 * kTileBytes / 16));
+                        bulk_g2s(dst, src, half_bytes, &bt_full[s]);
+                        bulk_g2s(dst + half_bytes, src + kTileBytes, half_bytes, &bt_full[s]);
+                    }
                 }
                 __syncwarp();
             }
@@ -713,7 +721,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         }
     } else if (warp == 1) {
         // ---- MMA issuer ----
-        const uint32_t idesc = idesc_tf32(kMBins, NS);
+        const uint32_t idesc = idesc_tf32(2 * kSlots, NBP);
         long long g = 0;
         int ms = 0, mc = 0;
         uint32_t mu = 0, mv = 0;
@@ -723,45 +731,41 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                 if (!s_continue) break;
             }
             bool ok = true;
-            int ch = 0, ch_next = (n_blk + nacc - 1) / nacc;   // hi x hi accumulator of the block
+            int ch = 0, ch_next = (n_blk + nacc - 1) / nacc;   // Bt_hi accumulator of the block
             bool first = true;
-            for (int b = 0; b < n_blk; b++, g++) {
+            for (int st = 0; st < n_st; st++, g++) {
                 const int sb = ms, sc = mc;
                 const uint32_t ub = mu, uc = mv;
                 if (++ms == SB) { ms = 0; mu++; }
-                if (++mc == SC) { mc = 0; mv++; }
-                if (b == ch_next) { ch++; ch_next = (int)(((long long)(ch + 1) * n_blk + nacc - 1) / nacc); first = true; }
+                if (++mc == kAStages) { mc = 0; mv++; }
                 if (!wwait(&bt_full[sb], ub & 1, &s_err, ERR_WAIT_MMA) ||
                     !wwait(&c_full[sc], uc & 1, &s_err, ERR_WAIT_MMA)) { ok = false; break; }
                 tc_fence_after();
-                if (lane == 0) {
-                    const uint32_t bt_hi = su32(bring + (size_t)sb * bstride), bt_lo = bt_hi + half_bytes;
-                    const uint32_t c_hi = su32(cring + (size_t)sc * cstride), c_lo = c_hi + NS * 128;
-                    const uint64_t dbh = sw128_desc(bt_hi), dbl = sw128_desc(bt_lo);
-                    const uint64_t dch = sw128_desc(c_hi), dcl = sw128_desc(c_lo);
-                    // the pass over all blocks is split across nacc TMEM
-                    // accumulators (contiguous block ranges) summed later in FP64
-                    const uint32_t dt = tmem + (uint32_t)(ch * NS);
-                    const uint32_t dc = tmem + (uint32_t)(nacc * NS);
-                    // hi x hi into the block's accumulator; hi x lo, lo x hi and
-                    // lo x lo into the correction accumulator
-                    mma_tf32(dt, dbh, dch, idesc, first ? 0u : 1u);
-                    mma_tf32(dc, dbh, dcl, idesc, b > 0 ? 1u : 0u);
-                    mma_tf32(dc, dbl, dch, idesc, 1u);
-                    mma_tf32(dc, dbl, dcl, idesc, 1u);
+                const int nb = 2 * st + 1 < n_blk ? 2 : 1;
+                for (int q = 0; q < nb; q++) {
+                    const int b = 2 * st + q;
+                    if (b == ch_next) { ch++; ch_next = (int)(((long long)(ch + 1) * n_blk + nacc - 1) / nacc); first = true; }
+                    if (lane == 0) {
+                        const uint32_t bt_hi = su32(bring + (size_t)sb * sstride + (size_t)q * bstride);
+                        const uint64_t dbh = sw128_desc(bt_hi), dbl = sw128_desc(bt_hi + half_bytes);
+                        const uint32_t at = tmem + (uint32_t)(sc * 64 + q * 32);
+                        const uint32_t dh = tmem + acol + (uint32_t)(ch * NBP);
+                        const uint32_t dl = tmem + acol + (uint32_t)(nacc * NBP);
+                        // the four K steps into one accumulator, then into the other
 #pragma unroll
-                    for (int kk = 1; kk < 4; kk++) {
-                        const uint64_t adv = (uint64_t)(kk * 2);   // 32 bytes per K step
-                        mma_tf32(dt, dbh + adv, dch + adv, idesc, 1u);
-                        mma_tf32(dc, dbh + adv, dcl + adv, idesc, 1u);
-                        mma_tf32(dc, dbl + adv, dch + adv, idesc, 1u);
-                        mma_tf32(dc, dbl + adv, dcl + adv, idesc, 1u);
+                        for (int kk = 0; kk < 4; kk++)
+                            mma_tf32_ts(dh, at + 8 * kk, dbh + 2 * kk, idesc, (first && kk == 0) ? 0u : 1u);
+#pragma unroll
+                        for (int kk = 0; kk < 4; kk++)
+                            mma_tf32_ts(dl, at + 8 * kk, dbl + 2 * kk, idesc, (b == 0 && kk == 0) ? 0u : 1u);
                     }
+                    first = false;
+                }
+                if (lane == 0) {
                     mma_commit(&bt_empty[sb]);
                     mma_commit(&c_empty[sc]);
-                    if (b == n_blk - 1) mma_commit(done);
+                    if (st == n_st - 1) mma_commit(done);
                 }
-                first = false;
                 __syncwarp();
             }
             if (!ok) break;
@@ -769,58 +773,66 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     } else {
         // ---- generators / per-slot epilogue ----
         const int gt = threadIdx.x - 64;              // 0 .. 255
-        const int P = NS / 16;                        // pairs per thread per block
-        const int row = gt % NS;
-        const int t0 = (gt / NS) * P;
-        const float *xr = xrows + (size_t)row * XS;
+        const int qd = warp & 3;                      // TMEM lane quadrant of this warp
+        const int row = 32 * qd + lane;               // TMEM row: slot (row & 63), hi or lo part
+        const int slot = row & (kSlots - 1);
+        const bool lo_half = row >= kSlots;
+        const int half = warp >= 6 ? 1 : 0;           // pairs 8 half .. 8 half + 7 of each block
+        const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
+        const float *xr = xrows + (size_t)slot * XS;
         const int n_slots_k = n_blk * kBlkPairs;
         uint32_t gphase = 0;
         long long g = 0;
         for (int r = 0;; r++) {
-            bool ok = true;
-            const int cell = slots[row].cell;             // fixed for the whole pass
-            const bool active = cell >= 0;
-            const float2 *kbase = a.K32 + (size_t)(active ? cell : 0) * n_slots_k + t0;
-            if (P == 4) ok = gen_pass<4>(a, cring, cstride, kbase, xr, c_empty, c_full, &s_err, g, n_blk,
-                                         SC, NS, row, t0, active, lane);
-            else if (P == 2) ok = gen_pass<2>(a, cring, cstride, kbase, xr, c_empty, c_full, &s_err, g,
-                                              n_blk, SC, NS, row, t0, active, lane);
-            else ok = gen_pass<1>(a, cring, cstride, kbase, xr, c_empty, c_full, &s_err, g, n_blk, SC,
-                                  NS, row, t0, active, lane);
-            g += n_blk;
+            const int cell = slot < NS ? slots[slot].cell : -1;   // fixed for the whole pass
+            const bool active = __any_sync(0xffffffffu, cell >= 0);
+            const float2 *kbase = a.K32 + (size_t)(cell >= 0 ? cell : 0) * n_slots_k + 8 * half;
+            GenCtx G;
+            G.a = &a; G.tmem = tmem; G.lane_base = lane_base; G.kbase = kbase; G.xr = xr;
+            G.c_empty = c_empty; G.c_full = c_full; G.s_err = &s_err; G.n_blk = n_blk;
+            G.half = half; G.lane = lane; G.lo_half = lo_half; G.active = active;
+            const bool ok = gen_pass(G, g);
+            g += (n_blk + 1) / 2;                 // stages per pass
             if (!ok) break;
             // ---- epilogue: D (TMEM) -> smem [slot][bin] ----
             if (!wwait(done, r & 1, &s_err, ERR_WAIT_EPI)) break;
             tc_fence_after();
             float *Dsm = (float *)bring;                  // the mapping-tile ring is idle now
             const int DS = N;
-            {
-                const int q = warp & 3;                   // TMEM lane quadrant of this warp
-                const int half = (warp - 2) >> 2;         // which half of the columns
-                const int c0 = half * (NS / 2), c1 = c0 + NS / 2;
-                const int bin = 32 * q + lane;
-                for (int cc = c0; cc < c1; cc += 8) {
-                    // compensated (Neumaier) FP32 sum of the accumulators
-                    float sum[8], cmp[8];
+            // rows 0..63 (hi parts) write their sums, rows 64..127 (lo parts) add theirs
+            for (int ph = 0; ph < 2; ph++) {
+                if ((qd >= 2) == (ph == 1)) {
+                    const int c0 = half * (NBP / 2), c1 = c0 + NBP / 2;
+                    for (int cc = c0; cc < c1; cc += 8) {
+                        // compensated (Neumaier) FP32 sum of the accumulators
+                        float sum[8], cmp[8];
 #pragma unroll
-                    for (int z = 0; z < 8; z++) { sum[z] = 0.f; cmp[z] = 0.f; }
-                    for (int ch = 0; ch <= nacc; ch++) {
-                        float v[8];
-                        tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ch * NS + cc), v);
+                        for (int z = 0; z < 8; z++) { sum[z] = 0.f; cmp[z] = 0.f; }
+                        for (int ch = 0; ch <= nacc; ch++) {
+                            float v[8];
+                            tmem_ld8(tmem + lane_base + acol + (uint32_t)(ch * NBP + cc), v);
 #pragma unroll
-                        for (int z = 0; z < 8; z++) {
-                            const float t = sum[z] + v[z];
-                            cmp[z] += (fabsf(sum[z]) >= fabsf(v[z])) ? (sum[z] - t) + v[z] : (v[z] - t) + sum[z];
-                            sum[z] = t;
+                            for (int z = 0; z < 8; z++) {
+                                const float t = sum[z] + v[z];
+                                cmp[z] += (fabsf(sum[z]) >= fabsf(v[z])) ? (sum[z] - t) + v[z] : (v[z] - t) + sum[z];
+                                sum[z] = t;
+                            }
+                        }
+                        if (slot < NS) {
+#pragma unroll
+                            for (int z = 0; z < 8; z++) {
+                                const int bin = cc + z;
+                                if (bin < N) {
+                                    float *dp = Dsm + (size_t)slot * DS + bin;
+                                    *dp = ph == 0 ? sum[z] + cmp[z] : *dp + (sum[z] + cmp[z]);
+                                }
+                            }
                         }
                     }
-                    if (bin < N) {
-#pragma unroll
-                        for (int z = 0; z < 8; z++)
-                            if (cc + z < c1) Dsm[(size_t)(cc + z) * DS + bin] = sum[z] + cmp[z];
-                    }
                 }
+                if (ph == 0 && !gen_sync(gbar, gphase, &s_err)) { r = -1; break; }
             }
+            if (r < 0) break;
             tc_fence_before();
             if (!gen_sync(gbar, gphase, &s_err)) break;
             // ---- per-slot integrator logic ----
@@ -875,8 +887,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     if (threadIdx.x == 0 && s_err) atomicCAS(a.err, 0, s_err);
 }
 
-struct Config { int grid, NS, S, XS, SB, NB8; size_t smem; };
-
+struct Config { int grid, NS, XS, SB, NBP, nacc; size_t smem; };
 
 Config mixed_config(int n_cells, int N)
 {
@@ -884,32 +895,27 @@ Config mixed_config(int n_cells, int N)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     Config c;
-    // every SM gets a CTA once there are 16 cells per SM; slots per CTA are
-    // a multiple of 16 (the MMA N), at most 64
-    c.grid = std::max(1, std::min(n_sm, (n_cells + 15) / 16));
-    const int per = (n_cells + c.grid - 1) / c.grid;
-    int NS = ((per + 15) / 16) * 16;
-    NS = std::min(NS, 64);
-    if (NS > 32) NS = 64;
-    c.NS = NS;
-    c.S = kCStages;
+    // 64 slots per CTA (the MMA's 128 rows are the hi and lo parts of 64
+    // slots); cells are spread over up to one CTA per SM, at least 8 a CTA
+    c.grid = std::max(1, std::min(n_sm, (n_cells + 7) / 8));
+    c.NS = kSlots;
     const int n16 = ((N + 15) / 16) * 16;
     c.XS = n16 + 4;                              // rows 16 B aligned, 4 words off the bank period
-    c.NB8 = ((N + 7) / 8) * 8;
-    const size_t bstride = 2 * (size_t)c.NB8 * 128;
-    const size_t cring = (size_t)kCStages * 2 * NS * 128;
-    const size_t tail = (size_t)NS * c.XS * 4 + (size_t)NS * sizeof(Slot) + 8 * (2 * kMaxSB + 2 * kCStages + 4);
+    c.NBP = n16;
+    // TMEM: 512 columns = generated stages + (nacc + 1) accumulators of NBP
+    c.nacc = std::min(kMaxMain, (512 - kAStages * 64) / n16 - 1);
+    const size_t bstride = 2 * (((2 * (size_t)c.NBP * 128 + 1023) / 1024) * 1024);   // a stage: two blocks
+    const size_t tail = (size_t)kSlots * c.XS * 4 + (size_t)kSlots * sizeof(Slot) +
+                        8 * (2 * kMaxSB + 2 * kAStages + 4);
     const size_t budget = 232448 - 1024 - 2048;  // opt-in shared memory, alignment, static
-    int SB = (int)((budget - cring - tail) / bstride);
+    int SB = (int)((budget - tail) / bstride);
     SB = std::min(SB, kMaxSB);
-    // the D staging area (NS x N doubles) aliases the mapping-tile ring
-    while ((size_t)SB * bstride < (size_t)NS * N * 8 && SB < kMaxSB) SB++;
+    // the D staging area (slots x N floats) aliases the mapping-tile ring
+    while ((size_t)SB * bstride < (size_t)kSlots * N * 4 && SB < kMaxSB) SB++;
     c.SB = SB;
-    // the MMA reads all 128 tile rows: rows past NB8 of the last tile fall in
-    // the bytes after the ring, which must stay inside the allocation
-    const size_t ring_end = (size_t)SB * bstride;
-    const size_t layout_end = ring_end + cring + tail;
-    c.smem = 1024 + std::max(layout_end, ring_end + (size_t)kTileBytes);
+    // at least 120 KB, so that no two CTAs share an SM (each holds all 512
+    // TMEM columns for the whole kernel)
+    c.smem = std::max((size_t)120 * 1024, 1024 + (size_t)SB * bstride + tail);
     return c;
 }
 
@@ -946,10 +952,10 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.rec_n = mode == MODE_RHS ? nullptr : c->rec_n;
     a.rec_status = mode == MODE_RHS ? nullptr : c->rec_status;
     a.NS = cf.NS;
-    a.S = cf.S;
     a.XS = cf.XS;
     a.SB = cf.SB;
-    a.NB8 = cf.NB8;
+    a.NBP = cf.NBP;
+    a.nacc = cf.nacc;
     a.mode = mode;
     step_mixed_kernel<<<cf.grid, kThreads, cf.smem, c->stream>>>(a);
     return cudaGetLastError();
@@ -1024,10 +1030,10 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     a.rec_n = c->rec_n;
     a.rec_status = c->rec_status;
     a.NS = cf.NS;
-    a.S = cf.S;
     a.XS = cf.XS;
     a.SB = cf.SB;
-    a.NB8 = cf.NB8;
+    a.NBP = cf.NBP;
+    a.nacc = cf.nacc;
     a.mode = MODE_STEP;
     step_mixed_kernel<<<cf.grid, kThreads, cf.smem, c->stream>>>(a);
     return cudaGetLastError();
