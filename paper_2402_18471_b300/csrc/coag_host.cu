@@ -165,8 +165,8 @@ static cudisc_status validate(const cudisc_coag_params *p, std::string &why)
         why = "n_bins > 160 is not supported by this build";
         return CUDISC_ENOTSUP;
     }
-    if (p->precision == CUDISC_MIXED_TF32 && p->n_bins > cdc::kMBins) {
-        why = "the mixed precision path supports n_bins <= 128";
+    if (p->precision == CUDISC_MIXED_TF32 && p->n_bins > cdc::kMaxMixedBins) {
+        why = "the mixed precision path supports n_bins <= 160";
         return CUDISC_ENOTSUP;
     }
     if (p->precision != CUDISC_FP64 && p->precision != CUDISC_MIXED_TF32) {
@@ -232,7 +232,7 @@ static cudisc_status build_tables(cudisc_coag_ctx *c)
     // All coefficients are divided by m_i m_j so that they multiply rho_i rho_j K.
     std::vector<std::vector<std::pair<int, double2>>> rows(N);
     std::vector<std::vector<std::pair<int, double>>> frows(N);
-    // mixed path dense tile image: per block b, hi then lo, 128 rows x 32 floats
+    // mixed path dense tile image: per block b, hi then lo, NBP rows x 32 floats
     c->n_blk = 0;
     std::vector<int> blk_i, blk_j0;
     for (int i = 0; i < N; i++)
@@ -240,7 +240,8 @@ static cudisc_status build_tables(cudisc_coag_ctx *c)
     c->n_blk = (int)blk_i.size();
     const bool mixed = p.precision == CUDISC_MIXED_TF32;
     std::vector<float> tiles;
-    if (mixed) tiles.assign((size_t)c->n_blk * 2 * cdc::kMBins * cdc::kBlkElems, 0.0f);
+    const int NBP = (N + 15) / 16 * 16;
+    if (mixed) tiles.assign((size_t)c->n_blk * 2 * NBP * cdc::kBlkElems, 0.0f);
 
     std::vector<dd> colA(N), colB(N);
     int blk = 0;
@@ -308,9 +309,9 @@ static cudisc_status build_tables(cudisc_coag_ctx *c)
                         float lo = bits_f(tf32_rn_bits((float)(v - (double)hi)));
                         int chunk = e >> 2;
                         size_t off = (size_t)k * 32 + (size_t)(((chunk ^ (k & 7)) << 2) | (e & 3));
-                        size_t base = (size_t)b * 2 * cdc::kMBins * 32;
+                        size_t base = (size_t)b * 2 * NBP * 32;
                         tiles[base + off] = hi;
-                        tiles[base + (size_t)cdc::kMBins * 32 + off] = lo;
+                        tiles[base + (size_t)NBP * 32 + off] = lo;
                     }
                 }
             }

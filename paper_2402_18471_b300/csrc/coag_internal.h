@@ -14,7 +14,7 @@ struct VjpState;                      // adjoint tables and workspace (vjp.cu)
 constexpr int kMaxBins = 160;         // FP64 path keeps the pair weights of one cell in smem
 constexpr int kBlkPairs = 16;         // pairs per K-block of the mixed contraction
 constexpr int kBlkElems = 32;         // TF32 elements per K-block row (a and b per pair)
-constexpr int kMBins = 128;           // MMA M: bins padded to 128 rows (N <= 128 here)
+constexpr int kMaxMixedBins = 160;    // mixed path: bins up to this (MMA N = bins rounded up to 16)
 constexpr int kMaxGridY = 65535;      // launches over cells are chunked to this
 
 // Per-cell scalars produced by the prep kernel (FP64).
@@ -64,7 +64,7 @@ struct DevTables {
     // mixed path
     int n_blk;
     const int *blk_i, *blk_j0;                // [n_blk]
-    const float4 *Btiles;                     // [n_blk][2][128][32] swizzled TF32 hi/lo
+    const float4 *Btiles;                     // [n_blk][2][NBP][32] swizzled TF32 hi/lo, NBP = N rounded to 16
 };
 
 } // namespace cdc

@@ -49,7 +49,7 @@ constexpr int kAStages = 2;                       // generated-operand stages in
 constexpr int kMaxMain = 8;                       // TMEM accumulators for the products with Bt_hi
 constexpr int kMaxSB = 4;                         // mapping-tile ring depth (stages of two blocks), at most
 constexpr int kThreads = 64 + 32 * kGenWarps;
-constexpr int kTileBytes = kMBins * 128;          // one 128-row x 128 B TF32 tile in global memory
+constexpr int kLaneBins = (kMaxMixedBins + 31) / 32;   // bins per lane in the per-slot logic
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 constexpr double A21 = 0.5, A32 = 0.75;
 constexpr double B1 = 2.0 / 9.0, B2 = 1.0 / 3.0, B3 = 4.0 / 9.0;
@@ -311,10 +311,10 @@ __device__ void slot_finish(const MixedArgs &a, Slot &sl, int slot)
 __device__ void commit_increment(const Slot &sl, SlotBufs B, int N, const float *dx)
 {
     const int lane = threadIdx.x & 31;
-    double d[(kMBins + 31) / 32];
+    double d[kLaneBins];
     double s = 0.0, sa = 0.0;
 #pragma unroll
-    for (int m = 0; m < (kMBins + 31) / 32; m++) {
+    for (int m = 0; m < kLaneBins; m++) {
         const int k = lane + 32 * m;
         d[m] = (k < N) ? (double)dx[m] * sl.Sx : 0.0;
         s += d[m];
@@ -325,7 +325,7 @@ __device__ void commit_increment(const Slot &sl, SlotBufs B, int N, const float 
     const double q = sa > 0.0 ? s / sa : 0.0;
     const double r = 1.0 / sl.Sx;
 #pragma unroll
-    for (int m = 0; m < (kMBins + 31) / 32; m++) {
+    for (int m = 0; m < kLaneBins; m++) {
         const int k = lane + 32 * m;
         if (k < N) {
             const double y = B.y[k] + (d[m] - q * fabs(d[m]));
@@ -356,7 +356,7 @@ __device__ bool begin_step(const MixedArgs &a, Slot &sl, float *xrow, SlotBufs B
 __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const float *Drow, int slot)
 {
     const int N = a.t.N, lane = threadIdx.x & 31;
-    constexpr int MB = (kMBins + 31) / 32;
+    constexpr int MB = kLaneBins;
     SlotBufs B = slot_bufs(a, slot);
     const float sx = (float)sl.Sx;
     float kv[MB];
@@ -710,9 +710,9 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     mbar_expect_tx(&bt_full[s], (uint32_t)(nb * 2 * half_bytes));
                     for (int q = 0; q < nb; q++) {
                         uint8_t *dst = bring + (size_t)s * sstride + (size_t)q * bstride;
-                        const uint8_t *src = (const uint8_t *)(a.t.Btiles + (size_t)(2 * st + q) * (2 * kTileBytes / 16));
+                        const uint8_t *src = (const uint8_t *)(a.t.Btiles + (size_t)(2 * st + q) * (2 * half_bytes / 16));
                         bulk_g2s(dst, src, half_bytes, &bt_full[s]);
-                        bulk_g2s(dst + half_bytes, src + kTileBytes, half_bytes, &bt_full[s]);
+                        bulk_g2s(dst + half_bytes, src + half_bytes, half_bytes, &bt_full[s]);
                     }
                 }
                 __syncwarp();

@@ -61,8 +61,13 @@ CASES = {
     "N24_9000_cells": lambda: synth.make_disc(100, 90, 24, 1e-5, 0.1, 5.0, 100.0, 20.0, seed=6),
     "N20_20000_cells_refill": lambda: synth.make_disc(200, 100, 20, 1e-5, 0.1, 5.0, 100.0, 20.0, seed=7),
     "N128_5_cells": lambda: synth.make_disc(1, 5, 128, 1e-5, 10.0, 10.0, 10.0, 20.0),
+    # bins past 128: MMA N of 144 and 160 (0.1 um - 1 m for 150 bins)
+    "N129_3_cells": lambda: synth.make_disc(1, 3, 129, 1e-5, 10.0, 10.0, 10.0, 20.0, seed=13),
+    "N150_9_cells": lambda: synth.make_disc(3, 3, 150, 1e-5, 100.0, 5.0, 100.0, 20.0, alpha=1e-4,
+                                            v_frag=1000.0, seed=14),
 }
-SMALL = ["N2_one_cell", "N17_37_cells", "column_1x32_N50", "N128_5_cells"]
+SMALL = ["N2_one_cell", "N17_37_cells", "column_1x32_N50", "N128_5_cells", "N129_3_cells",
+         "N150_9_cells"]
 
 
 def sample_of(d, k=24):
@@ -99,7 +104,7 @@ def test_kernel_build_fp32_matches_oracle(coag_mod, oracle_mod, case):
     assert np.all(np.abs(KFg - KFo) <= 3e-5 * np.abs(KFo) + 2e-6 * Ko)
 
 
-@pytest.mark.parametrize("case", ["N17_37_cells", "column_1x32_N50", "N128_5_cells"])
+@pytest.mark.parametrize("case", ["N17_37_cells", "column_1x32_N50", "N128_5_cells", "N150_9_cells"])
 def test_replay_mixed_matches_oracle(coag_mod, oracle_mod, case):
     """The oracle's own accepted step sequence replayed by both sides."""
     d = CASES[case]()
@@ -159,6 +164,23 @@ def test_full_size_grid_mixed_rhs_sampled(coag_mod, oracle_mod):
     ref = o.rhs(rho[cells])
     err = np.abs(out[cells] - ref) / gross(o, ds, rho[cells])[:, None]
     assert err.max() < 3e-6, err.max()
+
+
+def test_full_size_large_grid_mixed_rhs_sampled(coag_mod, oracle_mod):
+    """512 x 256 cells x 150 bins (0.1 um - 1 m): kernel build and the mixed
+    right-hand side of all 131072 cells; sampled cells against the oracle."""
+    d = synth.grid_512x256()
+    rho = synth.random_state(d, seed=17)
+    g = coag_mod.Coag(d, "mixed")
+    out = g.rhs(g.state(rho)).cpu().numpy()
+    g.close()
+    cells = np.arange(0, d.n_cells, 8191)
+    ds = d.subset(cells)
+    o = oracle_mod.Oracle(ds)
+    ref = o.rhs(rho[cells])
+    err = np.abs(out[cells] - ref) / gross(o, ds, rho[cells])[:, None]
+    assert err.max() < 3e-6, err.max()
+    assert np.isfinite(out).all()
 
 
 def test_full_size_fp64_step_conserves_mass(coag_mod):
