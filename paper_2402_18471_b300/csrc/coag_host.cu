@@ -414,7 +414,11 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
         if (params->precision == CUDISC_FP64)
             e = cudaMalloc(&c->d_K64, nc * (size_t)c->Np * sizeof(double2));
         else
-            e = cudaMalloc(&c->d_K32, nc * (size_t)c->n_blk * cdc::kBlkPairs * sizeof(float2));
+        {
+            cdc::mixed_layout(c->n_cells, c->N, &c->k32_G, &c->k32_C);
+            c->k32_n = std::max(c->n_cells, c->k32_G * c->k32_C);
+            e = cudaMalloc(&c->d_K32, (size_t)c->k32_n * c->n_blk * cdc::kBlkPairs * sizeof(float2));
+        }
     }
     if (e == cudaSuccess && params->precision == CUDISC_MIXED_TF32) {
         c->work_bytes = cdc::mixed_workspace_bytes(c->n_cells, c->N);

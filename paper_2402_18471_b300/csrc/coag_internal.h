@@ -17,6 +17,25 @@ constexpr int kBlkElems = 32;         // TF32 elements per K-block row (a and b 
 constexpr int kMaxMixedBins = 160;    // mixed path: bins up to this (MMA N = bins rounded up to 16)
 constexpr int kMaxGridY = 65535;      // launches over cells are chunked to this
 
+// Layout of the mixed path's FP32 kernel tables {K p_coag, K p_frag}.  The
+// integration kernel's CTA x (of G) starts with cells x, x + G, .. in its
+// slots 0, 1, .. C - 1 (cells of all radii in every CTA); a cell's table
+// sits at its slot position pos = x C + s, so that one CTA's cells are
+// adjacent, and cells past G C (refills) at pos = c.  Per 16-pair block b
+// and 2-pair chunk ch = t / 2 of pair slot q = 16 b + t the 16-byte chunks of
+// all positions are adjacent, [b][ch][pos][2 x float2]: a warp whose lanes
+// hold neighbouring positions reads 512 contiguous bytes.
+__host__ __device__ inline int k32_pos(int c, int G, int C)
+{
+    return c < G * C ? (c % G) * C + c / G : c;
+}
+// float2 index of pair slot q at position pos (n_pos positions in all)
+__host__ __device__ inline size_t k32_index(int pos, int q, int n_pos)
+{
+    const int b = q >> 4, t = q & 15;
+    return ((size_t)(8 * b + (t >> 1)) * n_pos + pos) * 2 + (t & 1);
+}
+
 // Per-cell scalars produced by the prep kernel (FP64).
 struct CellScal {
     double kT8pi;   // 8 k_B T / pi  (Eq. vbrown numerator per unit mass sum)
@@ -90,7 +109,8 @@ struct cudisc_coag_ctx {
     cdc::CellScal *d_scal = nullptr;   // [n_cells]
     float4 *d_scal32 = nullptr;        // [n_cells] {delta, Vg2, etavK, ZOm} in FP32
     double2 *d_K64 = nullptr;          // [n_cells][Np]      {K, K p_frag}
-    float2 *d_K32 = nullptr;           // [n_cells][n_blk*16] {K, K p_frag}
+    float2 *d_K32 = nullptr;           // k32_n x n_blk x 16 {K p_coag, K p_frag}, see k32_index
+    int k32_G = 1, k32_C = 1, k32_n = 0;   // its layout: CTAs, initial cells per CTA, positions
     // integration workspace
     cdc::CellOut *d_out = nullptr;     // [n_cells]
     double *d_work = nullptr;          // mixed path slot state
@@ -121,6 +141,7 @@ cudaError_t launch_step_mixed(const cudisc_coag_ctx *c, double *rho, double t_sp
                               double *dt_cell, const double *replay_h,
                               const long long *replay_n, long long replay_stride);
 size_t mixed_workspace_bytes(int n_cells, int N);
+void mixed_layout(int n_cells, int N, int *G, int *C);   // CTAs and initial cells per CTA
 // adjoint (vjp.cu)
 bool vjp_fits(const cudisc_coag_ctx *c);
 cudaError_t vjp_prepare(cudisc_coag_ctx *c, long long max_steps);

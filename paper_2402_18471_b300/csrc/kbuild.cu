@@ -189,6 +189,7 @@ enum { KB_INVA = P3_COUNT, KB_INVQ, KB_COUNT };
 
 // FP32 builder in the blocked pair layout of the mixed contraction: slot
 // q = 16 b + t is pair (blk_i[b], blk_j0[b] + t) and holds {K p_c, K p_f}
+// (stored cell-interleaved, see k32_index)
 // (p_c = 1 - p_f, each accurate to a few ulp of itself, so that neither
 // coagulation in a fragmentation-dominated cell nor fragmentation in a
 // coagulation-dominated one is lost to rounding); slots past the diagonal
@@ -204,7 +205,7 @@ enum { KB_INVA = P3_COUNT, KB_INVQ, KB_COUNT };
 template <bool Physical, bool HasVdust>
 __global__ void __launch_bounds__(256) kbuild32_kernel(
     float kc, float v_frag, int kernel_mode, int frag_mode, int n_cells, int N, int NR,
-    int n_slots, const int *__restrict__ blk_i, const int *__restrict__ blk_j0,
+    int n_slots, int kG, int kC, int kn, const int *__restrict__ blk_i, const int *__restrict__ blk_j0,
     const float *__restrict__ prep32, const float4 *__restrict__ scal32,
     float2 *__restrict__ Kout)
 {
@@ -227,7 +228,8 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
     const float vf2 = 1.5f * v_frag * v_frag;
     const float *St = f32s + P3_ST * NR, *U = f32s + P3_U * NR, *Aa = f32s + P3_A * NR;
     const float *IA = f32s + KB_INVA * NR, *IQ = f32s + KB_INVQ * NR;
-    float4 *dst = reinterpret_cast<float4 *>(Kout + (size_t)c * n_slots);
+    float4 *dst = reinterpret_cast<float4 *>(Kout);       // chunk (b, ch): (8 b + ch) kn + pos
+    const int pos = k32_pos(c, kG, kC);
     for (int g = threadIdx.x; 4 * g < n_slots; g += blockDim.x) {
         const int q0 = 4 * g;
         const int b = q0 >> 4;
@@ -316,12 +318,13 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
             o[2 * u] = live ? K * pc : 0.0f;
             o[2 * u + 1] = live ? K * pf : 0.0f;
         }
-        dst[2 * g] = make_float4(o[0], o[1], o[2], o[3]);
-        dst[2 * g + 1] = make_float4(o[4], o[5], o[6], o[7]);
+        const size_t ch0 = (size_t)(8 * b + ((q0 & 15) >> 1));  // the group's first 2-pair chunk
+        dst[ch0 * kn + pos] = make_float4(o[0], o[1], o[2], o[3]);
+        dst[(ch0 + 1) * kn + pos] = make_float4(o[4], o[5], o[6], o[7]);
     }
 }
 
-__global__ void get_kernel_kernel(int c0, int n_cells, int Np, int precision, int n_slots,
+__global__ void get_kernel_kernel(int c0, int n_cells, int Np, int precision, int kG, int kC, int kn,
                                   const unsigned int *__restrict__ pij,
                                   const double2 *__restrict__ K64,
                                   const float2 *__restrict__ K32, double *__restrict__ K,
@@ -340,7 +343,7 @@ __global__ void get_kernel_kernel(int c0, int n_cells, int Np, int precision, in
         int row0 = 0;
         for (int r = 0; r < i; r++) row0 += (r + 16) >> 4;
         const int q = (row0 + (j >> 4)) * 16 + (j & 15);
-        float2 v = K32[(size_t)c * n_slots + q];          // {K p_c, K p_f}
+        float2 v = K32[k32_index(k32_pos(c, kG, kC), q, kn)];   // {K p_c, K p_f}
         k = (double)v.x + (double)v.y; kf = v.y;
     }
     K[(size_t)c * Np + p] = k;
@@ -381,7 +384,8 @@ cudaError_t launch_kbuild(const cudisc_coag_ctx *c)
                          : (vd ? kbuild32_kernel<false, true> : kbuild32_kernel<false, false>);
         kern<<<c->n_cells, 256, smem, c->stream>>>(
             (float)p.kernel_const, (float)p.v_frag, p.kernel_mode, p.frag_mode, c->n_cells, c->N, NR,
-            n_slots, c->d_blk_i, c->d_blk_j0, c->d_prep32, c->d_scal32, c->d_K32);
+            n_slots, c->k32_G, c->k32_C, c->k32_n, c->d_blk_i, c->d_blk_j0, c->d_prep32, c->d_scal32,
+            c->d_K32);
     }
     return cudaGetLastError();
 }
@@ -391,8 +395,8 @@ cudaError_t launch_get_kernel(const cudisc_coag_ctx *c, double *K, double *KF)
     for (int c0 = 0; c0 < c->n_cells; c0 += kMaxGridY) {
     dim3 grid((c->Np + 255) / 256, std::min(kMaxGridY, c->n_cells - c0));
     get_kernel_kernel<<<grid, 256, 0, c->stream>>>(c0, c->n_cells, c->Np, c->p.precision,
-                                                   c->n_blk * kBlkPairs, c->d_pair_ij, c->d_K64,
-                                                   c->d_K32, K, KF);
+                                                   c->k32_G, c->k32_C, c->k32_n, c->d_pair_ij,
+                                                   c->d_K64, c->d_K32, K, KF);
     }
     return cudaGetLastError();
 }

@@ -80,6 +80,7 @@ struct MixedArgs {
     int *rec_status;
     int NS, XS, mode;
     int SB, NBP;                // mapping-tile ring depth; bins padded to 16 (MMA N, tile rows copied)
+    int kC, kn;                 // K table layout: initial cells per CTA, positions (k32_pos)
     int nacc;                   // TMEM accumulators for the products with Bt_hi
 };
 
@@ -518,11 +519,13 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
 // row holds and writes the 16 values into the stage's TMEM columns.
 struct KRegs { float4 v[4]; };           // {K p_coag, K p_frag} of 8 pairs
 
-__device__ __forceinline__ void load_k(KRegs &k, const float2 *kbase, int b)
+// The thread's four 2-pair chunks of block b: kbase points at chunk 4 half of
+// block 0 of its cell; chunks are n_cells float4 apart, blocks 8 n_cells.
+__device__ __forceinline__ void load_k(KRegs &k, const float4 *kbase, int b, int n_cells)
 {
-    const float4 *src = (const float4 *)(kbase + (size_t)b * kBlkPairs);
+    const float4 *src = kbase + (size_t)b * 8 * n_cells;
 #pragma unroll
-    for (int q = 0; q < 4; q++) k.v[q] = __ldg(src + q);
+    for (int q = 0; q < 4; q++) k.v[q] = __ldg(src + (size_t)q * n_cells);
 }
 
 __device__ __forceinline__ void gen_block(uint32_t taddr, const KRegs &kr, const float *xr, int bi,
@@ -562,11 +565,11 @@ __device__ __forceinline__ void gen_block(uint32_t taddr, const KRegs &kr, const
 struct GenCtx {
     const MixedArgs *a;
     uint32_t tmem, lane_base;
-    const float2 *kbase;
+    const float4 *kbase;
     const float *xr;
     uint64_t *c_empty, *c_full;
     volatile int *s_err;
-    int n_blk, half, lane;
+    int n_blk, half, lane, n_cells;
     bool lo_half, active;
     int bi, bj0;                         // pair row and first column of the next block
 };
@@ -590,8 +593,8 @@ __device__ __forceinline__ bool gen_stage(GenCtx &G, KRegs &ka, KRegs &kb, int s
         if (two) gen_block(base + 32, kb, G.xr, bi1, bj1 + 8 * G.half, G.lo_half);
         tmem_st_wait();
         tc_fence_before();
-        if (b + 4 < G.n_blk) load_k(ka, G.kbase, b + 4);
-        if (b + 5 < G.n_blk) load_k(kb, G.kbase, b + 5);
+        if (b + 4 < G.n_blk) load_k(ka, G.kbase, b + 4, G.n_cells);
+        if (b + 5 < G.n_blk) load_k(kb, G.kbase, b + 5, G.n_cells);
     }
     __syncwarp();
     if (G.lane == 0) mbar_arrive(&G.c_full[s]);
@@ -609,10 +612,10 @@ __device__ __forceinline__ bool gen_pass(GenCtx &G, long long g0)
     G.bj0 = 0;
     KRegs k0, k1, k2, k3;
     if (G.active) {
-        load_k(k0, G.kbase, 0);
-        if (G.n_blk > 1) load_k(k1, G.kbase, 1);
-        if (G.n_blk > 2) load_k(k2, G.kbase, 2);
-        if (G.n_blk > 3) load_k(k3, G.kbase, 3);
+        load_k(k0, G.kbase, 0, G.n_cells);
+        if (G.n_blk > 1) load_k(k1, G.kbase, 1, G.n_cells);
+        if (G.n_blk > 2) load_k(k2, G.kbase, 2, G.n_cells);
+        if (G.n_blk > 3) load_k(k3, G.kbase, 3, G.n_cells);
     }
     const int n_st = (G.n_blk + 1) / 2;
     int s = (int)(g0 % kAStages);
@@ -677,11 +680,14 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                      ::"r"(su32(&s_tmem)), "r"(ncols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // initial slot fill: slot s takes cell blockIdx.x + s * gridDim.x
+    // initial slot fill: CTA x takes cells x, x + G, .., x + (C - 1) G (C =
+    // the cells per CTA, at most NS): every CTA a spread of radii, and the
+    // cells' K tables adjacent (position x C + s, see k32_pos)
+    const int C = a.kC;
     if (warp >= 2) {
         for (int s = warp - 2; s < NS; s += kGenWarps) {
-            const int c = blockIdx.x + s * gridDim.x;
-            slot_load(a, slots[s], xrows + (size_t)s * XS, s, c < a.t.n_cells ? c : -1);
+            const int c = (int)blockIdx.x + s * (int)gridDim.x;
+            slot_load(a, slots[s], xrows + (size_t)s * XS, s, (s < C && c < a.t.n_cells) ? c : -1);
         }
     }
     tc_fence_before();
@@ -780,17 +786,17 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         const int half = warp >= 6 ? 1 : 0;           // pairs 8 half .. 8 half + 7 of each block
         const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
         const float *xr = xrows + (size_t)slot * XS;
-        const int n_slots_k = n_blk * kBlkPairs;
         uint32_t gphase = 0;
         long long g = 0;
         for (int r = 0;; r++) {
             const int cell = slot < NS ? slots[slot].cell : -1;   // fixed for the whole pass
             const bool active = __any_sync(0xffffffffu, cell >= 0);
-            const float2 *kbase = a.K32 + (size_t)(cell >= 0 ? cell : 0) * n_slots_k + 8 * half;
+            const float4 *kbase = reinterpret_cast<const float4 *>(a.K32) + (size_t)(4 * half) * a.kn +
+                                  k32_pos(cell >= 0 ? cell : 0, (int)gridDim.x, C);
             GenCtx G;
             G.a = &a; G.tmem = tmem; G.lane_base = lane_base; G.kbase = kbase; G.xr = xr;
             G.c_empty = c_empty; G.c_full = c_full; G.s_err = &s_err; G.n_blk = n_blk;
-            G.half = half; G.lane = lane; G.lo_half = lo_half; G.active = active;
+            G.half = half; G.lane = lane; G.lo_half = lo_half; G.active = active; G.n_cells = a.kn;
             const bool ok = gen_pass(G, g);
             g += (n_blk + 1) / 2;                 // stages per pass
             if (!ok) break;
@@ -845,10 +851,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                 __syncwarp();
                 if (fin) {
                     slot_finish(a, loc, sidx);
-                    // refill from the global queue: cells 0 .. grid*NS-1 were the
+                    // refill from the global queue: cells 0 .. grid*C-1 were the
                     // initial fill, later ones go to whichever slot frees first
                     int c = 0;
-                    if (lane == 0) c = (int)gridDim.x * NS + atomicAdd(a.queue, 1);
+                    if (lane == 0) c = (int)gridDim.x * C + atomicAdd(a.queue, 1);
                     c = __shfl_sync(0xffffffffu, c, 0);
                     __syncwarp();
                     if (lane == 0) sl = loc;
@@ -887,7 +893,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     if (threadIdx.x == 0 && s_err) atomicCAS(a.err, 0, s_err);
 }
 
-struct Config { int grid, NS, XS, SB, NBP, nacc; size_t smem; };
+struct Config { int grid, NS, XS, SB, NBP, nacc, C; size_t smem; };
 
 Config mixed_config(int n_cells, int N)
 {
@@ -899,6 +905,7 @@ Config mixed_config(int n_cells, int N)
     // slots); cells are spread over up to one CTA per SM, at least 8 a CTA
     c.grid = std::max(1, std::min(n_sm, (n_cells + 7) / 8));
     c.NS = kSlots;
+    c.C = std::min(kSlots, (n_cells + c.grid - 1) / c.grid);
     const int n16 = ((N + 15) / 16) * 16;
     c.XS = n16 + 4;                              // rows 16 B aligned, 4 words off the bank period
     c.NBP = n16;
@@ -926,6 +933,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     Config cf = mixed_config(c->n_cells, c->N);
     const size_t need = (size_t)cf.grid * cf.NS * 5 * (size_t)c->N * sizeof(double);
     if (need > c->work_bytes) return cudaErrorInvalidValue;
+    if (cf.grid != c->k32_G || cf.C != c->k32_C) return cudaErrorInvalidValue;   // layout of the K tables
     cudaError_t e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(c->d_counter + 1, 0, 2 * sizeof(int), c->stream);
@@ -956,6 +964,8 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.SB = cf.SB;
     a.NBP = cf.NBP;
     a.nacc = cf.nacc;
+    a.kC = c->k32_C;
+    a.kn = c->k32_n;
     a.mode = mode;
     step_mixed_kernel<<<cf.grid, kThreads, cf.smem, c->stream>>>(a);
     return cudaGetLastError();
@@ -988,6 +998,7 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     Config cf = mixed_config(c->n_cells, c->N);
     const size_t need = (size_t)cf.grid * cf.NS * 5 * (size_t)c->N * sizeof(double);
     if (need > kStaticScratchBytes) { *too_big = true; return cudaSuccess; }
+    if (cf.grid != c->k32_G || cf.C != c->k32_C) return cudaErrorInvalidValue;   // layout of the K tables
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -1034,9 +1045,18 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     a.SB = cf.SB;
     a.NBP = cf.NBP;
     a.nacc = cf.nacc;
+    a.kC = c->k32_C;
+    a.kn = c->k32_n;
     a.mode = MODE_STEP;
     step_mixed_kernel<<<cf.grid, kThreads, cf.smem, c->stream>>>(a);
     return cudaGetLastError();
+}
+
+void mixed_layout(int n_cells, int N, int *G, int *C)
+{
+    const Config cf = mixed_config(n_cells, N);
+    *G = cf.grid;
+    *C = cf.C;
 }
 
 size_t mixed_workspace_bytes(int n_cells, int N)
