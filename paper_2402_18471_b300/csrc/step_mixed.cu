@@ -45,7 +45,7 @@ namespace {
 
 constexpr int kGenWarps = 8;
 constexpr int kSlots = 64;                        // cell slots per CTA (TMEM rows / 2)
-constexpr int kAStages = 2;                       // generated-operand stages in TMEM (two blocks, 64 columns each)
+constexpr int kAStages = 3;                       // generated-operand stages in TMEM (two blocks, 64 columns each)
 constexpr int kMaxMain = 8;                       // TMEM accumulators for the products with Bt_hi
 constexpr int kMaxSB = 4;                         // mapping-tile ring depth (stages of two blocks), at most
 constexpr int kThreads = 64 + 32 * kGenWarps;
@@ -114,16 +114,24 @@ __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity)
     return ok != 0;
 }
 // Bounded wait: false when the clock limit runs out or another role failed.
+// Waiting threads back off a little between tests, leaving issue slots to
+// the warps that work (the MMA issuer shares a scheduler with generators).
 __device__ __noinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *s_err, int code)
 {
     const long long t0 = clock64();
     for (int it = 0;; ++it) {
         if (mbar_test(b, parity)) return true;
+        if (it >= 2) __nanosleep(32);
         if ((it & 63) == 63) {
             if (*s_err) return false;
             if (clock64() - t0 > kWaitCycles) { atomicCAS((int *)s_err, 0, code); return false; }
         }
     }
+}
+// Single-thread wait with the common already-complete case inline.
+__device__ __forceinline__ bool twait(uint64_t *b, uint32_t parity, volatile int *s_err, int code)
+{
+    return mbar_test(b, parity) || mbar_wait(b, parity, s_err, code);
 }
 // The same wait, with one answer for the whole warp (all 32 lanes call it).
 __device__ __forceinline__ bool wwait(uint64_t *b, uint32_t parity, volatile int *s_err, int code)
@@ -164,6 +172,12 @@ __device__ __forceinline__ void mma_tf32_ts(uint32_t dt, uint32_t at, uint64_t b
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
                  ::"r"(dt), "r"(at), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+// The same, accumulating into D (enable-input-d given as an immediate).
+__device__ __forceinline__ void mma_tf32_ts_acc(uint32_t dt, uint32_t at, uint64_t b, uint32_t idesc)
+{
+    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;"
+                 ::"r"(dt), "r"(at), "l"(b), "r"(idesc) : "memory");
 }
 // Store 16 consecutive 32-bit columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
@@ -726,56 +740,55 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             if (!ok) break;
         }
     } else if (warp == 1) {
-        // ---- MMA issuer ----
-        const uint32_t idesc = idesc_tf32(2 * kSlots, NBP);
-        long long g = 0;
-        int ms = 0, mc = 0;
-        uint32_t mu = 0, mv = 0;
-        for (int r = 0;; r++) {
-            if (r > 0) {
-                if (!wwait(go, (r - 1) & 1, &s_err, ERR_WAIT_MMA)) break;
-                if (!s_continue) break;
-            }
-            bool ok = true;
-            int ch = 0, ch_next = (n_blk + nacc - 1) / nacc;   // Bt_hi accumulator of the block
-            bool first = true;
-            for (int st = 0; st < n_st; st++, g++) {
-                const int sb = ms, sc = mc;
-                const uint32_t ub = mu, uc = mv;
-                if (++ms == SB) { ms = 0; mu++; }
-                if (++mc == kAStages) { mc = 0; mv++; }
-                if (!wwait(&bt_full[sb], ub & 1, &s_err, ERR_WAIT_MMA) ||
-                    !wwait(&c_full[sc], uc & 1, &s_err, ERR_WAIT_MMA)) { ok = false; break; }
-                tc_fence_after();
-                const int nb = 2 * st + 1 < n_blk ? 2 : 1;
-                for (int q = 0; q < nb; q++) {
-                    const int b = 2 * st + q;
-                    if (b == ch_next) { ch++; ch_next = (int)(((long long)(ch + 1) * n_blk + nacc - 1) / nacc); first = true; }
-                    if (lane == 0) {
+        // ---- MMA issuer: one thread (the tensor pipe's queue is shallow, so
+        // the issuing thread does nothing between MMAs that it can avoid) ----
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(2 * kSlots, NBP);
+            long long g = 0;
+            int ms = 0, mc = 0;
+            uint32_t mu = 0, mv = 0;
+            for (int r = 0;; r++) {
+                if (r > 0) {
+                    if (!twait(go, (r - 1) & 1, &s_err, ERR_WAIT_MMA)) break;
+                    if (!s_continue) break;
+                }
+                bool ok = true;
+                int ch = 0, ch_next = (n_blk + nacc - 1) / nacc;   // Bt_hi accumulator of the block
+                bool first = true;
+                const uint32_t dl = tmem + acol + (uint32_t)(nacc * NBP);
+                for (int st = 0; st < n_st; st++, g++) {
+                    const int sb = ms, sc = mc;
+                    const uint32_t ub = mu, uc = mv;
+                    if (++ms == SB) { ms = 0; mu++; }
+                    if (++mc == kAStages) { mc = 0; mv++; }
+                    if (!twait(&bt_full[sb], ub & 1, &s_err, ERR_WAIT_MMA) ||
+                        !twait(&c_full[sc], uc & 1, &s_err, ERR_WAIT_MMA)) { ok = false; break; }
+                    tc_fence_after();
+                    const int nb = 2 * st + 1 < n_blk ? 2 : 1;
+                    for (int q = 0; q < nb; q++) {
+                        const int b = 2 * st + q;
+                        if (b == ch_next) { ch++; ch_next = (int)(((long long)(ch + 1) * n_blk + nacc - 1) / nacc); first = true; }
                         const uint32_t bt_hi = su32(bring + (size_t)sb * sstride + (size_t)q * bstride);
                         const uint64_t dbh = sw128_desc(bt_hi), dbl = sw128_desc(bt_hi + half_bytes);
                         const uint32_t at = tmem + (uint32_t)(sc * 64 + q * 32);
                         const uint32_t dh = tmem + acol + (uint32_t)(ch * NBP);
-                        const uint32_t dl = tmem + acol + (uint32_t)(nacc * NBP);
                         // the four K steps into one accumulator, then into the other
+                        mma_tf32_ts(dh, at, dbh, idesc, first ? 0u : 1u);
 #pragma unroll
-                        for (int kk = 0; kk < 4; kk++)
-                            mma_tf32_ts(dh, at + 8 * kk, dbh + 2 * kk, idesc, (first && kk == 0) ? 0u : 1u);
+                        for (int kk = 1; kk < 4; kk++) mma_tf32_ts_acc(dh, at + 8 * kk, dbh + 2 * kk, idesc);
+                        mma_tf32_ts(dl, at, dbl, idesc, b == 0 ? 0u : 1u);
 #pragma unroll
-                        for (int kk = 0; kk < 4; kk++)
-                            mma_tf32_ts(dl, at + 8 * kk, dbl + 2 * kk, idesc, (b == 0 && kk == 0) ? 0u : 1u);
+                        for (int kk = 1; kk < 4; kk++) mma_tf32_ts_acc(dl, at + 8 * kk, dbl + 2 * kk, idesc);
+                        first = false;
                     }
-                    first = false;
-                }
-                if (lane == 0) {
                     mma_commit(&bt_empty[sb]);
                     mma_commit(&c_empty[sc]);
                     if (st == n_st - 1) mma_commit(done);
                 }
-                __syncwarp();
+                if (!ok) break;
             }
-            if (!ok) break;
         }
+        __syncwarp();
     } else {
         // ---- generators / per-slot epilogue ----
         const int gt = threadIdx.x - 64;              // 0 .. 255
@@ -910,7 +923,7 @@ Config mixed_config(int n_cells, int N)
     c.XS = n16 + 4;                              // rows 16 B aligned, 4 words off the bank period
     c.NBP = n16;
     // TMEM: 512 columns = generated stages + (nacc + 1) accumulators of NBP
-    c.nacc = std::min(kMaxMain, (512 - kAStages * 64) / n16 - 1);
+    c.nacc = std::max(1, std::min(kMaxMain, (512 - kAStages * 64) / n16 - 1));
     const size_t bstride = 2 * (((2 * (size_t)c.NBP * 128 + 1023) / 1024) * 1024);   // a stage: two blocks
     const size_t tail = (size_t)kSlots * c.XS * 4 + (size_t)kSlots * sizeof(Slot) +
                         8 * (2 * kMaxSB + 2 * kAStages + 4);
