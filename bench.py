@@ -41,9 +41,9 @@ FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
 # from one ncu capture of the named kernel (summaries under profiles/), valid
 # only for the kernel source they were taken on: a changed source reports null.
 MEASURED_TRAFFIC = {
-    "step_mixed_kernel": {"bytes_per_rhs_eval": 29.219291e9 / 635531,
+    "step_mixed_kernel": {"bytes_per_rhs_eval": (37.402032e9 + 0.584335e9) / 635513,
                           "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
-                          "sha256": "ef739ba4ddf640ff14c01ab9605242ae84573605d70c9fb5c5a096a817bc3ed7"},
+                          "sha256": "2044ad254023c14ae876abf5746734f6f224b950806e9eedbb9e71961f8a6bf8"},
 }
 TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 rate ratio
 
