@@ -35,6 +35,7 @@
 // records an error code in the status word and the kernel winds down.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <mutex>
 
@@ -56,7 +57,7 @@ constexpr double B1 = 2.0 / 9.0, B2 = 1.0 / 3.0, B3 = 4.0 / 9.0;
 constexpr double E1 = -5.0 / 72.0, E2 = 1.0 / 12.0, E3 = 1.0 / 9.0, E4 = -1.0 / 8.0;
 
 enum Mode { MODE_STEP = 0, MODE_RHS = 1, MODE_REPLAY = 2 };
-enum ErrCode { ERR_WAIT_PRODUCER = 1, ERR_WAIT_MMA = 2, ERR_WAIT_GEN = 3, ERR_WAIT_EPI = 4 };
+enum ErrCode { ERR_WAIT_PRODUCER = 1, ERR_WAIT_MMA = 2, ERR_WAIT_GEN = 3, ERR_WAIT_EPI = 4, ERR_WAIT_PEER = 5 };
 
 struct MixedArgs {
     DevTables t;
@@ -80,7 +81,8 @@ struct MixedArgs {
     int *rec_status;
     int NS, XS, mode;
     int SB, NBP;                // mapping-tile ring depth; bins padded to 16 (MMA N, tile rows copied)
-    int kC, kn;                 // K table layout: initial cells per CTA, positions (k32_pos)
+    int kC, kn;                 // K table layout: initial cells per group, positions (k32_pos)
+    int paired;                 // 1: a cluster of two CTAs shares each group of slots (see the kernel)
     int nacc;                   // TMEM accumulators for the products with Bt_hi
 };
 
@@ -128,6 +130,66 @@ __device__ __noinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile in
         }
     }
 }
+// ---- cluster (CTA pair) helpers ----
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// shared::cluster address of the same shared location in CTA `rank`
+__device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, float a, float b, float c, float d)
+{
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_s32(uint32_t addr, int v)
+{
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+// arrive on an mbarrier of the peer CTA, releasing this thread's (and, after
+// a __syncwarp, its warp's) prior writes at cluster scope
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_test_cluster(uint64_t *b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded warp-wide wait for data the peer CTA released (acquire at cluster scope).
+__device__ __noinline__ bool cwait(uint64_t *b, uint32_t parity, volatile int *s_err, int code)
+{
+    const long long t0 = clock64();
+    for (int it = 0;; ++it) {
+        if (__all_sync(0xffffffffu, mbar_test_cluster(b, parity))) return true;
+        if (it >= 2) __nanosleep(32);
+        if ((it & 63) == 63) {
+            if (*s_err) return false;
+            if (clock64() - t0 > kWaitCycles) { atomicCAS((int *)s_err, 0, code); return false; }
+        }
+    }
+}
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Single-thread wait with the common already-complete case inline.
 __device__ __forceinline__ bool twait(uint64_t *b, uint32_t parity, volatile int *s_err, int code)
 {
@@ -250,13 +312,16 @@ struct SlotBufs { double *y; float *yx, *k1, *k2, *k3; };
 __device__ __forceinline__ SlotBufs slot_bufs(const MixedArgs &a, int slot)
 {
     const int N = a.t.N;
-    double *base = a.work + ((size_t)blockIdx.x * a.NS + slot) * 5 * (size_t)N;
+    const int grp = a.paired ? (int)blockIdx.x >> 1 : (int)blockIdx.x;
+    double *base = a.work + ((size_t)grp * a.NS + slot) * 5 * (size_t)N;
     float *f = (float *)(base + N);
     return {base, f, f + N, f + 2 * N, f + 3 * N};
 }
 
 // Load cell c into slot: state, scales, phase 0 (or mark the slot empty).
-__device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, int c)
+// owner = false: only the stage-input row and the cell id (a slot whose
+// integrator state the peer CTA of the pair keeps).
+__device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, int c, bool owner = true)
 {
     const int N = a.t.N, lane = threadIdx.x & 31;
     if (c < 0) {
@@ -269,7 +334,7 @@ __device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, i
     double s = 0.0, sa = 0.0;
     for (int k = lane; k < N; k += 32) {
         const double v = rc[k];
-        B.y[k] = v;
+        if (owner) B.y[k] = v;
         s += v;
         sa += fabs(v);
     }
@@ -278,8 +343,8 @@ __device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, i
     const double Sx = sa > 0.0 ? sa : 1.0;
     const double r = 1.0 / Sx;
     for (int k = lane; k < a.XS; k += 32) {
-        const float v = (k < N) ? (float)(B.y[k] * r) : 0.f;
-        if (k < N) B.yx[k] = v;
+        const float v = (k < N) ? (float)(rc[k] * r) : 0.f;
+        if (k < N && owner) B.yx[k] = v;
         xrow[k] = v;
     }
     if (lane == 0) {
@@ -620,28 +685,40 @@ __device__ __forceinline__ bool gen_stage(GenCtx &G, KRegs &ka, KRegs &kb, int s
     return true;
 }
 
-__device__ __forceinline__ bool gen_pass(GenCtx &G, long long g0)
+// Stages st_lo .. st_hi - 1 of a pass (blocks 2 st_lo .. min(n_blk, 2 st_hi) - 1);
+// G.n_blk is the end of that block range.
+__device__ __forceinline__ bool gen_pass(GenCtx &G, long long g0, int st_lo, int st_hi)
 {
-    G.bi = 0;
-    G.bj0 = 0;
+    const int b0 = 2 * st_lo;
+    G.bi = __ldg(G.a->t.blk_i + b0);
+    G.bj0 = __ldg(G.a->t.blk_j0 + b0);
     KRegs k0, k1, k2, k3;
     if (G.active) {
-        load_k(k0, G.kbase, 0, G.n_cells);
-        if (G.n_blk > 1) load_k(k1, G.kbase, 1, G.n_cells);
-        if (G.n_blk > 2) load_k(k2, G.kbase, 2, G.n_cells);
-        if (G.n_blk > 3) load_k(k3, G.kbase, 3, G.n_cells);
+        load_k(k0, G.kbase, b0, G.n_cells);
+        if (b0 + 1 < G.n_blk) load_k(k1, G.kbase, b0 + 1, G.n_cells);
+        if (b0 + 2 < G.n_blk) load_k(k2, G.kbase, b0 + 2, G.n_cells);
+        if (b0 + 3 < G.n_blk) load_k(k3, G.kbase, b0 + 3, G.n_cells);
     }
-    const int n_st = (G.n_blk + 1) / 2;
     int s = (int)(g0 % kAStages);
     uint32_t u = (uint32_t)(g0 / kAStages);
-    for (int st = 0; st < n_st; st += 2) {
-        const long long g = g0 + st;
-        if (!gen_stage(G, k0, k1, st, g, s, u) || !gen_stage(G, k2, k3, st + 1, g + 1, s, u)) return false;
+    for (int st = st_lo; st < st_hi; st += 2) {
+        const long long g = g0 + (st - st_lo);
+        if (!gen_stage(G, k0, k1, st, g, s, u)) return false;
+        if (st + 1 < st_hi && !gen_stage(G, k2, k3, st + 1, g + 1, s, u)) return false;
     }
     return true;
 }
 
 // ---- the kernel --------------------------------------------------------------
+//
+// Paired mode (a.paired): each group of 64 slots is served by a cluster of two
+// CTAs.  Both hold the stage inputs of all 64 slots and each streams half of
+// the stages of a pass (its tensor-core work halves); CTA r keeps the
+// integrator state of slots 32 r .. 32 r + 31.  After its MMAs a CTA sends
+// the partial sums of the peer's slots into the peer's shared memory; after
+// the per-slot logic it sends its slots' new stage inputs and cells.  Each
+// exchange is one remote mbarrier arrival (release/acquire at cluster scope).
+// Single mode: one CTA per group, all stages, all slots.
 
 __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
 {
@@ -649,25 +726,39 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int NS = a.NS, XS = a.XS, N = a.t.N, n_blk = a.t.n_blk, NBP = a.NBP;
     const int SB = a.SB;
+    const bool paired = a.paired != 0;
+    const int rank = paired ? (int)cluster_rank() : 0;
+    const int peer = rank ^ 1;
+    const int ngrp = paired ? (int)gridDim.x >> 1 : (int)gridDim.x;
+    const int grp = paired ? (int)blockIdx.x >> 1 : (int)blockIdx.x;
+    const int SL = paired ? NS / 2 : NS;                // slots whose state this CTA keeps
+    const int own0 = paired ? rank * SL : 0;
     const int half_bytes = NBP * 128;                   // rows of one Bt tile copied
     const int bstride = ((2 * half_bytes + 1023) / 1024) * 1024;   // hi then lo, 1024-aligned
     const int sstride = 2 * bstride;                    // one stage: two blocks
     const int n_st = (n_blk + 1) / 2;                   // stages per pass
+    const int st_h = (n_st + 1) / 2;
+    const int st_lo = paired ? (rank ? st_h : 0) : 0;
+    const int st_hi = paired ? (rank ? n_st : st_h) : n_st;
+    const int my_st = st_hi - st_lo;                    // >= 1 (paired mode needs n_st >= 2)
+    const int b_lo = 2 * st_lo, b_hi = min(n_blk, 2 * st_hi);
     uint8_t *bring = sm;                                // mapping tiles (also the D staging area)
     float *xrows = (float *)(bring + (size_t)SB * sstride);
-    Slot *slots = (Slot *)(xrows + (size_t)NS * XS);
+    float *dpeer = xrows + (size_t)NS * XS;             // [2][SL][NBP] partial sums from the peer
+    Slot *slots = (Slot *)(dpeer + (paired ? (size_t)2 * SL * NBP : 0));
     uint64_t *bars = (uint64_t *)(slots + NS);
     uint64_t *bt_full = bars, *bt_empty = bars + SB;
     uint64_t *c_full = bars + 2 * SB, *c_empty = bars + 2 * SB + kAStages;
     uint64_t *done = bars + 2 * SB + 2 * kAStages, *go = done + 1, *gbar = done + 2, *fin = done + 3;
+    uint64_t *dx_full = done + 4, *xg_full = done + 5;
     __shared__ uint32_t s_tmem;
     __shared__ int s_err, s_continue;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // TMEM columns: kAStages x 64 for the generated operand, then nacc
-    // accumulators for [A_hi; A_lo] x Bt_hi (each a contiguous share of the
-    // blocks, summed in the epilogue with a compensated FP32 sum) and one for
-    // [A_hi; A_lo] x Bt_lo, NBP columns each.
-    const int nacc = a.nacc < n_blk ? a.nacc : n_blk;   // every accumulator gets a block
+    // accumulators for [A_hi; A_lo] x Bt_hi (each a contiguous share of this
+    // CTA's blocks, summed in the epilogue with a compensated FP32 sum) and
+    // one for [A_hi; A_lo] x Bt_lo, NBP columns each.
+    const int nacc = a.nacc < b_hi - b_lo ? a.nacc : b_hi - b_lo;   // every accumulator gets a block
     const uint32_t acol = kAStages * 64;
     const int tcols = (int)acol + (nacc + 1) * NBP;
     const uint32_t ncols = tcols <= 32 ? 32 : tcols <= 64 ? 64 : tcols <= 128 ? 128 : tcols <= 256 ? 256 : 512;
@@ -685,6 +776,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         mbar_init(go, 1);
         mbar_init(gbar, 32 * kGenWarps);
         mbar_init(fin, 1);
+        mbar_init(dx_full, kGenWarps / 2);          // the peer's warps that hold my slots' rows
+        mbar_init(xg_full, kGenWarps);              // every peer generator warp
         s_err = 0;
         s_continue = 1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -694,18 +787,22 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                      ::"r"(su32(&s_tmem)), "r"(ncols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // initial slot fill: CTA x takes cells x, x + G, .., x + (C - 1) G (C =
-    // the cells per CTA, at most NS): every CTA a spread of radii, and the
-    // cells' K tables adjacent (position x C + s, see k32_pos)
+    // initial slot fill: group x takes cells x, x + G, .., x + (C - 1) G (C =
+    // the cells per group, at most NS): every group a spread of radii, and the
+    // cells' K tables adjacent (position x C + s, see k32_pos).  Both CTAs of a
+    // pair set up the stage inputs of all 64 slots; the state of each slot is
+    // kept by one of them.
     const int C = a.kC;
     if (warp >= 2) {
         for (int s = warp - 2; s < NS; s += kGenWarps) {
-            const int c = (int)blockIdx.x + s * (int)gridDim.x;
-            slot_load(a, slots[s], xrows + (size_t)s * XS, s, (s < C && c < a.t.n_cells) ? c : -1);
+            const int c = grp + s * ngrp;
+            slot_load(a, slots[s], xrows + (size_t)s * XS, s, (s < C && c < a.t.n_cells) ? c : -1,
+                      s >= own0 && s < own0 + SL);
         }
     }
     tc_fence_before();
     __syncthreads();
+    if (paired) cluster_sync_all();                   // the peer's barriers exist before any remote arrival
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
@@ -720,7 +817,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                 if (!s_continue) break;
             }
             bool ok = true;
-            for (int st = 0; st < n_st; st++, g++) {
+            for (int st = st_lo; st < st_hi; st++, g++) {
                 const int s = ps;
                 const uint32_t u = pu;
                 if (++ps == SB) { ps = 0; pu++; }      // ring position without divisions
@@ -744,6 +841,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         // the issuing thread does nothing between MMAs that it can avoid) ----
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(2 * kSlots, NBP);
+            const int nb_mine = b_hi - b_lo;
             long long g = 0;
             int ms = 0, mc = 0;
             uint32_t mu = 0, mv = 0;
@@ -753,10 +851,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     if (!s_continue) break;
                 }
                 bool ok = true;
-                int ch = 0, ch_next = (n_blk + nacc - 1) / nacc;   // Bt_hi accumulator of the block
+                int ch = 0, ch_next = (nb_mine + nacc - 1) / nacc;   // Bt_hi accumulator of the block
                 bool first = true;
                 const uint32_t dl = tmem + acol + (uint32_t)(nacc * NBP);
-                for (int st = 0; st < n_st; st++, g++) {
+                for (int st = st_lo; st < st_hi; st++, g++) {
                     const int sb = ms, sc = mc;
                     const uint32_t ub = mu, uc = mv;
                     if (++ms == SB) { ms = 0; mu++; }
@@ -766,8 +864,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     tc_fence_after();
                     const int nb = 2 * st + 1 < n_blk ? 2 : 1;
                     for (int q = 0; q < nb; q++) {
-                        const int b = 2 * st + q;
-                        if (b == ch_next) { ch++; ch_next = (int)(((long long)(ch + 1) * n_blk + nacc - 1) / nacc); first = true; }
+                        const int bl = 2 * st + q - b_lo;     // block index within this CTA's range
+                        if (bl == ch_next) { ch++; ch_next = (int)(((long long)(ch + 1) * nb_mine + nacc - 1) / nacc); first = true; }
                         const uint32_t bt_hi = su32(bring + (size_t)sb * sstride + (size_t)q * bstride);
                         const uint64_t dbh = sw128_desc(bt_hi), dbl = sw128_desc(bt_hi + half_bytes);
                         const uint32_t at = tmem + (uint32_t)(sc * 64 + q * 32);
@@ -776,14 +874,14 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                         mma_tf32_ts(dh, at, dbh, idesc, first ? 0u : 1u);
 #pragma unroll
                         for (int kk = 1; kk < 4; kk++) mma_tf32_ts_acc(dh, at + 8 * kk, dbh + 2 * kk, idesc);
-                        mma_tf32_ts(dl, at, dbl, idesc, b == 0 ? 0u : 1u);
+                        mma_tf32_ts(dl, at, dbl, idesc, bl == 0 ? 0u : 1u);
 #pragma unroll
                         for (int kk = 1; kk < 4; kk++) mma_tf32_ts_acc(dl, at + 8 * kk, dbl + 2 * kk, idesc);
                         first = false;
                     }
                     mma_commit(&bt_empty[sb]);
                     mma_commit(&c_empty[sc]);
-                    if (st == n_st - 1) mma_commit(done);
+                    if (st == st_hi - 1) mma_commit(done);
                 }
                 if (!ok) break;
             }
@@ -796,87 +894,122 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         const int row = 32 * qd + lane;               // TMEM row: slot (row & 63), hi or lo part
         const int slot = row & (kSlots - 1);
         const bool lo_half = row >= kSlots;
+        const int part = lo_half ? 1 : 0;
         const int half = warp >= 6 ? 1 : 0;           // pairs 8 half .. 8 half + 7 of each block
         const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
         const float *xr = xrows + (size_t)slot * XS;
+        // this warp's rows belong to slots kept here, or by the peer CTA
+        const bool rows_own = slot >= own0 && slot < own0 + SL;
+        float *Dsm = (float *)bring;                  // [2][SL][NBP]; the mapping-tile ring is idle then
+        const uint32_t dpeer_remote = paired ? mapa(su32(dpeer), (uint32_t)peer) : 0;
+        const uint32_t xrows_remote = paired ? mapa(su32(xrows), (uint32_t)peer) : 0;
+        const uint32_t slots_remote = paired ? mapa(su32(slots), (uint32_t)peer) : 0;
+        const uint32_t dx_remote = paired ? mapa(su32(dx_full), (uint32_t)peer) : 0;
+        const uint32_t xg_remote = paired ? mapa(su32(xg_full), (uint32_t)peer) : 0;
         uint32_t gphase = 0;
         long long g = 0;
         for (int r = 0;; r++) {
-            const int cell = slot < NS ? slots[slot].cell : -1;   // fixed for the whole pass
+            const int cell = slots[slot].cell;        // fixed for the whole pass
             const bool active = __any_sync(0xffffffffu, cell >= 0);
             const float4 *kbase = reinterpret_cast<const float4 *>(a.K32) + (size_t)(4 * half) * a.kn +
-                                  k32_pos(cell >= 0 ? cell : 0, (int)gridDim.x, C);
+                                  k32_pos(cell >= 0 ? cell : 0, ngrp, C);
             GenCtx G;
             G.a = &a; G.tmem = tmem; G.lane_base = lane_base; G.kbase = kbase; G.xr = xr;
-            G.c_empty = c_empty; G.c_full = c_full; G.s_err = &s_err; G.n_blk = n_blk;
+            G.c_empty = c_empty; G.c_full = c_full; G.s_err = &s_err; G.n_blk = b_hi;
             G.half = half; G.lane = lane; G.lo_half = lo_half; G.active = active; G.n_cells = a.kn;
-            const bool ok = gen_pass(G, g);
-            g += (n_blk + 1) / 2;                 // stages per pass
+            const bool ok = gen_pass(G, g, st_lo, st_hi);
+            g += my_st;
             if (!ok) break;
-            // ---- epilogue: D (TMEM) -> smem [slot][bin] ----
+            // ---- epilogue: D (TMEM) -> [part][slot][bin], here or in the peer ----
             if (!wwait(done, r & 1, &s_err, ERR_WAIT_EPI)) break;
             tc_fence_after();
-            float *Dsm = (float *)bring;                  // the mapping-tile ring is idle now
-            const int DS = N;
-            // rows 0..63 (hi parts) write their sums, rows 64..127 (lo parts) add theirs
-            for (int ph = 0; ph < 2; ph++) {
-                if ((qd >= 2) == (ph == 1)) {
-                    const int c0 = half * (NBP / 2), c1 = c0 + NBP / 2;
-                    for (int cc = c0; cc < c1; cc += 8) {
-                        // compensated (Neumaier) FP32 sum of the accumulators
-                        float sum[8], cmp[8];
+            {
+                const int sl = slot - (rows_own ? own0 : (paired ? peer * SL : 0));
+                const int c0 = half * (NBP / 2), c1 = c0 + NBP / 2;
+                for (int cc = c0; cc < c1; cc += 8) {
+                    // compensated (Neumaier) FP32 sum of the accumulators
+                    float sum[8], cmp[8];
 #pragma unroll
-                        for (int z = 0; z < 8; z++) { sum[z] = 0.f; cmp[z] = 0.f; }
-                        for (int ch = 0; ch <= nacc; ch++) {
-                            float v[8];
-                            tmem_ld8(tmem + lane_base + acol + (uint32_t)(ch * NBP + cc), v);
+                    for (int z = 0; z < 8; z++) { sum[z] = 0.f; cmp[z] = 0.f; }
+                    for (int ch = 0; ch <= nacc; ch++) {
+                        float v[8];
+                        tmem_ld8(tmem + lane_base + acol + (uint32_t)(ch * NBP + cc), v);
 #pragma unroll
-                            for (int z = 0; z < 8; z++) {
-                                const float t = sum[z] + v[z];
-                                cmp[z] += (fabsf(sum[z]) >= fabsf(v[z])) ? (sum[z] - t) + v[z] : (v[z] - t) + sum[z];
-                                sum[z] = t;
-                            }
-                        }
-                        if (slot < NS) {
-#pragma unroll
-                            for (int z = 0; z < 8; z++) {
-                                const int bin = cc + z;
-                                if (bin < N) {
-                                    float *dp = Dsm + (size_t)slot * DS + bin;
-                                    *dp = ph == 0 ? sum[z] + cmp[z] : *dp + (sum[z] + cmp[z]);
-                                }
-                            }
+                        for (int z = 0; z < 8; z++) {
+                            const float t = sum[z] + v[z];
+                            cmp[z] += (fabsf(sum[z]) >= fabsf(v[z])) ? (sum[z] - t) + v[z] : (v[z] - t) + sum[z];
+                            sum[z] = t;
                         }
                     }
+                    float o[8];
+#pragma unroll
+                    for (int z = 0; z < 8; z++) o[z] = sum[z] + cmp[z];
+                    const size_t off = ((size_t)part * SL + sl) * NBP + cc;   // floats
+                    if (rows_own) {
+                        *(float4 *)(Dsm + off) = make_float4(o[0], o[1], o[2], o[3]);
+                        *(float4 *)(Dsm + off + 4) = make_float4(o[4], o[5], o[6], o[7]);
+                    } else {
+                        st_cluster_v4(dpeer_remote + (uint32_t)(off * 4), o[0], o[1], o[2], o[3]);
+                        st_cluster_v4(dpeer_remote + (uint32_t)(off * 4 + 16), o[4], o[5], o[6], o[7]);
+                    }
                 }
-                if (ph == 0 && !gen_sync(gbar, gphase, &s_err)) { r = -1; break; }
+                if (paired && !rows_own) {
+                    fence_cluster();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_remote(dx_remote);
+                }
             }
-            if (r < 0) break;
             tc_fence_before();
+            if (paired && !cwait(dx_full, r & 1, &s_err, ERR_WAIT_PEER)) break;
             if (!gen_sync(gbar, gphase, &s_err)) break;
-            // ---- per-slot integrator logic ----
-            for (int sidx = warp - 2; sidx < NS; sidx += kGenWarps) {
-                Slot &sl = slots[sidx];
-                if (sl.cell < 0) continue;
-                Slot loc = sl;
-                __syncwarp();
-                bool fin = slot_advance(a, loc, xrows + (size_t)sidx * XS, Dsm + (size_t)sidx * DS, sidx);
-                __syncwarp();
-                if (fin) {
-                    slot_finish(a, loc, sidx);
-                    // refill from the global queue: cells 0 .. grid*C-1 were the
-                    // initial fill, later ones go to whichever slot frees first
-                    int c = 0;
-                    if (lane == 0) c = (int)gridDim.x * C + atomicAdd(a.queue, 1);
-                    c = __shfl_sync(0xffffffffu, c, 0);
-                    __syncwarp();
-                    if (lane == 0) sl = loc;
-                    __syncwarp();
-                    slot_load(a, sl, xrows + (size_t)sidx * XS, sidx, c < a.t.n_cells ? c : -1);
-                } else if (lane == 0) {
-                    sl = loc;
+            // ---- per-slot integrator logic for the slots kept here ----
+            for (int sl = warp - 2; sl < SL; sl += kGenWarps) {
+                const int sidx = own0 + sl;
+                Slot &slr = slots[sidx];
+                // D = sum of the parts (hi rows, lo rows; here and from the peer)
+                float *Drow = Dsm + (size_t)sl * NBP;
+                for (int k = lane; k < N; k += 32) {
+                    float v = Drow[k] + Dsm[((size_t)SL + sl) * NBP + k];
+                    if (paired) v += dpeer[(size_t)sl * NBP + k] + dpeer[((size_t)SL + sl) * NBP + k];
+                    Drow[k] = v;
                 }
                 __syncwarp();
+                if (slr.cell >= 0) {
+                    Slot loc = slr;
+                    __syncwarp();
+                    bool fin = slot_advance(a, loc, xrows + (size_t)sidx * XS, Drow, sidx);
+                    __syncwarp();
+                    if (fin) {
+                        slot_finish(a, loc, sidx);
+                        // refill from the global queue: cells 0 .. G*C-1 were the
+                        // initial fill, later ones go to whichever slot frees first
+                        int c = 0;
+                        if (lane == 0) c = ngrp * C + atomicAdd(a.queue, 1);
+                        c = __shfl_sync(0xffffffffu, c, 0);
+                        __syncwarp();
+                        if (lane == 0) slr = loc;
+                        __syncwarp();
+                        slot_load(a, slr, xrows + (size_t)sidx * XS, sidx, c < a.t.n_cells ? c : -1);
+                    } else if (lane == 0) {
+                        slr = loc;
+                    }
+                    __syncwarp();
+                }
+                if (paired) {
+                    // the slot's stage input and cell, to the peer
+                    const float *xs = xrows + (size_t)sidx * XS;
+                    const uint32_t xdst = xrows_remote + (uint32_t)((size_t)sidx * XS * 4);
+                    for (int k = lane; k < N; k += 32) st_cluster_f32(xdst + 4 * k, xs[k]);
+                    if (lane == 0)
+                        st_cluster_s32(slots_remote + (uint32_t)((size_t)sidx * sizeof(Slot) + offsetof(Slot, cell)),
+                                       slr.cell);
+                }
+            }
+            if (paired) {
+                fence_cluster();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_remote(xg_remote);
+                if (!cwait(xg_full, r & 1, &s_err, ERR_WAIT_PEER)) break;
             }
             // generic-proxy writes to the stage memory (D staging) must be
             // ordered before the bulk copies of the next pass overwrite it
@@ -904,9 +1037,11 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
     }
     if (threadIdx.x == 0 && s_err) atomicCAS(a.err, 0, s_err);
+    // neither CTA of a pair leaves while the other may still write to it
+    if (paired) cluster_sync_all();
 }
 
-struct Config { int grid, NS, XS, SB, NBP, nacc, C; size_t smem; };
+struct Config { int grid, groups, paired, NS, XS, SB, NBP, nacc, C; size_t smem; };
 
 Config mixed_config(int n_cells, int N)
 {
@@ -914,29 +1049,59 @@ Config mixed_config(int n_cells, int N)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     Config c;
-    // 64 slots per CTA (the MMA's 128 rows are the hi and lo parts of 64
-    // slots); cells are spread over up to one CTA per SM, at least 8 a CTA
-    c.grid = std::max(1, std::min(n_sm, (n_cells + 7) / 8));
     c.NS = kSlots;
-    c.C = std::min(kSlots, (n_cells + c.grid - 1) / c.grid);
     const int n16 = ((N + 15) / 16) * 16;
     c.XS = n16 + 4;                              // rows 16 B aligned, 4 words off the bank period
     c.NBP = n16;
     // TMEM: 512 columns = generated stages + (nacc + 1) accumulators of NBP
     c.nacc = std::max(1, std::min(kMaxMain, (512 - kAStages * 64) / n16 - 1));
-    const size_t bstride = 2 * (((2 * (size_t)c.NBP * 128 + 1023) / 1024) * 1024);   // a stage: two blocks
+    int n_blk = 0;
+    for (int i = 0; i < N; i++) n_blk += (i + kBlkPairs) / kBlkPairs;
+    const int n_st = (n_blk + 1) / 2;
+    const size_t sstride = 2 * (((2 * (size_t)c.NBP * 128 + 1023) / 1024) * 1024);   // a stage: two blocks
     const size_t tail = (size_t)kSlots * c.XS * 4 + (size_t)kSlots * sizeof(Slot) +
-                        8 * (2 * kMaxSB + 2 * kAStages + 4);
+                        8 * (2 * kMaxSB + 2 * kAStages + 6);
     const size_t budget = 232448 - 1024 - 2048;  // opt-in shared memory, alignment, static
-    int SB = (int)((budget - tail) / bstride);
+    // paired (two CTAs per group of slots) when two mapping-tile stages fit
+    // next to the buffer for the peer's partial sums, and there are two
+    // stages to share out
+    const size_t dpeer = (size_t)2 * (kSlots / 2) * c.NBP * 4;
+    const int sb_paired = (int)((budget - tail - dpeer) / sstride);
+    c.paired = (sb_paired >= 2 && n_st >= 2) ? 1 : 0;
+    const int SL = c.paired ? kSlots / 2 : kSlots;
+    int SB = c.paired ? sb_paired : (int)((budget - tail) / sstride);
     SB = std::min(SB, kMaxSB);
-    // the D staging area (slots x N floats) aliases the mapping-tile ring
-    while ((size_t)SB * bstride < (size_t)kSlots * N * 4 && SB < kMaxSB) SB++;
+    // the D staging area ([2][slots kept][NBP] floats) aliases the mapping-tile ring
+    while ((size_t)SB * sstride < (size_t)2 * SL * c.NBP * 4 && SB < kMaxSB) SB++;
     c.SB = SB;
     // at least 120 KB, so that no two CTAs share an SM (each holds all 512
     // TMEM columns for the whole kernel)
-    c.smem = std::max((size_t)120 * 1024, 1024 + (size_t)SB * bstride + tail);
+    c.smem = std::max((size_t)120 * 1024, 1024 + (size_t)SB * sstride + tail + (c.paired ? dpeer : 0));
+    // cells are spread over up to one CTA (pair) per SM (pair of SMs), at least 8 a group
+    const int max_groups = c.paired ? n_sm / 2 : n_sm;
+    c.groups = std::max(1, std::min(max_groups, (n_cells + 7) / 8));
+    c.grid = c.paired ? 2 * c.groups : c.groups;
+    c.C = std::min(kSlots, (n_cells + c.groups - 1) / c.groups);
     return c;
+}
+
+cudaError_t launch_kernel(const Config &cf, const MixedArgs &a, cudaStream_t stream)
+{
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cf.grid);
+    lc.blockDim = dim3(kThreads);
+    lc.dynamicSmemBytes = cf.smem;
+    lc.stream = stream;
+    cudaLaunchAttribute at[1];
+    if (cf.paired) {
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&lc, step_mixed_kernel, a);
 }
 
 cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double *drho, double t_span,
@@ -944,9 +1109,9 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
                          long long replay_stride)
 {
     Config cf = mixed_config(c->n_cells, c->N);
-    const size_t need = (size_t)cf.grid * cf.NS * 5 * (size_t)c->N * sizeof(double);
+    const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(double);
     if (need > c->work_bytes) return cudaErrorInvalidValue;
-    if (cf.grid != c->k32_G || cf.C != c->k32_C) return cudaErrorInvalidValue;   // layout of the K tables
+    if (cf.groups != c->k32_G || cf.C != c->k32_C) return cudaErrorInvalidValue;   // layout of the K tables
     cudaError_t e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(c->d_counter + 1, 0, 2 * sizeof(int), c->stream);
@@ -979,9 +1144,9 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.nacc = cf.nacc;
     a.kC = c->k32_C;
     a.kn = c->k32_n;
+    a.paired = cf.paired;
     a.mode = mode;
-    step_mixed_kernel<<<cf.grid, kThreads, cf.smem, c->stream>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(cf, a, c->stream);
 }
 
 } // namespace
@@ -1009,9 +1174,9 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
 {
     *too_big = false;
     Config cf = mixed_config(c->n_cells, c->N);
-    const size_t need = (size_t)cf.grid * cf.NS * 5 * (size_t)c->N * sizeof(double);
+    const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(double);
     if (need > kStaticScratchBytes) { *too_big = true; return cudaSuccess; }
-    if (cf.grid != c->k32_G || cf.C != c->k32_C) return cudaErrorInvalidValue;   // layout of the K tables
+    if (cf.groups != c->k32_G || cf.C != c->k32_C) return cudaErrorInvalidValue;   // layout of the K tables
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -1060,22 +1225,22 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     a.nacc = cf.nacc;
     a.kC = c->k32_C;
     a.kn = c->k32_n;
+    a.paired = cf.paired;
     a.mode = MODE_STEP;
-    step_mixed_kernel<<<cf.grid, kThreads, cf.smem, c->stream>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(cf, a, c->stream);
 }
 
 void mixed_layout(int n_cells, int N, int *G, int *C)
 {
     const Config cf = mixed_config(n_cells, N);
-    *G = cf.grid;
+    *G = cf.groups;
     *C = cf.C;
 }
 
 size_t mixed_workspace_bytes(int n_cells, int N)
 {
     Config cf = mixed_config(n_cells, N);
-    return (size_t)cf.grid * cf.NS * 5 * (size_t)N * sizeof(double);
+    return (size_t)cf.groups * cf.NS * 5 * (size_t)N * sizeof(double);
 }
 
 cudaError_t launch_rhs_mixed(const cudisc_coag_ctx *c, const double *rho, double *drho)
