@@ -22,8 +22,13 @@
 //   step two MMAs: [A_hi; A_lo] x Bt_hi into one of several FP32
 //   accumulators (a contiguous share of the blocks each) and [A_hi; A_lo] x
 //   Bt_lo into one more; the four split products hi.hi, lo.hi, hi.lo and
-//   lo.lo are the four row-halves of the two accumulators.  Only the Bt
-//   tiles pass through shared memory, once each way.
+//   lo.lo are the four row-halves of the two accumulators.  Up to 128 bins
+//   the two products are one MMA of N = 2 NBP: the Bt_lo tile follows the
+//   Bt_hi tile in shared memory, so [Bt_hi; Bt_lo] is one B operand, and each
+//   accumulator holds both products side by side (half as many
+//   instructions, each twice as long, keep the tensor pipe's short queue
+//   full through the issuer's barrier checks).  Only the Bt tiles pass
+//   through shared memory, once each way.
 // Warp roles: warp 0 bulk-copy producer, warp 1 MMA issuer and TMEM owner,
 // warps 2..9 generate A (two warps per TMEM lane quadrant, one per half of a
 // block's pairs) and, between right-hand sides, run the per-slot logic: the
@@ -83,7 +88,8 @@ struct MixedArgs {
     int SB, NBP;                // mapping-tile ring depth; bins padded to 16 (MMA N, tile rows copied)
     int kC, kn;                 // K table layout: initial cells per group, positions (k32_pos)
     int paired;                 // 1: a cluster of two CTAs shares each group of slots (see the kernel)
-    int nacc;                   // TMEM accumulators for the products with Bt_hi
+    int nacc;                   // TMEM accumulators for the products with Bt_hi (stacked: with [Bt_hi; Bt_lo])
+    int stacked;                // 1: one MMA of N = 2 NBP takes Bt_hi and Bt_lo together (2 NBP <= 256)
 };
 
 struct __align__(16) Slot {
@@ -757,10 +763,14 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     // TMEM columns: kAStages x 64 for the generated operand, then nacc
     // accumulators for [A_hi; A_lo] x Bt_hi (each a contiguous share of this
     // CTA's blocks, summed in the epilogue with a compensated FP32 sum) and
-    // one for [A_hi; A_lo] x Bt_lo, NBP columns each.
+    // one for [A_hi; A_lo] x Bt_lo, NBP columns each; stacked, nacc
+    // accumulators of 2 NBP columns for [A_hi; A_lo] x [Bt_hi; Bt_lo].  Either
+    // way the epilogue sums nreg regions of NBP columns.
+    const bool stacked = a.stacked != 0;
     const int nacc = a.nacc < b_hi - b_lo ? a.nacc : b_hi - b_lo;   // every accumulator gets a block
+    const int nreg = stacked ? 2 * nacc : nacc + 1;
     const uint32_t acol = kAStages * 64;
-    const int tcols = (int)acol + (nacc + 1) * NBP;
+    const int tcols = (int)acol + nreg * NBP;
     const uint32_t ncols = tcols <= 32 ? 32 : tcols <= 64 ? 64 : tcols <= 128 ? 128 : tcols <= 256 ? 256 : 512;
 
     if (threadIdx.x == 0) {
@@ -840,7 +850,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         // ---- MMA issuer: one thread (the tensor pipe's queue is shallow, so
         // the issuing thread does nothing between MMAs that it can avoid) ----
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(2 * kSlots, NBP);
+            const uint32_t idesc = idesc_tf32(2 * kSlots, stacked ? 2 * NBP : NBP);
             const int nb_mine = b_hi - b_lo;
             long long g = 0;
             int ms = 0, mc = 0;
@@ -869,14 +879,17 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                         const uint32_t bt_hi = su32(bring + (size_t)sb * sstride + (size_t)q * bstride);
                         const uint64_t dbh = sw128_desc(bt_hi), dbl = sw128_desc(bt_hi + half_bytes);
                         const uint32_t at = tmem + (uint32_t)(sc * 64 + q * 32);
-                        const uint32_t dh = tmem + acol + (uint32_t)(ch * NBP);
-                        // the four K steps into one accumulator, then into the other
+                        const uint32_t dh = tmem + acol + (uint32_t)(ch * (stacked ? 2 * NBP : NBP));
+                        // the four K steps into one accumulator (stacked: both
+                        // products at once), else then into the Bt_lo one
                         mma_tf32_ts(dh, at, dbh, idesc, first ? 0u : 1u);
 #pragma unroll
                         for (int kk = 1; kk < 4; kk++) mma_tf32_ts_acc(dh, at + 8 * kk, dbh + 2 * kk, idesc);
-                        mma_tf32_ts(dl, at, dbl, idesc, bl == 0 ? 0u : 1u);
+                        if (!stacked) {
+                            mma_tf32_ts(dl, at, dbl, idesc, bl == 0 ? 0u : 1u);
 #pragma unroll
-                        for (int kk = 1; kk < 4; kk++) mma_tf32_ts_acc(dl, at + 8 * kk, dbl + 2 * kk, idesc);
+                            for (int kk = 1; kk < 4; kk++) mma_tf32_ts_acc(dl, at + 8 * kk, dbl + 2 * kk, idesc);
+                        }
                         first = false;
                     }
                     mma_commit(&bt_empty[sb]);
@@ -931,7 +944,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     float sum[8], cmp[8];
 #pragma unroll
                     for (int z = 0; z < 8; z++) { sum[z] = 0.f; cmp[z] = 0.f; }
-                    for (int ch = 0; ch <= nacc; ch++) {
+                    for (int ch = 0; ch < nreg; ch++) {
                         float v[8];
                         tmem_ld8(tmem + lane_base + acol + (uint32_t)(ch * NBP + cc), v);
 #pragma unroll
@@ -1041,7 +1054,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     if (paired) cluster_sync_all();
 }
 
-struct Config { int grid, groups, paired, NS, XS, SB, NBP, nacc, C; size_t smem; };
+struct Config { int grid, groups, paired, NS, XS, SB, NBP, nacc, stacked, C; size_t smem; };
 
 Config mixed_config(int n_cells, int N)
 {
@@ -1053,8 +1066,11 @@ Config mixed_config(int n_cells, int N)
     const int n16 = ((N + 15) / 16) * 16;
     c.XS = n16 + 4;                              // rows 16 B aligned, 4 words off the bank period
     c.NBP = n16;
-    // TMEM: 512 columns = generated stages + (nacc + 1) accumulators of NBP
-    c.nacc = std::max(1, std::min(kMaxMain, (512 - kAStages * 64) / n16 - 1));
+    // TMEM: 512 columns = generated stages + (nacc + 1) accumulators of NBP,
+    // or stacked (MMA N = 2 NBP at most 256) nacc accumulators of 2 NBP
+    c.stacked = 2 * n16 <= 256 ? 1 : 0;
+    c.nacc = c.stacked ? std::max(1, std::min(kMaxMain, (512 - kAStages * 64) / (2 * n16)))
+                       : std::max(1, std::min(kMaxMain, (512 - kAStages * 64) / n16 - 1));
     int n_blk = 0;
     for (int i = 0; i < N; i++) n_blk += (i + kBlkPairs) / kBlkPairs;
     const int n_st = (n_blk + 1) / 2;
@@ -1142,6 +1158,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.SB = cf.SB;
     a.NBP = cf.NBP;
     a.nacc = cf.nacc;
+    a.stacked = cf.stacked;
     a.kC = c->k32_C;
     a.kn = c->k32_n;
     a.paired = cf.paired;
@@ -1223,6 +1240,7 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     a.SB = cf.SB;
     a.NBP = cf.NBP;
     a.nacc = cf.nacc;
+    a.stacked = cf.stacked;
     a.kC = c->k32_C;
     a.kn = c->k32_n;
     a.paired = cf.paired;
