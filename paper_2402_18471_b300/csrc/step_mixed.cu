@@ -72,6 +72,7 @@ struct MixedArgs {
     double t_span;
     double *dt_cell;
     double rtol, atol_rel;
+    float rtol_f;
     long long max_steps;
     const double *replay_h;
     const long long *replay_n;
@@ -93,8 +94,9 @@ struct MixedArgs {
 };
 
 struct __align__(16) Slot {
-    double t, h, hs, S, Sx, atol;
+    double t, h, hs, S, Sx;
     long long nacc, nrej, nrep;
+    float sxf, atolx, hsf;             // Sx, atol / Sx and hs in FP32 for the per-bin work
     int cell, phase, last, status;
 };
 
@@ -307,21 +309,41 @@ __device__ __forceinline__ float tf32_rn(float v)
 
 // ---- per-slot logic (one warp per slot, lanes over bins) ------------------
 
-// Slot state in global scratch (per slot 5 N doubles are reserved): the state
-// y in FP64, its scaled copy yx = y / Sx and the stage right-hand sides in the
-// same scaled units (kx = f / Sx = Sx D) in FP32.  The stage inputs, the error
-// norm and the step controller work in FP32 (their rounding sits below the
-// contraction's own ~3e-7); FP64 holds the state and the mass budget of every
-// accepted increment, so total mass is conserved to FP64 rounding.
-struct SlotBufs { double *y; float *yx, *k1, *k2, *k3; };
+// Slot state in global scratch (per slot 5 N doubles are reserved, 5 N floats
+// used): the state y / Sx as an unevaluated float pair yh + yl (48 significant
+// bits; yh, the state rounded to FP32, is also the stage input), and the stage
+// right-hand sides in the same scaled units (kx = f / Sx = Sx D).  B300
+// executes FP64 at a small fraction of its FP32 rate, so the per-step work
+// stays in FP32: the stage inputs, error norm and step controller (their
+// rounding sits below the contraction's own ~3e-7) and the state update,
+// where error-free FP32 transformations keep the pair exact to 2^-48 and
+// the mass budget of every accepted increment holds to that level.  FP64
+// only carries the time, the step size and the cell's conversion at load and
+// finish.
+struct SlotBufs { float *yh, *yl, *k1, *k2, *k3; };
 
 __device__ __forceinline__ SlotBufs slot_bufs(const MixedArgs &a, int slot)
 {
     const int N = a.t.N;
     const int grp = a.paired ? (int)blockIdx.x >> 1 : (int)blockIdx.x;
-    double *base = a.work + ((size_t)grp * a.NS + slot) * 5 * (size_t)N;
-    float *f = (float *)(base + N);
-    return {base, f, f + N, f + 2 * N, f + 3 * N};
+    float *f = (float *)(a.work + ((size_t)grp * a.NS + slot) * 5 * (size_t)N);
+    return {f, f + N, f + 2 * N, f + 3 * N, f + 4 * N};
+}
+
+// s + e = a + b exactly (Knuth's TwoSum; explicit roundings so that no
+// operation is fused or reassociated).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (h, l) += x for an unevaluated pair h + l with |l| <= ulp(h) / 2.
+__device__ __forceinline__ void pair_add(float &h, float &l, float x)
+{
+    float s, e;
+    two_sum(h, x, s, e);
+    two_sum(s, __fadd_rn(e, l), h, l);
 }
 
 // Load cell c into slot: state, scales, phase 0 (or mark the slot empty).
@@ -340,7 +362,6 @@ __device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, i
     double s = 0.0, sa = 0.0;
     for (int k = lane; k < N; k += 32) {
         const double v = rc[k];
-        if (owner) B.y[k] = v;
         s += v;
         sa += fabs(v);
     }
@@ -349,19 +370,28 @@ __device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, i
     const double Sx = sa > 0.0 ? sa : 1.0;
     const double r = 1.0 / Sx;
     for (int k = lane; k < a.XS; k += 32) {
-        const float v = (k < N) ? (float)(rc[k] * r) : 0.f;
-        if (k < N && owner) B.yx[k] = v;
-        xrow[k] = v;
+        float h = 0.f;
+        if (k < N) {
+            const double z = rc[k] * r;
+            h = (float)z;
+            if (owner) {
+                B.yh[k] = h;
+                B.yl[k] = (float)(z - (double)h);
+            }
+        }
+        xrow[k] = h;
     }
     if (lane == 0) {
         sl.cell = c;
         sl.phase = 0;
         sl.S = s;
         sl.Sx = Sx;
-        sl.atol = a.atol_rel * s;
+        sl.sxf = (float)Sx;
+        sl.atolx = (float)(a.atol_rel * s * r);
         sl.t = 0.0;
         sl.h = (a.mode == MODE_STEP && a.dt_cell) ? a.dt_cell[c] : 0.0;
         sl.hs = 0.0;
+        sl.hsf = 0.f;
         sl.nacc = sl.nrej = sl.nrep = 0;
         sl.last = 0;
         sl.status = CUDISC_OK;
@@ -376,7 +406,11 @@ __device__ void slot_finish(const MixedArgs &a, Slot &sl, int slot)
         SlotBufs B = slot_bufs(a, slot);
         double *rc = a.rho + (size_t)c * N;
         double s1 = 0.0;
-        for (int k = lane; k < N; k += 32) { rc[k] = B.y[k]; s1 += B.y[k]; }
+        for (int k = lane; k < N; k += 32) {
+            const double v = sl.Sx * ((double)B.yh[k] + (double)B.yl[k]);
+            rc[k] = v;
+            s1 += v;
+        }
         s1 = warp_sum(s1);
         if (lane == 0) {
             CellOut o;
@@ -391,38 +425,51 @@ __device__ void slot_finish(const MixedArgs &a, Slot &sl, int slot)
     }
 }
 
-// Accept an increment dx (scaled units, FP32) into the FP64 state: the
-// residual of sum_k dx_k is moved in proportion to |dx_k| (mass budget),
-// then y += Sx dx and yx = y / Sx.
-__device__ void commit_increment(const Slot &sl, SlotBufs B, int N, const float *dx)
+// Accept an increment dx (scaled units) into the state pair: the residual
+// s = sum_k dx_k is moved in proportion to |dx_k| (mass budget), y += dx_k -
+// q |dx_k| with q = s / sum_k |dx_k|, both terms added exactly.  The two sums
+// are exact float pairs, so the budget leaves about 2^-23 of the residual s
+// (itself the contraction's rounding), and yh, the new leading part, is the
+// next stage input.
+__device__ void commit_increment(SlotBufs B, int N, const float *dx)
 {
     const int lane = threadIdx.x & 31;
-    double d[kLaneBins];
-    double s = 0.0, sa = 0.0;
+    float sh = 0.f, sl = 0.f, ah = 0.f, al = 0.f;
 #pragma unroll
-    for (int m = 0; m < kLaneBins; m++) {
-        const int k = lane + 32 * m;
-        d[m] = (k < N) ? (double)dx[m] * sl.Sx : 0.0;
-        s += d[m];
-        sa += fabs(d[m]);
+    for (int m = 0; m < kLaneBins; m++) {          // dx is 0 beyond N
+        float e;
+        two_sum(sh, dx[m], sh, e);
+        sl = __fadd_rn(sl, e);
+        two_sum(ah, fabsf(dx[m]), ah, e);
+        al = __fadd_rn(al, e);
     }
-    s = warp_sum(s);
-    sa = warp_sum(sa);
-    const double q = sa > 0.0 ? s / sa : 0.0;
-    const double r = 1.0 / sl.Sx;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+        const float bh = __shfl_xor_sync(0xffffffffu, ah, o), bl = __shfl_xor_sync(0xffffffffu, al, o);
+        float e;
+        two_sum(sh, oh, sh, e);
+        sl = __fadd_rn(sl, __fadd_rn(ol, e));
+        two_sum(ah, bh, ah, e);
+        al = __fadd_rn(al, __fadd_rn(bl, e));
+    }
+    const float sa = __fadd_rn(ah, al);
+    const float q = sa > 0.f ? __fdiv_rn(__fadd_rn(sh, sl), sa) : 0.f;
 #pragma unroll
     for (int m = 0; m < kLaneBins; m++) {
         const int k = lane + 32 * m;
         if (k < N) {
-            const double y = B.y[k] + (d[m] - q * fabs(d[m]));
-            B.y[k] = y;
-            B.yx[k] = (float)(y * r);
+            float h = B.yh[k], l = B.yl[k];
+            pair_add(h, l, dx[m]);
+            pair_add(h, l, -__fmul_rn(q, fabsf(dx[m])));
+            B.yh[k] = h;
+            B.yl[k] = l;
         }
     }
     __syncwarp();
 }
 
-// First stage input x = yx + hs A21 k1 after choosing the step (shared by
+// First stage input x = yh + hs A21 k1 after choosing the step (shared by
 // the first step and every step after an accept or reject).
 __device__ bool begin_step(const MixedArgs &a, Slot &sl, float *xrow, SlotBufs B)
 {
@@ -430,8 +477,9 @@ __device__ bool begin_step(const MixedArgs &a, Slot &sl, float *xrow, SlotBufs B
     if (sl.nacc + sl.nrej >= a.max_steps) { sl.status = CUDISC_EMAXSTEPS; return false; }
     sl.last = (sl.h >= a.t_span - sl.t);
     sl.hs = sl.last ? (a.t_span - sl.t) : sl.h;
-    const float c1 = (float)(sl.hs * A21);
-    for (int k = lane; k < N; k += 32) xrow[k] = B.yx[k] + c1 * B.k1[k];
+    sl.hsf = (float)sl.hs;
+    const float c1 = sl.hsf * (float)A21;
+    for (int k = lane; k < N; k += 32) xrow[k] = B.yh[k] + c1 * B.k1[k];
     sl.phase = 1;
     return true;
 }
@@ -444,7 +492,7 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
     const int N = a.t.N, lane = threadIdx.x & 31;
     constexpr int MB = kLaneBins;
     SlotBufs B = slot_bufs(a, slot);
-    const float sx = (float)sl.Sx;
+    const float sx = sl.sxf;
     float kv[MB];
 #pragma unroll
     for (int m = 0; m < MB; m++) {
@@ -452,7 +500,7 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
         kv[m] = (k < N) ? sx * Drow[k] : 0.f;
     }
     if (a.mode == MODE_RHS) {
-        // d rho / dt = Sx^2 D with the FP64 mass budget
+        // d rho / dt = Sx^2 D with the FP64 mass budget (one pass, no state)
         double fv[MB], s = 0.0, sa = 0.0;
 #pragma unroll
         for (int m = 0; m < MB; m++) {
@@ -486,11 +534,11 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
         if (sl.phase == 0) {
             if (nh == 0) return true;
             const float c1 = (float)(hh * A21);
-            for (int k = lane; k < N; k += 32) xrow[k] = B.yx[k] + c1 * B.k1[k];
+            for (int k = lane; k < N; k += 32) xrow[k] = B.yh[k] + c1 * B.k1[k];
             sl.phase = 1;
         } else if (sl.phase == 1) {
             const float c2 = (float)(hh * A32);
-            for (int k = lane; k < N; k += 32) xrow[k] = B.yx[k] + c2 * B.k2[k];
+            for (int k = lane; k < N; k += 32) xrow[k] = B.yh[k] + c2 * B.k2[k];
             sl.phase = 2;
         } else {
             const float b1 = (float)(hh * B1), b2 = (float)(hh * B2), b3 = (float)(hh * B3);
@@ -500,11 +548,11 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
                 const int k = lane + 32 * m;
                 dx[m] = (k < N) ? b1 * B.k1[k] + b2 * B.k2[k] + b3 * B.k3[k] : 0.f;
             }
-            commit_increment(sl, B, N, dx);
+            commit_increment(B, N, dx);
             sl.nrep++;
             sl.nacc = sl.nrep;
             if (sl.nrep >= nh) return true;
-            for (int k = lane; k < N; k += 32) xrow[k] = B.yx[k];
+            for (int k = lane; k < N; k += 32) xrow[k] = B.yh[k];
             sl.phase = 0;
         }
         return false;
@@ -513,10 +561,10 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
     switch (sl.phase) {
     case 0: {
         if (!(sl.h > 0.0)) {
-            const float atolx = (float)(sl.atol / sl.Sx);
+            const float atolx = sl.atolx;
             float q = INFINITY;
             for (int k = lane; k < N; k += 32)
-                if (B.k1[k] != 0.f) q = fminf(q, (fabsf(B.yx[k]) + atolx) / fabsf(B.k1[k]));
+                if (B.k1[k] != 0.f) q = fminf(q, (fabsf(B.yh[k]) + atolx) / fabsf(B.k1[k]));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) q = fminf(q, __shfl_xor_sync(0xffffffffu, q, o));
             sl.h = isfinite(q) ? 0.1 * (double)q : a.t_span;
@@ -525,24 +573,25 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
         return !begin_step(a, sl, xrow, B);
     }
     case 1: {
-        const float c2 = (float)(sl.hs * A32);
-        for (int k = lane; k < N; k += 32) xrow[k] = B.yx[k] + c2 * B.k2[k];
+        const float c2 = sl.hsf * (float)A32;
+        for (int k = lane; k < N; k += 32) xrow[k] = B.yh[k] + c2 * B.k2[k];
         sl.phase = 2;
         return false;
     }
     case 2: {
-        const float b1 = (float)(sl.hs * B1), b2 = (float)(sl.hs * B2), b3 = (float)(sl.hs * B3);
+        const float hf = sl.hsf;
+        const float b1 = hf * (float)B1, b2 = hf * (float)B2, b3 = hf * (float)B3;
         for (int k = lane; k < N; k += 32)
-            xrow[k] = B.yx[k] + (b1 * B.k1[k] + b2 * B.k2[k] + b3 * B.k3[k]);
+            xrow[k] = B.yh[k] + (b1 * B.k1[k] + b2 * B.k2[k] + b3 * B.k3[k]);
         sl.phase = 3;
         return false;
     }
     default: {
-        // phase 3: kv holds k4 = f(y1); y1 = yx + dx is the stage input
-        const float b1 = (float)(sl.hs * B1), b2 = (float)(sl.hs * B2), b3 = (float)(sl.hs * B3);
-        const float e1 = (float)(sl.hs * E1), e2 = (float)(sl.hs * E2), e3 = (float)(sl.hs * E3),
-                    e4 = (float)(sl.hs * E4);
-        const float atolx = (float)(sl.atol / sl.Sx), rtol = (float)a.rtol;
+        // phase 3: kv holds k4 = f(y1); y1 = yh + dx is the stage input
+        const float hf = sl.hsf;
+        const float b1 = hf * (float)B1, b2 = hf * (float)B2, b3 = hf * (float)B3;
+        const float e1 = hf * (float)E1, e2 = hf * (float)E2, e3 = hf * (float)E3, e4 = hf * (float)E4;
+        const float atolx = sl.atolx, rtol = a.rtol_f;
         float dx[MB];
         float E = 0.f, ymin = INFINITY, fin = 1.f;
 #pragma unroll
@@ -550,7 +599,7 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
             const int k = lane + 32 * m;
             dx[m] = 0.f;
             if (k < N) {
-                const float k1 = B.k1[k], k2 = B.k2[k], k3 = B.k3[k], yx = B.yx[k];
+                const float k1 = B.k1[k], k2 = B.k2[k], k3 = B.k3[k], yx = B.yh[k];
                 dx[m] = b1 * k1 + b2 * k2 + b3 * k3;
                 const float y1 = yx + dx[m];
                 const float e = e1 * k1 + e2 * k2 + e3 * k3 + e4 * kv[m];
@@ -569,7 +618,7 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
         }
         const bool finite = fin > 0.5f;
         if (finite && E <= 1.f && ymin >= -atolx) {
-            commit_increment(sl, B, N, dx);
+            commit_increment(B, N, dx);
             sl.t = sl.last ? a.t_span : sl.t + sl.hs;
 #pragma unroll
             for (int m = 0; m < MB; m++) {
@@ -580,17 +629,17 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
             if (lane == 0 && a.rec_dt && sl.nacc < a.rec_cap)
                 a.rec_dt[(size_t)sl.cell * a.rec_cap + sl.nacc] = sl.hs;
             sl.nacc++;
-            double fac = (E > 0.f) ? 0.9 * pow((double)E, -1.0 / 3.0) : 5.0;
-            fac = fmin(fmax(fac, 0.2), 5.0);
-            if (!(sl.last && sl.hs < sl.h)) sl.h = sl.hs * fac;
+            float fac = (E > 0.f) ? 0.9f * rcbrtf(E) : 5.f;
+            fac = fminf(fmaxf(fac, 0.2f), 5.f);
+            if (!(sl.last && sl.hs < sl.h)) sl.h = sl.hs * (double)fac;
             if (sl.t >= a.t_span) return true;
         } else {
             sl.nrej++;
-            double fac;
-            if (!finite) fac = 0.2;
-            else if (E > 1.f) fac = fmax(0.9 * pow((double)E, -1.0 / 3.0), 0.2);
-            else fac = 0.5;
-            sl.h = sl.hs * fac;
+            float fac;
+            if (!finite) fac = 0.2f;
+            else if (E > 1.f) fac = fmaxf(0.9f * rcbrtf(E), 0.2f);
+            else fac = 0.5f;
+            sl.h = sl.hs * (double)fac;
             if (sl.h < 1e-14 * a.t_span) { sl.status = finite ? CUDISC_EDTMIN : CUDISC_ENONFINITE; return true; }
         }
         return !begin_step(a, sl, xrow, B);
@@ -1140,6 +1189,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.t_span = t_span;
     a.dt_cell = dt_cell;
     a.rtol = c->p.rtol;
+    a.rtol_f = (float)c->p.rtol;
     a.atol_rel = c->p.atol_rel;
     a.max_steps = c->p.max_substeps;
     a.replay_h = replay_h;
@@ -1222,6 +1272,7 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     a.t_span = t_span;
     a.dt_cell = dt_cell;
     a.rtol = c->p.rtol;
+    a.rtol_f = (float)c->p.rtol;
     a.atol_rel = c->p.atol_rel;
     a.max_steps = c->p.max_substeps;
     a.replay_h = nullptr;
