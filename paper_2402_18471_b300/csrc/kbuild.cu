@@ -193,15 +193,24 @@ enum { KB_INVA = P3_COUNT, KB_INVQ, KB_COUNT };
 // (p_c = 1 - p_f, each accurate to a few ulp of itself, so that neither
 // coagulation in a fragmentation-dominated cell nor fragmentation in a
 // coagulation-dominated one is lost to rounding); slots past the diagonal
-// hold zeros.  One CTA per cell: the cell's per-bin fields are staged in
+// hold zeros.  One CTA per kPosTile consecutive table positions (the cells
+// at those positions, see k32_pos): their per-bin fields are staged in
 // shared memory once; each thread then produces four consecutive slots of a
-// block (same i, j .. j+3) and writes them as two 16-byte stores.  The
+// block (same i, j .. j+3) of one cell and writes them as two 16-byte
+// chunks.  Neighbouring threads take neighbouring positions, so each store
+// instruction writes whole 128-byte lines of the interleaved table.  The
 // larger Stokes number of a pair (i, j <= i) is always St_i: St = rho_m a
 // Omega / (rho_g v_th) rises with the bin's size.  Divisions, the square
 // root and the exponential use the hardware approximations: K stays within
 // 1e-6 and K p_frag within 1e-5 of FP64.
 //   Physical = physical kernel and fragmentation probability (the other
 //   modes are the closed-form test kernels); HasVdust = input velocities.
+constexpr int kPosTile = 8;
+
+// words of shared memory per cell: KB_COUNT fields of NR, padded to 4 mod 32
+// so that the tile's cells fall in distinct banks
+__host__ __device__ inline int kb_cell_stride(int NR) { return (KB_COUNT * NR + 27) / 32 * 32 + 4; }
+
 template <bool Physical, bool HasVdust>
 __global__ void __launch_bounds__(256) kbuild32_kernel(
     float kc, float v_frag, int kernel_mode, int frag_mode, int n_cells, int N, int NR,
@@ -209,35 +218,51 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
     const float *__restrict__ prep32, const float4 *__restrict__ scal32,
     float2 *__restrict__ Kout)
 {
-    extern __shared__ __align__(16) float f32s[];       // [KB_COUNT][NR]
-    const int c = blockIdx.x;
-    if (c >= n_cells) return;
-    const float *src = prep32 + (size_t)c * P3_COUNT * N;
-    for (int t = threadIdx.x; t < P3_COUNT * NR; t += blockDim.x) {
-        const int f = t / NR, k = t - f * NR;
-        f32s[t] = k < N ? src[f * N + k] : 0.0f;
-    }
-    for (int k = threadIdx.x; k < NR; k += blockDim.x) {
-        const float S = f32s[P3_ST * NR + k];
-        f32s[KB_INVA * NR + k] = 1.0f / (1.0f + S * S);
-        f32s[KB_INVQ * NR + k] = 1.0f / (1.0f + S);
+    extern __shared__ __align__(16) float f32s[];       // [kPosTile][cell stride]: [KB_COUNT][NR] each
+    const int CS = kb_cell_stride(NR);
+    const int pos0 = blockIdx.x * kPosTile;
+    __shared__ int s_cell[kPosTile];
+    if (threadIdx.x < kPosTile) {
+        // the cell at position pos (inverse of k32_pos), or -1
+        const int pos = pos0 + threadIdx.x;
+        int c = pos;
+        if (pos < kG * kC) c = pos / kC + (pos % kC) * kG;
+        s_cell[threadIdx.x] = (pos < kn && c < n_cells) ? c : -1;
     }
     __syncthreads();
+    for (int t = threadIdx.x; t < kPosTile * P3_COUNT * NR; t += blockDim.x) {
+        const int jc = t / (P3_COUNT * NR), r = t - jc * (P3_COUNT * NR);
+        const int f = r / NR, k = r - f * NR;
+        const int c = s_cell[jc];
+        f32s[jc * CS + r] = (c >= 0 && k < N) ? prep32[((size_t)c * P3_COUNT + f) * N + k] : 0.0f;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kPosTile * NR; t += blockDim.x) {
+        const int jc = t / NR, k = t - jc * NR;
+        float *F = f32s + jc * CS;
+        const float S = F[P3_ST * NR + k];
+        F[KB_INVA * NR + k] = 1.0f / (1.0f + S * S);
+        F[KB_INVQ * NR + k] = 1.0f / (1.0f + S);
+    }
+    __syncthreads();
+    const int jc = threadIdx.x % kPosTile;                // this thread's cell of the tile
+    const int c = s_cell[jc];
+    if (c < 0) return;
+    const float *F = f32s + jc * CS;
     const float4 s4 = scal32[c];
     const float d = s4.x, Vg2 = s4.y, ev = s4.z, zo = s4.w;
     const float vf2 = 1.5f * v_frag * v_frag;
-    const float *St = f32s + P3_ST * NR, *U = f32s + P3_U * NR, *Aa = f32s + P3_A * NR;
-    const float *IA = f32s + KB_INVA * NR, *IQ = f32s + KB_INVQ * NR;
-    float4 *dst = reinterpret_cast<float4 *>(Kout);       // chunk (b, ch): (8 b + ch) kn + pos
-    const int pos = k32_pos(c, kG, kC);
-    for (int g = threadIdx.x; 4 * g < n_slots; g += blockDim.x) {
+    const float *St = F + P3_ST * NR, *U = F + P3_U * NR, *Aa = F + P3_A * NR;
+    const float *IA = F + KB_INVA * NR, *IQ = F + KB_INVQ * NR;
+    float4 *dst = reinterpret_cast<float4 *>(Kout) + pos0 + jc;   // chunk (b, ch): (8 b + ch) kn + pos
+    for (int g = threadIdx.x / kPosTile; 4 * g < n_slots; g += blockDim.x / kPosTile) {
         const int q0 = 4 * g;
         const int b = q0 >> 4;
         const int i = __ldg(blk_i + b);
         const int j0 = __ldg(blk_j0 + b) + (q0 & 15);
         // bin i (the larger Stokes number)
-        const float S1 = St[i], Ss = f32s[P3_SS * NR + i], Ssmd = f32s[P3_SSMD * NR + i];
-        const float omSs = f32s[P3_OMSS * NR + i], Ui = U[i], ai = Aa[i], ia1 = IA[i], iq1 = IQ[i];
+        const float S1 = St[i], Ss = F[P3_SS * NR + i], Ssmd = F[P3_SSMD * NR + i];
+        const float omSs = F[P3_OMSS * NR + i], Ui = U[i], ai = Aa[i], ia1 = IA[i], iq1 = IQ[i];
         const float P1 = S1 + Ss, Q1 = 1.0f + S1, R1 = S1 + d;
         const float sd = Ss + d, Sd = Ss * d, opSs = 1.0f + Ss;
         const float c1 = S1 * sd + Sd, PQ1 = P1 * Q1, PR1 = P1 * R1;
@@ -277,10 +302,9 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
             float dR, dP, dZ;
             if (HasVdust) {
                 // input velocities: difference of FP32 hi/lo pairs
-                const float *f = f32s;
-                dR = (f[P3_VRH * NR + i] - f[P3_VRH * NR + j]) + (f[P3_VRL * NR + i] - f[P3_VRL * NR + j]);
-                dP = (f[P3_VPH * NR + i] - f[P3_VPH * NR + j]) + (f[P3_VPL * NR + i] - f[P3_VPL * NR + j]);
-                dZ = (f[P3_VZH * NR + i] - f[P3_VZH * NR + j]) + (f[P3_VZL * NR + i] - f[P3_VZL * NR + j]);
+                dR = (F[P3_VRH * NR + i] - F[P3_VRH * NR + j]) + (F[P3_VRL * NR + i] - F[P3_VRL * NR + j]);
+                dP = (F[P3_VPH * NR + i] - F[P3_VPH * NR + j]) + (F[P3_VPL * NR + i] - F[P3_VPL * NR + j]);
+                dZ = (F[P3_VZH * NR + i] - F[P3_VZH * NR + j]) + (F[P3_VZL * NR + i] - F[P3_VZL * NR + j]);
             } else {
                 // terminal velocities: differences factored through St_i - St_j
                 //   v_R   = -2 eta v_K St/(1+St^2), v_phi = -eta v_K/(1+St^2),
@@ -301,7 +325,7 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
                 pf = (x + 1.0f) * e;
                 pc = pcoag_f32(x, e);
             } else {
-                const float *Mm = f32s + P3_M * NR;
+                const float *Mm = F + P3_M * NR;
                 if (kernel_mode == CUDISC_KERNEL_CONSTANT) K = kc;
                 else if (kernel_mode == CUDISC_KERNEL_ADDITIVE) K = kc * (Mm[i] + Mm[j]);
                 else { const float sa = ai + aja[u]; K = 3.14159265358979f * sa * sa * (dv2 * rs); }
@@ -319,8 +343,8 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
             o[2 * u + 1] = live ? K * pf : 0.0f;
         }
         const size_t ch0 = (size_t)(8 * b + ((q0 & 15) >> 1));  // the group's first 2-pair chunk
-        dst[ch0 * kn + pos] = make_float4(o[0], o[1], o[2], o[3]);
-        dst[(ch0 + 1) * kn + pos] = make_float4(o[4], o[5], o[6], o[7]);
+        dst[ch0 * kn] = make_float4(o[0], o[1], o[2], o[3]);
+        dst[(ch0 + 1) * kn] = make_float4(o[4], o[5], o[6], o[7]);
     }
 }
 
@@ -377,12 +401,14 @@ cudaError_t launch_kbuild(const cudisc_coag_ctx *c)
     } else {
         const int n_slots = c->n_blk * kBlkPairs;
         const int NR = (c->N + 15) / 16 * 16;
-        const size_t smem = (size_t)KB_COUNT * NR * sizeof(float);
+        const size_t smem = (size_t)kPosTile * kb_cell_stride(NR) * sizeof(float);
         const bool phys = p.kernel_mode == CUDISC_KERNEL_PHYSICAL && p.frag_mode == CUDISC_FRAG_PHYSICAL;
         const bool vd = p.v_dust != nullptr;
         auto kern = phys ? (vd ? kbuild32_kernel<true, true> : kbuild32_kernel<true, false>)
                          : (vd ? kbuild32_kernel<false, true> : kbuild32_kernel<false, false>);
-        kern<<<c->n_cells, 256, smem, c->stream>>>(
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<(c->k32_n + kPosTile - 1) / kPosTile, 256, smem, c->stream>>>(
             (float)p.kernel_const, (float)p.v_frag, p.kernel_mode, p.frag_mode, c->n_cells, c->N, NR,
             n_slots, c->k32_G, c->k32_C, c->k32_n, c->d_blk_i, c->d_blk_j0, c->d_prep32, c->d_scal32,
             c->d_K32);
