@@ -352,13 +352,17 @@ def main():
             "metric": METRIC, "value": value, "unit": "cell-substeps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "tf32x4+f32+f64" if args.precision == "mixed" else "f64",
+            "dtype": "tf32x4+f32" if args.precision == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "n_cells": disc.n_cells, "n_bins": N,
                        "t_span_yr": disc.t_span / synth.CONST["yr"],
                        "precision": args.precision, "rtol": disc.rtol, "atol_rel": disc.atol_rel,
                        "l2": "K tables larger than L2 (FP32 331 MB / FP64 404 MB) are rebuilt every step",
-                       "step": "kernel build + BS3 integration of all cells over t_span"},
+                       "step": "kernel build + BS3 integration of all cells over t_span",
+                       **({"state": "FP32 pair y/Sx = yh + yl (48 bits), FP64 time and step size",
+                           "mixed_cluster": main_res["g"].mixed_cluster()[0],
+                           "slot_groups": main_res["g"].mixed_cluster()[1]}
+                          if args.precision == "mixed" else {})},
             "ms_kernel_per_step": main_res["kern_ms"] / args.steps,
             "accepted_per_step": main_res["last"]["accepted"],
             "rejected_per_step": main_res["last"]["rejected"],

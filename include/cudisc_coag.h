@@ -111,6 +111,13 @@ typedef struct {
     double atol_rel;             /* absolute tolerance / sum_k rho_k (1e-10) */
     long long max_substeps;      /* per cell, accepted + rejected attempts */
     void *stream;                /* cudaStream_t, NULL = legacy default stream */
+    int mixed_cluster;           /* CUDISC_MIXED_TF32 only: CTAs (one cluster) per
+                                    group of 64 cell slots, 1, 2, 4 or 8, each
+                                    taking that share of the contraction; 0 =
+                                    chosen from n_cells and n_bins (see
+                                    cudisc_coag_mixed_cluster).  A size whose
+                                    buffers do not fit falls back to the
+                                    largest smaller one that does. */
 } cudisc_coag_params;
 
 typedef struct {
@@ -189,9 +196,10 @@ cudisc_status cudisc_coag_replay(cudisc_coag_ctx *ctx, double *rho, const double
  *   - All calls share the one array (it keeps the last call's contents, and
  *     every slot is written before it is read): calls that overlap on the GPU,
  *     from any context, race and give wrong results.
- *   - Problems whose slot state exceeds 16 MiB (148 CTAs x slots x 5 x N x
- *     8 bytes) are rejected with CUDISC_ENOTSUP and a message; use
- *     cudisc_coag_step for them.
+ *   - Problems whose slot state exceeds 16 MiB (slot groups x 64 slots x 5
+ *     x N x 4 bytes; see cudisc_coag_mixed_cluster for the groups) are
+ *     rejected with CUDISC_ENOTSUP and a message; use cudisc_coag_step for
+ *     them.
  *   - Returns CUDISC_EINVAL for a context of another precision. */
 cudisc_status cudisc_coag_step_static_scratch(cudisc_coag_ctx *ctx, double *rho, double t_span,
                                               double *dt_cell, cudisc_step_stats *stats);
@@ -207,6 +215,12 @@ typedef struct {
     double vjp_ms;
 } cudisc_timings;
 cudisc_status cudisc_coag_get_timings(const cudisc_coag_ctx *ctx, cudisc_timings *out);
+
+/* Launch layout of the mixed-precision integration kernel chosen at init:
+ * *cluster = CTAs per group of 64 cell slots (1, 2, 4 or 8; the contraction
+ * of a group's pass is split between them), *groups = groups resident at
+ * once.  Both 0 for an FP64 context.  EINVAL for a NULL argument.  Host only. */
+cudisc_status cudisc_coag_mixed_cluster(const cudisc_coag_ctx *ctx, int *cluster, int *groups);
 
 /* Vector-Jacobian product of the integration (the paper has no adjoint; this
  * is the discrete adjoint of the BS3 map of Sec. 5 with the step sizes held

@@ -41,6 +41,7 @@ class cudisc_coag_params(C.Structure):
         ("rtol", C.c_double), ("atol_rel", C.c_double),
         ("max_substeps", C.c_longlong),
         ("stream", C.c_void_p),
+        ("mixed_cluster", C.c_int),
     ]
 
 
@@ -85,6 +86,7 @@ def lib():
         L.cudisc_coag_replay.argtypes = [v, v, v, v, C.c_longlong]
         L.cudisc_coag_step_static_scratch.argtypes = [v, v, d, v, C.POINTER(cudisc_step_stats)]
         L.cudisc_coag_get_timings.argtypes = [v, C.POINTER(cudisc_timings)]
+        L.cudisc_coag_mixed_cluster.argtypes = [v, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.cudisc_coag_set_v_frag.argtypes = [v, d]
         L.cudisc_coag_vjp.argtypes = [v, v, d, v, v, C.c_longlong, v, v, v, v]
         L.cudisc_coag_destroy.argtypes = [v]
@@ -95,7 +97,8 @@ def lib():
         for fn in ("cudisc_coag_init", "cudisc_coag_build_kernel", "cudisc_coag_get_kernel",
                    "cudisc_coag_rhs", "cudisc_coag_step", "cudisc_coag_set_records",
                    "cudisc_coag_replay", "cudisc_coag_step_static_scratch",
-                   "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp"):
+                   "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp",
+                   "cudisc_coag_mixed_cluster"):
             getattr(L, fn).restype = C.c_int
         _lib = L
     return _lib
@@ -169,6 +172,13 @@ def cudisc_coag_get_timings(ctx) -> dict:
     return t.as_dict()
 
 
+def cudisc_coag_mixed_cluster(ctx) -> tuple:
+    """(CTAs per slot group, groups) of the mixed kernel; (0, 0) for FP64."""
+    cl, gr = C.c_int(), C.c_int()
+    _check(lib().cudisc_coag_mixed_cluster(ctx, C.byref(cl), C.byref(gr)), ctx)
+    return cl.value, gr.value
+
+
 def cudisc_coag_destroy(ctx):
     lib().cudisc_coag_destroy(ctx)
 
@@ -215,6 +225,7 @@ class Coag:
             setattr(p, k, int(s[k]))
         p.precision = self.precision
         p.max_substeps = int(s["max_substeps"])
+        p.mixed_cluster = int(s.get("mixed_cluster", 0))
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         p.stream = self.stream.cuda_stream
         self.params = p
@@ -240,6 +251,10 @@ class Coag:
 
     def timings(self) -> dict:
         return cudisc_coag_get_timings(self.ctx)
+
+    def mixed_cluster(self) -> tuple:
+        """(CTAs per group of 64 slots, groups) of the mixed kernel."""
+        return cudisc_coag_mixed_cluster(self.ctx)
 
     def get_kernel(self):
         t = self.torch

@@ -194,6 +194,11 @@ static cudisc_status validate(const cudisc_coag_params *p, std::string &why)
     if (p->split_mode < 0 || p->split_mode > 1) { why = "split_mode out of range"; return CUDISC_EINVAL; }
     if (!(p->rtol > 0.0) || !(p->atol_rel >= 0.0)) { why = "rtol must be > 0 and atol_rel >= 0"; return CUDISC_EINVAL; }
     if (p->max_substeps < 1) { why = "max_substeps must be >= 1"; return CUDISC_EINVAL; }
+    if (p->mixed_cluster != 0 && p->mixed_cluster != 1 && p->mixed_cluster != 2 && p->mixed_cluster != 4 &&
+        p->mixed_cluster != 8) {
+        why = "mixed_cluster must be 0 (automatic), 1, 2, 4 or 8";
+        return CUDISC_EINVAL;
+    }
     if (!(p->rho_m > 0) || !(p->mu > 0) || !(p->Mstar > 0) || !(p->k_B > 0) || !(p->m_H > 0) ||
         !(p->G > 0) || !(p->sigma_H2 > 0)) {
         why = "rho_m, mu, Mstar, k_B, m_H, G and sigma_H2 must be positive";
@@ -415,13 +420,13 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
             e = cudaMalloc(&c->d_K64, nc * (size_t)c->Np * sizeof(double2));
         else
         {
-            cdc::mixed_layout(c->n_cells, c->N, &c->k32_G, &c->k32_C);
+            cdc::mixed_layout(c->n_cells, c->N, params->mixed_cluster, &c->mix_P, &c->k32_G, &c->k32_C);
             c->k32_n = std::max(c->n_cells, c->k32_G * c->k32_C);
             e = cudaMalloc(&c->d_K32, (size_t)c->k32_n * c->n_blk * cdc::kBlkPairs * sizeof(float2));
         }
     }
     if (e == cudaSuccess && params->precision == CUDISC_MIXED_TF32) {
-        c->work_bytes = cdc::mixed_workspace_bytes(c->n_cells, c->N);
+        c->work_bytes = cdc::mixed_workspace_bytes(c->n_cells, c->N, c->mix_P);
         e = cudaMalloc(&c->d_work, c->work_bytes);
     }
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
@@ -450,6 +455,16 @@ cudisc_status cudisc_coag_get_timings(const cudisc_coag_ctx *c, cudisc_timings *
     out->kbuild_ms = c->t_kbuild;
     out->step_ms = c->t_step;
     out->vjp_ms = c->t_vjp;
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_coag_mixed_cluster(const cudisc_coag_ctx *c, int *cluster, int *groups)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!cluster || !groups) return CUDISC_EINVAL;
+    const bool mixed = c->p.precision == CUDISC_MIXED_TF32;
+    *cluster = mixed ? c->mix_P : 0;
+    *groups = mixed ? c->k32_G : 0;
     return CUDISC_OK;
 }
 

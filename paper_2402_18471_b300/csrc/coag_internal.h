@@ -110,7 +110,8 @@ struct cudisc_coag_ctx {
     float4 *d_scal32 = nullptr;        // [n_cells] {delta, Vg2, etavK, ZOm} in FP32
     double2 *d_K64 = nullptr;          // [n_cells][Np]      {K, K p_frag}
     float2 *d_K32 = nullptr;           // k32_n x n_blk x 16 {K p_coag, K p_frag}, see k32_index
-    int k32_G = 1, k32_C = 1, k32_n = 0;   // its layout: CTAs, initial cells per CTA, positions
+    int k32_G = 1, k32_C = 1, k32_n = 0;   // its layout: slot groups, initial cells per group, positions
+    int mix_P = 1;                     // CTAs per slot group of the mixed kernel
     // integration workspace
     cdc::CellOut *d_out = nullptr;     // [n_cells]
     double *d_work = nullptr;          // mixed path slot state
@@ -140,8 +141,10 @@ cudaError_t launch_rhs_mixed(const cudisc_coag_ctx *c, const double *rho, double
 cudaError_t launch_step_mixed(const cudisc_coag_ctx *c, double *rho, double t_span,
                               double *dt_cell, const double *replay_h,
                               const long long *replay_n, long long replay_stride);
-size_t mixed_workspace_bytes(int n_cells, int N);
-void mixed_layout(int n_cells, int N, int *G, int *C);   // CTAs and initial cells per CTA
+size_t mixed_workspace_bytes(int n_cells, int N, int P);
+// cluster size P for a request P_req (0: automatic), groups of slots G and
+// initial cells per group C of the mixed kernel
+void mixed_layout(int n_cells, int N, int P_req, int *P, int *G, int *C);
 // adjoint (vjp.cu)
 bool vjp_fits(const cudisc_coag_ctx *c);
 cudaError_t vjp_prepare(cudisc_coag_ctx *c, long long max_steps);

@@ -13,7 +13,7 @@
 //
 // Layout on chip (one CTA per SM, persistent over all right-hand sides):
 //   MMA M = 128 rows = 64 cell slots x {A_hi, A_lo}: the generated operand
-//   A (x_i x_j K p, split into TF32 hi and lo, both rounded to nearest) is
+//   A (x_i x_j K p, split into a TF32 hi part and the remainder lo) is
 //   written by the generator warps straight into tensor memory, rows 0..63
 //   the hi parts and rows 64..127 the lo parts of the same 64 slots.
 //   MMA N = the bins padded to 16 (Bt, streamed as swizzled TF32 hi and lo
@@ -30,8 +30,8 @@
 //   full through the issuer's barrier checks).  Only the Bt tiles pass
 //   through shared memory, once each way.
 // Warp roles: warp 0 bulk-copy producer, warp 1 MMA issuer and TMEM owner,
-// warps 2..9 generate A (two warps per TMEM lane quadrant, one per half of a
-// block's pairs) and, between right-hand sides, run the per-slot logic: the
+// warps 2..17 generate A (four warps per TMEM lane quadrant, one per quarter
+// of a block's pairs) and, between right-hand sides, run the per-slot logic: the
 // mass budget (sum_k f_k = 0 restored in FP64), the Bogacki-Shampine 3(2)
 // stages, the error norm, step control and refilling a slot with the next
 // cell when one finishes.
@@ -49,7 +49,10 @@
 namespace cdc {
 namespace {
 
-constexpr int kGenWarps = 8;
+constexpr int kGenWarps = 16;                     // generator warps, kGenQ per TMEM lane quadrant
+constexpr int kGenQ = kGenWarps / 4;
+constexpr int kGP = kBlkPairs / kGenQ;            // pairs of each block a generator thread makes
+constexpr int kGC = kGP / 2;                      // its 2-pair chunks of the K table
 constexpr int kSlots = 64;                        // cell slots per CTA (TMEM rows / 2)
 constexpr int kAStages = 3;                       // generated-operand stages in TMEM (two blocks, 64 columns each)
 constexpr int kMaxMain = 8;                       // TMEM accumulators for the products with Bt_hi
@@ -80,7 +83,7 @@ struct MixedArgs {
     CellOut *out;
     int *err;                   // device status word
     int *queue;                 // global work-queue head (cells past the initial fill)
-    double *work;               // [grid][NS][5][N] FP64 slot state
+    float *work;                // [groups][NS][5][N] slot state (see SlotBufs)
     double *rec_dt;
     long long rec_cap;
     long long *rec_n;
@@ -88,7 +91,7 @@ struct MixedArgs {
     int NS, XS, mode;
     int SB, NBP;                // mapping-tile ring depth; bins padded to 16 (MMA N, tile rows copied)
     int kC, kn;                 // K table layout: initial cells per group, positions (k32_pos)
-    int paired;                 // 1: a cluster of two CTAs shares each group of slots (see the kernel)
+    int P;                      // CTAs per group of slots (a cluster of 1, 2, 4 or 8; see the kernel)
     int nacc;                   // TMEM accumulators for the products with Bt_hi (stacked: with [Bt_hi; Bt_lo])
     int stacked;                // 1: one MMA of N = 2 NBP takes Bt_hi and Bt_lo together (2 NBP <= 256)
 };
@@ -166,7 +169,7 @@ __device__ __forceinline__ void st_cluster_s32(uint32_t addr, int v)
     asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 __device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
-// arrive on an mbarrier of the peer CTA, releasing this thread's (and, after
+// arrive on an mbarrier of another CTA of the cluster, releasing this thread's (and, after
 // a __syncwarp, its warp's) prior writes at cluster scope
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr)
 {
@@ -180,7 +183,7 @@ __device__ __forceinline__ bool mbar_test_cluster(uint64_t *b, uint32_t parity)
                  : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
     return ok != 0;
 }
-// Bounded warp-wide wait for data the peer CTA released (acquire at cluster scope).
+// Bounded warp-wide wait for data other CTAs of the cluster released (acquire at cluster scope).
 __device__ __noinline__ bool cwait(uint64_t *b, uint32_t parity, volatile int *s_err, int code)
 {
     const long long t0 = clock64();
@@ -249,6 +252,15 @@ __device__ __forceinline__ void mma_tf32_ts_acc(uint32_t dt, uint32_t at, uint64
     asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;"
                  ::"r"(dt), "r"(at), "l"(b), "r"(idesc) : "memory");
 }
+// Store 8 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+                   "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])),
+                   "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
 // Store 16 consecutive 32-bit columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
 {
@@ -262,6 +274,8 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
                    "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
                  : "memory");
 }
+__device__ __forceinline__ void tmem_st_row(uint32_t taddr, const float (&v)[8]) { tmem_st8(taddr, v); }
+__device__ __forceinline__ void tmem_st_row(uint32_t taddr, const float (&v)[16]) { tmem_st16(taddr, v); }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
@@ -295,9 +309,12 @@ __device__ __forceinline__ double warp_sum(double v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-// TF32 split, both parts rounded to nearest: hi = rn_tf32(v), lo =
-// rn_tf32(v - hi).  The tensor core then sees exact TF32 values and
-// hi + lo matches v to 2^-22 relative, without the bias of truncation.
+// TF32 split: hi = rn_tf32(v), an exact TF32 value, and lo = v - hi, exact in
+// FP32 (|lo| <= 2^-11 |v|).  The tensor core reads lo at TF32 precision (its
+// 13 low mantissa bits take no part), an error of at most 2^-10 |lo|, so the
+// hi + lo it multiplies matches v to 2^-21 relative.  (Rounding lo as well
+// would halve that bound for two more integer operations per element on the
+// generators, which bound the pass.)
 // Rounding to the 10-bit TF32 mantissa, ties away from zero, is integer
 // arithmetic on the bits of a finite float: add half a TF32 ulp (bit 12) to
 // the magnitude bits and clear the 13 dropped bits (a carry into the
@@ -309,8 +326,7 @@ __device__ __forceinline__ float tf32_rn(float v)
 
 // ---- per-slot logic (one warp per slot, lanes over bins) ------------------
 
-// Slot state in global scratch (per slot 5 N doubles are reserved, 5 N floats
-// used): the state y / Sx as an unevaluated float pair yh + yl (48 significant
+// Slot state in global scratch (5 N floats per slot): the state y / Sx as an unevaluated float pair yh + yl (48 significant
 // bits; yh, the state rounded to FP32, is also the stage input), and the stage
 // right-hand sides in the same scaled units (kx = f / Sx = Sx D).  B300
 // executes FP64 at a small fraction of its FP32 rate, so the per-step work
@@ -325,8 +341,8 @@ struct SlotBufs { float *yh, *yl, *k1, *k2, *k3; };
 __device__ __forceinline__ SlotBufs slot_bufs(const MixedArgs &a, int slot)
 {
     const int N = a.t.N;
-    const int grp = a.paired ? (int)blockIdx.x >> 1 : (int)blockIdx.x;
-    float *f = (float *)(a.work + ((size_t)grp * a.NS + slot) * 5 * (size_t)N);
+    const int grp = (int)blockIdx.x / a.P;
+    float *f = a.work + ((size_t)grp * a.NS + slot) * 5 * (size_t)N;
     return {f, f + N, f + 2 * N, f + 3 * N, f + 4 * N};
 }
 
@@ -348,7 +364,7 @@ __device__ __forceinline__ void pair_add(float &h, float &l, float x)
 
 // Load cell c into slot: state, scales, phase 0 (or mark the slot empty).
 // owner = false: only the stage-input row and the cell id (a slot whose
-// integrator state the peer CTA of the pair keeps).
+// integrator state another CTA of the cluster keeps).
 __device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, int c, bool owner = true)
 {
     const int N = a.t.N, lane = threadIdx.x & 31;
@@ -647,48 +663,58 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
     }
 }
 
-// Generator thread: one TMEM row (a slot's hi or lo part) and eight pairs of
-// every block (half of its 16).  a = x_i x_j K p_coag, b = x_i x_j K p_frag,
-// split hi = rn_tf32(v), lo = rn_tf32(v - hi); the thread keeps the half its
-// row holds and writes the 16 values into the stage's TMEM columns.
-struct KRegs { float4 v[4]; };           // {K p_coag, K p_frag} of 8 pairs
+// Generator thread: one TMEM row (a slot's hi or lo part) and kGP pairs of
+// every block (a kGenQ-th of its 16).  a = x_i x_j K p_coag, b = x_i x_j K
+// p_frag, split hi = rn_tf32(v), lo = v - hi; the thread keeps the
+// half its row holds and writes the 2 kGP values into the stage's TMEM
+// columns.
+struct KRegs { float4 v[kGC]; };         // {K p_coag, K p_frag} of kGP pairs
 
-// The thread's four 2-pair chunks of block b: kbase points at chunk 4 half of
+// The thread's 2-pair chunks of block b: kbase points at its first chunk of
 // block 0 of its cell; chunks are n_cells float4 apart, blocks 8 n_cells.
 __device__ __forceinline__ void load_k(KRegs &k, const float4 *kbase, int b, int n_cells)
 {
     const float4 *src = kbase + (size_t)b * 8 * n_cells;
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
 #pragma unroll
-    for (int q = 0; q < 4; q++) k.v[q] = __ldg(src + (size_t)q * n_cells);
+    for (int q = 0; q < kGC; q++) {
+        float4 r;
+        asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                     : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(src + (size_t)q * n_cells), "l"(pol));
+        k.v[q] = r;
+    }
 }
 
-__device__ __forceinline__ void gen_block(uint32_t taddr, const KRegs &kr, const float *xr, int bi,
-                                          int jfirst, bool lo_half)
+__device__ __forceinline__ void gen_vals(const KRegs &kr, const float *xr, int bi, int jfirst, bool lo_half,
+                                         float (&out)[2 * kGP])
 {
     const float xi = xr[bi];
-    const float4 xa = *(const float4 *)(xr + jfirst), xb = *(const float4 *)(xr + jfirst + 4);
-    const float xj[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+    float xj[kGP];
+#pragma unroll
+    for (int u = 0; u < kGP; u += 4) {
+        const float4 x4 = *(const float4 *)(xr + jfirst + u);
+        xj[u] = x4.x; xj[u + 1] = x4.y; xj[u + 2] = x4.z; xj[u + 3] = x4.w;
+    }
     const float *kv = (const float *)kr.v;
-    float out[16];
     if (lo_half) {
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
+        for (int u = 0; u < kGP; u++) {
             const float xx = xi * xj[u];
 #pragma unroll
             for (int w = 0; w < 2; w++) {
                 const float v = xx * kv[2 * u + w];
-                out[2 * u + w] = tf32_rn(v - tf32_rn(v));
+                out[2 * u + w] = v - tf32_rn(v);
             }
         }
     } else {
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
+        for (int u = 0; u < kGP; u++) {
             const float xx = xi * xj[u];
 #pragma unroll
             for (int w = 0; w < 2; w++) out[2 * u + w] = tf32_rn(xx * kv[2 * u + w]);
         }
     }
-    tmem_st16(taddr, out);
 }
 
 // One pass of a generator warp over all blocks, a stage of two a step.  K loads
@@ -703,28 +729,35 @@ struct GenCtx {
     const float *xr;
     uint64_t *c_empty, *c_full;
     volatile int *s_err;
-    int n_blk, half, lane, n_cells;
+    int n_blk, sub, lane, n_cells;       // sub: which kGP pairs of each block
     bool lo_half, active;
     int bi, bj0;                         // pair row and first column of the next block
 };
 
 // One pipeline stage = two blocks (b = 2 st, 2 st + 1; the last stage of a
-// pass may hold one): one wait, two independent products-and-splits into
-// the stage's 64 TMEM columns, one store wait, one arrival.
+// pass may hold one): one wait, two products-and-splits into the stage's 64
+// TMEM columns, one store wait, the next K loads, one arrival.  (Computing
+// the values before the wait holds them across it, which at this warp
+// count's register budget costs more in spills than it hides.)
 __device__ __forceinline__ bool gen_stage(GenCtx &G, KRegs &ka, KRegs &kb, int st, long long g, int &s,
                                           uint32_t &u)
 {
     const int b = 2 * st;
     if (b >= G.n_blk) return true;
     const bool two = b + 1 < G.n_blk;
-    if (g >= kAStages && !wwait(&G.c_empty[s], (u + 1) & 1, G.s_err, ERR_WAIT_GEN)) return false;
     int bi1 = G.bi, bj1 = G.bj0 + kBlkPairs;               // the second block's (i, j0)
     if (bj1 > bi1) { bi1++; bj1 = 0; }
+    if (g >= kAStages && !wwait(&G.c_empty[s], (u + 1) & 1, G.s_err, ERR_WAIT_GEN)) return false;
     if (G.active) {
         tc_fence_after();
-        const uint32_t base = G.tmem + G.lane_base + (uint32_t)(s * 64 + 16 * G.half);
-        gen_block(base, ka, G.xr, G.bi, G.bj0 + 8 * G.half, G.lo_half);
-        if (two) gen_block(base + 32, kb, G.xr, bi1, bj1 + 8 * G.half, G.lo_half);
+        float out[2 * kGP];
+        const uint32_t base = G.tmem + G.lane_base + (uint32_t)(s * 64 + 2 * kGP * G.sub);
+        gen_vals(ka, G.xr, G.bi, G.bj0 + kGP * G.sub, G.lo_half, out);
+        tmem_st_row(base, out);
+        if (two) {
+            gen_vals(kb, G.xr, bi1, bj1 + kGP * G.sub, G.lo_half, out);
+            tmem_st_row(base + 32, out);
+        }
         tmem_st_wait();
         tc_fence_before();
         if (b + 4 < G.n_blk) load_k(ka, G.kbase, b + 4, G.n_cells);
@@ -766,14 +799,17 @@ __device__ __forceinline__ bool gen_pass(GenCtx &G, long long g0, int st_lo, int
 
 // ---- the kernel --------------------------------------------------------------
 //
-// Paired mode (a.paired): each group of 64 slots is served by a cluster of two
-// CTAs.  Both hold the stage inputs of all 64 slots and each streams half of
-// the stages of a pass (its tensor-core work halves); CTA r keeps the
-// integrator state of slots 32 r .. 32 r + 31.  After its MMAs a CTA sends
-// the partial sums of the peer's slots into the peer's shared memory; after
-// the per-slot logic it sends its slots' new stage inputs and cells.  Each
-// exchange is one remote mbarrier arrival (release/acquire at cluster scope).
-// Single mode: one CTA per group, all stages, all slots.
+// Each group of 64 slots is served by a cluster of P CTAs (P = 1, 2, 4 or
+// 8).  All of them hold the stage inputs of all 64 slots and each streams a
+// contiguous P-th of the stages of a pass (its tensor-core work divides by
+// P); CTA r keeps the integrator state of slots SL r .. SL r + SL - 1 (SL =
+// 64 / P).  After its MMAs a CTA sends the partial sums of the other CTAs'
+// slots into their shared memory; after the per-slot logic it sends its own
+// slots' new stage inputs and cells to all of them.  Each exchange ends in
+// one remote mbarrier arrival per sending warp and receiving CTA
+// (release/acquire at cluster scope).  Smaller P loses less to the
+// exchanges; larger P shortens a pass, which bounds the time of the costliest
+// cells once there are fewer cells than slots to keep busy.
 
 __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
 {
@@ -781,26 +817,25 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int NS = a.NS, XS = a.XS, N = a.t.N, n_blk = a.t.n_blk, NBP = a.NBP;
     const int SB = a.SB;
-    const bool paired = a.paired != 0;
-    const int rank = paired ? (int)cluster_rank() : 0;
-    const int peer = rank ^ 1;
-    const int ngrp = paired ? (int)gridDim.x >> 1 : (int)gridDim.x;
-    const int grp = paired ? (int)blockIdx.x >> 1 : (int)blockIdx.x;
-    const int SL = paired ? NS / 2 : NS;                // slots whose state this CTA keeps
-    const int own0 = paired ? rank * SL : 0;
+    const int P = a.P;                                  // CTAs per group (cluster size)
+    const bool clustered = P > 1;
+    const int rank = clustered ? (int)cluster_rank() : 0;
+    const int ngrp = (int)gridDim.x / P;
+    const int grp = (int)blockIdx.x / P;
+    const int SL = NS / P;                              // slots whose state this CTA keeps
+    const int own0 = rank * SL;
     const int half_bytes = NBP * 128;                   // rows of one Bt tile copied
     const int bstride = ((2 * half_bytes + 1023) / 1024) * 1024;   // hi then lo, 1024-aligned
     const int sstride = 2 * bstride;                    // one stage: two blocks
     const int n_st = (n_blk + 1) / 2;                   // stages per pass
-    const int st_h = (n_st + 1) / 2;
-    const int st_lo = paired ? (rank ? st_h : 0) : 0;
-    const int st_hi = paired ? (rank ? n_st : st_h) : n_st;
-    const int my_st = st_hi - st_lo;                    // >= 1 (paired mode needs n_st >= 2)
+    const int st_lo = (int)((long long)rank * n_st / P);
+    const int st_hi = (int)((long long)(rank + 1) * n_st / P);
+    const int my_st = st_hi - st_lo;                    // >= 2 (the launch needs n_st >= 2 P)
     const int b_lo = 2 * st_lo, b_hi = min(n_blk, 2 * st_hi);
     uint8_t *bring = sm;                                // mapping tiles (also the D staging area)
     float *xrows = (float *)(bring + (size_t)SB * sstride);
-    float *dpeer = xrows + (size_t)NS * XS;             // [2][SL][NBP] partial sums from the peer
-    Slot *slots = (Slot *)(dpeer + (paired ? (size_t)2 * SL * NBP : 0));
+    float *dpeer = xrows + (size_t)NS * XS;             // [P-1][2][SL][NBP] partial sums from the others
+    Slot *slots = (Slot *)(dpeer + (size_t)(P - 1) * 2 * SL * NBP);
     uint64_t *bars = (uint64_t *)(slots + NS);
     uint64_t *bt_full = bars, *bt_empty = bars + SB;
     uint64_t *c_full = bars + 2 * SB, *c_empty = bars + 2 * SB + kAStages;
@@ -835,8 +870,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         mbar_init(go, 1);
         mbar_init(gbar, 32 * kGenWarps);
         mbar_init(fin, 1);
-        mbar_init(dx_full, kGenWarps / 2);          // the peer's warps that hold my slots' rows
-        mbar_init(xg_full, kGenWarps);              // every peer generator warp
+        // partial sums: the 4 warps of each other CTA whose rows hold slots
+        // kept here; stage inputs: every generator warp of each other CTA
+        mbar_init(dx_full, clustered ? (kGenWarps / 2) * (P - 1) : 1);
+        mbar_init(xg_full, clustered ? kGenWarps * (P - 1) : 1);
         s_err = 0;
         s_continue = 1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -848,9 +885,9 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     }
     // initial slot fill: group x takes cells x, x + G, .., x + (C - 1) G (C =
     // the cells per group, at most NS): every group a spread of radii, and the
-    // cells' K tables adjacent (position x C + s, see k32_pos).  Both CTAs of a
-    // pair set up the stage inputs of all 64 slots; the state of each slot is
-    // kept by one of them.
+    // cells' K tables adjacent (position x C + s, see k32_pos).  Every CTA of
+    // the cluster sets up the stage inputs of all 64 slots; the state of each
+    // slot is kept by one of them.
     const int C = a.kC;
     if (warp >= 2) {
         for (int s = warp - 2; s < NS; s += kGenWarps) {
@@ -861,7 +898,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     }
     tc_fence_before();
     __syncthreads();
-    if (paired) cluster_sync_all();                   // the peer's barriers exist before any remote arrival
+    if (clustered) cluster_sync_all();                // the others' barriers exist before any remote arrival
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
@@ -951,44 +988,46 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         __syncwarp();
     } else {
         // ---- generators / per-slot epilogue ----
-        const int gt = threadIdx.x - 64;              // 0 .. 255
+        const int gt = threadIdx.x - 64;              // 0 .. 32 kGenWarps - 1
         const int qd = warp & 3;                      // TMEM lane quadrant of this warp
         const int row = 32 * qd + lane;               // TMEM row: slot (row & 63), hi or lo part
         const int slot = row & (kSlots - 1);
         const bool lo_half = row >= kSlots;
         const int part = lo_half ? 1 : 0;
-        const int half = warp >= 6 ? 1 : 0;           // pairs 8 half .. 8 half + 7 of each block
+        const int sub = (warp - 2) / 4;               // pairs kGP sub .. kGP sub + kGP - 1 of each block
         const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
         const float *xr = xrows + (size_t)slot * XS;
-        // this warp's rows belong to slots kept here, or by the peer CTA
-        const bool rows_own = slot >= own0 && slot < own0 + SL;
+        // the CTA that keeps this row's slot, and where its partial sums go:
+        // here [part][slot][bin], or that CTA's buffer [src][part][slot][bin]
+        // for source index src (this CTA's rank among the others)
+        const int owner = slot / SL;
+        const bool rows_own = owner == rank;
+        const int sl_row = slot - owner * SL;
         float *Dsm = (float *)bring;                  // [2][SL][NBP]; the mapping-tile ring is idle then
-        const uint32_t dpeer_remote = paired ? mapa(su32(dpeer), (uint32_t)peer) : 0;
-        const uint32_t xrows_remote = paired ? mapa(su32(xrows), (uint32_t)peer) : 0;
-        const uint32_t slots_remote = paired ? mapa(su32(slots), (uint32_t)peer) : 0;
-        const uint32_t dx_remote = paired ? mapa(su32(dx_full), (uint32_t)peer) : 0;
-        const uint32_t xg_remote = paired ? mapa(su32(xg_full), (uint32_t)peer) : 0;
+        const uint32_t d_remote = rows_own ? 0u :
+            mapa(su32(dpeer), (uint32_t)owner) +
+            (uint32_t)((size_t)(2 * (rank < owner ? rank : rank - 1) * SL) * NBP * 4);
+        // owners of this warp's 32 consecutive slots
+        const int own_lo = (slot - lane) / SL, own_hi = (slot - lane + 31) / SL;
         uint32_t gphase = 0;
         long long g = 0;
         for (int r = 0;; r++) {
             const int cell = slots[slot].cell;        // fixed for the whole pass
             const bool active = __any_sync(0xffffffffu, cell >= 0);
-            const float4 *kbase = reinterpret_cast<const float4 *>(a.K32) + (size_t)(4 * half) * a.kn +
+            const float4 *kbase = reinterpret_cast<const float4 *>(a.K32) + (size_t)(kGC * sub) * a.kn +
                                   k32_pos(cell >= 0 ? cell : 0, ngrp, C);
             GenCtx G;
             G.a = &a; G.tmem = tmem; G.lane_base = lane_base; G.kbase = kbase; G.xr = xr;
             G.c_empty = c_empty; G.c_full = c_full; G.s_err = &s_err; G.n_blk = b_hi;
-            G.half = half; G.lane = lane; G.lo_half = lo_half; G.active = active; G.n_cells = a.kn;
+            G.sub = sub; G.lane = lane; G.lo_half = lo_half; G.active = active; G.n_cells = a.kn;
             const bool ok = gen_pass(G, g, st_lo, st_hi);
             g += my_st;
             if (!ok) break;
-            // ---- epilogue: D (TMEM) -> [part][slot][bin], here or in the peer ----
+            // ---- epilogue: D (TMEM) -> [part][slot][bin], here or in the owner ----
             if (!wwait(done, r & 1, &s_err, ERR_WAIT_EPI)) break;
             tc_fence_after();
             {
-                const int sl = slot - (rows_own ? own0 : (paired ? peer * SL : 0));
-                const int c0 = half * (NBP / 2), c1 = c0 + NBP / 2;
-                for (int cc = c0; cc < c1; cc += 8) {
+                for (int cc = 8 * sub; cc < NBP; cc += 8 * kGenQ) {
                     // compensated (Neumaier) FP32 sum of the accumulators
                     float sum[8], cmp[8];
 #pragma unroll
@@ -1006,33 +1045,36 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     float o[8];
 #pragma unroll
                     for (int z = 0; z < 8; z++) o[z] = sum[z] + cmp[z];
-                    const size_t off = ((size_t)part * SL + sl) * NBP + cc;   // floats
+                    const size_t off = ((size_t)part * SL + sl_row) * NBP + cc;   // floats
                     if (rows_own) {
                         *(float4 *)(Dsm + off) = make_float4(o[0], o[1], o[2], o[3]);
                         *(float4 *)(Dsm + off + 4) = make_float4(o[4], o[5], o[6], o[7]);
                     } else {
-                        st_cluster_v4(dpeer_remote + (uint32_t)(off * 4), o[0], o[1], o[2], o[3]);
-                        st_cluster_v4(dpeer_remote + (uint32_t)(off * 4 + 16), o[4], o[5], o[6], o[7]);
+                        st_cluster_v4(d_remote + (uint32_t)(off * 4), o[0], o[1], o[2], o[3]);
+                        st_cluster_v4(d_remote + (uint32_t)(off * 4 + 16), o[4], o[5], o[6], o[7]);
                     }
                 }
-                if (paired && !rows_own) {
+                if (clustered) {
+                    // one arrival at every other CTA whose slots this warp's rows hold
                     fence_cluster();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive_remote(dx_remote);
+                    if (lane == 0)
+                        for (int o = own_lo; o <= own_hi; o++)
+                            if (o != rank) mbar_arrive_remote(mapa(su32(dx_full), (uint32_t)o));
                 }
             }
             tc_fence_before();
-            if (paired && !cwait(dx_full, r & 1, &s_err, ERR_WAIT_PEER)) break;
+            if (clustered && !cwait(dx_full, r & 1, &s_err, ERR_WAIT_PEER)) break;
             if (!gen_sync(gbar, gphase, &s_err)) break;
             // ---- per-slot integrator logic for the slots kept here ----
             for (int sl = warp - 2; sl < SL; sl += kGenWarps) {
                 const int sidx = own0 + sl;
                 Slot &slr = slots[sidx];
-                // D = sum of the parts (hi rows, lo rows; here and from the peer)
+                // D = sum of the parts (hi rows, lo rows; here, then from the others)
                 float *Drow = Dsm + (size_t)sl * NBP;
                 for (int k = lane; k < N; k += 32) {
                     float v = Drow[k] + Dsm[((size_t)SL + sl) * NBP + k];
-                    if (paired) v += dpeer[(size_t)sl * NBP + k] + dpeer[((size_t)SL + sl) * NBP + k];
+                    for (int q = 0; q < 2 * (P - 1); q++) v += dpeer[((size_t)q * SL + sl) * NBP + k];
                     Drow[k] = v;
                 }
                 __syncwarp();
@@ -1057,20 +1099,26 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     }
                     __syncwarp();
                 }
-                if (paired) {
-                    // the slot's stage input and cell, to the peer
+                if (clustered) {
+                    // the slot's stage input and cell, to every other CTA
                     const float *xs = xrows + (size_t)sidx * XS;
-                    const uint32_t xdst = xrows_remote + (uint32_t)((size_t)sidx * XS * 4);
-                    for (int k = lane; k < N; k += 32) st_cluster_f32(xdst + 4 * k, xs[k]);
-                    if (lane == 0)
-                        st_cluster_s32(slots_remote + (uint32_t)((size_t)sidx * sizeof(Slot) + offsetof(Slot, cell)),
-                                       slr.cell);
+                    const uint32_t xoff = (uint32_t)((size_t)sidx * XS * 4);
+                    const uint32_t coff = (uint32_t)((size_t)sidx * sizeof(Slot) + offsetof(Slot, cell));
+                    const int cell_now = slr.cell;
+                    for (int o = 0; o < P; o++) {
+                        if (o == rank) continue;
+                        const uint32_t xdst = mapa(su32(xrows), (uint32_t)o) + xoff;
+                        for (int k = lane; k < N; k += 32) st_cluster_f32(xdst + 4 * k, xs[k]);
+                        if (lane == 0) st_cluster_s32(mapa(su32(slots), (uint32_t)o) + coff, cell_now);
+                    }
                 }
             }
-            if (paired) {
+            if (clustered) {
                 fence_cluster();
                 __syncwarp();
-                if (lane == 0) mbar_arrive_remote(xg_remote);
+                if (lane == 0)
+                    for (int o = 0; o < P; o++)
+                        if (o != rank) mbar_arrive_remote(mapa(su32(xg_full), (uint32_t)o));
                 if (!cwait(xg_full, r & 1, &s_err, ERR_WAIT_PEER)) break;
             }
             // generic-proxy writes to the stage memory (D staging) must be
@@ -1099,18 +1147,61 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
     }
     if (threadIdx.x == 0 && s_err) atomicCAS(a.err, 0, s_err);
-    // neither CTA of a pair leaves while the other may still write to it
-    if (paired) cluster_sync_all();
+    // no CTA of a cluster leaves while another may still write to it
+    if (clustered) cluster_sync_all();
 }
 
-struct Config { int grid, groups, paired, NS, XS, SB, NBP, nacc, stacked, C; size_t smem; };
+struct Config { int grid, groups, P, NS, XS, SB, NBP, nacc, stacked, C; size_t smem; bool ok; };
 
-Config mixed_config(int n_cells, int N)
+cudaError_t launch_kernel(const Config &cf, const MixedArgs &a, cudaStream_t stream);
+
+// Clusters of P CTAs that can run at once (the launch's groups must all be
+// resident together: a group that started late would find its initial cells
+// untouched).  Asked of the runtime once per device, P and shared-memory size.
+int max_clusters(int P, size_t smem, int n_sm)
 {
-    int dev = 0, n_sm = 148;
+    if (P == 1) return n_sm;
+    struct Entry { int dev, P; size_t smem; int n; };
+    static std::mutex mu;
+    static Entry cache[32];
+    static int n_cache = 0;
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    std::lock_guard<std::mutex> lk(mu);
+    for (int i = 0; i < n_cache; i++)
+        if (cache[i].dev == dev && cache[i].P == P && cache[i].smem == smem) return cache[i].n;
+    int n = 0;
+    cudaError_t e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)(P * (n_sm / P)));
+        lc.blockDim = dim3(kThreads);
+        lc.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)P;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        e = cudaOccupancyMaxActiveClusters(&n, step_mixed_kernel, &lc);
+    }
+    if (e != cudaSuccess) {
+        n = 0;
+        cudaGetLastError();   // clear the error of the refused query (the caller takes a smaller P)
+    }
+    n = std::min(n, n_sm / P);
+    if (n_cache < 32) cache[n_cache++] = {dev, P, smem, n};
+    return n;
+}
+
+// Launch layout for clusters of P CTAs (ok = false when P does not fit: fewer
+// than two mapping-tile stages beside the buffers, fewer than two stages of a
+// pass per CTA, or no cluster of P resident).
+Config config_for(int n_cells, int N, int P, int n_sm)
+{
     Config c;
+    c.P = P;
     c.NS = kSlots;
     const int n16 = ((N + 15) / 16) * 16;
     c.XS = n16 + 4;                              // rows 16 B aligned, 4 words off the bank period
@@ -1127,27 +1218,60 @@ Config mixed_config(int n_cells, int N)
     const size_t tail = (size_t)kSlots * c.XS * 4 + (size_t)kSlots * sizeof(Slot) +
                         8 * (2 * kMaxSB + 2 * kAStages + 6);
     const size_t budget = 232448 - 1024 - 2048;  // opt-in shared memory, alignment, static
-    // paired (two CTAs per group of slots) when two mapping-tile stages fit
-    // next to the buffer for the peer's partial sums, and there are two
-    // stages to share out
-    const size_t dpeer = (size_t)2 * (kSlots / 2) * c.NBP * 4;
-    const int sb_paired = (int)((budget - tail - dpeer) / sstride);
-    c.paired = (sb_paired >= 2 && n_st >= 2) ? 1 : 0;
-    const int SL = c.paired ? kSlots / 2 : kSlots;
-    int SB = c.paired ? sb_paired : (int)((budget - tail) / sstride);
-    SB = std::min(SB, kMaxSB);
+    const int SL = kSlots / P;
+    const size_t dpeer = (size_t)(P - 1) * 2 * SL * c.NBP * 4;   // partial sums from the other CTAs
+    const size_t room = budget > tail + dpeer ? budget - tail - dpeer : 0;
+    int SB = std::min((int)(room / sstride), kMaxSB);
     // the D staging area ([2][slots kept][NBP] floats) aliases the mapping-tile ring
     while ((size_t)SB * sstride < (size_t)2 * SL * c.NBP * 4 && SB < kMaxSB) SB++;
     c.SB = SB;
     // at least 120 KB, so that no two CTAs share an SM (each holds all 512
     // TMEM columns for the whole kernel)
-    c.smem = std::max((size_t)120 * 1024, 1024 + (size_t)SB * sstride + tail + (c.paired ? dpeer : 0));
-    // cells are spread over up to one CTA (pair) per SM (pair of SMs), at least 8 a group
-    const int max_groups = c.paired ? n_sm / 2 : n_sm;
-    c.groups = std::max(1, std::min(max_groups, (n_cells + 7) / 8));
-    c.grid = c.paired ? 2 * c.groups : c.groups;
+    c.smem = std::max((size_t)120 * 1024, 1024 + (size_t)SB * sstride + tail + dpeer);
+    c.ok = P == 1 ? SB >= 1 && (size_t)SB * sstride <= room
+                  : SB >= 2 && (size_t)SB * sstride <= room && n_st >= 2 * P;
+    // cells are spread over up to one cluster per P SMs, at least 8 a group
+    const int mc = P == 1 ? n_sm : (c.ok ? max_clusters(P, c.smem, n_sm) : 0);
+    if (mc < 1) c.ok = false;
+    c.groups = std::max(1, std::min(std::max(mc, 1), (n_cells + 7) / 8));
+    c.grid = P * c.groups;
     c.C = std::min(kSlots, (n_cells + c.groups - 1) / c.groups);
     return c;
+}
+
+int sm_count()
+{
+    int dev = 0, n_sm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    return n_sm;
+}
+
+// The cluster size for a request (0: automatic).  Automatic takes the P of
+// least modelled time: a pass costs about (1/P + 0.05) of a one-CTA pass (the
+// tensor work and per-slot logic divide by P, the exchanges do not), and the
+// passes a group runs are about max(1, n_cells / (3 slots)), the costliest
+// cells taking about three times the mean.  A request that does not fit
+// falls back to the largest smaller P that does.
+Config mixed_config(int n_cells, int N, int P_req)
+{
+    const int n_sm = sm_count();
+    if (P_req > 0) {
+        for (int P = P_req; P >= 1; P /= 2) {
+            Config c = config_for(n_cells, N, P, n_sm);
+            if (c.ok || P == 1) return c;
+        }
+    }
+    Config best = config_for(n_cells, N, 1, n_sm);
+    double best_cost = 1e300;
+    for (int P = 1; P <= 8; P *= 2) {
+        Config c = config_for(n_cells, N, P, n_sm);
+        if (!c.ok && P > 1) continue;
+        const double slots = (double)c.groups * kSlots;
+        const double cost = std::max(1.0, n_cells / (3.0 * slots)) * (1.0 / P + 0.05);
+        if (cost < best_cost) { best_cost = cost; best = c; }
+    }
+    return best;
 }
 
 cudaError_t launch_kernel(const Config &cf, const MixedArgs &a, cudaStream_t stream)
@@ -1158,9 +1282,9 @@ cudaError_t launch_kernel(const Config &cf, const MixedArgs &a, cudaStream_t str
     lc.dynamicSmemBytes = cf.smem;
     lc.stream = stream;
     cudaLaunchAttribute at[1];
-    if (cf.paired) {
+    if (cf.P > 1) {
         at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.x = (unsigned)cf.P;
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
         lc.attrs = at;
@@ -1173,10 +1297,11 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
                          double *dt_cell, const double *replay_h, const long long *replay_n,
                          long long replay_stride)
 {
-    Config cf = mixed_config(c->n_cells, c->N);
-    const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(double);
+    Config cf = mixed_config(c->n_cells, c->N, c->mix_P);
+    const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(float);
     if (need > c->work_bytes) return cudaErrorInvalidValue;
-    if (cf.groups != c->k32_G || cf.C != c->k32_C) return cudaErrorInvalidValue;   // layout of the K tables
+    if (cf.P != c->mix_P || cf.groups != c->k32_G || cf.C != c->k32_C)
+        return cudaErrorInvalidValue;   // layout of the K tables
     cudaError_t e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(c->d_counter + 1, 0, 2 * sizeof(int), c->stream);
@@ -1198,7 +1323,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.out = c->d_out;
     a.err = c->d_counter + 1;
     a.queue = c->d_counter + 2;
-    a.work = c->d_work;
+    a.work = (float *)c->d_work;
     a.rec_dt = mode == MODE_STEP ? c->rec_dt : nullptr;
     a.rec_cap = c->rec_cap;
     a.rec_n = mode == MODE_RHS ? nullptr : c->rec_n;
@@ -1211,7 +1336,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.stacked = cf.stacked;
     a.kC = c->k32_C;
     a.kn = c->k32_n;
-    a.paired = cf.paired;
+    a.P = cf.P;
     a.mode = mode;
     return launch_kernel(cf, a, c->stream);
 }
@@ -1240,10 +1365,11 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
                                      double *dt_cell, bool *too_big)
 {
     *too_big = false;
-    Config cf = mixed_config(c->n_cells, c->N);
-    const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(double);
+    Config cf = mixed_config(c->n_cells, c->N, c->mix_P);
+    const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(float);
     if (need > kStaticScratchBytes) { *too_big = true; return cudaSuccess; }
-    if (cf.groups != c->k32_G || cf.C != c->k32_C) return cudaErrorInvalidValue;   // layout of the K tables
+    if (cf.P != c->mix_P || cf.groups != c->k32_G || cf.C != c->k32_C)
+        return cudaErrorInvalidValue;   // layout of the K tables
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -1281,7 +1407,7 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     a.out = c->d_out;
     a.err = c->d_counter + 1;
     a.queue = c->d_counter + 2;
-    a.work = (double *)scratch;     // every slot is written before it is read
+    a.work = (float *)scratch;      // every slot is written before it is read
     a.rec_dt = c->rec_dt;
     a.rec_cap = c->rec_cap;
     a.rec_n = c->rec_n;
@@ -1294,22 +1420,23 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     a.stacked = cf.stacked;
     a.kC = c->k32_C;
     a.kn = c->k32_n;
-    a.paired = cf.paired;
+    a.P = cf.P;
     a.mode = MODE_STEP;
     return launch_kernel(cf, a, c->stream);
 }
 
-void mixed_layout(int n_cells, int N, int *G, int *C)
+void mixed_layout(int n_cells, int N, int P_req, int *P, int *G, int *C)
 {
-    const Config cf = mixed_config(n_cells, N);
+    const Config cf = mixed_config(n_cells, N, P_req);
+    *P = cf.P;
     *G = cf.groups;
     *C = cf.C;
 }
 
-size_t mixed_workspace_bytes(int n_cells, int N)
+size_t mixed_workspace_bytes(int n_cells, int N, int P)
 {
-    Config cf = mixed_config(n_cells, N);
-    return (size_t)cf.groups * cf.NS * 5 * (size_t)N * sizeof(double);
+    Config cf = mixed_config(n_cells, N, P);
+    return (size_t)cf.groups * cf.NS * 5 * (size_t)N * sizeof(float);
 }
 
 cudaError_t launch_rhs_mixed(const cudisc_coag_ctx *c, const double *rho, double *drho)

@@ -62,6 +62,8 @@ def _params(disc, **over):
     ("kernel_mode", 5, coag.EINVAL),
     ("rho_gas", None, coag.EINVAL),
     ("v_frag", -1.0, coag.EINVAL),
+    ("mixed_cluster", 3, coag.EINVAL),
+    ("mixed_cluster", 16, coag.EINVAL),
 ])
 def test_init_rejects_bad_arguments(field, value, code):
     d = synth.column_1x32()
@@ -93,4 +95,6 @@ def test_null_context_is_an_error_not_a_crash():
     assert L.cudisc_coag_set_v_frag(None, 1.0) == coag.EINVAL
     t = coag.cudisc_timings()
     assert L.cudisc_coag_get_timings(None, C.byref(t)) == coag.EINVAL
+    cl, gr = C.c_int(), C.c_int()
+    assert L.cudisc_coag_mixed_cluster(None, C.byref(cl), C.byref(gr)) == coag.EINVAL
     L.cudisc_coag_destroy(None)

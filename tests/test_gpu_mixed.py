@@ -3,7 +3,8 @@ FP64 CPU oracle, through the C ABI.
 
 Tolerances, derived from the arithmetic: each contraction term carries the
 FP32 rounding of x_i x_j K and K itself (~1e-7) and the TF32 hi/lo split
-(2^-22), and the tensor core accumulates in FP32, so a right-hand side
+(2^-21 of the generated operand, 2^-22 of the mapping coefficients), and the
+tensor core accumulates in FP32, so a right-hand side
 agrees with the oracle to a few 1e-7 of the cell's gross collision flux
 (checked at 3e-6).  Integrated states: |d rho_k| <= 1e-5 |rho_k| + 1e-10 S,
 i.e. 1e-5 relative with the paper's absolute tolerance (1e-10 of the cell's
@@ -141,6 +142,45 @@ def test_free_running_mixed_step(coag_mod, oracle_mod, case):
     check_state(y.cpu().numpy()[cells], want, S)
     # every cell ran to t_span: its accepted steps add up to it
     assert np.allclose(rec["dt"].cpu().numpy().sum(1), d.t_span, rtol=1e-12)
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+def test_cluster_sizes_match_oracle(coag_mod, oracle_mod, cluster):
+    """Every split of a slot group's pass over a cluster of CTAs (the partial
+    sums and stage inputs they exchange): right-hand sides, and a
+    free-running step with slot refills (4736 cells, more than the slots of
+    clusters of 4 or 8) replayed by the oracle on sampled cells."""
+    d = CASES["N40_4736_cells"]()
+    g = coag_mod.Coag(d, "mixed", mixed_cluster=cluster)
+    P, groups = g.mixed_cluster()
+    assert P == cluster and groups >= 1
+    rho = synth.random_state(d, seed=23)
+    out = g.rhs(g.state(rho)).cpu().numpy()
+    cells = sample_of(d, 12)
+    ds = d.subset(cells)
+    o = oracle_mod.Oracle(ds)
+    err = np.abs(out[cells] - o.rhs(rho[cells])) / gross(o, ds, rho[cells])[:, None]
+    assert err.max() < 3e-6, err.max()
+    rec = g.set_records(3000)
+    y = g.state(d.rho0)
+    st = g.step(y, d.t_span)
+    assert st["status"] == 0 and st["n_failed"] == 0
+    assert st["mass_err_max"] < 1e-9
+    n = rec["n"].cpu().numpy()
+    assert st["accepted"] == n.sum()
+    want = o.replay(d.rho0[cells], rec["dt"].cpu().numpy()[cells], n[cells])
+    check_state(y.cpu().numpy()[cells], want, d.rho0[cells].sum(1))
+    assert np.allclose(rec["dt"].cpu().numpy().sum(1), d.t_span, rtol=1e-12)
+
+
+def test_automatic_cluster_choice(coag_mod):
+    """Few cells per slot: the pass is split over more CTAs; many cells: one
+    CTA per group (its exchanges cost more than the split saves)."""
+    few = coag_mod.Coag(CASES["N17_37_cells"](), "mixed")
+    many = coag_mod.Coag(CASES["N20_20000_cells_refill"](), "mixed")
+    assert few.mixed_cluster()[0] >= 2
+    assert many.mixed_cluster()[0] <= 2
+    assert coag_mod.Coag(CASES["N17_37_cells"](), "fp64").mixed_cluster() == (0, 0)
 
 
 def test_mixed_maxsteps_status(coag_mod):

@@ -54,8 +54,10 @@ def test_static_scratch_step_matches_step_twice(coag_mod, disc_fn):
 
 
 def test_static_scratch_rejects_oversized_and_wrong_precision(coag_mod):
+    # one CTA per group: 148 groups x 64 slots x 5 x 100 bins x 4 B > 16 MiB
     big = synth.grid_128x64()
-    g = coag_mod.Coag(big, "mixed")
+    g = coag_mod.Coag(big, "mixed", mixed_cluster=1)
+    assert g.mixed_cluster() == (1, 148)
     y = g.state(big.rho0)
     st, _ = coag_mod.cudisc_coag_step_static_scratch(g.ctx, y.data_ptr(), big.t_span, None, check=False)
     assert st == coag_mod.ENOTSUP
