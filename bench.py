@@ -41,9 +41,14 @@ FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
 # from one ncu capture of the named kernel (summaries under profiles/), valid
 # only for the kernel source they were taken on: a changed source reports null.
 MEASURED_TRAFFIC = {
-    "step_mixed_kernel": {"bytes_per_rhs_eval": (37.402032e9 + 0.584335e9) / 635513,
+    # DRAM read + write of one ncu capture, per unit of work, valid while the
+    # kernel's source file is unchanged
+    "step_mixed_kernel": {"bytes_per_unit": (34.729480e9 + 0.669263e9) / 635513, "unit": "RHS evaluation",
                           "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
-                          "sha256": "2044ad254023c14ae876abf5746734f6f224b950806e9eedbb9e71961f8a6bf8"},
+                          "sha256": "76cc0ed5e4f402cf2c6418505fd1af09b302d38adcef3deaea1caa81fbb79f7c"},
+    "kbuild32_kernel": {"bytes_per_unit": 42.749696e6 + 322.308864e6, "unit": "launch (8192 cells x 100 bins)",
+                        "source": "paper_2402_18471_b300/csrc/kbuild.cu",
+                        "sha256": "546b1915c04cb1a63b2745e1348b8aaa4b5a800f9c85804ca20acd6c004a126e"},
 }
 TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 rate ratio
 
@@ -66,7 +71,7 @@ def measured_traffic(kernel: str, units: float):
     src = os.path.join(ROOT, m["source"])
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != m["sha256"]:
         return None
-    return m["bytes_per_rhs_eval"] * units
+    return m["bytes_per_unit"] * units
 
 
 class ClockSampler:
@@ -343,8 +348,10 @@ def main():
         kb_s = main_res["kb_ms"] / n_steps / 1e3
         kb_bytes = disc.n_cells * Np * (8 if args.precision == "mixed" else 16)
         kb_gbs = kb_bytes / kb_s / 1e9
+        kb_traffic = (measured_traffic("kbuild32_kernel", 1.0)
+                      if args.precision == "mixed" and args.workload == "grid_128x64_N100" else None)
         roof_kb = {"bound": "hbm", "achieved": kb_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                   "frac": kb_gbs / pk["hbm_gbs"], "traffic": None,
+                   "frac": kb_gbs / pk["hbm_gbs"], "traffic": kb_traffic,
                    "kernel": "kbuild32_kernel" if args.precision == "mixed" else "kbuild64_kernel",
                    "ms_per_launch": kb_s * 1e3, "bytes_per_launch": kb_bytes,
                    "peak_src": f"{pk['src']} copy bandwidth"}
