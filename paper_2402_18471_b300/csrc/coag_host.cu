@@ -365,7 +365,7 @@ static void free_ctx(cudisc_coag_ctx *c)
     void *ptrs[] = {c->d_m, c->d_minv, c->d_a, c->d_me, c->d_pair_ij, c->d_row, c->d_ent_p,
                     c->d_ent_ab, c->d_frow, c->d_fent_p, c->d_fent_m, c->d_Ntab, c->d_blk_i,
                     c->d_blk_j0, c->d_Btiles, c->d_prep, c->d_prep32, c->d_scal, c->d_K64,
-                    c->d_K32, c->d_out, c->d_work, c->d_counter, c->d_scal32};
+                    c->d_K32, c->d_Kslot, c->d_out, c->d_work, c->d_counter, c->d_scal32};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -420,9 +420,13 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
             e = cudaMalloc(&c->d_K64, nc * (size_t)c->Np * sizeof(double2));
         else
         {
-            cdc::mixed_layout(c->n_cells, c->N, params->mixed_cluster, &c->mix_P, &c->k32_G, &c->k32_C);
-            c->k32_n = std::max(c->n_cells, c->k32_G * c->k32_C);
-            e = cudaMalloc(&c->d_K32, (size_t)c->k32_n * c->n_blk * cdc::kBlkPairs * sizeof(float2));
+            cdc::mixed_layout(c->n_cells, c->N, params->mixed_cluster, &c->mix_P, &c->mix_G, &c->mix_C);
+            e = cudaMalloc(&c->d_K32, (size_t)c->n_cells * c->n_blk * cdc::kBlkPairs * sizeof(float2));
+            // the slot groups' tables: [group][block][8 chunks][64 slots] x 16 B
+            // (zeroed: slots that never hold a cell multiply zero stage inputs by it)
+            const size_t kslot = (size_t)c->mix_G * c->n_blk * 8 * 64 * sizeof(float4);
+            if (e == cudaSuccess) e = cudaMalloc(&c->d_Kslot, kslot);
+            if (e == cudaSuccess) e = cudaMemset(c->d_Kslot, 0, kslot);
         }
     }
     if (e == cudaSuccess && params->precision == CUDISC_MIXED_TF32) {
@@ -464,7 +468,7 @@ cudisc_status cudisc_coag_mixed_cluster(const cudisc_coag_ctx *c, int *cluster, 
     if (!cluster || !groups) return CUDISC_EINVAL;
     const bool mixed = c->p.precision == CUDISC_MIXED_TF32;
     *cluster = mixed ? c->mix_P : 0;
-    *groups = mixed ? c->k32_G : 0;
+    *groups = mixed ? c->mix_G : 0;
     return CUDISC_OK;
 }
 

@@ -17,24 +17,12 @@ constexpr int kBlkElems = 32;         // TF32 elements per K-block row (a and b 
 constexpr int kMaxMixedBins = 160;    // mixed path: bins up to this (MMA N = bins rounded up to 16)
 constexpr int kMaxGridY = 65535;      // launches over cells are chunked to this
 
-// Layout of the mixed path's FP32 kernel tables {K p_coag, K p_frag}.  The
-// integration kernel's CTA x (of G) starts with cells x, x + G, .. in its
-// slots 0, 1, .. C - 1 (cells of all radii in every CTA); a cell's table
-// sits at its slot position pos = x C + s, so that one CTA's cells are
-// adjacent, and cells past G C (refills) at pos = c.  Per 16-pair block b
-// and 2-pair chunk ch = t / 2 of pair slot q = 16 b + t the 16-byte chunks of
-// all positions are adjacent, [b][ch][pos][2 x float2]: a warp whose lanes
-// hold neighbouring positions reads 512 contiguous bytes.
-__host__ __device__ inline int k32_pos(int c, int G, int C)
-{
-    return c < G * C ? (c % G) * C + c / G : c;
-}
-// float2 index of pair slot q at position pos (n_pos positions in all)
-__host__ __device__ inline size_t k32_index(int pos, int q, int n_pos)
-{
-    const int b = q >> 4, t = q & 15;
-    return ((size_t)(8 * b + (t >> 1)) * n_pos + pos) * 2 + (t & 1);
-}
+// Layout of the mixed path's FP32 kernel tables {K p_coag, K p_frag}:
+// cell-major, n_slots = 16 n_blk pair slots per cell (pair slot q = 16 b + t
+// of block b), so a cell's table is 8 n_slots contiguous bytes.  The
+// integration kernel copies the table of each cell it takes into its slot
+// group's buffer (see the mixed kernel).
+__host__ __device__ inline size_t k32_index(int c, int q, int n_slots) { return (size_t)c * n_slots + q; }
 
 // Per-cell scalars produced by the prep kernel (FP64).
 struct CellScal {
@@ -109,9 +97,9 @@ struct cudisc_coag_ctx {
     cdc::CellScal *d_scal = nullptr;   // [n_cells]
     float4 *d_scal32 = nullptr;        // [n_cells] {delta, Vg2, etavK, ZOm} in FP32
     double2 *d_K64 = nullptr;          // [n_cells][Np]      {K, K p_frag}
-    float2 *d_K32 = nullptr;           // k32_n x n_blk x 16 {K p_coag, K p_frag}, see k32_index
-    int k32_G = 1, k32_C = 1, k32_n = 0;   // its layout: slot groups, initial cells per group, positions
-    int mix_P = 1;                     // CTAs per slot group of the mixed kernel
+    float2 *d_K32 = nullptr;           // n_cells x n_blk x 16 {K p_coag, K p_frag}, see k32_index
+    float4 *d_Kslot = nullptr;         // mixed kernel: [group][block][8 chunks][64 slots] of the slots' tables
+    int mix_P = 1, mix_G = 1, mix_C = 1;   // mixed kernel: CTAs per slot group, groups, initial cells per group
     // integration workspace
     cdc::CellOut *d_out = nullptr;     // [n_cells]
     double *d_work = nullptr;          // mixed path slot state

@@ -189,46 +189,38 @@ enum { KB_INVA = P3_COUNT, KB_INVQ, KB_COUNT };
 
 // FP32 builder in the blocked pair layout of the mixed contraction: slot
 // q = 16 b + t is pair (blk_i[b], blk_j0[b] + t) and holds {K p_c, K p_f}
-// (stored cell-interleaved, see k32_index)
+// (cell-major, see k32_index)
 // (p_c = 1 - p_f, each accurate to a few ulp of itself, so that neither
 // coagulation in a fragmentation-dominated cell nor fragmentation in a
 // coagulation-dominated one is lost to rounding); slots past the diagonal
-// hold zeros.  One CTA per kPosTile consecutive table positions (the cells
-// at those positions, see k32_pos): their per-bin fields are staged in
-// shared memory once; each thread then produces four consecutive slots of a
-// block (same i, j .. j+3) of one cell and writes them as two 16-byte
-// chunks.  Neighbouring threads take neighbouring positions, so each store
-// instruction writes whole 128-byte lines of the interleaved table.  The
+// hold zeros.  One CTA per kPosTile consecutive cells, one warp per cell:
+// the cells' per-bin fields are staged in shared memory once; each thread
+// then produces four consecutive slots of a block (same i, j .. j+3) and
+// writes them as two 16-byte chunks, a warp 1 KB of its cell's table per
+// store pair.  The
 // larger Stokes number of a pair (i, j <= i) is always St_i: St = rho_m a
 // Omega / (rho_g v_th) rises with the bin's size.  Divisions, the square
 // root and the exponential use the hardware approximations: K stays within
 // 1e-6 and K p_frag within 1e-5 of FP64.
 //   Physical = physical kernel and fragmentation probability (the other
 //   modes are the closed-form test kernels); HasVdust = input velocities.
-constexpr int kPosTile = 8;
+constexpr int kPosTile = 8;                 // cells per CTA (one per warp of 256 threads)
 
-// words of shared memory per cell: KB_COUNT fields of NR, padded to 4 mod 32
-// so that the tile's cells fall in distinct banks
-__host__ __device__ inline int kb_cell_stride(int NR) { return (KB_COUNT * NR + 27) / 32 * 32 + 4; }
+// words of shared memory per cell: KB_COUNT fields of NR, rounded to 16 bytes
+__host__ __device__ inline int kb_cell_stride(int NR) { return (KB_COUNT * NR + 3) / 4 * 4; }
 
 template <bool Physical, bool HasVdust>
 __global__ void __launch_bounds__(256) kbuild32_kernel(
     float kc, float v_frag, int kernel_mode, int frag_mode, int n_cells, int N, int NR,
-    int n_slots, int kG, int kC, int kn, const int *__restrict__ blk_i, const int *__restrict__ blk_j0,
+    int n_slots, const int *__restrict__ blk_i, const int *__restrict__ blk_j0,
     const float *__restrict__ prep32, const float4 *__restrict__ scal32,
     float2 *__restrict__ Kout)
 {
     extern __shared__ __align__(16) float f32s[];       // [kPosTile][cell stride]: [KB_COUNT][NR] each
     const int CS = kb_cell_stride(NR);
-    const int pos0 = blockIdx.x * kPosTile;
+    const int cell0 = blockIdx.x * kPosTile;
     __shared__ int s_cell[kPosTile];
-    if (threadIdx.x < kPosTile) {
-        // the cell at position pos (inverse of k32_pos), or -1
-        const int pos = pos0 + threadIdx.x;
-        int c = pos;
-        if (pos < kG * kC) c = pos / kC + (pos % kC) * kG;
-        s_cell[threadIdx.x] = (pos < kn && c < n_cells) ? c : -1;
-    }
+    if (threadIdx.x < kPosTile) s_cell[threadIdx.x] = cell0 + threadIdx.x < n_cells ? cell0 + threadIdx.x : -1;
     __syncthreads();
     for (int t = threadIdx.x; t < kPosTile * P3_COUNT * NR; t += blockDim.x) {
         const int jc = t / (P3_COUNT * NR), r = t - jc * (P3_COUNT * NR);
@@ -245,7 +237,7 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
         F[KB_INVQ * NR + k] = 1.0f / (1.0f + S);
     }
     __syncthreads();
-    const int jc = threadIdx.x % kPosTile;                // this thread's cell of the tile
+    const int jc = threadIdx.x >> 5;                      // this warp's cell of the tile
     const int c = s_cell[jc];
     if (c < 0) return;
     const float *F = f32s + jc * CS;
@@ -254,8 +246,8 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
     const float vf2 = 1.5f * v_frag * v_frag;
     const float *St = F + P3_ST * NR, *U = F + P3_U * NR, *Aa = F + P3_A * NR;
     const float *IA = F + KB_INVA * NR, *IQ = F + KB_INVQ * NR;
-    float4 *dst = reinterpret_cast<float4 *>(Kout) + pos0 + jc;   // chunk (b, ch): (8 b + ch) kn + pos
-    for (int g = threadIdx.x / kPosTile; 4 * g < n_slots; g += blockDim.x / kPosTile) {
+    float4 *dst = reinterpret_cast<float4 *>(Kout) + (size_t)c * (n_slots / 2);   // the cell's 2-pair chunks
+    for (int g = threadIdx.x & 31; 4 * g < n_slots; g += 32) {
         const int q0 = 4 * g;
         const int b = q0 >> 4;
         const int i = __ldg(blk_i + b);
@@ -342,13 +334,12 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
             o[2 * u] = live ? K * pc : 0.0f;
             o[2 * u + 1] = live ? K * pf : 0.0f;
         }
-        const size_t ch0 = (size_t)(8 * b + ((q0 & 15) >> 1));  // the group's first 2-pair chunk
-        dst[ch0 * kn] = make_float4(o[0], o[1], o[2], o[3]);
-        dst[(ch0 + 1) * kn] = make_float4(o[4], o[5], o[6], o[7]);
+        dst[2 * g] = make_float4(o[0], o[1], o[2], o[3]);
+        dst[2 * g + 1] = make_float4(o[4], o[5], o[6], o[7]);
     }
 }
 
-__global__ void get_kernel_kernel(int c0, int n_cells, int Np, int precision, int kG, int kC, int kn,
+__global__ void get_kernel_kernel(int c0, int n_cells, int Np, int precision, int n_slots,
                                   const unsigned int *__restrict__ pij,
                                   const double2 *__restrict__ K64,
                                   const float2 *__restrict__ K32, double *__restrict__ K,
@@ -367,7 +358,7 @@ __global__ void get_kernel_kernel(int c0, int n_cells, int Np, int precision, in
         int row0 = 0;
         for (int r = 0; r < i; r++) row0 += (r + 16) >> 4;
         const int q = (row0 + (j >> 4)) * 16 + (j & 15);
-        float2 v = K32[k32_index(k32_pos(c, kG, kC), q, kn)];   // {K p_c, K p_f}
+        float2 v = K32[k32_index(c, q, n_slots)];   // {K p_c, K p_f}
         k = (double)v.x + (double)v.y; kf = v.y;
     }
     K[(size_t)c * Np + p] = k;
@@ -408,9 +399,9 @@ cudaError_t launch_kbuild(const cudisc_coag_ctx *c)
                          : (vd ? kbuild32_kernel<false, true> : kbuild32_kernel<false, false>);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<(c->k32_n + kPosTile - 1) / kPosTile, 256, smem, c->stream>>>(
+        kern<<<(c->n_cells + kPosTile - 1) / kPosTile, 256, smem, c->stream>>>(
             (float)p.kernel_const, (float)p.v_frag, p.kernel_mode, p.frag_mode, c->n_cells, c->N, NR,
-            n_slots, c->k32_G, c->k32_C, c->k32_n, c->d_blk_i, c->d_blk_j0, c->d_prep32, c->d_scal32,
+            n_slots, c->d_blk_i, c->d_blk_j0, c->d_prep32, c->d_scal32,
             c->d_K32);
     }
     return cudaGetLastError();
@@ -421,7 +412,7 @@ cudaError_t launch_get_kernel(const cudisc_coag_ctx *c, double *K, double *KF)
     for (int c0 = 0; c0 < c->n_cells; c0 += kMaxGridY) {
     dim3 grid((c->Np + 255) / 256, std::min(kMaxGridY, c->n_cells - c0));
     get_kernel_kernel<<<grid, 256, 0, c->stream>>>(c0, c->n_cells, c->Np, c->p.precision,
-                                                   c->k32_G, c->k32_C, c->k32_n, c->d_pair_ij,
+                                                   c->n_blk * kBlkPairs, c->d_pair_ij,
                                                    c->d_K64, c->d_K32, K, KF);
     }
     return cudaGetLastError();

@@ -57,6 +57,8 @@ constexpr int kSlots = 64;                        // cell slots per CTA (TMEM ro
 constexpr int kAStages = 3;                       // generated-operand stages in TMEM (two blocks, 64 columns each)
 constexpr int kMaxMain = 8;                       // TMEM accumulators for the products with Bt_hi
 constexpr int kMaxSB = 4;                         // mapping-tile ring depth (stages of two blocks), at most
+constexpr int kMaxKS = 4;                         // K-table ring depth (stages of two blocks), at most
+constexpr int kKBlkBytes = 16 * 8 * 64;           // K tables of one block for 64 slots: 8 chunks x 64 x 16 B
 constexpr int kThreads = 64 + 32 * kGenWarps;
 constexpr int kLaneBins = (kMaxMixedBins + 31) / 32;   // bins per lane in the per-slot logic
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
@@ -69,7 +71,8 @@ enum ErrCode { ERR_WAIT_PRODUCER = 1, ERR_WAIT_MMA = 2, ERR_WAIT_GEN = 3, ERR_WA
 
 struct MixedArgs {
     DevTables t;
-    const float2 *K32;          // [n_cells][n_blk*16]
+    const float4 *K32;          // [n_cells][n_blk * 8] 2-pair chunks (k32_index)
+    float4 *Kslot;              // [groups][n_blk][8][64]: the tables of the cells in each group's slots
     double *rho;                // state in/out (STEP, REPLAY) or input (RHS)
     double *drho;               // output (RHS)
     double t_span;
@@ -90,7 +93,8 @@ struct MixedArgs {
     int *rec_status;
     int NS, XS, mode;
     int SB, NBP;                // mapping-tile ring depth; bins padded to 16 (MMA N, tile rows copied)
-    int kC, kn;                 // K table layout: initial cells per group, positions (k32_pos)
+    int kC;                     // initial cells per group (slot s of group x starts with cell x + s G)
+    int KS;                     // K-table ring depth
     int P;                      // CTAs per group of slots (a cluster of 1, 2, 4 or 8; see the kernel)
     int nacc;                   // TMEM accumulators for the products with Bt_hi (stacked: with [Bt_hi; Bt_lo])
     int stacked;                // 1: one MMA of N = 2 NBP takes Bt_hi and Bt_lo together (2 NBP <= 256)
@@ -261,21 +265,7 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8])
                    "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
                  : "memory");
 }
-// Store 16 consecutive 32-bit columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,"
-                 "%9,%10,%11,%12,%13,%14,%15,%16};"
-                 ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
-                   "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])),
-                   "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
-                   "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
-                   "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
-                   "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
-                 : "memory");
-}
 __device__ __forceinline__ void tmem_st_row(uint32_t taddr, const float (&v)[8]) { tmem_st8(taddr, v); }
-__device__ __forceinline__ void tmem_st_row(uint32_t taddr, const float (&v)[16]) { tmem_st16(taddr, v); }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
@@ -362,9 +352,24 @@ __device__ __forceinline__ void pair_add(float &h, float &l, float x)
     two_sum(s, __fadd_rn(e, l), h, l);
 }
 
+// Copy cell c's K table into the slot's column of its group's buffer
+// ([block][chunk][slot] x 16 B, one bulk copy per block for the producer),
+// then make the generic-proxy stores visible to those copies.
+__device__ void slot_copy_k(const MixedArgs &a, int slot, int c)
+{
+    const int lane = threadIdx.x & 31;
+    const int n_ch = a.t.n_blk * 8;                  // 2-pair chunks of a table
+    const float4 *src = a.K32 + (size_t)c * n_ch;
+    float4 *dst = a.Kslot + (size_t)(blockIdx.x / a.P) * n_ch * kSlots + slot;
+#pragma unroll 4
+    for (int i = lane; i < n_ch; i += 32) dst[(size_t)i * kSlots] = __ldg(src + i);
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncwarp();
+}
+
 // Load cell c into slot: state, scales, phase 0 (or mark the slot empty).
 // owner = false: only the stage-input row and the cell id (a slot whose
-// integrator state another CTA of the cluster keeps).
+// integrator state, and K-table copy, another CTA of the cluster keeps).
 __device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, int c, bool owner = true)
 {
     const int N = a.t.N, lane = threadIdx.x & 31;
@@ -373,6 +378,7 @@ __device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, i
         if (lane == 0) sl.cell = -1;
         return;
     }
+    if (owner) slot_copy_k(a, slot, c);
     SlotBufs B = slot_bufs(a, slot);
     const double *rc = a.rho + (size_t)c * N;
     double s = 0.0, sa = 0.0;
@@ -667,27 +673,9 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
 // every block (a kGenQ-th of its 16).  a = x_i x_j K p_coag, b = x_i x_j K
 // p_frag, split hi = rn_tf32(v), lo = v - hi; the thread keeps the
 // half its row holds and writes the 2 kGP values into the stage's TMEM
-// columns.
-struct KRegs { float4 v[kGC]; };         // {K p_coag, K p_frag} of kGP pairs
-
-// The thread's 2-pair chunks of block b: kbase points at its first chunk of
-// block 0 of its cell; chunks are n_cells float4 apart, blocks 8 n_cells.
-__device__ __forceinline__ void load_k(KRegs &k, const float4 *kbase, int b, int n_cells)
-{
-    const float4 *src = kbase + (size_t)b * 8 * n_cells;
-    uint64_t pol;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-#pragma unroll
-    for (int q = 0; q < kGC; q++) {
-        float4 r;
-        asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
-                     : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(src + (size_t)q * n_cells), "l"(pol));
-        k.v[q] = r;
-    }
-}
-
-__device__ __forceinline__ void gen_vals(const KRegs &kr, const float *xr, int bi, int jfirst, bool lo_half,
-                                         float (&out)[2 * kGP])
+// columns.  kv: the thread's 2-pair chunks {K p_c, K p_f, K p_c, K p_f}.
+__device__ __forceinline__ void gen_vals(const float4 (&kc)[kGC], const float *xr, int bi, int jfirst,
+                                         bool lo_half, float (&out)[2 * kGP])
 {
     const float xi = xr[bi];
     float xj[kGP];
@@ -696,7 +684,7 @@ __device__ __forceinline__ void gen_vals(const KRegs &kr, const float *xr, int b
         const float4 x4 = *(const float4 *)(xr + jfirst + u);
         xj[u] = x4.x; xj[u + 1] = x4.y; xj[u + 2] = x4.z; xj[u + 3] = x4.w;
     }
-    const float *kv = (const float *)kr.v;
+    const float *kv = (const float *)kc;
     if (lo_half) {
 #pragma unroll
         for (int u = 0; u < kGP; u++) {
@@ -717,59 +705,70 @@ __device__ __forceinline__ void gen_vals(const KRegs &kr, const float *xr, int b
     }
 }
 
-// One pass of a generator warp over all blocks, a stage of two a step.  K loads
-// run four blocks ahead in four register sets used in rotation by an unrolled
-// loop (no copies of registers whose loads are still in flight); a warp whose
-// rows have no cell only takes part in the stage hand-over (its TMEM rows
-// feed accumulator rows nobody reads).
+// One pass of a generator warp over its blocks, a stage of two a step.  The
+// stage's K tables (all 64 slots, [block][chunk][slot] x 16 B) arrive in a
+// shared-memory ring filled by the producer's bulk copies; a warp whose rows
+// have no cell only takes part in the hand-overs (its TMEM rows feed
+// accumulator rows nobody reads).
 struct GenCtx {
     const MixedArgs *a;
     uint32_t tmem, lane_base;
-    const float4 *kbase;
+    const uint8_t *kring;                // K ring: KS stages of 2 x kKBlkBytes
     const float *xr;
-    uint64_t *c_empty, *c_full;
+    uint64_t *c_empty, *c_full, *k_full, *k_empty;
     volatile int *s_err;
-    int n_blk, sub, lane, n_cells;       // sub: which kGP pairs of each block
+    int n_blk, sub, lane, slot, KS;      // sub: which kGP pairs of each block
     bool lo_half, active;
     int bi, bj0;                         // pair row and first column of the next block
+    int s, ks;                           // TMEM stage and K-ring stage of the next stage
+    uint32_t u, ku;                      // their ring rounds
 };
 
 // One pipeline stage = two blocks (b = 2 st, 2 st + 1; the last stage of a
-// pass may hold one): one wait, two products-and-splits into the stage's 64
-// TMEM columns, one store wait, the next K loads, one arrival.  (Computing
-// the values before the wait holds them across it, which at this warp
-// count's register budget costs more in spills than it hides.)
-__device__ __forceinline__ bool gen_stage(GenCtx &G, KRegs &ka, KRegs &kb, int st, long long g, int &s,
-                                          uint32_t &u)
+// pass may hold one): the waits for its K tables and its TMEM columns, two
+// products-and-splits into the stage's 64 TMEM columns, one store wait, one
+// arrival on each ring.
+__device__ __forceinline__ bool gen_stage(GenCtx &G, int st, long long g)
 {
     const int b = 2 * st;
     if (b >= G.n_blk) return true;
     const bool two = b + 1 < G.n_blk;
     int bi1 = G.bi, bj1 = G.bj0 + kBlkPairs;               // the second block's (i, j0)
     if (bj1 > bi1) { bi1++; bj1 = 0; }
-    if (g >= kAStages && !wwait(&G.c_empty[s], (u + 1) & 1, G.s_err, ERR_WAIT_GEN)) return false;
+    if (!wwait(&G.k_full[G.ks], G.ku & 1, G.s_err, ERR_WAIT_GEN)) return false;
+    if (g >= kAStages && !wwait(&G.c_empty[G.s], (G.u + 1) & 1, G.s_err, ERR_WAIT_GEN)) return false;
     if (G.active) {
         tc_fence_after();
+        // this thread's chunks 2 sub .. 2 sub + kGC - 1 of its slot, both blocks
+        const float4 *kp = reinterpret_cast<const float4 *>(G.kring + (size_t)G.ks * 2 * kKBlkBytes) +
+                           (size_t)(kGC * G.sub) * kSlots + G.slot;
+        float4 kc[kGC];
         float out[2 * kGP];
-        const uint32_t base = G.tmem + G.lane_base + (uint32_t)(s * 64 + 2 * kGP * G.sub);
-        gen_vals(ka, G.xr, G.bi, G.bj0 + kGP * G.sub, G.lo_half, out);
+        const uint32_t base = G.tmem + G.lane_base + (uint32_t)(G.s * 64 + 2 * kGP * G.sub);
+#pragma unroll
+        for (int q = 0; q < kGC; q++) kc[q] = kp[q * kSlots];
+        gen_vals(kc, G.xr, G.bi, G.bj0 + kGP * G.sub, G.lo_half, out);
         tmem_st_row(base, out);
         if (two) {
-            gen_vals(kb, G.xr, bi1, bj1 + kGP * G.sub, G.lo_half, out);
+#pragma unroll
+            for (int q = 0; q < kGC; q++) kc[q] = kp[kKBlkBytes / 16 + q * kSlots];
+            gen_vals(kc, G.xr, bi1, bj1 + kGP * G.sub, G.lo_half, out);
             tmem_st_row(base + 32, out);
         }
         tmem_st_wait();
         tc_fence_before();
-        if (b + 4 < G.n_blk) load_k(ka, G.kbase, b + 4, G.n_cells);
-        if (b + 5 < G.n_blk) load_k(kb, G.kbase, b + 5, G.n_cells);
     }
     __syncwarp();
-    if (G.lane == 0) mbar_arrive(&G.c_full[s]);
+    if (G.lane == 0) {
+        mbar_arrive(&G.c_full[G.s]);
+        mbar_arrive(&G.k_empty[G.ks]);
+    }
     // blocks run along rows: (i, 0), (i, 16), .. while j0 <= i, then (i + 1, 0)
     G.bi = bi1;
     G.bj0 = bj1 + kBlkPairs;
     if (G.bj0 > G.bi) { G.bi++; G.bj0 = 0; }
-    if (++s == kAStages) { s = 0; u++; }
+    if (++G.s == kAStages) { G.s = 0; G.u++; }
+    if (++G.ks == G.KS) { G.ks = 0; G.ku++; }
     return true;
 }
 
@@ -780,20 +779,8 @@ __device__ __forceinline__ bool gen_pass(GenCtx &G, long long g0, int st_lo, int
     const int b0 = 2 * st_lo;
     G.bi = __ldg(G.a->t.blk_i + b0);
     G.bj0 = __ldg(G.a->t.blk_j0 + b0);
-    KRegs k0, k1, k2, k3;
-    if (G.active) {
-        load_k(k0, G.kbase, b0, G.n_cells);
-        if (b0 + 1 < G.n_blk) load_k(k1, G.kbase, b0 + 1, G.n_cells);
-        if (b0 + 2 < G.n_blk) load_k(k2, G.kbase, b0 + 2, G.n_cells);
-        if (b0 + 3 < G.n_blk) load_k(k3, G.kbase, b0 + 3, G.n_cells);
-    }
-    int s = (int)(g0 % kAStages);
-    uint32_t u = (uint32_t)(g0 / kAStages);
-    for (int st = st_lo; st < st_hi; st += 2) {
-        const long long g = g0 + (st - st_lo);
-        if (!gen_stage(G, k0, k1, st, g, s, u)) return false;
-        if (st + 1 < st_hi && !gen_stage(G, k2, k3, st + 1, g + 1, s, u)) return false;
-    }
+    for (int st = st_lo; st < st_hi; st++)
+        if (!gen_stage(G, st, g0 + (st - st_lo))) return false;
     return true;
 }
 
@@ -832,8 +819,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     const int st_hi = (int)((long long)(rank + 1) * n_st / P);
     const int my_st = st_hi - st_lo;                    // >= 2 (the launch needs n_st >= 2 P)
     const int b_lo = 2 * st_lo, b_hi = min(n_blk, 2 * st_hi);
+    const int KS = a.KS;
     uint8_t *bring = sm;                                // mapping tiles (also the D staging area)
-    float *xrows = (float *)(bring + (size_t)SB * sstride);
+    uint8_t *kring = bring + (size_t)SB * sstride;      // K tables of the slots, KS stages of two blocks
+    float *xrows = (float *)(kring + (size_t)KS * 2 * kKBlkBytes);
     float *dpeer = xrows + (size_t)NS * XS;             // [P-1][2][SL][NBP] partial sums from the others
     Slot *slots = (Slot *)(dpeer + (size_t)(P - 1) * 2 * SL * NBP);
     uint64_t *bars = (uint64_t *)(slots + NS);
@@ -841,6 +830,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     uint64_t *c_full = bars + 2 * SB, *c_empty = bars + 2 * SB + kAStages;
     uint64_t *done = bars + 2 * SB + 2 * kAStages, *go = done + 1, *gbar = done + 2, *fin = done + 3;
     uint64_t *dx_full = done + 4, *xg_full = done + 5;
+    uint64_t *k_full = done + 6, *k_empty = done + 6 + KS;
     __shared__ uint32_t s_tmem;
     __shared__ int s_err, s_continue;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -874,6 +864,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         // kept here; stage inputs: every generator warp of each other CTA
         mbar_init(dx_full, clustered ? (kGenWarps / 2) * (P - 1) : 1);
         mbar_init(xg_full, clustered ? kGenWarps * (P - 1) : 1);
+        for (int s = 0; s < KS; s++) {
+            mbar_init(&k_full[s], 1);
+            mbar_init(&k_empty[s], kGenWarps);
+        }
         s_err = 0;
         s_continue = 1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -884,10 +878,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     // initial slot fill: group x takes cells x, x + G, .., x + (C - 1) G (C =
-    // the cells per group, at most NS): every group a spread of radii, and the
-    // cells' K tables adjacent (position x C + s, see k32_pos).  Every CTA of
-    // the cluster sets up the stage inputs of all 64 slots; the state of each
-    // slot is kept by one of them.
+    // the cells per group, at most NS): every group a spread of radii.  Every
+    // CTA of the cluster sets up the stage inputs of all 64 slots; the state
+    // of each slot, and the copy of its cell's K table into the group's
+    // buffer, is done by the one that keeps it.
     const int C = a.kC;
     if (warp >= 2) {
         for (int s = warp - 2; s < NS; s += kGenWarps) {
@@ -903,35 +897,71 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     const uint32_t tmem = s_tmem;
 
     if (warp == 0) {
-        // ---- producer: mapping tiles (rows 0..NBP-1 of hi and lo) by the bulk-copy engine ----
-        long long g = 0;
-        int ps = 0;
-        uint32_t pu = 0;
-        for (int r = 0;; r++) {
-            if (r > 0) {
-                if (!wwait(go, (r - 1) & 1, &s_err, ERR_WAIT_PRODUCER)) break;
-                if (!s_continue) break;
-            }
+        // ---- producer, one thread: the bulk-copy engine fills two rings, the
+        // slots' K tables (needed first, by the generators; up to KS stages
+        // ahead) and the mapping tiles (rows 0..NBP-1 of hi and lo, for the
+        // MMAs; up to SB stages ahead).  Each ring is refilled as soon as its
+        // oldest stage is released, without waiting on the other ----
+        if (lane == 0) {
+            long long g = 0, gk = 0;
+            int ps = 0, ks = 0;
+            uint32_t pu = 0, ku = 0;
+            const float4 *kgrp = a.Kslot + (size_t)grp * n_blk * 8 * kSlots;   // this group's tables
             bool ok = true;
-            for (int st = st_lo; st < st_hi; st++, g++) {
-                const int s = ps;
-                const uint32_t u = pu;
-                if (++ps == SB) { ps = 0; pu++; }      // ring position without divisions
-                if (g >= SB && !wwait(&bt_empty[s], (u + 1) & 1, &s_err, ERR_WAIT_PRODUCER)) { ok = false; break; }
-                if (lane == 0) {
-                    const int nb = 2 * st + 1 < n_blk ? 2 : 1;
-                    mbar_expect_tx(&bt_full[s], (uint32_t)(nb * 2 * half_bytes));
-                    for (int q = 0; q < nb; q++) {
-                        uint8_t *dst = bring + (size_t)s * sstride + (size_t)q * bstride;
-                        const uint8_t *src = (const uint8_t *)(a.t.Btiles + (size_t)(2 * st + q) * (2 * half_bytes / 16));
-                        bulk_g2s(dst, src, half_bytes, &bt_full[s]);
-                        bulk_g2s(dst + half_bytes, src + half_bytes, half_bytes, &bt_full[s]);
+            for (int r = 0; ok; r++) {
+                if (r > 0) {
+                    if (!twait(go, (r - 1) & 1, &s_err, ERR_WAIT_PRODUCER)) break;
+                    if (!s_continue) break;
+                }
+                int nt = 0, nk = 0;                     // tile and K stages of this pass issued
+                long long t_last = clock64();
+                for (int it = 0; nt < my_st; it++) {
+                    bool progress = false;
+                    if (nk < my_st && (gk < KS || mbar_test(&k_empty[ks], (ku + 1) & 1))) {
+                        const int sk = st_lo + nk;
+                        const int nb = 2 * sk + 1 < n_blk ? 2 : 1;
+                        mbar_expect_tx(&k_full[ks], (uint32_t)(nb * kKBlkBytes));
+                        for (int q = 0; q < nb; q++)
+                            bulk_g2s(kring + ((size_t)ks * 2 + q) * kKBlkBytes,
+                                     kgrp + (size_t)(2 * sk + q) * 8 * kSlots, kKBlkBytes, &k_full[ks]);
+                        nk++;
+                        gk++;
+                        if (++ks == KS) { ks = 0; ku++; }
+                        progress = true;
+                    }
+                    if (nt < nk && (g < SB || mbar_test(&bt_empty[ps], (pu + 1) & 1))) {
+                        const int st = st_lo + nt;
+                        const int nb = 2 * st + 1 < n_blk ? 2 : 1;
+                        mbar_expect_tx(&bt_full[ps], (uint32_t)(nb * 2 * half_bytes));
+                        for (int q = 0; q < nb; q++) {
+                            uint8_t *dst = bring + (size_t)ps * sstride + (size_t)q * bstride;
+                            const uint8_t *src =
+                                (const uint8_t *)(a.t.Btiles + (size_t)(2 * st + q) * (2 * half_bytes / 16));
+                            bulk_g2s(dst, src, half_bytes, &bt_full[ps]);
+                            bulk_g2s(dst + half_bytes, src + half_bytes, half_bytes, &bt_full[ps]);
+                        }
+                        nt++;
+                        g++;
+                        if (++ps == SB) { ps = 0; pu++; }
+                        progress = true;
+                    }
+                    if (progress) {
+                        t_last = clock64();
+                    } else {
+                        __nanosleep(32);
+                        if ((it & 63) == 63) {
+                            if (*(volatile int *)&s_err) { ok = false; break; }
+                            if (clock64() - t_last > kWaitCycles) {
+                                atomicCAS(&s_err, 0, ERR_WAIT_PRODUCER);
+                                ok = false;
+                                break;
+                            }
+                        }
                     }
                 }
-                __syncwarp();
             }
-            if (!ok) break;
         }
+        __syncwarp();
     } else if (warp == 1) {
         // ---- MMA issuer: one thread (the tensor pipe's queue is shallow, so
         // the issuing thread does nothing between MMAs that it can avoid) ----
@@ -1011,15 +1041,16 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         const int own_lo = (slot - lane) / SL, own_hi = (slot - lane + 31) / SL;
         uint32_t gphase = 0;
         long long g = 0;
+        GenCtx G;                                     // ring positions carry over between passes
+        G.a = &a; G.tmem = tmem; G.lane_base = lane_base; G.kring = kring; G.xr = xr;
+        G.c_empty = c_empty; G.c_full = c_full; G.k_full = k_full; G.k_empty = k_empty;
+        G.s_err = &s_err; G.n_blk = b_hi; G.sub = sub; G.lane = lane; G.slot = slot; G.KS = KS;
+        G.lo_half = lo_half; G.active = false; G.bi = G.bj0 = 0;
+        G.s = 0; G.ks = 0; G.u = 0; G.ku = 0;
         for (int r = 0;; r++) {
             const int cell = slots[slot].cell;        // fixed for the whole pass
             const bool active = __any_sync(0xffffffffu, cell >= 0);
-            const float4 *kbase = reinterpret_cast<const float4 *>(a.K32) + (size_t)(kGC * sub) * a.kn +
-                                  k32_pos(cell >= 0 ? cell : 0, ngrp, C);
-            GenCtx G;
-            G.a = &a; G.tmem = tmem; G.lane_base = lane_base; G.kbase = kbase; G.xr = xr;
-            G.c_empty = c_empty; G.c_full = c_full; G.s_err = &s_err; G.n_blk = b_hi;
-            G.sub = sub; G.lane = lane; G.lo_half = lo_half; G.active = active; G.n_cells = a.kn;
+            G.active = active;
             const bool ok = gen_pass(G, g, st_lo, st_hi);
             g += my_st;
             if (!ok) break;
@@ -1151,7 +1182,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     if (clustered) cluster_sync_all();
 }
 
-struct Config { int grid, groups, P, NS, XS, SB, NBP, nacc, stacked, C; size_t smem; bool ok; };
+struct Config { int grid, groups, P, NS, XS, SB, KS, NBP, nacc, stacked, C; size_t smem; bool ok; };
 
 cudaError_t launch_kernel(const Config &cf, const MixedArgs &a, cudaStream_t stream);
 
@@ -1216,20 +1247,26 @@ Config config_for(int n_cells, int N, int P, int n_sm)
     const int n_st = (n_blk + 1) / 2;
     const size_t sstride = 2 * (((2 * (size_t)c.NBP * 128 + 1023) / 1024) * 1024);   // a stage: two blocks
     const size_t tail = (size_t)kSlots * c.XS * 4 + (size_t)kSlots * sizeof(Slot) +
-                        8 * (2 * kMaxSB + 2 * kAStages + 6);
+                        8 * (2 * kMaxSB + 2 * kAStages + 6 + 2 * kMaxKS);
     const size_t budget = 232448 - 1024 - 2048;  // opt-in shared memory, alignment, static
     const int SL = kSlots / P;
     const size_t dpeer = (size_t)(P - 1) * 2 * SL * c.NBP * 4;   // partial sums from the other CTAs
     const size_t room = budget > tail + dpeer ? budget - tail - dpeer : 0;
-    int SB = std::min((int)(room / sstride), kMaxSB);
+    // the rings: the fewest mapping-tile stages that overlap (two, one for a
+    // single CTA that fits no more), then K-table stages (they come from
+    // DRAM), then more tile stages
+    const int sb_min = P > 1 ? 2 : (room >= 2 * sstride + 2 * (size_t)kKBlkBytes ? 2 : 1);
+    const size_t kstage = 2 * (size_t)kKBlkBytes;
+    const int KS = room > sb_min * sstride ? std::min(kMaxKS, (int)((room - sb_min * sstride) / kstage)) : 0;
+    int SB = KS >= 1 ? std::min(kMaxSB, (int)((room - KS * kstage) / sstride)) : 0;
     // the D staging area ([2][slots kept][NBP] floats) aliases the mapping-tile ring
     while ((size_t)SB * sstride < (size_t)2 * SL * c.NBP * 4 && SB < kMaxSB) SB++;
     c.SB = SB;
+    c.KS = KS;
     // at least 120 KB, so that no two CTAs share an SM (each holds all 512
     // TMEM columns for the whole kernel)
-    c.smem = std::max((size_t)120 * 1024, 1024 + (size_t)SB * sstride + tail + dpeer);
-    c.ok = P == 1 ? SB >= 1 && (size_t)SB * sstride <= room
-                  : SB >= 2 && (size_t)SB * sstride <= room && n_st >= 2 * P;
+    c.smem = std::max((size_t)120 * 1024, 1024 + (size_t)SB * sstride + KS * kstage + tail + dpeer);
+    c.ok = KS >= 1 && SB >= sb_min && (size_t)SB * sstride + KS * kstage <= room && (P == 1 || n_st >= 2 * P);
     // cells are spread over up to one cluster per P SMs, at least 8 a group
     const int mc = P == 1 ? n_sm : (c.ok ? max_clusters(P, c.smem, n_sm) : 0);
     if (mc < 1) c.ok = false;
@@ -1300,7 +1337,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     Config cf = mixed_config(c->n_cells, c->N, c->mix_P);
     const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(float);
     if (need > c->work_bytes) return cudaErrorInvalidValue;
-    if (cf.P != c->mix_P || cf.groups != c->k32_G || cf.C != c->k32_C)
+    if (cf.P != c->mix_P || cf.groups != c->mix_G || cf.C != c->mix_C)
         return cudaErrorInvalidValue;   // layout of the K tables
     cudaError_t e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
     if (e != cudaSuccess) return e;
@@ -1308,7 +1345,8 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     if (e != cudaSuccess) return e;
     MixedArgs a;
     a.t = c->tables();
-    a.K32 = c->d_K32;
+    a.K32 = reinterpret_cast<const float4 *>(c->d_K32);
+    a.Kslot = c->d_Kslot;
     a.rho = rho;
     a.drho = drho;
     a.t_span = t_span;
@@ -1334,8 +1372,8 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.NBP = cf.NBP;
     a.nacc = cf.nacc;
     a.stacked = cf.stacked;
-    a.kC = c->k32_C;
-    a.kn = c->k32_n;
+    a.kC = c->mix_C;
+    a.KS = cf.KS;
     a.P = cf.P;
     a.mode = mode;
     return launch_kernel(cf, a, c->stream);
@@ -1368,7 +1406,7 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     Config cf = mixed_config(c->n_cells, c->N, c->mix_P);
     const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(float);
     if (need > kStaticScratchBytes) { *too_big = true; return cudaSuccess; }
-    if (cf.P != c->mix_P || cf.groups != c->k32_G || cf.C != c->k32_C)
+    if (cf.P != c->mix_P || cf.groups != c->mix_G || cf.C != c->mix_C)
         return cudaErrorInvalidValue;   // layout of the K tables
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1392,7 +1430,8 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     if (e != cudaSuccess) return e;
     MixedArgs a;
     a.t = c->tables();
-    a.K32 = c->d_K32;
+    a.K32 = reinterpret_cast<const float4 *>(c->d_K32);
+    a.Kslot = c->d_Kslot;
     a.rho = rho;
     a.drho = nullptr;
     a.t_span = t_span;
@@ -1418,8 +1457,8 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     a.NBP = cf.NBP;
     a.nacc = cf.nacc;
     a.stacked = cf.stacked;
-    a.kC = c->k32_C;
-    a.kn = c->k32_n;
+    a.kC = c->mix_C;
+    a.KS = cf.KS;
     a.P = cf.P;
     a.mode = MODE_STEP;
     return launch_kernel(cf, a, c->stream);

@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kVjpThreads) vjp_kernel(VjpArgs<T> A)
 template <typename T>
 __global__ void __launch_bounds__(256) kderiv_kernel(
     int c0, int n_cells, int N, int Np, int kernel_mode, int frag_mode, double v_frag,
-    const unsigned int *__restrict__ pij, const int *__restrict__ pair_q, int kG, int kC, int kn,
+    const unsigned int *__restrict__ pij, const int *__restrict__ pair_q, int n_slots,
     const double *__restrict__ a, const double *__restrict__ minv,
     const double *__restrict__ prep, const CellScal *__restrict__ scal,
     const double *__restrict__ alpha, const double2 *__restrict__ K64,
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(256) kderiv_kernel(
     double K, KF;
     if (K64) { const double2 v = K64[(size_t)c * Np + p]; K = v.x; KF = v.y; }
     else {   // mixed tables hold {K p_c, K p_f}
-        const float2 v = K32[k32_index(k32_pos(c, kG, kC), pair_q[p], kn)];
+        const float2 v = K32[k32_index(c, pair_q[p], n_slots)];
         K = (double)v.x + (double)v.y;
         KF = v.y;
     }
@@ -563,7 +563,7 @@ cudaError_t launch_t(cudisc_coag_ctx *c, VjpState *S, const double *rho0, const 
         dim3 grid((Np + 255) / 256, std::min(kMaxGridY, c->n_cells - c0));
         kderiv_kernel<T><<<grid, 256, 0, c->stream>>>(
             c0, c->n_cells, N, Np, p.kernel_mode, p.frag_mode, p.v_frag, c->d_pair_ij, S->pair_q,
-            c->k32_G, c->k32_C, c->k32_n, c->d_a, c->d_minv, c->d_prep, c->d_scal, p.alpha, c->d_K64,
+            c->n_blk * kBlkPairs, c->d_a, c->d_minv, c->d_prep, c->d_scal, p.alpha, c->d_K64,
             c->d_K32, kt);
     }
     VjpArgs<T> A;
