@@ -361,8 +361,16 @@ __device__ void slot_copy_k(const MixedArgs &a, int slot, int c)
     const int n_ch = a.t.n_blk * 8;                  // 2-pair chunks of a table
     const float4 *src = a.K32 + (size_t)c * n_ch;
     float4 *dst = a.Kslot + (size_t)(blockIdx.x / a.P) * n_ch * kSlots + slot;
-#pragma unroll 4
-    for (int i = lane; i < n_ch; i += 32) dst[(size_t)i * kSlots] = __ldg(src + i);
+    // eight loads in flight per lane, then their stores
+    int i0 = lane;
+    for (; i0 + 7 * 32 < n_ch; i0 += 8 * 32) {
+        float4 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) v[j] = __ldg(src + i0 + 32 * j);
+#pragma unroll
+        for (int j = 0; j < 8; j++) dst[(size_t)(i0 + 32 * j) * kSlots] = v[j];
+    }
+    for (int i = i0; i < n_ch; i += 32) dst[(size_t)i * kSlots] = __ldg(src + i);
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncwarp();
 }
