@@ -831,14 +831,15 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     uint8_t *bring = sm;                                // mapping tiles (also the D staging area)
     uint8_t *kring = bring + (size_t)SB * sstride;      // K tables of the slots, KS stages of two blocks
     float *xrows = (float *)(kring + (size_t)KS * 2 * kKBlkBytes);
-    float *dpeer = xrows + (size_t)NS * XS;             // [P-1][2][SL][NBP] partial sums from the others
-    Slot *slots = (Slot *)(dpeer + (size_t)(P - 1) * 2 * SL * NBP);
+    float *dpeer = xrows + (size_t)NS * XS;             // [P-1][SL][NBP] partial sums from the others
+    Slot *slots = (Slot *)(dpeer + (size_t)(P - 1) * SL * NBP);
     uint64_t *bars = (uint64_t *)(slots + NS);
     uint64_t *bt_full = bars, *bt_empty = bars + SB;
     uint64_t *c_full = bars + 2 * SB, *c_empty = bars + 2 * SB + kAStages;
     uint64_t *done = bars + 2 * SB + 2 * kAStages, *go = done + 1, *gbar = done + 2, *fin = done + 3;
     uint64_t *dx_full = done + 4, *xg_full = done + 5;
     uint64_t *k_full = done + 6, *k_empty = done + 6 + KS;
+    uint64_t *pair_full = k_empty + KS;                 // [kGenWarps / 2]: a lo-row warp's sums are in Dlo
     __shared__ uint32_t s_tmem;
     __shared__ int s_err, s_continue;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -868,14 +869,16 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         mbar_init(go, 1);
         mbar_init(gbar, 32 * kGenWarps);
         mbar_init(fin, 1);
-        // partial sums: the 4 warps of each other CTA whose rows hold slots
-        // kept here; stage inputs: every generator warp of each other CTA
-        mbar_init(dx_full, clustered ? (kGenWarps / 2) * (P - 1) : 1);
+        // partial sums: the kGenQ hi-row warps of each other CTA whose rows
+        // hold slots kept here; stage inputs: every generator warp of each
+        // other CTA
+        mbar_init(dx_full, clustered ? kGenQ * (P - 1) : 1);
         mbar_init(xg_full, clustered ? kGenWarps * (P - 1) : 1);
         for (int s = 0; s < KS; s++) {
             mbar_init(&k_full[s], 1);
             mbar_init(&k_empty[s], kGenWarps);
         }
+        for (int s = 0; s < kGenWarps / 2; s++) mbar_init(&pair_full[s], 1);
         s_err = 0;
         s_continue = 1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1031,20 +1034,21 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         const int row = 32 * qd + lane;               // TMEM row: slot (row & 63), hi or lo part
         const int slot = row & (kSlots - 1);
         const bool lo_half = row >= kSlots;
-        const int part = lo_half ? 1 : 0;
         const int sub = (warp - 2) / 4;               // pairs kGP sub .. kGP sub + kGP - 1 of each block
         const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
         const float *xr = xrows + (size_t)slot * XS;
         // the CTA that keeps this row's slot, and where its partial sums go:
-        // here [part][slot][bin], or that CTA's buffer [src][part][slot][bin]
-        // for source index src (this CTA's rank among the others)
+        // here [slot][bin], or that CTA's buffer [src][slot][bin] for source
+        // index src (this CTA's rank among the others)
         const int owner = slot / SL;
         const bool rows_own = owner == rank;
         const int sl_row = slot - owner * SL;
-        float *Dsm = (float *)bring;                  // [2][SL][NBP]; the mapping-tile ring is idle then
+        float *Dsm = (float *)bring;                  // [SL][NBP]; the mapping-tile ring is idle then
+        float *Dlo = Dsm + (size_t)SL * NBP;          // [64][NBP]: the lo-row sums of every slot
+        const int pair = (qd & 1) * kGenQ + sub;      // the hi-row / lo-row warp pair of these slots and columns
         const uint32_t d_remote = rows_own ? 0u :
             mapa(su32(dpeer), (uint32_t)owner) +
-            (uint32_t)((size_t)(2 * (rank < owner ? rank : rank - 1) * SL) * NBP * 4);
+            (uint32_t)((size_t)((rank < owner ? rank : rank - 1) * SL) * NBP * 4);
         // owners of this warp's 32 consecutive slots
         const int own_lo = (slot - lane) / SL, own_hi = (slot - lane + 31) / SL;
         uint32_t gphase = 0;
@@ -1062,10 +1066,15 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             const bool ok = gen_pass(G, g, st_lo, st_hi);
             g += my_st;
             if (!ok) break;
-            // ---- epilogue: D (TMEM) -> [part][slot][bin], here or in the owner ----
+            // ---- epilogue: D (TMEM) -> [slot][bin], here or in the owner.  The
+            // lo-row warp of each column group leaves its sums in Dlo; the
+            // hi-row warp of the same slots and columns adds them and sends
+            // one row per slot ----
             if (!wwait(done, r & 1, &s_err, ERR_WAIT_EPI)) break;
             tc_fence_after();
+            bool epi_ok = true;
             {
+                bool got_lo = false;
                 for (int cc = 8 * sub; cc < NBP; cc += 8 * kGenQ) {
                     // compensated (Neumaier) FP32 sum of the accumulators
                     float sum[8], cmp[8];
@@ -1084,7 +1093,20 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     float o[8];
 #pragma unroll
                     for (int z = 0; z < 8; z++) o[z] = sum[z] + cmp[z];
-                    const size_t off = ((size_t)part * SL + sl_row) * NBP + cc;   // floats
+                    float *lo_at = Dlo + (size_t)slot * NBP + cc;
+                    if (lo_half) {
+                        *(float4 *)lo_at = make_float4(o[0], o[1], o[2], o[3]);
+                        *(float4 *)(lo_at + 4) = make_float4(o[4], o[5], o[6], o[7]);
+                        continue;
+                    }
+                    if (!got_lo) {
+                        if (!wwait(&pair_full[pair], r & 1, &s_err, ERR_WAIT_EPI)) { epi_ok = false; break; }
+                        got_lo = true;
+                    }
+                    const float4 la = *(const float4 *)lo_at, lb = *(const float4 *)(lo_at + 4);
+                    o[0] += la.x; o[1] += la.y; o[2] += la.z; o[3] += la.w;
+                    o[4] += lb.x; o[5] += lb.y; o[6] += lb.z; o[7] += lb.w;
+                    const size_t off = (size_t)sl_row * NBP + cc;   // floats
                     if (rows_own) {
                         *(float4 *)(Dsm + off) = make_float4(o[0], o[1], o[2], o[3]);
                         *(float4 *)(Dsm + off + 4) = make_float4(o[4], o[5], o[6], o[7]);
@@ -1093,15 +1115,22 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                         st_cluster_v4(d_remote + (uint32_t)(off * 4 + 16), o[4], o[5], o[6], o[7]);
                     }
                 }
-                if (clustered) {
-                    // one arrival at every other CTA whose slots this warp's rows hold
-                    fence_cluster();
+                if (lo_half) {
                     __syncwarp();
-                    if (lane == 0)
-                        for (int o = own_lo; o <= own_hi; o++)
-                            if (o != rank) mbar_arrive_remote(mapa(su32(dx_full), (uint32_t)o));
+                    if (lane == 0) mbar_arrive(&pair_full[pair]);
+                } else if (epi_ok) {
+                    if (!got_lo && !wwait(&pair_full[pair], r & 1, &s_err, ERR_WAIT_EPI)) epi_ok = false;
+                    if (epi_ok && clustered) {
+                        // one arrival at every other CTA whose slots this warp's rows hold
+                        fence_cluster();
+                        __syncwarp();
+                        if (lane == 0)
+                            for (int o = own_lo; o <= own_hi; o++)
+                                if (o != rank) mbar_arrive_remote(mapa(su32(dx_full), (uint32_t)o));
+                    }
                 }
             }
+            if (!epi_ok) break;
             tc_fence_before();
             if (clustered && !cwait(dx_full, r & 1, &s_err, ERR_WAIT_PEER)) break;
             if (!gen_sync(gbar, gphase, &s_err)) break;
@@ -1109,12 +1138,14 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             for (int sl = warp - 2; sl < SL; sl += kGenWarps) {
                 const int sidx = own0 + sl;
                 Slot &slr = slots[sidx];
-                // D = sum of the parts (hi rows, lo rows; here, then from the others)
+                // D = sum of the partial rows (here, then from the others)
                 float *Drow = Dsm + (size_t)sl * NBP;
-                for (int k = lane; k < N; k += 32) {
-                    float v = Drow[k] + Dsm[((size_t)SL + sl) * NBP + k];
-                    for (int q = 0; q < 2 * (P - 1); q++) v += dpeer[((size_t)q * SL + sl) * NBP + k];
-                    Drow[k] = v;
+                if (clustered) {
+                    for (int k = lane; k < N; k += 32) {
+                        float v = Drow[k];
+                        for (int q = 0; q < P - 1; q++) v += dpeer[((size_t)q * SL + sl) * NBP + k];
+                        Drow[k] = v;
+                    }
                 }
                 __syncwarp();
                 if (slr.cell >= 0) {
@@ -1255,10 +1286,10 @@ Config config_for(int n_cells, int N, int P, int n_sm)
     const int n_st = (n_blk + 1) / 2;
     const size_t sstride = 2 * (((2 * (size_t)c.NBP * 128 + 1023) / 1024) * 1024);   // a stage: two blocks
     const size_t tail = (size_t)kSlots * c.XS * 4 + (size_t)kSlots * sizeof(Slot) +
-                        8 * (2 * kMaxSB + 2 * kAStages + 6 + 2 * kMaxKS);
+                        8 * (2 * kMaxSB + 2 * kAStages + 6 + 2 * kMaxKS + kGenWarps / 2);
     const size_t budget = 232448 - 1024 - 2048;  // opt-in shared memory, alignment, static
     const int SL = kSlots / P;
-    const size_t dpeer = (size_t)(P - 1) * 2 * SL * c.NBP * 4;   // partial sums from the other CTAs
+    const size_t dpeer = (size_t)(P - 1) * SL * c.NBP * 4;   // partial sums from the other CTAs
     const size_t room = budget > tail + dpeer ? budget - tail - dpeer : 0;
     // the rings: the fewest mapping-tile stages that overlap (two, one for a
     // single CTA that fits no more), then K-table stages (they come from
@@ -1267,8 +1298,8 @@ Config config_for(int n_cells, int N, int P, int n_sm)
     const size_t kstage = 2 * (size_t)kKBlkBytes;
     const int KS = room > sb_min * sstride ? std::min(kMaxKS, (int)((room - sb_min * sstride) / kstage)) : 0;
     int SB = KS >= 1 ? std::min(kMaxSB, (int)((room - KS * kstage) / sstride)) : 0;
-    // the D staging area ([2][slots kept][NBP] floats) aliases the mapping-tile ring
-    while ((size_t)SB * sstride < (size_t)2 * SL * c.NBP * 4 && SB < kMaxSB) SB++;
+    // the D staging areas ([slots kept + 64][NBP] floats) alias the mapping-tile ring
+    while ((size_t)SB * sstride < (size_t)(SL + kSlots) * c.NBP * 4 && SB < kMaxSB) SB++;
     c.SB = SB;
     c.KS = KS;
     // at least 120 KB, so that no two CTAs share an SM (each holds all 512
