@@ -245,7 +245,7 @@ static cudisc_status build_tables(cudisc_coag_ctx *c)
     c->n_blk = (int)blk_i.size();
     const bool mixed = p.precision == CUDISC_MIXED_TF32;
     std::vector<float> tiles;
-    const int NBP = (N + 15) / 16 * 16;
+    const int NBP = cdc::mixed_nbp(N);
     if (mixed) tiles.assign((size_t)c->n_blk * 2 * NBP * cdc::kBlkElems, 0.0f);
 
     std::vector<dd> colA(N), colB(N);

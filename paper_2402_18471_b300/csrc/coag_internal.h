@@ -24,6 +24,16 @@ constexpr int kMaxGridY = 65535;      // launches over cells are chunked to this
 // group's buffer (see the mixed kernel).
 __host__ __device__ inline size_t k32_index(int c, int q, int n_slots) { return (size_t)c * n_slots + q; }
 
+// Rows of each mapping tile of the mixed contraction (the bins, padded):
+// up to 128 bins the hi and lo tiles form one MMA operand of N = 2 NBP,
+// which needs NBP to be a multiple of 8; above, each is its own operand of
+// N = NBP, a multiple of 16.
+inline int mixed_nbp(int N)
+{
+    const int n8 = (N + 7) / 8 * 8;
+    return 2 * n8 <= 256 ? n8 : (N + 15) / 16 * 16;
+}
+
 // Per-cell scalars produced by the prep kernel (FP64).
 struct CellScal {
     double kT8pi;   // 8 k_B T / pi  (Eq. vbrown numerator per unit mass sum)

@@ -95,6 +95,7 @@ struct MixedArgs {
     int SB, NBP;                // mapping-tile ring depth; bins padded to 16 (MMA N, tile rows copied)
     int kC;                     // initial cells per group (slot s of group x starts with cell x + s G)
     int KS;                     // K-table ring depth
+    int sst_off;                // byte offset of the per-slot state in shared memory, or -1: in work
     int P;                      // CTAs per group of slots (a cluster of 1, 2, 4 or 8; see the kernel)
     int nacc;                   // TMEM accumulators for the products with Bt_hi (stacked: with [Bt_hi; Bt_lo])
     int stacked;                // 1: one MMA of N = 2 NBP takes Bt_hi and Bt_lo together (2 NBP <= 256)
@@ -316,7 +317,15 @@ __device__ __forceinline__ float tf32_rn(float v)
 
 // ---- per-slot logic (one warp per slot, lanes over bins) ------------------
 
-// Slot state in global scratch (5 N floats per slot): the state y / Sx as an unevaluated float pair yh + yl (48 significant
+// Dynamic shared memory of the kernel (aligned to 1024 B where it is used).
+extern __shared__ __align__(1024) uint8_t smem_raw[];
+__device__ __forceinline__ uint8_t *smem_base()
+{
+    return (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+}
+
+// Slot state (5 N floats per slot kept by this CTA), in shared memory when
+// it fits beside the rings, else in global scratch: the state y / Sx as an unevaluated float pair yh + yl (48 significant
 // bits; yh, the state rounded to FP32, is also the stage input), and the stage
 // right-hand sides in the same scaled units (kx = f / Sx = Sx D).  B300
 // executes FP64 at a small fraction of its FP32 rate, so the per-step work
@@ -331,8 +340,15 @@ struct SlotBufs { float *yh, *yl, *k1, *k2, *k3; };
 __device__ __forceinline__ SlotBufs slot_bufs(const MixedArgs &a, int slot)
 {
     const int N = a.t.N;
-    const int grp = (int)blockIdx.x / a.P;
-    float *f = a.work + ((size_t)grp * a.NS + slot) * 5 * (size_t)N;
+    float *f;
+    if (a.sst_off >= 0) {
+        // the CTA keeps slots SL r .. SL r + SL - 1: index slot mod SL
+        const int SL = a.NS / a.P;
+        f = (float *)(smem_base() + a.sst_off) + (size_t)(slot % SL) * 5 * N;
+    } else {
+        const int grp = (int)blockIdx.x / a.P;
+        f = a.work + ((size_t)grp * a.NS + slot) * 5 * (size_t)N;
+    }
     return {f, f + N, f + 2 * N, f + 3 * N, f + 4 * N};
 }
 
@@ -808,8 +824,7 @@ __device__ __forceinline__ bool gen_pass(GenCtx &G, long long g0, int st_lo, int
 
 __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
 {
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sm = smem_base();
     const int NS = a.NS, XS = a.XS, N = a.t.N, n_blk = a.t.n_blk, NBP = a.NBP;
     const int SB = a.SB;
     const int P = a.P;                                  // CTAs per group (cluster size)
@@ -830,7 +845,9 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     const int KS = a.KS;
     uint8_t *bring = sm;                                // mapping tiles (also the D staging area)
     uint8_t *kring = bring + (size_t)SB * sstride;      // K tables of the slots, KS stages of two blocks
-    float *xrows = (float *)(kring + (size_t)KS * 2 * kKBlkBytes);
+    // (per-slot state at sm + a.sst_off, after the K ring, when it is in shared memory)
+    float *xrows = (float *)(kring + (size_t)KS * 2 * kKBlkBytes +
+                             (a.sst_off >= 0 ? (size_t)SL * 5 * N * sizeof(float) : 0));
     float *dpeer = xrows + (size_t)NS * XS;             // [P-1][SL][NBP] partial sums from the others
     Slot *slots = (Slot *)(dpeer + (size_t)(P - 1) * SL * NBP);
     uint64_t *bars = (uint64_t *)(slots + NS);
@@ -1221,7 +1238,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     if (clustered) cluster_sync_all();
 }
 
-struct Config { int grid, groups, P, NS, XS, SB, KS, NBP, nacc, stacked, C; size_t smem; bool ok; };
+struct Config { int grid, groups, P, NS, XS, SB, KS, NBP, nacc, stacked, C, sst_off; size_t smem; bool ok; };
 
 cudaError_t launch_kernel(const Config &cf, const MixedArgs &a, cudaStream_t stream);
 
@@ -1275,12 +1292,12 @@ Config config_for(int n_cells, int N, int P, int n_sm)
     c.NS = kSlots;
     const int n16 = ((N + 15) / 16) * 16;
     c.XS = n16 + 4;                              // rows 16 B aligned, 4 words off the bank period
-    c.NBP = n16;
+    c.NBP = mixed_nbp(N);                        // (the generators read x up to index n16 - 1)
     // TMEM: 512 columns = generated stages + (nacc + 1) accumulators of NBP,
     // or stacked (MMA N = 2 NBP at most 256) nacc accumulators of 2 NBP
-    c.stacked = 2 * n16 <= 256 ? 1 : 0;
-    c.nacc = c.stacked ? std::max(1, std::min(kMaxMain, (512 - kAStages * 64) / (2 * n16)))
-                       : std::max(1, std::min(kMaxMain, (512 - kAStages * 64) / n16 - 1));
+    c.stacked = 2 * c.NBP <= 256 ? 1 : 0;
+    c.nacc = c.stacked ? std::max(1, std::min(kMaxMain, (512 - kAStages * 64) / (2 * c.NBP)))
+                       : std::max(1, std::min(kMaxMain, (512 - kAStages * 64) / c.NBP - 1));
     int n_blk = 0;
     for (int i = 0; i < N; i++) n_blk += (i + kBlkPairs) / kBlkPairs;
     const int n_st = (n_blk + 1) / 2;
@@ -1291,21 +1308,32 @@ Config config_for(int n_cells, int N, int P, int n_sm)
     const int SL = kSlots / P;
     const size_t dpeer = (size_t)(P - 1) * SL * c.NBP * 4;   // partial sums from the other CTAs
     const size_t room = budget > tail + dpeer ? budget - tail - dpeer : 0;
-    // the rings: the fewest mapping-tile stages that overlap (two, one for a
-    // single CTA that fits no more), then K-table stages (they come from
-    // DRAM), then more tile stages
-    const int sb_min = P > 1 ? 2 : (room >= 2 * sstride + 2 * (size_t)kKBlkBytes ? 2 : 1);
+    // the rings and the per-slot state: the fewest mapping-tile stages that
+    // overlap (two, one for a single CTA that fits no more), two K-table
+    // stages (they come from DRAM), then the per-slot state if it fits (its
+    // per-step reads and writes stay on chip), then more K and tile stages
     const size_t kstage = 2 * (size_t)kKBlkBytes;
-    const int KS = room > sb_min * sstride ? std::min(kMaxKS, (int)((room - sb_min * sstride) / kstage)) : 0;
-    int SB = KS >= 1 ? std::min(kMaxSB, (int)((room - KS * kstage) / sstride)) : 0;
+    const size_t state = (size_t)SL * 5 * N * sizeof(float);
+    const int sb_min = P > 1 ? 2 : (room >= 2 * sstride + kstage ? 2 : 1);
+    size_t avail = room > sb_min * sstride ? room - sb_min * sstride : 0;
+    int KS = (int)std::min<size_t>(2, avail / kstage);
+    avail -= KS * kstage;
+    const bool st_smem = KS >= 2 && avail >= state;
+    if (st_smem) avail -= state;
+    const int KSx = (int)std::min<size_t>(kMaxKS - KS, avail / kstage);
+    KS += KSx;
+    avail -= KSx * kstage;
+    int SB = sb_min + (int)std::min<size_t>(kMaxSB - sb_min, avail / sstride);
     // the D staging areas ([slots kept + 64][NBP] floats) alias the mapping-tile ring
     while ((size_t)SB * sstride < (size_t)(SL + kSlots) * c.NBP * 4 && SB < kMaxSB) SB++;
     c.SB = SB;
     c.KS = KS;
+    c.sst_off = st_smem ? (int)((size_t)SB * sstride + KS * kstage) : -1;
+    const size_t used = (size_t)SB * sstride + KS * kstage + (st_smem ? state : 0);
     // at least 120 KB, so that no two CTAs share an SM (each holds all 512
     // TMEM columns for the whole kernel)
-    c.smem = std::max((size_t)120 * 1024, 1024 + (size_t)SB * sstride + KS * kstage + tail + dpeer);
-    c.ok = KS >= 1 && SB >= sb_min && (size_t)SB * sstride + KS * kstage <= room && (P == 1 || n_st >= 2 * P);
+    c.smem = std::max((size_t)120 * 1024, 1024 + used + tail + dpeer);
+    c.ok = KS >= 1 && SB >= sb_min && used <= room && (P == 1 || n_st >= 2 * P);
     // cells are spread over up to one cluster per P SMs, at least 8 a group
     const int mc = P == 1 ? n_sm : (c.ok ? max_clusters(P, c.smem, n_sm) : 0);
     if (mc < 1) c.ok = false;
@@ -1413,6 +1441,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.stacked = cf.stacked;
     a.kC = c->mix_C;
     a.KS = cf.KS;
+    a.sst_off = cf.sst_off;
     a.P = cf.P;
     a.mode = mode;
     return launch_kernel(cf, a, c->stream);
@@ -1498,6 +1527,7 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     a.stacked = cf.stacked;
     a.kC = c->mix_C;
     a.KS = cf.KS;
+    a.sst_off = cf.sst_off;
     a.P = cf.P;
     a.mode = MODE_STEP;
     return launch_kernel(cf, a, c->stream);
