@@ -165,10 +165,6 @@ __device__ __forceinline__ void st_cluster_v4(uint32_t addr, float a, float b, f
     asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
                  : "memory");
 }
-__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v)
-{
-    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
-}
 __device__ __forceinline__ void st_cluster_s32(uint32_t addr, int v)
 {
     asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
@@ -1158,11 +1154,18 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                 // D = sum of the partial rows (here, then from the others)
                 float *Drow = Dsm + (size_t)sl * NBP;
                 if (clustered) {
-                    for (int k = lane; k < N; k += 32) {
-                        float v = Drow[k];
-                        for (int q = 0; q < P - 1; q++) v += dpeer[((size_t)q * SL + sl) * NBP + k];
-                        Drow[k] = v;
+                    float v[kLaneBins];
+#pragma unroll
+                    for (int m = 0; m < kLaneBins; m++) v[m] = lane + 32 * m < N ? Drow[lane + 32 * m] : 0.f;
+                    for (int q = 0; q < P - 1; q++) {
+                        const float *dp = dpeer + ((size_t)q * SL + sl) * NBP;
+#pragma unroll
+                        for (int m = 0; m < kLaneBins; m++)
+                            if (lane + 32 * m < N) v[m] += dp[lane + 32 * m];
                     }
+#pragma unroll
+                    for (int m = 0; m < kLaneBins; m++)
+                        if (lane + 32 * m < N) Drow[lane + 32 * m] = v[m];
                 }
                 __syncwarp();
                 if (slr.cell >= 0) {
@@ -1187,15 +1190,20 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     __syncwarp();
                 }
                 if (clustered) {
-                    // the slot's stage input and cell, to every other CTA
-                    const float *xs = xrows + (size_t)sidx * XS;
+                    // the slot's stage input (16-byte pieces; the row is 16-byte
+                    // aligned and zero past N) and cell, to every other CTA
+                    const float4 *xs = (const float4 *)(xrows + (size_t)sidx * XS);
                     const uint32_t xoff = (uint32_t)((size_t)sidx * XS * 4);
                     const uint32_t coff = (uint32_t)((size_t)sidx * sizeof(Slot) + offsetof(Slot, cell));
                     const int cell_now = slr.cell;
+                    const int n4 = (N + 3) / 4;
+                    const float4 xv = lane < n4 ? xs[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 xw = lane + 32 < n4 ? xs[lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
                     for (int o = 0; o < P; o++) {
                         if (o == rank) continue;
                         const uint32_t xdst = mapa(su32(xrows), (uint32_t)o) + xoff;
-                        for (int k = lane; k < N; k += 32) st_cluster_f32(xdst + 4 * k, xs[k]);
+                        if (lane < n4) st_cluster_v4(xdst + 16 * lane, xv.x, xv.y, xv.z, xv.w);
+                        if (lane + 32 < n4) st_cluster_v4(xdst + 16 * (lane + 32), xw.x, xw.y, xw.z, xw.w);
                         if (lane == 0) st_cluster_s32(mapa(su32(slots), (uint32_t)o) + coff, cell_now);
                     }
                 }
