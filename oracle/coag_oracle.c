@@ -542,7 +542,8 @@ static int bs3_integrate(rhs_fn f, void *ctx, int n, double *y, double t_span,
         for (int k = 0; k < n; k++) {
             double e = hs * (BS_E1 * k1[k] + BS_E2 * k2[k] + BS_E3 * k3[k] + BS_E4 * k4[k]);
             double sc = atol + rtol * fmax(fabs(y[k]), fabs(y1[k]));
-            double r = fabs(e) / sc;
+            /* an empty cell has atol = 0 and y = 0: no error, not 0/0 */
+            double r = (e == 0.0) ? 0.0 : fabs(e) / sc;
             if (!isfinite(r) || !isfinite(y1[k])) finite = 0;
             if (r > E) E = r;
             if (y1[k] < ymin) ymin = y1[k];

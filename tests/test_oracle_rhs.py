@@ -265,3 +265,19 @@ def test_step_limits_report_status(oracle_mod):
     res = oracle_mod.Oracle(d).step(d.rho0, d.t_span)
     assert np.all(res["status"] == 4)
     assert np.all(res["n_acc"] + res["n_rej"] == 5)
+
+
+def test_empty_cell_passes_through(oracle_mod):
+    """A cell without dust has atol = 0 and a zero right-hand side: its error
+    ratio is 0 (not 0/0), so it takes one step of t_span and stays empty,
+    while the cell next to it integrates as it would alone."""
+    d = synth.column_1x32().subset([0, 1])
+    rho0 = d.rho0.copy()
+    rho0[1] = 0.0
+    o = oracle_mod.Oracle(d)
+    res = o.step(rho0, d.t_span)
+    assert np.all(res["status"] == 0)
+    assert res["n_acc"][1] == 1 and res["n_rej"][1] == 0
+    assert np.all(res["rho"][1] == 0.0)
+    alone = oracle_mod.Oracle(d.subset([0])).step(rho0[:1], d.t_span)
+    assert np.array_equal(res["rho"][0], alone["rho"][0])
