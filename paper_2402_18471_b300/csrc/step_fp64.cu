@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kThreads) step64_kernel(StepArgs a)
                 for (int k = threadIdx.x; k < N; k += blockDim.x) {
                     const double e = hs * (E1 * k1[k] + E2 * k2[k] + E3 * k3[k] + E4 * k4[k]);
                     const double sc = atol + a.rtol * fmax(fabs(y[k]), fabs(y1[k]));
-                    const double r = fabs(e) / sc;
+                    const double r = (e == 0.0) ? 0.0 : fabs(e) / sc;   // an empty cell: no error
                     if (!isfinite(r) || !isfinite(y1[k])) fin = 0.0;
                     if (r > E) E = r;
                     if (y1[k] < ymin) ymin = y1[k];

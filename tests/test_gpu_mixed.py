@@ -183,6 +183,26 @@ def test_automatic_cluster_choice(coag_mod):
     assert coag_mod.Coag(CASES["N17_37_cells"](), "fp64").mixed_cluster() == (0, 0)
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_empty_cell_passes_through(coag_mod, oracle_mod, precision):
+    """A cell without dust (atol = 0, zero right-hand side) takes one step of
+    t_span, stays empty and leaves the other cells as the oracle has them."""
+    d = CASES["N17_37_cells"]()
+    rho0 = d.rho0.copy()
+    rho0[[0, 5, 36]] = 0.0
+    g = coag_mod.Coag(d, precision)
+    rec = g.set_records(3000)
+    y = g.state(rho0)
+    st = g.step(y, d.t_span)
+    assert st["status"] == 0 and st["n_failed"] == 0
+    out = y.cpu().numpy()
+    n = rec["n"].cpu().numpy()
+    assert np.all(out[[0, 5, 36]] == 0.0) and np.all(n[[0, 5, 36]] == 1)
+    cells = [1, 2, 20, 35]
+    want = oracle_mod.Oracle(d.subset(cells)).replay(rho0[cells], rec["dt"].cpu().numpy()[cells], n[cells])
+    check_state(out[cells], want, rho0[cells].sum(1))
+
+
 def test_mixed_maxsteps_status(coag_mod):
     d = CASES["N17_37_cells"]()
     d.max_substeps = 4
