@@ -27,14 +27,17 @@
 //   Bt_hi tile in shared memory, so [Bt_hi; Bt_lo] is one B operand, and each
 //   accumulator holds both products side by side (half as many
 //   instructions, each twice as long, keep the tensor pipe's short queue
-//   full through the issuer's barrier checks).  Only the Bt tiles pass
-//   through shared memory, once each way.
+//   full through the issuer's barrier checks).  The Bt tiles and the slots'
+//   K tables pass through shared memory (bulk copies in, MMA and generator
+//   reads out).
 // Warp roles: warp 0 bulk-copy producer, warp 1 MMA issuer and TMEM owner,
-// warps 2..17 generate A (four warps per TMEM lane quadrant, one per quarter
-// of a block's pairs) and, between right-hand sides, run the per-slot logic: the
-// mass budget (sum_k f_k = 0 restored in FP64), the Bogacki-Shampine 3(2)
-// stages, the error norm, step control and refilling a slot with the next
-// cell when one finishes.
+// warps 2..9 generate A (two warps per TMEM lane quadrant, one per half of a
+// block's pairs) and, between right-hand sides, run the per-slot logic: the
+// Bogacki-Shampine 3(2) stages, the error norm, step control, the state
+// update with its mass budget, and refilling a slot with the next cell when
+// one finishes.  (Sixteen generator warps measured 2 % slower once the K
+// tables came from shared memory: the MMA-issuing thread shares its
+// scheduler with the generators of its quadrant.)
 //
 // Every mbarrier wait is bounded by a clock limit; a wait that runs out
 // records an error code in the status word and the kernel winds down.
@@ -49,7 +52,7 @@
 namespace cdc {
 namespace {
 
-constexpr int kGenWarps = 16;                     // generator warps, kGenQ per TMEM lane quadrant
+constexpr int kGenWarps = 8;                      // generator warps, kGenQ per TMEM lane quadrant
 constexpr int kGenQ = kGenWarps / 4;
 constexpr int kGP = kBlkPairs / kGenQ;            // pairs of each block a generator thread makes
 constexpr int kGC = kGP / 2;                      // its 2-pair chunks of the K table
@@ -254,7 +257,7 @@ __device__ __forceinline__ void mma_tf32_ts_acc(uint32_t dt, uint32_t at, uint64
                  ::"r"(dt), "r"(at), "l"(b), "r"(idesc) : "memory");
 }
 // Store 8 consecutive 32-bit columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8])
+__device__ __forceinline__ __attribute__((unused)) void tmem_st8(uint32_t taddr, const float (&v)[8])
 {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
                  ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
@@ -263,7 +266,7 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8])
                  : "memory");
 }
 // Store 16 consecutive 32-bit columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
+__device__ __forceinline__ __attribute__((unused)) void tmem_st16(uint32_t taddr, const float (&v)[16])
 {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,"
                  "%9,%10,%11,%12,%13,%14,%15,%16};"
