@@ -43,12 +43,12 @@ FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
 MEASURED_TRAFFIC = {
     # DRAM read + write of one ncu capture, per unit of work, valid while the
     # kernel's source file is unchanged
-    "step_mixed_kernel": {"bytes_per_unit": (34.729480e9 + 0.669263e9) / 635513, "unit": "RHS evaluation",
+    "step_mixed_kernel": {"bytes_per_unit": (25.678995e9 + 0.667511e9) / 635513, "unit": "RHS evaluation",
                           "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
-                          "sha256": "76cc0ed5e4f402cf2c6418505fd1af09b302d38adcef3deaea1caa81fbb79f7c"},
-    "kbuild32_kernel": {"bytes_per_unit": 42.749696e6 + 322.308864e6, "unit": "launch (8192 cells x 100 bins)",
+                          "sha256": "d6f889e2f24da4e667ba14246a75e8b883a6e750484782f7362d5a92bccefa27"},
+    "kbuild32_kernel": {"bytes_per_unit": 42.787328e6 + 322.076416e6, "unit": "launch (8192 cells x 100 bins)",
                         "source": "paper_2402_18471_b300/csrc/kbuild.cu",
-                        "sha256": "546b1915c04cb1a63b2745e1348b8aaa4b5a800f9c85804ca20acd6c004a126e"},
+                        "sha256": "dce06dc90e21fd56b035481ee777f722ee3247bb125924dca829e96a8f2ee3ee"},
 }
 TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 rate ratio
 
