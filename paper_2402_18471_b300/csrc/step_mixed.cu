@@ -394,14 +394,14 @@ __device__ void slot_copy_k(const MixedArgs &a, int slot, int c)
     const int n_ch = a.t.n_blk * 8;                  // 2-pair chunks of a table
     const float4 *src = a.K32 + (size_t)c * n_ch;
     float4 *dst = a.Kslot + (size_t)(blockIdx.x / a.P) * n_ch * kSlots + slot;
-    // eight loads in flight per lane, then their stores
+    // sixteen loads in flight per lane, then their stores
     int i0 = lane;
-    for (; i0 + 7 * 32 < n_ch; i0 += 8 * 32) {
-        float4 v[8];
+    for (; i0 + 15 * 32 < n_ch; i0 += 16 * 32) {
+        float4 v[16];
 #pragma unroll
-        for (int j = 0; j < 8; j++) v[j] = __ldg(src + i0 + 32 * j);
+        for (int j = 0; j < 16; j++) v[j] = __ldg(src + i0 + 32 * j);
 #pragma unroll
-        for (int j = 0; j < 8; j++) dst[(size_t)(i0 + 32 * j) * kSlots] = v[j];
+        for (int j = 0; j < 16; j++) dst[(size_t)(i0 + 32 * j) * kSlots] = v[j];
     }
     for (int i = i0; i < n_ch; i += 32) dst[(size_t)i * kSlots] = __ldg(src + i);
     asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -767,9 +767,10 @@ struct GenCtx {
 };
 
 // One pipeline stage = two blocks (b = 2 st, 2 st + 1; the last stage of a
-// pass may hold one): the waits for its K tables and its TMEM columns, two
-// products-and-splits into the stage's 64 TMEM columns, one store wait, one
-// arrival on each ring.
+// pass may hold one): the wait for its K tables, two products-and-splits
+// into registers (the K ring stage is released right after), then the wait
+// for its TMEM columns, the stores, one store wait and the arrival.  The
+// values are ready before the MMAs release the TMEM stage.
 __device__ __forceinline__ bool gen_stage(GenCtx &G, int st, long long g)
 {
     const int b = 2 * st;
@@ -778,33 +779,34 @@ __device__ __forceinline__ bool gen_stage(GenCtx &G, int st, long long g)
     int bi1 = G.bi, bj1 = G.bj0 + kBlkPairs;               // the second block's (i, j0)
     if (bj1 > bi1) { bi1++; bj1 = 0; }
     if (!wwait(&G.k_full[G.ks], G.ku & 1, G.s_err, ERR_WAIT_GEN)) return false;
-    if (g >= kAStages && !wwait(&G.c_empty[G.s], (G.u + 1) & 1, G.s_err, ERR_WAIT_GEN)) return false;
+    float oa[2 * kGP], ob[2 * kGP];
     if (G.active) {
-        tc_fence_after();
         // this thread's chunks 2 sub .. 2 sub + kGC - 1 of its slot, both blocks
         const float4 *kp = reinterpret_cast<const float4 *>(G.kring + (size_t)G.ks * 2 * kKBlkBytes) +
                            (size_t)(kGC * G.sub) * kSlots + G.slot;
         float4 kc[kGC];
-        float out[2 * kGP];
-        const uint32_t base = G.tmem + G.lane_base + (uint32_t)(G.s * 64 + 2 * kGP * G.sub);
 #pragma unroll
         for (int q = 0; q < kGC; q++) kc[q] = kp[q * kSlots];
-        gen_vals(kc, G.xr, G.bi, G.bj0 + kGP * G.sub, G.lo_half, out);
-        tmem_st_row(base, out);
+        gen_vals(kc, G.xr, G.bi, G.bj0 + kGP * G.sub, G.lo_half, oa);
         if (two) {
 #pragma unroll
             for (int q = 0; q < kGC; q++) kc[q] = kp[kKBlkBytes / 16 + q * kSlots];
-            gen_vals(kc, G.xr, bi1, bj1 + kGP * G.sub, G.lo_half, out);
-            tmem_st_row(base + 32, out);
+            gen_vals(kc, G.xr, bi1, bj1 + kGP * G.sub, G.lo_half, ob);
         }
+    }
+    __syncwarp();
+    if (G.lane == 0) mbar_arrive(&G.k_empty[G.ks]);
+    if (g >= kAStages && !wwait(&G.c_empty[G.s], (G.u + 1) & 1, G.s_err, ERR_WAIT_GEN)) return false;
+    if (G.active) {
+        tc_fence_after();
+        const uint32_t base = G.tmem + G.lane_base + (uint32_t)(G.s * 64 + 2 * kGP * G.sub);
+        tmem_st_row(base, oa);
+        if (two) tmem_st_row(base + 32, ob);
         tmem_st_wait();
         tc_fence_before();
     }
     __syncwarp();
-    if (G.lane == 0) {
-        mbar_arrive(&G.c_full[G.s]);
-        mbar_arrive(&G.k_empty[G.ks]);
-    }
+    if (G.lane == 0) mbar_arrive(&G.c_full[G.s]);
     // blocks run along rows: (i, 0), (i, 16), .. while j0 <= i, then (i + 1, 0)
     G.bi = bi1;
     G.bj0 = bj1 + kBlkPairs;
