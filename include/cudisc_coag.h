@@ -29,7 +29,8 @@
  *     error cudisc_coag_last_error(ctx) returns a message (NULL ctx: the last
  *     error of the calling thread).
  *   - Work is issued on params.stream (NULL: the legacy default stream).
- *     cudisc_coag_rhs is asynchronous.  cudisc_coag_step,
+ *     cudisc_coag_rhs and cudisc_coag_step_async are asynchronous (and may be
+ *     captured in a CUDA graph).  cudisc_coag_step, cudisc_coag_step_wait,
  *     cudisc_coag_build_kernel and cudisc_coag_vjp synchronise that stream
  *     before returning so they can report per-cell failures.
  */
@@ -118,6 +119,11 @@ typedef struct {
                                     cudisc_coag_mixed_cluster).  A size whose
                                     buffers do not fit falls back to the
                                     largest smaller one that does. */
+    int max_sms;                 /* SMs the integration kernels may occupy at
+                                    once (their persistent grids are sized
+                                    to it), so that several contexts run
+                                    side by side; 0 = all.  The batched
+                                    interface below sets it per disc. */
 } cudisc_coag_params;
 
 typedef struct {
@@ -163,6 +169,40 @@ cudisc_status cudisc_coag_rhs(cudisc_coag_ctx *ctx, const double *rho, double *d
  * be NULL) receives totals.  Returns the worst per-cell status. */
 cudisc_status cudisc_coag_step(cudisc_coag_ctx *ctx, double *rho, double t_span,
                                double *dt_cell, cudisc_step_stats *stats);
+
+/* The same integration split in two: cudisc_coag_step_async only issues the
+ * work on the stream (no host synchronisation, no allocation: it may be
+ * captured in a CUDA graph and replayed); cudisc_coag_step_wait then
+ * synchronises the stream, reads the per-cell results and fills stats (host,
+ * may be NULL) for the last integration issued.  Arguments and statuses as
+ * for cudisc_coag_step. */
+cudisc_status cudisc_coag_step_async(cudisc_coag_ctx *ctx, double *rho, double t_span, double *dt_cell);
+cudisc_status cudisc_coag_step_wait(cudisc_coag_ctx *ctx, cudisc_step_stats *stats);
+
+/* Batched discs: n_discs independent problems (each with its own grid, bin
+ * count and gas), integrated side by side.  Each disc gets a context of its
+ * own (params[i], with its stream and max_sms replaced: the batch owns one
+ * stream per disc and shares the SMs out in proportion to n_cells x
+ * n_bins^2), so that all discs' persistent kernels are resident together.
+ * The paper runs one disc at a time; this serves parameter studies. */
+typedef struct cudisc_coag_batch cudisc_coag_batch;   /* opaque, owned by the library */
+cudisc_status cudisc_coag_init_batched(const cudisc_coag_params *params, int n_discs,
+                                       cudisc_coag_batch **out);
+/* The context of disc i (owned by the batch: rhs, records, replay, vjp,
+ * get_kernel and set_v_frag work on it as on any context; its stream is the
+ * batch's stream for that disc). */
+cudisc_status cudisc_coag_batch_ctx(cudisc_coag_batch *batch, int i, cudisc_coag_ctx **ctx);
+/* Rebuild every disc's kernel tables (cudisc_coag_build_kernel), side by side. */
+cudisc_status cudisc_coag_batch_build_kernel(cudisc_coag_batch *batch);
+/* Integrate every disc over t_span: rho[i], dt_cell[i] as for cudisc_coag_step
+ * on disc i (dt_cell may be NULL, or hold NULLs); stats (host [n_discs], may
+ * be NULL) per disc.  The discs' work waits for what is already queued on
+ * stream (NULL: legacy default stream) and the call returns when all discs
+ * are done.  Returns the worst status over the discs (their messages: the
+ * discs' contexts). */
+cudisc_status cudisc_coag_batch_step(cudisc_coag_batch *batch, double *const *rho, double t_span,
+                                     double *const *dt_cell, void *stream, cudisc_step_stats *stats);
+void cudisc_coag_batch_destroy(cudisc_coag_batch *batch);
 
 /* Optional per-cell records for later cudisc_coag_step calls (all device
  * pointers; pass NULLs to stop recording):

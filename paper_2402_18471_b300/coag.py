@@ -42,6 +42,7 @@ class cudisc_coag_params(C.Structure):
         ("max_substeps", C.c_longlong),
         ("stream", C.c_void_p),
         ("mixed_cluster", C.c_int),
+        ("max_sms", C.c_int),
     ]
 
 
@@ -82,6 +83,14 @@ def lib():
         L.cudisc_coag_get_kernel.argtypes = [v, v, v]
         L.cudisc_coag_rhs.argtypes = [v, v, v]
         L.cudisc_coag_step.argtypes = [v, v, d, v, C.POINTER(cudisc_step_stats)]
+        L.cudisc_coag_step_async.argtypes = [v, v, d, v]
+        L.cudisc_coag_step_wait.argtypes = [v, C.POINTER(cudisc_step_stats)]
+        L.cudisc_coag_init_batched.argtypes = [C.POINTER(cudisc_coag_params), C.c_int, C.POINTER(v)]
+        L.cudisc_coag_batch_ctx.argtypes = [v, C.c_int, C.POINTER(v)]
+        L.cudisc_coag_batch_build_kernel.argtypes = [v]
+        L.cudisc_coag_batch_step.argtypes = [v, C.POINTER(v), d, C.POINTER(v), v, C.POINTER(cudisc_step_stats)]
+        L.cudisc_coag_batch_destroy.argtypes = [v]
+        L.cudisc_coag_batch_destroy.restype = None
         L.cudisc_coag_set_records.argtypes = [v, v, C.c_longlong, v, v]
         L.cudisc_coag_replay.argtypes = [v, v, v, v, C.c_longlong]
         L.cudisc_coag_step_static_scratch.argtypes = [v, v, d, v, C.POINTER(cudisc_step_stats)]
@@ -98,7 +107,9 @@ def lib():
                    "cudisc_coag_rhs", "cudisc_coag_step", "cudisc_coag_set_records",
                    "cudisc_coag_replay", "cudisc_coag_step_static_scratch",
                    "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp",
-                   "cudisc_coag_mixed_cluster"):
+                   "cudisc_coag_mixed_cluster", "cudisc_coag_step_async", "cudisc_coag_step_wait",
+                   "cudisc_coag_init_batched", "cudisc_coag_batch_ctx", "cudisc_coag_batch_build_kernel",
+                   "cudisc_coag_batch_step"):
             getattr(L, fn).restype = C.c_int
         _lib = L
     return _lib
@@ -136,6 +147,51 @@ def cudisc_coag_step(ctx, rho_ptr, t_span, dt_ptr, check=True):
     if check:
         _check(st, ctx)
     return st, s
+
+
+def cudisc_coag_step_async(ctx, rho_ptr, t_span, dt_ptr):
+    """Issue one integration on the context's stream (graph-capturable)."""
+    _check(lib().cudisc_coag_step_async(ctx, rho_ptr, float(t_span), dt_ptr), ctx)
+
+
+def cudisc_coag_step_wait(ctx, check=True):
+    s = cudisc_step_stats()
+    st = lib().cudisc_coag_step_wait(ctx, C.byref(s))
+    if check:
+        _check(st, ctx)
+    return st, s
+
+
+def cudisc_coag_init_batched(params_list):
+    arr = (cudisc_coag_params * len(params_list))(*params_list)
+    h = C.c_void_p()
+    _check(lib().cudisc_coag_init_batched(arr, len(params_list), C.byref(h)))
+    return h
+
+
+def cudisc_coag_batch_ctx(batch, i):
+    h = C.c_void_p()
+    _check(lib().cudisc_coag_batch_ctx(batch, int(i), C.byref(h)))
+    return h
+
+
+def cudisc_coag_batch_build_kernel(batch):
+    _check(lib().cudisc_coag_batch_build_kernel(batch))
+
+
+def cudisc_coag_batch_step(batch, rho_ptrs, t_span, dt_ptrs, stream_ptr, check=True):
+    n = len(rho_ptrs)
+    rho = (C.c_void_p * n)(*rho_ptrs)
+    dt = (C.c_void_p * n)(*dt_ptrs) if dt_ptrs is not None else None
+    stats = (cudisc_step_stats * n)()
+    st = lib().cudisc_coag_batch_step(batch, rho, float(t_span), dt, stream_ptr, stats)
+    if check:
+        _check(st)
+    return st, [x.as_dict() for x in stats]
+
+
+def cudisc_coag_batch_destroy(batch):
+    lib().cudisc_coag_batch_destroy(batch)
 
 
 def cudisc_coag_step_static_scratch(ctx, rho_ptr, t_span, dt_ptr, check=True):
@@ -196,6 +252,16 @@ class Coag:
     def __init__(self, disc, precision: str = "fp64", device: str = "cuda", stream=None,
                  use_v_dust: bool = True, **over):
         import torch
+        self._setup(disc, precision, device, use_v_dust, over)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.params.stream = self.stream.cuda_stream
+        self.ctx = cudisc_coag_init(self.params)
+        self._owned = True
+        self._rec = None
+
+    def _setup(self, disc, precision, device, use_v_dust, over):
+        """The disc's gas arrays on the device and its cudisc_coag_params."""
+        import torch
         self.torch = torch
         self.disc = disc
         self.device = torch.device(device)
@@ -226,15 +292,13 @@ class Coag:
         p.precision = self.precision
         p.max_substeps = int(s["max_substeps"])
         p.mixed_cluster = int(s.get("mixed_cluster", 0))
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        p.stream = self.stream.cuda_stream
+        p.max_sms = int(s.get("max_sms", 0))
         self.params = p
-        self.ctx = cudisc_coag_init(p)
-        self._rec = None
 
     def close(self):
         if getattr(self, "ctx", None):
-            cudisc_coag_destroy(self.ctx)
+            if getattr(self, "_owned", True):
+                cudisc_coag_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):
@@ -292,6 +356,18 @@ class Coag:
         d["status"] = st
         return d
 
+    def step_async(self, rho, t_span, dt=None):
+        """Issue the integration on the context's stream and return at once
+        (graph-capturable); step_wait() then gives the stats dict."""
+        assert rho.is_contiguous() and rho.dtype == self.torch.float64
+        cudisc_coag_step_async(self.ctx, rho.data_ptr(), t_span, dt.data_ptr() if dt is not None else None)
+
+    def step_wait(self, check=True):
+        st, s = cudisc_coag_step_wait(self.ctx, check=check)
+        d = s.as_dict()
+        d["status"] = st
+        return d
+
     def replay(self, rho, hs, n_h):
         assert rho.is_contiguous()
         hs = hs.contiguous()
@@ -328,6 +404,61 @@ class Coag:
                             hs.shape[1], grad_rhoT.data_ptr(), g0.data_ptr(), ga.data_ptr(),
                             gv.data_ptr())
         return g0, ga, gv
+
+
+class Batch:
+    """Several discs integrated side by side through the batched interface:
+    one context per disc (disc(i) gives a Coag view of it), SMs shared out in
+    proportion to n_cells x n_bins^2."""
+
+    def __init__(self, discs, precision: str = "mixed", device: str = "cuda", use_v_dust: bool = True,
+                 **over):
+        import torch
+        self.torch = torch
+        self.discs = list(discs)
+        self._views = []
+        for d in self.discs:
+            v = Coag.__new__(Coag)
+            v._setup(d, precision, device, use_v_dust, dict(over))
+            v._owned = False
+            v._rec = None
+            self._views.append(v)
+        self.handle = cudisc_coag_init_batched([v.params for v in self._views])
+        for i, v in enumerate(self._views):
+            v.ctx = cudisc_coag_batch_ctx(self.handle, i)
+            v.stream = None
+
+    def disc(self, i) -> "Coag":
+        return self._views[i]
+
+    def __len__(self):
+        return len(self._views)
+
+    def build_kernel(self):
+        cudisc_coag_batch_build_kernel(self.handle)
+
+    def step(self, rhos, t_span, dts=None, check=True):
+        """Integrate every disc's state (in place) over t_span; per-disc stats."""
+        stream = self.torch.cuda.current_stream().cuda_stream
+        st, stats = cudisc_coag_batch_step(self.handle, [r.data_ptr() for r in rhos], t_span,
+                                           [d.data_ptr() if d is not None else None for d in dts]
+                                           if dts is not None else None, stream, check=check)
+        for s in stats:
+            s["status"] = s["worst_status"]
+        return stats
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for v in self._views:
+                v.ctx = None
+            cudisc_coag_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _coag_step_function():

@@ -199,6 +199,7 @@ static cudisc_status validate(const cudisc_coag_params *p, std::string &why)
         why = "mixed_cluster must be 0 (automatic), 1, 2, 4 or 8";
         return CUDISC_EINVAL;
     }
+    if (p->max_sms < 0) { why = "max_sms must be >= 0 (0: all SMs)"; return CUDISC_EINVAL; }
     if (!(p->rho_m > 0) || !(p->mu > 0) || !(p->Mstar > 0) || !(p->k_B > 0) || !(p->m_H > 0) ||
         !(p->G > 0) || !(p->sigma_H2 > 0)) {
         why = "rho_m, mu, Mstar, k_B, m_H, G and sigma_H2 must be positive";
@@ -420,7 +421,8 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
             e = cudaMalloc(&c->d_K64, nc * (size_t)c->Np * sizeof(double2));
         else
         {
-            cdc::mixed_layout(c->n_cells, c->N, params->mixed_cluster, &c->mix_P, &c->mix_G, &c->mix_C);
+            cdc::mixed_layout(c->n_cells, c->N, params->mixed_cluster, params->max_sms, &c->mix_P, &c->mix_G,
+                              &c->mix_C);
             e = cudaMalloc(&c->d_K32, (size_t)c->n_cells * c->n_blk * cdc::kBlkPairs * sizeof(float2));
             // the slot groups' tables: [group][block][8 chunks][64 slots] x 16 B
             // (zeroed: slots that never hold a cell multiply zero stage inputs by it)
@@ -430,7 +432,7 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
         }
     }
     if (e == cudaSuccess && params->precision == CUDISC_MIXED_TF32) {
-        c->work_bytes = cdc::mixed_workspace_bytes(c->n_cells, c->N, c->mix_P);
+        c->work_bytes = cdc::mixed_workspace_bytes(c->n_cells, c->N, c->mix_P, params->max_sms);
         e = cudaMalloc(&c->d_work, c->work_bytes);
     }
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
@@ -551,7 +553,7 @@ static cudisc_status finish_step(cudisc_coag_ctx *c, cudisc_step_stats *stats)
         if (o.mass_err > s.mass_err_max) s.mass_err_max = o.mass_err;
     }
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    if (c->timed) cudaEventElapsedTime(&ms, c->ev0, c->ev1);   // untimed (asynchronous) steps report 0
     s.elapsed_ms = ms;
     c->t_step = ms;
     if (stats) *stats = s;
@@ -565,18 +567,39 @@ static cudisc_status finish_step(cudisc_coag_ctx *c, cudisc_step_stats *stats)
     return CUDISC_OK;
 }
 
-cudisc_status cudisc_coag_step(cudisc_coag_ctx *c, double *rho, double t_span, double *dt_cell,
-                               cudisc_step_stats *stats)
+// Issue one integration on the context's stream (no synchronisation).
+static cudisc_status issue_step(cudisc_coag_ctx *c, double *rho, double t_span, double *dt_cell, bool timed)
 {
-    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
     if (!rho) return fail(c, CUDISC_EINVAL, "rho is NULL");
     if (!(t_span > 0.0) || !std::isfinite(t_span)) return fail(c, CUDISC_EINVAL, "t_span must be positive and finite");
-    CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
+    if (timed) CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
     if (c->p.precision == CUDISC_FP64)
         CUDA_TRY(c, cdc::launch_step_fp64(c, rho, t_span, dt_cell, nullptr, nullptr, 0));
     else
         CUDA_TRY(c, cdc::launch_step_mixed(c, rho, t_span, dt_cell, nullptr, nullptr, 0));
-    CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
+    if (timed) CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
+    c->timed = timed;
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_coag_step(cudisc_coag_ctx *c, double *rho, double t_span, double *dt_cell,
+                               cudisc_step_stats *stats)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    cudisc_status st = issue_step(c, rho, t_span, dt_cell, true);
+    if (st != CUDISC_OK) return st;
+    return finish_step(c, stats);
+}
+
+cudisc_status cudisc_coag_step_async(cudisc_coag_ctx *c, double *rho, double t_span, double *dt_cell)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    return issue_step(c, rho, t_span, dt_cell, false);
+}
+
+cudisc_status cudisc_coag_step_wait(cudisc_coag_ctx *c, cudisc_step_stats *stats)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
     return finish_step(c, stats);
 }
 
@@ -687,5 +710,157 @@ cudisc_status cudisc_coag_vjp(cudisc_coag_ctx *c, const double *rho0, double t_s
     if (worst != 0) return fail(c, (cudisc_status)worst, "non-finite adjoint in some cell");
     return CUDISC_OK;
 }
+
+// ---- batched discs -------------------------------------------------------
+
+} // extern "C"
+
+struct cudisc_coag_batch {
+    std::vector<cudisc_coag_ctx *> ctx;
+    std::vector<cudaStream_t> stream;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t ready = nullptr;
+};
+
+static void free_batch(cudisc_coag_batch *b)
+{
+    if (!b) return;
+    for (cudisc_coag_ctx *c : b->ctx) free_ctx(c);
+    for (cudaEvent_t e : b->done)
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t s : b->stream)
+        if (s) cudaStreamDestroy(s);
+    if (b->ready) cudaEventDestroy(b->ready);
+    delete b;
+}
+
+extern "C" {
+
+cudisc_status cudisc_coag_init_batched(const cudisc_coag_params *params, int n_discs, cudisc_coag_batch **out)
+{
+    g_thread_err.clear();
+    if (!out) return fail(nullptr, CUDISC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!params || n_discs < 1) return fail(nullptr, CUDISC_EINVAL, "params must hold n_discs >= 1 discs");
+    for (int i = 0; i < n_discs; i++) {
+        std::string why;
+        const cudisc_status st = validate(&params[i], why);
+        if (st != CUDISC_OK) return fail(nullptr, st, "disc " + std::to_string(i) + ": " + why);
+    }
+    int dev = 0, n_sm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    // SM shares in proportion to n_cells x n_bins^2 (the work of a pass), at
+    // least one each, handed out largest remainder first
+    std::vector<double> w(n_discs);
+    double W = 0.0;
+    for (int i = 0; i < n_discs; i++) {
+        w[i] = (double)params[i].n_cells * params[i].n_bins * params[i].n_bins;
+        W += w[i];
+    }
+    std::vector<int> sms(n_discs, 1);
+    int left = n_sm - n_discs;
+    if (left > 0) {
+        std::vector<std::pair<double, int>> rem;
+        int given = 0;
+        for (int i = 0; i < n_discs; i++) {
+            const double q = left * w[i] / W;
+            const int f = (int)q;
+            sms[i] += f;
+            given += f;
+            rem.push_back({q - f, i});
+        }
+        std::sort(rem.begin(), rem.end(), [](const std::pair<double, int> &x, const std::pair<double, int> &y) {
+            return x.first > y.first;
+        });
+        for (int k = 0; k < left - given && k < n_discs; k++) sms[rem[k].second]++;
+    }
+    cudisc_coag_batch *b = new cudisc_coag_batch();
+    cudaError_t e = cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming);
+    for (int i = 0; i < n_discs && e == cudaSuccess; i++) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t d = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d, cudaEventDisableTiming);
+        b->stream.push_back(s);
+        b->done.push_back(d);
+    }
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return fail(nullptr, CUDISC_ECUDA, std::string("cudisc_coag_init_batched: ") + cudaGetErrorString(e));
+    }
+    for (int i = 0; i < n_discs; i++) {
+        cudisc_coag_params p = params[i];
+        p.stream = b->stream[i];
+        p.max_sms = sms[i];
+        cudisc_coag_ctx *c = nullptr;
+        const cudisc_status st = cudisc_coag_init(&p, &c);
+        if (st != CUDISC_OK) {
+            const std::string msg = "disc " + std::to_string(i) + ": " + g_thread_err;
+            free_batch(b);
+            return fail(nullptr, st, msg);
+        }
+        b->ctx.push_back(c);
+    }
+    *out = b;
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_coag_batch_ctx(cudisc_coag_batch *b, int i, cudisc_coag_ctx **ctx)
+{
+    if (!b || !ctx) return fail(nullptr, CUDISC_EINVAL, "batch or ctx is NULL");
+    if (i < 0 || i >= (int)b->ctx.size()) return fail(nullptr, CUDISC_EINVAL, "disc index out of range");
+    *ctx = b->ctx[i];
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_coag_batch_build_kernel(cudisc_coag_batch *b)
+{
+    if (!b) return fail(nullptr, CUDISC_EINVAL, "batch is NULL");
+    // each build synchronises its own stream only; issue them all, then wait
+    cudisc_status worst = CUDISC_OK;
+    for (cudisc_coag_ctx *c : b->ctx) {
+        const cudisc_status st = cudisc_coag_build_kernel(c);
+        if (st != CUDISC_OK && worst == CUDISC_OK) worst = st;
+    }
+    return worst;
+}
+
+cudisc_status cudisc_coag_batch_step(cudisc_coag_batch *b, double *const *rho, double t_span,
+                                     double *const *dt_cell, void *stream, cudisc_step_stats *stats)
+{
+    if (!b) return fail(nullptr, CUDISC_EINVAL, "batch is NULL");
+    if (!rho) return fail(nullptr, CUDISC_EINVAL, "rho is NULL");
+    const int n = (int)b->ctx.size();
+    cudaStream_t s0 = (cudaStream_t)stream;
+    cudaError_t e = cudaEventRecord(b->ready, s0);
+    if (e != cudaSuccess) return fail(nullptr, CUDISC_ECUDA, cudaGetErrorString(e));
+    // issue every disc on its own stream, after the caller's queued work
+    cudisc_status worst = CUDISC_OK;
+    std::vector<bool> issued(n, false);
+    for (int i = 0; i < n; i++) {
+        cudisc_coag_ctx *c = b->ctx[i];
+        e = cudaStreamWaitEvent(b->stream[i], b->ready, 0);
+        if (e != cudaSuccess) { cuda_fail(c, e, "batch step"); worst = CUDISC_ECUDA; continue; }
+        const cudisc_status st = issue_step(c, rho[i], t_span, dt_cell ? dt_cell[i] : nullptr, true);
+        if (st != CUDISC_OK) { if (worst == CUDISC_OK || st > worst) worst = st; continue; }
+        issued[i] = true;
+        e = cudaEventRecord(b->done[i], b->stream[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, b->done[i], 0);
+        if (e != cudaSuccess) { cuda_fail(c, e, "batch step"); worst = CUDISC_ECUDA; }
+    }
+    // then collect each disc (its stream is already running)
+    for (int i = 0; i < n; i++) {
+        if (!issued[i]) {
+            if (stats) std::memset(&stats[i], 0, sizeof(cudisc_step_stats));
+            continue;
+        }
+        const cudisc_status st = finish_step(b->ctx[i], stats ? &stats[i] : nullptr);
+        if (st != CUDISC_OK && (worst == CUDISC_OK || st > worst)) worst = st;
+    }
+    return worst;
+}
+
+void cudisc_coag_batch_destroy(cudisc_coag_batch *b) { free_batch(b); }
 
 } // extern "C"

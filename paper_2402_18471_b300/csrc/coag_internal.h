@@ -110,6 +110,7 @@ struct cudisc_coag_ctx {
     float2 *d_K32 = nullptr;           // n_cells x n_blk x 16 {K p_coag, K p_frag}, see k32_index
     float4 *d_Kslot = nullptr;         // mixed kernel: [group][block][8 chunks][64 slots] of the slots' tables
     int mix_P = 1, mix_G = 1, mix_C = 1;   // mixed kernel: CTAs per slot group, groups, initial cells per group
+    bool timed = false;                // the last integration issued recorded ev0/ev1
     // integration workspace
     cdc::CellOut *d_out = nullptr;     // [n_cells]
     double *d_work = nullptr;          // mixed path slot state
@@ -139,10 +140,10 @@ cudaError_t launch_rhs_mixed(const cudisc_coag_ctx *c, const double *rho, double
 cudaError_t launch_step_mixed(const cudisc_coag_ctx *c, double *rho, double t_span,
                               double *dt_cell, const double *replay_h,
                               const long long *replay_n, long long replay_stride);
-size_t mixed_workspace_bytes(int n_cells, int N, int P);
+size_t mixed_workspace_bytes(int n_cells, int N, int P, int max_sms);
 // cluster size P for a request P_req (0: automatic), groups of slots G and
 // initial cells per group C of the mixed kernel
-void mixed_layout(int n_cells, int N, int P_req, int *P, int *G, int *C);
+void mixed_layout(int n_cells, int N, int P_req, int max_sms, int *P, int *G, int *C);
 // adjoint (vjp.cu)
 bool vjp_fits(const cudisc_coag_ctx *c);
 cudaError_t vjp_prepare(cudisc_coag_ctx *c, long long max_steps);

@@ -253,6 +253,7 @@ cudaError_t launch_step_fp64(const cudisc_coag_ctx *c, double *rho, double t_spa
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step64_kernel, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (c->p.max_sms > 0) n_sm = std::min(n_sm, c->p.max_sms);
     const int grid = std::max(1, std::min(c->n_cells, n_sm * per_sm));
     e = cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) return e;

@@ -1273,6 +1273,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
 struct Config { int grid, groups, P, NS, XS, SB, KS, NBP, nacc, stacked, C, sst_off; size_t smem; bool ok; };
 
 cudaError_t launch_kernel(const Config &cf, const MixedArgs &a, cudaStream_t stream);
+int sm_count();
 
 // Clusters of P CTAs that can run at once (the launch's groups must all be
 // resident together: a group that started late would find its initial cells
@@ -1317,7 +1318,7 @@ int max_clusters(int P, size_t smem, int n_sm)
 // Launch layout for clusters of P CTAs (ok = false when P does not fit: fewer
 // than two mapping-tile stages beside the buffers, fewer than two stages of a
 // pass per CTA, or no cluster of P resident).
-Config config_for(int n_cells, int N, int P, int n_sm)
+Config config_for(int n_cells, int N, int P, int n_sm)   // n_sm: the SMs this launch may occupy
 {
     Config c;
     c.P = P;
@@ -1367,7 +1368,7 @@ Config config_for(int n_cells, int N, int P, int n_sm)
     c.smem = std::max((size_t)120 * 1024, 1024 + used + tail + dpeer);
     c.ok = KS >= 1 && SB >= sb_min && used <= room && (P == 1 || n_st >= 2 * P);
     // cells are spread over up to one cluster per P SMs, at least 8 a group
-    const int mc = P == 1 ? n_sm : (c.ok ? max_clusters(P, c.smem, n_sm) : 0);
+    const int mc = P == 1 ? n_sm : (c.ok ? std::min(max_clusters(P, c.smem, sm_count()), n_sm / P) : 0);
     if (mc < 1) c.ok = false;
     c.groups = std::max(1, std::min(std::max(mc, 1), (n_cells + 7) / 8));
     c.grid = P * c.groups;
@@ -1389,9 +1390,10 @@ int sm_count()
 // passes a group runs are about max(1, n_cells / (3 slots)), the costliest
 // cells taking about three times the mean.  A request that does not fit
 // falls back to the largest smaller P that does.
-Config mixed_config(int n_cells, int N, int P_req)
+// max_sms > 0: the launch may occupy at most that many SMs.
+Config mixed_config(int n_cells, int N, int P_req, int max_sms)
 {
-    const int n_sm = sm_count();
+    const int n_sm = max_sms > 0 ? std::min(max_sms, sm_count()) : sm_count();
     if (P_req > 0) {
         for (int P = P_req; P >= 1; P /= 2) {
             Config c = config_for(n_cells, N, P, n_sm);
@@ -1433,7 +1435,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
                          double *dt_cell, const double *replay_h, const long long *replay_n,
                          long long replay_stride)
 {
-    Config cf = mixed_config(c->n_cells, c->N, c->mix_P);
+    Config cf = mixed_config(c->n_cells, c->N, c->mix_P, c->p.max_sms);
     const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(float);
     if (need > c->work_bytes) return cudaErrorInvalidValue;
     if (cf.P != c->mix_P || cf.groups != c->mix_G || cf.C != c->mix_C)
@@ -1503,7 +1505,7 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
                                      double *dt_cell, bool *too_big)
 {
     *too_big = false;
-    Config cf = mixed_config(c->n_cells, c->N, c->mix_P);
+    Config cf = mixed_config(c->n_cells, c->N, c->mix_P, c->p.max_sms);
     const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(float);
     if (need > kStaticScratchBytes) { *too_big = true; return cudaSuccess; }
     if (cf.P != c->mix_P || cf.groups != c->mix_G || cf.C != c->mix_C)
@@ -1565,17 +1567,17 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     return launch_kernel(cf, a, c->stream);
 }
 
-void mixed_layout(int n_cells, int N, int P_req, int *P, int *G, int *C)
+void mixed_layout(int n_cells, int N, int P_req, int max_sms, int *P, int *G, int *C)
 {
-    const Config cf = mixed_config(n_cells, N, P_req);
+    const Config cf = mixed_config(n_cells, N, P_req, max_sms);
     *P = cf.P;
     *G = cf.groups;
     *C = cf.C;
 }
 
-size_t mixed_workspace_bytes(int n_cells, int N, int P)
+size_t mixed_workspace_bytes(int n_cells, int N, int P, int max_sms)
 {
-    Config cf = mixed_config(n_cells, N, P);
+    Config cf = mixed_config(n_cells, N, P, max_sms);
     return (size_t)cf.groups * cf.NS * 5 * (size_t)N * sizeof(float);
 }
 

@@ -64,6 +64,7 @@ def _params(disc, **over):
     ("v_frag", -1.0, coag.EINVAL),
     ("mixed_cluster", 3, coag.EINVAL),
     ("mixed_cluster", 16, coag.EINVAL),
+    ("max_sms", -1, coag.EINVAL),
 ])
 def test_init_rejects_bad_arguments(field, value, code):
     d = synth.column_1x32()
@@ -97,4 +98,12 @@ def test_null_context_is_an_error_not_a_crash():
     assert L.cudisc_coag_get_timings(None, C.byref(t)) == coag.EINVAL
     cl, gr = C.c_int(), C.c_int()
     assert L.cudisc_coag_mixed_cluster(None, C.byref(cl), C.byref(gr)) == coag.EINVAL
+    assert L.cudisc_coag_step_async(None, None, 1.0, None) == coag.EINVAL
+    assert L.cudisc_coag_step_wait(None, None) == coag.EINVAL
+    h = C.c_void_p()
+    assert L.cudisc_coag_init_batched(None, 0, C.byref(h)) == coag.EINVAL and h.value is None
+    assert L.cudisc_coag_batch_ctx(None, 0, C.byref(h)) == coag.EINVAL
+    assert L.cudisc_coag_batch_build_kernel(None) == coag.EINVAL
+    assert L.cudisc_coag_batch_step(None, None, 1.0, None, None, None) == coag.EINVAL
+    L.cudisc_coag_batch_destroy(None)
     L.cudisc_coag_destroy(None)

@@ -1,0 +1,119 @@
+"""Batched discs and the asynchronous (graph-capturable) step, on the GPU.
+
+Batched discs: several independent discs of uneven grid and bin counts,
+integrated side by side through cudisc_coag_batch_step; every disc is
+checked against the oracle replaying that disc's own accepted step
+sequence (tolerances as in test_gpu_mixed: 1e-5 relative with the paper's
+absolute tolerance 1e-10 S as the floor; FP64 1e-10).  The asynchronous
+step is captured in a CUDA graph, replayed, and compared with the
+synchronous call on the same input.
+"""
+import numpy as np
+import pytest
+
+from paper_2402_18471_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def coag_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_18471_b300 import coag
+    return coag
+
+
+def small_batch():
+    """Four discs: cell counts 24..600, 17..72 bins, different alpha and v_frag."""
+    return [
+        synth.make_disc(3, 8, 17, 1e-5, 0.1, 10.0, 20.0, 100.0, alpha=1e-2, v_frag=300.0, seed=31),
+        synth.make_disc(20, 30, 40, 1e-5, 1.0, 5.0, 100.0, 300.0, alpha=1e-3, v_frag=100.0, seed=32),
+        synth.make_disc(6, 10, 72, 1e-5, 10.0, 5.0, 50.0, 300.0, alpha=1e-4, v_frag=1000.0, seed=33),
+        synth.make_disc(12, 16, 33, 1e-5, 1.0, 10.0, 100.0, 200.0, alpha=3e-3, v_frag=500.0, seed=34),
+    ]
+
+
+def check_rel(out, ref, S, rel, atol_rel=1e-10):
+    r = np.abs(out - ref) / (rel * np.abs(ref) + atol_rel * S[:, None])
+    assert r.max() <= 1.0, r.max()
+
+
+@pytest.mark.parametrize("precision,rel", [("mixed", 1e-5), ("fp64", 1e-10)])
+def test_batched_discs_match_oracle(coag_mod, oracle_mod, precision, rel):
+    discs = small_batch()
+    b = coag_mod.Batch(discs, precision)
+    recs = [b.disc(i).set_records(4000) for i in range(len(b))]
+    ys = [b.disc(i).state(d.rho0) for i, d in enumerate(discs)]
+    stats = b.step(ys, discs[0].t_span)
+    for i, d in enumerate(discs):
+        st = stats[i]
+        assert st["worst_status"] == 0 and st["n_failed"] == 0
+        assert st["mass_err_max"] < 1e-9
+        n = recs[i]["n"].cpu().numpy()
+        assert st["accepted"] == n.sum()
+        cells = np.unique(np.linspace(0, d.n_cells - 1, 6).astype(int))
+        want = oracle_mod.Oracle(d.subset(cells)).replay(d.rho0[cells], recs[i]["dt"].cpu().numpy()[cells],
+                                                         n[cells])
+        check_rel(ys[i].cpu().numpy()[cells], want, d.rho0[cells].sum(1), rel)
+    b.close()
+
+
+def test_batch_shares_the_sms(coag_mod):
+    """Every disc's persistent grid fits in its share, the shares in the GPU."""
+    discs = small_batch()
+    b = coag_mod.Batch(discs, "mixed")
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    used = 0
+    for i in range(len(b)):
+        P, groups = b.disc(i).mixed_cluster()
+        assert P >= 1 and groups >= 1
+        used += P * groups
+    assert used <= n_sm
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_async_step_in_a_cuda_graph(coag_mod, precision):
+    d = synth.make_disc(8, 16, 40, 1e-5, 1.0, 5.0, 100.0, 300.0, alpha=1e-3, v_frag=100.0, seed=35)
+    s = torch.cuda.Stream()
+    g = coag_mod.Coag(d, precision, stream=s)
+    rho0 = g.state(d.rho0)
+    ref = rho0.clone()
+    with torch.cuda.stream(s):
+        st = g.step(ref, d.t_span)
+    assert st["status"] == 0
+    y = rho0.clone()
+    dt = torch.zeros(d.n_cells, dtype=torch.float64, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        g.step_async(y, d.t_span, dt)
+    for _ in range(2):
+        with torch.cuda.stream(s):
+            y.copy_(rho0)
+            dt.zero_()
+        graph.replay()
+        st2 = g.step_wait()
+        assert st2["status"] == 0 and st2["accepted"] == st["accepted"]
+        assert torch.equal(y, ref)
+
+
+def test_full_size_32_disc_batch_sampled(coag_mod, oracle_mod):
+    """The 32 uneven discs (~3e5 cells, 40-150 bins) in one batched step of
+    the mixed path; two sampled cells per disc against the oracle replay."""
+    discs = synth.batch_32_discs()
+    t_span = 100.0 * synth.CONST["yr"]
+    b = coag_mod.Batch(discs, "mixed")
+    recs = [b.disc(i).set_records(4000) for i in range(len(b))]
+    ys = [b.disc(i).state(d.rho0) for i, d in enumerate(discs)]
+    stats = b.step(ys, t_span)
+    for i, d in enumerate(discs):
+        assert stats[i]["worst_status"] == 0 and stats[i]["mass_err_max"] < 1e-9
+        n = recs[i]["n"].cpu().numpy()
+        cells = np.array([0, d.n_cells - 1 - (7 * i) % d.n_cells])
+        want = oracle_mod.Oracle(d.subset(cells)).replay(d.rho0[cells], recs[i]["dt"].cpu().numpy()[cells],
+                                                         n[cells])
+        check_rel(ys[i].cpu().numpy()[cells], want, d.rho0[cells].sum(1), 1e-5)
+    b.close()
