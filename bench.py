@@ -158,6 +158,20 @@ def cpu_baseline(disc, budget_s=20.0, t_span=None):
                       f"{total_t:.1f} s, OpenMP over cells"}
 
 
+def combine_ranks(dist, device, ms, e2e_s, sub, e2e_sub):
+    """The job's figures from every rank's own: the timed regions' maximum
+    (ms, e2e seconds) and the units' sum (accepted cell-substeps) over the
+    ranks of the process group (dist None: one rank)."""
+    if dist is None:
+        return ms, e2e_s, sub, e2e_sub
+    import torch
+    t = torch.tensor([float(ms), float(e2e_s)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([int(sub), int(e2e_sub)], dtype=torch.int64, device=device)
+    dist.all_reduce(u)
+    return float(t[0]), float(t[1]), int(u[0]), int(u[1])
+
+
 def run_reference(args, disc, rank, world):
     if rank != 0:
         return
@@ -295,17 +309,8 @@ def main():
         fp64_res = measure("fp64", 1, 1, False)
 
     # max over ranks of the timed region; units summed over ranks
-    ms = main_res["ms"]
-    sub = main_res["sub"]
-    if dist:
-        t = torch.tensor([ms, main_res.get("e2e_s", 0.0)], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
-        u = torch.tensor([float(sub), float(main_res.get("e2e_sub", 0))], device="cuda")
-        dist.all_reduce(u)
-        sub, e2e_sub = int(u[0]), int(u[1])
-    else:
-        e2e_s, e2e_sub = main_res["e2e_s"], main_res["e2e_sub"]
+    ms, e2e_s, sub, e2e_sub = combine_ranks(dist, "cuda", main_res["ms"], main_res.get("e2e_s", 0.0),
+                                            main_res["sub"], main_res.get("e2e_sub", 0))
 
     if rank == 0:
         pk = peaks()
