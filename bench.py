@@ -43,9 +43,9 @@ FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
 MEASURED_TRAFFIC = {
     # DRAM read + write of one ncu capture, per unit of work, valid while the
     # kernel's source file is unchanged
-    "step_mixed_kernel": {"bytes_per_unit": (25.678995e9 + 0.667511e9) / 635513, "unit": "RHS evaluation",
+    "step_mixed_kernel": {"bytes_per_unit": (25.722631e9 + 0.669711e9) / 635513, "unit": "RHS evaluation",
                           "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
-                          "sha256": "d6f889e2f24da4e667ba14246a75e8b883a6e750484782f7362d5a92bccefa27"},
+                          "sha256": "0c86fec4351919f64007d69b47a3946525c359d8da67b09399aa6ecb9d97253f"},
     "kbuild32_kernel": {"bytes_per_unit": 42.787328e6 + 322.076416e6, "unit": "launch (8192 cells x 100 bins)",
                         "source": "paper_2402_18471_b300/csrc/kbuild.cu",
                         "sha256": "dce06dc90e21fd56b035481ee777f722ee3247bb125924dca829e96a8f2ee3ee"},
