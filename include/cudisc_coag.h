@@ -179,6 +179,36 @@ cudisc_status cudisc_coag_step(cudisc_coag_ctx *ctx, double *rho, double t_span,
 cudisc_status cudisc_coag_step_async(cudisc_coag_ctx *ctx, double *rho, double t_span, double *dt_cell);
 cudisc_status cudisc_coag_step_wait(cudisc_coag_ctx *ctx, cudisc_step_stats *stats);
 
+/* As cudisc_coag_step with a span per cell: cell c is integrated over
+ * t_span[c] seconds (device [n_cells], FP64).  A cell with t_span[c] <= 0
+ * (or NaN) is left as it is: no steps, status OK, its rho and dt_cell
+ * unchanged.  The cells to integrate are gathered on the device, so the
+ * integration kernel's queue holds only those cells.  t_span NULL:
+ * CUDISC_EINVAL.  Synchronises the stream. */
+cudisc_status cudisc_coag_step_spans(cudisc_coag_ctx *ctx, double *rho, const double *t_span,
+                                     double *dt_cell, cudisc_step_stats *stats);
+
+/* Sub-cycled coagulation (Sec. 6): the coagulation solver takes its own
+ * sub-steps inside the global time steps of the disc model, and a cell's
+ * coagulation is brought up to date only once one (by default) of its last
+ * sub-steps has elapsed in global time.  Call once per global step of
+ * dt_global seconds (>= 0, finite).  The context keeps, per cell, the
+ * global time elapsed since its last update (its pending time, 0 at init).
+ * Each call adds dt_global to it; a cell whose pending time has reached
+ * trigger (> 0; 1 is the default of Sec. 6) times its last sub-step
+ * dt_cell[c], or that has none yet (dt_cell NULL or dt_cell[c] <= 0), is
+ * integrated over its whole pending time, which then restarts at 0; the
+ * others are left as in cudisc_coag_step_spans.  dt_cell (device
+ * [n_cells], may be NULL) is read and written as in cudisc_coag_step.
+ * Synchronises the stream. */
+cudisc_status cudisc_coag_subcycle(cudisc_coag_ctx *ctx, double *rho, double dt_global, double trigger,
+                                   double *dt_cell, cudisc_step_stats *stats);
+
+/* Copy the cells' pending times into pending (device [n_cells] FP64; NULL:
+ * no copy) and, with reset != 0, set them to 0 (e.g. after the caller has
+ * brought every cell up to date itself).  Synchronises the stream. */
+cudisc_status cudisc_coag_subcycle_pending(cudisc_coag_ctx *ctx, double *pending, int reset);
+
 /* Batched discs: n_discs independent problems (each with its own grid, bin
  * count and gas), integrated side by side.  Each disc gets a context of its
  * own (params[i], with its stream and max_sms replaced: the batch owns one

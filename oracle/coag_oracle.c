@@ -593,18 +593,27 @@ static void bs3_fixed(rhs_fn f, void *ctx, int n, double *y, const double *hs, l
     free(k1); free(k2); free(k3); free(Y);
 }
 
-/* Adaptive coagulation step of every cell over t_span.
+/* Adaptive coagulation step of every cell c over its span: spans[c] when
+ * spans is given (a cell with spans[c] <= 0 is not touched: no steps,
+ * status 0, dt[c] kept), else t_span for all cells.
  * dt[c]: in = first step (<= 0: automatic), out = last proposed step.
- * Optional per-cell logs of accepted steps: dt_log[c*log_cap + s].
- * Parity: pinned (closed-form constant/additive kernels, BS3 order tests). */
-int oracle_step(const oracle_params *P, double *rho, double t_span, double *dt,
-                long *n_acc, long *n_rej, int *status, double *dt_log,
-                long log_cap, long *n_log)
+ * Optional per-cell logs of accepted steps: dt_log[c*log_cap + s]. */
+static int step_cells(const oracle_params *P, double *rho, double t_span, const double *spans,
+                      double *dt, long *n_acc, long *n_rej, int *status, double *dt_log,
+                      long log_cap, long *n_log)
 {
     const int N = P->n_bins;
     int worst = 0;
     #pragma omp parallel for schedule(dynamic) num_threads(nthreads_of(P)) reduction(max:worst)
     for (int c = 0; c < P->n_cells; c++) {
+        const double span = spans ? spans[c] : t_span;
+        if (!(span > 0.0)) {
+            if (n_acc) n_acc[c] = 0;
+            if (n_rej) n_rej[c] = 0;
+            if (status) status[c] = 0;
+            if (n_log) n_log[c] = 0;
+            continue;
+        }
         cellctx cx;
         cell_alloc(P, c, &cx);
         double *y = rho + (size_t)c * N;
@@ -613,7 +622,7 @@ int oracle_step(const oracle_params *P, double *rho, double t_span, double *dt,
         double atol = P->atol_rel * s;
         bs3_stats st;
         long nl = 0;
-        bs3_integrate(rhs_cell, &cx, N, y, t_span, dt ? dt[c] : 0.0, P->rtol, atol,
+        bs3_integrate(rhs_cell, &cx, N, y, span, dt ? dt[c] : 0.0, P->rtol, atol,
                       P->max_substeps, dt_log ? dt_log + (size_t)c * log_cap : NULL,
                       log_cap, &nl, &st);
         if (dt) dt[c] = st.h_last;
@@ -625,6 +634,26 @@ int oracle_step(const oracle_params *P, double *rho, double t_span, double *dt,
         cell_free(&cx);
     }
     return worst;
+}
+
+/* Every cell over t_span.  Parity: pinned (closed-form constant/additive
+ * kernels, BS3 order tests). */
+int oracle_step(const oracle_params *P, double *rho, double t_span, double *dt,
+                long *n_acc, long *n_rej, int *status, double *dt_log,
+                long log_cap, long *n_log)
+{
+    return step_cells(P, rho, t_span, NULL, dt, n_acc, n_rej, status, dt_log, log_cap, n_log);
+}
+
+/* Cell c over spans[c] (cells with spans[c] <= 0 untouched): the update of
+ * the cells that a sub-cycled global step (Sec. 6) brings up to date.
+ * Parity: pinned as oracle_step (a single-cell span equals a whole-grid
+ * step of that span; skipped cells are bitwise unchanged). */
+int oracle_step_spans(const oracle_params *P, double *rho, const double *spans, double *dt,
+                      long *n_acc, long *n_rej, int *status, double *dt_log,
+                      long log_cap, long *n_log)
+{
+    return step_cells(P, rho, 0.0, spans, dt, n_acc, n_rej, status, dt_log, log_cap, n_log);
 }
 
 /* Replay: apply a given sequence of accepted BS3 steps to every cell

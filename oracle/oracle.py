@@ -63,11 +63,12 @@ def lib():
         _lib.oracle_rhs_bruteforce.argtypes = [P, d, d]
         _lib.oracle_step.argtypes = [P, d, C.c_double, d, d, d, d, d, C.c_long, d]
         _lib.oracle_step_replay.argtypes = [P, d, d, d, C.c_long]
+        _lib.oracle_step_spans.argtypes = [P, d, d, d, d, d, d, d, C.c_long, d]
         _lib.oracle_bs3_scalar.argtypes = [C.c_double] * 6 + [C.c_int, C.c_long, d]
         _lib.oracle_vjp.argtypes = [P, d, d, d, C.c_long, d, d, d, d]
         for fn in ("oracle_cell_physics", "oracle_kernel", "oracle_pair_map",
                    "oracle_frag_table", "oracle_rhs", "oracle_rhs_bruteforce",
-                   "oracle_step", "oracle_step_replay", "oracle_bs3_scalar", "oracle_vjp"):
+                   "oracle_step", "oracle_step_replay", "oracle_step_spans", "oracle_bs3_scalar", "oracle_vjp"):
             getattr(_lib, fn).restype = C.c_int
     return _lib
 
@@ -148,6 +149,9 @@ class Oracle:
         return out
 
     def step(self, rho, t_span, dt=None, log_cap=0):
+        """BS3 integration of every cell over t_span: one number for all
+        cells, or an array of per-cell spans (cells with a span <= 0 are not
+        touched)."""
         y = _f64(rho).copy()
         nc = self.n_cells
         dtv = np.zeros(nc) if dt is None else _f64(dt).copy()
@@ -155,11 +159,39 @@ class Oracle:
         stt = np.zeros(nc, dtype=np.int32)
         log = np.zeros((nc, max(log_cap, 1)))
         nl = np.zeros(nc, dtype=np.int64)
-        rc = lib().oracle_step(C.byref(self.p), _ptr(y), float(t_span), _ptr(dtv), _ptr(na),
-                               _ptr(nr), _ptr(stt), _ptr(log) if log_cap else None,
-                               int(log_cap), _ptr(nl))
+        if np.ndim(t_span):
+            spans = _f64(t_span).reshape(-1)
+            assert spans.size == nc
+            rc = lib().oracle_step_spans(C.byref(self.p), _ptr(y), _ptr(spans), _ptr(dtv), _ptr(na),
+                                         _ptr(nr), _ptr(stt), _ptr(log) if log_cap else None,
+                                         int(log_cap), _ptr(nl))
+        else:
+            rc = lib().oracle_step(C.byref(self.p), _ptr(y), float(t_span), _ptr(dtv), _ptr(na),
+                                   _ptr(nr), _ptr(stt), _ptr(log) if log_cap else None,
+                                   int(log_cap), _ptr(nl))
         return dict(rho=y, dt=dtv, n_acc=na, n_rej=nr, status=stt, rc=rc,
                     log=log[:, :log_cap] if log_cap else None, n_log=nl)
+
+    def subcycle(self, rho, pending, dt, dt_global, trigger=1.0, log_cap=0):
+        """One global time step of a sub-cycled coagulation update (Sec. 6).
+
+        The coagulation solver takes its own sub-steps; a cell is brought up
+        to date once the global time elapsed since its last update (pending,
+        plus this step's dt_global) has reached trigger x its last sub-step
+        dt[c] (trigger 1 is the paper's default), or when it has no sub-step
+        yet (dt[c] <= 0).  Such a cell is integrated over its whole pending
+        time, which restarts at 0; the others only accumulate.  Returns the
+        step() result (rho, dt, counts and logs after the update) with the
+        spans used and the new pending times."""
+        pending = _f64(pending).reshape(-1)
+        dt = _f64(dt).reshape(-1)
+        acc = pending + dt_global
+        due = ~(dt > 0.0) | (acc >= trigger * dt)
+        spans = np.where(due, acc, 0.0)
+        res = self.step(rho, spans, dt, log_cap)
+        res["spans"] = spans
+        res["pending"] = np.where(due, 0.0, acc)
+        return res
 
     def vjp(self, rho0, hs, n_h, w):
         """Gradient of sum(w * rho(T)) after replaying hs w.r.t. rho0, alpha, v_frag."""

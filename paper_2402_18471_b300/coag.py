@@ -85,6 +85,9 @@ def lib():
         L.cudisc_coag_step.argtypes = [v, v, d, v, C.POINTER(cudisc_step_stats)]
         L.cudisc_coag_step_async.argtypes = [v, v, d, v]
         L.cudisc_coag_step_wait.argtypes = [v, C.POINTER(cudisc_step_stats)]
+        L.cudisc_coag_step_spans.argtypes = [v, v, v, v, C.POINTER(cudisc_step_stats)]
+        L.cudisc_coag_subcycle.argtypes = [v, v, d, d, v, C.POINTER(cudisc_step_stats)]
+        L.cudisc_coag_subcycle_pending.argtypes = [v, v, C.c_int]
         L.cudisc_coag_init_batched.argtypes = [C.POINTER(cudisc_coag_params), C.c_int, C.POINTER(v)]
         L.cudisc_coag_batch_ctx.argtypes = [v, C.c_int, C.POINTER(v)]
         L.cudisc_coag_batch_build_kernel.argtypes = [v]
@@ -109,7 +112,8 @@ def lib():
                    "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp",
                    "cudisc_coag_mixed_cluster", "cudisc_coag_step_async", "cudisc_coag_step_wait",
                    "cudisc_coag_init_batched", "cudisc_coag_batch_ctx", "cudisc_coag_batch_build_kernel",
-                   "cudisc_coag_batch_step"):
+                   "cudisc_coag_batch_step", "cudisc_coag_step_spans", "cudisc_coag_subcycle",
+                   "cudisc_coag_subcycle_pending"):
             getattr(L, fn).restype = C.c_int
         _lib = L
     return _lib
@@ -160,6 +164,26 @@ def cudisc_coag_step_wait(ctx, check=True):
     if check:
         _check(st, ctx)
     return st, s
+
+
+def cudisc_coag_step_spans(ctx, rho_ptr, spans_ptr, dt_ptr, check=True):
+    s = cudisc_step_stats()
+    st = lib().cudisc_coag_step_spans(ctx, rho_ptr, spans_ptr, dt_ptr, C.byref(s))
+    if check:
+        _check(st, ctx)
+    return st, s
+
+
+def cudisc_coag_subcycle(ctx, rho_ptr, dt_global, trigger, dt_ptr, check=True):
+    s = cudisc_step_stats()
+    st = lib().cudisc_coag_subcycle(ctx, rho_ptr, float(dt_global), float(trigger), dt_ptr, C.byref(s))
+    if check:
+        _check(st, ctx)
+    return st, s
+
+
+def cudisc_coag_subcycle_pending(ctx, pending_ptr, reset):
+    _check(lib().cudisc_coag_subcycle_pending(ctx, pending_ptr, int(bool(reset))), ctx)
 
 
 def cudisc_coag_init_batched(params_list):
@@ -367,6 +391,34 @@ class Coag:
         d = s.as_dict()
         d["status"] = st
         return d
+
+    def step_spans(self, rho, spans, dt=None, check=True):
+        """Integrate cell c of rho (in place) over spans[c] (device FP64
+        [n_cells]); cells with spans[c] <= 0 are left as they are."""
+        assert rho.is_contiguous() and rho.dtype == self.torch.float64
+        spans = spans.contiguous()
+        assert spans.dtype == self.torch.float64 and spans.numel() == self.n_cells
+        st, s = cudisc_coag_step_spans(self.ctx, rho.data_ptr(), spans.data_ptr(),
+                                       dt.data_ptr() if dt is not None else None, check=check)
+        d = s.as_dict()
+        d["status"] = st
+        return d
+
+    def subcycle(self, rho, dt_global, dt=None, trigger=1.0, check=True):
+        """One global step of dt_global: update the cells whose pending time
+        has reached trigger x their last coagulation sub-step (Sec. 6)."""
+        assert rho.is_contiguous() and rho.dtype == self.torch.float64
+        st, s = cudisc_coag_subcycle(self.ctx, rho.data_ptr(), dt_global, trigger,
+                                     dt.data_ptr() if dt is not None else None, check=check)
+        d = s.as_dict()
+        d["status"] = st
+        return d
+
+    def pending(self, reset=False):
+        """The cells' pending (not yet integrated) global times."""
+        out = self.torch.empty(self.n_cells, dtype=self.torch.float64, device=self.device)
+        cudisc_coag_subcycle_pending(self.ctx, out.data_ptr(), reset)
+        return out
 
     def replay(self, rho, hs, n_h):
         assert rho.is_contiguous()

@@ -38,6 +38,43 @@ cudisc_status cuda_fail(cudisc_coag_ctx *c, cudaError_t e, const char *where)
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
     } while (0)
 
+// Work list of an integration with per-cell spans: cells with a positive
+// span (given, or, sub-cycling, the pending global time once it reaches
+// trigger x the cell's last sub-step) are listed; the others get an empty
+// result record (no steps, status OK, their state and dt_cell kept).
+__global__ void worklist_kernel(int n_cells, const double *span_in, double *pending, double dt_global,
+                                double trigger, const double *dt_cell, double *spans, int *list, int *count,
+                                CellOut *out, long long *rec_n, int *rec_status)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cells) return;
+    double span;
+    if (span_in) {
+        span = span_in[c];
+    } else {
+        const double acc = pending[c] + dt_global;
+        const double h = dt_cell ? dt_cell[c] : 0.0;
+        const bool due = !(h > 0.0) || acc >= trigger * h;
+        span = due ? acc : 0.0;
+        pending[c] = due ? 0.0 : acc;
+    }
+    if (span > 0.0) {
+        spans[c] = span;
+        list[atomicAdd(count, 1)] = c;
+    } else {
+        CellOut o;
+        o.n_acc = 0;
+        o.n_rej = 0;
+        o.h_last = dt_cell ? dt_cell[c] : 0.0;
+        o.mass_err = 0.0;
+        o.status = CUDISC_OK;
+        o.pad = 0;
+        out[c] = o;
+        if (rec_n) rec_n[c] = 0;
+        if (rec_status) rec_status[c] = CUDISC_OK;
+    }
+}
+
 template <class T>
 cudaError_t upload(T **dst, const std::vector<T> &src, cudaStream_t s)
 {
@@ -366,7 +403,8 @@ static void free_ctx(cudisc_coag_ctx *c)
     void *ptrs[] = {c->d_m, c->d_minv, c->d_a, c->d_me, c->d_pair_ij, c->d_row, c->d_ent_p,
                     c->d_ent_ab, c->d_frow, c->d_fent_p, c->d_fent_m, c->d_Ntab, c->d_blk_i,
                     c->d_blk_j0, c->d_Btiles, c->d_prep, c->d_prep32, c->d_scal, c->d_K64,
-                    c->d_K32, c->d_Kslot, c->d_out, c->d_work, c->d_counter, c->d_scal32};
+                    c->d_K32, c->d_Kslot, c->d_out, c->d_work, c->d_counter, c->d_scal32, c->d_list,
+                    c->d_spans, c->d_pending};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -415,6 +453,10 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
     if (e == cudaSuccess) e = cudaMalloc(&c->d_scal32, nc * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_out, nc * sizeof(CellOut));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, 64 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_list, nc * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_spans, nc * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_pending, nc * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(c->d_pending, 0, nc * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(c->d_counter, 0, 64 * sizeof(int));
     if (e == cudaSuccess) {
         if (params->precision == CUDISC_FP64)
@@ -589,6 +631,62 @@ cudisc_status cudisc_coag_step(cudisc_coag_ctx *c, double *rho, double t_span, d
     cudisc_status st = issue_step(c, rho, t_span, dt_cell, true);
     if (st != CUDISC_OK) return st;
     return finish_step(c, stats);
+}
+
+// Build the work list on the device, then one timed integration over it.
+static cudisc_status issue_worklist_step(cudisc_coag_ctx *c, double *rho, const double *span_in,
+                                         double dt_global, double trigger, double *dt_cell)
+{
+    if (!rho) return fail(c, CUDISC_EINVAL, "rho is NULL");
+    CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_counter + 3, 0, sizeof(int), c->stream));
+    worklist_kernel<<<(c->n_cells + 255) / 256, 256, 0, c->stream>>>(
+        c->n_cells, span_in, c->d_pending, dt_global, trigger, dt_cell, c->d_spans, c->d_list, c->d_counter + 3,
+        c->d_out, c->rec_n, c->rec_status);
+    CUDA_TRY(c, cudaGetLastError());
+    cdc::WorkList wl;
+    wl.cells = c->d_list;
+    wl.count = c->d_counter + 3;
+    wl.spans = c->d_spans;
+    if (c->p.precision == CUDISC_FP64)
+        CUDA_TRY(c, cdc::launch_step_fp64(c, rho, 1.0, dt_cell, nullptr, nullptr, 0, wl));
+    else
+        CUDA_TRY(c, cdc::launch_step_mixed(c, rho, 1.0, dt_cell, nullptr, nullptr, 0, wl));
+    CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
+    c->timed = true;
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_coag_step_spans(cudisc_coag_ctx *c, double *rho, const double *t_span, double *dt_cell,
+                                     cudisc_step_stats *stats)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!t_span) return fail(c, CUDISC_EINVAL, "t_span is NULL");
+    cudisc_status st = issue_worklist_step(c, rho, t_span, 0.0, 1.0, dt_cell);
+    if (st != CUDISC_OK) return st;
+    return finish_step(c, stats);
+}
+
+cudisc_status cudisc_coag_subcycle(cudisc_coag_ctx *c, double *rho, double dt_global, double trigger,
+                                   double *dt_cell, cudisc_step_stats *stats)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!(dt_global >= 0.0) || !std::isfinite(dt_global))
+        return fail(c, CUDISC_EINVAL, "dt_global must be >= 0 and finite");
+    if (!(trigger > 0.0) || !std::isfinite(trigger)) return fail(c, CUDISC_EINVAL, "trigger must be positive and finite");
+    cudisc_status st = issue_worklist_step(c, rho, nullptr, dt_global, trigger, dt_cell);
+    if (st != CUDISC_OK) return st;
+    return finish_step(c, stats);
+}
+
+cudisc_status cudisc_coag_subcycle_pending(cudisc_coag_ctx *c, double *pending, int reset)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    const size_t bytes = (size_t)c->n_cells * sizeof(double);
+    if (pending) CUDA_TRY(c, cudaMemcpyAsync(pending, c->d_pending, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (reset) CUDA_TRY(c, cudaMemsetAsync(c->d_pending, 0, bytes, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return CUDISC_OK;
 }
 
 cudisc_status cudisc_coag_step_async(cudisc_coag_ctx *c, double *rho, double t_span, double *dt_cell)

@@ -115,7 +115,10 @@ struct cudisc_coag_ctx {
     cdc::CellOut *d_out = nullptr;     // [n_cells]
     double *d_work = nullptr;          // mixed path slot state
     size_t work_bytes = 0;
-    int *d_counter = nullptr;          // work queue head
+    int *d_counter = nullptr;          // work queue head (d_counter[3]: work-list length)
+    int *d_list = nullptr;             // [n_cells] work list of per-cell-span integrations
+    double *d_spans = nullptr;         // [n_cells] their spans
+    double *d_pending = nullptr;       // [n_cells] global time since each cell's last sub-cycled update
     // optional records
     double *rec_dt = nullptr; long long rec_cap = 0; long long *rec_n = nullptr;
     int *rec_status = nullptr;
@@ -128,6 +131,14 @@ struct cudisc_coag_ctx {
 };
 
 namespace cdc {
+// The cells an integration covers: all of them (cells == NULL) or
+// cells[0 .. *count - 1] (device; the count is read by the kernels), each
+// over spans[c] seconds (device [n_cells]; NULL: the call's t_span).
+struct WorkList {
+    const int *cells = nullptr;
+    const int *count = nullptr;
+    const double *spans = nullptr;
+};
 // kernel launchers (defined in the .cu files)
 cudaError_t launch_prep(const cudisc_coag_ctx *c);
 cudaError_t launch_kbuild(const cudisc_coag_ctx *c);
@@ -135,11 +146,11 @@ cudaError_t launch_get_kernel(const cudisc_coag_ctx *c, double *K, double *KF);
 cudaError_t launch_rhs_fp64(const cudisc_coag_ctx *c, const double *rho, double *drho);
 cudaError_t launch_step_fp64(const cudisc_coag_ctx *c, double *rho, double t_span,
                              double *dt_cell, const double *replay_h,
-                             const long long *replay_n, long long replay_stride);
+                             const long long *replay_n, long long replay_stride, WorkList wl = WorkList());
 cudaError_t launch_rhs_mixed(const cudisc_coag_ctx *c, const double *rho, double *drho);
 cudaError_t launch_step_mixed(const cudisc_coag_ctx *c, double *rho, double t_span,
                               double *dt_cell, const double *replay_h,
-                              const long long *replay_n, long long replay_stride);
+                              const long long *replay_n, long long replay_stride, WorkList wl = WorkList());
 size_t mixed_workspace_bytes(int n_cells, int N, int P, int max_sms);
 // cluster size P for a request P_req (0: automatic), groups of slots G and
 // initial cells per group C of the mixed kernel

@@ -36,6 +36,7 @@ struct StepArgs {
     long long rec_cap;
     long long *rec_n;
     int *rec_status;
+    WorkList wl;                // the cells to integrate and their spans
 };
 
 size_t smem_doubles(int N, int Np) { return 2 * (size_t)Np + 8 * (size_t)N + 32; }
@@ -121,8 +122,10 @@ __global__ void __launch_bounds__(kThreads) step64_kernel(StepArgs a)
         __syncthreads();
         if (threadIdx.x == 0) s_cell = atomicAdd(a.counter, 1);
         __syncthreads();
-        const int c = s_cell;
-        if (c >= t.n_cells) break;
+        const int idx = s_cell;
+        if (idx >= (a.wl.count ? *a.wl.count : t.n_cells)) break;
+        const int c = a.wl.cells ? a.wl.cells[idx] : idx;
+        const double t_span = a.wl.spans ? a.wl.spans[c] : a.t_span;   // this cell's span
         const double2 *Kc = a.K64 + (size_t)c * Np;
         double *rc = a.rho + (size_t)c * N;
         for (int k = threadIdx.x; k < N; k += blockDim.x) y[k] = rc[k];
@@ -158,14 +161,14 @@ __global__ void __launch_bounds__(kThreads) step64_kernel(StepArgs a)
                 for (int k = threadIdx.x; k < N; k += blockDim.x)
                     if (k1[k] != 0.0) q = fmin(q, (fabs(y[k]) + atol) / fabs(k1[k]));
                 const double hmin = block_reduce(q, red, MinOp());
-                h = isfinite(hmin) ? 0.1 * hmin : a.t_span;
-                if (h > a.t_span) h = a.t_span;
+                h = isfinite(hmin) ? 0.1 * hmin : t_span;
+                if (h > t_span) h = t_span;
             }
             double tt = 0.0;
-            while (tt < a.t_span) {
+            while (tt < t_span) {
                 if (nacc + nrej >= a.max_steps) { status = CUDISC_EMAXSTEPS; break; }
-                const bool last = (h >= a.t_span - tt);
-                const double hs = last ? (a.t_span - tt) : h;
+                const bool last = (h >= t_span - tt);
+                const double hs = last ? (t_span - tt) : h;
                 for (int k = threadIdx.x; k < N; k += blockDim.x) Y[k] = y[k] + hs * A21 * k1[k];
                 __syncthreads();
                 rhs64(t, Kc, Y, k2, Wa, Wb, fl);
@@ -189,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) step64_kernel(StepArgs a)
                 ymin = block_reduce(ymin, red, MinOp());
                 const bool finite = block_reduce(fin, red, MinOp()) > 0.5;
                 if (finite && E <= 1.0 && ymin >= -atol) {
-                    tt = last ? a.t_span : tt + hs;
+                    tt = last ? t_span : tt + hs;
                     for (int k = threadIdx.x; k < N; k += blockDim.x) { y[k] = y1[k]; k1[k] = k4[k]; }
                     if (threadIdx.x == 0 && a.rec_dt && nacc < a.rec_cap)
                         a.rec_dt[(size_t)c * a.rec_cap + nacc] = hs;
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(kThreads) step64_kernel(StepArgs a)
                     else if (E > 1.0) fac = fmax(0.9 * pow(E, -1.0 / 3.0), 0.2);
                     else fac = 0.5;
                     h = hs * fac;
-                    if (h < 1e-14 * a.t_span) { status = finite ? CUDISC_EDTMIN : CUDISC_ENONFINITE; break; }
+                    if (h < 1e-14 * t_span) { status = finite ? CUDISC_EDTMIN : CUDISC_ENONFINITE; break; }
                 }
             }
         }
@@ -242,7 +245,7 @@ cudaError_t launch_rhs_fp64(const cudisc_coag_ctx *c, const double *rho, double 
 
 cudaError_t launch_step_fp64(const cudisc_coag_ctx *c, double *rho, double t_span,
                              double *dt_cell, const double *replay_h,
-                             const long long *replay_n, long long replay_stride)
+                             const long long *replay_n, long long replay_stride, WorkList wl)
 {
     const size_t smem = smem_doubles(c->N, c->Np) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(step64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -275,6 +278,7 @@ cudaError_t launch_step_fp64(const cudisc_coag_ctx *c, double *rho, double t_spa
     a.rec_cap = c->rec_cap;
     a.rec_n = c->rec_n;
     a.rec_status = c->rec_status;
+    a.wl = wl;
     step64_kernel<<<grid, kThreads, smem, c->stream>>>(a);
     return cudaGetLastError();
 }

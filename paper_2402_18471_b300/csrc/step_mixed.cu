@@ -99,13 +99,14 @@ struct MixedArgs {
     int kC;                     // initial cells per group (slot s of group x starts with cell x + s G)
     int KS;                     // K-table ring depth
     int sst_off;                // byte offset of the per-slot state in shared memory, or -1: in work
+    WorkList wl;                // the cells to integrate (work item -> cell) and their spans
     int P;                      // CTAs per group of slots (a cluster of 1, 2, 4 or 8; see the kernel)
     int nacc;                   // TMEM accumulators for the products with Bt_hi (stacked: with [Bt_hi; Bt_lo])
     int stacked;                // 1: one MMA of N = 2 NBP takes Bt_hi and Bt_lo together (2 NBP <= 256)
 };
 
 struct __align__(16) Slot {
-    double t, h, hs, S, Sx;
+    double t, h, hs, S, Sx, tend;      // tend: the cell's span
     long long nacc, nrej, nrep;
     float sxf, atolx, hsf;             // Sx, atol / Sx and hs in FP32 for the per-bin work
     int cell, phase, last, status;
@@ -452,6 +453,7 @@ __device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, i
         sl.sxf = (float)Sx;
         sl.atolx = (float)(a.atol_rel * s * r);
         sl.t = 0.0;
+        sl.tend = a.wl.spans ? a.wl.spans[c] : a.t_span;
         sl.h = (a.mode == MODE_STEP && a.dt_cell) ? a.dt_cell[c] : 0.0;
         sl.hs = 0.0;
         sl.hsf = 0.f;
@@ -535,8 +537,8 @@ __device__ bool begin_step(const MixedArgs &a, Slot &sl, float *xrow, SlotBufs B
 {
     const int N = a.t.N, lane = threadIdx.x & 31;
     if (sl.nacc + sl.nrej >= a.max_steps) { sl.status = CUDISC_EMAXSTEPS; return false; }
-    sl.last = (sl.h >= a.t_span - sl.t);
-    sl.hs = sl.last ? (a.t_span - sl.t) : sl.h;
+    sl.last = (sl.h >= sl.tend - sl.t);
+    sl.hs = sl.last ? (sl.tend - sl.t) : sl.h;
     sl.hsf = (float)sl.hs;
     const float c1 = sl.hsf * (float)A21;
     for (int k = lane; k < N; k += 32) xrow[k] = B.yh[k] + c1 * B.k1[k];
@@ -627,8 +629,8 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
                 if (B.k1[k] != 0.f) q = fminf(q, (fabsf(B.yh[k]) + atolx) / fabsf(B.k1[k]));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) q = fminf(q, __shfl_xor_sync(0xffffffffu, q, o));
-            sl.h = isfinite(q) ? 0.1 * (double)q : a.t_span;
-            if (sl.h > a.t_span) sl.h = a.t_span;
+            sl.h = isfinite(q) ? 0.1 * (double)q : sl.tend;
+            if (sl.h > sl.tend) sl.h = sl.tend;
         }
         return !begin_step(a, sl, xrow, B);
     }
@@ -680,7 +682,7 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
         const bool nonneg = __all_sync(0xffffffffu, pos);
         if (finite && E <= 1.f && nonneg) {
             commit_increment(B, N, dx);
-            sl.t = sl.last ? a.t_span : sl.t + sl.hs;
+            sl.t = sl.last ? sl.tend : sl.t + sl.hs;
 #pragma unroll
             for (int m = 0; m < MB; m++) {
                 const int k = lane + 32 * m;
@@ -693,7 +695,7 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
             float fac = (E > 0.f) ? 0.9f * rcbrtf(E) : 5.f;
             fac = fminf(fmaxf(fac, 0.2f), 5.f);
             if (!(sl.last && sl.hs < sl.h)) sl.h = sl.hs * (double)fac;
-            if (sl.t >= a.t_span) return true;
+            if (sl.t >= sl.tend) return true;
         } else {
             sl.nrej++;
             float fac;
@@ -701,7 +703,7 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
             else if (E > 1.f) fac = fmaxf(0.9f * rcbrtf(E), 0.2f);
             else fac = 0.5f;
             sl.h = sl.hs * (double)fac;
-            if (sl.h < 1e-14 * a.t_span) { sl.status = finite ? CUDISC_EDTMIN : CUDISC_ENONFINITE; return true; }
+            if (sl.h < 1e-14 * sl.tend) { sl.status = finite ? CUDISC_EDTMIN : CUDISC_ENONFINITE; return true; }
         }
         return !begin_step(a, sl, xrow, B);
     }
@@ -928,11 +930,12 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     // of each slot, and the copy of its cell's K table into the group's
     // buffer, is done by the one that keeps it.
     const int C = a.kC;
+    const int n_work = a.wl.count ? *a.wl.count : a.t.n_cells;   // work item w is cell wl.cells[w] (or w)
     if (warp >= 2) {
         for (int s = warp - 2; s < NS; s += kGenWarps) {
-            const int c = grp + s * ngrp;
-            slot_load(a, slots[s], xrows + (size_t)s * XS, s, (s < C && c < a.t.n_cells) ? c : -1,
-                      s >= own0 && s < own0 + SL);
+            const int w = grp + s * ngrp;
+            const int c = (s < C && w < n_work) ? (a.wl.cells ? a.wl.cells[w] : w) : -1;
+            slot_load(a, slots[s], xrows + (size_t)s * XS, s, c, s >= own0 && s < own0 + SL);
         }
     }
     tc_fence_before();
@@ -1198,13 +1201,14 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                         slot_finish(a, loc, sidx);
                         // refill from the global queue: cells 0 .. G*C-1 were the
                         // initial fill, later ones go to whichever slot frees first
-                        int c = 0;
-                        if (lane == 0) c = ngrp * C + atomicAdd(a.queue, 1);
-                        c = __shfl_sync(0xffffffffu, c, 0);
+                        int w = 0;
+                        if (lane == 0) w = ngrp * C + atomicAdd(a.queue, 1);
+                        w = __shfl_sync(0xffffffffu, w, 0);
                         __syncwarp();
                         if (lane == 0) slr = loc;
                         __syncwarp();
-                        slot_load(a, slr, xrows + (size_t)sidx * XS, sidx, c < a.t.n_cells ? c : -1);
+                        slot_load(a, slr, xrows + (size_t)sidx * XS, sidx,
+                                  w < n_work ? (a.wl.cells ? a.wl.cells[w] : w) : -1);
                     } else if (lane == 0) {
                         slr = loc;
                     }
@@ -1430,7 +1434,7 @@ cudaError_t launch_kernel(const Config &cf, const MixedArgs &a, cudaStream_t str
 
 cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double *drho, double t_span,
                          double *dt_cell, const double *replay_h, const long long *replay_n,
-                         long long replay_stride)
+                         long long replay_stride, WorkList wl = WorkList())
 {
     Config cf = mixed_config(c->n_cells, c->N, c->mix_P, c->p.max_sms);
     const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(float);
@@ -1474,6 +1478,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.KS = cf.KS;
     a.sst_off = cf.sst_off;
     a.P = cf.P;
+    a.wl = wl;
     a.mode = mode;
     return launch_kernel(cf, a, c->stream);
 }
@@ -1560,6 +1565,7 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     a.KS = cf.KS;
     a.sst_off = cf.sst_off;
     a.P = cf.P;
+    a.wl = WorkList();
     a.mode = MODE_STEP;
     return launch_kernel(cf, a, c->stream);
 }
@@ -1584,10 +1590,11 @@ cudaError_t launch_rhs_mixed(const cudisc_coag_ctx *c, const double *rho, double
 }
 
 cudaError_t launch_step_mixed(const cudisc_coag_ctx *c, double *rho, double t_span, double *dt_cell,
-                              const double *replay_h, const long long *replay_n, long long replay_stride)
+                              const double *replay_h, const long long *replay_n, long long replay_stride,
+                              WorkList wl)
 {
     return launch_mixed(c, replay_h ? MODE_REPLAY : MODE_STEP, rho, nullptr, t_span, dt_cell, replay_h,
-                        replay_n, replay_stride);
+                        replay_n, replay_stride, wl);
 }
 
 } // namespace cdc
