@@ -48,6 +48,12 @@
  *   - laminar dv from input dust velocities, or terminal drift/settling
  *     velocities v_R = -2 eta v_K St/(1+St^2), v_phi = -eta v_K/(1+St^2),
  *     v_Z = -Z Omega St/(1+St), with v_K = Omega R.
+ *   - vertically integrated kernel (Sec. 5.1, the 1D comparison with a
+ *     surface-density code): states are surface densities, the cell is a
+ *     radius (Z unused, Omega = Omega_mid, rho_gas = mid-plane density),
+ *     grain scale heights h = H sqrt(alpha / (alpha + St)), settling
+ *     velocities v_Z = -h Omega St/(1+St) (each grain at its own scale
+ *     height), and K -> K / sqrt(2 pi (h_i^2 + h_j^2)).
  *   - integrator: per-cell step, max-norm error, safety 0.9, factor clamp
  *     [0.2, 5], reject on y' < -atol, first step 0.1 min (|y|+atol)/|f|.
  *
@@ -80,6 +86,7 @@ typedef struct {
     int n_threads;          /* <= 0: library default */
     double rtol, atol_rel;
     long max_substeps;
+    int vertical;           /* 1: vertically integrated kernel (Sec. 5.1) */
 } oracle_params;
 
 enum { ST_OK = 0, ST_MAXSTEPS = 4, ST_NONFINITE = 5, ST_DTMIN = 7 };
@@ -174,13 +181,13 @@ double oracle_pfrag(double dv, double vf)
 /* Per-cell, per-bin quantities: sizes, Stokes numbers, dust velocities. */
 typedef struct {
     double cs, Re, Vg2, T;
-    double *a, *St, *vR, *vphi, *vZ;
+    double *a, *St, *vR, *vphi, *vZ, *h;   /* h: grain scale heights (vertical mode) */
 } cellphys;
 
 static void cell_physics(const oracle_params *P, int c, cellphys *cp)
 {
     const int N = P->n_bins;
-    double T = P->T[c], rg = P->rho_gas[c], R = P->R[c], Z = P->Z[c];
+    double T = P->T[c], rg = P->rho_gas[c], R = P->R[c], Z = P->vertical ? 0.0 : P->Z[c];
     double cs = sqrt(P->k_B * T / (P->mu * P->m_H));
     double vth = sqrt(8.0 / M_PI) * cs;
     double r2 = R * R + Z * Z;
@@ -202,6 +209,8 @@ static void cell_physics(const oracle_params *P, int c, cellphys *cp)
         double St = ts * Omega;
         cp->a[k] = a;
         cp->St[k] = St;
+        /* dust scale height of a Gaussian layer stirred by turbulence */
+        cp->h[k] = P->vertical ? H * sqrt(P->alpha[c] / (P->alpha[c] + St)) : 0.0;
         if (P->v_dust) {
             size_t nc = (size_t)P->n_cells * N;
             cp->vR[k] = P->v_dust[(size_t)c * N + k];
@@ -210,7 +219,9 @@ static void cell_physics(const oracle_params *P, int c, cellphys *cp)
         } else {
             cp->vR[k] = -2.0 * eta * vK * St / (1.0 + St * St);
             cp->vphi[k] = -eta * vK / (1.0 + St * St);
-            cp->vZ[k] = -Z * Omega * St / (1.0 + St);
+            /* settling at the height Z, or at the grain's own scale height */
+            double zk = P->vertical ? cp->h[k] : Z;
+            cp->vZ[k] = -zk * Omega * St / (1.0 + St);
         }
     }
 }
@@ -232,6 +243,8 @@ static void pair_kernel(const oracle_params *P, const cellphys *cp, int i, int j
     if (P->kernel_mode == 1) k = P->kernel_const;
     else if (P->kernel_mode == 2) k = P->kernel_const * (m[i] + m[j]);
     else k = M_PI * s * s * dv;
+    /* vertically integrated: the rate of two Gaussian layers per unit area */
+    if (P->vertical) k /= sqrt(2.0 * M_PI * (cp->h[i] * cp->h[i] + cp->h[j] * cp->h[j]));
     double p;
     if (P->frag_mode == 1) p = 0.0;
     else if (P->frag_mode == 2) p = 1.0;
@@ -263,9 +276,9 @@ static void cell_alloc(const oracle_params *P, int c, cellctx *cx)
 {
     const int N = P->n_bins;
     cellphys cp;
-    double *buf = xmalloc(sizeof(double) * 5 * N);
+    double *buf = xmalloc(sizeof(double) * 6 * N);
     cp.a = buf; cp.St = buf + N; cp.vR = buf + 2 * N; cp.vphi = buf + 3 * N;
-    cp.vZ = buf + 4 * N;
+    cp.vZ = buf + 4 * N; cp.h = buf + 5 * N;
     cell_physics(P, c, &cp);
     cx->P = P; cx->c = c;
     cx->K = xmalloc(sizeof(double) * N * N);
@@ -357,12 +370,15 @@ int oracle_threads(void)
 #endif
 }
 
-/* Per-cell diagnostics for tests: St[N], a[N], and {cs, Re, Vg2}.
- * Parity: pinned (Stokes / Epstein closed forms are re-derived in tests). */
+/* Per-cell diagnostics for tests: St[N], a[N], velocities, grain scale
+ * heights h[N] (vertical mode; zeros otherwise) and {cs, Re, Vg2}.
+ * Parity: pinned (Stokes / Epstein closed forms are re-derived in tests;
+ * h by its small- and large-St limits and the vertical integral of the
+ * volume rate). */
 int oracle_cell_physics(const oracle_params *P, int c, double *a, double *St,
-                        double *vR, double *vphi, double *vZ, double *scal3)
+                        double *vR, double *vphi, double *vZ, double *h, double *scal3)
 {
-    cellphys cp; cp.a = a; cp.St = St; cp.vR = vR; cp.vphi = vphi; cp.vZ = vZ;
+    cellphys cp; cp.a = a; cp.St = St; cp.vR = vR; cp.vphi = vphi; cp.vZ = vZ; cp.h = h;
     cell_physics(P, c, &cp);
     scal3[0] = cp.cs; scal3[1] = cp.Re; scal3[2] = cp.Vg2;
     return 0;
@@ -377,9 +393,9 @@ int oracle_kernel(const oracle_params *P, double *K, double *pf, double *dv)
     #pragma omp parallel for schedule(dynamic) num_threads(nthreads_of(P))
     for (int c = 0; c < P->n_cells; c++) {
         cellphys cp;
-        double *buf = xmalloc(sizeof(double) * 5 * N);
+        double *buf = xmalloc(sizeof(double) * 6 * N);
         cp.a = buf; cp.St = buf + N; cp.vR = buf + 2 * N; cp.vphi = buf + 3 * N;
-        cp.vZ = buf + 4 * N;
+        cp.vZ = buf + 4 * N; cp.h = buf + 5 * N;
         cell_physics(P, c, &cp);
         size_t o = (size_t)c * N * N;
         for (int i = 0; i < N; i++)
@@ -790,6 +806,7 @@ int oracle_vjp(const oracle_params *P, const double *rho0, const double *hs, con
                long stride, const double *w, double *g_rho0, double *g_alpha, double *g_vfrag)
 {
     const int N = P->n_bins;
+    if (P->vertical) return 6;   /* the kernel's alpha derivative covers the volume form only */
     double vf_total = 0.0;
     #pragma omp parallel for schedule(dynamic) num_threads(nthreads_of(P)) reduction(+:vf_total)
     for (int c = 0; c < P->n_cells; c++) {
@@ -840,8 +857,9 @@ int oracle_vjp(const oracle_params *P, const double *rho0, const double *hs, con
         memcpy(g_rho0 + (size_t)c * N, lam, sizeof(double) * N);
         /* parameters: chain the accumulated pair cotangents */
         cellphys cp;
-        double *buf = xmalloc(sizeof(double) * 5 * N);
+        double *buf = xmalloc(sizeof(double) * 6 * N);
         cp.a = buf; cp.St = buf + N; cp.vR = buf + 2 * N; cp.vphi = buf + 3 * N; cp.vZ = buf + 4 * N;
+        cp.h = buf + 5 * N;
         cell_physics(P, c, &cp);
         double ga = 0.0, gv = 0.0;
         for (int i = 0; i < N; i++)

@@ -41,6 +41,7 @@ class OracleParams(C.Structure):
         ("n_threads", C.c_int),
         ("rtol", C.c_double), ("atol_rel", C.c_double),
         ("max_substeps", C.c_long),
+        ("vertical", C.c_int),
     ]
 
 
@@ -55,7 +56,7 @@ def lib():
         _lib.oracle_pfrag.restype = C.c_double
         _lib.oracle_pfrag.argtypes = [C.c_double, C.c_double]
         _lib.oracle_threads.restype = C.c_int
-        _lib.oracle_cell_physics.argtypes = [P, C.c_int, d, d, d, d, d, d]
+        _lib.oracle_cell_physics.argtypes = [P, C.c_int, d, d, d, d, d, d, d]
         _lib.oracle_kernel.argtypes = [P, d, d, d]
         _lib.oracle_pair_map.argtypes = [P, C.c_int, C.c_int, d, d]
         _lib.oracle_frag_table.argtypes = [P, d]
@@ -107,6 +108,7 @@ class Oracle:
         for k in ("kernel_mode", "frag_mode", "split_mode"):
             setattr(p, k, int(s[k]))
         p.max_substeps = int(s["max_substeps"])
+        p.vertical = int(s.get("vertical", 0))
         p.n_threads = int(n_threads)
         self.p = p
         self.N = disc.n_bins
@@ -115,11 +117,11 @@ class Oracle:
     # -- per-pair pieces -----------------------------------------------------
     def cell_physics(self, c):
         N = self.N
-        a, St, vR, vp, vZ = (np.zeros(N) for _ in range(5))
+        a, St, vR, vp, vZ, h = (np.zeros(N) for _ in range(6))
         sc = np.zeros(3)
         lib().oracle_cell_physics(C.byref(self.p), c, _ptr(a), _ptr(St), _ptr(vR),
-                                  _ptr(vp), _ptr(vZ), _ptr(sc))
-        return dict(a=a, St=St, vR=vR, vphi=vp, vZ=vZ, cs=sc[0], Re=sc[1], Vg2=sc[2])
+                                  _ptr(vp), _ptr(vZ), _ptr(h), _ptr(sc))
+        return dict(a=a, St=St, vR=vR, vphi=vp, vZ=vZ, h=h, cs=sc[0], Re=sc[1], Vg2=sc[2])
 
     def kernel(self):
         N, nc = self.N, self.n_cells
@@ -198,8 +200,10 @@ class Oracle:
         rho0 = _f64(rho0); hs = _f64(hs); w = _f64(w)
         n_h = np.ascontiguousarray(n_h, dtype=np.int64)
         g_rho0 = np.zeros_like(rho0); g_alpha = np.zeros(self.n_cells); g_vf = np.zeros(1)
-        lib().oracle_vjp(C.byref(self.p), _ptr(rho0), _ptr(hs), _ptr(n_h), hs.shape[1], _ptr(w),
-                         _ptr(g_rho0), _ptr(g_alpha), _ptr(g_vf))
+        rc = lib().oracle_vjp(C.byref(self.p), _ptr(rho0), _ptr(hs), _ptr(n_h), hs.shape[1], _ptr(w),
+                              _ptr(g_rho0), _ptr(g_alpha), _ptr(g_vf))
+        if rc:
+            raise ValueError("the oracle's adjoint covers the volume-density kernel only")
         return g_rho0, g_alpha, float(g_vf[0])
 
     def replay(self, rho, hs, n_h):

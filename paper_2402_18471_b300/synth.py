@@ -99,6 +99,7 @@ class Disc:
     atol_rel: float = 1e-10
     max_substeps: int = 2_000_000
     v_dust: np.ndarray | None = None   # [3, n_cells, N] or None
+    vertical: int = 0                  # 1: surface densities, vertically integrated kernel
     R_edges: np.ndarray | None = None  # [n_R+1] cm, for cell volumes
     Z_edges: np.ndarray | None = None  # [n_R, n_Z+1] cm
     extra: dict = field(default_factory=dict)
@@ -118,7 +119,8 @@ class Disc:
                  sigma_H2=CONST["sigma_H2"], kernel_mode=self.kernel_mode,
                  kernel_const=self.kernel_const, frag_mode=self.frag_mode,
                  split_mode=self.split_mode, rtol=self.rtol,
-                 atol_rel=self.atol_rel, max_substeps=self.max_substeps)
+                 atol_rel=self.atol_rel, max_substeps=self.max_substeps,
+                 vertical=self.vertical)
         return d
 
     def subset(self, cells) -> "Disc":
@@ -233,6 +235,57 @@ def batch_32_discs(seed=4):
                                alpha=al, v_frag=vf, seed=1000 + d,
                                name=f"batch{d}_{n_R}x{n_Z}_N{n_b}"))
     return discs
+
+
+def make_ring_disc(n_R, n_bins, a_min, a_max, R_in_au, R_out_au, t_span_yr, alpha=1e-3,
+                   v_frag=100.0, T=None, Sigma_g=None, mu=2.4, rho_m=1.6, d2g=0.01,
+                   name="rings", seed=None):
+    """Radii of a 1D disc for the vertically integrated kernel: the state is
+    the dust SURFACE density per bin, rho_gas the mid-plane gas density
+    Sigma_g / (sqrt(2 pi) H) with H = c_s / Omega_K of an isothermal column
+    (gas structure, input only), Z = 0.
+
+    T(R) = 36 K (R / 20 au)^-1/2 and Sigma_g = 10 g cm^-2 (R / 20 au)^-1 by
+    default, so that the 20 au ring has the temperature of the paper's
+    comparison with a surface-density code (Sec. 5.1: 20 au, 36 K, mu 2.4,
+    alpha 1e-3, v_frag 1 m/s); the surface density is not given there and
+    is a choice of this generator.  Initial dust: MRN below 1 micron with
+    dust-to-gas ratio d2g (in surface density)."""
+    au, yr = CONST["au"], CONST["yr"]
+    if n_R == 1:
+        R = np.array([R_in_au * au])
+    else:
+        R_edges = au * np.exp(np.linspace(np.log(R_in_au), np.log(R_out_au), n_R + 1))
+        R = np.sqrt(R_edges[1:] * R_edges[:-1])
+    x = R / (20.0 * au)
+    Tc = np.full(n_R, 36.0) * x ** -0.5 if T is None else np.broadcast_to(np.asarray(T, float), (n_R,)).copy()
+    Sg = 10.0 * x ** -1.0 if Sigma_g is None else np.broadcast_to(np.asarray(Sigma_g, float), (n_R,)).copy()
+    cs = np.sqrt(CONST["k_B"] * Tc / (mu * CONST["m_H"]))
+    Om = np.sqrt(CONST["G"] * CONST["M_sun"] / R ** 3)
+    H = cs / Om
+    rho_mid = Sg / (np.sqrt(2 * np.pi) * H)
+    m, me, a = log_mass_grid(n_bins, a_min, a_max, rho_m)
+    rng = np.random.default_rng(seed if seed is not None else 0)
+    al = np.full(n_R, alpha) if seed is None else alpha * 10.0 ** (0.2 * rng.standard_normal(n_R))
+    sig0 = mrn_initial(a, Sg, d2g=d2g)
+    return Disc(name=name, n_R=n_R, n_Z=1, m=m, me=me, rho_gas=rho_mid, T=Tc, alpha=al, R=R,
+                Z=np.zeros(n_R), eta=11.0 / 8.0 * (H / R) ** 2, rho0=sig0, t_span=t_span_yr * yr,
+                v_frag=v_frag, rho_m=rho_m, mu=mu, vertical=1, extra=dict(a=a, H=H, Sigma_g=Sg))
+
+
+def ring_20au(**kw) -> Disc:
+    """One ring at 20 au with the paper's comparison parameters (Sec. 5.1),
+    150 bins 0.1 um - 10 cm (the paper used 200 species; 160 is this
+    library's limit), 1e4 yr."""
+    return make_ring_disc(1, 150, 1e-5, 10.0, 20.0, 20.0, 1e4, alpha=1e-3, v_frag=100.0,
+                          name="ring_20au_N150", **kw)
+
+
+def rings_4096(**kw) -> Disc:
+    """4096 rings log-spaced over 5-100 au, 100 bins 0.1 um - 10 cm,
+    alpha 1e-3 (0.2 dex scatter), v_frag 1 m/s, 1e4 yr."""
+    return make_ring_disc(4096, 100, 1e-5, 10.0, 5.0, 100.0, 1e4, alpha=1e-3, v_frag=100.0,
+                          seed=8, name="rings_4096_N100", **kw)
 
 
 def adjoint_loss_weights(disc: Disc, a_max_small=1e-3):
