@@ -124,6 +124,18 @@ typedef struct {
                                     to it), so that several contexts run
                                     side by side; 0 = all.  The batched
                                     interface below sets it per disc. */
+    int vertical;                /* 0: volume densities of (R, Z) cells (Sec. 5);
+                                    1: vertically integrated kernel (Sec. 5.1):
+                                    rho holds dust SURFACE densities per bin,
+                                    each cell is a radius (Z unused), rho_gas
+                                    its mid-plane gas density; grains form
+                                    Gaussian layers of scale height
+                                    h = H sqrt(alpha / (alpha + St)) (H =
+                                    c_s / Omega_K), settle at their terminal
+                                    velocity at Z = h (unless v_dust is given)
+                                    and K_ij is divided by
+                                    sqrt(2 pi (h_i^2 + h_j^2)).  The adjoint
+                                    (cudisc_coag_vjp) returns CUDISC_ENOTSUP. */
 } cudisc_coag_params;
 
 typedef struct {

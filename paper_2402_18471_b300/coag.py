@@ -43,6 +43,7 @@ class cudisc_coag_params(C.Structure):
         ("stream", C.c_void_p),
         ("mixed_cluster", C.c_int),
         ("max_sms", C.c_int),
+        ("vertical", C.c_int),
     ]
 
 
@@ -317,6 +318,7 @@ class Coag:
         p.max_substeps = int(s["max_substeps"])
         p.mixed_cluster = int(s.get("mixed_cluster", 0))
         p.max_sms = int(s.get("max_sms", 0))
+        p.vertical = int(s.get("vertical", 0))
         self.params = p
 
     def close(self):

@@ -237,6 +237,7 @@ static cudisc_status validate(const cudisc_coag_params *p, std::string &why)
         return CUDISC_EINVAL;
     }
     if (p->max_sms < 0) { why = "max_sms must be >= 0 (0: all SMs)"; return CUDISC_EINVAL; }
+    if (p->vertical != 0 && p->vertical != 1) { why = "vertical must be 0 or 1"; return CUDISC_EINVAL; }
     if (!(p->rho_m > 0) || !(p->mu > 0) || !(p->Mstar > 0) || !(p->k_B > 0) || !(p->m_H > 0) ||
         !(p->G > 0) || !(p->sigma_H2 > 0)) {
         why = "rho_m, mu, Mstar, k_B, m_H, G and sigma_H2 must be positive";
@@ -746,6 +747,8 @@ cudisc_status cudisc_coag_vjp(cudisc_coag_ctx *c, const double *rho0, double t_s
     if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
     if (!rho0 || !grad_rhoT || !grad_rho0)
         return fail(c, CUDISC_EINVAL, "rho0, grad_rhoT and grad_rho0 must be device arrays");
+    if (c->p.vertical)
+        return fail(c, CUDISC_ENOTSUP, "the adjoint covers the volume-density kernel only (vertical = 0)");
     if (!cdc::vjp_fits(c))
         return fail(c, CUDISC_ENOTSUP, "n_bins too large for the adjoint's per-cell shared memory");
     const size_t nc = (size_t)c->n_cells;

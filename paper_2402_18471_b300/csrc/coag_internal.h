@@ -45,7 +45,8 @@ struct CellScal {
 };
 
 // Per-cell, per-bin fields of the prep kernel, stored [cell][field][N].
-enum PrepField { PF_ST = 0, PF_VR, PF_VPHI, PF_VZ, PF_G1, PF_G2, PF_COUNT };
+// PF_H: grain scale height (vertically integrated kernel; 0 otherwise).
+enum PrepField { PF_ST = 0, PF_VR, PF_VPHI, PF_VZ, PF_G1, PF_G2, PF_H, PF_COUNT };
 // FP32 copy: St and each input velocity as an FP32 hi/lo pair, so that
 // differences of nearly equal velocities keep their precision.
 // P3_SS, P3_SSMD, P3_OMSS: St* = clamp(1.6 St, Re^-1/2, 1), St* - Re^-1/2 and
@@ -53,8 +54,9 @@ enum PrepField { PF_ST = 0, PF_VR, PF_VPHI, PF_VZ, PF_G1, PF_G2, PF_COUNT };
 // differences can be tiny next to their operands).
 // P3_U = 8 k_B T / (pi m_k) (so v_BM^2 = U_i + U_j), P3_A = a_k, P3_M = m_k:
 // the pair loop of the FP32 builder then needs no FP64 arithmetic.
+// P3_HH = 2 pi h^2 (vertically integrated kernel: K / sqrt(HH_i + HH_j)).
 enum Prep32Field { P3_ST = 0, P3_VRH, P3_VRL, P3_VPH, P3_VPL, P3_VZH, P3_VZL,
-                   P3_SS, P3_SSMD, P3_OMSS, P3_U, P3_A, P3_M, P3_COUNT };
+                   P3_SS, P3_SSMD, P3_OMSS, P3_U, P3_A, P3_M, P3_HH, P3_COUNT };
 
 // Per-cell integration scalars written back by the step kernels.
 struct CellOut {

@@ -17,7 +17,7 @@ namespace {
 
 struct KParams {
     double k_B, m_H, G, Mstar, mu, rho_m, sigma_H2, v_frag, kernel_const;
-    int kernel_mode, frag_mode;
+    int kernel_mode, frag_mode, vertical;
 };
 
 KParams kparams(const cudisc_coag_params &p)
@@ -26,12 +26,16 @@ KParams kparams(const cudisc_coag_params &p)
     k.k_B = p.k_B; k.m_H = p.m_H; k.G = p.G; k.Mstar = p.Mstar; k.mu = p.mu;
     k.rho_m = p.rho_m; k.sigma_H2 = p.sigma_H2; k.v_frag = p.v_frag;
     k.kernel_const = p.kernel_const; k.kernel_mode = p.kernel_mode; k.frag_mode = p.frag_mode;
+    k.vertical = p.vertical;
     return k;
 }
 
 // One thread per (cell, bin): Epstein Stokes number (Eq. t_stop, St = t_s
 // Omega), dust velocities (input or terminal drift and settling), and the
-// per-bin parts of the Ormel & Cuzzi closed forms.
+// per-bin parts of the Ormel & Cuzzi closed forms.  Vertically integrated
+// kernel (Sec. 5.1): the cell is a radius at Z = 0, each grain a Gaussian
+// layer of scale height h = H sqrt(alpha / (alpha + St)) settling at its
+// terminal velocity at Z = h.
 __global__ void __launch_bounds__(128) prep_kernel(
     int c0, KParams kp, int n_cells, int N, const double *__restrict__ a, const double *__restrict__ m,
     const double *__restrict__ rho_gas, const double *__restrict__ T,
@@ -43,7 +47,7 @@ __global__ void __launch_bounds__(128) prep_kernel(
     const int c = c0 + blockIdx.y;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cells || k >= N) return;
-    const double Tc = T[c], rg = rho_gas[c], Rc = R[c], Zc = Z[c], al = alpha[c];
+    const double Tc = T[c], rg = rho_gas[c], Rc = R[c], Zc = kp.vertical ? 0.0 : Z[c], al = alpha[c];
     const double cs = sqrt(kp.k_B * Tc / (kp.mu * kp.m_H));
     const double vth = sqrt(8.0 / M_PI) * cs;
     const double r2 = Rc * Rc + Zc * Zc;
@@ -54,6 +58,7 @@ __global__ void __launch_bounds__(128) prep_kernel(
     const double Re = nu_t / nu_mol;
     const double delta = 1.0 / sqrt(Re);
     const double St = kp.rho_m * a[k] / (rg * vth) * Om;
+    const double hk = kp.vertical ? (cs / Om_mid) * sqrt(al / (al + St)) : 0.0;
     double vR, vphi, vZ;
     if (v_dust) {
         const size_t nc = (size_t)n_cells * N;
@@ -65,13 +70,13 @@ __global__ void __launch_bounds__(128) prep_kernel(
         const double vK = Om * Rc;
         vR = -2.0 * et * vK * St / (1.0 + St * St);
         vphi = -et * vK / (1.0 + St * St);
-        vZ = -Zc * Om * St / (1.0 + St);
+        vZ = -(kp.vertical ? hk : Zc) * Om * St / (1.0 + St);
     }
     const double g1 = St * St / (1.0 + St);      // St^2 / (t_L + St), t_L = 1
     const double g2 = St * St / (St + delta);    // St^2 / (t_eta + St)
     double *pr = prep + (size_t)c * PF_COUNT * N;
     float *pf = prep32 + (size_t)c * P3_COUNT * N;
-    const double v[PF_COUNT] = {St, vR, vphi, vZ, g1, g2};
+    const double v[PF_COUNT] = {St, vR, vphi, vZ, g1, g2, hk};
 #pragma unroll
     for (int f = 0; f < PF_COUNT; f++) pr[f * N + k] = v[f];
     const float vRh = (float)vR, vPh = (float)vphi, vZh = (float)vZ;
@@ -79,7 +84,7 @@ __global__ void __launch_bounds__(128) prep_kernel(
     const float v32[P3_COUNT] = {(float)St, vRh, (float)(vR - vRh), vPh, (float)(vphi - vPh),
                                  vZh, (float)(vZ - vZh), (float)Ss, (float)(Ss - delta),
                                  (float)(1.0 - Ss), (float)(8.0 * kp.k_B * Tc / (M_PI * m[k])),
-                                 (float)a[k], (float)m[k]};
+                                 (float)a[k], (float)m[k], (float)(2.0 * M_PI * hk * hk)};
 #pragma unroll
     for (int f = 0; f < P3_COUNT; f++) pf[f * N + k] = v32[f];
     if (k == 0) {
@@ -122,6 +127,10 @@ __global__ void __launch_bounds__(256) kbuild64_kernel(
     if (kp.kernel_mode == CUDISC_KERNEL_CONSTANT) K = kp.kernel_const;
     else if (kp.kernel_mode == CUDISC_KERNEL_ADDITIVE) K = kp.kernel_const * (m[i] + m[j]);
     else { const double sa = a[i] + a[j]; K = M_PI * sa * sa * dv; }
+    if (kp.vertical) {
+        const double hi = pr[PF_H * N + i], hj = pr[PF_H * N + j];
+        K /= sqrt(2.0 * M_PI * (hi * hi + hj * hj));
+    }
     double pf;
     if (kp.frag_mode == CUDISC_FRAG_NONE) pf = 0.0;
     else if (kp.frag_mode == CUDISC_FRAG_ALL) pf = 1.0;
@@ -184,8 +193,9 @@ __device__ __forceinline__ float pcoag_f32(float x, float e)
 
 // Shared-memory fields of the FP32 builder, each [NR] (NR = N rounded up to
 // 16, zero-padded so that four consecutive bins load as one 16-byte word):
-// the prep fields P3_*, then 1/(1+St^2) and 1/(1+St).
-enum { KB_INVA = P3_COUNT, KB_INVQ, KB_COUNT };
+// the prep fields P3_* up to P3_M, then 1/(1+St^2) and 1/(1+St), and, for the
+// vertically integrated kernel only, 2 pi h^2.
+enum { KB_INVA = P3_HH, KB_INVQ, KB_HH, KB_COUNT };
 
 // FP32 builder in the blocked pair layout of the mixed contraction: slot
 // q = 16 b + t is pair (blk_i[b], blk_j0[b] + t) and holds {K p_c, K p_f}
@@ -206,27 +216,38 @@ enum { KB_INVA = P3_COUNT, KB_INVQ, KB_COUNT };
 //   modes are the closed-form test kernels); HasVdust = input velocities.
 constexpr int kPosTile = 8;                 // cells per CTA (one per warp of 256 threads)
 
-// words of shared memory per cell: KB_COUNT fields of NR, rounded to 16 bytes
-__host__ __device__ inline int kb_cell_stride(int NR) { return (KB_COUNT * NR + 3) / 4 * 4; }
+// words of shared memory per cell: the fields above (without KB_HH unless
+// vertical) of NR each, rounded to 16 bytes
+__host__ __device__ inline int kb_cell_stride(int NR, bool vertical)
+{
+    return ((vertical ? KB_COUNT : KB_HH) * NR + 3) / 4 * 4;
+}
 
 template <bool Physical, bool HasVdust>
 __global__ void __launch_bounds__(256) kbuild32_kernel(
-    float kc, float v_frag, int kernel_mode, int frag_mode, int n_cells, int N, int NR,
+    float kc, float v_frag, int kernel_mode, int frag_mode, int vertical, int n_cells, int N, int NR,
     int n_slots, const int *__restrict__ blk_i, const int *__restrict__ blk_j0,
     const float *__restrict__ prep32, const float4 *__restrict__ scal32,
     float2 *__restrict__ Kout)
 {
     extern __shared__ __align__(16) float f32s[];       // [kPosTile][cell stride]: [KB_COUNT][NR] each
-    const int CS = kb_cell_stride(NR);
+    const int CS = kb_cell_stride(NR, vertical);
     const int cell0 = blockIdx.x * kPosTile;
     __shared__ int s_cell[kPosTile];
     if (threadIdx.x < kPosTile) s_cell[threadIdx.x] = cell0 + threadIdx.x < n_cells ? cell0 + threadIdx.x : -1;
     __syncthreads();
-    for (int t = threadIdx.x; t < kPosTile * P3_COUNT * NR; t += blockDim.x) {
-        const int jc = t / (P3_COUNT * NR), r = t - jc * (P3_COUNT * NR);
+    for (int t = threadIdx.x; t < kPosTile * P3_HH * NR; t += blockDim.x) {
+        const int jc = t / (P3_HH * NR), r = t - jc * (P3_HH * NR);
         const int f = r / NR, k = r - f * NR;
         const int c = s_cell[jc];
         f32s[jc * CS + r] = (c >= 0 && k < N) ? prep32[((size_t)c * P3_COUNT + f) * N + k] : 0.0f;
+    }
+    if (vertical) {
+        for (int t = threadIdx.x; t < kPosTile * NR; t += blockDim.x) {
+            const int jc = t / NR, k = t - jc * NR;
+            const int c = s_cell[jc];
+            f32s[jc * CS + KB_HH * NR + k] = (c >= 0 && k < N) ? prep32[((size_t)c * P3_COUNT + P3_HH) * N + k] : 0.0f;
+        }
     }
     __syncthreads();
     for (int t = threadIdx.x; t < kPosTile * NR; t += blockDim.x) {
@@ -330,6 +351,7 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
                     pc = pcoag_f32(x, e);
                 }
             }
+            if (vertical) K *= rsqrt_ftz(F[KB_HH * NR + i] + F[KB_HH * NR + j]);
             const bool live = j <= i;
             o[2 * u] = live ? K * pc : 0.0f;
             o[2 * u + 1] = live ? K * pf : 0.0f;
@@ -392,15 +414,18 @@ cudaError_t launch_kbuild(const cudisc_coag_ctx *c)
     } else {
         const int n_slots = c->n_blk * kBlkPairs;
         const int NR = (c->N + 15) / 16 * 16;
-        const size_t smem = (size_t)kPosTile * kb_cell_stride(NR) * sizeof(float);
+        const size_t smem = (size_t)kPosTile * kb_cell_stride(NR, p.vertical != 0) * sizeof(float);
         const bool phys = p.kernel_mode == CUDISC_KERNEL_PHYSICAL && p.frag_mode == CUDISC_FRAG_PHYSICAL;
-        const bool vd = p.v_dust != nullptr;
+        // the vertically integrated kernel's settling velocities (each grain
+        // at its own height) do not factor through St_i - St_j: take the
+        // differences of the prep kernel's FP32 hi/lo velocity pairs
+        const bool vd = p.v_dust != nullptr || p.vertical;
         auto kern = phys ? (vd ? kbuild32_kernel<true, true> : kbuild32_kernel<true, false>)
                          : (vd ? kbuild32_kernel<false, true> : kbuild32_kernel<false, false>);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<(c->n_cells + kPosTile - 1) / kPosTile, 256, smem, c->stream>>>(
-            (float)p.kernel_const, (float)p.v_frag, p.kernel_mode, p.frag_mode, c->n_cells, c->N, NR,
+            (float)p.kernel_const, (float)p.v_frag, p.kernel_mode, p.frag_mode, p.vertical, c->n_cells, c->N, NR,
             n_slots, c->d_blk_i, c->d_blk_j0, c->d_prep32, c->d_scal32,
             c->d_K32);
     }
