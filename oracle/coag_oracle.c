@@ -87,6 +87,13 @@ typedef struct {
     double rtol, atol_rel;
     long max_substeps;
     int vertical;           /* 1: vertically integrated kernel (Sec. 5.1) */
+    /* Sensitivity runs only (not part of the method): K_ij (1 + kernel_perturb
+     * u) and, in replays, every stage input y_k (1 + stage_noise u), u uniform
+     * in [-1/2, 1/2), drawn per (perturb_seed, cell, pair) and per
+     * (perturb_seed, cell, step, stage, bin). */
+    double kernel_perturb;
+    unsigned long long perturb_seed;
+    double stage_noise;
 } oracle_params;
 
 enum { ST_OK = 0, ST_MAXSTEPS = 4, ST_NONFINITE = 5, ST_DTMIN = 7 };
@@ -182,7 +189,22 @@ double oracle_pfrag(double dv, double vf)
 typedef struct {
     double cs, Re, Vg2, T;
     double *a, *St, *vR, *vphi, *vZ, *h;   /* h: grain scale heights (vertical mode) */
+    int cell;
 } cellphys;
+
+/* SplitMix64 finaliser (Steele, Lea & Flood 2014) of a counter: a uniform
+ * number in [-1/2, 1/2) for the sensitivity runs. */
+static double counter_uniform(unsigned long long seed, unsigned long long a, unsigned long long b,
+                              unsigned long long c)
+{
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (1ull + a);
+    z ^= b * 0xD1B54A32D192ED03ull;
+    z += c * 0x8CB92BA72F3D8DD7ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+}
 
 static void cell_physics(const oracle_params *P, int c, cellphys *cp)
 {
@@ -198,6 +220,7 @@ static void cell_physics(const oracle_params *P, int c, cellphys *cp)
     double lmfp = P->mu * P->m_H / (rg * P->sigma_H2);
     double nu_mol = 0.5 * vth * lmfp;
     cp->cs = cs;
+    cp->cell = c;
     cp->Re = nu_t / nu_mol;
     cp->Vg2 = P->alpha[c] * cs * cs;
     cp->T = T;
@@ -245,6 +268,11 @@ static void pair_kernel(const oracle_params *P, const cellphys *cp, int i, int j
     else k = M_PI * s * s * dv;
     /* vertically integrated: the rate of two Gaussian layers per unit area */
     if (P->vertical) k /= sqrt(2.0 * M_PI * (cp->h[i] * cp->h[i] + cp->h[j] * cp->h[j]));
+    if (P->kernel_perturb != 0.0) {   /* sensitivity runs only, symmetric in i, j */
+        const int a = i > j ? i : j, b = i > j ? j : i;
+        k *= 1.0 + P->kernel_perturb * counter_uniform(P->perturb_seed, (unsigned long long)cp->cell,
+                                                       (unsigned long long)a, (unsigned long long)b);
+    }
     double p;
     if (P->frag_mode == 1) p = 0.0;
     else if (P->frag_mode == 2) p = 1.0;
@@ -674,6 +702,31 @@ int oracle_step_spans(const oracle_params *P, double *rho, const double *spans, 
 
 /* Replay: apply a given sequence of accepted BS3 steps to every cell
  * (hs[c*stride + s], s < n_h[c]).  Parity: pinned as oracle_step. */
+/* The replay of bs3_fixed with every stage input perturbed by a relative
+ * stage_noise u (sensitivity runs only): the same three stages, each right-
+ * hand side evaluated at Y_k (1 + stage_noise u). */
+static void bs3_fixed_noisy(cellctx *cx, int n, double *y, const double *hs, long nh)
+{
+    const oracle_params *P = cx->P;
+    double *k1 = xmalloc(sizeof(double) * n), *k2 = xmalloc(sizeof(double) * n);
+    double *k3 = xmalloc(sizeof(double) * n), *Y = xmalloc(sizeof(double) * n);
+    for (long s = 0; s < nh; s++) {
+        double h = hs[s];
+        for (int st = 0; st < 3; st++) {
+            for (int k = 0; k < n; k++) {
+                double v = st == 0 ? y[k] : st == 1 ? y[k] + h * BS_A21 * k1[k] : y[k] + h * BS_A32 * k2[k];
+                Y[k] = v * (1.0 + P->stage_noise * counter_uniform(P->perturb_seed, (unsigned long long)cx->c,
+                                                                    (unsigned long long)(3 * s + st),
+                                                                    (unsigned long long)k + 0x100000000ull));
+            }
+            rhs_cell(cx, Y, st == 0 ? k1 : st == 1 ? k2 : k3);
+        }
+        for (int k = 0; k < n; k++)
+            y[k] = y[k] + h * (BS_B1 * k1[k] + BS_B2 * k2[k] + BS_B3 * k3[k]);
+    }
+    free(k1); free(k2); free(k3); free(Y);
+}
+
 int oracle_step_replay(const oracle_params *P, double *rho, const double *hs,
                        const long *n_h, long stride)
 {
@@ -682,7 +735,10 @@ int oracle_step_replay(const oracle_params *P, double *rho, const double *hs,
     for (int c = 0; c < P->n_cells; c++) {
         cellctx cx;
         cell_alloc(P, c, &cx);
-        bs3_fixed(rhs_cell, &cx, N, rho + (size_t)c * N, hs + (size_t)c * stride, n_h[c]);
+        if (P->stage_noise != 0.0)
+            bs3_fixed_noisy(&cx, N, rho + (size_t)c * N, hs + (size_t)c * stride, n_h[c]);
+        else
+            bs3_fixed(rhs_cell, &cx, N, rho + (size_t)c * N, hs + (size_t)c * stride, n_h[c]);
         cell_free(&cx);
     }
     return 0;

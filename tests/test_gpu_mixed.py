@@ -18,6 +18,8 @@ import pytest
 
 from paper_2402_18471_b300 import synth
 
+from long_run import long_run_bound
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -252,3 +254,26 @@ def test_full_size_fp64_step_conserves_mass(coag_mod):
     st = g.step(y, d.t_span)
     assert st["status"] == 0
     assert st["mass_err_max"] < 1e-12, st["mass_err_max"]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_size_long_run_sampled_cells(coag_mod, oracle_mod, precision):
+    """The benchmark's step at full size and in its launch configuration:
+    all 8192 cells over 1e4 yr; on 12 sampled cells the oracle replays the
+    GPU's accepted steps.  Every bin within the long-run bound (see
+    long_run.py), at least 97 % within 1e-5 |rho| + 1e-10 S, mass to 1e-9."""
+    d = synth.grid_128x64()
+    g = coag_mod.Coag(d, precision)
+    rec = g.set_records(2000)
+    y = g.state(d.rho0)
+    st = g.step(y, d.t_span)
+    assert st["status"] == 0 and st["n_failed"] == 0
+    assert st["mass_err_max"] < (1e-12 if precision == "fp64" else 1e-9)
+    n = rec["n"].cpu().numpy()
+    assert n.max() <= 2000 and st["accepted"] == n.sum()
+    cells = np.arange(0, d.n_cells, 683)[:12]
+    y0, strict, bound = long_run_bound(oracle_mod, d.subset(cells), d.rho0[cells],
+                                       rec["dt"].cpu().numpy()[cells], n[cells], precision)
+    dev = np.abs(y.cpu().numpy()[cells] - y0)
+    assert np.all(dev <= bound), (dev / bound).max()
+    assert np.mean(dev <= strict) >= 0.97
