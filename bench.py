@@ -33,6 +33,7 @@ WORKLOADS = {
     "column_1x32_N50": synth.column_1x32,
     "adjoint_64x32_N80": synth.adjoint_64x32,
     "grid_512x256_N150": synth.grid_512x256,
+    "rings_4096_N100": synth.rings_4096,     # vertically integrated kernel (surface densities)
 }
 METRIC = "cell-substeps/s, 128x64 cells x 100 bins: mixed vs FP64 GPU, rel err<=1e-5"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -369,7 +370,9 @@ def main():
             "config": {"workload": args.workload, "n_cells": disc.n_cells, "n_bins": N,
                        "t_span_yr": disc.t_span / synth.CONST["yr"],
                        "precision": args.precision, "rtol": disc.rtol, "atol_rel": disc.atol_rel,
-                       "l2": "K tables larger than L2 (FP32 331 MB / FP64 404 MB) are rebuilt every step",
+                       "l2": "K tables (FP32 %.0f MB / FP64 %.0f MB; L2 126 MB) are rebuilt every step"
+                             % (disc.n_cells * N * (N + 1) / 2 * 8 / 1e6, disc.n_cells * N * (N + 1) / 2 * 16 / 1e6),
+                       **({"vertical": 1} if disc.vertical else {}),
                        "step": "kernel build + BS3 integration of all cells over t_span",
                        **({"state": "FP32 pair y/Sx = yh + yl (48 bits), FP64 time and step size",
                            "mixed_cluster": main_res["g"].mixed_cluster()[0],
