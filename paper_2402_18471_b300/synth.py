@@ -157,7 +157,7 @@ def _disc_fields(R_c, n_Z, T0, Sigma0, h0, rng, rho_pert):
     Rg = np.repeat(R_c[:, None], n_Z, axis=1)
     eta = np.repeat((11.0 / 8.0 * hR ** 2)[:, None], n_Z, axis=1)
     return (rho.reshape(-1), T.reshape(-1), Rg.reshape(-1), Z_c.reshape(-1),
-            eta.reshape(-1), Z_edges)
+            eta.reshape(-1), Z_edges, Sig)
 
 
 def mrn_initial(a, rho_gas, a_cut=1e-4, d2g=0.01):
@@ -178,7 +178,7 @@ def make_disc(n_R, n_Z, n_bins, a_min, a_max, R_in_au, R_out_au, t_span_yr,
     else:
         R_edges = au * np.exp(np.linspace(np.log(R_in_au), np.log(R_out_au), n_R + 1))
         R_c = np.sqrt(R_edges[1:] * R_edges[:-1])
-    rho, T, R, Z, eta, Z_edges = _disc_fields(R_c, n_Z, T0, Sigma0, h0, rng, rho_pert)
+    rho, T, R, Z, eta, Z_edges, Sig = _disc_fields(R_c, n_Z, T0, Sigma0, h0, rng, rho_pert)
     n_cells = rho.shape[0]
     if alpha_dex:
         al = alpha * 10.0 ** (alpha_dex * rng.standard_normal(n_cells))
@@ -189,7 +189,7 @@ def make_disc(n_R, n_Z, n_bins, a_min, a_max, R_in_au, R_out_au, t_span_yr,
     return Disc(name=name, n_R=n_R, n_Z=n_Z, m=m, me=me, rho_gas=rho, T=T,
                 alpha=al, R=R, Z=Z, eta=eta, rho0=rho0, t_span=t_span_yr * yr,
                 v_frag=v_frag, rho_m=rho_m, R_edges=R_edges, Z_edges=Z_edges,
-                extra=dict(a=a))
+                extra=dict(a=a, Sigma_g=Sig))
 
 
 # ---------------------------------------------------------------------------
@@ -286,6 +286,28 @@ def rings_4096(**kw) -> Disc:
     alpha 1e-3 (0.2 dex scatter), v_frag 1 m/s, 1e4 yr."""
     return make_ring_disc(4096, 100, 1e-5, 10.0, 5.0, 100.0, 1e4, alpha=1e-3, v_frag=100.0,
                           seed=8, name="rings_4096_N100", **kw)
+
+
+def hse_inputs(disc: Disc, t_rise=0.0):
+    """Inputs of the hydrostatic-equilibrium gas density for the (R, Z) grid
+    of a disc from make_disc: cell centres R, Z and temperatures T as
+    [n_R, n_Z] arrays, cylindrical cell volumes per radian V = (R dR) dZ
+    with (R dR) = (R_{i+1}^2 - R_i^2) / 2 over the radial edges, those edges,
+    and the column surface densities.  The grid holds the upper half of each
+    column (Z >= 0), so its surface density is half of Sigma_g.  t_rise > 0
+    warms the upper layers: T = T_mid (1 + t_rise (Z / Z_top)^2), Z_top the
+    column's upper edge (a stand-in for a temperature solver's output)."""
+    n_R, n_Z = disc.n_R, disc.n_Z
+    R = disc.R.reshape(n_R, n_Z)
+    Z = disc.Z.reshape(n_R, n_Z)
+    Ze = disc.Z_edges
+    T = disc.T.reshape(n_R, n_Z) * (1.0 + t_rise * (Z / Ze[:, -1:]) ** 2)
+    RdR = 0.5 * (disc.R_edges[1:] ** 2 - disc.R_edges[:-1] ** 2)
+    V = RdR[:, None] * np.diff(Ze, axis=1)
+    return dict(R=np.ascontiguousarray(R), Z=np.ascontiguousarray(Z), T=np.ascontiguousarray(T),
+                V=np.ascontiguousarray(V), R_edges=np.ascontiguousarray(disc.R_edges),
+                Sigma_g=np.ascontiguousarray(0.5 * disc.extra["Sigma_g"]), mu=disc.mu,
+                m_H=CONST["m_H"], k_B=CONST["k_B"], GM=CONST["G"] * disc.Mstar)
 
 
 def adjoint_loss_weights(disc: Disc, a_max_small=1e-3):
