@@ -173,6 +173,36 @@ def combine_ranks(dist, device, ms, e2e_s, sub, e2e_sub):
     return float(t[0]), float(t[1]), int(u[0]), int(u[1])
 
 
+def hse_roofline(coag, device, pk, n_R=4096, n_Z=1024, reps=10):
+    """The hydrostatic-equilibrium density kernel (Sec. 3.5) on a 4096 x 1024
+    grid (inputs 134 MB + output 34 MB, larger than L2), timed with CUDA
+    events on torch's current stream, which it launches on.  Algorithmic
+    bytes: R, Z, T, V read and rho written once, 40 B per cell."""
+    import torch
+    d = synth.make_disc(n_R, n_Z, 2, 1e-5, 1e-4, 5.0, 100.0, 1.0, seed=1)
+    inp = synth.hse_inputs(d, t_rise=2.0)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=device)
+    args = [dev(inp[k]) for k in ("R", "Z", "T", "V", "R_edges", "Sigma_g")]
+    out = torch.empty((n_R, n_Z), dtype=torch.float64, device=device)
+    consts = (inp["mu"], inp["m_H"], inp["k_B"], inp["GM"])
+    for _ in range(3):
+        coag.hse_rho_gas(*args, *consts, out=out)
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        coag.hse_rho_gas(*args, *consts, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.mean(ts))
+    gbs = 40.0 * n_R * n_Z / (ms * 1e-3) / 1e9
+    return {"kernel": "hse_kernel", "grid": f"{n_R}x{n_Z}", "ms_per_launch": ms, "bound": "fp64 alu",
+            "achieved": gbs, "unit": "GB/s", "hbm_frac": gbs / pk["hbm_gbs"],
+            "note": "one FP64 exp (or a 12-term series), division and reciprocal square root per cell; "
+                    "FP64 issue, not HBM, bounds it"}
+
+
 def run_reference(args, disc, rank, world):
     if rank != 0:
         return
@@ -392,6 +422,7 @@ def main():
         if fp64_res is not None:
             v64 = fp64_res["sub"] / (fp64_res["ms"] / 1e3)
             line["fp64_gpu"] = {"value": v64, "unit": "cell-substeps/s", "speedup_mixed_over_fp64": value / v64}
+        line["roofline_hse"] = hse_roofline(coag, "cuda", pk)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(disc, budget_s=args.cpu_budget)
         print(json.dumps(line), flush=True)

@@ -200,6 +200,27 @@ cudisc_status cudisc_coag_step_wait(cudisc_coag_ctx *ctx, cudisc_step_stats *sta
 cudisc_status cudisc_coag_step_spans(cudisc_coag_ctx *ctx, double *rho, const double *t_span,
                                      double *dt_cell, cudisc_step_stats *stats);
 
+/* Gas density from hydrostatic equilibrium (Sec. 3.5, Eqs. hydroeqbm,
+ * hedisc, avcs, heprod, rhonorm), the rho_gas a context's kernel build
+ * reads.  Per column i of an (R, Z) grid, for cells j = 0 .. n_Z - 1 in
+ * order of height: P_j / P_{j-1} = exp[GM <1/c_s^2> (1/r_j - 1/r_{j-1})]
+ * with <1/c_s^2> the mean of the two cells' 1/c_s^2, c_s^2 = k_B T /
+ * (mu m_H), r = sqrt(R^2 + Z^2); P_j / P_0 their running product; the
+ * density P / c_s^2 scaled so that sum_j rho_j V_j = Sigma_g,i (R dR)_i,
+ * (R dR)_i = ((R_edges[i+1])^2 - R_edges[i]^2) / 2.
+ * Device arrays, FP64, cell (i, j) at i * n_Z + j: R, Z (cell centres, cm),
+ * T (K, > 0), V (cell volumes per radian, > 0), rho_gas (out, g cm^-3);
+ * R_edges [n_R + 1] (cm), Sigma_g [n_R] (the column mass per unit area
+ * held by its cells, g cm^-2).  mu, m_H (g), k_B (erg/K) and GM = G M_*
+ * (cm^3 s^-2) must be positive.  Asynchronous on stream (a cudaStream_t,
+ * NULL: the legacy default stream); allocates nothing; needs no context.
+ * Errors: CUDISC_EINVAL for sizes < 1, NULL arrays or non-positive
+ * constants (cudisc_coag_last_error(NULL) names it), CUDISC_ECUDA for a
+ * failed launch. */
+cudisc_status cudisc_hse_rho_gas(int n_R, int n_Z, const double *R, const double *Z, const double *T,
+                                 const double *V, const double *R_edges, const double *Sigma_g, double mu,
+                                 double m_H, double k_B, double GM, double *rho_gas, void *stream);
+
 /* Sub-cycled coagulation (Sec. 6): the coagulation solver takes its own
  * sub-steps inside the global time steps of the disc model, and a cell's
  * coagulation is brought up to date only once one (by default) of its last

@@ -86,6 +86,7 @@ def lib():
         L.cudisc_coag_step.argtypes = [v, v, d, v, C.POINTER(cudisc_step_stats)]
         L.cudisc_coag_step_async.argtypes = [v, v, d, v]
         L.cudisc_coag_step_wait.argtypes = [v, C.POINTER(cudisc_step_stats)]
+        L.cudisc_hse_rho_gas.argtypes = [C.c_int, C.c_int, v, v, v, v, v, v, d, d, d, d, v, v]
         L.cudisc_coag_step_spans.argtypes = [v, v, v, v, C.POINTER(cudisc_step_stats)]
         L.cudisc_coag_subcycle.argtypes = [v, v, d, d, v, C.POINTER(cudisc_step_stats)]
         L.cudisc_coag_subcycle_pending.argtypes = [v, v, C.c_int]
@@ -113,7 +114,7 @@ def lib():
                    "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp",
                    "cudisc_coag_mixed_cluster", "cudisc_coag_step_async", "cudisc_coag_step_wait",
                    "cudisc_coag_init_batched", "cudisc_coag_batch_ctx", "cudisc_coag_batch_build_kernel",
-                   "cudisc_coag_batch_step", "cudisc_coag_step_spans", "cudisc_coag_subcycle",
+                   "cudisc_hse_rho_gas", "cudisc_coag_batch_step", "cudisc_coag_step_spans", "cudisc_coag_subcycle",
                    "cudisc_coag_subcycle_pending"):
             getattr(L, fn).restype = C.c_int
         _lib = L
@@ -185,6 +186,30 @@ def cudisc_coag_subcycle(ctx, rho_ptr, dt_global, trigger, dt_ptr, check=True):
 
 def cudisc_coag_subcycle_pending(ctx, pending_ptr, reset):
     _check(lib().cudisc_coag_subcycle_pending(ctx, pending_ptr, int(bool(reset))), ctx)
+
+
+def cudisc_hse_rho_gas(n_R, n_Z, R_ptr, Z_ptr, T_ptr, V_ptr, Re_ptr, Sig_ptr, mu, m_H, k_B, GM, rho_ptr,
+                       stream=None):
+    _check(lib().cudisc_hse_rho_gas(int(n_R), int(n_Z), R_ptr, Z_ptr, T_ptr, V_ptr, Re_ptr, Sig_ptr,
+                                    float(mu), float(m_H), float(k_B), float(GM), rho_ptr, stream))
+
+
+def hse_rho_gas(R, Z, T, V, R_edges, Sigma_g, mu, m_H, k_B, GM, out=None):
+    """Hydrostatic-equilibrium gas density [n_R, n_Z] on the GPU (Sec. 3.5)
+    from device FP64 tensors R, Z, T, V [n_R, n_Z], R_edges [n_R + 1] and
+    Sigma_g [n_R], on torch's current stream; out (optional) receives it."""
+    import torch
+    ts = [t.contiguous() for t in (R, Z, T, V, R_edges, Sigma_g)]
+    for t in ts:
+        assert t.dtype == torch.float64 and t.is_cuda
+    n_R, n_Z = ts[0].shape
+    assert ts[4].numel() == n_R + 1 and ts[5].numel() == n_R
+    assert all(t.shape == (n_R, n_Z) for t in ts[1:4])
+    if out is None:
+        out = torch.empty((n_R, n_Z), dtype=torch.float64, device=ts[0].device)
+    cudisc_hse_rho_gas(n_R, n_Z, *(t.data_ptr() for t in ts), mu, m_H, k_B, GM, out.data_ptr(),
+                       torch.cuda.current_stream(ts[0].device).cuda_stream)
+    return out
 
 
 def cudisc_coag_init_batched(params_list):

@@ -690,6 +690,24 @@ cudisc_status cudisc_coag_subcycle_pending(cudisc_coag_ctx *c, double *pending, 
     return CUDISC_OK;
 }
 
+cudisc_status cudisc_hse_rho_gas(int n_R, int n_Z, const double *R, const double *Z, const double *T,
+                                 const double *V, const double *R_edges, const double *Sigma_g, double mu,
+                                 double m_H, double k_B, double GM, double *rho_gas, void *stream)
+{
+    g_thread_err.clear();
+    if (n_R < 1 || n_Z < 1) return fail(nullptr, CUDISC_EINVAL, "n_R and n_Z must be >= 1");
+    if ((long long)n_R * n_Z > (1ll << 40)) return fail(nullptr, CUDISC_EINVAL, "n_R x n_Z is too large");
+    if (!R || !Z || !T || !V || !R_edges || !Sigma_g || !rho_gas)
+        return fail(nullptr, CUDISC_EINVAL, "R, Z, T, V, R_edges, Sigma_g and rho_gas must be device arrays");
+    const double pos[4] = {mu, m_H, k_B, GM};
+    for (double v : pos)
+        if (!(v > 0.0) || !std::isfinite(v)) return fail(nullptr, CUDISC_EINVAL, "mu, m_H, k_B and GM must be positive");
+    cudaError_t e = cdc::launch_hse(n_R, n_Z, R, Z, T, V, R_edges, Sigma_g, mu, m_H, k_B, GM, rho_gas,
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudisc_hse_rho_gas");
+    return CUDISC_OK;
+}
+
 cudisc_status cudisc_coag_step_async(cudisc_coag_ctx *c, double *rho, double t_span, double *dt_cell)
 {
     if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");

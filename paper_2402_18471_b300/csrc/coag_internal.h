@@ -157,6 +157,10 @@ size_t mixed_workspace_bytes(int n_cells, int N, int P, int max_sms);
 // cluster size P for a request P_req (0: automatic), groups of slots G and
 // initial cells per group C of the mixed kernel
 void mixed_layout(int n_cells, int N, int P_req, int max_sms, int *P, int *G, int *C);
+// hydrostatic-equilibrium gas density (hse.cu)
+cudaError_t launch_hse(int n_R, int n_Z, const double *R, const double *Z, const double *T, const double *V,
+                       const double *R_edges, const double *Sigma_g, double mu, double m_H, double k_B,
+                       double GM, double *rho, cudaStream_t stream);
 // adjoint (vjp.cu)
 bool vjp_fits(const cudisc_coag_ctx *c);
 cudaError_t vjp_prepare(cudisc_coag_ctx *c, long long max_steps);

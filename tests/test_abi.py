@@ -107,3 +107,15 @@ def test_null_context_is_an_error_not_a_crash():
     assert L.cudisc_coag_batch_step(None, None, 1.0, None, None, None) == coag.EINVAL
     L.cudisc_coag_batch_destroy(None)
     L.cudisc_coag_destroy(None)
+
+
+def test_hse_rejects_bad_arguments_before_any_launch():
+    L = coag.lib()
+    fake = C.c_void_p(16)     # never dereferenced: validation fails first
+    args = [fake] * 6
+    assert L.cudisc_hse_rho_gas(0, 4, *args, 2.4, 1.67e-24, 1.38e-16, 1.3e26, fake, None) == coag.EINVAL
+    assert L.cudisc_hse_rho_gas(3, 0, *args, 2.4, 1.67e-24, 1.38e-16, 1.3e26, fake, None) == coag.EINVAL
+    assert L.cudisc_hse_rho_gas(3, 4, *args, 2.4, 1.67e-24, 1.38e-16, 1.3e26, None, None) == coag.EINVAL
+    assert b"device arrays" in L.cudisc_coag_last_error(None)
+    assert L.cudisc_hse_rho_gas(3, 4, *args, 2.4, 1.67e-24, 1.38e-16, -1.0, fake, None) == coag.EINVAL
+    assert b"positive" in L.cudisc_coag_last_error(None)
