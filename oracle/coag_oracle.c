@@ -802,9 +802,29 @@ static void pair_kernel_deriv(const oracle_params *P, const cellphys *cp, int c,
     double cs2 = cp->cs * cp->cs;
     double dd_da = -0.5 * d / alpha;                 /* delta ~ alpha^-1/2 */
     double dvt2_da = cs2 * V + alpha * cs2 * dV_dd * dd_da;
+    /* vertically integrated kernel: h = H sqrt(alpha / (alpha + St)) gives
+     * dh/dalpha = h g with g = St / (2 alpha (alpha + St)); the settling
+     * velocities -h Omega St/(1+St) scale with h, and the factor
+     * f = (2 pi (h_i^2 + h_j^2))^-1/2 has d ln f / dalpha =
+     * -(h_i^2 g_i + h_j^2 g_j) / (h_i^2 + h_j^2) */
+    double gi = 0.0, gj = 0.0;
+    if (P->vertical) {
+        gi = cp->St[i] / (2.0 * alpha * (alpha + cp->St[i]));
+        gj = cp->St[j] / (2.0 * alpha * (alpha + cp->St[j]));
+        if (!P->v_dust) {
+            double dZ = cp->vZ[i] - cp->vZ[j];
+            dvt2_da += 2.0 * dZ * (cp->vZ[i] * gi - cp->vZ[j] * gj);
+        }
+    }
     double ddv_da = dv > 0.0 ? dvt2_da / (2.0 * dv) : 0.0;
     double s = cp->a[i] + cp->a[j];
     *dK_da = (P->kernel_mode == 0) ? M_PI * s * s * ddv_da : 0.0;
+    if (P->vertical) {
+        double hi2 = cp->h[i] * cp->h[i], hj2 = cp->h[j] * cp->h[j];
+        double f = 1.0 / sqrt(2.0 * M_PI * (hi2 + hj2));
+        double dlnf = -(hi2 * gi + hj2 * gj) / (hi2 + hj2);
+        *dK_da = f * *dK_da + K * dlnf;              /* K includes f */
+    }
     double dpf_ddv = 0.0, dpfdvf = 0.0;
     if (P->frag_mode == 0 && dv > 0.0) {
         double x = 1.5 * (P->v_frag / dv) * (P->v_frag / dv);
@@ -862,7 +882,6 @@ int oracle_vjp(const oracle_params *P, const double *rho0, const double *hs, con
                long stride, const double *w, double *g_rho0, double *g_alpha, double *g_vfrag)
 {
     const int N = P->n_bins;
-    if (P->vertical) return 6;   /* the kernel's alpha derivative covers the volume form only */
     double vf_total = 0.0;
     #pragma omp parallel for schedule(dynamic) num_threads(nthreads_of(P)) reduction(+:vf_total)
     for (int c = 0; c < P->n_cells; c++) {
