@@ -135,7 +135,8 @@ typedef struct {
                                     velocity at Z = h (unless v_dust is given)
                                     and K_ij is divided by
                                     sqrt(2 pi (h_i^2 + h_j^2)).  The adjoint
-                                    (cudisc_coag_vjp) returns CUDISC_ENOTSUP. */
+                                    (cudisc_coag_vjp) differentiates h, the
+                                    settling and that factor too. */
 } cudisc_coag_params;
 
 typedef struct {

@@ -765,8 +765,6 @@ cudisc_status cudisc_coag_vjp(cudisc_coag_ctx *c, const double *rho0, double t_s
     if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
     if (!rho0 || !grad_rhoT || !grad_rho0)
         return fail(c, CUDISC_EINVAL, "rho0, grad_rhoT and grad_rho0 must be device arrays");
-    if (c->p.vertical)
-        return fail(c, CUDISC_ENOTSUP, "the adjoint covers the volume-density kernel only (vertical = 0)");
     if (!cdc::vjp_fits(c))
         return fail(c, CUDISC_ENOTSUP, "n_bins too large for the adjoint's per-cell shared memory");
     const size_t nc = (size_t)c->n_cells;

@@ -368,8 +368,8 @@ __global__ void __launch_bounds__(kVjpThreads) vjp_kernel(VjpArgs<T> A)
 //       dp/d dv = 2 x^2 e^-x / dv,   dp/d v_f = -2 x^2 e^-x / v_f
 template <typename T>
 __global__ void __launch_bounds__(256) kderiv_kernel(
-    int c0, int n_cells, int N, int Np, int kernel_mode, int frag_mode, double v_frag,
-    const unsigned int *__restrict__ pij, const int *__restrict__ pair_q, int n_slots,
+    int c0, int n_cells, int N, int Np, int kernel_mode, int frag_mode, double v_frag, int vertical,
+    int has_vdust, const unsigned int *__restrict__ pij, const int *__restrict__ pair_q, int n_slots,
     const double *__restrict__ a, const double *__restrict__ minv,
     const double *__restrict__ prep, const CellScal *__restrict__ scal,
     const double *__restrict__ alpha, const double2 *__restrict__ K64,
@@ -398,13 +398,30 @@ __global__ void __launch_bounds__(256) kderiv_kernel(
     const double dP = pr[PF_VPHI * N + i] - pr[PF_VPHI * N + j];
     const double dZ = pr[PF_VZ * N + i] - pr[PF_VZ * N + j];
     const double dv = sqrt(s.kT8pi * (minv[i] + minv[j]) + s.Vg2 * V + (dR * dR + dP * dP + dZ * dZ));
-    const double cs2 = s.Vg2 / alpha[c];
-    const double ddv2_da = cs2 * (V - 0.5 * s.delta * dvrel2_dd_f64(S1, S2, s.delta));
+    const double al = alpha[c];
+    const double cs2 = s.Vg2 / al;
+    double ddv2_da = cs2 * (V - 0.5 * s.delta * dvrel2_dd_f64(S1, S2, s.delta));
+    // vertically integrated kernel: dh/dalpha = h g, g = St / (2 alpha
+    // (alpha + St)); the settling velocities (at Z = h) scale with h, and the
+    // layer factor f = (2 pi (h_i^2 + h_j^2))^-1/2 has d ln f / dalpha =
+    // -(h_i^2 g_i + h_j^2 g_j) / (h_i^2 + h_j^2)
+    double gi = 0.0, gj = 0.0;
+    if (vertical) {
+        gi = Si / (2.0 * al * (al + Si));
+        gj = Sj / (2.0 * al * (al + Sj));
+        if (!has_vdust) ddv2_da += 2.0 * dZ * (pr[PF_VZ * N + i] * gi - pr[PF_VZ * N + j] * gj);
+    }
     const double ddv_da = dv > 0.0 ? ddv2_da / (2.0 * dv) : 0.0;
     double dK_da = 0.0;
     if (kernel_mode == CUDISC_KERNEL_PHYSICAL) {
         const double sa = a[i] + a[j];
         dK_da = M_PI * sa * sa * ddv_da;
+    }
+    if (vertical) {
+        const double hi = pr[PF_H * N + i], hj = pr[PF_H * N + j];
+        const double hi2 = hi * hi, hj2 = hj * hj;
+        const double f = 1.0 / sqrt(2.0 * M_PI * (hi2 + hj2));
+        dK_da = f * dK_da - K * (hi2 * gi + hj2 * gj) / (hi2 + hj2);   // K includes f
     }
     double pf = 0.0, dpf_ddv = 0.0, dpf_dvf = 0.0;
     if (frag_mode == CUDISC_FRAG_ALL) pf = 1.0;
@@ -562,7 +579,8 @@ cudaError_t launch_t(cudisc_coag_ctx *c, VjpState *S, const double *rho0, const 
     for (int c0 = 0; c0 < c->n_cells; c0 += kMaxGridY) {
         dim3 grid((Np + 255) / 256, std::min(kMaxGridY, c->n_cells - c0));
         kderiv_kernel<T><<<grid, 256, 0, c->stream>>>(
-            c0, c->n_cells, N, Np, p.kernel_mode, p.frag_mode, p.v_frag, c->d_pair_ij, S->pair_q,
+            c0, c->n_cells, N, Np, p.kernel_mode, p.frag_mode, p.v_frag, p.vertical, p.v_dust != nullptr,
+            c->d_pair_ij, S->pair_q,
             c->n_blk * kBlkPairs, c->d_a, c->d_minv, c->d_prep, c->d_scal, p.alpha, c->d_K64,
             c->d_K32, kt);
     }

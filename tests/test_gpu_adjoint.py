@@ -29,6 +29,8 @@ import pytest
 
 from paper_2402_18471_b300 import synth
 
+from test_oracle_vertical import vi_adj_disc
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -69,7 +71,11 @@ def narrow_alpha():
     return d
 
 
-NARROW = {"adj_disc_N14": adj_disc, "narrow_alpha_N40": narrow_alpha}
+NARROW = {"adj_disc_N14": adj_disc, "narrow_alpha_N40": narrow_alpha,
+          # vertically integrated kernel (Sec. 5.1): alpha also moves the
+          # scale heights, the settling and the layer factor
+          "vertical_rings3_N14": lambda: vi_adj_disc(False),
+          "vertical_rings3_N14_vdust": lambda: vi_adj_disc(True)}
 WIDE = {"column8_N50": column8, "wide_alpha_N40": wide_alpha}
 CASES = {**NARROW, **WIDE}
 

@@ -126,12 +126,3 @@ def test_vertical_long_run_replayed_by_oracle(coag_mod, oracle_mod, precision, c
     assert np.all(dev <= bound), (dev / bound).max()
     assert np.mean(dev <= strict) >= 0.95
     assert np.allclose(rec["dt"].cpu().numpy().sum(1), d.t_span, rtol=1e-12)
-
-
-def test_vertical_adjoint_not_supported(coag_mod):
-    d = make("rings_37_N60")
-    g = coag_mod.Coag(d, "fp64")
-    y = g.state(d.rho0)
-    with pytest.raises(coag_mod.CoagError) as e:
-        g.vjp(y, torch.ones_like(y), t_span=d.t_span)
-    assert e.value.status == coag_mod.ENOTSUP
