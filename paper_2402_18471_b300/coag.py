@@ -485,6 +485,52 @@ class Coag:
         return g0, ga, gv
 
 
+def autotune_cluster(disc, t_probe=None, candidates=(1, 2, 4, 8), cache_path=None, device="cuda", **over):
+    """Measured choice of the mixed kernel's cluster size (CTAs that split each
+    pass of a slot group) for this problem's cell and bin counts.
+
+    Each candidate runs one warm-up and one timed integration over t_probe
+    (default: a tenth of disc.t_span) from disc.rho0; the best throughput in
+    accepted cell-substeps per second wins.  Candidates whose buffers do not
+    fit (the library falls back to a smaller size) are skipped.  With
+    cache_path, results are kept in a JSON file keyed by (bins, cells,
+    precision) and later calls read them instead of measuring.  Returns the
+    cluster size, to pass as mixed_cluster."""
+    import json
+    import torch
+    key = f"N{disc.n_bins}_cells{disc.n_cells}_mixed"
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+        if key in cache:
+            return int(cache[key]["best"])
+    t = disc.t_span / 10.0 if t_probe is None else float(t_probe)
+    rates = {}
+    for P in candidates:
+        g = Coag(disc, "mixed", device=device, mixed_cluster=P, **over)
+        try:
+            if g.mixed_cluster()[0] != P:
+                continue
+            for rep in range(2):
+                y = g.state(disc.rho0)
+                st = g.step(y, t)
+            rates[P] = st["accepted"] / max(st["elapsed_ms"], 1e-9) * 1e3
+        finally:
+            g.close()
+            torch.cuda.synchronize()
+    if not rates:
+        raise CoagError(ENOTSUP, "no cluster size fits this problem")
+    best = max(rates, key=rates.get)
+    if cache_path:
+        cache[key] = {"best": int(best), "rates": {str(k): v for k, v in rates.items()}, "t_probe": t}
+        d = os.path.dirname(os.path.abspath(cache_path))
+        os.makedirs(d, exist_ok=True)
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return int(best)
+
+
 class Batch:
     """Several discs integrated side by side through the batched interface:
     one context per disc (disc(i) gives a Coag view of it), SMs shared out in
