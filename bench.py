@@ -51,6 +51,7 @@ MEASURED_TRAFFIC = {
                         "source": "paper_2402_18471_b300/csrc/kbuild.cu",
                         "sha256": "657891c5620844420fe01dc0f9c0e9048f29952044a7d8fff2ee761be276734f"},
 }
+MEASURED_TRAFFIC_WORKLOAD = "grid_128x64_N100"   # the captures above are of this grid
 TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 rate ratio
 
 
@@ -62,12 +63,13 @@ def peaks():
     return dict(hbm_gbs=6400.0, bf16=1800.0, bf16_sus=1400.0, src="fallback")
 
 
-def measured_traffic(kernel: str, units: float):
+def measured_traffic(kernel: str, units: float, workload: str):
     """Traffic per launch scaled from the profiled per-unit bytes, or None
-    when no capture exists for the kernel's current source."""
+    when no capture exists for the kernel's current source on this workload
+    (the bytes per unit depend on the bin count and the L2 reuse)."""
     import hashlib
     m = MEASURED_TRAFFIC.get(kernel)
-    if not m:
+    if not m or workload != MEASURED_TRAFFIC_WORKLOAD:
         return None
     src = os.path.join(ROOT, m["source"])
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != m["sha256"]:
@@ -373,7 +375,7 @@ def main():
             peak_tf32 = pk["bf16_sus"] * TF32_OVER_BF16
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tf32, "unit": "TFLOP/s",
                     "frac": achieved / peak_tf32,
-                    "traffic": measured_traffic("step_mixed_kernel", evals),
+                    "traffic": measured_traffic("step_mixed_kernel", evals, args.workload),
                     "traffic_note": "DRAM bytes per RHS evaluation from an ncu capture of a "
                                     "300-yr launch of the same grid, scaled to this launch's "
                                     "evaluations", "kernel": "step_mixed_kernel",
@@ -384,8 +386,8 @@ def main():
         kb_s = main_res["kb_ms"] / n_steps / 1e3
         kb_bytes = disc.n_cells * Np * (8 if args.precision == "mixed" else 16)
         kb_gbs = kb_bytes / kb_s / 1e9
-        kb_traffic = (measured_traffic("kbuild32_kernel", 1.0)
-                      if args.precision == "mixed" and args.workload == "grid_128x64_N100" else None)
+        kb_traffic = (measured_traffic("kbuild32_kernel", 1.0, args.workload)
+                      if args.precision == "mixed" else None)
         roof_kb = {"bound": "hbm", "achieved": kb_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                    "frac": kb_gbs / pk["hbm_gbs"], "traffic": kb_traffic,
                    "kernel": "kbuild32_kernel" if args.precision == "mixed" else "kbuild64_kernel",
