@@ -230,6 +230,51 @@ def run_reference(args, disc, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """The batch of 32 uneven discs (batch_32_discs): every disc integrated
+    over t_span through the batched interface (one context and stream per
+    disc, SMs shared in proportion to n_cells x n_bins^2); aggregate accepted
+    cell-substeps per second of the whole batch step, timed with CUDA events
+    on the stream the batch joins on, and the worst per-disc mass error.
+    One GPU; an informational line, not the default benchmark."""
+    import torch
+    from paper_2402_18471_b300 import coag
+    discs = synth.batch_32_discs()
+    if args.t_span_yr:
+        for d in discs:
+            d.t_span = args.t_span_yr * synth.CONST["yr"]
+    b = coag.Batch(discs, args.precision)
+    init = [torch.as_tensor(np.ascontiguousarray(d.rho0), device="cuda") for d in discs]
+    ys = [x.clone() for x in init]
+    t_span = discs[0].t_span
+    ms, acc, mass = 0.0, 0, 0.0
+    for s in range(args.warmup + args.steps):
+        for y, x in zip(ys, init):
+            y.copy_(x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        stats = b.step(ys, t_span)
+        e1.record()
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            ms += e0.elapsed_time(e1)
+            acc += sum(st["accepted"] for st in stats)
+            mass = max([mass] + [st["mass_err_max"] for st in stats])
+    b.close()
+    cells = sum(d.n_cells for d in discs)
+    line = {"metric": "cell-substeps/s, batch of 32 uneven discs (batched interface)",
+            "value": acc / (ms / 1e3), "unit": "cell-substeps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "tf32x4+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": "batch_32_discs", "n_discs": len(discs), "n_cells": cells,
+                       "n_bins": [min(d.n_bins for d in discs), max(d.n_bins for d in discs)],
+                       "t_span_yr": t_span / synth.CONST["yr"], "precision": args.precision},
+            "accepted_per_step": acc // args.steps, "mass_err_max_per_disc": mass}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -237,7 +282,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="grid_128x64_N100", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="grid_128x64_N100", choices=list(WORKLOADS) + ["batch_32_discs"])
     ap.add_argument("--t-span-yr", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-leg", action="store_true")
@@ -249,6 +294,13 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
+    if args.workload == "batch_32_discs":
+        if args.impl == "reference" or world > 1:
+            print(json.dumps({"impl": args.impl, "workload": "batch_32_discs",
+                              "unavailable": "the batch line is a one-GPU measurement of this library"}))
+            return
+        run_batch(args)
+        return
     disc = WORKLOADS[args.workload]()
     if args.t_span_yr:
         disc.t_span = args.t_span_yr * synth.CONST["yr"]
