@@ -30,9 +30,12 @@
  *     error of the calling thread).
  *   - Work is issued on params.stream (NULL: the legacy default stream).
  *     cudisc_coag_rhs and cudisc_coag_step_async are asynchronous (and may be
- *     captured in a CUDA graph).  cudisc_coag_step, cudisc_coag_step_wait,
- *     cudisc_coag_build_kernel and cudisc_coag_vjp synchronise that stream
- *     before returning so they can report per-cell failures.
+ *     captured in a CUDA graph); so is cudisc_hse_rho_gas, on the stream it
+ *     is given.  cudisc_coag_step, cudisc_coag_step_wait,
+ *     cudisc_coag_step_spans, cudisc_coag_subcycle,
+ *     cudisc_coag_subcycle_pending, cudisc_coag_build_kernel and
+ *     cudisc_coag_vjp synchronise that stream before returning so they can
+ *     report per-cell failures.
  */
 #ifndef CUDISC_COAG_H
 #define CUDISC_COAG_H
