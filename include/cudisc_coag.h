@@ -225,6 +225,41 @@ cudisc_status cudisc_hse_rho_gas(int n_R, int n_Z, const double *R, const double
                                  const double *V, const double *R_edges, const double *Sigma_g, double mu,
                                  double m_H, double k_B, double GM, double *rho_gas, void *stream);
 
+/* The source update of the dust dynamics step (Sec. 3.1, the full step's
+ * items ii-iv with h = dt/2 and vi-viii with h = dt), for n_species dust
+ * fluids on n_cells cells.  Conserved Q and primitive P_n are device
+ * [4][n_species][n_cells] FP64: Q = (rho, rho v_R, rho v_phi R, rho v_Z)
+ * after the transport (in; out: after the sources and drag), P_n = (rho,
+ * v_R, v_phi, v_Z) at the start of the step.  Per cell (device [n_cells]):
+ * R, Z (cm), rho_g (g cm^-3), c_s (cm/s); v_g device [3][n_cells] the gas
+ * velocity (R, phi, Z); a device [n_species] grain radii (cm).  Steps:
+ * Q += h (0, rho v_phi^2 / R - rho Omega^2 R, 0, -rho Omega^2 Z) on P_n
+ * (Eq. sources without drag), Omega^2 = GM / (R^2 + Z^2)^(3/2); conversion
+ * to primitives; the implicit drag v <- v - h / (h + t_s) (v - v_g) with
+ * the Epstein t_s = rho_m a / (rho_g sqrt(8/pi) c_s) (Eqs. dragforce,
+ * t_stop); back to conserved quantities.  rho must be positive.
+ * Asynchronous on stream; allocates nothing; needs no context.  Errors:
+ * CUDISC_EINVAL (sizes, NULL arrays, h < 0, rho_m <= 0, GM < 0),
+ * CUDISC_ECUDA. */
+cudisc_status cudisc_dust_source_update(int n_species, int n_cells, double *Q, const double *P_n, double h,
+                                        const double *R, const double *Z, const double *rho_g,
+                                        const double *c_s, const double *v_g, const double *a, double rho_m,
+                                        double GM, void *stream);
+
+/* The CFL time step of the dust dynamics (Sec. 3.1, Eqs. dtCFL, dt_adv,
+ * dt_diff): the minimum over cells and species of C_adv |dR / v_R|,
+ * C_adv |dZ / v_Z| (zero velocities impose none) and C_diff d^2 Sc / nu for
+ * d = dR, dZ.  P device [4][n_species][n_cells] primitives (components 1
+ * and 3 are read), dR, dZ, nu device [n_cells] (cm, cm, cm^2/s), Sc device
+ * [n_species] Schmidt numbers; the paper's defaults are C_adv = 0.4 and
+ * C_diff = 0.2.  dt_out is device FP64 [3]: the result in dt_out[0], the
+ * largest |v| / d and the smallest Sc d^2 / nu in dt_out[1], dt_out[2]
+ * (the reduction's workspace).  Asynchronous on stream; allocates nothing;
+ * calls that overlap on one dt_out race.  Errors as above. */
+cudisc_status cudisc_dust_cfl_dt(int n_species, int n_cells, const double *P, const double *dR, const double *dZ,
+                                 const double *nu, const double *Sc, double C_adv, double C_diff, double *dt_out,
+                                 void *stream);
+
 /* Sub-cycled coagulation (Sec. 6): the coagulation solver takes its own
  * sub-steps inside the global time steps of the disc model, and a cell's
  * coagulation is brought up to date only once one (by default) of its last

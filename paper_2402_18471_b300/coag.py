@@ -87,6 +87,8 @@ def lib():
         L.cudisc_coag_step_async.argtypes = [v, v, d, v]
         L.cudisc_coag_step_wait.argtypes = [v, C.POINTER(cudisc_step_stats)]
         L.cudisc_hse_rho_gas.argtypes = [C.c_int, C.c_int, v, v, v, v, v, v, d, d, d, d, v, v]
+        L.cudisc_dust_source_update.argtypes = [C.c_int, C.c_int, v, v, d, v, v, v, v, v, v, d, d, v]
+        L.cudisc_dust_cfl_dt.argtypes = [C.c_int, C.c_int, v, v, v, v, v, d, d, v, v]
         L.cudisc_coag_step_spans.argtypes = [v, v, v, v, C.POINTER(cudisc_step_stats)]
         L.cudisc_coag_subcycle.argtypes = [v, v, d, d, v, C.POINTER(cudisc_step_stats)]
         L.cudisc_coag_subcycle_pending.argtypes = [v, v, C.c_int]
@@ -114,7 +116,7 @@ def lib():
                    "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp",
                    "cudisc_coag_mixed_cluster", "cudisc_coag_step_async", "cudisc_coag_step_wait",
                    "cudisc_coag_init_batched", "cudisc_coag_batch_ctx", "cudisc_coag_batch_build_kernel",
-                   "cudisc_hse_rho_gas", "cudisc_coag_batch_step", "cudisc_coag_step_spans", "cudisc_coag_subcycle",
+                   "cudisc_dust_source_update", "cudisc_dust_cfl_dt", "cudisc_hse_rho_gas", "cudisc_coag_batch_step", "cudisc_coag_step_spans", "cudisc_coag_subcycle",
                    "cudisc_coag_subcycle_pending"):
             getattr(L, fn).restype = C.c_int
         _lib = L
@@ -209,6 +211,35 @@ def hse_rho_gas(R, Z, T, V, R_edges, Sigma_g, mu, m_H, k_B, GM, out=None):
         out = torch.empty((n_R, n_Z), dtype=torch.float64, device=ts[0].device)
     cudisc_hse_rho_gas(n_R, n_Z, *(t.data_ptr() for t in ts), mu, m_H, k_B, GM, out.data_ptr(),
                        torch.cuda.current_stream(ts[0].device).cuda_stream)
+    return out
+
+
+def dust_source_update(Q, P_n, h, R, Z, rho_g, c_s, v_g, a, rho_m, GM):
+    """The dust source update of Sec. 3.1 (sources, then implicit drag) on
+    device FP64 tensors: Q (updated in place) and P_n [4, n_species, n_cells],
+    R, Z, rho_g, c_s [n_cells], v_g [3, n_cells], a [n_species]; on torch's
+    current stream."""
+    import torch
+    n_s, n_c = Q.shape[1], Q.shape[2]
+    ts = [t.contiguous() for t in (P_n, R, Z, rho_g, c_s, v_g, a)]
+    assert Q.is_contiguous() and Q.dtype == torch.float64
+    Pn_, R_, Z_, rg_, cs_, vg_, a_ = (t.data_ptr() for t in ts)
+    _check(lib().cudisc_dust_source_update(n_s, n_c, Q.data_ptr(), Pn_, float(h), R_, Z_, rg_, cs_, vg_, a_,
+                                           float(rho_m), float(GM),
+                                           torch.cuda.current_stream(Q.device).cuda_stream))
+    return Q
+
+
+def dust_cfl_dt(P, dR, dZ, nu, Sc, C_adv=0.4, C_diff=0.2, out=None):
+    """The CFL time step of Sec. 3.1: a three-element device tensor whose
+    element 0 is the step (1 and 2 hold the reduction's partial results)."""
+    import torch
+    n_s, n_c = P.shape[1], P.shape[2]
+    ts = [t.contiguous() for t in (P, dR, dZ, nu, Sc)]
+    if out is None:
+        out = torch.empty(3, dtype=torch.float64, device=P.device)
+    _check(lib().cudisc_dust_cfl_dt(n_s, n_c, *(t.data_ptr() for t in ts), float(C_adv), float(C_diff),
+                                    out.data_ptr(), torch.cuda.current_stream(P.device).cuda_stream))
     return out
 
 

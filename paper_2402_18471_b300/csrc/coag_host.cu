@@ -708,6 +708,40 @@ cudisc_status cudisc_hse_rho_gas(int n_R, int n_Z, const double *R, const double
     return CUDISC_OK;
 }
 
+cudisc_status cudisc_dust_source_update(int n_species, int n_cells, double *Q, const double *P_n, double h,
+                                        const double *R, const double *Z, const double *rho_g,
+                                        const double *c_s, const double *v_g, const double *a, double rho_m,
+                                        double GM, void *stream)
+{
+    g_thread_err.clear();
+    if (n_species < 1 || n_cells < 1) return fail(nullptr, CUDISC_EINVAL, "n_species and n_cells must be >= 1");
+    if (!Q || !P_n || !R || !Z || !rho_g || !c_s || !v_g || !a)
+        return fail(nullptr, CUDISC_EINVAL, "Q, P_n, R, Z, rho_g, c_s, v_g and a must be device arrays");
+    if (!(h >= 0.0) || !std::isfinite(h)) return fail(nullptr, CUDISC_EINVAL, "h must be >= 0 and finite");
+    if (!(rho_m > 0.0) || !(GM >= 0.0) || !std::isfinite(rho_m) || !std::isfinite(GM))
+        return fail(nullptr, CUDISC_EINVAL, "rho_m must be positive and GM >= 0");
+    cudaError_t e = cdc::launch_dust_source(n_species, n_cells, Q, P_n, h, R, Z, rho_g, c_s, v_g, a, rho_m, GM,
+                                            (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudisc_dust_source_update");
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_dust_cfl_dt(int n_species, int n_cells, const double *P, const double *dR, const double *dZ,
+                                 const double *nu, const double *Sc, double C_adv, double C_diff, double *dt_out,
+                                 void *stream)
+{
+    g_thread_err.clear();
+    if (n_species < 1 || n_cells < 1) return fail(nullptr, CUDISC_EINVAL, "n_species and n_cells must be >= 1");
+    if (!P || !dR || !dZ || !nu || !Sc || !dt_out)
+        return fail(nullptr, CUDISC_EINVAL, "P, dR, dZ, nu, Sc and dt_out must be device arrays");
+    if (!(C_adv > 0.0) || !(C_diff > 0.0) || !std::isfinite(C_adv) || !std::isfinite(C_diff))
+        return fail(nullptr, CUDISC_EINVAL, "C_adv and C_diff must be positive");
+    cudaError_t e = cdc::launch_dust_cfl(n_species, n_cells, P, dR, dZ, nu, Sc, C_adv, C_diff, dt_out,
+                                         (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudisc_dust_cfl_dt");
+    return CUDISC_OK;
+}
+
 cudisc_status cudisc_coag_step_async(cudisc_coag_ctx *c, double *rho, double t_span, double *dt_cell)
 {
     if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");

@@ -161,6 +161,13 @@ void mixed_layout(int n_cells, int N, int P_req, int max_sms, int *P, int *G, in
 cudaError_t launch_hse(int n_R, int n_Z, const double *R, const double *Z, const double *T, const double *V,
                        const double *R_edges, const double *Sigma_g, double mu, double m_H, double k_B,
                        double GM, double *rho, cudaStream_t stream);
+// dust source update and CFL step (dust.cu)
+cudaError_t launch_dust_source(int n_s, int n_c, double *Q, const double *Pn, double h, const double *R,
+                               const double *Z, const double *rho_g, const double *c_s, const double *v_g,
+                               const double *a, double rho_m, double GM, cudaStream_t stream);
+cudaError_t launch_dust_cfl(int n_s, int n_c, const double *P, const double *dR, const double *dZ,
+                            const double *nu, const double *Sc, double C_adv, double C_diff, double *dt,
+                            cudaStream_t stream);
 // adjoint (vjp.cu)
 bool vjp_fits(const cudisc_coag_ctx *c);
 cudaError_t vjp_prepare(cudisc_coag_ctx *c, long long max_steps);

@@ -119,3 +119,14 @@ def test_hse_rejects_bad_arguments_before_any_launch():
     assert b"device arrays" in L.cudisc_coag_last_error(None)
     assert L.cudisc_hse_rho_gas(3, 4, *args, 2.4, 1.67e-24, 1.38e-16, -1.0, fake, None) == coag.EINVAL
     assert b"positive" in L.cudisc_coag_last_error(None)
+
+
+def test_dust_calls_reject_bad_arguments_before_any_launch():
+    L = coag.lib()
+    f = C.c_void_p(16)     # never dereferenced: validation fails first
+    assert L.cudisc_dust_source_update(0, 4, f, f, 1.0, f, f, f, f, f, f, 1.6, 1.0, None) == coag.EINVAL
+    assert L.cudisc_dust_source_update(2, 4, None, f, 1.0, f, f, f, f, f, f, 1.6, 1.0, None) == coag.EINVAL
+    assert L.cudisc_dust_source_update(2, 4, f, f, -1.0, f, f, f, f, f, f, 1.6, 1.0, None) == coag.EINVAL
+    assert L.cudisc_dust_cfl_dt(2, 0, f, f, f, f, f, 0.4, 0.2, f, None) == coag.EINVAL
+    assert L.cudisc_dust_cfl_dt(2, 4, f, f, f, f, f, 0.0, 0.2, f, None) == coag.EINVAL
+    assert L.cudisc_dust_cfl_dt(2, 4, f, f, f, f, f, 0.4, 0.2, None, None) == coag.EINVAL
