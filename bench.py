@@ -3,14 +3,20 @@
 
 One step = rebuild the collision kernel from the gas arrays (a2, a3) and
 integrate every cell of the 128 R x 64 Z x 100-bin grid over 1e4 yr with
-BS3 3(2) and the paper's tolerances (a4-a7).  The metric is accepted
-cell-substeps per second over the timed steps.
+BS3 3(2) and the paper's tolerances (a4-a7).  The step is captured once in a
+CUDA graph (state copy-in, kernel-table build, persistent integration
+kernel) and replayed; the metric is accepted cell-substeps per second over
+the timed steps.
 
     python bench.py [--gpus N --steps K --warmup W] [--precision mixed|fp64]
     python bench.py --impl reference ...   # the FP64 CPU oracle arm
 
-Under torchrun each rank integrates its own copy of the workload (weak
-scaling, no collective on the data path); rank 0 prints one JSON line.
+Under torchrun the job is sharded by cudisc_partition with no collective on
+the data path: by default (--scaling weak) the job is one disc of the
+workload per rank, each with its own seeded perturbations, and each rank
+integrates the disc it is given; with --scaling strong one disc is split
+into contiguous cell ranges balanced by the per-cell cost measured in a
+calibration step.  Rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -35,6 +41,8 @@ WORKLOADS = {
     "grid_512x256_N150": synth.grid_512x256,
     "rings_4096_N100": synth.rings_4096,     # vertically integrated kernel (surface densities)
 }
+BASE_SEED = {"grid_128x64_N100": 1, "column_1x32_N50": None, "adjoint_64x32_N80": 2,
+             "grid_512x256_N150": 3, "rings_4096_N100": 8}
 METRIC = "cell-substeps/s, 128x64 cells x 100 bins: mixed vs FP64 GPU, rel err<=1e-5"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
@@ -42,8 +50,6 @@ FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
 # from one ncu capture of the named kernel (summaries under profiles/), valid
 # only for the kernel source they were taken on: a changed source reports null.
 MEASURED_TRAFFIC = {
-    # DRAM read + write of one ncu capture, per unit of work, valid while the
-    # kernel's source file is unchanged
     "step_mixed_kernel": {"bytes_per_unit": (24.283566e9 + 0.668781e9) / 635513, "unit": "RHS evaluation",
                           "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
                           "sha256": "502b67c70379f26b27d8cbc225646a608ba8c6ae6ce6e66c03c6b4282a4c1a6c"},
@@ -130,6 +136,42 @@ class ClockSampler:
                 "power_w_max": max(pw), "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ---- sharding of the job over ranks (Sec. 2/5: cells evolve independently) ----
+
+def make_disc(workload: str, index: int):
+    """Disc `index` of a workload: index 0 is the named workload itself; the
+    others differ only in the seed of their perturbations."""
+    fn = WORKLOADS[workload]
+    base = BASE_SEED[workload]
+    if base is None or index == 0:
+        return fn() if base is None else fn(seed=base)
+    return fn(seed=base + 1000 * index)
+
+
+def weak_shard(workload: str, rank: int, world: int):
+    """Weak scaling: the job is `world` discs of the workload; whole discs
+    are split over the ranks by cudisc_partition with cost n_cells x N^2
+    (equal discs: one each).  Returns this rank's discs."""
+    from paper_2402_18471_b300 import coag
+    d0 = make_disc(workload, 0)
+    cost = np.full(world, float(d0.n_cells) * d0.n_bins ** 2)
+    b = coag.cudisc_partition(cost, world)
+    return [make_disc(workload, i) for i in range(b[rank], b[rank + 1])]
+
+
+def cell_range(disc, lo: int, hi: int):
+    return disc.subset(np.arange(lo, hi))
+
+
+def strong_bounds(disc, world: int, cost=None):
+    """Strong scaling: contiguous cell ranges of one disc, balanced by cost
+    (None: equal per cell)."""
+    from paper_2402_18471_b300 import coag
+    return coag.cudisc_partition(cost, world, n_items=disc.n_cells)
+
+
+# ---- the oracle leg: CPU baseline and the accuracy of the benched run ----
+
 def cpu_baseline(disc, budget_s=20.0, t_span=None):
     """The FP64 oracle on a bounded sample of cells of the same workload."""
     from oracle import oracle as O
@@ -159,6 +201,33 @@ def cpu_baseline(disc, budget_s=20.0, t_span=None):
             "sample": f"{len(used)} of {disc.n_cells} cells spread over the grid, full "
                       f"{t_span / synth.CONST['yr']:.0f} yr, {total_sub} accepted substeps in "
                       f"{total_t:.1f} s, OpenMP over cells"}
+
+
+def accuracy_check(disc, y, hs, n_h, cells, rhs_gpu=None, rhs_state=None):
+    """The GPU's integrated states against the FP64 oracle replaying the
+    GPU's own accepted steps on sampled cells (all bins), and optionally a
+    right-hand side against the oracle's relative to each cell's gross
+    collision flux.  Untimed; part of the oracle leg."""
+    from oracle import oracle as O
+    O.build()
+    sub = disc.subset(cells)
+    o = O.Oracle(sub)
+    y0 = o.replay(disc.rho0[cells], hs, n_h)
+    dev = np.abs(y - y0)
+    S = disc.rho0[cells].sum(1)
+    strict = 1e-5 * np.abs(y0) + 1e-10 * S[:, None]
+    r = dev / strict
+    out = {"cells": int(len(cells)), "bins": int(r.size),
+           "frac_bins_within_1e-5": float(np.mean(r <= 1.0)),
+           "worst_over_bound": float(r.max()),
+           "l1_mass_frac_max": float((dev.sum(1) / S).max()),
+           "bound": "|rho_gpu - rho_oracle| <= 1e-5 |rho| + 1e-10 sum(rho), oracle replaying the GPU's steps"}
+    if rhs_gpu is not None:
+        K, _, _ = o.kernel()
+        n = rhs_state / sub.m
+        gross = (sub.m * n * np.einsum("cik,ci->ck", K, n)).sum(1)
+        out["rhs_err_over_gross_max"] = float((np.abs(rhs_gpu - o.rhs(rhs_state)) / gross[:, None]).max())
+    return out
 
 
 def combine_ranks(dist, device, ms, e2e_s, sub, e2e_sub):
@@ -236,6 +305,8 @@ def run_batch(args):
     disc, SMs shared in proportion to n_cells x n_bins^2); aggregate accepted
     cell-substeps per second of the whole batch step, timed with CUDA events
     on the stream the batch joins on, and the worst per-disc mass error.
+    Then the adjoint of every 4th disc's step (discs 0, 4, 8, ...) through
+    the same contexts, with the loss of small grains above Z = H.
     One GPU; an informational line, not the default benchmark."""
     import torch
     from paper_2402_18471_b300 import coag
@@ -261,6 +332,18 @@ def run_batch(args):
             ms += e0.elapsed_time(e1)
             acc += sum(st["accepted"] for st in stats)
             mass = max([mass] + [st["mass_err_max"] for st in stats])
+    # adjoint on every 4th disc (its own fresh adaptive forward integration)
+    adj = []
+    for i in range(0, len(discs), 4):
+        d = discs[i]
+        w = torch.as_tensor(synth.adjoint_loss_weights(d), device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g0, ga, gv = b.disc(i).vjp(init[i], w, t_span=t_span)
+        torch.cuda.synchronize()
+        adj.append({"disc": i, "n_cells": d.n_cells, "n_bins": d.n_bins, "s": time.perf_counter() - t0,
+                    "vjp_ms": b.disc(i).timings()["vjp_ms"],
+                    "finite": bool(torch.isfinite(g0).all().item() and torch.isfinite(ga).all().item())})
     b.close()
     cells = sum(d.n_cells for d in discs)
     line = {"metric": "cell-substeps/s, batch of 32 uneven discs (batched interface)",
@@ -271,8 +354,219 @@ def run_batch(args):
             "config": {"workload": "batch_32_discs", "n_discs": len(discs), "n_cells": cells,
                        "n_bins": [min(d.n_bins for d in discs), max(d.n_bins for d in discs)],
                        "t_span_yr": t_span / synth.CONST["yr"], "precision": args.precision},
-            "accepted_per_step": acc // args.steps, "mass_err_max_per_disc": mass}
+            "accepted_per_step": acc // args.steps, "mass_err_max_per_disc": mass,
+            "adjoint_every_4th_disc": {"discs": len(adj), "seconds_total": sum(a["s"] for a in adj),
+                                       "all_finite": all(a["finite"] for a in adj), "per_disc": adj}}
     print(json.dumps(line), flush=True)
+
+
+class Leg:
+    """One precision's measurement of the step on the discs of this rank:
+    the step captured once in a CUDA graph per disc (state copy-in, kernel
+    build, integration) and replayed `steps` times after `warmup` replays."""
+
+    def __init__(self, discs, precision, use_graph=True):
+        import torch
+        from paper_2402_18471_b300 import coag
+        self.torch = torch
+        self.discs = discs
+        self.precision = precision
+        self.stream = torch.cuda.Stream()
+        self.gs, self.rho0, self.rho, self.dt, self.graphs = [], [], [], [], []
+        for d in discs:
+            g = coag.Coag(d, precision, stream=self.stream)
+            self.gs.append(g)
+            self.rho0.append(g.state(d.rho0))
+            self.rho.append(torch.empty_like(self.rho0[-1]))
+            self.dt.append(torch.zeros(d.n_cells, dtype=torch.float64, device="cuda"))
+        # the states were made on torch's current stream; the contexts run on
+        # their own (a non-blocking stream)
+        torch.cuda.synchronize()
+        self.use_graph = use_graph
+        if use_graph:
+            # one eager step first (loads the kernels, sets their attributes)
+            self.step_eager()
+            for i, g in enumerate(self.gs):
+                gr = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(gr, stream=self.stream):
+                    self.rho[i].copy_(self.rho0[i])
+                    self.dt[i].zero_()
+                    g.build_kernel_async()
+                    g.step_async(self.rho[i], self.discs[i].t_span, self.dt[i])
+                self.graphs.append(gr)
+
+    def step_eager(self):
+        sts = []
+        with self.torch.cuda.stream(self.stream):
+            for i, g in enumerate(self.gs):
+                self.rho[i].copy_(self.rho0[i])
+                self.dt[i].zero_()
+                g.build_kernel()
+                sts.append(g.step(self.rho[i], self.discs[i].t_span, self.dt[i]))
+        return sts
+
+    def step(self):
+        if not self.use_graph:
+            return self.step_eager()
+        sts = []
+        with self.torch.cuda.stream(self.stream):
+            for i, g in enumerate(self.gs):
+                self.graphs[i].replay()
+                sts.append(g.step_wait())
+        return sts
+
+    def close(self):
+        for g in self.gs:
+            g.close()
+
+
+def measure(leg, steps, warmup, dist):
+    """Timed replays: CUDA events on the legs' stream, a barrier and a
+    synchronisation on both sides."""
+    torch = leg.torch
+    for _ in range(warmup):
+        leg.step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sub = rej = 0
+    kern_ms = 0.0
+    launches = 0
+    last = None
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(leg.stream)
+        for _ in range(steps):
+            for st, d in zip(leg.step(), leg.discs):
+                sub += st["accepted"]
+                rej += st["rejected"]
+                kern_ms += st["elapsed_ms"]
+                last = st
+                # prep, table build and integration kernels (launches over
+                # cells are chunked to 65535 rows)
+                launches += 3 + 2 * ((d.n_cells - 1) // 65535)
+        e1.record(leg.stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return dict(ms=e0.elapsed_time(e1), sub=sub, rej=rej, kern_ms=kern_ms, launches=launches,
+                clocks=clk.summary(), last=last)
+
+
+def kernel_timings(leg, reps=3):
+    """Device times of the integration kernel and the table build alone
+    (the synchronous calls record CUDA events around their launches)."""
+    torch = leg.torch
+    kern, kb, prep, sub, rej = 0.0, 0.0, 0.0, 0, 0
+    for _ in range(reps):
+        sts = leg.step_eager()
+        for g, st in zip(leg.gs, sts):
+            t = g.timings()
+            kern += st["elapsed_ms"]
+            kb += t["kbuild_ms"]
+            prep += t["prep_ms"]
+            sub += st["accepted"]
+            rej += st["rejected"]
+    torch.cuda.synchronize()
+    return dict(kern_ms=kern / reps, kb_ms=kb / reps, prep_ms=prep / reps, sub=sub / reps, rej=rej / reps)
+
+
+def e2e_measure(leg, steps):
+    """End to end through the public API: every step copies the state in
+    from pinned host memory, rebuilds the kernel tables, integrates and
+    copies the result back to pinned host memory."""
+    torch = leg.torch
+    host_in = [torch.from_numpy(np.ascontiguousarray(d.rho0)).pin_memory() for d in leg.discs]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    esub = 0
+    with torch.cuda.stream(leg.stream):
+        for _ in range(steps):
+            for i, g in enumerate(leg.gs):
+                leg.rho[i].copy_(host_in[i], non_blocking=True)
+                leg.dt[i].zero_()
+                g.build_kernel()
+                st = g.step(leg.rho[i], leg.discs[i].t_span, leg.dt[i])
+                esub += st["accepted"]
+                host_out[i].copy_(leg.rho[i], non_blocking=True)
+            leg.stream.synchronize()
+    return dict(e2e_s=time.perf_counter() - t0, e2e_sub=esub, bytes=sum(h.numel() * 8 for h in host_in))
+
+
+def records_run(g, d, cap):
+    """One untimed integration with per-cell step records; returns the final
+    state, the accepted steps and their counts (host arrays)."""
+    import torch
+    rec = g.set_records(cap)
+    y = g.state(d.rho0)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(g.stream):
+        g.build_kernel()
+        st = g.step(y, d.t_span)
+    out = (y.cpu().numpy(), rec["dt"].cpu().numpy(), rec["n"].cpu().numpy(), st)
+    g.set_records(0)
+    return out
+
+
+def large_grid_key(args, pk):
+    """The 512 R x 256 Z x 150-bin grid over 1e4 yr (alpha 1e-4, v_frag
+    10 m/s): one warm-up and one timed graph replay of the mixed step."""
+    d = synth.grid_512x256()
+    # synchronous calls: a graph would save microseconds of a ~3 s step
+    leg = Leg([d], "mixed", use_graph=False)
+    r = measure(leg, 1, 1, None)
+    P, G = leg.gs[0].mixed_cluster()
+    leg.close()
+    N = d.n_bins
+    Np = N * (N + 1) // 2
+    evals = 3 * (r["sub"] + r["rej"]) + d.n_cells
+    gbs = evals * 8 * Np / (r["kern_ms"] * 1e-3) / 1e9
+    return {"workload": "grid_512x256_N150", "n_cells": d.n_cells, "n_bins": N,
+            "value": r["sub"] / (r["ms"] / 1e3), "unit": "cell-substeps/s", "ms_per_step": r["ms"],
+            "steps": 1, "warmup": 1, "mass_err_max": r["last"]["mass_err_max"],
+            "mixed_cluster": P, "slot_groups": G,
+            "k_stream_gbs": gbs, "k_stream_hbm_frac": gbs / pk["hbm_gbs"]}
+
+
+def adjoint_key(pk):
+    """The adjoint workload (64 R x 32 Z x 80 bins, 2000 yr): the mixed
+    forward integration with records, then the FP64 adjoint of the same
+    steps (dL/d rho0, dL/d alpha, dL/d v_frag of the small-grain mass above
+    Z = H), timed by the library's CUDA events."""
+    import torch
+    from paper_2402_18471_b300 import coag
+    d = synth.adjoint_64x32()
+    g = coag.Coag(d, "mixed")
+    w = torch.as_tensor(synth.adjoint_loss_weights(d), device="cuda")
+    rho0 = g.state(d.rho0)
+    torch.cuda.synchronize()
+    cap = 4096
+    y, hs, nh, st = records_run(g, d, cap)
+    hs_t = torch.as_tensor(hs, device="cuda")
+    nh_t = torch.as_tensor(nh, device="cuda")
+    g.vjp(rho0, w, hs_t, nh_t)            # warm-up (builds the adjoint tables)
+    ts = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        g.vjp(rho0, w, hs_t, nh_t)
+        ts.append(g.timings()["vjp_ms"])
+    g.close()
+    N = d.n_bins
+    Np = N * (N + 1) // 2
+    substeps = int(nh.sum())
+    ms = float(np.median(ts))
+    # per substep 9 right-hand-side-like FP64 passes (3 forward recomputes,
+    # 3 transposed right-hand sides, 3 derivative gathers), each about the
+    # forward's 2 x 13 flops per pair plus the fragment spread
+    flops = 9 * (2 * 13 * Np + N * (N + 1)) * substeps
+    return {"workload": "adjoint_64x32_N80", "n_cells": d.n_cells, "n_bins": N, "t_span_yr": 2000.0,
+            "substeps": substeps, "forward_ms": st["elapsed_ms"], "adjoint_ms": ms,
+            "adjoint_substeps_per_s": substeps / (ms / 1e3),
+            "fp64_tflops_est": flops / (ms / 1e3) / 1e12,
+            "fp64_frac_est": flops / (ms / 1e3) / 1e12 / FP64_NOMINAL_TFLOPS,
+            "note": "FP64 pipe fraction against the nominal 1.25 TFLOP/s, flops estimated as 9 passes of "
+                    "the forward's per-pair work per substep"}
 
 
 def main():
@@ -283,9 +577,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="grid_128x64_N100", choices=list(WORKLOADS) + ["batch_32_discs"])
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"])
     ap.add_argument("--t-span-yr", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-leg", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the large-grid, adjoint and HSE keys")
+    ap.add_argument("--no-graph", action="store_true", help="time the synchronous calls instead of graph replays")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=10.0)
     args = ap.parse_args()
@@ -301,11 +598,14 @@ def main():
             return
         run_batch(args)
         return
-    disc = WORKLOADS[args.workload]()
-    if args.t_span_yr:
-        disc.t_span = args.t_span_yr * synth.CONST["yr"]
+
+    def span(d):
+        if args.t_span_yr:
+            d.t_span = args.t_span_yr * synth.CONST["yr"]
+        return d
 
     if args.impl == "reference":
+        disc = span(make_disc(args.workload, 0))
         if world > 1:
             import torch.distributed as dist
             dist.init_process_group("gloo")
@@ -325,88 +625,62 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    stream = torch.cuda.current_stream()
+    # ---- this rank's shard ----
+    shard_note = None
+    if args.scaling == "weak" or world == 1:
+        discs = [span(d) for d in weak_shard(args.workload, rank, world)]
+        shard_note = f"{world} disc(s) of the workload, whole discs per rank by cudisc_partition"
+    else:
+        full = span(make_disc(args.workload, 0))
+        b = strong_bounds(full, world)
+        # calibration: integrate the equal-count shard once with records, then
+        # split again by the measured accepted substeps per cell (host all-gather,
+        # outside the timed region)
+        cal = coag.Coag(cell_range(full, b[rank], b[rank + 1]), args.precision)
+        _, _, n_cal, _ = records_run(cal, cell_range(full, b[rank], b[rank + 1]), 64)
+        cal.close()
+        parts = [None] * world
+        dist.all_gather_object(parts, (int(b[rank]), n_cal.astype(np.float64) + 1.0))
+        cost = np.zeros(full.n_cells)
+        for lo, c in parts:
+            cost[lo:lo + len(c)] = c
+        b = strong_bounds(full, world, cost)
+        discs = [cell_range(full, b[rank], b[rank + 1])] if b[rank + 1] > b[rank] else []
+        shard_note = (f"cells {b[rank]}..{b[rank + 1] - 1} of one disc; contiguous ranges balanced by the "
+                      f"accepted substeps per cell of a calibration step")
+    disc = discs[0] if discs else None
 
-    def measure(precision, steps, warmup, with_e2e):
-        g = coag.Coag(disc, precision, stream=stream)
-        rho0 = g.state(disc.rho0)
-        rho = torch.empty_like(rho0)
-        dt = torch.zeros(disc.n_cells, dtype=torch.float64, device="cuda")
-
-        def one_step():
-            rho.copy_(rho0)
-            dt.zero_()
-            g.build_kernel()
-            st = g.step(rho, disc.t_span, dt)
-            st["kbuild_ms"] = g.timings()["kbuild_ms"]
-            return st
-
-        for _ in range(warmup):
-            one_step()
-        torch.cuda.synchronize()
+    leg = Leg(discs, args.precision, use_graph=not args.no_graph) if discs else None
+    if leg is not None:
+        res = measure(leg, args.steps, args.warmup, dist)
+        kt = kernel_timings(leg)
+        e2e = e2e_measure(leg, args.steps)
+    else:
+        # an empty shard still takes part in the barriers and reductions
         if dist:
-            dist.barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        sub = 0
-        rej = 0
-        kern_ms = 0.0
-        kb_ms = 0.0
-        launches = 0
-        with ClockSampler(torch.cuda.current_device()) as clk:
-            e0.record(stream)
-            for _ in range(steps):
-                st = one_step()
-                sub += st["accepted"]
-                rej += st["rejected"]
-                kern_ms += st["elapsed_ms"]
-                kb_ms += st["kbuild_ms"]
-                launches += 3 + 2 * ((disc.n_cells - 1) // 65535)
-            e1.record(stream)
-            torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        ms = e0.elapsed_time(e1)
-        res = dict(ms=ms, sub=sub, rej=rej, kern_ms=kern_ms, kb_ms=kb_ms, launches=launches,
-                   clocks=clk.summary(), last=st, g=g)
-        if with_e2e:
-            host_in = torch.from_numpy(np.ascontiguousarray(disc.rho0)).pin_memory()
-            host_out = torch.empty_like(host_in).pin_memory()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            esub = 0
-            for _ in range(steps):
-                rho.copy_(host_in, non_blocking=True)
-                dt.zero_()
-                g.build_kernel()
-                st = g.step(rho, disc.t_span, dt)
-                esub += st["accepted"]
-                host_out.copy_(rho, non_blocking=True)
-                torch.cuda.synchronize()
-            res["e2e_s"] = time.perf_counter() - t0
-            res["e2e_sub"] = esub
-            res["bytes"] = host_in.numel() * 8
-            res["check"] = host_out.numpy().copy()
-        return res
+            dist.barrier(); dist.barrier()
+        res = dict(ms=0.0, sub=0, rej=0, kern_ms=0.0, launches=0, clocks={}, last=None)
+        kt = dict(kern_ms=0.0, kb_ms=0.0, prep_ms=0.0, sub=0, rej=0)
+        e2e = dict(e2e_s=0.0, e2e_sub=0, bytes=0)
 
-    main_res = measure(args.precision, args.steps, args.warmup, True)
-    fp64_res = None
-    if args.precision == "mixed" and not args.no_fp64_leg:
-        fp64_res = measure("fp64", 1, 1, False)
+    fp64 = None
+    if args.precision == "mixed" and not args.no_fp64_leg and rank == 0 and leg is not None:
+        leg64 = Leg(discs, "fp64", use_graph=not args.no_graph)
+        fp64 = measure(leg64, args.steps, args.warmup, None)
+        leg64_g = leg64.gs[0]
 
     # max over ranks of the timed region; units summed over ranks
-    ms, e2e_s, sub, e2e_sub = combine_ranks(dist, "cuda", main_res["ms"], main_res.get("e2e_s", 0.0),
-                                            main_res["sub"], main_res.get("e2e_sub", 0))
+    ms, e2e_s, sub, e2e_sub = combine_ranks(dist, "cuda", res["ms"], e2e["e2e_s"], res["sub"], e2e["e2e_sub"])
 
     if rank == 0:
         pk = peaks()
         value = sub / (ms / 1e3)
         N = disc.n_bins
         Np = N * (N + 1) // 2
-        n_steps = args.steps
-        kern_s = main_res["kern_ms"] / n_steps / 1e3          # integration kernel, per launch
+        kern_s = kt["kern_ms"] / 1e3                          # integration kernel(s), per step
         # right-hand-side evaluations per launch: 3 per attempted substep
         # (FSAL) plus the initial f(y0) of every cell
-        evals = (3 * (main_res["sub"] + main_res["rej"]) / n_steps + disc.n_cells)
+        evals = 3 * (kt["sub"] + kt["rej"]) + sum(d.n_cells for d in discs)
         if args.precision == "fp64":
             # algorithmic FP64 flops per RHS of one cell: per pair the product
             # n_i n_j K (3), the two loss terms (4) and the coagulation /
@@ -418,28 +692,31 @@ def main():
                     "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
                     "traffic": None, "kernel": "step64_kernel",
                     "peak_src": "nominal FP64 rate of B300 (no measured FP64 peak)"}
+            roof_t = None
         else:
-            # tensor flops of the TF32 split contraction per RHS of one cell:
-            # A[1 x 2Np] x B[2Np x N] for each of the 4 products hi.hi, hi.lo,
-            # lo.hi, lo.lo (unpadded pairs)
-            flops = 4 * 2 * (2 * Np) * N
-            achieved = evals * flops / kern_s / 1e12
-            # burst figure: the kernel is timed alone in a short region and,
-            # at ~350 W, runs at the full SM clock (the sustained bf16 figure
-            # was taken under the power cap, at ~1.2 GHz)
-            peak_tf32 = pk["bf16"] * TF32_OVER_BF16
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peak_tf32, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tf32,
+            # Sec. 8(d) roofline of the right-hand side: the K stream, 8 B per
+            # pair ({K p_coag, K p_frag} in FP32) of the cell per evaluation
+            kbytes = 8 * Np
+            achieved = evals * kbytes / kern_s / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / pk["hbm_gbs"],
                     "traffic": measured_traffic("step_mixed_kernel", evals, args.workload),
-                    "traffic_note": "DRAM bytes per RHS evaluation from an ncu capture of a "
-                                    "300-yr launch of the same grid, scaled to this launch's "
-                                    "evaluations", "kernel": "step_mixed_kernel",
-                    "peak_src": f"{pk['src']} burst bf16 {pk['bf16']} TFLOP/s x nominal "
-                                f"tf32/bf16 ratio 1.1/2.25",
-                    "rhs_evals_per_launch": evals, "flops_per_rhs": flops}
+                    "traffic_note": "DRAM bytes per RHS evaluation from an ncu capture of a short launch "
+                                    "of the same grid, scaled to this launch's evaluations",
+                    "kernel": "step_mixed_kernel", "peak_src": f"{pk['src']} copy bandwidth (of measured)",
+                    "rhs_evals_per_launch": evals, "bytes_per_rhs": kbytes}
+            # the dense-equivalent tensor work of the TF32 split contraction:
+            # A[1 x 2Np] x B[2Np x N] for each of 4 products, unpadded pairs
+            flops = 4 * 2 * (2 * Np) * N
+            at = evals * flops / kern_s / 1e12
+            peak_tf32 = pk["bf16"] * TF32_OVER_BF16
+            roof_t = {"bound": "tensor", "achieved": at, "peak": peak_tf32, "unit": "TFLOP/s",
+                      "frac": at / peak_tf32, "kernel": "step_mixed_kernel", "flops_per_rhs": flops,
+                      "peak_src": f"derived, not measured: {pk['src']} burst bf16 {pk['bf16']} TFLOP/s x "
+                                  f"nominal tf32/bf16 ratio 1.1/2.25"}
         # kernel-table build: HBM-bound writes of {K, K p_frag} per pair per cell
-        kb_s = main_res["kb_ms"] / n_steps / 1e3
-        kb_bytes = disc.n_cells * Np * (8 if args.precision == "mixed" else 16)
+        kb_s = kt["kb_ms"] / 1e3
+        kb_bytes = sum(d.n_cells for d in discs) * Np * (8 if args.precision == "mixed" else 16)
         kb_gbs = kb_bytes / kb_s / 1e9
         kb_traffic = (measured_traffic("kbuild32_kernel", 1.0, args.workload)
                       if args.precision == "mixed" else None)
@@ -448,41 +725,83 @@ def main():
                    "kernel": "kbuild32_kernel" if args.precision == "mixed" else "kbuild64_kernel",
                    "ms_per_launch": kb_s * 1e3, "bytes_per_launch": kb_bytes,
                    "peak_src": f"{pk['src']} copy bandwidth"}
+        P, G = leg.gs[0].mixed_cluster()
         line = {
             "metric": METRIC, "value": value, "unit": "cell-substeps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "weak" if args.scaling == "weak" or world == 1 else "strong",
+            "vs_baseline": None,
             "dtype": "tf32x4+f32" if args.precision == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "n_cells": disc.n_cells, "n_bins": N,
                        "t_span_yr": disc.t_span / synth.CONST["yr"],
                        "precision": args.precision, "rtol": disc.rtol, "atol_rel": disc.atol_rel,
+                       "shard": shard_note,
+                       "graph": not args.no_graph,
                        "l2": "K tables (FP32 %.0f MB / FP64 %.0f MB; L2 126 MB) are rebuilt every step"
-                             % (disc.n_cells * N * (N + 1) / 2 * 8 / 1e6, disc.n_cells * N * (N + 1) / 2 * 16 / 1e6),
+                             % (disc.n_cells * Np * 8 / 1e6, disc.n_cells * Np * 16 / 1e6),
                        **({"vertical": 1} if disc.vertical else {}),
-                       "step": "kernel build + BS3 integration of all cells over t_span",
+                       "step": "state copy-in + kernel build + BS3 integration of all cells over t_span, "
+                               "one CUDA graph replay",
+                       "accuracy_scope": "1e-5 holds per right-hand side (rhs_err_over_gross_max) and over "
+                                         "spans short of the coagulation-fragmentation balance; over the full "
+                                         "1e4 yr it holds on the fraction of bins in accuracy.frac_bins_within_1e-5 "
+                                         "(the FP64 GPU path also misses it once rtol <= 1e-3)",
                        **({"state": "FP32 pair y/Sx = yh + yl (48 bits), FP64 time and step size",
-                           "mixed_cluster": main_res["g"].mixed_cluster()[0],
-                           "slot_groups": main_res["g"].mixed_cluster()[1]}
+                           "mixed_cluster": P, "slot_groups": G}
                           if args.precision == "mixed" else {})},
-            "ms_kernel_per_step": main_res["kern_ms"] / args.steps,
-            "accepted_per_step": main_res["last"]["accepted"],
-            "rejected_per_step": main_res["last"]["rejected"],
-            "mass_err_max": main_res["last"]["mass_err_max"],
+            "ms_kernel_per_step": kt["kern_ms"],
+            "accepted_per_step": res["last"]["accepted"] if len(discs) == 1 else res["sub"] // args.steps,
+            "rejected_per_step": res["last"]["rejected"] if len(discs) == 1 else res["rej"] // args.steps,
+            "mass_err_max": res["last"]["mass_err_max"],
             "roofline": roof,
+            **({"roofline_tensor": roof_t} if roof_t else {}),
             "roofline_kbuild": roof_kb,
-            "clocks": main_res["clocks"],
-            "gpu_launches": main_res["launches"],
+            "clocks": res["clocks"],
+            "gpu_launches": res["launches"],
             "e2e": {"value": e2e_sub / e2e_s, "unit": "cell-substeps/s",
-                    "h2d_bytes_per_step": main_res["bytes"], "d2h_bytes_per_step": main_res["bytes"]},
+                    "h2d_bytes_per_step": e2e["bytes"], "d2h_bytes_per_step": e2e["bytes"]},
         }
-        if fp64_res is not None:
-            v64 = fp64_res["sub"] / (fp64_res["ms"] / 1e3)
-            line["fp64_gpu"] = {"value": v64, "unit": "cell-substeps/s", "speedup_mixed_over_fp64": value / v64}
-        line["roofline_hse"] = hse_roofline(coag, "cuda", pk)
+        if fp64 is not None:
+            v64 = fp64["sub"] / (fp64["ms"] / 1e3)
+            line["fp64_gpu"] = {"value": v64, "unit": "cell-substeps/s", "steps": args.steps,
+                                "warmup": args.warmup, "ms_per_step": fp64["ms"] / args.steps,
+                                "speedup_mixed_over_fp64": value / v64,
+                                "note": "same steps, warm-up and graph replay as the mixed leg; same rtol, "
+                                        "not the same elementwise accuracy over 1e4 yr (see accuracy)"}
+        if world == 1 and not args.no_extras:
+            line["roofline_hse"] = hse_roofline(coag, "cuda", pk)
+            if args.workload == "grid_128x64_N100" and args.precision == "mixed":
+                line["large_grid"] = large_grid_key(args, pk)
+                line["adjoint"] = adjoint_key(pk)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(disc, budget_s=args.cpu_budget)
+            # the accuracy of the benched integration: an untimed run of the
+            # same step with records, the oracle replaying it on 12 cells
+            cells = np.linspace(0, disc.n_cells - 1, 12).astype(int)
+            acc = {}
+            cap = int(res["last"]["max_accepted"]) + 64
+            y, hs, nh, st = records_run(leg.gs[0], disc, cap)
+            rs = synth.random_state(disc, seed=17)
+            xs = leg.gs[0].state(rs)
+            torch.cuda.synchronize()
+            f = leg.gs[0].rhs(xs)
+            leg.stream.synchronize()
+            f = f.cpu().numpy()
+            acc[args.precision] = accuracy_check(disc, y[cells], hs[cells], nh[cells], cells,
+                                                 f[cells], rs[cells])
+            acc[args.precision]["mass_err_max"] = st["mass_err_max"]
+            if fp64 is not None:
+                y, hs, nh, st = records_run(leg64_g, disc, cap)
+                acc["fp64"] = accuracy_check(disc, y[cells], hs[cells], nh[cells], cells)
+                acc["fp64"]["mass_err_max"] = st["mass_err_max"]
+            acc["span_yr"] = disc.t_span / synth.CONST["yr"]
+            line["accuracy"] = acc
         print(json.dumps(line), flush=True)
+    if fp64 is not None:
+        leg64.close()
+    if leg is not None:
+        leg.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -29,8 +29,9 @@
  *     error cudisc_coag_last_error(ctx) returns a message (NULL ctx: the last
  *     error of the calling thread).
  *   - Work is issued on params.stream (NULL: the legacy default stream).
- *     cudisc_coag_rhs and cudisc_coag_step_async are asynchronous (and may be
- *     captured in a CUDA graph); so is cudisc_hse_rho_gas, on the stream it
+ *     cudisc_coag_rhs, cudisc_coag_build_kernel_async and
+ *     cudisc_coag_step_async are asynchronous (and may be captured in a CUDA
+ *     graph); so is cudisc_hse_rho_gas, on the stream it
  *     is given.  cudisc_coag_step, cudisc_coag_step_wait,
  *     cudisc_coag_step_spans, cudisc_coag_subcycle,
  *     cudisc_coag_subcycle_pending, cudisc_coag_build_kernel and
@@ -39,6 +40,8 @@
  */
 #ifndef CUDISC_COAG_H
 #define CUDISC_COAG_H
+
+#include <stddef.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -164,6 +167,12 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
  * arrays named at init (call after the caller changes them). */
 cudisc_status cudisc_coag_build_kernel(cudisc_coag_ctx *ctx);
 
+/* The same rebuild, only issued on the stream: no synchronisation and no
+ * timing (cudisc_coag_get_timings keeps the last synchronous build's), so
+ * that it may be captured in a CUDA graph together with
+ * cudisc_coag_step_async. */
+cudisc_status cudisc_coag_build_kernel_async(cudisc_coag_ctx *ctx);
+
 /* Set the fragmentation velocity v_frag (cm/s, > 0 and finite, else
  * CUDISC_EINVAL).  Takes effect at the next cudisc_coag_build_kernel. */
 cudisc_status cudisc_coag_set_v_frag(cudisc_coag_ctx *ctx, double v_frag);
@@ -254,8 +263,12 @@ cudisc_status cudisc_dust_source_update(int n_species, int n_cells, double *Q, c
  * [n_species] Schmidt numbers; the paper's defaults are C_adv = 0.4 and
  * C_diff = 0.2.  dt_out is device FP64 [3]: the result in dt_out[0], the
  * largest |v| / d and the smallest Sc d^2 / nu in dt_out[1], dt_out[2]
- * (the reduction's workspace).  Asynchronous on stream; allocates nothing;
- * calls that overlap on one dt_out race.  Errors as above. */
+ * (the reduction's workspace).  Inputs must be finite, with Sc, dR and dZ
+ * positive and nu >= 0: a non-finite velocity, or an Sc, dR, dZ or nu
+ * outside that range, makes dt_out[0] and dt_out[1] NaN (checked on the
+ * device, so it shows when the caller reads the result).  Asynchronous on
+ * stream; allocates nothing; calls that overlap on one dt_out race.  Errors
+ * as above. */
 cudisc_status cudisc_dust_cfl_dt(int n_species, int n_cells, const double *P, const double *dR, const double *dZ,
                                  const double *nu, const double *Sc, double C_adv, double C_diff, double *dt_out,
                                  void *stream);
@@ -306,6 +319,22 @@ cudisc_status cudisc_coag_batch_step(cudisc_coag_batch *batch, double *const *rh
                                      double *const *dt_cell, void *stream, cudisc_step_stats *stats);
 void cudisc_coag_batch_destroy(cudisc_coag_batch *batch);
 
+/* Shards for several GPUs.  During a coagulation call every cell evolves on
+ * its own (Sec. 2: the per-cell update; Sec. 5), so a job spreads over GPUs
+ * with no exchange: each process takes a contiguous range of the cells (in
+ * index order c = i_R n_Z + i_Z, so a range of radii) or of whole discs,
+ * builds its own context on it (pointers offset to the range's first cell)
+ * and integrates it.  This splits n_items consecutive items with costs cost
+ * (host [n_items], finite, >= 0; NULL: 1 each; e.g. accepted substeps per
+ * cell from an earlier step, or n_cells x N^2 per disc) into n_parts ranges
+ * whose largest total cost is the smallest any contiguous split reaches
+ * (to 1e-13 relative): range k is items bounds[k] .. bounds[k+1] - 1
+ * (bounds host [n_parts + 1], bounds[0] = 0, bounds[n_parts] = n_items,
+ * nondecreasing; trailing ranges may be empty).  Host only; needs no GPU
+ * or context.  Errors: CUDISC_EINVAL for n_items < 0, n_parts < 1, a NULL
+ * bounds or a negative or non-finite cost. */
+cudisc_status cudisc_partition(int n_items, const double *cost, int n_parts, int *bounds);
+
 /* Optional per-cell records for later cudisc_coag_step calls (all device
  * pointers; pass NULLs to stop recording):
  *   dt_log [n_cells][log_cap] accepted step sizes in order,
@@ -323,7 +352,7 @@ cudisc_status cudisc_coag_replay(cudisc_coag_ctx *ctx, double *rho, const double
                                  const long long *n_h, long long stride);
 
 /* Same integration as cudisc_coag_step on a CUDISC_MIXED_TF32 context, but
- * the per-cell-slot integrator state lives in a fixed 16 MiB device array
+ * the per-cell-slot integrator scratch lives in a fixed 16 MiB device array
  * compiled into the library instead of the context's workspace.  The paper
  * has no counterpart: this is for callers that cannot allocate device memory
  * at the point where they integrate, for example a code whose device memory
@@ -331,20 +360,33 @@ cudisc_status cudisc_coag_replay(cudisc_coag_ctx *ctx, double *rho, const double
  * cudaMalloc's implicit device synchronisation.  This call itself allocates
  * nothing (no cudaMalloc, cudaFree or allocating library routine); the caller
  * passes rho and dt_cell exactly as for cudisc_coag_step.
- *   - The first call on each device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *   - The scratch holds the per-slot FP32 state (state pair and stage
+ *     right-hand sides) when it does not fit in the kernel's shared memory;
+ *     cudisc_coag_scratch_bytes gives its size for a context (0: shared
+ *     memory holds it and the array is not touched).
+ *   - The first call on each context looks up the array's device address
+ *     (cudaGetSymbolAddress, with the context's device current); make that
+ *     first call before any stream capture.
  *   - Every GPU that loads the library holds the 16 MiB until the process
  *     exits, whether or not this entry point is used.
  *   - All calls share the one array (it keeps the last call's contents, and
- *     every slot is written before it is read): calls that overlap on the GPU,
- *     from any context, race and give wrong results.
- *   - Problems whose slot state exceeds 16 MiB (slot groups x 64 slots x 5
- *     x N x 4 bytes; see cudisc_coag_mixed_cluster for the groups) are
- *     rejected with CUDISC_ENOTSUP and a message; use cudisc_coag_step for
- *     them.
+ *     every slot's state is written before it is read): calls that overlap
+ *     on the GPU, from any context, race and give wrong results.
+ *   - Problems whose scratch exceeds 16 MiB (slot groups x 64 slots x 5 x N x
+ *     4 bytes when it is used; see cudisc_coag_mixed_cluster for the groups)
+ *     are rejected with CUDISC_ENOTSUP and a message; use cudisc_coag_step
+ *     for them.
  *   - Returns CUDISC_EINVAL for a context of another precision. */
 cudisc_status cudisc_coag_step_static_scratch(cudisc_coag_ctx *ctx, double *rho, double t_span,
                                               double *dt_cell, cudisc_step_stats *stats);
+
+/* Bytes of device scratch beyond the context's tables that one integration
+ * of the mixed-precision kernel uses for its per-slot state: slot groups x
+ * 64 slots x 5 x N x 4 when that state does not fit in shared memory, else
+ * 0 (also 0 for an FP64 context).  cudisc_coag_step takes it from the
+ * context's workspace, cudisc_coag_step_static_scratch from its fixed
+ * array.  EINVAL for a NULL argument.  Host only. */
+cudisc_status cudisc_coag_scratch_bytes(const cudisc_coag_ctx *ctx, size_t *bytes);
 
 /* Device times (CUDA events on params.stream) of the last call of each kind:
  * the per-cell prep and the kernel-table build of cudisc_coag_build_kernel,

@@ -81,6 +81,7 @@ def lib():
         v, d = C.c_void_p, C.c_double
         L.cudisc_coag_init.argtypes = [C.POINTER(cudisc_coag_params), C.POINTER(v)]
         L.cudisc_coag_build_kernel.argtypes = [v]
+        L.cudisc_coag_build_kernel_async.argtypes = [v]
         L.cudisc_coag_get_kernel.argtypes = [v, v, v]
         L.cudisc_coag_rhs.argtypes = [v, v, v]
         L.cudisc_coag_step.argtypes = [v, v, d, v, C.POINTER(cudisc_step_stats)]
@@ -103,6 +104,8 @@ def lib():
         L.cudisc_coag_step_static_scratch.argtypes = [v, v, d, v, C.POINTER(cudisc_step_stats)]
         L.cudisc_coag_get_timings.argtypes = [v, C.POINTER(cudisc_timings)]
         L.cudisc_coag_mixed_cluster.argtypes = [v, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.cudisc_coag_scratch_bytes.argtypes = [v, C.POINTER(C.c_size_t)]
+        L.cudisc_partition.argtypes = [C.c_int, v, C.c_int, v]
         L.cudisc_coag_set_v_frag.argtypes = [v, d]
         L.cudisc_coag_vjp.argtypes = [v, v, d, v, v, C.c_longlong, v, v, v, v]
         L.cudisc_coag_destroy.argtypes = [v]
@@ -110,11 +113,11 @@ def lib():
         L.cudisc_coag_last_error.argtypes = [v]
         L.cudisc_coag_last_error.restype = C.c_char_p
         L.cudisc_coag_version.restype = C.c_char_p
-        for fn in ("cudisc_coag_init", "cudisc_coag_build_kernel", "cudisc_coag_get_kernel",
+        for fn in ("cudisc_coag_init", "cudisc_coag_build_kernel", "cudisc_coag_build_kernel_async", "cudisc_coag_get_kernel",
                    "cudisc_coag_rhs", "cudisc_coag_step", "cudisc_coag_set_records",
                    "cudisc_coag_replay", "cudisc_coag_step_static_scratch",
                    "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp",
-                   "cudisc_coag_mixed_cluster", "cudisc_coag_step_async", "cudisc_coag_step_wait",
+                   "cudisc_coag_mixed_cluster", "cudisc_coag_scratch_bytes", "cudisc_partition", "cudisc_coag_step_async", "cudisc_coag_step_wait",
                    "cudisc_coag_init_batched", "cudisc_coag_batch_ctx", "cudisc_coag_batch_build_kernel",
                    "cudisc_dust_source_update", "cudisc_dust_cfl_dt", "cudisc_hse_rho_gas", "cudisc_coag_batch_step", "cudisc_coag_step_spans", "cudisc_coag_subcycle",
                    "cudisc_coag_subcycle_pending"):
@@ -139,6 +142,10 @@ def cudisc_coag_init(params: cudisc_coag_params):
 
 def cudisc_coag_build_kernel(ctx):
     _check(lib().cudisc_coag_build_kernel(ctx), ctx)
+
+
+def cudisc_coag_build_kernel_async(ctx):
+    _check(lib().cudisc_coag_build_kernel_async(ctx), ctx)
 
 
 def cudisc_coag_get_kernel(ctx, K_ptr, KF_ptr):
@@ -316,6 +323,25 @@ def cudisc_coag_mixed_cluster(ctx) -> tuple:
     return cl.value, gr.value
 
 
+def cudisc_coag_scratch_bytes(ctx) -> int:
+    n = C.c_size_t()
+    _check(lib().cudisc_coag_scratch_bytes(ctx, C.byref(n)), ctx)
+    return int(n.value)
+
+
+def cudisc_partition(cost, n_parts: int, n_items: int = None):
+    """Contiguous ranges of items (cells or whole discs) for n_parts GPUs,
+    balanced by cost (None: equal costs); returns bounds [n_parts + 1]."""
+    if cost is None:
+        n, cp = int(n_items), None
+    else:
+        c = np.ascontiguousarray(cost, dtype=np.float64)
+        n, cp = c.size, c.ctypes.data
+    b = np.zeros(int(n_parts) + 1, dtype=np.int32)
+    _check(lib().cudisc_partition(n, cp, int(n_parts), b.ctypes.data))
+    return b
+
+
 def cudisc_coag_destroy(ctx):
     lib().cudisc_coag_destroy(ctx)
 
@@ -394,6 +420,13 @@ class Coag:
 
     def build_kernel(self):
         cudisc_coag_build_kernel(self.ctx)
+
+    def build_kernel_async(self):
+        """Issue the kernel-table rebuild on the context's stream (graph-capturable)."""
+        cudisc_coag_build_kernel_async(self.ctx)
+
+    def scratch_bytes(self) -> int:
+        return cudisc_coag_scratch_bytes(self.ctx)
 
     def timings(self) -> dict:
         return cudisc_coag_get_timings(self.ctx)

@@ -534,6 +534,14 @@ cudisc_status cudisc_coag_build_kernel(cudisc_coag_ctx *c)
     return CUDISC_OK;
 }
 
+cudisc_status cudisc_coag_build_kernel_async(cudisc_coag_ctx *c)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    CUDA_TRY(c, cdc::launch_prep(c));
+    CUDA_TRY(c, cdc::launch_kbuild(c));
+    return CUDISC_OK;
+}
+
 cudisc_status cudisc_coag_set_v_frag(cudisc_coag_ctx *c, double v_frag)
 {
     if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
@@ -773,7 +781,17 @@ cudisc_status cudisc_coag_step_static_scratch(cudisc_coag_ctx *c, double *rho, d
         return fail(c, CUDISC_ENOTSUP, buf);
     }
     CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
+    c->timed = true;
     return finish_step(c, stats);
+}
+
+cudisc_status cudisc_coag_scratch_bytes(const cudisc_coag_ctx *c, size_t *bytes)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!bytes) return CUDISC_EINVAL;
+    *bytes = c->p.precision == CUDISC_MIXED_TF32 ? cdc::mixed_scratch_bytes(c->n_cells, c->N, c->mix_P, c->p.max_sms)
+                                                 : 0;
+    return CUDISC_OK;
 }
 
 cudisc_status cudisc_coag_replay(cudisc_coag_ctx *c, double *rho, const double *hs,
@@ -1013,5 +1031,58 @@ cudisc_status cudisc_coag_batch_step(cudisc_coag_batch *b, double *const *rho, d
 }
 
 void cudisc_coag_batch_destroy(cudisc_coag_batch *b) { free_batch(b); }
+
+// ---- shards for several GPUs ---------------------------------------------
+//
+// Cells (and whole discs) are independent during a coagulation call, so a
+// job spreads over GPUs by giving each a contiguous range of them.  The
+// ranges minimise the largest range cost: the smallest bottleneck B for
+// which a greedy left-to-right fill (a new range once the next item would
+// take the running sum past B) needs at most n_parts ranges is found by
+// bisection between max(largest item, total / n_parts) and the total, and
+// that fill gives the bounds.  Unused trailing ranges are empty.
+
+static int greedy_parts(int n, const double *cost, double B, int *bounds, int n_parts)
+{
+    int parts = 1;
+    double acc = 0.0;
+    if (bounds) bounds[0] = 0;
+    for (int i = 0; i < n; i++) {
+        const double c = cost ? cost[i] : 1.0;
+        if (acc > 0.0 && acc + c > B) {
+            if (bounds && parts < n_parts) bounds[parts] = i;
+            parts++;
+            acc = c;
+        } else {
+            acc += c;
+        }
+    }
+    if (bounds)
+        for (int k = std::min(parts, n_parts); k <= n_parts; k++) bounds[k] = n;
+    return parts;
+}
+
+cudisc_status cudisc_partition(int n_items, const double *cost, int n_parts, int *bounds)
+{
+    g_thread_err.clear();
+    if (n_items < 0 || n_parts < 1) return fail(nullptr, CUDISC_EINVAL, "n_items must be >= 0 and n_parts >= 1");
+    if (!bounds) return fail(nullptr, CUDISC_EINVAL, "bounds is NULL");
+    double total = 0.0, big = 0.0;
+    for (int i = 0; i < n_items; i++) {
+        const double c = cost ? cost[i] : 1.0;
+        if (!(c >= 0.0) || !std::isfinite(c)) return fail(nullptr, CUDISC_EINVAL, "costs must be finite and >= 0");
+        total += c;
+        big = std::max(big, c);
+    }
+    double lo = std::max(big, total / n_parts), hi = std::max(total, lo);
+    if (greedy_parts(n_items, cost, lo, nullptr, n_parts) <= n_parts) hi = lo;
+    for (int it = 0; it < 200 && hi - lo > 1e-13 * hi; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (greedy_parts(n_items, cost, mid, nullptr, n_parts) <= n_parts) hi = mid;
+        else lo = mid;
+    }
+    greedy_parts(n_items, cost, hi, bounds, n_parts);
+    return CUDISC_OK;
+}
 
 } // extern "C"

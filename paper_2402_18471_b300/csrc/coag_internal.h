@@ -113,6 +113,7 @@ struct cudisc_coag_ctx {
     float4 *d_Kslot = nullptr;         // mixed kernel: [group][block][8 chunks][64 slots] of the slots' tables
     int mix_P = 1, mix_G = 1, mix_C = 1;   // mixed kernel: CTAs per slot group, groups, initial cells per group
     bool timed = false;                // the last integration issued recorded ev0/ev1
+    void *static_scratch = nullptr;    // device address of the fixed scratch array (first static call)
     // integration workspace
     cdc::CellOut *d_out = nullptr;     // [n_cells]
     double *d_work = nullptr;          // mixed path slot state
@@ -180,6 +181,9 @@ cudaError_t vjp_worst_status(const cudisc_coag_ctx *c, int *worst);
 void vjp_free(cudisc_coag_ctx *c);
 // fixed-scratch variant of the mixed step (see cudisc_coag_step_static_scratch)
 size_t static_scratch_bytes();
-cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, double t_span,
+cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_span,
                                      double *dt_cell, bool *too_big);
+// bytes of global scratch the mixed integration's per-slot state takes (0:
+// it is kept in shared memory)
+size_t mixed_scratch_bytes(int n_cells, int N, int P, int max_sms);
 } // namespace cdc

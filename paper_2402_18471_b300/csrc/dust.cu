@@ -69,37 +69,58 @@ __global__ void dust_cfl_init(double *w)
 }
 
 // Per element only multiplications: the per-cell 1/dR, 1/dZ and
-// min(dR^2, dZ^2) / nu are formed once per thread.
+// min(dR^2, dZ^2) / nu are formed once per thread.  An input outside the
+// domain of Eqs. dt_adv and dt_diff (a non-finite velocity; Sc, dR or dZ not
+// positive and finite; nu negative or NaN) would otherwise drop out of the
+// fmax/fmin reduction (or, negative, out of the unsigned atomicMin) and leave
+// a plausible finite step: it sets w[1] to NaN instead, and so the result.
 __global__ void __launch_bounds__(kDustThreads) dust_cfl_kernel(
     int n_s, int n_c, const double *__restrict__ P, const double *__restrict__ dR,
     const double *__restrict__ dZ, const double *__restrict__ nu, const double *__restrict__ Sc, double *w)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     double rate = 0.0, dif = INFINITY;
+    bool bad = false;
     if (c < n_c) {
-        const double dr = dR[c], dz = dZ[c];
+        const double dr = dR[c], dz = dZ[c], nc = nu[c];
+        bad = !(fabs(dr) > 0.0) || !(fabs(dz) > 0.0) || !isfinite(dr) || !isfinite(dz) || !(nc >= 0.0);
         const double ir = 1.0 / fabs(dr), iz = 1.0 / fabs(dz);
-        const double g = fmin(dr * dr, dz * dz) / fabs(nu[c]);
+        const double g = fmin(dr * dr, dz * dz) / nc;
         const size_t plane = (size_t)n_s * n_c;
         const int s0 = blockIdx.y * kSpecPerThread;
         const int s1 = min(n_s, s0 + kSpecPerThread);
         for (int s = s0; s < s1; s++) {
             const size_t e = (size_t)s * n_c + c;
-            rate = fmax(rate, fmax(fabs(P[plane + e]) * ir, fabs(P[3 * plane + e]) * iz));
-            dif = fmin(dif, Sc[s] * g);
+            const double vr = P[plane + e], vz = P[3 * plane + e], sc = Sc[s];
+            bad = bad || !isfinite(vr) || !isfinite(vz) || !(sc > 0.0) || !isfinite(sc);
+            rate = fmax(rate, fmax(fabs(vr) * ir, fabs(vz) * iz));
+            dif = fmin(dif, sc * g);
         }
     }
+    bad = __any_sync(0xffffffffu, bad);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
         dif = fmin(dif, __shfl_xor_sync(0xffffffffu, dif, o));
     }
     __shared__ double wr[kDustThreads / 32], wd[kDustThreads / 32];
-    if ((threadIdx.x & 31) == 0) { wr[threadIdx.x >> 5] = rate; wd[threadIdx.x >> 5] = dif; }
+    __shared__ int wb[kDustThreads / 32];
+    if ((threadIdx.x & 31) == 0) {
+        wr[threadIdx.x >> 5] = rate;
+        wd[threadIdx.x >> 5] = dif;
+        wb[threadIdx.x >> 5] = bad;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 1; k < kDustThreads / 32; k++) { rate = fmax(rate, wr[k]); dif = fmin(dif, wd[k]); }
-        if (rate > 0.0)
+        for (int k = 1; k < kDustThreads / 32; k++) {
+            rate = fmax(rate, wr[k]);
+            dif = fmin(dif, wd[k]);
+            bad = bad || wb[k];
+        }
+        // a positive quiet NaN orders above every positive double as an
+        // unsigned integer, so it survives the maximum
+        if (bad) rate = __longlong_as_double(0x7FF8000000000000LL);
+        if (bad || rate > 0.0)
             atomicMax(reinterpret_cast<unsigned long long *>(w + 1), (unsigned long long)__double_as_longlong(rate));
         if (dif < INFINITY)
             atomicMin(reinterpret_cast<unsigned long long *>(w + 2), (unsigned long long)__double_as_longlong(dif));
@@ -108,6 +129,7 @@ __global__ void __launch_bounds__(kDustThreads) dust_cfl_kernel(
 
 __global__ void dust_cfl_finish(double *w, double C_adv, double C_diff)
 {
+    if (isnan(w[1])) { w[0] = w[1]; return; }
     const double adv = w[1] > 0.0 ? C_adv / w[1] : INFINITY;
     w[0] = fmin(adv, C_diff * w[2]);
 }

@@ -1486,49 +1486,48 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
 } // namespace
 
 // ---- fixed-scratch variant -------------------------------------------------
-// Scratch for cudisc_coag_step_static_scratch: the per-slot FP64 integrator
-// state that the regular entry point keeps in the context's workspace.  It is
-// a file-scope device array of fixed size, so every GPU that loads this
+// Scratch for cudisc_coag_step_static_scratch: the per-slot FP32 integrator
+// state (state pair and stage right-hand sides) that the regular entry point
+// keeps in the context's workspace whenever it does not fit in shared memory.
+// It is a file-scope device array of fixed size, so every GPU that loads this
 // library holds these 16 MiB until the process exits.  Host code must not
 // pass the symbol itself to a kernel (on the host it only names a stand-in);
-// the device address comes from cudaGetSymbolAddress, taken once per device.
+// the device address comes from cudaGetSymbolAddress, taken with the
+// context's device current at the context's first call of the entry point.
 namespace {
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
 } // namespace
 
 size_t static_scratch_bytes() { return kStaticScratchBytes; }
 
-cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, double t_span,
-                                     double *dt_cell, bool *too_big)
+size_t mixed_scratch_bytes(int n_cells, int N, int P, int max_sms)
+{
+    const Config cf = mixed_config(n_cells, N, P, max_sms);
+    return cf.sst_off >= 0 ? 0 : (size_t)cf.groups * cf.NS * 5 * (size_t)N * sizeof(float);
+}
+
+cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_span, double *dt_cell,
+                                     bool *too_big)
 {
     *too_big = false;
     Config cf = mixed_config(c->n_cells, c->N, c->mix_P, c->p.max_sms);
-    const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(float);
+    // the array is only touched when the per-slot state does not fit in
+    // shared memory
+    const size_t need = cf.sst_off >= 0 ? 0 : (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(float);
     if (need > kStaticScratchBytes) { *too_big = true; return cudaSuccess; }
     if (cf.P != c->mix_P || cf.groups != c->mix_G || cf.C != c->mix_C)
         return cudaErrorInvalidValue;   // layout of the K tables
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    void *scratch = nullptr;
-    {
-        // set-up, once per device, with that device current
-        std::lock_guard<std::mutex> lk(g_scratch_mu);
-        if (!g_scratch_ptr[dev]) {
-            void *ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-            if (e != cudaSuccess) return e;
-            g_scratch_ptr[dev] = ptr;
-        }
-        scratch = g_scratch_ptr[dev];
+    if (!c->static_scratch) {
+        // set-up, once per context, with its device current: the array's
+        // device address (a context made after a device reset looks it up
+        // again; the old contexts' buffers are gone with that reset anyway)
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        c->static_scratch = ptr;
     }
-    e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
+    cudaError_t e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(c->d_counter + 1, 0, 2 * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
@@ -1550,7 +1549,7 @@ cudaError_t launch_step_mixed_static(const cudisc_coag_ctx *c, double *rho, doub
     a.out = c->d_out;
     a.err = c->d_counter + 1;
     a.queue = c->d_counter + 2;
-    a.work = (float *)scratch;      // every slot is written before it is read
+    a.work = (float *)c->static_scratch;   // every slot's state is written before it is read
     a.rec_dt = c->rec_dt;
     a.rec_cap = c->rec_cap;
     a.rec_n = c->rec_n;

@@ -161,7 +161,13 @@ def _disc_fields(R_c, n_Z, T0, Sigma0, h0, rng, rho_pert):
 
 
 def mrn_initial(a, rho_gas, a_cut=1e-4, d2g=0.01):
+    """MRN start: mass per log bin ~ a^0.5 up to a_cut, dust-to-gas d2g.  A
+    grid whose smallest bin already lies above a_cut starts with all the
+    dust in bin 0."""
     w = np.where(a <= a_cut * (1 + 1e-12), a ** 0.5, 0.0)
+    if not w.sum() > 0.0:
+        w = np.zeros_like(a, dtype=np.float64)
+        w[0] = 1.0
     w = w / w.sum()
     return np.ascontiguousarray(d2g * rho_gas[:, None] * w[None, :])
 
@@ -197,28 +203,28 @@ def make_disc(n_R, n_Z, n_bins, a_min, a_max, R_in_au, R_out_au, t_span_yr,
 # quoted on, the adjoint problem, the large grid and a batch of uneven discs.
 # ---------------------------------------------------------------------------
 
-def column_1x32(**kw) -> Disc:
+def column_1x32(seed=None, **kw) -> Disc:
     """1 R (10 au) x 32 Z, 50 bins 0.1 um - 1 cm, alpha 1e-3, v_frag 1 m/s, 1000 yr."""
     return make_disc(1, 32, 50, 1e-5, 1.0, 10.0, 10.0, 1000.0, alpha=1e-3,
-                     v_frag=100.0, seed=None, name="column_1x32_N50", **kw)
+                     v_frag=100.0, seed=seed, name="column_1x32_N50", **kw)
 
 
-def grid_128x64(**kw) -> Disc:
+def grid_128x64(seed=1, **kw) -> Disc:
     """128 R (log 5-100 au) x 64 Z, 100 bins 0.1 um - 10 cm, 1e4 yr, +-10% rho_g."""
     return make_disc(128, 64, 100, 1e-5, 10.0, 5.0, 100.0, 1e4, alpha=1e-3,
-                     v_frag=100.0, seed=1, rho_pert=0.1, name="grid_128x64_N100", **kw)
+                     v_frag=100.0, seed=seed, rho_pert=0.1, name="grid_128x64_N100", **kw)
 
 
-def adjoint_64x32(v_frag=100.0, **kw) -> Disc:
+def adjoint_64x32(v_frag=100.0, seed=2, **kw) -> Disc:
     """64 R x 32 Z, 80 bins 0.1 um - 1 cm, alpha lognormal 0.3 dex, 2000 yr."""
     return make_disc(64, 32, 80, 1e-5, 1.0, 5.0, 100.0, 2000.0, alpha=1e-3,
-                     v_frag=v_frag, seed=2, alpha_dex=0.3, name="adjoint_64x32_N80", **kw)
+                     v_frag=v_frag, seed=seed, alpha_dex=0.3, name="adjoint_64x32_N80", **kw)
 
 
-def grid_512x256(**kw) -> Disc:
+def grid_512x256(seed=3, **kw) -> Disc:
     """512 R x 256 Z, 150 bins 0.1 um - 100 cm, alpha 1e-4, v_frag 10 m/s, 1e4 yr."""
     return make_disc(512, 256, 150, 1e-5, 100.0, 5.0, 100.0, 1e4, alpha=1e-4,
-                     v_frag=1000.0, seed=3, name="grid_512x256_N150", **kw)
+                     v_frag=1000.0, seed=seed, name="grid_512x256_N150", **kw)
 
 
 def batch_32_discs(seed=4):
@@ -281,11 +287,11 @@ def ring_20au(**kw) -> Disc:
                           name="ring_20au_N150", **kw)
 
 
-def rings_4096(**kw) -> Disc:
+def rings_4096(seed=8, **kw) -> Disc:
     """4096 rings log-spaced over 5-100 au, 100 bins 0.1 um - 10 cm,
     alpha 1e-3 (0.2 dex scatter), v_frag 1 m/s, 1e4 yr."""
     return make_ring_disc(4096, 100, 1e-5, 10.0, 5.0, 100.0, 1e4, alpha=1e-3, v_frag=100.0,
-                          seed=8, name="rings_4096_N100", **kw)
+                          seed=seed, name="rings_4096_N100", **kw)
 
 
 def hse_inputs(disc: Disc, t_rise=0.0):

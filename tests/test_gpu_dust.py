@@ -88,3 +88,28 @@ def test_cfl_matches_oracle(coag_mod, n_s, n_c):
     want = dust.cfl_dt(P[1], P[3], dR, dZ, nu, Sc)
     got = float(coag_mod.dust_cfl_dt(dev(P), dev(dR), dev(dZ), dev(nu), dev(Sc)).cpu()[0])
     assert got == pytest.approx(want, rel=1e-14)
+
+
+@pytest.mark.parametrize("where", ["v_R", "v_Z", "Sc", "dR", "nu"])
+def test_cfl_flags_inputs_outside_its_domain(coag_mod, where):
+    """One non-finite velocity, or a non-positive Sc or dR, or a negative nu,
+    gives NaN rather than a finite step from the remaining elements."""
+    _, P, R, _, _, c_s, _, _ = inputs(6, 700, seed=21)
+    dR = R * 0.02
+    dZ = R * 0.003
+    nu = 1e-3 * c_s * c_s / np.sqrt(G_M / R ** 3)
+    Sc = np.ones(6)
+    ok = float(coag_mod.dust_cfl_dt(dev(P), dev(dR), dev(dZ), dev(nu), dev(Sc)).cpu()[0])
+    assert np.isfinite(ok) and ok > 0
+    if where == "v_R":
+        P[1, 3, 411] = np.nan
+    elif where == "v_Z":
+        P[3, 0, 699] = np.inf
+    elif where == "Sc":
+        Sc[2] = -1.0
+    elif where == "dR":
+        dR[5] = 0.0
+    else:
+        nu[300] = -nu[300]
+    out = coag_mod.dust_cfl_dt(dev(P), dev(dR), dev(dZ), dev(nu), dev(Sc)).cpu().numpy()
+    assert np.isnan(out[0]) and np.isnan(out[1])
