@@ -226,7 +226,14 @@ def accuracy_check(disc, y, hs, n_h, cells, rhs_gpu=None, rhs_state=None):
         K, _, _ = o.kernel()
         n = rhs_state / sub.m
         gross = (sub.m * n * np.einsum("cik,ci->ck", K, n)).sum(1)
-        out["rhs_err_over_gross_max"] = float((np.abs(rhs_gpu - o.rhs(rhs_state)) / gross[:, None]).max())
+        ref = o.rhs(rhs_state)
+        err = np.abs(rhs_gpu - ref)
+        out["rhs_err_over_gross_max"] = float((err / gross[:, None]).max())
+        # per bin, against the net rate itself (floor 1e-6 of the cell's
+        # largest net rate): random states' net rates are ~1e-11 of the gross
+        # collision flux, so the gross-relative figure alone says little
+        scale = np.abs(ref) + 1e-6 * np.abs(ref).max(1, keepdims=True)
+        out["rhs_rel_err_max"] = float((err / scale).max())
     return out
 
 
@@ -743,7 +750,7 @@ def main():
                        **({"vertical": 1} if disc.vertical else {}),
                        "step": "state copy-in + kernel build + BS3 integration of all cells over t_span, "
                                "one CUDA graph replay",
-                       "accuracy_scope": "1e-5 holds per right-hand side (rhs_err_over_gross_max) and over "
+                       "accuracy_scope": "1e-5 holds per right-hand side (accuracy.*.rhs_rel_err_max) and over "
                                          "spans short of the coagulation-fragmentation balance; over the full "
                                          "1e4 yr it holds on the fraction of bins in accuracy.frac_bins_within_1e-5 "
                                          "(the FP64 GPU path also misses it once rtol <= 1e-3)",
