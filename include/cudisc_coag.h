@@ -273,6 +273,77 @@ cudisc_status cudisc_dust_cfl_dt(int n_species, int n_cells, const double *P, co
                                  const double *nu, const double *Sc, double C_adv, double C_diff, double *dt_out,
                                  void *stream);
 
+/* The dust transport step of Sec. 3.1-3.2 (Eqs. quants, dynfluxes,
+ * advgen, advdisc, fluxarea, halftimestepupdate, roeav, riemann, diffflux,
+ * Fdiffmom, fluxes, weights, vkl, normaldecomp, F_k; Appendix A) on the
+ * (R, theta) grid of Sec. 2, for n_species pressureless dust fluids: the
+ * full step's items i-viii.  Stage 1: donor-cell face states of the
+ * primitives at t^n, the upwind flux of the pressureless Riemann problem by
+ * the sign of the Roe-averaged normal velocity (0 where the two sides move
+ * apart), plus the diffusive flux -(rho_g nu / Sc) grad(rho / rho_g)
+ * through the non-orthogonal stencil of Wu, Gao & Dai as the paper applies
+ * it (each momentum component carried by the diffusive mass flux from its
+ * upwind face state), Q* = Q^n - dt/2 (FA)^n / V, then the half-step
+ * source update.  Stage 2: piecewise-linear face states of the n + 1/2
+ * primitives with the van Leer limiter generalised to non-uniform grids,
+ * the same fluxes, Q = Q^n - dt (FA)^(n+1/2) / V, then the full-step source
+ * update.  The sources (curvature, gravity, exact implicit Epstein drag) are
+ * those of cudisc_dust_source_update.
+ * Grid: radial edges R_e [n_R + 1] (cm, increasing, > 0) and polar-angle
+ * edges th_e [n_Z + 1] (radians above the mid-plane, increasing, |th| < 1.5)
+ * as host arrays; centres R_c [n_R], th_c [n_Z] (host, NULL: midpoints);
+ * cell (i, j) has centre (R_c[i], R_c[i] tan th_c[j]) and index c = i n_Z + j.
+ * Geometry: volumes V = d(R^3)/3 d(tan th), radial face areas
+ * (R_e)^2 d(tan th) and polar face areas d(R^2)/2 / cos(th_e) (cylindrical,
+ * per radian of azimuth), or the planar V = d(R^2)/2 d(tan th), R_e d(tan
+ * th), dR / cos(th_e) (cartesian, the paper's test geometry).
+ * Boundaries bc[4] (inner R, outer R, lower theta, upper theta): OUTFLOW
+ * (two ghost layers copy the adjacent active cell), CLOSED (the same, with
+ * no flux through the boundary face), ZERO (ghosts at the floor density at
+ * rest); the paper's default is {OUTFLOW, OUTFLOW, CLOSED, OUTFLOW} with the
+ * mid-plane at th_e[0] = 0.  Ghost cells mirror the widths of the boundary
+ * cells.
+ * Fields (device, FP64): rho_g, nu [n_R n_Z] (gas density, kinematic
+ * viscosity; nu NULL: no diffusion), Sc [n_species] (with nu); sources (all
+ * or none; c_s NULL: transport only): c_s [n_R n_Z], v_g [3][n_R n_Z], a
+ * [n_species], rho_m, GM.  The context keeps these pointers and its own
+ * workspace (about 10 x 4 n_species n_R n_Z doubles).  A cell with density
+ * <= 0 has zero velocity. */
+typedef struct cudisc_dust_ctx cudisc_dust_ctx;   /* opaque, owned by the library */
+typedef enum { CUDISC_GEOM_CYLINDRICAL = 0, CUDISC_GEOM_CARTESIAN = 1 } cudisc_geometry;
+typedef enum { CUDISC_BC_OUTFLOW = 0, CUDISC_BC_CLOSED = 1, CUDISC_BC_ZERO = 2 } cudisc_boundary;
+typedef struct {
+    int n_species, n_R, n_Z;
+    const double *R_e, *th_e;    /* host [n_R + 1], [n_Z + 1] */
+    const double *R_c, *th_c;    /* host [n_R], [n_Z], or NULL: midpoints */
+    int geometry;                /* cudisc_geometry */
+    int bc[4];                   /* cudisc_boundary: inner R, outer R, lower th, upper th */
+    double floor;                /* density of ZERO ghost cells */
+    const double *rho_g, *nu;    /* device [n_R n_Z]; nu NULL: no diffusion */
+    const double *Sc;            /* device [n_species] Schmidt numbers (with nu) */
+    const double *c_s, *v_g, *a; /* device [n_R n_Z], [3][n_R n_Z], [n_species]; c_s NULL: no sources */
+    double rho_m, GM;            /* grain material density; G M_* (sources) */
+    void *stream;                /* cudaStream_t, NULL: legacy default stream */
+} cudisc_dust_params;
+/* Validate (CUDISC_EINVAL naming the field, through
+ * cudisc_coag_last_error(NULL)), build the geometry on the host, allocate the
+ * workspace and the diffusion stencil (as cudisc_dust_update_gas). */
+cudisc_status cudisc_dust_init(const cudisc_dust_params *params, cudisc_dust_ctx **out);
+/* Recompute the diffusion stencil's coefficients after the caller changed
+ * the rho_g or nu arrays (asynchronous on the stream). */
+cudisc_status cudisc_dust_update_gas(cudisc_dust_ctx *ctx);
+/* One full step of dt seconds (>= 0, finite): Q [4][n_species][n_R n_Z]
+ * device FP64 (rho, rho v_R, rho v_phi R, rho v_Z), read and overwritten.
+ * Asynchronous on the stream; allocates nothing (graph-capturable); steps on
+ * one context must not overlap.  The CFL step is cudisc_dust_cfl_dt's. */
+cudisc_status cudisc_dust_step(cudisc_dust_ctx *ctx, double *Q, double dt);
+/* Copy the geometry out (device FP64, each may be NULL): V [n_R n_Z], radial
+ * face areas AR [(n_R + 1) n_Z] (face a at R_e[a], row j: a n_Z + j), polar
+ * face areas AZ [n_R (n_Z + 1)] (cell row i, face b at th_e[b]: i (n_Z + 1)
+ * + b).  Synchronises the stream. */
+cudisc_status cudisc_dust_geometry(const cudisc_dust_ctx *ctx, double *V, double *AR, double *AZ);
+void cudisc_dust_destroy(cudisc_dust_ctx *ctx);
+
 /* Sub-cycled coagulation (Sec. 6): the coagulation solver takes its own
  * sub-steps inside the global time steps of the disc model, and a cell's
  * coagulation is brought up to date only once one (by default) of its last

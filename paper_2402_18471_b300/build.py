@@ -8,7 +8,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcudisc_coag.so")
-SOURCES = ["coag_host.cu", "kbuild.cu", "step_fp64.cu", "step_mixed.cu", "vjp.cu", "hse.cu", "dust.cu"]
+SOURCES = ["coag_host.cu", "kbuild.cu", "step_fp64.cu", "step_mixed.cu", "vjp.cu", "hse.cu", "dust.cu",
+           "transport.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -47,6 +47,17 @@ class cudisc_coag_params(C.Structure):
     ]
 
 
+class cudisc_dust_params(C.Structure):
+    _fields_ = [
+        ("n_species", C.c_int), ("n_R", C.c_int), ("n_Z", C.c_int),
+        ("R_e", C.c_void_p), ("th_e", C.c_void_p), ("R_c", C.c_void_p), ("th_c", C.c_void_p),
+        ("geometry", C.c_int), ("bc", C.c_int * 4), ("floor", C.c_double),
+        ("rho_g", C.c_void_p), ("nu", C.c_void_p), ("Sc", C.c_void_p),
+        ("c_s", C.c_void_p), ("v_g", C.c_void_p), ("a", C.c_void_p),
+        ("rho_m", C.c_double), ("GM", C.c_double), ("stream", C.c_void_p),
+    ]
+
+
 class cudisc_timings(C.Structure):
     _fields_ = [("prep_ms", C.c_double), ("kbuild_ms", C.c_double),
                 ("step_ms", C.c_double), ("vjp_ms", C.c_double)]
@@ -106,6 +117,12 @@ def lib():
         L.cudisc_coag_mixed_cluster.argtypes = [v, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.cudisc_coag_scratch_bytes.argtypes = [v, C.POINTER(C.c_size_t)]
         L.cudisc_partition.argtypes = [C.c_int, v, C.c_int, v]
+        L.cudisc_dust_init.argtypes = [C.POINTER(cudisc_dust_params), C.POINTER(v)]
+        L.cudisc_dust_update_gas.argtypes = [v]
+        L.cudisc_dust_step.argtypes = [v, v, d]
+        L.cudisc_dust_geometry.argtypes = [v, v, v, v]
+        L.cudisc_dust_destroy.argtypes = [v]
+        L.cudisc_dust_destroy.restype = None
         L.cudisc_coag_set_v_frag.argtypes = [v, d]
         L.cudisc_coag_vjp.argtypes = [v, v, d, v, v, C.c_longlong, v, v, v, v]
         L.cudisc_coag_destroy.argtypes = [v]
@@ -117,7 +134,8 @@ def lib():
                    "cudisc_coag_rhs", "cudisc_coag_step", "cudisc_coag_set_records",
                    "cudisc_coag_replay", "cudisc_coag_step_static_scratch",
                    "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp",
-                   "cudisc_coag_mixed_cluster", "cudisc_coag_scratch_bytes", "cudisc_partition", "cudisc_coag_step_async", "cudisc_coag_step_wait",
+                   "cudisc_coag_mixed_cluster", "cudisc_coag_scratch_bytes", "cudisc_partition", "cudisc_dust_init", "cudisc_dust_update_gas",
+                   "cudisc_dust_step", "cudisc_dust_geometry", "cudisc_coag_step_async", "cudisc_coag_step_wait",
                    "cudisc_coag_init_batched", "cudisc_coag_batch_ctx", "cudisc_coag_batch_build_kernel",
                    "cudisc_dust_source_update", "cudisc_dust_cfl_dt", "cudisc_hse_rho_gas", "cudisc_coag_batch_step", "cudisc_coag_step_spans", "cudisc_coag_subcycle",
                    "cudisc_coag_subcycle_pending"):
@@ -248,6 +266,81 @@ def dust_cfl_dt(P, dR, dZ, nu, Sc, C_adv=0.4, C_diff=0.2, out=None):
     _check(lib().cudisc_dust_cfl_dt(n_s, n_c, *(t.data_ptr() for t in ts), float(C_adv), float(C_diff),
                                     out.data_ptr(), torch.cuda.current_stream(P.device).cuda_stream))
     return out
+
+
+GEOM = {"cylindrical": 0, "cartesian": 1}
+BC_OUTFLOW, BC_CLOSED, BC_ZERO = 0, 1, 2
+
+
+class DustTransport:
+    """The dust transport step (Sec. 3.1-3.2) on an (R, theta) grid through
+    cudisc_dust_init / _step.  Fields are torch float64 CUDA tensors: gas
+    rho_g, nu [n_R, n_Z]; Sc [n_species]; sources (c_s [n_R, n_Z], v_g
+    [3, n_R, n_Z], a [n_species], rho_m, GM) or None; Q [4, n_species, n_R,
+    n_Z] (rho, rho v_R, rho v_phi R, rho v_Z)."""
+
+    def __init__(self, R_e, th_e, n_species, rho_g, nu=None, Sc=None, R_c=None, th_c=None,
+                 geometry="cylindrical", bc=(BC_OUTFLOW, BC_OUTFLOW, BC_CLOSED, BC_OUTFLOW), floor=0.0,
+                 sources=None, stream=None):
+        import torch
+        self.torch = torch
+        dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+        self._h = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in
+                   (("R_e", R_e), ("th_e", th_e), ("R_c", R_c), ("th_c", th_c)) if v is not None}
+        self.n_R, self.n_Z, self.n_species = len(R_e) - 1, len(th_e) - 1, int(n_species)
+        self._d = {"rho_g": dev(rho_g)}
+        if nu is not None:
+            self._d["nu"] = dev(nu)
+            self._d["Sc"] = dev(Sc)
+        if sources is not None:
+            for k in ("c_s", "v_g", "a"):
+                self._d[k] = dev(sources[k])
+        p = cudisc_dust_params()
+        p.n_species, p.n_R, p.n_Z = self.n_species, self.n_R, self.n_Z
+        for k in ("R_e", "th_e", "R_c", "th_c"):
+            setattr(p, k, self._h[k].ctypes.data if k in self._h else None)
+        p.geometry = GEOM[geometry]
+        for k in range(4):
+            p.bc[k] = int(bc[k])
+        p.floor = float(floor)
+        for k in ("rho_g", "nu", "Sc", "c_s", "v_g", "a"):
+            setattr(p, k, self._d[k].data_ptr() if k in self._d else None)
+        p.rho_m = float(sources["rho_m"]) if sources is not None else 0.0
+        p.GM = float(sources["GM"]) if sources is not None else 0.0
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        p.stream = self.stream.cuda_stream
+        h = C.c_void_p()
+        _check(lib().cudisc_dust_init(C.byref(p), C.byref(h)))
+        self.ctx = h
+
+    def step(self, Q, dt: float):
+        """One full step of Q (in place; [4, n_species, n_R, n_Z] float64 CUDA)."""
+        assert Q.is_contiguous() and Q.dtype == self.torch.float64
+        assert tuple(Q.shape) == (4, self.n_species, self.n_R, self.n_Z)
+        _check(lib().cudisc_dust_step(self.ctx, Q.data_ptr(), float(dt)))
+        return Q
+
+    def update_gas(self):
+        _check(lib().cudisc_dust_update_gas(self.ctx))
+
+    def geometry(self):
+        t = self.torch
+        V = t.empty((self.n_R, self.n_Z), dtype=t.float64, device="cuda")
+        AR = t.empty((self.n_R + 1, self.n_Z), dtype=t.float64, device="cuda")
+        AZ = t.empty((self.n_R, self.n_Z + 1), dtype=t.float64, device="cuda")
+        _check(lib().cudisc_dust_geometry(self.ctx, V.data_ptr(), AR.data_ptr(), AZ.data_ptr()))
+        return V, AR, AZ
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().cudisc_dust_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cudisc_coag_init_batched(params_list):

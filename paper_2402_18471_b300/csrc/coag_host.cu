@@ -18,6 +18,12 @@ namespace {
 
 thread_local std::string g_thread_err;
 
+} // namespace
+
+void cdc::set_thread_error(const std::string &msg) { g_thread_err = msg; }
+
+namespace {
+
 cudisc_status fail(cudisc_coag_ctx *c, cudisc_status st, const std::string &msg)
 {
     if (c) c->err = msg;

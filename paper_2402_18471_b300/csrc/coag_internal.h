@@ -179,6 +179,9 @@ cudaError_t launch_vjp(cudisc_coag_ctx *c, const double *rho0, const double *hs,
                        double *g_alpha, double *g_vf);
 cudaError_t vjp_worst_status(const cudisc_coag_ctx *c, int *worst);
 void vjp_free(cudisc_coag_ctx *c);
+// the thread's last error message (cudisc_coag_last_error(NULL)), for entry
+// points outside coag_host.cu
+void set_thread_error(const std::string &msg);
 // fixed-scratch variant of the mixed step (see cudisc_coag_step_static_scratch)
 size_t static_scratch_bytes();
 cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_span,
