@@ -342,3 +342,38 @@ def random_state(disc: Disc, seed=0, spread=6.0):
     x = 10.0 ** (-spread * rng.random((disc.n_cells, disc.n_bins)))
     x = x / x.sum(axis=1, keepdims=True)
     return np.ascontiguousarray(0.01 * disc.rho_gas[:, None] * x)
+
+
+def transport_disc(n_R=128, n_Z=64, n_species=100, seed=21, R_in_au=5.0, R_out_au=100.0, th_max=0.25):
+    """Inputs of the dust transport step (Sec. 3.1) on an (R, theta) grid:
+    log-spaced radial edges, polar-angle edges 0..th_max above the mid-plane,
+    a Gaussian gas disc (T-derived c_s, alpha = 1e-3 viscosity), dust species
+    of sizes 1 um - 1 cm at 1 % of the gas with near-Keplerian velocities,
+    Schmidt numbers 1, and the source-update fields (c_s, v_g, a, rho_m, GM).
+    Returns a dict of host arrays; Q is [4, n_species, n_R, n_Z]."""
+    au, G, Ms = CONST["au"], CONST["G"], CONST["M_sun"]
+    rng = np.random.default_rng(seed)
+    R_e = au * np.geomspace(R_in_au, R_out_au, n_R + 1)
+    th_e = np.linspace(0.0, th_max, n_Z + 1)
+    Rc = 0.5 * (R_e[1:] + R_e[:-1])
+    thc = 0.5 * (th_e[1:] + th_e[:-1])
+    Z = Rc[:, None] * np.tan(thc)[None, :]
+    GM = G * Ms
+    cs = 1e5 * (Rc / au / 10.0) ** -0.25
+    Om = np.sqrt(GM / Rc ** 3)
+    H = cs / Om
+    rho_g = 1e-10 * ((Rc / au) ** -2.25)[:, None] * np.exp(-0.5 * (Z / H[:, None]) ** 2)
+    nu = 1e-3 * (cs * H)[:, None] * np.ones((1, n_Z))
+    vK = np.sqrt(GM / Rc)
+    a = np.geomspace(1e-4, 1.0, n_species)
+    P = np.zeros((4, n_species, n_R, n_Z))
+    P[0] = 0.01 / n_species * rho_g[None] * (1 + 0.1 * rng.random((n_species, n_R, n_Z)))
+    P[1] = -30.0 * rng.random((n_species, n_R, n_Z))
+    P[2] = vK[None, :, None] * (1 + 1e-3 * rng.normal(size=(n_species, n_R, n_Z)))
+    P[3] = -Z[None] * Om[None, :, None] * 1e-2 * rng.random((n_species, n_R, n_Z))
+    Q = np.stack([P[0], P[0] * P[1], P[0] * P[2] * Rc[None, :, None], P[0] * P[3]])
+    return dict(R_e=R_e, th_e=th_e, Q=np.ascontiguousarray(Q), rho_g=rho_g, nu=nu, Sc=np.ones(n_species),
+                sources=dict(c_s=np.repeat(cs[:, None], n_Z, 1),
+                             v_g=np.stack([0 * Z, vK[:, None] * np.ones((1, n_Z)), 0 * Z]),
+                             a=a, rho_m=1.6, GM=GM),
+                dt=0.02 / np.sqrt(GM / R_e[0] ** 3))
