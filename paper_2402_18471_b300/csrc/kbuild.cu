@@ -164,31 +164,55 @@ __device__ __forceinline__ float exp_neg_ftz(float x)
 }
 
 // Coagulation probability p_c = 1 - (1 + x) e^-x of Eq. (p_frag), accurate in
-// FP32 also where p_frag rounds to 1: for x < 1 from its Taylor series
-//   1 - (1 + x) e^-x = sum_{n>=2} (-1)^n (n - 1) x^n / n!
-//                    = x^2 sum_{m>=0} (-1)^m (m + 1) x^m / (m + 2)!,
-// 13 terms (truncation < 3e-9 at x = 1), evaluated by Horner; for x >= 1 from
-// the closed form (p_c >= 0.26 there, no cancellation).  Given e = e^-x.
-__device__ __forceinline__ float pcoag_f32(float x, float e)
+// FP32 also where p_frag rounds to 1: for x < 1 as x^2 g(x) with
+//   g(x) = (1 - (1 + x) e^-x) / x^2 = e^-x sum_{m>=0} x^m / (m + 2)!,
+// a smooth function with g(0) = 1/2, approximated on [0, 1] by its degree-6
+// Chebyshev interpolant (interpolation error 6e-9 relative; evaluated by
+// Horner in FP32 it is as accurate as the 13-term Taylor series it replaces,
+// 1.6e-7); for x >= 1 from the closed form (p_c >= 0.26 there, no
+// cancellation).  Given e = e^-x.  The coefficients are computed on the host
+// (pcoag_poly).
+struct PcoagPoly { float c[7]; };   // monomial coefficients, c[0] the constant term
+
+__device__ __forceinline__ float pcoag_f32(float x, float e, const PcoagPoly &P)
 {
     if (x >= 1.0f) return 1.0f - (1.0f + x) * e;
-    constexpr double f2 = 2, f3 = 6, f4 = 24, f5 = 120, f6 = 720, f7 = 5040, f8 = 40320,
-                     f9 = 362880, f10 = 3628800, f11 = 39916800, f12 = 479001600,
-                     f13 = 6227020800.0, f14 = 87178291200.0;
-    float s = (float)(13 / f14);
-    s = s * x + (float)(-12 / f13);
-    s = s * x + (float)(11 / f12);
-    s = s * x + (float)(-10 / f11);
-    s = s * x + (float)(9 / f10);
-    s = s * x + (float)(-8 / f9);
-    s = s * x + (float)(7 / f8);
-    s = s * x + (float)(-6 / f7);
-    s = s * x + (float)(5 / f6);
-    s = s * x + (float)(-4 / f5);
-    s = s * x + (float)(3 / f4);
-    s = s * x + (float)(-2 / f3);
-    s = s * x + (float)(1 / f2);
+    float s = P.c[6];
+#pragma unroll
+    for (int k = 5; k >= 0; k--) s = s * x + P.c[k];
     return x * x * s;
+}
+
+// The degree-6 interpolant of g at the Chebyshev nodes of [0, 1], as monomial
+// coefficients: g at the nodes from its all-positive series in FP64 (exact to
+// rounding for x <= 1), then the Vandermonde system solved by Gaussian
+// elimination with partial pivoting.
+PcoagPoly pcoag_poly()
+{
+    constexpr int n = 7;
+    double A[n][n + 1];
+    for (int k = 0; k < n; k++) {
+        const double x = 0.5 + 0.5 * std::cos((2 * k + 1) * M_PI / (2.0 * n));
+        double s = 0.0, t = 0.5;
+        for (int m = 0; m < 40; m++) { s += t; t *= x / (m + 3); }
+        double p = 1.0;
+        for (int j = 0; j < n; j++) { A[k][j] = p; p *= x; }
+        A[k][n] = std::exp(-x) * s;
+    }
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++)
+            if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+        for (int j = 0; j <= n; j++) std::swap(A[c][j], A[piv][j]);
+        for (int r = 0; r < n; r++) {
+            if (r == c) continue;
+            const double f = A[r][c] / A[c][c];
+            for (int j = c; j <= n; j++) A[r][j] -= f * A[c][j];
+        }
+    }
+    PcoagPoly P;
+    for (int j = 0; j < n; j++) P.c[j] = (float)(A[j][n] / A[j][j]);
+    return P;
 }
 
 // Shared-memory fields of the FP32 builder, each [NR] (NR = N rounded up to
@@ -227,7 +251,7 @@ template <bool Physical, bool HasVdust>
 __global__ void __launch_bounds__(256) kbuild32_kernel(
     float kc, float v_frag, int kernel_mode, int frag_mode, int vertical, int n_cells, int N, int NR,
     int n_slots, const int *__restrict__ blk_i, const int *__restrict__ blk_j0,
-    const float *__restrict__ prep32, const float4 *__restrict__ scal32,
+    const float *__restrict__ prep32, const float4 *__restrict__ scal32, PcoagPoly poly,
     float2 *__restrict__ Kout)
 {
     extern __shared__ __align__(16) float f32s[];       // [kPosTile][cell stride]: [KB_COUNT][NR] each
@@ -273,6 +297,12 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
         const int b = q0 >> 4;
         const int i = __ldg(blk_i + b);
         const int j0 = __ldg(blk_j0 + b) + (q0 & 15);
+        if (j0 > i) {
+            // all four slots lie past the diagonal
+            dst[2 * g] = make_float4(0.f, 0.f, 0.f, 0.f);
+            dst[2 * g + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
         // bin i (the larger Stokes number)
         const float S1 = St[i], Ss = F[P3_SS * NR + i], Ssmd = F[P3_SSMD * NR + i];
         const float omSs = F[P3_OMSS * NR + i], Ui = U[i], ai = Aa[i], ia1 = IA[i], iq1 = IQ[i];
@@ -336,7 +366,7 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
                 const float x = vf2 * (rs * rs);
                 const float e = exp_neg_ftz(x);
                 pf = (x + 1.0f) * e;
-                pc = pcoag_f32(x, e);
+                pc = pcoag_f32(x, e, poly);
             } else {
                 const float *Mm = F + P3_M * NR;
                 if (kernel_mode == CUDISC_KERNEL_CONSTANT) K = kc;
@@ -348,7 +378,7 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
                     const float x = vf2 * (rs * rs);
                     const float e = exp_neg_ftz(x);
                     pf = (x + 1.0f) * e;
-                    pc = pcoag_f32(x, e);
+                    pc = pcoag_f32(x, e, poly);
                 }
             }
             if (vertical) K *= rsqrt_ftz(F[KB_HH * NR + i] + F[KB_HH * NR + j]);
@@ -422,12 +452,12 @@ cudaError_t launch_kbuild(const cudisc_coag_ctx *c)
         const bool vd = p.v_dust != nullptr || p.vertical;
         auto kern = phys ? (vd ? kbuild32_kernel<true, true> : kbuild32_kernel<true, false>)
                          : (vd ? kbuild32_kernel<false, true> : kbuild32_kernel<false, false>);
+        static const PcoagPoly poly = pcoag_poly();
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<(c->n_cells + kPosTile - 1) / kPosTile, 256, smem, c->stream>>>(
             (float)p.kernel_const, (float)p.v_frag, p.kernel_mode, p.frag_mode, p.vertical, c->n_cells, c->N, NR,
-            n_slots, c->d_blk_i, c->d_blk_j0, c->d_prep32, c->d_scal32,
-            c->d_K32);
+            n_slots, c->d_blk_i, c->d_blk_j0, c->d_prep32, c->d_scal32, poly, c->d_K32);
     }
     return cudaGetLastError();
 }
