@@ -451,6 +451,19 @@ cudisc_status cudisc_coag_replay(cudisc_coag_ctx *ctx, double *rho, const double
 cudisc_status cudisc_coag_step_static_scratch(cudisc_coag_ctx *ctx, double *rho, double t_span,
                                               double *dt_cell, cudisc_step_stats *stats);
 
+/* Failure-path test hook of the mixed-precision integration kernel (the
+ * paper has no counterpart).  Every wait of that kernel on another role's
+ * progress is bounded by a clock limit (~2 s); when one runs out the kernel
+ * records the fact in a status word, waits (with its own bound) for the
+ * bulk copies and MMAs it has issued, frees its tensor memory and returns,
+ * and the call reports CUDISC_ECUDA ("a bounded device wait ran out").
+ * wait_cycles > 0 sets that limit in SM clocks for later integrations on
+ * this context (0: the default); withhold = 1 makes the kernel's bulk-copy
+ * producer issue no copies, so that every consumer's wait runs out (needs
+ * wait_cycles > 0).  (0, 0) restores normal operation.  Host only;
+ * CUDISC_EINVAL for other values.  FP64 contexts ignore it. */
+cudisc_status cudisc_coag_set_fault_injection(cudisc_coag_ctx *ctx, long long wait_cycles, int withhold);
+
 /* Bytes of device scratch beyond the context's tables that one integration
  * of the mixed-precision kernel uses for its per-slot state: slot groups x
  * 64 slots x 5 x N x 4 when that state does not fit in shared memory, else

@@ -116,6 +116,7 @@ def lib():
         L.cudisc_coag_get_timings.argtypes = [v, C.POINTER(cudisc_timings)]
         L.cudisc_coag_mixed_cluster.argtypes = [v, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.cudisc_coag_scratch_bytes.argtypes = [v, C.POINTER(C.c_size_t)]
+        L.cudisc_coag_set_fault_injection.argtypes = [v, C.c_longlong, C.c_int]
         L.cudisc_partition.argtypes = [C.c_int, v, C.c_int, v]
         L.cudisc_dust_init.argtypes = [C.POINTER(cudisc_dust_params), C.POINTER(v)]
         L.cudisc_dust_update_gas.argtypes = [v]
@@ -134,7 +135,7 @@ def lib():
                    "cudisc_coag_rhs", "cudisc_coag_step", "cudisc_coag_set_records",
                    "cudisc_coag_replay", "cudisc_coag_step_static_scratch",
                    "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp",
-                   "cudisc_coag_mixed_cluster", "cudisc_coag_scratch_bytes", "cudisc_partition", "cudisc_dust_init", "cudisc_dust_update_gas",
+                   "cudisc_coag_mixed_cluster", "cudisc_coag_scratch_bytes", "cudisc_coag_set_fault_injection", "cudisc_partition", "cudisc_dust_init", "cudisc_dust_update_gas",
                    "cudisc_dust_step", "cudisc_dust_geometry", "cudisc_coag_step_async", "cudisc_coag_step_wait",
                    "cudisc_coag_init_batched", "cudisc_coag_batch_ctx", "cudisc_coag_batch_build_kernel",
                    "cudisc_dust_source_update", "cudisc_dust_cfl_dt", "cudisc_hse_rho_gas", "cudisc_coag_batch_step", "cudisc_coag_step_spans", "cudisc_coag_subcycle",
@@ -414,6 +415,10 @@ def cudisc_coag_mixed_cluster(ctx) -> tuple:
     cl, gr = C.c_int(), C.c_int()
     _check(lib().cudisc_coag_mixed_cluster(ctx, C.byref(cl), C.byref(gr)), ctx)
     return cl.value, gr.value
+
+
+def cudisc_coag_set_fault_injection(ctx, wait_cycles: int, withhold: int):
+    _check(lib().cudisc_coag_set_fault_injection(ctx, int(wait_cycles), int(withhold)), ctx)
 
 
 def cudisc_coag_scratch_bytes(ctx) -> int:

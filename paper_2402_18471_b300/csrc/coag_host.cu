@@ -791,6 +791,18 @@ cudisc_status cudisc_coag_step_static_scratch(cudisc_coag_ctx *c, double *rho, d
     return finish_step(c, stats);
 }
 
+cudisc_status cudisc_coag_set_fault_injection(cudisc_coag_ctx *c, long long wait_cycles, int withhold)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (wait_cycles < 0 || (withhold != 0 && withhold != 1))
+        return fail(c, CUDISC_EINVAL, "wait_cycles must be >= 0 and withhold 0 or 1");
+    if (withhold && wait_cycles == 0)
+        return fail(c, CUDISC_EINVAL, "withhold needs a short wait_cycles (the default limit is ~2 s)");
+    c->inject_wait_cycles = wait_cycles;
+    c->inject_withhold = withhold;
+    return CUDISC_OK;
+}
+
 cudisc_status cudisc_coag_scratch_bytes(const cudisc_coag_ctx *c, size_t *bytes)
 {
     if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");

@@ -114,6 +114,8 @@ struct cudisc_coag_ctx {
     int mix_P = 1, mix_G = 1, mix_C = 1;   // mixed kernel: CTAs per slot group, groups, initial cells per group
     bool timed = false;                // the last integration issued recorded ev0/ev1
     void *static_scratch = nullptr;    // device address of the fixed scratch array (first static call)
+    long long inject_wait_cycles = 0;  // test hook: wait limit of the mixed kernel (0: the default)
+    int inject_withhold = 0;           // test hook: the mixed kernel's producer issues no copies
     // integration workspace
     cdc::CellOut *d_out = nullptr;     // [n_cells]
     double *d_work = nullptr;          // mixed path slot state

@@ -227,18 +227,21 @@ enum { KB_INVA = P3_HH, KB_INVQ, KB_HH, KB_COUNT };
 // (p_c = 1 - p_f, each accurate to a few ulp of itself, so that neither
 // coagulation in a fragmentation-dominated cell nor fragmentation in a
 // coagulation-dominated one is lost to rounding); slots past the diagonal
-// hold zeros.  One CTA per kPosTile consecutive cells, one warp per cell:
-// the cells' per-bin fields are staged in shared memory once; each thread
-// then produces four consecutive slots of a block (same i, j .. j+3) and
-// writes them as two 16-byte chunks, a warp 1 KB of its cell's table per
-// store pair.  The
+// hold zeros.  One CTA per kPosTile consecutive cells, kWarpsPerCell warps
+// per cell, each taking a contiguous quarter of the cell's 4-slot groups
+// (so that the grid is ~7 waves of the four CTAs an SM holds, not 1.7: the
+// last, partial wave then costs ~1 % instead of ~15 %): the cells' per-bin
+// fields are staged in shared memory once; each thread then produces four
+// consecutive slots of a block (same i, j .. j+3) and writes them as two
+// 16-byte chunks, a warp 1 KB of its cell's table per store pair.  The
 // larger Stokes number of a pair (i, j <= i) is always St_i: St = rho_m a
 // Omega / (rho_g v_th) rises with the bin's size.  Divisions, the square
 // root and the exponential use the hardware approximations: K stays within
 // 1e-6 and K p_frag within 1e-5 of FP64.
 //   Physical = physical kernel and fragmentation probability (the other
 //   modes are the closed-form test kernels); HasVdust = input velocities.
-constexpr int kPosTile = 8;                 // cells per CTA (one per warp of 256 threads)
+constexpr int kWarpsPerCell = 4;            // warps sharing one cell's table
+constexpr int kPosTile = 8 / kWarpsPerCell; // cells per CTA of 256 threads
 
 // words of shared memory per cell: the fields above (without KB_HH unless
 // vertical) of NR each, rounded to 16 bytes
@@ -282,7 +285,8 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
         F[KB_INVQ * NR + k] = 1.0f / (1.0f + S);
     }
     __syncthreads();
-    const int jc = threadIdx.x >> 5;                      // this warp's cell of the tile
+    const int jc = (threadIdx.x >> 5) / kWarpsPerCell;    // this warp's cell of the tile
+    const int part = (threadIdx.x >> 5) % kWarpsPerCell;  // and its share of the cell's groups
     const int c = s_cell[jc];
     if (c < 0) return;
     const float *F = f32s + jc * CS;
@@ -292,7 +296,9 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
     const float *St = F + P3_ST * NR, *U = F + P3_U * NR, *Aa = F + P3_A * NR;
     const float *IA = F + KB_INVA * NR, *IQ = F + KB_INVQ * NR;
     float4 *dst = reinterpret_cast<float4 *>(Kout) + (size_t)c * (n_slots / 2);   // the cell's 2-pair chunks
-    for (int g = threadIdx.x & 31; 4 * g < n_slots; g += 32) {
+    const int n_grp = n_slots / 4;
+    const int g_end = (int)((long long)(part + 1) * n_grp / kWarpsPerCell);
+    for (int g = (int)((long long)part * n_grp / kWarpsPerCell) + (threadIdx.x & 31); g < g_end; g += 32) {
         const int q0 = 4 * g;
         const int b = q0 >> 4;
         const int i = __ldg(blk_i + b);

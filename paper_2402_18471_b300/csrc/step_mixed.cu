@@ -65,6 +65,7 @@ constexpr int kKBlkBytes = 16 * 8 * 64;           // K tables of one block for 6
 constexpr int kThreads = 64 + 32 * kGenWarps;
 constexpr int kLaneBins = (kMaxMixedBins + 31) / 32;   // bins per lane in the per-slot logic
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+constexpr long long kDrainCycles = 4000000000LL;  // ~2 s: drains of issued copies and MMAs
 constexpr double A21 = 0.5, A32 = 0.75;
 constexpr double B1 = 2.0 / 9.0, B2 = 1.0 / 3.0, B3 = 4.0 / 9.0;
 constexpr double E1 = -5.0 / 72.0, E2 = 1.0 / 12.0, E3 = 1.0 / 9.0, E4 = -1.0 / 8.0;
@@ -103,6 +104,8 @@ struct MixedArgs {
     int P;                      // CTAs per group of slots (a cluster of 1, 2, 4 or 8; see the kernel)
     int nacc;                   // TMEM accumulators for the products with Bt_hi (stacked: with [Bt_hi; Bt_lo])
     int stacked;                // 1: one MMA of N = 2 NBP takes Bt_hi and Bt_lo together (2 NBP <= 256)
+    long long wait_cycles;      // clock limit of the bounded waits (kWaitCycles; shorter only in tests)
+    int withhold;               // test hook: 1 = the producer issues no copies, so the waits run out
 };
 
 struct __align__(16) Slot {
@@ -135,6 +138,10 @@ __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity)
                  : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
     return ok != 0;
 }
+// The clock limit of every bounded wait of this CTA (kWaitCycles unless a
+// test shortened it through the arguments), set before the first wait.
+__shared__ long long s_wait_lim;
+
 // Bounded wait: false when the clock limit runs out or another role failed.
 // Waiting threads back off a little between tests, leaving issue slots to
 // the warps that work (the MMA issuer shares a scheduler with generators).
@@ -146,8 +153,20 @@ __device__ __noinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile in
         if (it >= 2) __nanosleep(32);
         if ((it & 63) == 63) {
             if (*s_err) return false;
-            if (clock64() - t0 > kWaitCycles) { atomicCAS((int *)s_err, 0, code); return false; }
+            if (clock64() - t0 > s_wait_lim) { atomicCAS((int *)s_err, 0, code); return false; }
         }
+    }
+}
+// Wait for asynchronous work this thread issued (bulk copies, MMAs) before
+// the CTA frees what that work writes: unlike mbar_wait it does not give up
+// when another role has failed, only after its own limit (kDrainCycles).
+__device__ __noinline__ void mbar_drain(uint64_t *b, uint32_t parity)
+{
+    const long long t0 = clock64();
+    for (int it = 0;; ++it) {
+        if (mbar_test(b, parity)) return;
+        __nanosleep(64);
+        if ((it & 63) == 63 && clock64() - t0 > kDrainCycles) return;
     }
 }
 // ---- cluster (CTA pair) helpers ----
@@ -197,7 +216,7 @@ __device__ __noinline__ bool cwait(uint64_t *b, uint32_t parity, volatile int *s
         if (it >= 2) __nanosleep(32);
         if ((it & 63) == 63) {
             if (*s_err) return false;
-            if (clock64() - t0 > kWaitCycles) { atomicCAS((int *)s_err, 0, code); return false; }
+            if (clock64() - t0 > s_wait_lim) { atomicCAS((int *)s_err, 0, code); return false; }
         }
     }
 }
@@ -917,6 +936,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         for (int s = 0; s < kGenWarps / 2; s++) mbar_init(&pair_full[s], 1);
         s_err = 0;
         s_continue = 1;
+        s_wait_lim = a.wait_cycles;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -955,7 +975,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             int ps = 0, ks = 0;
             uint32_t pu = 0, ku = 0;
             const float4 *kgrp = a.Kslot + (size_t)grp * n_blk * 8 * kSlots;   // this group's tables
-            bool ok = true;
+            bool ok = a.withhold == 0;
             for (int r = 0; ok; r++) {
                 if (r > 0) {
                     if (!twait(go, (r - 1) & 1, &s_err, ERR_WAIT_PRODUCER)) break;
@@ -999,7 +1019,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                         __nanosleep(32);
                         if ((it & 63) == 63) {
                             if (*(volatile int *)&s_err) { ok = false; break; }
-                            if (clock64() - t_last > kWaitCycles) {
+                            if (clock64() - t_last > s_wait_lim) {
                                 atomicCAS(&s_err, 0, ERR_WAIT_PRODUCER);
                                 ok = false;
                                 break;
@@ -1008,6 +1028,13 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     }
                 }
             }
+            // every copy issued has landed before the CTA can leave: wait for
+            // the last issued round of each ring stage (the rings only advance
+            // on this thread's issues, so its parity is unambiguous)
+            for (int q = 0; q < SB; q++)
+                if (g > q) mbar_drain(&bt_full[q], (uint32_t)(((g - 1 - q) / SB) & 1));
+            for (int q = 0; q < KS; q++)
+                if (gk > q) mbar_drain(&k_full[q], (uint32_t)(((gk - 1 - q) / KS) & 1));
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -1258,7 +1285,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     if (warp == 1 && lane == 0) {
         // every MMA this thread issued has completed before TMEM is freed
         mma_commit(fin);
-        mbar_wait(fin, 0, &s_err, ERR_WAIT_MMA);
+        mbar_drain(fin, 0);
     }
     tc_fence_before();
     __syncthreads();
@@ -1478,6 +1505,8 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.KS = cf.KS;
     a.sst_off = cf.sst_off;
     a.P = cf.P;
+    a.wait_cycles = c->inject_wait_cycles > 0 ? c->inject_wait_cycles : kWaitCycles;
+    a.withhold = c->inject_withhold;
     a.wl = wl;
     a.mode = mode;
     return launch_kernel(cf, a, c->stream);
@@ -1564,6 +1593,8 @@ cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_s
     a.KS = cf.KS;
     a.sst_off = cf.sst_off;
     a.P = cf.P;
+    a.wait_cycles = c->inject_wait_cycles > 0 ? c->inject_wait_cycles : kWaitCycles;
+    a.withhold = c->inject_withhold;
     a.wl = WorkList();
     a.mode = MODE_STEP;
     return launch_kernel(cf, a, c->stream);

@@ -107,6 +107,47 @@ def test_null_context_is_an_error_not_a_crash():
     assert L.cudisc_coag_batch_step(None, None, 1.0, None, None, None) == coag.EINVAL
     L.cudisc_coag_batch_destroy(None)
     L.cudisc_coag_destroy(None)
+    assert L.cudisc_coag_build_kernel_async(None) == coag.EINVAL
+    assert L.cudisc_coag_set_fault_injection(None, 0, 0) == coag.EINVAL
+    n = C.c_size_t()
+    assert L.cudisc_coag_scratch_bytes(None, C.byref(n)) == coag.EINVAL
+    assert L.cudisc_dust_step(None, None, 1.0) == coag.EINVAL
+    assert L.cudisc_dust_update_gas(None) == coag.EINVAL
+    assert L.cudisc_dust_geometry(None, None, None, None) == coag.EINVAL
+    L.cudisc_dust_destroy(None)
+
+
+def test_transport_init_rejects_bad_arguments_before_any_allocation():
+    L = coag.lib()
+    Re = np.array([1.0, 2.0, 3.0])
+    te = np.array([0.0, 0.1, 0.2])
+    f = C.c_void_p(16)     # never dereferenced: validation fails first
+
+    def params(**kw):
+        p = coag.cudisc_dust_params()
+        p.n_species, p.n_R, p.n_Z = 2, 2, 2
+        p.R_e, p.th_e = Re.ctypes.data, te.ctypes.data
+        p.rho_g = f.value
+        for k, v in kw.items():
+            if k == "bc":
+                for i in range(4):
+                    p.bc[i] = v[i]
+            else:
+                setattr(p, k, v)
+        return p
+
+    h = C.c_void_p()
+    for kw, word in [(dict(n_species=0), b"n_species"), (dict(rho_g=None), b"rho_g"),
+                     (dict(nu=f.value), b"Sc"), (dict(geometry=7), b"geometry"),
+                     (dict(bc=(0, 0, 5, 0)), b"bc"), (dict(c_s=f.value), b"sources")]:
+        p = params(**kw)
+        assert L.cudisc_dust_init(C.byref(p), C.byref(h)) == coag.EINVAL and h.value is None
+        assert word in L.cudisc_coag_last_error(None)
+    bad = np.array([1.0, 0.5, 3.0])
+    p = params()
+    p.R_e = bad.ctypes.data
+    assert L.cudisc_dust_init(C.byref(p), C.byref(h)) == coag.EINVAL
+    assert b"R_e" in L.cudisc_coag_last_error(None)
 
 
 def test_hse_rejects_bad_arguments_before_any_launch():
