@@ -143,6 +143,15 @@ typedef struct {
                                     sqrt(2 pi (h_i^2 + h_j^2)).  The adjoint
                                     (cudisc_coag_vjp) differentiates h, the
                                     settling and that factor too. */
+    int mixed_pair;              /* CUDISC_MIXED_TF32 only: 2 = CTA pairs share
+                                    each M = 256 tensor-core MMA (tcgen05
+                                    cta_group::2): a cluster of 2 x
+                                    mixed_cluster CTAs serves two groups of 64
+                                    slots, each CTA keeping half of every
+                                    mapping tile (bins up to 128; else, or if it
+                                    does not fit, single CTAs); 1 = single CTAs;
+                                    0 = chosen at init (see
+                                    cudisc_coag_mixed_pair). */
 } cudisc_coag_params;
 
 typedef struct {
@@ -489,6 +498,11 @@ cudisc_status cudisc_coag_get_timings(const cudisc_coag_ctx *ctx, cudisc_timings
  * of a group's pass is split between them), *groups = groups resident at
  * once.  Both 0 for an FP64 context.  EINVAL for a NULL argument.  Host only. */
 cudisc_status cudisc_coag_mixed_cluster(const cudisc_coag_ctx *ctx, int *cluster, int *groups);
+
+/* *pair = 1 when the mixed-precision kernel of this context runs in CTA
+ * pairs (see mixed_pair), else 0 (also for an FP64 context).  EINVAL for a
+ * NULL argument.  Host only. */
+cudisc_status cudisc_coag_mixed_pair(const cudisc_coag_ctx *ctx, int *pair);
 
 /* Vector-Jacobian product of the integration (the paper has no adjoint; this
  * is the discrete adjoint of the BS3 map of Sec. 5 with the step sizes held

@@ -43,7 +43,7 @@ class cudisc_coag_params(C.Structure):
         ("stream", C.c_void_p),
         ("mixed_cluster", C.c_int),
         ("max_sms", C.c_int),
-        ("vertical", C.c_int),
+        ("vertical", C.c_int), ("mixed_pair", C.c_int),
     ]
 
 
@@ -116,6 +116,7 @@ def lib():
         L.cudisc_coag_get_timings.argtypes = [v, C.POINTER(cudisc_timings)]
         L.cudisc_coag_mixed_cluster.argtypes = [v, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.cudisc_coag_scratch_bytes.argtypes = [v, C.POINTER(C.c_size_t)]
+        L.cudisc_coag_mixed_pair.argtypes = [v, C.POINTER(C.c_int)]
         L.cudisc_coag_set_fault_injection.argtypes = [v, C.c_longlong, C.c_int]
         L.cudisc_partition.argtypes = [C.c_int, v, C.c_int, v]
         L.cudisc_dust_init.argtypes = [C.POINTER(cudisc_dust_params), C.POINTER(v)]
@@ -135,7 +136,7 @@ def lib():
                    "cudisc_coag_rhs", "cudisc_coag_step", "cudisc_coag_set_records",
                    "cudisc_coag_replay", "cudisc_coag_step_static_scratch",
                    "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp",
-                   "cudisc_coag_mixed_cluster", "cudisc_coag_scratch_bytes", "cudisc_coag_set_fault_injection", "cudisc_partition", "cudisc_dust_init", "cudisc_dust_update_gas",
+                   "cudisc_coag_mixed_cluster", "cudisc_coag_scratch_bytes", "cudisc_coag_mixed_pair", "cudisc_coag_set_fault_injection", "cudisc_partition", "cudisc_dust_init", "cudisc_dust_update_gas",
                    "cudisc_dust_step", "cudisc_dust_geometry", "cudisc_coag_step_async", "cudisc_coag_step_wait",
                    "cudisc_coag_init_batched", "cudisc_coag_batch_ctx", "cudisc_coag_batch_build_kernel",
                    "cudisc_dust_source_update", "cudisc_dust_cfl_dt", "cudisc_hse_rho_gas", "cudisc_coag_batch_step", "cudisc_coag_step_spans", "cudisc_coag_subcycle",
@@ -499,6 +500,7 @@ class Coag:
         p.mixed_cluster = int(s.get("mixed_cluster", 0))
         p.max_sms = int(s.get("max_sms", 0))
         p.vertical = int(s.get("vertical", 0))
+        p.mixed_pair = int(s.get("mixed_pair", 0))
         self.params = p
 
     def close(self):
@@ -528,6 +530,12 @@ class Coag:
 
     def timings(self) -> dict:
         return cudisc_coag_get_timings(self.ctx)
+
+    def mixed_pair(self) -> int:
+        """1 when the mixed kernel runs in CTA pairs sharing M = 256 MMAs."""
+        v = C.c_int()
+        _check(lib().cudisc_coag_mixed_pair(self.ctx, C.byref(v)), self.ctx)
+        return v.value
 
     def mixed_cluster(self) -> tuple:
         """(CTAs per group of 64 slots, groups) of the mixed kernel."""

@@ -237,6 +237,10 @@ static cudisc_status validate(const cudisc_coag_params *p, std::string &why)
     if (p->split_mode < 0 || p->split_mode > 1) { why = "split_mode out of range"; return CUDISC_EINVAL; }
     if (!(p->rtol > 0.0) || !(p->atol_rel >= 0.0)) { why = "rtol must be > 0 and atol_rel >= 0"; return CUDISC_EINVAL; }
     if (p->max_substeps < 1) { why = "max_substeps must be >= 1"; return CUDISC_EINVAL; }
+    if (p->mixed_pair < 0 || p->mixed_pair > 2) {
+        why = "mixed_pair must be 0 (automatic), 1 (single CTAs) or 2 (CTA pairs)";
+        return CUDISC_EINVAL;
+    }
     if (p->mixed_cluster != 0 && p->mixed_cluster != 1 && p->mixed_cluster != 2 && p->mixed_cluster != 4 &&
         p->mixed_cluster != 8) {
         why = "mixed_cluster must be 0 (automatic), 1, 2, 4 or 8";
@@ -470,8 +474,8 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
             e = cudaMalloc(&c->d_K64, nc * (size_t)c->Np * sizeof(double2));
         else
         {
-            cdc::mixed_layout(c->n_cells, c->N, params->mixed_cluster, params->max_sms, &c->mix_P, &c->mix_G,
-                              &c->mix_C);
+            cdc::mixed_layout(c->n_cells, c->N, params->mixed_cluster, params->max_sms, params->mixed_pair,
+                              &c->mix_P, &c->mix_G, &c->mix_C, &c->mix_pair);
             e = cudaMalloc(&c->d_K32, (size_t)c->n_cells * c->n_blk * cdc::kBlkPairs * sizeof(float2));
             // the slot groups' tables: [group][block][8 chunks][64 slots] x 16 B
             // (zeroed: slots that never hold a cell multiply zero stage inputs by it)
@@ -481,7 +485,7 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
         }
     }
     if (e == cudaSuccess && params->precision == CUDISC_MIXED_TF32) {
-        c->work_bytes = cdc::mixed_workspace_bytes(c->n_cells, c->N, c->mix_P, params->max_sms);
+        c->work_bytes = cdc::mixed_workspace_bytes(c->n_cells, c->N, c->mix_P, params->max_sms, c->mix_pair);
         e = cudaMalloc(&c->d_work, c->work_bytes);
     }
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
@@ -520,6 +524,14 @@ cudisc_status cudisc_coag_mixed_cluster(const cudisc_coag_ctx *c, int *cluster, 
     const bool mixed = c->p.precision == CUDISC_MIXED_TF32;
     *cluster = mixed ? c->mix_P : 0;
     *groups = mixed ? c->mix_G : 0;
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_coag_mixed_pair(const cudisc_coag_ctx *c, int *pair)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!pair) return CUDISC_EINVAL;
+    *pair = c->p.precision == CUDISC_MIXED_TF32 ? c->mix_pair : 0;
     return CUDISC_OK;
 }
 
@@ -807,7 +819,7 @@ cudisc_status cudisc_coag_scratch_bytes(const cudisc_coag_ctx *c, size_t *bytes)
 {
     if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
     if (!bytes) return CUDISC_EINVAL;
-    *bytes = c->p.precision == CUDISC_MIXED_TF32 ? cdc::mixed_scratch_bytes(c->n_cells, c->N, c->mix_P, c->p.max_sms)
+    *bytes = c->p.precision == CUDISC_MIXED_TF32 ? cdc::mixed_scratch_bytes(c->n_cells, c->N, c->mix_P, c->p.max_sms, c->mix_pair)
                                                  : 0;
     return CUDISC_OK;
 }

@@ -112,6 +112,7 @@ struct cudisc_coag_ctx {
     float2 *d_K32 = nullptr;           // n_cells x n_blk x 16 {K p_coag, K p_frag}, see k32_index
     float4 *d_Kslot = nullptr;         // mixed kernel: [group][block][8 chunks][64 slots] of the slots' tables
     int mix_P = 1, mix_G = 1, mix_C = 1;   // mixed kernel: CTAs per slot group, groups, initial cells per group
+    int mix_pair = 0;                  // mixed kernel: CTA pairs share M = 256 MMAs
     bool timed = false;                // the last integration issued recorded ev0/ev1
     void *static_scratch = nullptr;    // device address of the fixed scratch array (first static call)
     long long inject_wait_cycles = 0;  // test hook: wait limit of the mixed kernel (0: the default)
@@ -156,10 +157,11 @@ cudaError_t launch_rhs_mixed(const cudisc_coag_ctx *c, const double *rho, double
 cudaError_t launch_step_mixed(const cudisc_coag_ctx *c, double *rho, double t_span,
                               double *dt_cell, const double *replay_h,
                               const long long *replay_n, long long replay_stride, WorkList wl = WorkList());
-size_t mixed_workspace_bytes(int n_cells, int N, int P, int max_sms);
-// cluster size P for a request P_req (0: automatic), groups of slots G and
-// initial cells per group C of the mixed kernel
-void mixed_layout(int n_cells, int N, int P_req, int max_sms, int *P, int *G, int *C);
+size_t mixed_workspace_bytes(int n_cells, int N, int P, int max_sms, int pair);
+// CTAs per slot group P for a request P_req (0: automatic), groups of slots G,
+// initial cells per group C and CTA-pair mode (pair_req: 0 automatic, 1 off,
+// 2 on) of the mixed kernel
+void mixed_layout(int n_cells, int N, int P_req, int max_sms, int pair_req, int *P, int *G, int *C, int *pair);
 // hydrostatic-equilibrium gas density (hse.cu)
 cudaError_t launch_hse(int n_R, int n_Z, const double *R, const double *Z, const double *T, const double *V,
                        const double *R_edges, const double *Sigma_g, double mu, double m_H, double k_B,
@@ -190,5 +192,5 @@ cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_s
                                      double *dt_cell, bool *too_big);
 // bytes of global scratch the mixed integration's per-slot state takes (0:
 // it is kept in shared memory)
-size_t mixed_scratch_bytes(int n_cells, int N, int P, int max_sms);
+size_t mixed_scratch_bytes(int n_cells, int N, int P, int max_sms, int pair);
 } // namespace cdc

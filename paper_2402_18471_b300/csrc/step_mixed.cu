@@ -59,7 +59,7 @@ constexpr int kGC = kGP / 2;                      // its 2-pair chunks of the K 
 constexpr int kSlots = 64;                        // cell slots per CTA (TMEM rows / 2)
 constexpr int kAStages = 3;                       // generated-operand stages in TMEM (two blocks, 64 columns each)
 constexpr int kMaxMain = 8;                       // TMEM accumulators for the products with Bt_hi
-constexpr int kMaxSB = 4;                         // mapping-tile ring depth (stages of two blocks), at most
+constexpr int kMaxSB = 8;                         // mapping-tile ring depth (stages of two blocks), at most
 constexpr int kMaxKS = 4;                         // K-table ring depth (stages of two blocks), at most
 constexpr int kKBlkBytes = 16 * 8 * 64;           // K tables of one block for 64 slots: 8 chunks x 64 x 16 B
 constexpr int kThreads = 64 + 32 * kGenWarps;
@@ -104,6 +104,7 @@ struct MixedArgs {
     int P;                      // CTAs per group of slots (a cluster of 1, 2, 4 or 8; see the kernel)
     int nacc;                   // TMEM accumulators for the products with Bt_hi (stacked: with [Bt_hi; Bt_lo])
     int stacked;                // 1: one MMA of N = 2 NBP takes Bt_hi and Bt_lo together (2 NBP <= 256)
+    int pair;                   // 1: CTA pairs share M = 256 MMAs (two groups of slots per pair, see the kernel)
     long long wait_cycles;      // clock limit of the bounded waits (kWaitCycles; shorter only in tests)
     int withhold;               // test hook: 1 = the producer issues no copies, so the waits run out
 };
@@ -220,6 +221,20 @@ __device__ __noinline__ bool cwait(uint64_t *b, uint32_t parity, volatile int *s
         }
     }
 }
+// Single-thread bounded wait for an mbarrier that other CTAs of the cluster
+// arrive on (acquire at cluster scope).
+__device__ __noinline__ bool twait_cluster(uint64_t *b, uint32_t parity, volatile int *s_err, int code)
+{
+    const long long t0 = clock64();
+    for (int it = 0;; ++it) {
+        if (mbar_test_cluster(b, parity)) return true;
+        if (it >= 2) __nanosleep(32);
+        if ((it & 63) == 63) {
+            if (*s_err) return false;
+            if (clock64() - t0 > s_wait_lim) { atomicCAS((int *)s_err, 0, code); return false; }
+        }
+    }
+}
 __device__ __forceinline__ void cluster_sync_all()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -276,6 +291,16 @@ __device__ __forceinline__ void mma_tf32_ts_acc(uint32_t dt, uint32_t at, uint64
     asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;"
                  ::"r"(dt), "r"(at), "l"(b), "r"(idesc) : "memory");
 }
+// The same for a CTA pair (cta_group::2, issued by the even CTA): M = 256
+// rows, rows 0..127 from this CTA's tensor memory and 128..255 from the odd
+// CTA's at the same address; B's N rows split in two halves at the same
+// shared-memory address of the two CTAs; D in each CTA's own tensor memory.
+__device__ __forceinline__ void mma2_tf32_ts(uint32_t dt, uint32_t at, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::2.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+                 ::"r"(dt), "r"(at), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
 // Store 8 consecutive 32-bit columns of this thread's TMEM lane.
 __device__ __forceinline__ __attribute__((unused)) void tmem_st8(uint32_t taddr, const float (&v)[8])
 {
@@ -309,6 +334,13 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                  ::"r"(su32(bar)) : "memory");
+}
+// Completion of this pair's MMAs, signalled on the mbarrier at the same
+// shared-memory offset in both CTAs of the pair (mask: their cluster ranks).
+__device__ __forceinline__ void mma_commit2(uint64_t *bar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(su32(bar)), "h"(mask) : "memory");
 }
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 {
@@ -361,6 +393,16 @@ __device__ __forceinline__ uint8_t *smem_base()
     return (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
 }
 
+// The slot group this CTA serves.  Groups of P CTAs (a cluster of P); in
+// pair mode a cluster of P pairs serves two groups, the even CTAs of the
+// pairs group 2 x + 0 and the odd ones group 2 x + 1 (cluster ranks follow
+// blockIdx.x in a one-dimensional cluster).
+__device__ __forceinline__ int group_of_block(const MixedArgs &a)
+{
+    if (!a.pair) return (int)blockIdx.x / a.P;
+    return ((int)blockIdx.x / (2 * a.P)) * 2 + ((int)blockIdx.x & 1);
+}
+
 // Slot state (5 N floats per slot kept by this CTA), in shared memory when
 // it fits beside the rings, else in global scratch: the state y / Sx as an unevaluated float pair yh + yl (48 significant
 // bits; yh, the state rounded to FP32, is also the stage input), and the stage
@@ -383,8 +425,7 @@ __device__ __forceinline__ SlotBufs slot_bufs(const MixedArgs &a, int slot)
         const int SL = a.NS / a.P;
         f = (float *)(smem_base() + a.sst_off) + (size_t)(slot % SL) * 5 * N;
     } else {
-        const int grp = (int)blockIdx.x / a.P;
-        f = a.work + ((size_t)grp * a.NS + slot) * 5 * (size_t)N;
+        f = a.work + ((size_t)group_of_block(a) * a.NS + slot) * 5 * (size_t)N;
     }
     return {f, f + N, f + 2 * N, f + 3 * N, f + 4 * N};
 }
@@ -413,7 +454,7 @@ __device__ void slot_copy_k(const MixedArgs &a, int slot, int c)
     const int lane = threadIdx.x & 31;
     const int n_ch = a.t.n_blk * 8;                  // 2-pair chunks of a table
     const float4 *src = a.K32 + (size_t)c * n_ch;
-    float4 *dst = a.Kslot + (size_t)(blockIdx.x / a.P) * n_ch * kSlots + slot;
+    float4 *dst = a.Kslot + (size_t)group_of_block(a) * n_ch * kSlots + slot;
     // sixteen loads in flight per lane, then their stores
     int i0 = lane;
     for (; i0 + 15 * 32 < n_ch; i0 += 16 * 32) {
@@ -860,20 +901,32 @@ __device__ __forceinline__ bool gen_pass(GenCtx &G, long long g0, int st_lo, int
 // exchanges; larger P shortens a pass, which bounds the time of the costliest
 // cells once there are fewer cells than slots to keep busy.
 
+template <bool Pair>
 __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
 {
     uint8_t *sm = smem_base();
     const int NS = a.NS, XS = a.XS, N = a.t.N, n_blk = a.t.n_blk, NBP = a.NBP;
     const int SB = a.SB;
-    const int P = a.P;                                  // CTAs per group (cluster size)
-    const bool clustered = P > 1;
-    const int rank = clustered ? (int)cluster_rank() : 0;
-    const int ngrp = (int)gridDim.x / P;
-    const int grp = (int)blockIdx.x / P;
+    const int P = a.P;                                  // CTAs per group (its members)
+    constexpr bool pairm = Pair;                        // CTA pairs share M = 256 MMAs
+    const int Q = pairm ? 2 * P : P;                    // cluster size
+    const bool clustered = Q > 1;                       // cluster-wide barriers needed
+    const bool xchg = P > 1;                            // partial sums and stage inputs exchanged
+    const int crank = clustered ? (int)cluster_rank() : 0;
+    const int half = pairm ? (crank & 1) : 0;           // pair mode: 0 = even CTA (issues the MMAs), 1 = odd
+    const int rank = pairm ? (crank >> 1) : crank;      // this CTA's member index in its group
+    const bool leader = half == 0;
+    // cluster rank of member o of this CTA's group
+    auto member = [&](int o) { return (uint32_t)(pairm ? 2 * o + half : o); };
+    const uint16_t pair_mask = (uint16_t)(3u << (crank & ~1));
+    const int ngrp = pairm ? ((int)gridDim.x / Q) * 2 : (int)gridDim.x / P;
+    const int grp = group_of_block(a);
     const int SL = NS / P;                              // slots whose state this CTA keeps
     const int own0 = rank * SL;
     const int half_bytes = NBP * 128;                   // rows of one Bt tile copied
-    const int bstride = ((2 * half_bytes + 1023) / 1024) * 1024;   // hi then lo, 1024-aligned
+    // one block of tiles: hi then lo (pair mode: this CTA's half, hi rows in
+    // the even CTA and lo rows in the odd one), 1024-aligned
+    const int bstride = (((pairm ? 1 : 2) * half_bytes + 1023) / 1024) * 1024;
     const int sstride = 2 * bstride;                    // one stage: two blocks
     const int n_st = (n_blk + 1) / 2;                   // stages per pass
     const int st_lo = (int)((long long)rank * n_st / P);
@@ -895,8 +948,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     uint64_t *dx_full = done + 4, *xg_full = done + 5;
     uint64_t *k_full = done + 6, *k_empty = done + 6 + KS;
     uint64_t *pair_full = k_empty + KS;                 // [kGenWarps / 2]: a lo-row warp's sums are in Dlo
+    uint64_t *pr_full = pair_full + kGenWarps / 2;      // [kAStages] pair mode, even CTA: the odd one's stage is ready
+    uint64_t *cx_full = pr_full + kAStages;             // pair mode: the partner's continue flag arrived
     __shared__ uint32_t s_tmem;
-    __shared__ int s_err, s_continue;
+    __shared__ int s_err, s_continue, s_any_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // TMEM columns: kAStages x 64 for the generated operand, then nacc
     // accumulators for [A_hi; A_lo] x Bt_hi (each a contiguous share of this
@@ -927,22 +982,31 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         // partial sums: the kGenQ hi-row warps of each other CTA whose rows
         // hold slots kept here; stage inputs: every generator warp of each
         // other CTA
-        mbar_init(dx_full, clustered ? kGenQ * (P - 1) : 1);
-        mbar_init(xg_full, clustered ? kGenWarps * (P - 1) : 1);
+        mbar_init(dx_full, xchg ? kGenQ * (P - 1) : 1);
+        mbar_init(xg_full, xchg ? kGenWarps * (P - 1) : 1);
         for (int s = 0; s < KS; s++) {
             mbar_init(&k_full[s], 1);
             mbar_init(&k_empty[s], kGenWarps);
         }
         for (int s = 0; s < kGenWarps / 2; s++) mbar_init(&pair_full[s], 1);
+        for (int s = 0; s < kAStages; s++) mbar_init(&pr_full[s], 1);
+        mbar_init(cx_full, 1);
         s_err = 0;
         s_continue = 1;
         s_wait_lim = a.wait_cycles;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(su32(&s_tmem)), "r"(ncols) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if constexpr (Pair) {
+            // both CTAs of the pair allocate together (the same columns in each)
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+                         ::"r"(su32(&s_tmem)), "r"(ncols) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                         ::"r"(su32(&s_tmem)), "r"(ncols) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     // initial slot fill: group x takes cells x, x + G, .., x + (C - 1) G (C =
     // the cells per group, at most NS): every group a spread of radii.  Every
@@ -1000,13 +1064,18 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     if (nt < nk && (g < SB || mbar_test(&bt_empty[ps], (pu + 1) & 1))) {
                         const int st = st_lo + nt;
                         const int nb = 2 * st + 1 < n_blk ? 2 : 1;
-                        mbar_expect_tx(&bt_full[ps], (uint32_t)(nb * 2 * half_bytes));
+                        mbar_expect_tx(&bt_full[ps], (uint32_t)(nb * (pairm ? 1 : 2) * half_bytes));
                         for (int q = 0; q < nb; q++) {
                             uint8_t *dst = bring + (size_t)ps * sstride + (size_t)q * bstride;
                             const uint8_t *src =
                                 (const uint8_t *)(a.t.Btiles + (size_t)(2 * st + q) * (2 * half_bytes / 16));
-                            bulk_g2s(dst, src, half_bytes, &bt_full[ps]);
-                            bulk_g2s(dst + half_bytes, src + half_bytes, half_bytes, &bt_full[ps]);
+                            if (pairm) {
+                                // this CTA's rows of the stacked B operand: hi (even CTA) or lo (odd)
+                                bulk_g2s(dst, src + (size_t)half * half_bytes, half_bytes, &bt_full[ps]);
+                            } else {
+                                bulk_g2s(dst, src, half_bytes, &bt_full[ps]);
+                                bulk_g2s(dst + half_bytes, src + half_bytes, half_bytes, &bt_full[ps]);
+                            }
                         }
                         nt++;
                         g++;
@@ -1039,9 +1108,34 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         __syncwarp();
     } else if (warp == 1) {
         // ---- MMA issuer: one thread (the tensor pipe's queue is shallow, so
-        // the issuing thread does nothing between MMAs that it can avoid) ----
-        if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(2 * kSlots, stacked ? 2 * NBP : NBP);
+        // the issuing thread does nothing between MMAs that it can avoid).
+        // Pair mode: the even CTA issues M = 256 MMAs for both CTAs; the odd
+        // CTA's thread instead tells it, stage by stage, that its half of the
+        // mapping tiles has landed and its generated operand is written ----
+        if (lane == 0 && pairm && !leader) {
+            const uint32_t pr_remote = mapa(su32(pr_full), (uint32_t)(crank ^ 1));
+            int ms = 0, mc = 0;
+            uint32_t mu = 0, mv = 0;
+            for (int r = 0;; r++) {
+                if (r > 0) {
+                    if (!twait(go, (r - 1) & 1, &s_err, ERR_WAIT_MMA)) break;
+                    if (!s_continue) break;
+                }
+                bool ok = true;
+                for (int st = st_lo; st < st_hi; st++) {
+                    const int sb = ms, sc = mc;
+                    const uint32_t ub = mu, uc = mv;
+                    if (++ms == SB) { ms = 0; mu++; }
+                    if (++mc == kAStages) { mc = 0; mv++; }
+                    if (!twait(&bt_full[sb], ub & 1, &s_err, ERR_WAIT_MMA) ||
+                        !twait(&c_full[sc], uc & 1, &s_err, ERR_WAIT_MMA)) { ok = false; break; }
+                    fence_cluster();
+                    mbar_arrive_remote(pr_remote + 8u * (uint32_t)sc);
+                }
+                if (!ok) break;
+            }
+        } else if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(pairm ? 4 * kSlots : 2 * kSlots, stacked ? 2 * NBP : NBP);
             const int nb_mine = b_hi - b_lo;
             long long g = 0;
             int ms = 0, mc = 0;
@@ -1061,7 +1155,11 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     if (++ms == SB) { ms = 0; mu++; }
                     if (++mc == kAStages) { mc = 0; mv++; }
                     if (!twait(&bt_full[sb], ub & 1, &s_err, ERR_WAIT_MMA) ||
-                        !twait(&c_full[sc], uc & 1, &s_err, ERR_WAIT_MMA)) { ok = false; break; }
+                        !twait(&c_full[sc], uc & 1, &s_err, ERR_WAIT_MMA) ||
+                        (pairm && !twait_cluster(&pr_full[sc], uc & 1, &s_err, ERR_WAIT_PEER))) {
+                        ok = false;
+                        break;
+                    }
                     tc_fence_after();
                     const int nb = 2 * st + 1 < n_blk ? 2 : 1;
                     for (int q = 0; q < nb; q++) {
@@ -1073,19 +1171,32 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                         const uint32_t dh = tmem + acol + (uint32_t)(ch * (stacked ? 2 * NBP : NBP));
                         // the four K steps into one accumulator (stacked: both
                         // products at once), else then into the Bt_lo one
-                        mma_tf32_ts(dh, at, dbh, idesc, first ? 0u : 1u);
+                        if constexpr (Pair) {
 #pragma unroll
-                        for (int kk = 1; kk < 4; kk++) mma_tf32_ts_acc(dh, at + 8 * kk, dbh + 2 * kk, idesc);
-                        if (!stacked) {
-                            mma_tf32_ts(dl, at, dbl, idesc, bl == 0 ? 0u : 1u);
+                            for (int kk = 0; kk < 4; kk++)
+                                mma2_tf32_ts(dh, at + 8 * kk, dbh + 2 * kk, idesc, (first && kk == 0) ? 0u : 1u);
+                            first = false;
+                        } else {
+                            mma_tf32_ts(dh, at, dbh, idesc, first ? 0u : 1u);
 #pragma unroll
-                            for (int kk = 1; kk < 4; kk++) mma_tf32_ts_acc(dl, at + 8 * kk, dbl + 2 * kk, idesc);
+                            for (int kk = 1; kk < 4; kk++) mma_tf32_ts_acc(dh, at + 8 * kk, dbh + 2 * kk, idesc);
+                            if (!stacked) {
+                                mma_tf32_ts(dl, at, dbl, idesc, bl == 0 ? 0u : 1u);
+#pragma unroll
+                                for (int kk = 1; kk < 4; kk++) mma_tf32_ts_acc(dl, at + 8 * kk, dbl + 2 * kk, idesc);
+                            }
+                            first = false;
                         }
-                        first = false;
                     }
-                    mma_commit(&bt_empty[sb]);
-                    mma_commit(&c_empty[sc]);
-                    if (st == st_hi - 1) mma_commit(done);
+                    if constexpr (Pair) {
+                        mma_commit2(&bt_empty[sb], pair_mask);
+                        mma_commit2(&c_empty[sc], pair_mask);
+                        if (st == st_hi - 1) mma_commit2(done, pair_mask);
+                    } else {
+                        mma_commit(&bt_empty[sb]);
+                        mma_commit(&c_empty[sc]);
+                        if (st == st_hi - 1) mma_commit(done);
+                    }
                 }
                 if (!ok) break;
             }
@@ -1111,7 +1222,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         float *Dlo = Dsm + (size_t)SL * NBP;          // [64][NBP]: the lo-row sums of every slot
         const int pair = (qd & 1) * kGenQ + sub;      // the hi-row / lo-row warp pair of these slots and columns
         const uint32_t d_remote = rows_own ? 0u :
-            mapa(su32(dpeer), (uint32_t)owner) +
+            mapa(su32(dpeer), member(owner)) +
             (uint32_t)((size_t)((rank < owner ? rank : rank - 1) * SL) * NBP * 4);
         // owners of this warp's 32 consecutive slots
         const int own_lo = (slot - lane) / SL, own_hi = (slot - lane + 31) / SL;
@@ -1184,19 +1295,19 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     if (lane == 0) mbar_arrive(&pair_full[pair]);
                 } else if (epi_ok) {
                     if (!got_lo && !wwait(&pair_full[pair], r & 1, &s_err, ERR_WAIT_EPI)) epi_ok = false;
-                    if (epi_ok && clustered) {
+                    if (epi_ok && xchg) {
                         // one arrival at every other CTA whose slots this warp's rows hold
                         fence_cluster();
                         __syncwarp();
                         if (lane == 0)
                             for (int o = own_lo; o <= own_hi; o++)
-                                if (o != rank) mbar_arrive_remote(mapa(su32(dx_full), (uint32_t)o));
+                                if (o != rank) mbar_arrive_remote(mapa(su32(dx_full), member(o)));
                     }
                 }
             }
             if (!epi_ok) break;
             tc_fence_before();
-            if (clustered && !cwait(dx_full, r & 1, &s_err, ERR_WAIT_PEER)) break;
+            if (xchg && !cwait(dx_full, r & 1, &s_err, ERR_WAIT_PEER)) break;
             if (!gen_sync(gbar, gphase, &s_err)) break;
             // ---- per-slot integrator logic for the slots kept here ----
             for (int sl = warp - 2; sl < SL; sl += kGenWarps) {
@@ -1204,7 +1315,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                 Slot &slr = slots[sidx];
                 // D = sum of the partial rows (here, then from the others)
                 float *Drow = Dsm + (size_t)sl * NBP;
-                if (clustered) {
+                if (xchg) {
                     float v[kLaneBins];
 #pragma unroll
                     for (int m = 0; m < kLaneBins; m++) v[m] = lane + 32 * m < N ? Drow[lane + 32 * m] : 0.f;
@@ -1241,7 +1352,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     }
                     __syncwarp();
                 }
-                if (clustered) {
+                if (xchg) {
                     // the slot's stage input (16-byte pieces; the row is 16-byte
                     // aligned and zero past N) and cell, to every other CTA
                     const float4 *xs = (const float4 *)(xrows + (size_t)sidx * XS);
@@ -1253,19 +1364,19 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     const float4 xw = lane + 32 < n4 ? xs[lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
                     for (int o = 0; o < P; o++) {
                         if (o == rank) continue;
-                        const uint32_t xdst = mapa(su32(xrows), (uint32_t)o) + xoff;
+                        const uint32_t xdst = mapa(su32(xrows), member(o)) + xoff;
                         if (lane < n4) st_cluster_v4(xdst + 16 * lane, xv.x, xv.y, xv.z, xv.w);
                         if (lane + 32 < n4) st_cluster_v4(xdst + 16 * (lane + 32), xw.x, xw.y, xw.z, xw.w);
-                        if (lane == 0) st_cluster_s32(mapa(su32(slots), (uint32_t)o) + coff, cell_now);
+                        if (lane == 0) st_cluster_s32(mapa(su32(slots), member(o)) + coff, cell_now);
                     }
                 }
             }
-            if (clustered) {
+            if (xchg) {
                 fence_cluster();
                 __syncwarp();
                 if (lane == 0)
                     for (int o = 0; o < P; o++)
-                        if (o != rank) mbar_arrive_remote(mapa(su32(xg_full), (uint32_t)o));
+                        if (o != rank) mbar_arrive_remote(mapa(su32(xg_full), member(o)));
                 if (!cwait(xg_full, r & 1, &s_err, ERR_WAIT_PEER)) break;
             }
             // generic-proxy writes to the stage memory (D staging) must be
@@ -1275,6 +1386,16 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             if (gt == 0) {
                 int any = 0;
                 for (int s2 = 0; s2 < NS; s2++) any |= (slots[s2].cell >= 0);
+                if (pairm) {
+                    // the pair's MMAs serve both its groups: passes go on while
+                    // either has cells (the partner CTA is in the other group)
+                    const uint32_t prt = (uint32_t)(crank ^ 1);
+                    st_cluster_s32(mapa(su32(&s_any_x), prt), any);
+                    fence_cluster();
+                    mbar_arrive_remote(mapa(su32(cx_full), prt));
+                    if (twait_cluster(cx_full, r & 1, &s_err, ERR_WAIT_PEER)) any |= *(volatile int *)&s_any_x;
+                    else any = 0;
+                }
                 s_continue = any;
                 mbar_arrive(go);
             }
@@ -1283,22 +1404,28 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         }
     }
     if (warp == 1 && lane == 0) {
-        // every MMA this thread issued has completed before TMEM is freed
-        mma_commit(fin);
+        // every MMA this thread (pair mode: the even CTA's) issued has completed
+        // before TMEM is freed
+        if constexpr (!Pair) mma_commit(fin);
+        else if (leader) mma_commit2(fin, pair_mask);
         mbar_drain(fin, 0);
     }
     tc_fence_before();
-    __syncthreads();
+    if (pairm) cluster_sync_all();                    // neither CTA of a pair frees TMEM before both are done
+    else __syncthreads();
     tc_fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+        if constexpr (Pair)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
     }
     if (threadIdx.x == 0 && s_err) atomicCAS(a.err, 0, s_err);
     // no CTA of a cluster leaves while another may still write to it
     if (clustered) cluster_sync_all();
 }
 
-struct Config { int grid, groups, P, NS, XS, SB, KS, NBP, nacc, stacked, C, sst_off; size_t smem; bool ok; };
+struct Config { int grid, groups, P, NS, XS, SB, KS, NBP, nacc, stacked, C, sst_off, pair; size_t smem; bool ok; };
 
 cudaError_t launch_kernel(const Config &cf, const MixedArgs &a, cudaStream_t stream);
 int sm_count();
@@ -1306,7 +1433,7 @@ int sm_count();
 // Clusters of P CTAs that can run at once (the launch's groups must all be
 // resident together: a group that started late would find its initial cells
 // untouched).  Asked of the runtime once per device, P and shared-memory size.
-int max_clusters(int P, size_t smem, int n_sm)
+int max_clusters(int P, size_t smem, int n_sm, bool pair = false)   // P: the cluster size
 {
     if (P == 1) return n_sm;
     struct Entry { int dev, P; size_t smem; int n; };
@@ -1317,9 +1444,10 @@ int max_clusters(int P, size_t smem, int n_sm)
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(mu);
     for (int i = 0; i < n_cache; i++)
-        if (cache[i].dev == dev && cache[i].P == P && cache[i].smem == smem) return cache[i].n;
+        if (cache[i].dev == dev && cache[i].P == (pair ? -P : P) && cache[i].smem == smem) return cache[i].n;
     int n = 0;
-    cudaError_t e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = pair ? step_mixed_kernel<true> : step_mixed_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
         cudaLaunchConfig_t lc = {};
         lc.gridDim = dim3((unsigned)(P * (n_sm / P)));
@@ -1332,24 +1460,28 @@ int max_clusters(int P, size_t smem, int n_sm)
         at[0].val.clusterDim.z = 1;
         lc.attrs = at;
         lc.numAttrs = 1;
-        e = cudaOccupancyMaxActiveClusters(&n, step_mixed_kernel, &lc);
+        e = cudaOccupancyMaxActiveClusters(&n, kern, &lc);
     }
     if (e != cudaSuccess) {
         n = 0;
         cudaGetLastError();   // clear the error of the refused query (the caller takes a smaller P)
     }
     n = std::min(n, n_sm / P);
-    if (n_cache < 32) cache[n_cache++] = {dev, P, smem, n};
+    if (n_cache < 32) cache[n_cache++] = {dev, pair ? -P : P, smem, n};
     return n;
 }
 
 // Launch layout for clusters of P CTAs (ok = false when P does not fit: fewer
 // than two mapping-tile stages beside the buffers, fewer than two stages of a
 // pass per CTA, or no cluster of P resident).
-Config config_for(int n_cells, int N, int P, int n_sm)   // n_sm: the SMs this launch may occupy
+// pair: CTA pairs share M = 256 MMAs, a cluster of 2 P CTAs serving two
+// groups of 64 slots (each CTA keeps half of every mapping tile)
+Config config_for(int n_cells, int N, int P, int n_sm, bool pair = false)   // n_sm: the SMs this launch may occupy
 {
     Config c;
     c.P = P;
+    c.pair = pair ? 1 : 0;
+    const int Q = pair ? 2 * P : P;              // CTAs per cluster
     c.NS = kSlots;
     const int n16 = ((N + 15) / 16) * 16;
     c.XS = n16 + 4;                              // rows 16 B aligned, 4 words off the bank period
@@ -1362,9 +1494,11 @@ Config config_for(int n_cells, int N, int P, int n_sm)   // n_sm: the SMs this l
     int n_blk = 0;
     for (int i = 0; i < N; i++) n_blk += (i + kBlkPairs) / kBlkPairs;
     const int n_st = (n_blk + 1) / 2;
-    const size_t sstride = 2 * (((2 * (size_t)c.NBP * 128 + 1023) / 1024) * 1024);   // a stage: two blocks
+    // a stage: two blocks of tiles (pair mode: this CTA's half of each)
+    const size_t sstride = 2 * ((((pair ? 1 : 2) * (size_t)c.NBP * 128 + 1023) / 1024) * 1024);
+    const int max_sb = pair ? kMaxSB : 4;
     const size_t tail = (size_t)kSlots * c.XS * 4 + (size_t)kSlots * sizeof(Slot) +
-                        8 * (2 * kMaxSB + 2 * kAStages + 6 + 2 * kMaxKS + kGenWarps / 2);
+                        8 * (2 * kMaxSB + 3 * kAStages + 7 + 2 * kMaxKS + kGenWarps / 2);
     const size_t budget = 232448 - 1024 - 2048;  // opt-in shared memory, alignment, static
     const int SL = kSlots / P;
     const size_t dpeer = (size_t)(P - 1) * SL * c.NBP * 4;   // partial sums from the other CTAs
@@ -1384,9 +1518,9 @@ Config config_for(int n_cells, int N, int P, int n_sm)   // n_sm: the SMs this l
     const int KSx = (int)std::min<size_t>(kMaxKS - KS, avail / kstage);
     KS += KSx;
     avail -= KSx * kstage;
-    int SB = sb_min + (int)std::min<size_t>(kMaxSB - sb_min, avail / sstride);
+    int SB = sb_min + (int)std::min<size_t>(max_sb - sb_min, avail / sstride);
     // the D staging areas ([slots kept + 64][NBP] floats) alias the mapping-tile ring
-    while ((size_t)SB * sstride < (size_t)(SL + kSlots) * c.NBP * 4 && SB < kMaxSB) SB++;
+    while ((size_t)SB * sstride < (size_t)(SL + kSlots) * c.NBP * 4 && SB < max_sb) SB++;
     c.SB = SB;
     c.KS = KS;
     c.sst_off = st_smem ? (int)((size_t)SB * sstride + KS * kstage) : -1;
@@ -1394,12 +1528,19 @@ Config config_for(int n_cells, int N, int P, int n_sm)   // n_sm: the SMs this l
     // at least 120 KB, so that no two CTAs share an SM (each holds all 512
     // TMEM columns for the whole kernel)
     c.smem = std::max((size_t)120 * 1024, 1024 + used + tail + dpeer);
-    c.ok = KS >= 1 && SB >= sb_min && used <= room && (P == 1 || n_st >= 2 * P);
-    // cells are spread over up to one cluster per P SMs, at least 8 a group
-    const int mc = P == 1 ? n_sm : (c.ok ? std::min(max_clusters(P, c.smem, sm_count()), n_sm / P) : 0);
+    c.ok = KS >= 1 && SB >= sb_min && used <= room && (P == 1 || n_st >= 2 * P) &&
+           (!pair || (c.stacked && (size_t)SB * sstride >= (size_t)(SL + kSlots) * c.NBP * 4));
+    // cells are spread over up to one cluster per Q SMs, at least 8 a group
+    const int mc = Q == 1 ? n_sm : (c.ok ? std::min(max_clusters(Q, c.smem, sm_count(), pair), n_sm / Q) : 0);
     if (mc < 1) c.ok = false;
-    c.groups = std::max(1, std::min(std::max(mc, 1), (n_cells + 7) / 8));
-    c.grid = P * c.groups;
+    if (pair) {
+        const int clusters = std::max(1, std::min(std::max(mc, 1), (n_cells + 15) / 16));
+        c.groups = 2 * clusters;
+        c.grid = Q * clusters;
+    } else {
+        c.groups = std::max(1, std::min(std::max(mc, 1), (n_cells + 7) / 8));
+        c.grid = P * c.groups;
+    }
     c.C = std::min(kSlots, (n_cells + c.groups - 1) / c.groups);
     return c;
 }
@@ -1419,9 +1560,19 @@ int sm_count()
 // cells taking about three times the mean.  A request that does not fit
 // falls back to the largest smaller P that does.
 // max_sms > 0: the launch may occupy at most that many SMs.
-Config mixed_config(int n_cells, int N, int P_req, int max_sms)
+// pair_req: 2 = CTA pairs (P_req pairs per cluster, 0: two), falling back to
+// fewer pairs and then to single CTAs when it does not fit; otherwise single
+// CTAs as below.
+Config mixed_config(int n_cells, int N, int P_req, int max_sms, int pair_req = 0)
 {
     const int n_sm = max_sms > 0 ? std::min(max_sms, sm_count()) : sm_count();
+    if (pair_req == 2) {
+        for (int P = P_req > 0 ? P_req : 2; P >= 1; P /= 2) {
+            Config c = config_for(n_cells, N, P, n_sm, true);
+            if (c.ok) return c;
+        }
+        P_req = 0;
+    }
     if (P_req > 0) {
         for (int P = P_req; P >= 1; P /= 2) {
             Config c = config_for(n_cells, N, P, n_sm);
@@ -1448,27 +1599,30 @@ cudaError_t launch_kernel(const Config &cf, const MixedArgs &a, cudaStream_t str
     lc.dynamicSmemBytes = cf.smem;
     lc.stream = stream;
     cudaLaunchAttribute at[1];
-    if (cf.P > 1) {
+    const int Q = cf.pair ? 2 * cf.P : cf.P;
+    if (Q > 1) {
         at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = (unsigned)cf.P;
+        at[0].val.clusterDim.x = (unsigned)Q;
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
         lc.attrs = at;
         lc.numAttrs = 1;
     }
-    return cudaLaunchKernelEx(&lc, step_mixed_kernel, a);
+    return cf.pair ? cudaLaunchKernelEx(&lc, step_mixed_kernel<true>, a)
+                   : cudaLaunchKernelEx(&lc, step_mixed_kernel<false>, a);
 }
 
 cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double *drho, double t_span,
                          double *dt_cell, const double *replay_h, const long long *replay_n,
                          long long replay_stride, WorkList wl = WorkList())
 {
-    Config cf = mixed_config(c->n_cells, c->N, c->mix_P, c->p.max_sms);
+    Config cf = mixed_config(c->n_cells, c->N, c->mix_P, c->p.max_sms, c->mix_pair ? 2 : 1);
     const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(float);
     if (need > c->work_bytes) return cudaErrorInvalidValue;
-    if (cf.P != c->mix_P || cf.groups != c->mix_G || cf.C != c->mix_C)
+    if (cf.P != c->mix_P || cf.groups != c->mix_G || cf.C != c->mix_C || cf.pair != c->mix_pair)
         return cudaErrorInvalidValue;   // layout of the K tables
-    cudaError_t e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
+    cudaError_t e = cudaFuncSetAttribute(cf.pair ? step_mixed_kernel<true> : step_mixed_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(c->d_counter + 1, 0, 2 * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
@@ -1505,6 +1659,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.KS = cf.KS;
     a.sst_off = cf.sst_off;
     a.P = cf.P;
+    a.pair = cf.pair;
     a.wait_cycles = c->inject_wait_cycles > 0 ? c->inject_wait_cycles : kWaitCycles;
     a.withhold = c->inject_withhold;
     a.wl = wl;
@@ -1530,9 +1685,9 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 size_t static_scratch_bytes() { return kStaticScratchBytes; }
 
-size_t mixed_scratch_bytes(int n_cells, int N, int P, int max_sms)
+size_t mixed_scratch_bytes(int n_cells, int N, int P, int max_sms, int pair)
 {
-    const Config cf = mixed_config(n_cells, N, P, max_sms);
+    const Config cf = mixed_config(n_cells, N, P, max_sms, pair ? 2 : 1);
     return cf.sst_off >= 0 ? 0 : (size_t)cf.groups * cf.NS * 5 * (size_t)N * sizeof(float);
 }
 
@@ -1540,12 +1695,12 @@ cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_s
                                      bool *too_big)
 {
     *too_big = false;
-    Config cf = mixed_config(c->n_cells, c->N, c->mix_P, c->p.max_sms);
+    Config cf = mixed_config(c->n_cells, c->N, c->mix_P, c->p.max_sms, c->mix_pair ? 2 : 1);
     // the array is only touched when the per-slot state does not fit in
     // shared memory
     const size_t need = cf.sst_off >= 0 ? 0 : (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(float);
     if (need > kStaticScratchBytes) { *too_big = true; return cudaSuccess; }
-    if (cf.P != c->mix_P || cf.groups != c->mix_G || cf.C != c->mix_C)
+    if (cf.P != c->mix_P || cf.groups != c->mix_G || cf.C != c->mix_C || cf.pair != c->mix_pair)
         return cudaErrorInvalidValue;   // layout of the K tables
     if (!c->static_scratch) {
         // set-up, once per context, with its device current: the array's
@@ -1556,7 +1711,8 @@ cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_s
         if (e != cudaSuccess) return e;
         c->static_scratch = ptr;
     }
-    cudaError_t e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
+    cudaError_t e = cudaFuncSetAttribute(cf.pair ? step_mixed_kernel<true> : step_mixed_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(c->d_counter + 1, 0, 2 * sizeof(int), c->stream);
     if (e != cudaSuccess) return e;
@@ -1593,6 +1749,7 @@ cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_s
     a.KS = cf.KS;
     a.sst_off = cf.sst_off;
     a.P = cf.P;
+    a.pair = cf.pair;
     a.wait_cycles = c->inject_wait_cycles > 0 ? c->inject_wait_cycles : kWaitCycles;
     a.withhold = c->inject_withhold;
     a.wl = WorkList();
@@ -1600,17 +1757,18 @@ cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_s
     return launch_kernel(cf, a, c->stream);
 }
 
-void mixed_layout(int n_cells, int N, int P_req, int max_sms, int *P, int *G, int *C)
+void mixed_layout(int n_cells, int N, int P_req, int max_sms, int pair_req, int *P, int *G, int *C, int *pair)
 {
-    const Config cf = mixed_config(n_cells, N, P_req, max_sms);
+    const Config cf = mixed_config(n_cells, N, P_req, max_sms, pair_req);
     *P = cf.P;
     *G = cf.groups;
     *C = cf.C;
+    *pair = cf.pair;
 }
 
-size_t mixed_workspace_bytes(int n_cells, int N, int P, int max_sms)
+size_t mixed_workspace_bytes(int n_cells, int N, int P, int max_sms, int pair)
 {
-    Config cf = mixed_config(n_cells, N, P, max_sms);
+    Config cf = mixed_config(n_cells, N, P, max_sms, pair ? 2 : 1);
     return (size_t)cf.groups * cf.NS * 5 * (size_t)N * sizeof(float);
 }
 
