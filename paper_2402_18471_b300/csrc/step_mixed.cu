@@ -1316,14 +1316,17 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                 // D = sum of the partial rows (here, then from the others)
                 float *Drow = Dsm + (size_t)sl * NBP;
                 if (xchg) {
+                    // the members' partial rows added in member order (not
+                    // starting with this CTA's own), so that a cell's result
+                    // does not depend on which member keeps its slot
                     float v[kLaneBins];
 #pragma unroll
-                    for (int m = 0; m < kLaneBins; m++) v[m] = lane + 32 * m < N ? Drow[lane + 32 * m] : 0.f;
-                    for (int q = 0; q < P - 1; q++) {
-                        const float *dp = dpeer + ((size_t)q * SL + sl) * NBP;
+                    for (int m = 0; m < kLaneBins; m++) v[m] = 0.f;
+                    for (int o = 0; o < P; o++) {
+                        const float *dp = o == rank ? Drow : dpeer + ((size_t)(o < rank ? o : o - 1) * SL + sl) * NBP;
 #pragma unroll
                         for (int m = 0; m < kLaneBins; m++)
-                            if (lane + 32 * m < N) v[m] += dp[lane + 32 * m];
+                            if (lane + 32 * m < N) v[m] = o == 0 ? dp[lane + 32 * m] : v[m] + dp[lane + 32 * m];
                     }
 #pragma unroll
                     for (int m = 0; m < kLaneBins; m++)
