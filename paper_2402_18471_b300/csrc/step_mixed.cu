@@ -817,6 +817,7 @@ struct GenCtx {
     const uint8_t *kring;                // K ring: KS stages of 2 x kKBlkBytes
     const float *xr;
     uint64_t *c_empty, *c_full, *k_full, *k_empty;
+    uint32_t c_full_remote;              // pair mode, odd CTA: the even CTA's c_full (0: arrive locally)
     volatile int *s_err;
     int n_blk, sub, lane, slot, KS;      // sub: which kGP pairs of each block
     bool lo_half, active;
@@ -865,7 +866,10 @@ __device__ __forceinline__ bool gen_stage(GenCtx &G, int st, long long g)
         tc_fence_before();
     }
     __syncwarp();
-    if (G.lane == 0) mbar_arrive(&G.c_full[G.s]);
+    if (G.lane == 0) {
+        if (G.c_full_remote) mbar_arrive_remote(G.c_full_remote + 8u * (uint32_t)G.s);   // release, cluster scope
+        else mbar_arrive(&G.c_full[G.s]);
+    }
     // blocks run along rows: (i, 0), (i, 16), .. while j0 <= i, then (i + 1, 0)
     G.bi = bi1;
     G.bj0 = bj1 + kBlkPairs;
@@ -948,7 +952,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     uint64_t *dx_full = done + 4, *xg_full = done + 5;
     uint64_t *k_full = done + 6, *k_empty = done + 6 + KS;
     uint64_t *pair_full = k_empty + KS;                 // [kGenWarps / 2]: a lo-row warp's sums are in Dlo
-    uint64_t *pr_full = pair_full + kGenWarps / 2;      // [kAStages] pair mode, even CTA: the odd one's stage is ready
+    uint64_t *pr_full = pair_full + kGenWarps / 2;      // [kAStages] pair mode, even CTA: the odd one's tiles landed
     uint64_t *cx_full = pr_full + kAStages;             // pair mode: the partner's continue flag arrived
     __shared__ uint32_t s_tmem;
     __shared__ int s_err, s_continue, s_any_x;
@@ -972,7 +976,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             mbar_init(&bt_empty[s], 1);
         }
         for (int s = 0; s < kAStages; s++) {
-            mbar_init(&c_full[s], kGenWarps);
+            // pair mode: the even CTA's stage takes both CTAs' generators
+            mbar_init(&c_full[s], pairm ? 2 * kGenWarps : kGenWarps);
             mbar_init(&c_empty[s], 1);
         }
         mbar_init(done, 1);
@@ -1111,7 +1116,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         // the issuing thread does nothing between MMAs that it can avoid).
         // Pair mode: the even CTA issues M = 256 MMAs for both CTAs; the odd
         // CTA's thread instead tells it, stage by stage, that its half of the
-        // mapping tiles has landed and its generated operand is written ----
+        // mapping tiles has landed (its generators arrive on the even CTA's
+        // c_full themselves) ----
         if (lane == 0 && pairm && !leader) {
             const uint32_t pr_remote = mapa(su32(pr_full), (uint32_t)(crank ^ 1));
             int ms = 0, mc = 0;
@@ -1127,10 +1133,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     const uint32_t ub = mu, uc = mv;
                     if (++ms == SB) { ms = 0; mu++; }
                     if (++mc == kAStages) { mc = 0; mv++; }
-                    if (!twait(&bt_full[sb], ub & 1, &s_err, ERR_WAIT_MMA) ||
-                        !twait(&c_full[sc], uc & 1, &s_err, ERR_WAIT_MMA)) { ok = false; break; }
-                    fence_cluster();
-                    mbar_arrive_remote(pr_remote + 8u * (uint32_t)sc);
+                    if (!twait(&bt_full[sb], ub & 1, &s_err, ERR_WAIT_MMA)) { ok = false; break; }
+                    mbar_arrive_remote(pr_remote + 8u * (uint32_t)sc);   // release, cluster scope
                 }
                 if (!ok) break;
             }
@@ -1155,7 +1159,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     if (++ms == SB) { ms = 0; mu++; }
                     if (++mc == kAStages) { mc = 0; mv++; }
                     if (!twait(&bt_full[sb], ub & 1, &s_err, ERR_WAIT_MMA) ||
-                        !twait(&c_full[sc], uc & 1, &s_err, ERR_WAIT_MMA) ||
+                        !(pairm ? twait_cluster(&c_full[sc], uc & 1, &s_err, ERR_WAIT_MMA)
+                                : twait(&c_full[sc], uc & 1, &s_err, ERR_WAIT_MMA)) ||
                         (pairm && !twait_cluster(&pr_full[sc], uc & 1, &s_err, ERR_WAIT_PEER))) {
                         ok = false;
                         break;
@@ -1231,6 +1236,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         GenCtx G;                                     // ring positions carry over between passes
         G.a = &a; G.tmem = tmem; G.lane_base = lane_base; G.kring = kring; G.xr = xr;
         G.c_empty = c_empty; G.c_full = c_full; G.k_full = k_full; G.k_empty = k_empty;
+        G.c_full_remote = (pairm && !leader) ? mapa(su32(c_full), (uint32_t)(crank ^ 1)) : 0u;
         G.s_err = &s_err; G.n_blk = b_hi; G.sub = sub; G.lane = lane; G.slot = slot; G.KS = KS;
         G.lo_half = lo_half; G.active = false; G.bi = G.bj0 = 0;
         G.s = 0; G.ks = 0; G.u = 0; G.ku = 0;
