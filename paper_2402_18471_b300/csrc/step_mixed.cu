@@ -952,8 +952,11 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     uint64_t *dx_full = done + 4, *xg_full = done + 5;
     uint64_t *k_full = done + 6, *k_empty = done + 6 + KS;
     uint64_t *pair_full = k_empty + KS;                 // [kGenWarps / 2]: a lo-row warp's sums are in Dlo
-    uint64_t *pr_full = pair_full + kGenWarps / 2;      // [kAStages] pair mode, even CTA: the odd one's tiles landed
-    uint64_t *cx_full = pr_full + kAStages;             // pair mode: the partner's continue flag arrived
+    // [SB] pair mode, even CTA: the odd one's tiles landed (indexed like the
+    // tile ring: the odd CTA can relay stage g + SB only after this CTA's
+    // commit for stage g released that ring slot, so one round at a time)
+    uint64_t *pr_full = pair_full + kGenWarps / 2;
+    uint64_t *cx_full = pr_full + kMaxSB;               // pair mode: the partner's continue flag arrived
     __shared__ uint32_t s_tmem;
     __shared__ int s_err, s_continue, s_any_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -994,7 +997,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             mbar_init(&k_empty[s], kGenWarps);
         }
         for (int s = 0; s < kGenWarps / 2; s++) mbar_init(&pair_full[s], 1);
-        for (int s = 0; s < kAStages; s++) mbar_init(&pr_full[s], 1);
+        for (int s = 0; s < SB; s++) mbar_init(&pr_full[s], 1);
         mbar_init(cx_full, 1);
         s_err = 0;
         s_continue = 1;
@@ -1134,7 +1137,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     if (++ms == SB) { ms = 0; mu++; }
                     if (++mc == kAStages) { mc = 0; mv++; }
                     if (!twait(&bt_full[sb], ub & 1, &s_err, ERR_WAIT_MMA)) { ok = false; break; }
-                    mbar_arrive_remote(pr_remote + 8u * (uint32_t)sc);   // release, cluster scope
+                    mbar_arrive_remote(pr_remote + 8u * (uint32_t)sb);   // release, cluster scope
                 }
                 if (!ok) break;
             }
@@ -1161,7 +1164,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     if (!twait(&bt_full[sb], ub & 1, &s_err, ERR_WAIT_MMA) ||
                         !(pairm ? twait_cluster(&c_full[sc], uc & 1, &s_err, ERR_WAIT_MMA)
                                 : twait(&c_full[sc], uc & 1, &s_err, ERR_WAIT_MMA)) ||
-                        (pairm && !twait_cluster(&pr_full[sc], uc & 1, &s_err, ERR_WAIT_PEER))) {
+                        (pairm && !twait_cluster(&pr_full[sb], ub & 1, &s_err, ERR_WAIT_PEER))) {
                         ok = false;
                         break;
                     }
@@ -1507,7 +1510,7 @@ Config config_for(int n_cells, int N, int P, int n_sm, bool pair = false)   // n
     const size_t sstride = 2 * ((((pair ? 1 : 2) * (size_t)c.NBP * 128 + 1023) / 1024) * 1024);
     const int max_sb = pair ? kMaxSB : 4;
     const size_t tail = (size_t)kSlots * c.XS * 4 + (size_t)kSlots * sizeof(Slot) +
-                        8 * (2 * kMaxSB + 3 * kAStages + 7 + 2 * kMaxKS + kGenWarps / 2);
+                        8 * (3 * kMaxSB + 2 * kAStages + 7 + 2 * kMaxKS + kGenWarps / 2);
     const size_t budget = 232448 - 1024 - 2048;  // opt-in shared memory, alignment, static
     const int SL = kSlots / P;
     const size_t dpeer = (size_t)(P - 1) * SL * c.NBP * 4;   // partial sums from the other CTAs
