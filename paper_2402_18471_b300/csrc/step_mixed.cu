@@ -775,6 +775,40 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
 // p_frag, split hi = rn_tf32(v), lo = v - hi; the thread keeps the
 // half its row holds and writes the 2 kGP values into the stage's TMEM
 // columns.  kv: the thread's 2-pair chunks {K p_c, K p_f, K p_c, K p_f}.
+// Packed FP32 pairs (two lanes of one 64-bit register): one instruction
+// rounds both products (mul.rn.f32x2 / sub.rn.f32x2, the same IEEE
+// round-to-nearest as two scalar ones), halving the generators' FP32 issue.
+__device__ __forceinline__ unsigned long long pk2(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long r, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// TF32 rounding to nearest, ties away from zero, in one conversion (the same
+// rounding as tf32_rn's integer form)
+__device__ __forceinline__ float tf32_rna(float v)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
 __device__ __forceinline__ void gen_vals(const float4 (&kc)[kGC], const float *xr, int bi, int jfirst,
                                          bool lo_half, float (&out)[2 * kGP])
 {
@@ -786,22 +820,21 @@ __device__ __forceinline__ void gen_vals(const float4 (&kc)[kGC], const float *x
         xj[u] = x4.x; xj[u + 1] = x4.y; xj[u + 2] = x4.z; xj[u + 3] = x4.w;
     }
     const float *kv = (const float *)kc;
-    if (lo_half) {
+    const unsigned long long xi2 = pk2(xi, xi);
 #pragma unroll
-        for (int u = 0; u < kGP; u++) {
-            const float xx = xi * xj[u];
+    for (int u = 0; u < kGP; u += 2) {
+        float xa, xb;
+        upk2(mul2(xi2, pk2(xj[u], xj[u + 1])), xa, xb);          // x_i x_j of pairs u, u + 1
 #pragma unroll
-            for (int w = 0; w < 2; w++) {
-                const float v = xx * kv[2 * u + w];
-                out[2 * u + w] = v - tf32_rn(v);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int u = 0; u < kGP; u++) {
-            const float xx = xi * xj[u];
-#pragma unroll
-            for (int w = 0; w < 2; w++) out[2 * u + w] = tf32_rn(xx * kv[2 * u + w]);
+        for (int t = 0; t < 2; t++) {
+            const float xx = t == 0 ? xa : xb;
+            const int q = 2 * (u + t);
+            const unsigned long long v2 = mul2(pk2(xx, xx), pk2(kv[q], kv[q + 1]));   // x_i x_j {K p_c, K p_f}
+            float v0, v1;
+            upk2(v2, v0, v1);
+            const float h0 = tf32_rna(v0), h1 = tf32_rna(v1);
+            if (lo_half) upk2(sub2(v2, pk2(h0, h1)), out[q], out[q + 1]);
+            else { out[q] = h0; out[q + 1] = h1; }
         }
     }
 }
