@@ -701,6 +701,55 @@ def autotune_cluster(disc, t_probe=None, candidates=(1, 2, 4, 8), cache_path=Non
     return int(best)
 
 
+def autotune_launch(disc, t_probe=None, clusters=(1, 2, 4, 8), pairs=(1, 2), cache_path=None, device="cuda",
+                    **over):
+    """Measured choice of the mixed kernel's launch layout for this problem:
+    the cluster size (mixed_cluster: CTAs that split each pass of a slot
+    group) and the CTA-pair mode (mixed_pair = 2: two CTAs share each
+    M = 256 tensor-core MMA, each keeping half of every mapping tile; 1:
+    single CTAs).  Every layout that fits gets one warm-up and one timed
+    integration over t_probe (default: a tenth of disc.t_span) from
+    disc.rho0; the best accepted cell-substeps per second wins.  With
+    cache_path the results are kept in a JSON file keyed by (bins, cells,
+    precision) and later calls read them instead of measuring.  Returns
+    {"mixed_cluster": P, "mixed_pair": 1 or 2}, to pass to Coag."""
+    import json
+    import torch
+    key = f"N{disc.n_bins}_cells{disc.n_cells}_mixed_launch"
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+        if key in cache:
+            return dict(cache[key]["best"])
+    t = disc.t_span / 10.0 if t_probe is None else float(t_probe)
+    rates = {}
+    for pair in pairs:
+        for P in clusters:
+            g = Coag(disc, "mixed", device=device, mixed_cluster=P, mixed_pair=pair, **over)
+            try:
+                if g.mixed_cluster()[0] != P or g.mixed_pair() != (1 if pair == 2 else 0):
+                    continue                   # the library fell back: this layout does not fit
+                for rep in range(2):
+                    y = g.state(disc.rho0)
+                    st = g.step(y, t)
+                rates[(P, pair)] = st["accepted"] / max(st["elapsed_ms"], 1e-9) * 1e3
+            finally:
+                g.close()
+                torch.cuda.synchronize()
+    if not rates:
+        raise CoagError(ENOTSUP, "no launch layout fits this problem")
+    P, pair = max(rates, key=rates.get)
+    best = {"mixed_cluster": int(P), "mixed_pair": int(pair)}
+    if cache_path:
+        cache[key] = {"best": best, "rates": {f"P{k[0]}_pair{k[1]}": v for k, v in rates.items()}, "t_probe": t}
+        d = os.path.dirname(os.path.abspath(cache_path))
+        os.makedirs(d, exist_ok=True)
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return best
+
+
 class Batch:
     """Several discs integrated side by side through the batched interface:
     one context per disc (disc(i) gives a Coag view of it), SMs shared out in

@@ -37,3 +37,22 @@ def test_autotune_cluster_measures_caches_and_reuses(coag_mod):
     # a second call reads the cache: with no candidates it could not measure
     assert coag_mod.autotune_cluster(d, candidates=(), cache_path=CACHE) == P
     os.remove(CACHE)
+
+
+def test_autotune_launch_searches_cluster_and_pair_mode(coag_mod):
+    cache = CACHE.replace(".json", "_launch.json")
+    if os.path.exists(cache):
+        os.remove(cache)
+    d = synth.make_disc(74, 64, 40, 1e-5, 1.0, 5.0, 100.0, 50.0, seed=5)
+    best = coag_mod.autotune_launch(d, clusters=(1, 2, 4), cache_path=cache)
+    assert best["mixed_cluster"] in (1, 2, 4) and best["mixed_pair"] in (1, 2)
+    entry = json.load(open(cache))[f"N40_cells{d.n_cells}_mixed_launch"]
+    rates = entry["rates"]
+    assert any(k.endswith("pair2") for k in rates) and any(k.endswith("pair1") for k in rates)
+    assert max(rates.values()) == rates[f"P{best['mixed_cluster']}_pair{best['mixed_pair']}"]
+    # the layout it returns is the one a context then runs
+    g = coag_mod.Coag(d, "mixed", **best)
+    assert g.mixed_cluster()[0] == best["mixed_cluster"] and g.mixed_pair() == (best["mixed_pair"] == 2)
+    g.close()
+    assert coag_mod.autotune_launch(d, clusters=(), cache_path=cache) == best
+    os.remove(cache)
