@@ -634,7 +634,9 @@ def main():
     ap.add_argument("--t-span-yr", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-leg", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the large-grid, adjoint and HSE keys")
+    ap.add_argument("--no-extras", action="store_true", help="skip the large-grid, adjoint, transport and HSE keys")
+    ap.add_argument("--extras", default="hse,transport,large_grid,adjoint",
+                    help="comma-separated extra keys to measure (default all)")
     ap.add_argument("--no-graph", action="store_true", help="time the synchronous calls instead of graph replays")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=10.0)
@@ -822,12 +824,17 @@ def main():
                                 "speedup_mixed_over_fp64": value / v64,
                                 "note": "same steps, warm-up and graph replay as the mixed leg; same rtol, "
                                         "not the same elementwise accuracy over 1e4 yr (see accuracy)"}
-        if world == 1 and not args.no_extras:
-            line["roofline_hse"] = hse_roofline(coag, "cuda", pk)
-            line["transport"] = transport_key(pk)
+        extras = set() if args.no_extras else set(x for x in args.extras.split(",") if x)
+        if world == 1:
+            if "hse" in extras:
+                line["roofline_hse"] = hse_roofline(coag, "cuda", pk)
+            if "transport" in extras:
+                line["transport"] = transport_key(pk)
             if args.workload == "grid_128x64_N100" and args.precision == "mixed":
-                line["large_grid"] = large_grid_key(args, pk)
-                line["adjoint"] = adjoint_key(pk)
+                if "large_grid" in extras:
+                    line["large_grid"] = large_grid_key(args, pk)
+                if "adjoint" in extras:
+                    line["adjoint"] = adjoint_key(pk)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(disc, budget_s=args.cpu_budget)
             # the accuracy of the benched integration: an untimed run of the
