@@ -50,12 +50,12 @@ FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
 # from one ncu capture of the named kernel (summaries under profiles/), valid
 # only for the kernel source they were taken on: a changed source reports null.
 MEASURED_TRAFFIC = {
-    "step_mixed_kernel": {"bytes_per_unit": (24.283566e9 + 0.668781e9) / 635513, "unit": "RHS evaluation",
+    "step_mixed_kernel": {"bytes_per_unit": (25.854755e9 + 0.665149e9) / 635513, "unit": "RHS evaluation",
                           "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
-                          "sha256": "502b67c70379f26b27d8cbc225646a608ba8c6ae6ce6e66c03c6b4282a4c1a6c"},
-    "kbuild32_kernel": {"bytes_per_unit": 43.673600e6 + 321.431552e6, "unit": "launch (8192 cells x 100 bins)",
+                          "sha256": "0bc2cf10e3035198a25dfe66b8b5e39b0dd62e98476b9cf23fddf95987b3499b"},
+    "kbuild32_kernel": {"bytes_per_unit": 43.704576e6 + 322.752512e6, "unit": "launch (8192 cells x 100 bins)",
                         "source": "paper_2402_18471_b300/csrc/kbuild.cu",
-                        "sha256": "657891c5620844420fe01dc0f9c0e9048f29952044a7d8fff2ee761be276734f"},
+                        "sha256": "f54951cf585f15c9033ff60e15efa987e04e8703e154878589dc63c1b6b45c04"},
 }
 MEASURED_TRAFFIC_WORKLOAD = "grid_128x64_N100"   # the captures above are of this grid
 TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 rate ratio
@@ -614,12 +614,13 @@ def transport_key(pk, steps=20, warmup=3):
     ok = bool(torch.isfinite(q).all().item())
     tr.close()
     return {"workload": f"dust transport {nR}x{nZ} cells x {ns} species", "ms_per_step": ms,
-            "cell_species_steps_per_s": units / (ms * 1e-3), "launches_per_step": 14,
-            "bound": "fp64 alu", "achieved": gbs, "unit": "GB/s", "hbm_frac": gbs / pk["hbm_gbs"],
+            "cell_species_steps_per_s": units / (ms * 1e-3), "launches_per_step": 13,
+            "bound": "fp64 pipe", "achieved": gbs, "unit": "GB/s", "hbm_frac": gbs / pk["hbm_gbs"],
             "finite": ok,
             "note": "two stages of ghost fill, face fluxes and update in FP64 plus the source updates; the "
-                    "generalised van Leer slopes and the Riemann and stencil arithmetic (FP64 divisions) "
-                    "bound it, not the HBM traffic"}
+                    "second stage's slope pass (eight limited slopes per cell, one FP64 division each) and "
+                    "the face fluxes keep the FP64 pipe 84-88 % busy (ncu), so FP64 issue, not the HBM "
+                    "traffic of hbm_frac, bounds the step"}
 
 
 def main():

@@ -338,8 +338,9 @@ typedef struct {
  * cudisc_coag_last_error(NULL)), build the geometry on the host, allocate the
  * workspace and the diffusion stencil (as cudisc_dust_update_gas). */
 cudisc_status cudisc_dust_init(const cudisc_dust_params *params, cudisc_dust_ctx **out);
-/* Recompute the diffusion stencil's coefficients after the caller changed
- * the rho_g or nu arrays (asynchronous on the stream). */
+/* Recompute the diffusion stencil's coefficients and the cached reciprocals
+ * of rho_g and Sc after the caller changed the rho_g, nu or Sc arrays
+ * (asynchronous on the stream). */
 cudisc_status cudisc_dust_update_gas(cudisc_dust_ctx *ctx);
 /* One full step of dt seconds (>= 0, finite): Q [4][n_species][n_R n_Z]
  * device FP64 (rho, rho v_R, rho v_phi R, rho v_Z), read and overwritten.

@@ -322,6 +322,12 @@ class DustTransport:
         _check(lib().cudisc_dust_step(self.ctx, Q.data_ptr(), float(dt)))
         return Q
 
+    def gas(self, name: str):
+        """The context's device copy of a gas field ("rho_g", "nu", "Sc",
+        "c_s", "v_g", "a"); after changing rho_g, nu or Sc in place call
+        update_gas()."""
+        return self._d[name]
+
     def update_gas(self):
         _check(lib().cudisc_dust_update_gas(self.ctx))
 

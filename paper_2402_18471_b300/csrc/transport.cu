@@ -14,9 +14,11 @@
 // context: the ghosted primitives (two ghost layers a side) [4][n_s][(n_R +
 // 4)(n_Z + 4)], the face fluxes of the radial faces [4][n_s][(n_R + 1) n_Z]
 // and polar faces [4][n_s][n_R (n_Z + 1)], the half-step state, the
-// start-of-stage primitives of the source update, and the species-free
-// stencil coefficients of every face (4 each).  FP64 throughout: the step is
-// a handful of passes over Q, bound by FP64 issue and HBM.
+// start-of-stage primitives of the source update, the species-free stencil
+// coefficients of every face (4 each), and per ghosted cell the limited
+// slopes along R and theta [4][n_s][ng] and the diffusion variable u
+// [n_s][ng].  FP64 throughout: the step is a handful of passes over Q,
+// bound by FP64 issue and HBM.
 //
 // Readings of the paper (the same as the FP64 oracle's): the azimuthal
 // primitive reconstructed is l = v_phi R; reconstruction coordinates are R
@@ -44,9 +46,13 @@ struct cudisc_dust_ctx {
     double *sn = nullptr, *cs = nullptr;          // g: sin, cos theta^e [nZg + 1]
     double *V = nullptr, *AR = nullptr, *AZ = nullptr;   // [nR nZ], [(nR + 1) nZ], [nR (nZ + 1)]
     double *Rcell = nullptr, *Zcell = nullptr;    // [nR nZ] cell centres (sources)
+    double *iV = nullptr, *iRcell = nullptr;      // [nR nZ] 1 / V, 1 / R of the cell centres
+    double *irg = nullptr, *iSc = nullptr;        // [nR nZ] 1 / rho_g, [n_s] 1 / Sc (with diffusion)
     double *cR = nullptr, *cZ = nullptr;          // [4][faces] stencil coefficients
+    double *gR = nullptr, *gZ = nullptr;          // g: [kGeo][nRg], [kGeo][nZg] reconstruction factors
     // workspace
     double *Pg = nullptr, *FR = nullptr, *FZ = nullptr, *Qh = nullptr, *Pn = nullptr;
+    double *SR = nullptr, *SZ = nullptr, *U = nullptr;   // g: limited slopes [4][n_s][ng], D-scaled u [n_s][ng]
 };
 
 namespace cdc {
@@ -55,9 +61,16 @@ namespace {
 constexpr int NG = 2;
 constexpr int kT = 256;
 
+// Per-cell factors of the limited linear reconstruction along one direction
+// (ghosted index k, centres x, edges e): inverse forward centre spacing,
+// the grid factors c_F, c_B of the generalised van Leer limiter, c_F + c_B -
+// 2, and the offsets of the upper and lower edge from the centre.
+enum { G_IF = 0, G_CF, G_CB, G_CS, G_HI, G_LO, kGeo };
+
 struct TView {
     int ns, nR, nZ, nRg, nZg;
     const double *Rc, *tc, *Re, *te, *sn, *cs, *V, *AR, *AZ;
+    const double *gR, *gZ, *iV, *irg, *iSc;
     const double *rho_g, *nu, *Sc;     // active per cell; Sc per species
     int bc[4];
     double floor;
@@ -69,6 +82,7 @@ TView view(const cudisc_dust_ctx *c)
     v.ns = c->ns; v.nR = c->nR; v.nZ = c->nZ; v.nRg = c->nRg; v.nZg = c->nZg;
     v.Rc = c->Rc; v.tc = c->tc; v.Re = c->Re; v.te = c->te; v.sn = c->sn; v.cs = c->cs;
     v.V = c->V; v.AR = c->AR; v.AZ = c->AZ;
+    v.gR = c->gR; v.gZ = c->gZ; v.iV = c->iV; v.irg = c->irg; v.iSc = c->iSc;
     v.rho_g = c->p.rho_g; v.nu = c->p.nu; v.Sc = c->p.Sc;
     for (int k = 0; k < 4; k++) v.bc[k] = c->p.bc[k];
     v.floor = c->p.floor;
@@ -85,8 +99,11 @@ __device__ __forceinline__ int active_cell(const TView &t, int gi, int gj)
 // Ghosted primitives (rho, v_R, l, v_Z) from the active conserved field: a
 // polar-side ghost of a ZERO boundary, else a radial-side ghost of one, is
 // the floor density at rest; every other cell copies the nearest active cell
-// (outflow and closed alike).
-__global__ void ghost_prim_kernel(TView t, const double *__restrict__ Q, double *__restrict__ Pg)
+// (outflow and closed alike).  With diffusion, also u = rho / (rho_g Sc) per
+// ghosted cell: the dust-to-gas ratio over the species' Schmidt number,
+// whose differences the diffusion flux takes.
+__global__ void ghost_prim_kernel(TView t, const double *__restrict__ Q, double *__restrict__ Pg,
+                                  double *__restrict__ U)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int s = blockIdx.y;
@@ -103,13 +120,19 @@ __global__ void ghost_prim_kernel(TView t, const double *__restrict__ Q, double 
     } else {
         const size_t e = (size_t)s * nc + active_cell(t, gi, gj);
         rho = Q[e];
-        if (rho > 0.0) {
+        if (rho >= 1e-300) {            // 1 / rho finite: one division for the three velocities
+            const double r = 1.0 / rho;
+            v1 = Q[pl + e] * r;
+            v2 = Q[2 * pl + e] * r;
+            v3 = Q[3 * pl + e] * r;
+        } else if (rho > 0.0) {
             v1 = Q[pl + e] / rho;
             v2 = Q[2 * pl + e] / rho;
             v3 = Q[3 * pl + e] / rho;
         }
     }
     const size_t o = (size_t)s * ng + g;
+    if (t.nu) U[o] = rho * t.irg[active_cell(t, gi, gj)] * t.iSc[s];
     Pg[o] = rho;
     Pg[pg + o] = v1;
     Pg[2 * pg + o] = v2;
@@ -117,7 +140,7 @@ __global__ void ghost_prim_kernel(TView t, const double *__restrict__ Q, double 
 }
 
 // Primitives of the source update, (rho, v_R, v_phi, v_Z) with v_phi = l / R.
-__global__ void prim_kernel(int ns, int nc, const double *__restrict__ Q, const double *__restrict__ Rcell,
+__global__ void prim_kernel(int ns, int nc, const double *__restrict__ Q, const double *__restrict__ iRcell,
                             double *__restrict__ P)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -126,9 +149,14 @@ __global__ void prim_kernel(int ns, int nc, const double *__restrict__ Q, const 
     const size_t pl = (size_t)ns * nc, e = (size_t)s * nc + c;
     const double rho = Q[e];
     double v1 = 0.0, v2 = 0.0, v3 = 0.0;
-    if (rho > 0.0) {
+    if (rho >= 1e-300) {
+        const double r = 1.0 / rho;
+        v1 = Q[pl + e] * r;
+        v2 = Q[2 * pl + e] * r * iRcell[c];
+        v3 = Q[3 * pl + e] * r;
+    } else if (rho > 0.0) {
         v1 = Q[pl + e] / rho;
-        v2 = Q[2 * pl + e] / rho / Rcell[c];
+        v2 = Q[2 * pl + e] / rho * iRcell[c];
         v3 = Q[3 * pl + e] / rho;
     }
     P[e] = rho;
@@ -138,46 +166,86 @@ __global__ void prim_kernel(int ns, int nc, const double *__restrict__ Q, const 
 }
 
 // Generalised van Leer slope of a cell (forward and backward slopes per unit
-// length between centres, grid factors c_F, c_B; zero at an extremum).
-__device__ __forceinline__ double vl_slope(double sF, double sB, double cF, double cB)
+// length between centres, grid factors c_F, c_B, cs = c_F + c_B - 2; zero at
+// an extremum).
+__device__ __forceinline__ double vl_slope(double sF, double sB, double cF, double cB, double cs)
 {
     if (!(sF * sB > 0.0)) return 0.0;
-    const double den = sB * sB + (cF + cB - 2.0) * sF * sB + sF * sF;
+    const double den = sB * sB + cs * sF * sB + sF * sF;
     return den != 0.0 ? sF * sB * (cF * sB + cB * sF) / den : 0.0;
 }
 
-// Face values of a cell along one direction: centre x, neighbours' centres
-// xm, xp, the cell's edges elo, ehi; q the values (qm, q, qp).
-__device__ __forceinline__ void plm(double qm, double q, double qp, double xm, double x, double xp, double elo,
-                                    double ehi, double &at_lo, double &at_hi)
+// Limited slopes of the four primitives per ghosted cell and species, along
+// R (rows NG - 1 .. NG + n_R of the active columns) and along theta (columns
+// NG - 1 .. NG + n_Z of the active rows), for the
+// second-order face states: each cell's slopes are computed once here rather
+// than once for each of its faces in the flux kernels.
+__global__ void slope_kernel(TView t, const double *__restrict__ Pg, double *__restrict__ SR,
+                             double *__restrict__ SZ)
 {
-    const double sF = (qp - q) / (xp - x), sB = (q - qm) / (x - xm);
-    const double s = vl_slope(sF, sB, (xp - x) / (ehi - x), (x - xm) / (x - elo));
-    at_lo = q + s * (elo - x);
-    at_hi = q + s * (ehi - x);
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    const int ng = t.nRg * t.nZg;
+    if (g >= ng) return;
+    const int gi = g / t.nZg, gj = g - gi * t.nZg;
+    const size_t pg = (size_t)t.ns * ng, o = (size_t)s * ng + g;
+    // R slopes of the cells beside a radial face (active columns), theta
+    // slopes of the cells beside a polar face (active rows)
+    const bool acol = gj >= NG && gj < NG + t.nZ, arow = gi >= NG && gi < NG + t.nR;
+    const bool rok = acol && gi >= NG - 1 && gi <= NG + t.nR, zok = arow && gj >= NG - 1 && gj <= NG + t.nZ;
+    if (!rok && !zok) return;
+    const double *gr = t.gR, *gz = t.gZ;
+    const int nRg = t.nRg, nZg = t.nZg;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const double *P = Pg + q * pg + o;
+        const double c = P[0];
+        if (rok) {
+            const double sF = (P[nZg] - c) * gr[G_IF * nRg + gi], sB = (c - P[-nZg]) * gr[G_IF * nRg + gi - 1];
+            SR[q * pg + o] = vl_slope(sF, sB, gr[G_CF * nRg + gi], gr[G_CB * nRg + gi], gr[G_CS * nRg + gi]);
+        }
+        if (zok) {
+            const double sF = (P[1] - c) * gz[G_IF * nZg + gj], sB = (c - P[-1]) * gz[G_IF * nZg + gj - 1];
+            SZ[q * pg + o] = vl_slope(sF, sB, gz[G_CF * nZg + gj], gz[G_CB * nZg + gj], gz[G_CS * nZg + gj]);
+        }
+    }
 }
 
 // Upwind flux of the pressureless Riemann problem for face states (rho, v_R,
-// l, v_Z) with normal velocities uL, uR.
+// l, v_Z) with normal velocities uL, uR.  The upwind side is the sign of the
+// Roe-averaged velocity (sqrt(rho_L) uL + sqrt(rho_R) uR) / (sqrt(rho_L) +
+// sqrt(rho_R)); only its sign is used, and that sign is fixed without the
+// square roots: it is the common sign of the two terms where they agree,
+// and where uL > 0 > uR the sign of rho_L uL^2 - rho_R uR^2 (both sides of
+// the comparison squared).  A zero average (no mass on either side, or equal
+// and opposite terms) takes the mean of the two one-sided fluxes.
 __device__ __forceinline__ void riemann(const double (&L)[4], const double (&R)[4], double uL, double uR,
                                         double (&F)[4])
 {
-    const double sl = sqrt(fmax(L[0], 0.0)), sr = sqrt(fmax(R[0], 0.0));
-    const double den = sl + sr;
-    const double vhat = den > 0.0 ? (sl * uL + sr * uR) / den : 0.0;
+    const double rl = fmax(L[0], 0.0), rr = fmax(R[0], 0.0);
+    const double tl = rl > 0.0 ? uL : 0.0, tr = rr > 0.0 ? uR : 0.0;   // signs of the two terms
+    int sg;
+    if (tl >= 0.0 && tr >= 0.0) sg = (tl > 0.0 || tr > 0.0) ? 1 : 0;
+    else if (tl <= 0.0 && tr <= 0.0) sg = -1;
+    else if (tl > 0.0) {
+        const double pl = rl * uL * uL, pr = rr * uR * uR;
+        sg = pl > pr ? 1 : pl < pr ? -1 : 0;
+    } else sg = 0;                                 // uL < 0 < uR: the vacuum case below
     const double fl[4] = {L[0] * uL, L[0] * L[1] * uL, L[0] * L[2] * uL, L[0] * L[3] * uL};
     const double fr[4] = {R[0] * uR, R[0] * R[1] * uR, R[0] * R[2] * uR, R[0] * R[3] * uR};
     const bool vac = uL < 0.0 && uR > 0.0;
 #pragma unroll
     for (int f = 0; f < 4; f++)
-        F[f] = vac ? 0.0 : vhat > 0.0 ? fl[f] : vhat < 0.0 ? fr[f] : 0.5 * (fl[f] + fr[f]);
+        F[f] = vac ? 0.0 : sg > 0 ? fl[f] : sg < 0 ? fr[f] : 0.5 * (fl[f] + fr[f]);
 }
 
 // Fluxes (per unit area) through the radial faces: thread (s, a, jj), face
 // at ghosted edge i + 1 = NG + a between cells (i, j) and (i + 1, j), j =
-// NG + jj.  Order 1: donor cell; order 2: limited linear states.
+// NG + jj.  Order 1: donor cell; order 2: the cells' limited linear states
+// at the face (slopes from slope_kernel).
 template <int Order>
-__global__ void flux_R_kernel(TView t, const double *__restrict__ Pg, const double *__restrict__ cR,
+__global__ void flux_R_kernel(TView t, const double *__restrict__ Pg, const double *__restrict__ SR,
+                              const double *__restrict__ U, const double *__restrict__ cR,
                               double *__restrict__ FR)
 {
     const int nf = (t.nR + 1) * t.nZ;
@@ -187,36 +255,28 @@ __global__ void flux_R_kernel(TView t, const double *__restrict__ Pg, const doub
     const int a = f / t.nZ, jj = f - a * t.nZ;
     const int i = NG - 1 + a, j = NG + jj;
     const size_t ng = (size_t)t.nRg * t.nZg, pg = (size_t)t.ns * ng;
-    const double *P = Pg + (size_t)s * ng;
-    auto at = [&](int comp, int gi, int gj) { return P[comp * pg + (size_t)gi * t.nZg + gj]; };
+    const size_t ok = (size_t)s * ng + (size_t)i * t.nZg + j, ol = ok + t.nZg;   // cells (i, j), (i + 1, j)
     double L[4], R[4];
-    if (Order == 1) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) { L[q] = at(q, i, j); R[q] = at(q, i + 1, j); }
-    } else {
-        const double *x = t.Rc, *e = t.Re;
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            double lo, hi, lo2, hi2;
-            plm(at(q, i - 1, j), at(q, i, j), at(q, i + 1, j), x[i - 1], x[i], x[i + 1], e[i], e[i + 1], lo, hi);
-            plm(at(q, i, j), at(q, i + 1, j), at(q, i + 2, j), x[i], x[i + 1], x[i + 2], e[i + 1], e[i + 2], lo2, hi2);
-            L[q] = hi;
-            R[q] = lo2;
+    for (int q = 0; q < 4; q++) {
+        L[q] = Pg[q * pg + ok];
+        R[q] = Pg[q * pg + ol];
+        if (Order == 2) {
+            L[q] += SR[q * pg + ok] * t.gR[G_HI * t.nRg + i];
+            R[q] += SR[q * pg + ol] * t.gR[G_LO * t.nRg + i + 1];
         }
     }
     double F[4];
     riemann(L, R, L[1], R[1], F);
     if (t.nu) {
-        const double u_k = at(0, i, j) / t.rho_g[active_cell(t, i, j)];
-        const double u_l = at(0, i + 1, j) / t.rho_g[active_cell(t, i + 1, j)];
-        const double u_m = at(0, i, j - 1) / t.rho_g[active_cell(t, i, j - 1)];
-        const double u_p = at(0, i + 1, j + 1) / t.rho_g[active_cell(t, i + 1, j + 1)];
-        const double d = (cR[f] * u_k + cR[nf + f] * u_l + cR[2 * nf + f] * u_m + cR[3 * nf + f] * u_p) / t.Sc[s];
-        const double *U = d > 0.0 ? L : R;
+        // partners: (i, j - 1) of the low-R cell, (i + 1, j + 1) of the high-R cell
+        const double d = cR[f] * U[ok] + cR[nf + f] * U[ol] + cR[2 * nf + f] * U[ok - 1] +
+                         cR[3 * nf + f] * U[ol + 1];
+        const double *W = d > 0.0 ? L : R;
         F[0] += d;
-        F[1] += d * U[1];
-        F[2] += d * U[2];
-        F[3] += d * U[3];
+        F[1] += d * W[1];
+        F[2] += d * W[2];
+        F[3] += d * W[3];
     }
     const bool shut = (a == 0 && t.bc[0] == CUDISC_BC_CLOSED) || (a == t.nR && t.bc[1] == CUDISC_BC_CLOSED);
     const size_t fs = (size_t)t.ns * nf, o = (size_t)s * nf + f;
@@ -228,7 +288,8 @@ __global__ void flux_R_kernel(TView t, const double *__restrict__ Pg, const doub
 // edge j + 1 = NG + b between cells (i, j) and (i, j + 1), i = NG + ii; the
 // flux is along the face normal (-sin theta^e, cos theta^e).
 template <int Order>
-__global__ void flux_Z_kernel(TView t, const double *__restrict__ Pg, const double *__restrict__ cZ,
+__global__ void flux_Z_kernel(TView t, const double *__restrict__ Pg, const double *__restrict__ SZ,
+                              const double *__restrict__ U, const double *__restrict__ cZ,
                               double *__restrict__ FZ)
 {
     const int nf = t.nR * (t.nZ + 1);
@@ -238,37 +299,29 @@ __global__ void flux_Z_kernel(TView t, const double *__restrict__ Pg, const doub
     const int ii = f / (t.nZ + 1), b = f - ii * (t.nZ + 1);
     const int i = NG + ii, j = NG - 1 + b;
     const size_t ng = (size_t)t.nRg * t.nZg, pg = (size_t)t.ns * ng;
-    const double *P = Pg + (size_t)s * ng;
-    auto at = [&](int comp, int gi, int gj) { return P[comp * pg + (size_t)gi * t.nZg + gj]; };
+    const size_t oa = (size_t)s * ng + (size_t)i * t.nZg + j, ol = oa + 1;       // cells (i, j), (i, j + 1)
     double L[4], R[4];
-    if (Order == 1) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) { L[q] = at(q, i, j); R[q] = at(q, i, j + 1); }
-    } else {
-        const double *x = t.tc, *e = t.te;
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            double lo, hi, lo2, hi2;
-            plm(at(q, i, j - 1), at(q, i, j), at(q, i, j + 1), x[j - 1], x[j], x[j + 1], e[j], e[j + 1], lo, hi);
-            plm(at(q, i, j), at(q, i, j + 1), at(q, i, j + 2), x[j], x[j + 1], x[j + 2], e[j + 1], e[j + 2], lo2, hi2);
-            L[q] = hi;
-            R[q] = lo2;
+    for (int q = 0; q < 4; q++) {
+        L[q] = Pg[q * pg + oa];
+        R[q] = Pg[q * pg + ol];
+        if (Order == 2) {
+            L[q] += SZ[q * pg + oa] * t.gZ[G_HI * t.nZg + j];
+            R[q] += SZ[q * pg + ol] * t.gZ[G_LO * t.nZg + j + 1];
         }
     }
     const double sn = t.sn[j + 1], cs = t.cs[j + 1];
     double F[4];
     riemann(L, R, -sn * L[1] + cs * L[3], -sn * R[1] + cs * R[3], F);
     if (t.nu) {
-        const double u_a = at(0, i, j) / t.rho_g[active_cell(t, i, j)];
-        const double u_l = at(0, i, j + 1) / t.rho_g[active_cell(t, i, j + 1)];
-        const double u_m = at(0, i - 1, j) / t.rho_g[active_cell(t, i - 1, j)];
-        const double u_b = at(0, i + 1, j + 1) / t.rho_g[active_cell(t, i + 1, j + 1)];
-        const double d = (cZ[f] * u_a + cZ[nf + f] * u_l + cZ[2 * nf + f] * u_m + cZ[3 * nf + f] * u_b) / t.Sc[s];
-        const double *U = d > 0.0 ? L : R;
+        // partners: (i - 1, j) of the lower cell, (i + 1, j + 1) of the upper cell
+        const double d = cZ[f] * U[oa] + cZ[nf + f] * U[ol] + cZ[2 * nf + f] * U[oa - t.nZg] +
+                         cZ[3 * nf + f] * U[ol + t.nZg];
+        const double *W = d > 0.0 ? L : R;
         F[0] += d;
-        F[1] += d * U[1];
-        F[2] += d * U[2];
-        F[3] += d * U[3];
+        F[1] += d * W[1];
+        F[2] += d * W[2];
+        F[3] += d * W[3];
     }
     const bool shut = (b == 0 && t.bc[2] == CUDISC_BC_CLOSED) || (b == t.nZ && t.bc[3] == CUDISC_BC_CLOSED);
     const size_t fs = (size_t)t.ns * nf, o = (size_t)s * nf + f;
@@ -290,7 +343,7 @@ __global__ void update_kernel(TView t, const double *__restrict__ Qb, const doub
     const int r0 = i * t.nZ + j, r1 = (i + 1) * t.nZ + j;          // inner, outer radial faces
     const int z0 = i * (t.nZ + 1) + j, z1 = z0 + 1;               // lower, upper polar faces
     const double ar0 = t.AR[r0], ar1 = t.AR[r1], az0 = t.AZ[z0], az1 = t.AZ[z1];
-    const double k = kdt / t.V[c];
+    const double k = kdt * t.iV[c];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
         const double *fr = FR + q * fsr + (size_t)s * nfr, *fz = FZ + q * fsz + (size_t)s * nfz;
@@ -346,6 +399,16 @@ __device__ void net_coeffs(double Dk, double Dl, double wk, double wl, double wm
     o[1] = wk * fk_l - wl * -(fl_k + fl_p);
     o[2] = wk * fk_m;
     o[3] = -wl * fl_p;
+}
+
+// Reciprocals of the gas density per cell and of the Schmidt number per
+// species, for the diffusion variable u of ghost_prim_kernel.
+__global__ void gas_recip_kernel(int nc, int ns, const double *__restrict__ rho_g, const double *__restrict__ Sc,
+                                 double *__restrict__ irg, double *__restrict__ iSc)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nc) irg[k] = 1.0 / rho_g[k];
+    if (k < ns) iSc[k] = 1.0 / Sc[k];
 }
 
 __global__ void stencil_kernel(TView t, double *__restrict__ cR, double *__restrict__ cZ)
@@ -423,6 +486,29 @@ std::vector<double> extend_centres(const double *c, const double *e, int n)
     return o;
 }
 
+// Reconstruction factors along one ghosted direction of n cells (centres x,
+// edges e): G_IF at k = 1 / (x[k + 1] - x[k]) (k < n - 1), and at cells
+// 1 .. n - 2 the limiter's c_F = (x[k + 1] - x[k]) / (e[k + 1] - x[k]),
+// c_B = (x[k] - x[k - 1]) / (x[k] - e[k]), c_F + c_B - 2, and the edge
+// offsets e[k + 1] - x[k], e[k] - x[k].
+std::vector<double> recon_factors(const std::vector<double> &x, const std::vector<double> &e)
+{
+    const int n = (int)x.size();
+    std::vector<double> g((size_t)kGeo * n, 0.0);
+    for (int k = 0; k + 1 < n; k++) g[G_IF * n + k] = 1.0 / (x[k + 1] - x[k]);
+    for (int k = 1; k + 1 < n; k++) {
+        const double cF = (x[k + 1] - x[k]) / (e[k + 1] - x[k]), cB = (x[k] - x[k - 1]) / (x[k] - e[k]);
+        g[G_CF * n + k] = cF;
+        g[G_CB * n + k] = cB;
+        g[G_CS * n + k] = cF + cB - 2.0;
+    }
+    for (int k = 0; k < n; k++) {
+        g[G_HI * n + k] = e[k + 1] - x[k];
+        g[G_LO * n + k] = e[k] - x[k];
+    }
+    return g;
+}
+
 template <class T> cudaError_t up(T **d, const std::vector<T> &h, cudaStream_t s)
 {
     cudaError_t e = cudaMalloc(d, h.size() * sizeof(T));
@@ -441,7 +527,7 @@ static void free_dust(cudisc_dust_ctx *c)
 {
     if (!c) return;
     double *ptrs[] = {c->Rc, c->tc, c->Re, c->te, c->sn, c->cs, c->V, c->AR, c->AZ, c->Rcell, c->Zcell,
-                      c->cR, c->cZ, c->Pg, c->FR, c->FZ, c->Qh, c->Pn};
+                      c->iV, c->iRcell, c->irg, c->iSc, c->cR, c->cZ, c->gR, c->gZ, c->Pg, c->FR, c->FZ, c->Qh, c->Pn, c->SR, c->SZ, c->U};
     for (double *q : ptrs)
         if (q) cudaFree(q);
     delete c;
@@ -538,12 +624,20 @@ cudisc_status cudisc_dust_init(const cudisc_dust_params *p, cudisc_dust_ctx **ou
     auto U = [&](double **d, const std::vector<double> &h) { if (e == cudaSuccess) e = up(d, h, c->stream); };
     U(&c->Rc, Rcg); U(&c->tc, tc); U(&c->Re, Re); U(&c->te, te); U(&c->sn, sn); U(&c->cs, cs);
     U(&c->V, V); U(&c->AR, AR); U(&c->AZ, AZ); U(&c->Rcell, Rcell); U(&c->Zcell, Zcell);
+    U(&c->gR, recon_factors(Rcg, Re)); U(&c->gZ, recon_factors(tc, te));
+    {
+        std::vector<double> iV(V.size()), iRc(Rcell.size());
+        for (size_t k = 0; k < V.size(); k++) { iV[k] = 1.0 / V[k]; iRc[k] = 1.0 / Rcell[k]; }
+        U(&c->iV, iV); U(&c->iRcell, iRc);
+    }
     const size_t nc = (size_t)nR * nZ, ns = c->ns;
     const size_t nfr = (size_t)(nR + 1) * nZ, nfz = (size_t)nR * (nZ + 1);
     auto A = [&](double **d, size_t n) { if (e == cudaSuccess) e = cudaMalloc(d, n * sizeof(double)); };
     A(&c->cR, 4 * nfr); A(&c->cZ, 4 * nfz);
     A(&c->Pg, 4 * ns * (size_t)nRg * nZg); A(&c->FR, 4 * ns * nfr); A(&c->FZ, 4 * ns * nfz);
     A(&c->Qh, 4 * ns * nc); A(&c->Pn, 4 * ns * nc);
+    A(&c->SR, 4 * ns * (size_t)nRg * nZg); A(&c->SZ, 4 * ns * (size_t)nRg * nZg);
+    if (p->nu) { A(&c->U, ns * (size_t)nRg * nZg); A(&c->irg, nc); A(&c->iSc, ns); }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         const cudisc_status st = e == cudaErrorMemoryAllocation ? CUDISC_ENOMEM : CUDISC_ECUDA;
@@ -566,6 +660,9 @@ cudisc_status cudisc_dust_update_gas(cudisc_dust_ctx *c)
     if (!c) return dust_fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
     if (!c->p.nu) return CUDISC_OK;
     const TView t = view(c);
+    const size_t nc = (size_t)c->nR * c->nZ, nr = nc > (size_t)c->ns ? nc : (size_t)c->ns;
+    gas_recip_kernel<<<(unsigned)((nr + kT - 1) / kT), kT, 0, c->stream>>>((int)nc, c->ns, c->p.rho_g, c->p.Sc,
+                                                                         c->irg, c->iSc);
     const size_t nf = (size_t)(c->nR + 1) * c->nZ + (size_t)c->nR * (c->nZ + 1);
     stencil_kernel<<<(unsigned)((nf + kT - 1) / kT), kT, 0, c->stream>>>(t, c->cR, c->cZ);
     DUST_TRY(c, cudaGetLastError());
@@ -584,20 +681,21 @@ cudisc_status cudisc_dust_step(cudisc_dust_ctx *c, double *Q, double dt)
     const bool src = c->p.c_s != nullptr;
     cudaStream_t s = c->stream;
     // stage 1: donor-cell fluxes at n, half step, half-step sources
-    ghost_prim_kernel<<<grid2(ng, ns), kT, 0, s>>>(t, Q, c->Pg);
-    if (src) prim_kernel<<<grid2(nc, ns), kT, 0, s>>>(ns, (int)nc, Q, c->Rcell, c->Pn);
-    flux_R_kernel<1><<<grid2(nfr, ns), kT, 0, s>>>(t, c->Pg, c->cR, c->FR);
-    flux_Z_kernel<1><<<grid2(nfz, ns), kT, 0, s>>>(t, c->Pg, c->cZ, c->FZ);
+    ghost_prim_kernel<<<grid2(ng, ns), kT, 0, s>>>(t, Q, c->Pg, c->U);
+    if (src) prim_kernel<<<grid2(nc, ns), kT, 0, s>>>(ns, (int)nc, Q, c->iRcell, c->Pn);
+    flux_R_kernel<1><<<grid2(nfr, ns), kT, 0, s>>>(t, c->Pg, c->SR, c->U, c->cR, c->FR);
+    flux_Z_kernel<1><<<grid2(nfz, ns), kT, 0, s>>>(t, c->Pg, c->SZ, c->U, c->cZ, c->FZ);
     update_kernel<<<grid2(nc, ns), kT, 0, s>>>(t, Q, c->FR, c->FZ, 0.5 * dt, c->Qh);
     DUST_TRY(c, cudaGetLastError());
     if (src)
         DUST_TRY(c, launch_dust_source(ns, (int)nc, c->Qh, c->Pn, 0.5 * dt, c->Rcell, c->Zcell, c->p.rho_g, c->p.c_s,
                                        c->p.v_g, c->p.a, c->p.rho_m, c->p.GM, s));
     // stage 2: limited linear fluxes at n + 1/2, full step, full-step sources
-    ghost_prim_kernel<<<grid2(ng, ns), kT, 0, s>>>(t, c->Qh, c->Pg);
-    if (src) prim_kernel<<<grid2(nc, ns), kT, 0, s>>>(ns, (int)nc, c->Qh, c->Rcell, c->Pn);
-    flux_R_kernel<2><<<grid2(nfr, ns), kT, 0, s>>>(t, c->Pg, c->cR, c->FR);
-    flux_Z_kernel<2><<<grid2(nfz, ns), kT, 0, s>>>(t, c->Pg, c->cZ, c->FZ);
+    ghost_prim_kernel<<<grid2(ng, ns), kT, 0, s>>>(t, c->Qh, c->Pg, c->U);
+    if (src) prim_kernel<<<grid2(nc, ns), kT, 0, s>>>(ns, (int)nc, c->Qh, c->iRcell, c->Pn);
+    slope_kernel<<<grid2(ng, ns), kT, 0, s>>>(t, c->Pg, c->SR, c->SZ);
+    flux_R_kernel<2><<<grid2(nfr, ns), kT, 0, s>>>(t, c->Pg, c->SR, c->U, c->cR, c->FR);
+    flux_Z_kernel<2><<<grid2(nfz, ns), kT, 0, s>>>(t, c->Pg, c->SZ, c->U, c->cZ, c->FZ);
     update_kernel<<<grid2(nc, ns), kT, 0, s>>>(t, Q, c->FR, c->FZ, dt, Q);
     DUST_TRY(c, cudaGetLastError());
     if (src)

@@ -184,3 +184,29 @@ def test_bench_grid_with_sources_conserves_mass(coag_mod):
     assert torch.all(torch.abs(m1 / m0 - 1) < 1e-13), (m1 / m0 - 1).abs().max().item()
     assert torch.isfinite(q).all()
     gpu.close()
+
+
+def test_update_gas_matches_a_fresh_context(coag_mod):
+    """Changing rho_g, nu and Sc in place, then cudisc_dust_update_gas, gives
+    the step of a context built on the new gas, bitwise (the stencil and the
+    cached reciprocals of rho_g and Sc are rebuilt)."""
+    nR, nZ, ns = 21, 17, 4
+    R_e, th_e, Q, rho_g, nu, Sc, src = disc_setup(nR, nZ, ns, seed=41)
+    rng = np.random.default_rng(42)
+    rho_g2, nu2, Sc2 = rho_g * (1 + 0.2 * rng.random(rho_g.shape)), nu * 1.7, Sc * 0.8
+    a = coag_mod.DustTransport(R_e, th_e, ns, rho_g, nu=nu, Sc=Sc, bc=BCS["paper"])
+    b = coag_mod.DustTransport(R_e, th_e, ns, rho_g2, nu=nu2, Sc=Sc2, bc=BCS["paper"])
+    dt = 0.3 * T.Transport(T.Grid(R_e, th_e), rho_g2, nu=nu2, Sc=Sc2).cfl_dt(Q)
+    a.gas("rho_g").copy_(torch.as_tensor(rho_g2))
+    a.gas("nu").copy_(torch.as_tensor(nu2))
+    a.gas("Sc").copy_(torch.as_tensor(Sc2))
+    a.update_gas()
+    qa = torch.as_tensor(Q, device="cuda").contiguous()
+    qb = qa.clone()
+    for _ in range(2):
+        a.step(qa, dt)
+        b.step(qb, dt)
+    torch.cuda.synchronize()
+    assert torch.equal(qa, qb)
+    a.close()
+    b.close()
