@@ -799,10 +799,15 @@ def main():
                        **({"vertical": 1} if disc.vertical else {}),
                        "step": "state copy-in + kernel build + BS3 integration of all cells over t_span, "
                                "one CUDA graph replay",
-                       "accuracy_scope": "1e-5 holds per right-hand side relative to each bin's collision flux against the FP64 GPU path (accuracy.mixed.rhs_vs_fp64_gpu_over_bin_flux_max; the literal FP64 oracle itself is off by up to ~2 % in bins fed by sweep-up remnants) and over "
-                                         "spans short of the coagulation-fragmentation balance; over the full "
-                                         "1e4 yr it holds on the fraction of bins in accuracy.frac_bins_within_1e-5 "
-                                         "(the FP64 GPU path also misses it once rtol <= 1e-3)",
+                       "accuracy_scope": "per right-hand side the mixed path differs from the FP64 GPU path by "
+                                         "about 1e-5 of each bin's collision flux at most (accuracy.mixed."
+                                         "rhs_vs_fp64_gpu_over_bin_flux_max; the FP32 accumulation of ~2900 split "
+                                         "products per partial row sets that level; the literal FP64 oracle itself is "
+                                         "off by up to ~2 % in bins fed by sweep-up remnants); bin densities hold "
+                                         "1e-5 |rho| + 1e-10 sum(rho) over spans short of the coagulation-"
+                                         "fragmentation balance (tests, 50-1000 yr); over the full 1e4 yr they hold "
+                                         "on the fraction of bins in accuracy.mixed.frac_bins_within_1e-5 (the FP64 "
+                                         "GPU path also misses it once rtol <= 1e-3); total mass to 1e-9 (mass_err_max)",
                        **({"state": "FP32 pair y/Sx = yh + yl (48 bits), FP64 time and step size",
                            "mixed_cluster": P, "slot_groups": G}
                           if args.precision == "mixed" else {})},

@@ -68,9 +68,12 @@ CASES = {
     "N129_3_cells": lambda: synth.make_disc(1, 3, 129, 1e-5, 10.0, 10.0, 10.0, 20.0, seed=13),
     "N150_9_cells": lambda: synth.make_disc(3, 3, 150, 1e-5, 100.0, 5.0, 100.0, 20.0, alpha=1e-4,
                                             v_frag=1000.0, seed=14),
+    # the largest bin count the library takes (MMA N of 160 per tile)
+    "N160_4_cells": lambda: synth.make_disc(2, 2, 160, 1e-5, 300.0, 5.0, 100.0, 20.0, alpha=1e-4,
+                                            v_frag=1000.0, seed=15),
 }
 SMALL = ["N2_one_cell", "N17_37_cells", "column_1x32_N50", "N128_5_cells", "N129_3_cells",
-         "N150_9_cells"]
+         "N150_9_cells", "N160_4_cells"]
 
 
 def sample_of(d, k=24):

@@ -210,3 +210,26 @@ def test_update_gas_matches_a_fresh_context(coag_mod):
     assert torch.equal(qa, qb)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 6), (6, 1), (2, 2)])
+@pytest.mark.parametrize("bc", list(BCS))
+def test_degenerate_grids_match_oracle(coag_mod, shape, bc):
+    """One or two cells along a direction: every face is a boundary face or
+    borders a ghost cell, and the stencil partners are ghosts.  Diffusion and
+    sources on, two steps against the oracle."""
+    nR, nZ = shape
+    ns = 2
+    R_e, th_e, Q, rho_g, nu, Sc, src = disc_setup(nR, nZ, ns, seed=5 + nR + 7 * nZ, R0=5.0, R1=6.0)
+    g = T.Grid(R_e, th_e)
+    tr = T.Transport(g, rho_g, nu=nu, Sc=Sc, bc=BCS[bc], floor=1e-25, sources=src)
+    gpu = coag_mod.DustTransport(R_e, th_e, ns, rho_g, nu=nu, Sc=Sc, bc=BCS[bc], floor=1e-25, sources=src)
+    q = torch.as_tensor(Q, device="cuda").contiguous()
+    want = Q
+    for _ in range(2):
+        dt = min(0.5 * tr.cfl_dt(want), 0.02 / math.sqrt(G_M / R_e[0] ** 3))
+        want = tr.step(want, dt)
+        gpu.step(q, dt)
+    torch.cuda.synchronize()
+    compare(q.cpu().numpy(), want)
+    gpu.close()
