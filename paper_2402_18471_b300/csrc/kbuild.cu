@@ -261,7 +261,10 @@ __global__ void __launch_bounds__(256) kbuild32_kernel(
     const int CS = kb_cell_stride(NR, vertical);
     const int cell0 = blockIdx.x * kPosTile;
     __shared__ int s_cell[kPosTile];
-    if (threadIdx.x < kPosTile) s_cell[threadIdx.x] = cell0 + threadIdx.x < n_cells ? cell0 + threadIdx.x : -1;
+    if (threadIdx.x < kPosTile) {
+        const int c = cell0 + (int)threadIdx.x;
+        s_cell[threadIdx.x] = c < n_cells ? c : -1;
+    }
     __syncthreads();
     for (int t = threadIdx.x; t < kPosTile * P3_HH * NR; t += blockDim.x) {
         const int jc = t / (P3_HH * NR), r = t - jc * (P3_HH * NR);
