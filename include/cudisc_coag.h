@@ -152,6 +152,22 @@ typedef struct {
                                     does not fit, single CTAs); 1 = single CTAs;
                                     0 = chosen at init (see
                                     cudisc_coag_mixed_pair). */
+    int mixed_tile_stages;       /* CUDISC_MIXED_TF32 only: depth of the
+                                    shared-memory ring of mapping tiles, in
+                                    stages of two 16-pair blocks (1..4; 1 only
+                                    with one CTA per group; CTA pairs 2..8);
+                                    0 = chosen at init */
+    int mixed_k_stages;          /* CUDISC_MIXED_TF32 only: depth of the
+                                    shared-memory ring of the slots' K tables
+                                    (1..4); 0 = chosen at init.  With either
+                                    ring given, the rings take shared memory
+                                    first and the per-slot integrator state
+                                    follows only if it still fits (else it
+                                    lives in the context's device workspace);
+                                    cudisc_coag_init returns CUDISC_EINVAL
+                                    when no cluster size takes the rings.
+                                    The results do not depend on either
+                                    depth, only the speed. */
 } cudisc_coag_params;
 
 typedef struct {
@@ -504,6 +520,14 @@ cudisc_status cudisc_coag_mixed_cluster(const cudisc_coag_ctx *ctx, int *cluster
  * pairs (see mixed_pair), else 0 (also for an FP64 context).  EINVAL for a
  * NULL argument.  Host only. */
 cudisc_status cudisc_coag_mixed_pair(const cudisc_coag_ctx *ctx, int *pair);
+
+/* Ring depths of the mixed-precision kernel of this context: *tile_stages
+ * (mapping tiles) and *k_stages (K tables), in stages of two blocks, and
+ * *state_in_smem = 1 when the per-slot integrator state is in shared memory
+ * (0: in the device workspace).  All 0 for an FP64 context.  EINVAL for a
+ * NULL argument.  Host only. */
+cudisc_status cudisc_coag_mixed_rings(const cudisc_coag_ctx *ctx, int *tile_stages, int *k_stages,
+                                      int *state_in_smem);
 
 /* Vector-Jacobian product of the integration (the paper has no adjoint; this
  * is the discrete adjoint of the BS3 map of Sec. 5 with the step sizes held

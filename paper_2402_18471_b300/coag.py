@@ -44,6 +44,7 @@ class cudisc_coag_params(C.Structure):
         ("mixed_cluster", C.c_int),
         ("max_sms", C.c_int),
         ("vertical", C.c_int), ("mixed_pair", C.c_int),
+        ("mixed_tile_stages", C.c_int), ("mixed_k_stages", C.c_int),
     ]
 
 
@@ -117,6 +118,7 @@ def lib():
         L.cudisc_coag_mixed_cluster.argtypes = [v, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.cudisc_coag_scratch_bytes.argtypes = [v, C.POINTER(C.c_size_t)]
         L.cudisc_coag_mixed_pair.argtypes = [v, C.POINTER(C.c_int)]
+        L.cudisc_coag_mixed_rings.argtypes = [v, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.cudisc_coag_set_fault_injection.argtypes = [v, C.c_longlong, C.c_int]
         L.cudisc_partition.argtypes = [C.c_int, v, C.c_int, v]
         L.cudisc_dust_init.argtypes = [C.POINTER(cudisc_dust_params), C.POINTER(v)]
@@ -136,7 +138,7 @@ def lib():
                    "cudisc_coag_rhs", "cudisc_coag_step", "cudisc_coag_set_records",
                    "cudisc_coag_replay", "cudisc_coag_step_static_scratch",
                    "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp",
-                   "cudisc_coag_mixed_cluster", "cudisc_coag_scratch_bytes", "cudisc_coag_mixed_pair", "cudisc_coag_set_fault_injection", "cudisc_partition", "cudisc_dust_init", "cudisc_dust_update_gas",
+                   "cudisc_coag_mixed_cluster", "cudisc_coag_scratch_bytes", "cudisc_coag_mixed_pair", "cudisc_coag_mixed_rings", "cudisc_coag_set_fault_injection", "cudisc_partition", "cudisc_dust_init", "cudisc_dust_update_gas",
                    "cudisc_dust_step", "cudisc_dust_geometry", "cudisc_coag_step_async", "cudisc_coag_step_wait",
                    "cudisc_coag_init_batched", "cudisc_coag_batch_ctx", "cudisc_coag_batch_build_kernel",
                    "cudisc_dust_source_update", "cudisc_dust_cfl_dt", "cudisc_hse_rho_gas", "cudisc_coag_batch_step", "cudisc_coag_step_spans", "cudisc_coag_subcycle",
@@ -507,6 +509,8 @@ class Coag:
         p.max_sms = int(s.get("max_sms", 0))
         p.vertical = int(s.get("vertical", 0))
         p.mixed_pair = int(s.get("mixed_pair", 0))
+        p.mixed_tile_stages = int(s.get("mixed_tile_stages", 0))
+        p.mixed_k_stages = int(s.get("mixed_k_stages", 0))
         self.params = p
 
     def close(self):
@@ -546,6 +550,13 @@ class Coag:
     def mixed_cluster(self) -> tuple:
         """(CTAs per group of 64 slots, groups) of the mixed kernel."""
         return cudisc_coag_mixed_cluster(self.ctx)
+
+    def mixed_rings(self) -> tuple:
+        """(mapping-tile stages, K-table stages, per-slot state in shared
+        memory 0/1) of the mixed kernel."""
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().cudisc_coag_mixed_rings(self.ctx, C.byref(a), C.byref(b), C.byref(c)), self.ctx)
+        return a.value, b.value, c.value
 
     def get_kernel(self):
         t = self.torch
@@ -707,18 +718,24 @@ def autotune_cluster(disc, t_probe=None, candidates=(1, 2, 4, 8), cache_path=Non
     return int(best)
 
 
-def autotune_launch(disc, t_probe=None, clusters=(1, 2, 4, 8), pairs=(1, 2), cache_path=None, device="cuda",
-                    **over):
+RING_CANDIDATES = ((2, 1), (2, 2), (2, 3), (2, 4), (3, 1), (3, 2), (4, 1))
+
+
+def autotune_launch(disc, t_probe=None, clusters=(1, 2, 4, 8), pairs=(1, 2), rings=RING_CANDIDATES,
+                    cache_path=None, device="cuda", **over):
     """Measured choice of the mixed kernel's launch layout for this problem:
     the cluster size (mixed_cluster: CTAs that split each pass of a slot
-    group) and the CTA-pair mode (mixed_pair = 2: two CTAs share each
-    M = 256 tensor-core MMA, each keeping half of every mapping tile; 1:
-    single CTAs).  Every layout that fits gets one warm-up and one timed
-    integration over t_probe (default: a tenth of disc.t_span) from
-    disc.rho0; the best accepted cell-substeps per second wins.  With
-    cache_path the results are kept in a JSON file keyed by (bins, cells,
-    precision) and later calls read them instead of measuring.  Returns
-    {"mixed_cluster": P, "mixed_pair": 1 or 2}, to pass to Coag."""
+    group), the CTA-pair mode (mixed_pair = 2: two CTAs share each M = 256
+    tensor-core MMA, each keeping half of every mapping tile; 1: single
+    CTAs), then, for the best of those, the shared-memory ring depths
+    (mixed_tile_stages, mixed_k_stages; (0, 0) = the library's own choice,
+    which puts the per-slot state in shared memory first).  Every layout
+    that fits gets one warm-up and one timed integration over t_probe
+    (default: a tenth of disc.t_span) from disc.rho0; the best accepted
+    cell-substeps per second wins.  With cache_path the results are kept in
+    a JSON file keyed by (bins, cells, precision) and later calls read them
+    instead of measuring.  Returns {"mixed_cluster": P, "mixed_pair": 1 or
+    2, "mixed_tile_stages": SB, "mixed_k_stages": KS}, to pass to Coag."""
     import json
     import torch
     key = f"N{disc.n_bins}_cells{disc.n_cells}_mixed_launch"
@@ -729,26 +746,47 @@ def autotune_launch(disc, t_probe=None, clusters=(1, 2, 4, 8), pairs=(1, 2), cac
         if key in cache:
             return dict(cache[key]["best"])
     t = disc.t_span / 10.0 if t_probe is None else float(t_probe)
+
+    def probe(P, pair, sb, ks):
+        try:
+            g = Coag(disc, "mixed", device=device, mixed_cluster=P, mixed_pair=pair, mixed_tile_stages=sb,
+                     mixed_k_stages=ks, **over)
+        except CoagError as e:
+            if e.status == EINVAL and (sb or ks):
+                return None                    # these rings do not fit
+            raise
+        try:
+            if g.mixed_cluster()[0] != P or g.mixed_pair() != (1 if pair == 2 else 0):
+                return None                    # the library fell back: this layout does not fit
+            if (sb or ks) and g.mixed_rings()[:2] != (sb, ks):
+                return None
+            for rep in range(2):
+                y = g.state(disc.rho0)
+                st = g.step(y, t)
+            return st["accepted"] / max(st["elapsed_ms"], 1e-9) * 1e3
+        finally:
+            g.close()
+            torch.cuda.synchronize()
+
     rates = {}
     for pair in pairs:
         for P in clusters:
-            g = Coag(disc, "mixed", device=device, mixed_cluster=P, mixed_pair=pair, **over)
-            try:
-                if g.mixed_cluster()[0] != P or g.mixed_pair() != (1 if pair == 2 else 0):
-                    continue                   # the library fell back: this layout does not fit
-                for rep in range(2):
-                    y = g.state(disc.rho0)
-                    st = g.step(y, t)
-                rates[(P, pair)] = st["accepted"] / max(st["elapsed_ms"], 1e-9) * 1e3
-            finally:
-                g.close()
-                torch.cuda.synchronize()
+            r = probe(P, pair, 0, 0)
+            if r is not None:
+                rates[(P, pair, 0, 0)] = r
     if not rates:
         raise CoagError(ENOTSUP, "no launch layout fits this problem")
-    P, pair = max(rates, key=rates.get)
-    best = {"mixed_cluster": int(P), "mixed_pair": int(pair)}
+    P, pair, _, _ = max(rates, key=rates.get)
+    for sb, ks in rings:
+        r = probe(P, pair, sb, ks)
+        if r is not None:
+            rates[(P, pair, sb, ks)] = r
+    P, pair, sb, ks = max(rates, key=rates.get)
+    best = {"mixed_cluster": int(P), "mixed_pair": int(pair), "mixed_tile_stages": int(sb),
+            "mixed_k_stages": int(ks)}
     if cache_path:
-        cache[key] = {"best": best, "rates": {f"P{k[0]}_pair{k[1]}": v for k, v in rates.items()}, "t_probe": t}
+        cache[key] = {"best": best, "rates": {f"P{k[0]}_pair{k[1]}_sb{k[2]}_ks{k[3]}": v for k, v in rates.items()},
+                      "t_probe": t}
         d = os.path.dirname(os.path.abspath(cache_path))
         os.makedirs(d, exist_ok=True)
         with open(cache_path, "w") as f:

@@ -247,6 +247,14 @@ static cudisc_status validate(const cudisc_coag_params *p, std::string &why)
         return CUDISC_EINVAL;
     }
     if (p->max_sms < 0) { why = "max_sms must be >= 0 (0: all SMs)"; return CUDISC_EINVAL; }
+    if (p->mixed_tile_stages < 0 || p->mixed_tile_stages > 8) {
+        why = "mixed_tile_stages must be 0 (automatic) or 1..8";
+        return CUDISC_EINVAL;
+    }
+    if (p->mixed_k_stages < 0 || p->mixed_k_stages > 4) {
+        why = "mixed_k_stages must be 0 (automatic) or 1..4";
+        return CUDISC_EINVAL;
+    }
     if (p->vertical != 0 && p->vertical != 1) { why = "vertical must be 0 or 1"; return CUDISC_EINVAL; }
     if (!(p->rho_m > 0) || !(p->mu > 0) || !(p->Mstar > 0) || !(p->k_B > 0) || !(p->m_H > 0) ||
         !(p->G > 0) || !(p->sigma_H2 > 0)) {
@@ -474,8 +482,15 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
             e = cudaMalloc(&c->d_K64, nc * (size_t)c->Np * sizeof(double2));
         else
         {
-            cdc::mixed_layout(c->n_cells, c->N, params->mixed_cluster, params->max_sms, params->mixed_pair,
-                              &c->mix_P, &c->mix_G, &c->mix_C, &c->mix_pair);
+            const bool fits = cdc::mixed_layout(c->n_cells, c->N, params->mixed_cluster, params->max_sms,
+                                                params->mixed_pair, params->mixed_tile_stages,
+                                                params->mixed_k_stages, &c->mix_P, &c->mix_G, &c->mix_C,
+                                                &c->mix_pair);
+            if (!fits && (params->mixed_tile_stages || params->mixed_k_stages)) {
+                free_ctx(c);
+                return fail(nullptr, CUDISC_EINVAL,
+                            "mixed_tile_stages / mixed_k_stages do not fit the shared memory at this size");
+            }
             e = cudaMalloc(&c->d_K32, (size_t)c->n_cells * c->n_blk * cdc::kBlkPairs * sizeof(float2));
             // the slot groups' tables: [group][block][8 chunks][64 slots] x 16 B
             // (zeroed: slots that never hold a cell multiply zero stage inputs by it)
@@ -485,7 +500,8 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
         }
     }
     if (e == cudaSuccess && params->precision == CUDISC_MIXED_TF32) {
-        c->work_bytes = cdc::mixed_workspace_bytes(c->n_cells, c->N, c->mix_P, params->max_sms, c->mix_pair);
+        c->work_bytes = cdc::mixed_workspace_bytes(c->n_cells, c->N, c->mix_P, params->max_sms, c->mix_pair,
+                                                   params->mixed_tile_stages, params->mixed_k_stages);
         e = cudaMalloc(&c->d_work, c->work_bytes);
     }
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
@@ -532,6 +548,17 @@ cudisc_status cudisc_coag_mixed_pair(const cudisc_coag_ctx *c, int *pair)
     if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
     if (!pair) return CUDISC_EINVAL;
     *pair = c->p.precision == CUDISC_MIXED_TF32 ? c->mix_pair : 0;
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_coag_mixed_rings(const cudisc_coag_ctx *c, int *tile_stages, int *k_stages, int *state_in_smem)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!tile_stages || !k_stages || !state_in_smem) return CUDISC_EINVAL;
+    *tile_stages = *k_stages = *state_in_smem = 0;
+    if (c->p.precision == CUDISC_MIXED_TF32)
+        cdc::mixed_rings(c->n_cells, c->N, c->mix_P, c->p.max_sms, c->mix_pair, c->p.mixed_tile_stages,
+                         c->p.mixed_k_stages, tile_stages, k_stages, state_in_smem);
     return CUDISC_OK;
 }
 
@@ -819,8 +846,10 @@ cudisc_status cudisc_coag_scratch_bytes(const cudisc_coag_ctx *c, size_t *bytes)
 {
     if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
     if (!bytes) return CUDISC_EINVAL;
-    *bytes = c->p.precision == CUDISC_MIXED_TF32 ? cdc::mixed_scratch_bytes(c->n_cells, c->N, c->mix_P, c->p.max_sms, c->mix_pair)
-                                                 : 0;
+    *bytes = c->p.precision == CUDISC_MIXED_TF32
+                 ? cdc::mixed_scratch_bytes(c->n_cells, c->N, c->mix_P, c->p.max_sms, c->mix_pair,
+                                            c->p.mixed_tile_stages, c->p.mixed_k_stages)
+                 : 0;
     return CUDISC_OK;
 }
 

@@ -157,11 +157,14 @@ cudaError_t launch_rhs_mixed(const cudisc_coag_ctx *c, const double *rho, double
 cudaError_t launch_step_mixed(const cudisc_coag_ctx *c, double *rho, double t_span,
                               double *dt_cell, const double *replay_h,
                               const long long *replay_n, long long replay_stride, WorkList wl = WorkList());
-size_t mixed_workspace_bytes(int n_cells, int N, int P, int max_sms, int pair);
+size_t mixed_workspace_bytes(int n_cells, int N, int P, int max_sms, int pair, int sb_req, int ks_req);
 // CTAs per slot group P for a request P_req (0: automatic), groups of slots G,
 // initial cells per group C and CTA-pair mode (pair_req: 0 automatic, 1 off,
 // 2 on) of the mixed kernel
-void mixed_layout(int n_cells, int N, int P_req, int max_sms, int pair_req, int *P, int *G, int *C, int *pair);
+bool mixed_layout(int n_cells, int N, int P_req, int max_sms, int pair_req, int sb_req, int ks_req, int *P, int *G,
+                  int *C, int *pair);
+void mixed_rings(int n_cells, int N, int P, int max_sms, int pair, int sb_req, int ks_req, int *SB, int *KS,
+                 int *state_smem);
 // hydrostatic-equilibrium gas density (hse.cu)
 cudaError_t launch_hse(int n_R, int n_Z, const double *R, const double *Z, const double *T, const double *V,
                        const double *R_edges, const double *Sigma_g, double mu, double m_H, double k_B,
@@ -192,5 +195,5 @@ cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_s
                                      double *dt_cell, bool *too_big);
 // bytes of global scratch the mixed integration's per-slot state takes (0:
 // it is kept in shared memory)
-size_t mixed_scratch_bytes(int n_cells, int N, int P, int max_sms, int pair);
+size_t mixed_scratch_bytes(int n_cells, int N, int P, int max_sms, int pair, int sb_req, int ks_req);
 } // namespace cdc

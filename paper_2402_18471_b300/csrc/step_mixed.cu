@@ -1521,7 +1521,11 @@ int max_clusters(int P, size_t smem, int n_sm, bool pair = false)   // P: the cl
 // pass per CTA, or no cluster of P resident).
 // pair: CTA pairs share M = 256 MMAs, a cluster of 2 P CTAs serving two
 // groups of 64 slots (each CTA keeps half of every mapping tile)
-Config config_for(int n_cells, int N, int P, int n_sm, bool pair = false)   // n_sm: the SMs this launch may occupy
+// sb_req, ks_req > 0: exactly that many mapping-tile / K-table stages (the
+// per-slot state then takes shared memory only if it still fits); 0: the
+// automatic choice below.
+Config config_for(int n_cells, int N, int P, int n_sm, bool pair = false, int sb_req = 0,
+                  int ks_req = 0)   // n_sm: the SMs this launch may occupy
 {
     Config c;
     c.P = P;
@@ -1555,17 +1559,26 @@ Config config_for(int n_cells, int N, int P, int n_sm, bool pair = false)   // n
     const size_t kstage = 2 * (size_t)kKBlkBytes;
     const size_t state = (size_t)SL * 5 * N * sizeof(float);
     const int sb_min = P > 1 ? 2 : (room >= 2 * sstride + kstage ? 2 : 1);
-    size_t avail = room > sb_min * sstride ? room - sb_min * sstride : 0;
-    int KS = (int)std::min<size_t>(2, avail / kstage);
-    avail -= KS * kstage;
-    const bool st_smem = KS >= 2 && avail >= state;
-    if (st_smem) avail -= state;
-    const int KSx = (int)std::min<size_t>(kMaxKS - KS, avail / kstage);
-    KS += KSx;
-    avail -= KSx * kstage;
-    int SB = sb_min + (int)std::min<size_t>(max_sb - sb_min, avail / sstride);
-    // the D staging areas ([slots kept + 64][NBP] floats) alias the mapping-tile ring
-    while ((size_t)SB * sstride < (size_t)(SL + kSlots) * c.NBP * 4 && SB < max_sb) SB++;
+    int SB, KS;
+    bool st_smem;
+    if (sb_req > 0 || ks_req > 0) {
+        SB = sb_req > 0 ? sb_req : sb_min;
+        KS = ks_req > 0 ? ks_req : 2;
+        const size_t rings = (size_t)SB * sstride + (size_t)KS * kstage;
+        st_smem = rings + state <= room;
+    } else {
+        size_t avail = room > sb_min * sstride ? room - sb_min * sstride : 0;
+        KS = (int)std::min<size_t>(2, avail / kstage);
+        avail -= KS * kstage;
+        st_smem = KS >= 2 && avail >= state;
+        if (st_smem) avail -= state;
+        const int KSx = (int)std::min<size_t>(kMaxKS - KS, avail / kstage);
+        KS += KSx;
+        avail -= KSx * kstage;
+        SB = sb_min + (int)std::min<size_t>(max_sb - sb_min, avail / sstride);
+        // the D staging areas ([slots kept + 64][NBP] floats) alias the mapping-tile ring
+        while ((size_t)SB * sstride < (size_t)(SL + kSlots) * c.NBP * 4 && SB < max_sb) SB++;
+    }
     c.SB = SB;
     c.KS = KS;
     c.sst_off = st_smem ? (int)((size_t)SB * sstride + KS * kstage) : -1;
@@ -1573,8 +1586,9 @@ Config config_for(int n_cells, int N, int P, int n_sm, bool pair = false)   // n
     // at least 120 KB, so that no two CTAs share an SM (each holds all 512
     // TMEM columns for the whole kernel)
     c.smem = std::max((size_t)120 * 1024, 1024 + used + tail + dpeer);
-    c.ok = KS >= 1 && SB >= sb_min && used <= room && (P == 1 || n_st >= 2 * P) &&
-           (!pair || (c.stacked && (size_t)SB * sstride >= (size_t)(SL + kSlots) * c.NBP * 4));
+    c.ok = KS >= 1 && KS <= kMaxKS && SB >= (P > 1 ? 2 : 1) && SB <= max_sb && used <= room &&
+           (P == 1 || n_st >= 2 * P) && (size_t)SB * sstride >= (size_t)(SL + kSlots) * c.NBP * 4 &&
+           (!pair || c.stacked);
     // cells are spread over up to one cluster per Q SMs, at least 8 a group
     const int mc = Q == 1 ? n_sm : (c.ok ? std::min(max_clusters(Q, c.smem, sm_count(), pair), n_sm / Q) : 0);
     if (mc < 1) c.ok = false;
@@ -1607,28 +1621,29 @@ int sm_count()
 // max_sms > 0: the launch may occupy at most that many SMs.
 // pair_req: 2 = CTA pairs (P_req pairs per cluster, 0: two), falling back to
 // fewer pairs and then to single CTAs when it does not fit; otherwise single
-// CTAs as below.
-Config mixed_config(int n_cells, int N, int P_req, int max_sms, int pair_req = 0)
+// CTAs as below.  sb_req, ks_req: ring depths (0: automatic), see config_for;
+// the result's ok is false when no P takes them.
+Config mixed_config(int n_cells, int N, int P_req, int max_sms, int pair_req = 0, int sb_req = 0, int ks_req = 0)
 {
     const int n_sm = max_sms > 0 ? std::min(max_sms, sm_count()) : sm_count();
     if (pair_req == 2) {
         for (int P = P_req > 0 ? P_req : 2; P >= 1; P /= 2) {
-            Config c = config_for(n_cells, N, P, n_sm, true);
+            Config c = config_for(n_cells, N, P, n_sm, true, sb_req, ks_req);
             if (c.ok) return c;
         }
         P_req = 0;
     }
     if (P_req > 0) {
         for (int P = P_req; P >= 1; P /= 2) {
-            Config c = config_for(n_cells, N, P, n_sm);
+            Config c = config_for(n_cells, N, P, n_sm, false, sb_req, ks_req);
             if (c.ok || P == 1) return c;
         }
     }
-    Config best = config_for(n_cells, N, 1, n_sm);
+    Config best = config_for(n_cells, N, 1, n_sm, false, sb_req, ks_req);
     double best_cost = 1e300;
     for (int P = 1; P <= 8; P *= 2) {
-        Config c = config_for(n_cells, N, P, n_sm);
-        if (!c.ok && P > 1) continue;
+        Config c = config_for(n_cells, N, P, n_sm, false, sb_req, ks_req);
+        if (!c.ok) continue;                    // (P = 1 stays the answer when nothing fits)
         const double slots = (double)c.groups * kSlots;
         const double cost = std::max(1.0, n_cells / (3.0 * slots)) * (1.0 / P + 0.05);
         if (cost < best_cost) { best_cost = cost; best = c; }
@@ -1661,7 +1676,8 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
                          double *dt_cell, const double *replay_h, const long long *replay_n,
                          long long replay_stride, WorkList wl = WorkList())
 {
-    Config cf = mixed_config(c->n_cells, c->N, c->mix_P, c->p.max_sms, c->mix_pair ? 2 : 1);
+    Config cf = mixed_config(c->n_cells, c->N, c->mix_P, c->p.max_sms, c->mix_pair ? 2 : 1, c->p.mixed_tile_stages,
+                             c->p.mixed_k_stages);
     const size_t need = (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(float);
     if (need > c->work_bytes) return cudaErrorInvalidValue;
     if (cf.P != c->mix_P || cf.groups != c->mix_G || cf.C != c->mix_C || cf.pair != c->mix_pair)
@@ -1730,9 +1746,9 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 size_t static_scratch_bytes() { return kStaticScratchBytes; }
 
-size_t mixed_scratch_bytes(int n_cells, int N, int P, int max_sms, int pair)
+size_t mixed_scratch_bytes(int n_cells, int N, int P, int max_sms, int pair, int sb_req, int ks_req)
 {
-    const Config cf = mixed_config(n_cells, N, P, max_sms, pair ? 2 : 1);
+    const Config cf = mixed_config(n_cells, N, P, max_sms, pair ? 2 : 1, sb_req, ks_req);
     return cf.sst_off >= 0 ? 0 : (size_t)cf.groups * cf.NS * 5 * (size_t)N * sizeof(float);
 }
 
@@ -1740,7 +1756,8 @@ cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_s
                                      bool *too_big)
 {
     *too_big = false;
-    Config cf = mixed_config(c->n_cells, c->N, c->mix_P, c->p.max_sms, c->mix_pair ? 2 : 1);
+    Config cf = mixed_config(c->n_cells, c->N, c->mix_P, c->p.max_sms, c->mix_pair ? 2 : 1, c->p.mixed_tile_stages,
+                             c->p.mixed_k_stages);
     // the array is only touched when the per-slot state does not fit in
     // shared memory
     const size_t need = cf.sst_off >= 0 ? 0 : (size_t)cf.groups * cf.NS * 5 * (size_t)c->N * sizeof(float);
@@ -1802,18 +1819,29 @@ cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_s
     return launch_kernel(cf, a, c->stream);
 }
 
-void mixed_layout(int n_cells, int N, int P_req, int max_sms, int pair_req, int *P, int *G, int *C, int *pair)
+bool mixed_layout(int n_cells, int N, int P_req, int max_sms, int pair_req, int sb_req, int ks_req, int *P, int *G,
+                  int *C, int *pair)
 {
-    const Config cf = mixed_config(n_cells, N, P_req, max_sms, pair_req);
+    const Config cf = mixed_config(n_cells, N, P_req, max_sms, pair_req, sb_req, ks_req);
     *P = cf.P;
     *G = cf.groups;
     *C = cf.C;
     *pair = cf.pair;
+    return cf.ok;
 }
 
-size_t mixed_workspace_bytes(int n_cells, int N, int P, int max_sms, int pair)
+void mixed_rings(int n_cells, int N, int P, int max_sms, int pair, int sb_req, int ks_req, int *SB, int *KS,
+                 int *state_smem)
 {
-    Config cf = mixed_config(n_cells, N, P, max_sms, pair ? 2 : 1);
+    const Config cf = mixed_config(n_cells, N, P, max_sms, pair ? 2 : 1, sb_req, ks_req);
+    *SB = cf.SB;
+    *KS = cf.KS;
+    *state_smem = cf.sst_off >= 0 ? 1 : 0;
+}
+
+size_t mixed_workspace_bytes(int n_cells, int N, int P, int max_sms, int pair, int sb_req, int ks_req)
+{
+    Config cf = mixed_config(n_cells, N, P, max_sms, pair ? 2 : 1, sb_req, ks_req);
     return (size_t)cf.groups * cf.NS * 5 * (size_t)N * sizeof(float);
 }
 

@@ -65,6 +65,9 @@ def _params(disc, **over):
     ("mixed_cluster", 3, coag.EINVAL),
     ("mixed_cluster", 16, coag.EINVAL),
     ("max_sms", -1, coag.EINVAL),
+    ("mixed_tile_stages", 9, coag.EINVAL),
+    ("mixed_tile_stages", -1, coag.EINVAL),
+    ("mixed_k_stages", 5, coag.EINVAL),
 ])
 def test_init_rejects_bad_arguments(field, value, code):
     d = synth.column_1x32()
@@ -111,6 +114,7 @@ def test_null_context_is_an_error_not_a_crash():
     assert L.cudisc_coag_set_fault_injection(None, 0, 0) == coag.EINVAL
     n = C.c_size_t()
     assert L.cudisc_coag_scratch_bytes(None, C.byref(n)) == coag.EINVAL
+    assert L.cudisc_coag_mixed_rings(None, C.byref(cl), C.byref(gr), C.byref(cl)) == coag.EINVAL
     assert L.cudisc_dust_step(None, None, 1.0) == coag.EINVAL
     assert L.cudisc_dust_update_gas(None) == coag.EINVAL
     assert L.cudisc_dust_geometry(None, None, None, None) == coag.EINVAL

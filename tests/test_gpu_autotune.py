@@ -39,7 +39,7 @@ def test_autotune_cluster_measures_caches_and_reuses(coag_mod):
     os.remove(CACHE)
 
 
-def test_autotune_launch_searches_cluster_and_pair_mode(coag_mod):
+def test_autotune_launch_searches_cluster_pair_mode_and_rings(coag_mod):
     cache = CACHE.replace(".json", "_launch.json")
     if os.path.exists(cache):
         os.remove(cache)
@@ -48,11 +48,16 @@ def test_autotune_launch_searches_cluster_and_pair_mode(coag_mod):
     assert best["mixed_cluster"] in (1, 2, 4) and best["mixed_pair"] in (1, 2)
     entry = json.load(open(cache))[f"N40_cells{d.n_cells}_mixed_launch"]
     rates = entry["rates"]
-    assert any(k.endswith("pair2") for k in rates) and any(k.endswith("pair1") for k in rates)
-    assert max(rates.values()) == rates[f"P{best['mixed_cluster']}_pair{best['mixed_pair']}"]
+    assert any("pair2_" in k for k in rates) and any("pair1_" in k for k in rates)
+    # ring depths were measured for the best layout (some fit at 40 bins)
+    assert any(not k.endswith("sb0_ks0") for k in rates)
+    key = "P{mixed_cluster}_pair{mixed_pair}_sb{mixed_tile_stages}_ks{mixed_k_stages}".format(**best)
+    assert max(rates.values()) == rates[key]
     # the layout it returns is the one a context then runs
     g = coag_mod.Coag(d, "mixed", **best)
     assert g.mixed_cluster()[0] == best["mixed_cluster"] and g.mixed_pair() == (best["mixed_pair"] == 2)
+    if best["mixed_tile_stages"]:
+        assert g.mixed_rings()[:2] == (best["mixed_tile_stages"], best["mixed_k_stages"])
     g.close()
     assert coag_mod.autotune_launch(d, clusters=(), cache_path=cache) == best
     os.remove(cache)
