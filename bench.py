@@ -196,11 +196,27 @@ def cpu_baseline(disc, budget_s=20.0, t_span=None):
         total_t += dt
         used = np.concatenate([used, cells]).astype(int)
         n *= 2
+    # the same oracle on one thread, over 64 cells of that sample
+    one = np.sort(used)[np.linspace(0, len(used) - 1, min(64, len(used))).astype(int)]
+    sub1 = disc.subset(one)
+    t0 = time.perf_counter()
+    r1 = O.Oracle(sub1, n_threads=1).step(sub1.rho0, t_span)
+    t1 = time.perf_counter() - t0
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            model = next((ln.split(":", 1)[1].strip() for ln in f if ln.startswith("model name")), "")
+    except OSError:
+        pass
     return {"value": total_sub / total_t, "unit": "cell-substeps/s", "cores": cores,
             "kind": "oracle", "seconds": total_t,
             "sample": f"{len(used)} of {disc.n_cells} cells spread over the grid, full "
                       f"{t_span / synth.CONST['yr']:.0f} yr, {total_sub} accepted substeps in "
-                      f"{total_t:.1f} s, OpenMP over cells"}
+                      f"{total_t:.1f} s, OpenMP over cells",
+            "value_1thread": int(r1["n_acc"].sum()) / t1,
+            "sample_1thread": f"{len(one)} of those cells on one thread, {int(r1['n_acc'].sum())} accepted "
+                              f"substeps in {t1:.1f} s",
+            "cpu_model": model}
 
 
 def accuracy_check(disc, y, hs, n_h, cells, rhs_gpu=None, rhs_state=None, rhs_fp64=None):
