@@ -477,6 +477,25 @@ cudisc_status cudisc_coag_replay(cudisc_coag_ctx *ctx, double *rho, const double
 cudisc_status cudisc_coag_step_static_scratch(cudisc_coag_ctx *ctx, double *rho, double t_span,
                                               double *dt_cell, cudisc_step_stats *stats);
 
+/* The integration of cudisc_coag_step from and to HOST memory, for callers
+ * whose state lives on the host: copies rho_in (host [n_cells][N], FP64) to
+ * a device state array the context keeps, rebuilds the kernel tables from
+ * the gas arrays when rebuild != 0 (as cudisc_coag_build_kernel), integrates
+ * every cell over t_span with fresh initial step sizes (dt_cell NULL), and
+ * copies the result to rho_out (host [n_cells][N]; may be rho_in).  All on
+ * the context's stream, which is synchronised before the call returns.
+ *   - Pinned host memory (cudaHostAlloc / cudaHostRegister) makes both
+ *     copies DMA transfers; pageable memory works, through the driver's
+ *     staging buffers.
+ *   - The device state array (n_cells x N doubles) is allocated at the first
+ *     call on a context and freed by cudisc_coag_destroy; later calls
+ *     allocate nothing.
+ *   - stats as cudisc_coag_step (elapsed_ms: the integration alone).
+ *   - CUDISC_EINVAL for a NULL context or host pointer; per-cell failures as
+ *     cudisc_coag_step (rho_out then holds the states reached). */
+cudisc_status cudisc_coag_step_host(cudisc_coag_ctx *ctx, const double *rho_in, double *rho_out, double t_span,
+                                    int rebuild, cudisc_step_stats *stats);
+
 /* Failure-path test hook of the mixed-precision integration kernel (the
  * paper has no counterpart).  Every wait of that kernel on another role's
  * progress is bounded by a clock limit (~2 s); when one runs out the kernel

@@ -114,6 +114,7 @@ def lib():
         L.cudisc_coag_set_records.argtypes = [v, v, C.c_longlong, v, v]
         L.cudisc_coag_replay.argtypes = [v, v, v, v, C.c_longlong]
         L.cudisc_coag_step_static_scratch.argtypes = [v, v, d, v, C.POINTER(cudisc_step_stats)]
+        L.cudisc_coag_step_host.argtypes = [v, v, v, d, C.c_int, C.POINTER(cudisc_step_stats)]
         L.cudisc_coag_get_timings.argtypes = [v, C.POINTER(cudisc_timings)]
         L.cudisc_coag_mixed_cluster.argtypes = [v, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.cudisc_coag_scratch_bytes.argtypes = [v, C.POINTER(C.c_size_t)]
@@ -136,7 +137,7 @@ def lib():
         L.cudisc_coag_version.restype = C.c_char_p
         for fn in ("cudisc_coag_init", "cudisc_coag_build_kernel", "cudisc_coag_build_kernel_async", "cudisc_coag_get_kernel",
                    "cudisc_coag_rhs", "cudisc_coag_step", "cudisc_coag_set_records",
-                   "cudisc_coag_replay", "cudisc_coag_step_static_scratch",
+                   "cudisc_coag_replay", "cudisc_coag_step_static_scratch", "cudisc_coag_step_host",
                    "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp",
                    "cudisc_coag_mixed_cluster", "cudisc_coag_scratch_bytes", "cudisc_coag_mixed_pair", "cudisc_coag_mixed_rings", "cudisc_coag_set_fault_injection", "cudisc_partition", "cudisc_dust_init", "cudisc_dust_update_gas",
                    "cudisc_dust_step", "cudisc_dust_geometry", "cudisc_coag_step_async", "cudisc_coag_step_wait",
@@ -181,6 +182,16 @@ def cudisc_coag_rhs(ctx, rho_ptr, drho_ptr):
 def cudisc_coag_step(ctx, rho_ptr, t_span, dt_ptr, check=True):
     s = cudisc_step_stats()
     st = lib().cudisc_coag_step(ctx, rho_ptr, float(t_span), dt_ptr, C.byref(s))
+    if check:
+        _check(st, ctx)
+    return st, s
+
+
+def cudisc_coag_step_host(ctx, rho_in_ptr, rho_out_ptr, t_span, rebuild=True, check=True):
+    """cudisc_coag_step from and to host arrays (pointers to [n_cells][N]
+    float64 host memory, pinned for DMA copies)."""
+    s = cudisc_step_stats()
+    st = lib().cudisc_coag_step_host(ctx, rho_in_ptr, rho_out_ptr, float(t_span), 1 if rebuild else 0, C.byref(s))
     if check:
         _check(st, ctx)
     return st, s
@@ -590,6 +601,21 @@ class Coag:
         assert rho.is_contiguous() and rho.dtype == self.torch.float64
         st, s = cudisc_coag_step(self.ctx, rho.data_ptr(), t_span,
                                  dt.data_ptr() if dt is not None else None, check=check)
+        d = s.as_dict()
+        d["status"] = st
+        return d
+
+    def step_host(self, rho_in, rho_out, t_span, rebuild=True, check=True):
+        """cudisc_coag_step_host: host float64 tensors or arrays [n_cells, N]
+        in and out (may be the same; pin them for DMA copies), the kernel
+        tables rebuilt first when rebuild; returns the stats dict."""
+        def ptr(x):
+            if hasattr(x, "data_ptr"):
+                assert not x.is_cuda and x.is_contiguous() and x.dtype == self.torch.float64
+                return x.data_ptr()
+            assert x.flags["C_CONTIGUOUS"] and x.dtype == np.float64
+            return x.ctypes.data
+        st, s = cudisc_coag_step_host(self.ctx, ptr(rho_in), ptr(rho_out), t_span, rebuild, check=check)
         d = s.as_dict()
         d["status"] = st
         return d

@@ -423,7 +423,7 @@ static void free_ctx(cudisc_coag_ctx *c)
                     c->d_ent_ab, c->d_frow, c->d_fent_p, c->d_fent_m, c->d_Ntab, c->d_blk_i,
                     c->d_blk_j0, c->d_Btiles, c->d_prep, c->d_prep32, c->d_scal, c->d_K64,
                     c->d_K32, c->d_Kslot, c->d_out, c->d_work, c->d_counter, c->d_scal32, c->d_list,
-                    c->d_spans, c->d_pending};
+                    c->d_spans, c->d_pending, c->d_host_state};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -684,6 +684,25 @@ cudisc_status cudisc_coag_step(cudisc_coag_ctx *c, double *rho, double t_span, d
     if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
     cudisc_status st = issue_step(c, rho, t_span, dt_cell, true);
     if (st != CUDISC_OK) return st;
+    return finish_step(c, stats);
+}
+
+cudisc_status cudisc_coag_step_host(cudisc_coag_ctx *c, const double *rho_in, double *rho_out, double t_span,
+                                    int rebuild, cudisc_step_stats *stats)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (!rho_in || !rho_out) return fail(c, CUDISC_EINVAL, "rho_in and rho_out must be host arrays");
+    if (!(t_span > 0.0) || !std::isfinite(t_span)) return fail(c, CUDISC_EINVAL, "t_span must be positive and finite");
+    const size_t bytes = (size_t)c->n_cells * c->N * sizeof(double);
+    if (!c->d_host_state) CUDA_TRY(c, cudaMalloc(&c->d_host_state, bytes));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_host_state, rho_in, bytes, cudaMemcpyHostToDevice, c->stream));
+    if (rebuild) {
+        const cudisc_status sb = cudisc_coag_build_kernel_async(c);
+        if (sb != CUDISC_OK) return sb;
+    }
+    cudisc_status st = issue_step(c, c->d_host_state, t_span, nullptr, true);
+    if (st != CUDISC_OK) return st;
+    CUDA_TRY(c, cudaMemcpyAsync(rho_out, c->d_host_state, bytes, cudaMemcpyDeviceToHost, c->stream));
     return finish_step(c, stats);
 }
 

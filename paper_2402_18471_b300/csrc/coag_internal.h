@@ -115,6 +115,7 @@ struct cudisc_coag_ctx {
     int mix_pair = 0;                  // mixed kernel: CTA pairs share M = 256 MMAs
     bool timed = false;                // the last integration issued recorded ev0/ev1
     void *static_scratch = nullptr;    // device address of the fixed scratch array (first static call)
+    double *d_host_state = nullptr;    // [n_cells][N] device state of cudisc_coag_step_host (first call)
     long long inject_wait_cycles = 0;  // test hook: wait limit of the mixed kernel (0: the default)
     int inject_withhold = 0;           // test hook: the mixed kernel's producer issues no copies
     // integration workspace

@@ -115,6 +115,7 @@ def test_null_context_is_an_error_not_a_crash():
     n = C.c_size_t()
     assert L.cudisc_coag_scratch_bytes(None, C.byref(n)) == coag.EINVAL
     assert L.cudisc_coag_mixed_rings(None, C.byref(cl), C.byref(gr), C.byref(cl)) == coag.EINVAL
+    assert L.cudisc_coag_step_host(None, None, None, 1.0, 0, None) == coag.EINVAL
     assert L.cudisc_dust_step(None, None, 1.0) == coag.EINVAL
     assert L.cudisc_dust_update_gas(None) == coag.EINVAL
     assert L.cudisc_dust_geometry(None, None, None, None) == coag.EINVAL

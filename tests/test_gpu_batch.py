@@ -117,3 +117,25 @@ def test_full_size_32_disc_batch_sampled(coag_mod, oracle_mod):
                                                          n[cells])
         check_rel(ys[i].cpu().numpy()[cells], want, d.rho0[cells].sum(1), 1e-5)
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_step_host_equals_device_step(coag_mod, precision):
+    """cudisc_coag_step_host (host buffers in and out, kernel rebuilt)
+    integrates exactly as cudisc_coag_step on a device copy of the state,
+    from pinned and from pageable memory, in place or not."""
+    d = synth.make_disc(4, 64, 50, 1e-5, 1.0, 5.0, 40.0, 20.0, seed=31)
+    g = coag_mod.Coag(d, precision)
+    y = g.state(d.rho0)
+    ref = g.step(y, d.t_span)
+    want = y.cpu().numpy()
+    pinned = torch.from_numpy(np.ascontiguousarray(d.rho0)).pin_memory()
+    out = torch.empty_like(pinned).pin_memory()
+    st = g.step_host(pinned, out, d.t_span)
+    assert st["status"] == 0 and st["accepted"] == ref["accepted"]
+    assert np.array_equal(out.numpy(), want)
+    assert np.array_equal(pinned.numpy(), d.rho0)            # the input is left as it was
+    pageable = np.ascontiguousarray(d.rho0).copy()
+    st = g.step_host(pageable, pageable, d.t_span, rebuild=False)
+    assert st["accepted"] == ref["accepted"] and np.array_equal(pageable, want)
+    g.close()
