@@ -57,10 +57,22 @@ def test_split_fractions_sum_to_one_and_bracket(oracle_mod, split):
                 if split == 1:
                     # number fractions conserve the number of grains
                     assert od[0] * M / m[oi[0]] + od[1] * M / m[oi[1]] == pytest.approx(1.0, rel=1e-14)
+                else:
+                    # mass fractions interpolate linearly in mass: the mass
+                    # placed has the product's mass as its mean grain mass,
+                    # which fixes the fraction given the bracketing bins
+                    assert od[0] * m[oi[0]] + od[1] * m[oi[1]] == pytest.approx(M, rel=1e-14)
             # remnant + fragments carry the colliding mass (Eq. fragrem)
             assert od[4] + od[5] == pytest.approx(M, rel=1e-15)
             if od[4] > 0:
                 assert od[2] + od[3] == pytest.approx(1.0, abs=1e-15)
+                mr = od[4]
+                if m[0] < mr < m[-1]:
+                    assert m[oi[2]] <= mr < m[oi[3]] and oi[3] == oi[2] + 1
+                    if split == 1:
+                        assert od[2] * mr / m[oi[2]] + od[3] * mr / m[oi[3]] == pytest.approx(1.0, rel=1e-14)
+                    else:
+                        assert od[2] * m[oi[2]] + od[3] * m[oi[3]] == pytest.approx(mr, rel=1e-14)
             # the largest fragment min(chi m_im, m_tar) lies in bin l
             mx = min(d.chi_im * min(m[i], m[j]), max(m[i], m[j]))
             l = oi[4]
@@ -183,6 +195,59 @@ def test_bs3_adaptive_error_tracks_tolerance(oracle_mod):
         assert abs(out[0] - exact) / exact < 50 * rtol
         assert out[1] > prev_n
         prev_n = out[1]
+
+
+def _bs3_controller_closed_form(lam, y0, T, h, rtol, atol):
+    """The step controller's reading (per-cell max-norm error against atol +
+    rtol max(|y|, |y'|); accept when E <= 1 and y' >= -atol; next step h E
+    -> h min(5, max(0.2, 0.9 E^-1/3)), 5 at E = 0; a rejected step shrinks
+    by max(0.2, 0.9 E^-1/3); the last step cut to the end keeps h; h0 = 0.1
+    (|y| + atol) / |f|) on y' = lam y, with the local error taken from the
+    published embedded weights (7/24, 1/4, 1/3, 1/8) and the stage
+    polynomials of a linear problem: k2 = lam y (1 + z/2), k3 = lam y (1 +
+    3z/4 + 3z^2/8), y' = y R(z), R = 1 + z + z^2/2 + z^3/6, z = lam h."""
+    t, y, nacc, nrej = 0.0, y0, 0, 0
+    if not h > 0.0:
+        h = min(0.1 * (abs(y) + atol) / abs(lam * y), T)
+    while t < T:
+        last = h >= T - t
+        hs = T - t if last else h
+        z = lam * hs
+        R = 1 + z + z * z / 2 + z ** 3 / 6
+        Rhat = 1 + z * (7 / 24 + (1 + z / 2) / 4 + (1 + 3 * z / 4 + 3 * z * z / 8) / 3 + R / 8)
+        y1 = y * R
+        E = abs(y * (R - Rhat)) / (atol + rtol * max(abs(y), abs(y1)))
+        if E <= 1.0 and y1 >= -atol:
+            t = T if last else t + hs
+            y = y1
+            nacc += 1
+            fac = min(5.0, max(0.2, 0.9 * E ** (-1 / 3))) if E > 0 else 5.0
+            if not (last and hs < h):
+                h = hs * fac
+        else:
+            nrej += 1
+            h = hs * max(0.2, 0.9 * E ** (-1 / 3))
+    return y, nacc, nrej
+
+
+@pytest.mark.parametrize("lam,y0,T,h0,rtol", [
+    (-1.0, 1.0, 5.0, 0.0, 1e-3),      # automatic first step, smooth decay
+    (-1.0, 1.0, 5.0, 0.0, 1e-6),
+    (-10.0, 2.0, 3.0, 2.0, 1e-4),     # a first step far too long: rejections at the 0.2 clamp
+    (0.7, 1.0, 4.0, 1e-6, 1e-5),      # growth from a tiny step: the factor-5 clamp
+    (-3.0, 1.0, 2.0, 0.05, 1e-2),     # the paper's rtol
+])
+def test_bs3_step_controller_matches_its_closed_form(oracle_mod, lam, y0, T, h0, rtol):
+    """Pins the controller constants and rules (not given by the paper) and
+    the embedded error estimate: the oracle's accepted and rejected step
+    counts and end state on y' = lam y equal those of the rules applied to
+    the closed-form stage values."""
+    y, nacc, nrej = _bs3_controller_closed_form(lam, y0, T, h0, rtol, 1e-12)
+    out = oracle_mod.bs3_scalar(lam, y0, T, h0, rtol=rtol, atol=1e-12)
+    assert (int(out[1]), int(out[2])) == (nacc, nrej)
+    assert out[0] == pytest.approx(y, rel=1e-12)
+    if h0 == 2.0:
+        assert nrej >= 2
 
 
 def _constant_kernel_analytic(N, N0, tau):
