@@ -331,27 +331,26 @@ def run_reference(args, disc, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def batch_measure(precision, steps, warmup, t_span_yr=None):
     """The batch of 32 uneven discs (batch_32_discs): every disc integrated
     over t_span through the batched interface (one context and stream per
     disc, SMs shared in proportion to n_cells x n_bins^2); aggregate accepted
     cell-substeps per second of the whole batch step, timed with CUDA events
     on the stream the batch joins on, and the worst per-disc mass error.
     Then the adjoint of every 4th disc's step (discs 0, 4, 8, ...) through
-    the same contexts, with the loss of small grains above Z = H.
-    One GPU; an informational line, not the default benchmark."""
+    the same contexts, with the loss of small grains above Z = H."""
     import torch
     from paper_2402_18471_b300 import coag
     discs = synth.batch_32_discs()
-    if args.t_span_yr:
+    if t_span_yr:
         for d in discs:
-            d.t_span = args.t_span_yr * synth.CONST["yr"]
-    b = coag.Batch(discs, args.precision)
+            d.t_span = t_span_yr * synth.CONST["yr"]
+    b = coag.Batch(discs, precision)
     init = [torch.as_tensor(np.ascontiguousarray(d.rho0), device="cuda") for d in discs]
     ys = [x.clone() for x in init]
     t_span = discs[0].t_span
     ms, acc, mass = 0.0, 0, 0.0
-    for s in range(args.warmup + args.steps):
+    for s in range(warmup + steps):
         for y, x in zip(ys, init):
             y.copy_(x)
         torch.cuda.synchronize()
@@ -360,7 +359,7 @@ def run_batch(args):
         stats = b.step(ys, t_span)
         e1.record()
         torch.cuda.synchronize()
-        if s >= args.warmup:
+        if s >= warmup:
             ms += e0.elapsed_time(e1)
             acc += sum(st["accepted"] for st in stats)
             mass = max([mass] + [st["mass_err_max"] for st in stats])
@@ -378,18 +377,40 @@ def run_batch(args):
                     "finite": bool(torch.isfinite(g0).all().item() and torch.isfinite(ga).all().item())})
     b.close()
     cells = sum(d.n_cells for d in discs)
-    line = {"metric": "cell-substeps/s, batch of 32 uneven discs (batched interface)",
-            "value": acc / (ms / 1e3), "unit": "cell-substeps/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "tf32x4+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": "batch_32_discs", "n_discs": len(discs), "n_cells": cells,
-                       "n_bins": [min(d.n_bins for d in discs), max(d.n_bins for d in discs)],
-                       "t_span_yr": t_span / synth.CONST["yr"], "precision": args.precision},
-            "accepted_per_step": acc // args.steps, "mass_err_max_per_disc": mass,
+    return {"value": acc / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
+            "n_discs": len(discs), "n_cells": cells,
+            "n_bins": [min(d.n_bins for d in discs), max(d.n_bins for d in discs)],
+            "t_span_yr": t_span / synth.CONST["yr"], "accepted_per_step": acc // steps,
+            "mass_err_max_per_disc": mass,
             "adjoint_every_4th_disc": {"discs": len(adj), "seconds_total": sum(a["s"] for a in adj),
                                        "all_finite": all(a["finite"] for a in adj), "per_disc": adj}}
+
+
+def run_batch(args):
+    """The batch workload as its own JSON line (one GPU; informational, not
+    the default benchmark)."""
+    r = batch_measure(args.precision, args.steps, args.warmup, args.t_span_yr)
+    line = {"metric": "cell-substeps/s, batch of 32 uneven discs (batched interface)",
+            "value": r["value"], "unit": "cell-substeps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "tf32x4+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": "batch_32_discs", "n_discs": r["n_discs"], "n_cells": r["n_cells"],
+                       "n_bins": r["n_bins"], "t_span_yr": r["t_span_yr"], "precision": args.precision},
+            "accepted_per_step": r["accepted_per_step"], "mass_err_max_per_disc": r["mass_err_max_per_disc"],
+            "adjoint_every_4th_disc": r["adjoint_every_4th_disc"]}
     print(json.dumps(line), flush=True)
+
+
+def batch_key():
+    """The batch of 32 uneven discs as an extra key of the default line: one
+    warm-up and one timed batch step over 1e4 yr, then the adjoint of every
+    4th disc."""
+    r = batch_measure("mixed", 1, 1)
+    adj = r["adjoint_every_4th_disc"]
+    adj["per_disc"] = [{k: v for k, v in a.items() if k in ("disc", "n_cells", "n_bins", "vjp_ms")}
+                       for a in adj["per_disc"]]
+    return {"workload": "batch_32_discs", "unit": "cell-substeps/s", **r}
 
 
 class Leg:
@@ -647,8 +668,8 @@ def main():
     ap.add_argument("--t-span-yr", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-leg", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the large-grid, adjoint, transport and HSE keys")
-    ap.add_argument("--extras", default="hse,transport,large_grid,adjoint",
+    ap.add_argument("--no-extras", action="store_true", help="skip the large-grid, adjoint, batch, transport and HSE keys")
+    ap.add_argument("--extras", default="hse,transport,large_grid,adjoint,batch",
                     help="comma-separated extra keys to measure (default all)")
     ap.add_argument("--no-graph", action="store_true", help="time the synchronous calls instead of graph replays")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -855,6 +876,8 @@ def main():
                     line["large_grid"] = large_grid_key(args, pk)
                 if "adjoint" in extras:
                     line["adjoint"] = adjoint_key(pk)
+                if "batch" in extras:
+                    line["batch"] = batch_key()
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(disc, budget_s=args.cpu_budget)
             # the accuracy of the benched integration: an untimed run of the
