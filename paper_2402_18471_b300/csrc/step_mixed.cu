@@ -860,10 +860,10 @@ struct GenCtx {
 };
 
 // One pipeline stage = two blocks (b = 2 st, 2 st + 1; the last stage of a
-// pass may hold one): the wait for its K tables, two products-and-splits
-// into registers (the K ring stage is released right after), then the wait
-// for its TMEM columns, the stores, one store wait and the arrival.  The
-// values are ready before the MMAs release the TMEM stage.
+// pass may hold one): the wait for its K tables, their loads into registers
+// and the release of the K ring stage, two products-and-splits, then the
+// wait for its TMEM columns, the stores, one store wait and the arrival.
+// The values are ready before the MMAs release the TMEM stage.
 __device__ __forceinline__ bool gen_stage(GenCtx &G, int st, long long g)
 {
     const int b = 2 * st;
@@ -873,22 +873,24 @@ __device__ __forceinline__ bool gen_stage(GenCtx &G, int st, long long g)
     if (bj1 > bi1) { bi1++; bj1 = 0; }
     if (!wwait(&G.k_full[G.ks], G.ku & 1, G.s_err, ERR_WAIT_GEN)) return false;
     float oa[2 * kGP], ob[2 * kGP];
+    // this thread's chunks 2 sub .. 2 sub + kGC - 1 of its slot, both blocks,
+    // into registers; the ring stage is released before the products so that
+    // the producer refills it a stage's arithmetic earlier
+    float4 ka[kGC], kb[kGC];
     if (G.active) {
-        // this thread's chunks 2 sub .. 2 sub + kGC - 1 of its slot, both blocks
         const float4 *kp = reinterpret_cast<const float4 *>(G.kring + (size_t)G.ks * 2 * kKBlkBytes) +
                            (size_t)(kGC * G.sub) * kSlots + G.slot;
-        float4 kc[kGC];
 #pragma unroll
-        for (int q = 0; q < kGC; q++) kc[q] = kp[q * kSlots];
-        gen_vals(kc, G.xr, G.bi, G.bj0 + kGP * G.sub, G.lo_half, oa);
-        if (two) {
+        for (int q = 0; q < kGC; q++) ka[q] = kp[q * kSlots];
 #pragma unroll
-            for (int q = 0; q < kGC; q++) kc[q] = kp[kKBlkBytes / 16 + q * kSlots];
-            gen_vals(kc, G.xr, bi1, bj1 + kGP * G.sub, G.lo_half, ob);
-        }
+        for (int q = 0; q < kGC; q++) kb[q] = two ? kp[kKBlkBytes / 16 + q * kSlots] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncwarp();
     if (G.lane == 0) mbar_arrive(&G.k_empty[G.ks]);
+    if (G.active) {
+        gen_vals(ka, G.xr, G.bi, G.bj0 + kGP * G.sub, G.lo_half, oa);
+        if (two) gen_vals(kb, G.xr, bi1, bj1 + kGP * G.sub, G.lo_half, ob);
+    }
     if (g >= kAStages && !wwait(&G.c_empty[G.s], (G.u + 1) & 1, G.s_err, ERR_WAIT_GEN)) return false;
     if (G.active) {
         tc_fence_after();
