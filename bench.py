@@ -50,12 +50,12 @@ FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
 # from one ncu capture of the named kernel (summaries under profiles/), valid
 # only for the kernel source they were taken on: a changed source reports null.
 MEASURED_TRAFFIC = {
-    "step_mixed_kernel": {"bytes_per_unit": (25.854755e9 + 0.665149e9) / 635513, "unit": "RHS evaluation",
+    "step_mixed_kernel": {"bytes_per_unit": (26.267218e9 + 0.788401e9) / 635513, "unit": "RHS evaluation",
                           "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
-                          "sha256": "0bc2cf10e3035198a25dfe66b8b5e39b0dd62e98476b9cf23fddf95987b3499b"},
-    "kbuild32_kernel": {"bytes_per_unit": 43.704576e6 + 322.752512e6, "unit": "launch (8192 cells x 100 bins)",
+                          "sha256": "a859fa7c28f8dbf24ff1d9ef5bd20292aaecc42b6966164c9d1f684a8b56a053"},
+    "kbuild32_kernel": {"bytes_per_unit": 43.672064e6 + 322.585344e6, "unit": "launch (8192 cells x 100 bins)",
                         "source": "paper_2402_18471_b300/csrc/kbuild.cu",
-                        "sha256": "f54951cf585f15c9033ff60e15efa987e04e8703e154878589dc63c1b6b45c04"},
+                        "sha256": "49c922bebb2f12ffd1da8af6d069e3cb34b9611ce24d12f85271c017bf7372fd"},
 }
 MEASURED_TRAFFIC_WORKLOAD = "grid_128x64_N100"   # the captures above are of this grid
 TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 rate ratio
