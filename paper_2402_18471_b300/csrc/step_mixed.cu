@@ -1523,6 +1523,23 @@ int max_clusters(int P, size_t smem, int n_sm, bool pair = false)   // P: the cl
 // pass per CTA, or no cluster of P resident).
 // pair: CTA pairs share M = 256 MMAs, a cluster of 2 P CTAs serving two
 // groups of 64 slots (each CTA keeps half of every mapping tile)
+// Static shared memory of the kernel (as compiled; 2048 if the runtime cannot
+// say), asked once per instantiation.
+size_t static_smem_bytes(bool pair)
+{
+    static size_t cached[2] = {0, 0};
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &v = cached[pair ? 1 : 0];
+    if (v == 0) {
+        cudaFuncAttributes fa;
+        const cudaError_t e = cudaFuncGetAttributes(&fa, pair ? step_mixed_kernel<true> : step_mixed_kernel<false>);
+        v = (e == cudaSuccess && fa.sharedSizeBytes > 0 && fa.sharedSizeBytes <= 8192) ? fa.sharedSizeBytes : 2048;
+        if (e != cudaSuccess) cudaGetLastError();
+    }
+    return v;
+}
+
 // sb_req, ks_req > 0: exactly that many mapping-tile / K-table stages (the
 // per-slot state then takes shared memory only if it still fits); 0: the
 // automatic choice below.
@@ -1550,7 +1567,9 @@ Config config_for(int n_cells, int N, int P, int n_sm, bool pair = false, int sb
     const int max_sb = pair ? kMaxSB : 4;
     const size_t tail = (size_t)kSlots * c.XS * 4 + (size_t)kSlots * sizeof(Slot) +
                         8 * (3 * kMaxSB + 2 * kAStages + 7 + 2 * kMaxKS + kGenWarps / 2);
-    const size_t budget = 232448 - 1024 - 2048;  // opt-in shared memory, alignment, static
+    // opt-in shared memory less the kernel's static shared memory and the
+    // 1024-byte alignment of the dynamic base
+    const size_t budget = 232448 - 1024 - static_smem_bytes(pair);
     const int SL = kSlots / P;
     const size_t dpeer = (size_t)(P - 1) * SL * c.NBP * 4;   // partial sums from the other CTAs
     const size_t room = budget > tail + dpeer ? budget - tail - dpeer : 0;
