@@ -61,6 +61,8 @@ constexpr int kAStages = 3;                       // generated-operand stages in
 constexpr int kMaxMain = 8;                       // TMEM accumulators for the products with Bt_hi
 constexpr int kMaxSB = 8;                         // mapping-tile ring depth (stages of two blocks), at most
 constexpr int kMaxKS = 4;                         // K-table ring depth (stages of two blocks), at most
+constexpr int kPrefetchK = 2;                     // K-table stages prefetched into L2 ahead of the ring,
+                                                  // when the groups' K tables exceed L2
 constexpr int kKBlkBytes = 16 * 8 * 64;           // K tables of one block for 64 slots: 8 chunks x 64 x 16 B
 constexpr int kThreads = 64 + 32 * kGenWarps;
 constexpr int kLaneBins = (kMaxMixedBins + 31) / 32;   // bins per lane in the per-slot logic
@@ -107,6 +109,7 @@ struct MixedArgs {
     int pair;                   // 1: CTA pairs share M = 256 MMAs (two groups of slots per pair, see the kernel)
     long long wait_cycles;      // clock limit of the bounded waits (kWaitCycles; shorter only in tests)
     int withhold;               // test hook: 1 = the producer issues no copies, so the waits run out
+    int prefetch_k;             // K-table stages prefetched into L2 ahead of the ring (0: none)
 };
 
 struct __align__(16) Slot {
@@ -256,6 +259,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(su32(dst)), "l"(src), "r"(bytes), "r"(su32(bar)) : "memory");
+}
+// Bulk prefetch of global memory into L2 (no destination, no completion)
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -1099,6 +1107,17 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                         for (int q = 0; q < nb; q++)
                             bulk_g2s(kring + ((size_t)ks * 2 + q) * kKBlkBytes,
                                      kgrp + (size_t)(2 * sk + q) * 8 * kSlots, kKBlkBytes, &k_full[ks]);
+                        if (a.prefetch_k > 0) {
+                            // the K tables prefetch_k stages on (this CTA's range,
+                            // wrapping into the next pass) into L2, so that their
+                            // copy into the ring reads L2 rather than DRAM
+                            int sp = sk + a.prefetch_k;
+                            if (sp >= st_hi) sp = st_lo + (sp - st_hi);
+                            if (sp < st_hi) {
+                                const int nbp = 2 * sp + 1 < n_blk ? 2 : 1;
+                                bulk_prefetch_l2(kgrp + (size_t)(2 * sp) * 8 * kSlots, (uint32_t)(nbp * kKBlkBytes));
+                            }
+                        }
                         nk++;
                         gk++;
                         if (++ks == KS) { ks = 0; ku++; }
@@ -1693,6 +1712,24 @@ cudaError_t launch_kernel(const Config &cf, const MixedArgs &a, cudaStream_t str
                    : cudaLaunchKernelEx(&lc, step_mixed_kernel<false>, a);
 }
 
+// L2 prefetch of the K tables pays when the slot groups' tables (8 KB per
+// block and group) do not fit in L2: measured +15 % at 148 groups x 780
+// blocks (946 MB), -3.5 % at 33 groups x 364 blocks (98 MB of a 126 MB L2)
+int prefetch_k_stages(const Config &cf, int n_blk)
+{
+    static int l2 = -1;
+    if (l2 < 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+            cudaGetLastError();
+            v = 0;
+        }
+        l2 = v;
+    }
+    const double kbytes = (double)cf.groups * n_blk * kKBlkBytes;
+    return (l2 > 0 && kbytes > (double)l2) ? kPrefetchK : 0;
+}
+
 cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double *drho, double t_span,
                          double *dt_cell, const double *replay_h, const long long *replay_n,
                          long long replay_stride, WorkList wl = WorkList())
@@ -1744,6 +1781,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     a.pair = cf.pair;
     a.wait_cycles = c->inject_wait_cycles > 0 ? c->inject_wait_cycles : kWaitCycles;
     a.withhold = c->inject_withhold;
+    a.prefetch_k = prefetch_k_stages(cf, c->n_blk);
     a.wl = wl;
     a.mode = mode;
     return launch_kernel(cf, a, c->stream);
@@ -1835,6 +1873,7 @@ cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_s
     a.pair = cf.pair;
     a.wait_cycles = c->inject_wait_cycles > 0 ? c->inject_wait_cycles : kWaitCycles;
     a.withhold = c->inject_withhold;
+    a.prefetch_k = prefetch_k_stages(cf, c->n_blk);
     a.wl = WorkList();
     a.mode = MODE_STEP;
     return launch_kernel(cf, a, c->stream);
