@@ -168,6 +168,16 @@ typedef struct {
                                     when no cluster size takes the rings.
                                     The results do not depend on either
                                     depth, only the speed. */
+    int cost_order;              /* 0 = the integration kernels (both
+                                    precisions) hand cells to their slots in
+                                    order of each cell's cost (accepted +
+                                    rejected substeps) in the context's
+                                    previous full-grid step, costliest first,
+                                    which shortens the tail of a launch; the
+                                    first step takes index order; 1 = always
+                                    index order.  A cell's result does not
+                                    depend on its slot, so the results are the
+                                    same either way. */
 } cudisc_coag_params;
 
 typedef struct {

@@ -44,7 +44,7 @@ class cudisc_coag_params(C.Structure):
         ("mixed_cluster", C.c_int),
         ("max_sms", C.c_int),
         ("vertical", C.c_int), ("mixed_pair", C.c_int),
-        ("mixed_tile_stages", C.c_int), ("mixed_k_stages", C.c_int),
+        ("mixed_tile_stages", C.c_int), ("mixed_k_stages", C.c_int), ("cost_order", C.c_int),
     ]
 
 
@@ -522,6 +522,7 @@ class Coag:
         p.mixed_pair = int(s.get("mixed_pair", 0))
         p.mixed_tile_stages = int(s.get("mixed_tile_stages", 0))
         p.mixed_k_stages = int(s.get("mixed_k_stages", 0))
+        p.cost_order = int(s.get("cost_order", 0))
         self.params = p
 
     def close(self):

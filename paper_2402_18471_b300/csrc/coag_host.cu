@@ -48,6 +48,42 @@ cudisc_status cuda_fail(cudisc_coag_ctx *c, cudaError_t e, const char *where)
 // span (given, or, sub-cycling, the pending global time once it reaches
 // trigger x the cell's last sub-step) are listed; the others get an empty
 // result record (no steps, status OK, their state and dt_cell kept).
+// The order in which the next full-grid step hands cells to its slots:
+// costliest first by this step's accepted + rejected substeps, in buckets of
+// 1/16 octave (counting sort in one CTA; the order within a bucket is
+// whatever the atomics give, which is harmless because a cell's result does
+// not depend on its slot).
+constexpr int kOrderBuckets = 256;
+__device__ __forceinline__ int cost_bucket(const CellOut &o)
+{
+    const long long cost = o.n_acc + o.n_rej;
+    if (cost <= 0) return 0;
+    const int b = 1 + (int)(16.0f * __log2f((float)cost));
+    return b < kOrderBuckets - 1 ? b : kOrderBuckets - 1;
+}
+
+__global__ void __launch_bounds__(1024) cost_order_kernel(int n_cells, const CellOut *__restrict__ out,
+                                                          int *__restrict__ order)
+{
+    __shared__ int hist[kOrderBuckets], base[kOrderBuckets];
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < n_cells; c += blockDim.x) atomicAdd(&hist[cost_bucket(out[c])], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int sum = 0;
+        for (int b = kOrderBuckets - 1; b >= 0; b--) { base[b] = sum; sum += hist[b]; }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n_cells; c += blockDim.x) order[atomicAdd(&base[cost_bucket(out[c])], 1)] = c;
+}
+
+__global__ void iota_kernel(int n, int *v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = i;
+}
+
 __global__ void worklist_kernel(int n_cells, const double *span_in, double *pending, double dt_global,
                                 double trigger, const double *dt_cell, double *spans, int *list, int *count,
                                 CellOut *out, long long *rec_n, int *rec_status)
@@ -251,6 +287,10 @@ static cudisc_status validate(const cudisc_coag_params *p, std::string &why)
         why = "mixed_tile_stages must be 0 (automatic) or 1..8";
         return CUDISC_EINVAL;
     }
+    if (p->cost_order != 0 && p->cost_order != 1) {
+        why = "cost_order must be 0 (previous step's cost order) or 1 (index order)";
+        return CUDISC_EINVAL;
+    }
     if (p->mixed_k_stages < 0 || p->mixed_k_stages > 4) {
         why = "mixed_k_stages must be 0 (automatic) or 1..4";
         return CUDISC_EINVAL;
@@ -423,7 +463,7 @@ static void free_ctx(cudisc_coag_ctx *c)
                     c->d_ent_ab, c->d_frow, c->d_fent_p, c->d_fent_m, c->d_Ntab, c->d_blk_i,
                     c->d_blk_j0, c->d_Btiles, c->d_prep, c->d_prep32, c->d_scal, c->d_K64,
                     c->d_K32, c->d_Kslot, c->d_out, c->d_work, c->d_counter, c->d_scal32, c->d_list,
-                    c->d_spans, c->d_pending, c->d_host_state};
+                    c->d_spans, c->d_pending, c->d_host_state, c->d_order};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -473,6 +513,11 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
     if (e == cudaSuccess) e = cudaMalloc(&c->d_out, nc * sizeof(CellOut));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, 64 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_list, nc * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_order, nc * sizeof(int));
+    if (e == cudaSuccess) {
+        iota_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, c->stream>>>((int)nc, c->d_order);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaMalloc(&c->d_spans, nc * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_pending, nc * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(c->d_pending, 0, nc * sizeof(double));
@@ -669,11 +714,17 @@ static cudisc_status issue_step(cudisc_coag_ctx *c, double *rho, double t_span, 
     if (!rho) return fail(c, CUDISC_EINVAL, "rho is NULL");
     if (!(t_span > 0.0) || !std::isfinite(t_span)) return fail(c, CUDISC_EINVAL, "t_span must be positive and finite");
     if (timed) CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
+    cdc::WorkList wl;                 // every cell, in the previous step's cost order
+    if (c->p.cost_order == 0) wl.cells = c->d_order;
     if (c->p.precision == CUDISC_FP64)
-        CUDA_TRY(c, cdc::launch_step_fp64(c, rho, t_span, dt_cell, nullptr, nullptr, 0));
+        CUDA_TRY(c, cdc::launch_step_fp64(c, rho, t_span, dt_cell, nullptr, nullptr, 0, wl));
     else
-        CUDA_TRY(c, cdc::launch_step_mixed(c, rho, t_span, dt_cell, nullptr, nullptr, 0));
+        CUDA_TRY(c, cdc::launch_step_mixed(c, rho, t_span, dt_cell, nullptr, nullptr, 0, wl));
     if (timed) CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
+    if (c->p.cost_order == 0) {
+        cost_order_kernel<<<1, 1024, 0, c->stream>>>(c->n_cells, c->d_out, c->d_order);
+        CUDA_TRY(c, cudaGetLastError());
+    }
     c->timed = timed;
     return CUDISC_OK;
 }

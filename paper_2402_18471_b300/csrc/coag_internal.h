@@ -124,6 +124,7 @@ struct cudisc_coag_ctx {
     size_t work_bytes = 0;
     int *d_counter = nullptr;          // work queue head (d_counter[3]: work-list length)
     int *d_list = nullptr;             // [n_cells] work list of per-cell-span integrations
+    int *d_order = nullptr;            // [n_cells] cells by the previous full-grid step's cost (identity at first)
     double *d_spans = nullptr;         // [n_cells] their spans
     double *d_pending = nullptr;       // [n_cells] global time since each cell's last sub-cycled update
     // optional records

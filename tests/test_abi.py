@@ -68,6 +68,7 @@ def _params(disc, **over):
     ("mixed_tile_stages", 9, coag.EINVAL),
     ("mixed_tile_stages", -1, coag.EINVAL),
     ("mixed_k_stages", 5, coag.EINVAL),
+    ("cost_order", 2, coag.EINVAL),
 ])
 def test_init_rejects_bad_arguments(field, value, code):
     d = synth.column_1x32()

@@ -139,3 +139,28 @@ def test_step_host_equals_device_step(coag_mod, precision):
     st = g.step_host(pageable, pageable, d.t_span, rebuild=False)
     assert st["accepted"] == ref["accepted"] and np.array_equal(pageable, want)
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_cost_ordered_slots_change_no_result(coag_mod, precision):
+    """With cost_order = 0 the second step hands cells to slots in order of
+    the first step's per-cell cost (costliest first); every cell's result,
+    step count and step size equal those of index order (cost_order = 1),
+    bitwise."""
+    d = synth.make_disc(16, 64, 40, 1e-5, 1.0, 5.0, 100.0, 100.0, seed=5, rho_pert=0.1)
+    a = coag_mod.Coag(d, precision, cost_order=0)
+    b = coag_mod.Coag(d, precision, cost_order=1)
+    outs = []
+    for g in (a, a, b):
+        y = g.state(d.rho0)
+        dt = torch.zeros(d.n_cells, dtype=torch.float64, device="cuda")
+        rec = g.set_records(4000)
+        st = g.step(y, d.t_span, dt)
+        assert st["status"] == 0
+        outs.append((y.clone(), dt.clone(), rec["n"].clone(), st["accepted"], st["rejected"]))
+        g.set_records(0)
+    for o in outs[1:]:
+        assert torch.equal(o[0], outs[0][0]) and torch.equal(o[1], outs[0][1]) and torch.equal(o[2], outs[0][2])
+        assert o[3:] == outs[0][3:]
+    a.close()
+    b.close()
