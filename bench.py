@@ -50,9 +50,9 @@ FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
 # from one ncu capture of the named kernel (summaries under profiles/), valid
 # only for the kernel source they were taken on: a changed source reports null.
 MEASURED_TRAFFIC = {
-    "step_mixed_kernel": {"bytes_per_unit": (26.267583e9 + 0.787278e9) / 635513, "unit": "RHS evaluation",
+    "step_mixed_kernel": {"bytes_per_unit": (27.934206e9 + 0.641626e9) / 635513, "unit": "RHS evaluation",
                           "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
-                          "sha256": "1128a3ed8f334e07402f8ca5e3b19bfbaa48ab8837965f38b5bf0a2c8635c7fc"},
+                          "sha256": "4c9ba385ca268fe12da33bada02a8fc80e08bb0fc53347c94441711d07083aa3"},
     "kbuild32_kernel": {"bytes_per_unit": 43.672064e6 + 322.585344e6, "unit": "launch (8192 cells x 100 bins)",
                         "source": "paper_2402_18471_b300/csrc/kbuild.cu",
                         "sha256": "49c922bebb2f12ffd1da8af6d069e3cb34b9611ce24d12f85271c017bf7372fd"},
