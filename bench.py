@@ -172,7 +172,7 @@ def strong_bounds(disc, world: int, cost=None):
 
 # ---- the oracle leg: CPU baseline and the accuracy of the benched run ----
 
-def cpu_baseline(disc, budget_s=20.0, t_span=None):
+def cpu_baseline(disc, budget_s=20.0, t_span=None, one_thread=True):
     """The FP64 oracle on a bounded sample of cells of the same workload."""
     from oracle import oracle as O
     O.build()
@@ -196,6 +196,13 @@ def cpu_baseline(disc, budget_s=20.0, t_span=None):
         total_t += dt
         used = np.concatenate([used, cells]).astype(int)
         n *= 2
+    out = {"value": total_sub / total_t, "unit": "cell-substeps/s", "cores": cores,
+           "kind": "oracle", "seconds": total_t,
+           "sample": f"{len(used)} of {disc.n_cells} cells spread over the grid, full "
+                     f"{t_span / synth.CONST['yr']:.0f} yr, {total_sub} accepted substeps in "
+                     f"{total_t:.1f} s, OpenMP over cells"}
+    if not one_thread:
+        return out
     # the same oracle on one thread, over 64 cells of that sample
     one = np.sort(used)[np.linspace(0, len(used) - 1, min(64, len(used))).astype(int)]
     sub1 = disc.subset(one)
@@ -208,11 +215,7 @@ def cpu_baseline(disc, budget_s=20.0, t_span=None):
             model = next((ln.split(":", 1)[1].strip() for ln in f if ln.startswith("model name")), "")
     except OSError:
         pass
-    return {"value": total_sub / total_t, "unit": "cell-substeps/s", "cores": cores,
-            "kind": "oracle", "seconds": total_t,
-            "sample": f"{len(used)} of {disc.n_cells} cells spread over the grid, full "
-                      f"{t_span / synth.CONST['yr']:.0f} yr, {total_sub} accepted substeps in "
-                      f"{total_t:.1f} s, OpenMP over cells",
+    return {**out,
             "value_1thread": int(r1["n_acc"].sum()) / t1,
             "sample_1thread": f"{len(one)} of those cells on one thread, {int(r1['n_acc'].sum())} accepted "
                               f"substeps in {t1:.1f} s",
@@ -312,7 +315,7 @@ def run_reference(args, disc, rank, world):
     cb = None
     vals, secs = [], []
     for s in range(args.warmup + args.steps):
-        r = cpu_baseline(disc, budget_s=args.ref_budget)
+        r = cpu_baseline(disc, budget_s=args.ref_budget, one_thread=False)
         if s >= args.warmup:
             vals.append(r["value"])
             secs.append(r["seconds"])
