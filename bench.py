@@ -493,14 +493,15 @@ def measure(leg, steps, warmup, dist):
     with ClockSampler(torch.cuda.current_device()) as clk:
         e0.record(leg.stream)
         for _ in range(steps):
-            for st, d in zip(leg.step(), leg.discs):
+            for st, d, g in zip(leg.step(), leg.discs, leg.gs):
                 sub += st["accepted"]
                 rej += st["rejected"]
                 kern_ms += st["elapsed_ms"]
                 last = st
                 # prep, table build and integration kernels (launches over
-                # cells are chunked to 65535 rows)
-                launches += 3 + 2 * ((d.n_cells - 1) // 65535)
+                # cells are chunked to 65535 rows), and the kernel that orders
+                # the cells by cost for the next step's slots
+                launches += 3 + 2 * ((d.n_cells - 1) // 65535) + (1 if g.params.cost_order == 0 else 0)
         e1.record(leg.stream)
         torch.cuda.synchronize()
     if dist:
