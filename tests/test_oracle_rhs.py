@@ -294,6 +294,66 @@ def test_additive_kernel_matches_golovin(oracle_mod):
     assert n.sum() == pytest.approx(N0 * (1 - g), rel=1e-6)
 
 
+def log_disc(per_decade, m0, lo=-3, hi=4, **kw):
+    """One cell on a logarithmic mass grid of per_decade bins per decade from
+    10^lo m0 to 10^hi m0, edges at the geometric midpoints of the centres."""
+    N = per_decade * (hi - lo)
+    r = 10.0 ** (1.0 / per_decade)
+    m = m0 * 10.0 ** lo * r ** (np.arange(N) + 0.5)
+    me = np.empty(N + 1)
+    me[1:-1] = np.sqrt(m[1:] * m[:-1])
+    me[0], me[-1] = m[0] / math.sqrt(r), m[-1] * math.sqrt(r)
+    d = small_disc(n_bins=N, n_cells=1)
+    d.m, d.me = m, me
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+def _exp_bin_mass(me, m0, s=1.0, N0=1.0):
+    """Mass per bin of n(m) = N0 / (m0 s^2) exp(-m / (m0 s)): the integral of
+    m n(m) over each bin, N0 m0 [(1 + a) e^-a]_b^a with a = m / (m0 s)."""
+    a, b = me[:-1] / (m0 * s), me[1:] / (m0 * s)
+    return N0 * m0 * ((1 + a) * np.exp(-a) - (1 + b) * np.exp(-b))
+
+
+@pytest.mark.parametrize("kind", ["constant", "additive"])
+@pytest.mark.parametrize("split", [0, 1])
+def test_log_grid_converges_to_continuous_solutions(oracle_mod, kind, split):
+    """On logarithmic grids (the method's own) from an exponential start,
+    n(m, 0) = N0/m0 exp(-m/m0), the binned solution approaches the continuous
+    one: constant kernel n = N0 / (m0 s^2) exp(-m / (m0 s)), s = 1 + tau/2,
+    tau = K N0 t; additive kernel (Golovin) m n = N0 (1-g)/sqrt(g) exp(-(1+g)x)
+    I1(2 x sqrt(g)), x = m/m0, g = 1 - exp(-beta N0 m0 t).  The L1 error of
+    the mass distribution must fall by more than 3 for each doubling of the
+    bins per decade (second order) and be below 1 % at 20 bins per decade."""
+    m0 = 2.0 ** -40
+    errs = []
+    for per_decade in (5, 10, 20):
+        if kind == "constant":
+            K, tau = 1e-6, 2.0
+            d = log_disc(per_decade, m0, kernel_mode=1, kernel_const=K, frag_mode=1, split_mode=split,
+                         rtol=1e-8, atol_rel=1e-25)
+            t = tau / K
+            want = _exp_bin_mass(d.me, m0, s=1 + tau / 2)
+        else:
+            beta, g = 1e-6 / m0, 0.5
+            d = log_disc(per_decade, m0, kernel_mode=2, kernel_const=beta, frag_mode=1, split_mode=split,
+                         rtol=1e-8, atol_rel=1e-25)
+            t = -math.log(1 - g) / (beta * m0)
+            sg = math.sqrt(g)
+            f = lambda x: (1 - g) / sg * special.i1e(2 * x * sg) * math.exp(-x * (1 - sg) ** 2)
+            want = np.array([m0 * integrate.quad(f, d.me[k] / m0, d.me[k + 1] / m0, epsrel=1e-12, limit=200)[0]
+                             for k in range(d.n_bins)])
+        rho = _exp_bin_mass(d.me, m0)[None]
+        res = oracle_mod.Oracle(d).step(rho, t)
+        assert res["status"][0] == 0
+        assert res["rho"].sum() == pytest.approx(rho.sum(), rel=1e-12)
+        errs.append(np.abs(res["rho"][0] - want).sum() / want.sum())
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, errs
+    assert errs[2] < 1e-2, errs
+
+
 def test_fixed_step_convergence_on_constant_kernel(oracle_mod):
     """Third-order convergence of the coagulation integration itself."""
     N, m0, N0, K = 48, 2.0 ** -40, 1.0, 1e-6
