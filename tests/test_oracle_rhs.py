@@ -79,6 +79,25 @@ def test_split_fractions_sum_to_one_and_bracket(oracle_mod, split):
             assert d.me[l] <= mx < d.me[l + 1]
 
 
+def test_equal_masses_leave_no_remnant(oracle_mod):
+    """Eq. (fragrem): a collision of equal masses fragments completely (no
+    remnant, 2 m_i in fragments); otherwise the remnant is less than the
+    target's mass and shrinks as the projectile grows."""
+    d = synth.column_1x32()
+    o = oracle_mod.Oracle(d)
+    m = d.m
+    for i in range(d.n_bins):
+        oi, od = o.pair_map(i, i)
+        assert od[4] == 0.0 and od[5] == pytest.approx(2 * m[i], rel=1e-15)
+        prev = None
+        for j in range(i):
+            oi, od = o.pair_map(i, j)
+            assert 0.0 <= od[4] < m[i]
+            if prev is not None:
+                assert od[4] <= prev
+            prev = od[4]
+
+
 def test_exact_grid_hit_goes_to_one_bin(oracle_mod):
     d = linear_disc(16, 2.0 ** -30)   # power of two: sums on the grid are exact
     o = oracle_mod.Oracle(d)
