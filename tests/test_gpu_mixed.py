@@ -306,3 +306,27 @@ def test_full_size_large_grid_short_integration_replayed(coag_mod, oracle_mod):
     got = y.cpu().numpy()[cells]
     assert np.all(np.abs(got - want) <= 1e-5 * np.abs(want) + 1e-10 * S[:, None])
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_non_finite_cell_fails_alone(coag_mod, precision):
+    """A NaN in one cell's state: that cell ends with ENONFINITE, every other
+    cell succeeds and equals a clean integration bitwise (a slot's generated
+    operand rows reach only that slot's outputs)."""
+    d = synth.make_disc(4, 64, 40, 1e-5, 1.0, 5.0, 100.0, 50.0, seed=5)
+    bad = 77
+    rho = d.rho0.copy()
+    rho[bad, 3] = np.nan
+    g = coag_mod.Coag(d, precision)
+    rec = g.set_records(4000)
+    y = g.state(rho)
+    st = g.step(y, d.t_span, check=False)
+    assert st["status"] == coag_mod.ENONFINITE and st["n_failed"] == 1
+    status = rec["status"].cpu().numpy()
+    ok = np.arange(d.n_cells) != bad
+    assert status[bad] == coag_mod.ENONFINITE and np.all(status[ok] == 0)
+    g.set_records(0)
+    y2 = g.state(d.rho0)
+    assert g.step(y2, d.t_span)["status"] == 0
+    assert np.array_equal(y.cpu().numpy()[ok], y2.cpu().numpy()[ok])
+    g.close()
