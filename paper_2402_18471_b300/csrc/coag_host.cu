@@ -536,7 +536,11 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
                 return fail(nullptr, CUDISC_EINVAL,
                             "mixed_tile_stages / mixed_k_stages do not fit the shared memory at this size");
             }
-            e = cudaMalloc(&c->d_K32, (size_t)c->n_cells * c->n_blk * cdc::kBlkPairs * sizeof(float2));
+            // zeroed once: groups of four slots that lie wholly past a block's
+            // diagonal are never written by the kernel builder
+            const size_t k32 = (size_t)c->n_cells * c->n_blk * cdc::kBlkPairs * sizeof(float2);
+            e = cudaMalloc(&c->d_K32, k32);
+            if (e == cudaSuccess) e = cudaMemset(c->d_K32, 0, k32);
             // the slot groups' tables: [group][block][8 chunks][64 slots] x 16 B
             // (zeroed: slots that never hold a cell multiply zero stage inputs by it)
             const size_t kslot = (size_t)c->mix_G * c->n_blk * 8 * 64 * sizeof(float4);
