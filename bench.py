@@ -341,7 +341,8 @@ def batch_measure(precision, steps, warmup, t_span_yr=None):
     cell-substeps per second of the whole batch step, timed with CUDA events
     on the stream the batch joins on, and the worst per-disc mass error.
     Then the adjoint of every 4th disc's step (discs 0, 4, 8, ...) through
-    the same contexts, with the loss of small grains above Z = H."""
+    the same contexts, with the loss of small grains above Z = H, its
+    per-pair work in double-float."""
     import torch
     from paper_2402_18471_b300 import coag
     discs = synth.batch_32_discs()
@@ -371,6 +372,7 @@ def batch_measure(precision, steps, warmup, t_span_yr=None):
     for i in range(0, len(discs), 4):
         d = discs[i]
         w = torch.as_tensor(synth.adjoint_loss_weights(d), device="cuda")
+        b.disc(i).set_adjoint_precision("double_float")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g0, ga, gv = b.disc(i).vjp(init[i], w, t_span=t_span)
@@ -385,7 +387,8 @@ def batch_measure(precision, steps, warmup, t_span_yr=None):
             "n_bins": [min(d.n_bins for d in discs), max(d.n_bins for d in discs)],
             "t_span_yr": t_span / synth.CONST["yr"], "accepted_per_step": acc // steps,
             "mass_err_max_per_disc": mass,
-            "adjoint_every_4th_disc": {"discs": len(adj), "seconds_total": sum(a["s"] for a in adj),
+            "adjoint_every_4th_disc": {"discs": len(adj), "precision": "double_float",
+                                       "seconds_total": sum(a["s"] for a in adj),
                                        "all_finite": all(a["finite"] for a in adj), "per_disc": adj}}
 
 
@@ -584,9 +587,10 @@ def large_grid_key(args, pk):
 
 def adjoint_key(pk):
     """The adjoint workload (64 R x 32 Z x 80 bins, 2000 yr): the mixed
-    forward integration with records, then the FP64 adjoint of the same
-    steps (dL/d rho0, dL/d alpha, dL/d v_frag of the small-grain mass above
-    Z = H), timed by the library's CUDA events."""
+    forward integration with records, then the adjoint of the same steps
+    (dL/d rho0, dL/d alpha, dL/d v_frag of the small-grain mass above Z = H)
+    in FP64 and in double-float, each timed by the library's CUDA events;
+    the double-float gradients' largest difference from the FP64 ones."""
     import torch
     from paper_2402_18471_b300 import coag
     d = synth.adjoint_64x32()
@@ -598,26 +602,40 @@ def adjoint_key(pk):
     y, hs, nh, st = records_run(g, d, cap)
     hs_t = torch.as_tensor(hs, device="cuda")
     nh_t = torch.as_tensor(nh, device="cuda")
-    g.vjp(rho0, w, hs_t, nh_t)            # warm-up (builds the adjoint tables)
-    ts = []
-    for _ in range(3):
-        torch.cuda.synchronize()
-        g.vjp(rho0, w, hs_t, nh_t)
-        ts.append(g.timings()["vjp_ms"])
+    ms, grads = {}, {}
+    for prec in ("fp64", "double_float"):
+        g.set_adjoint_precision(prec)
+        g.vjp(rho0, w, hs_t, nh_t)            # warm-up (builds the adjoint tables)
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            out = g.vjp(rho0, w, hs_t, nh_t)
+            ts.append(g.timings()["vjp_ms"])
+        ms[prec] = float(np.median(ts))
+        grads[prec] = [x.cpu().numpy() for x in out]
     g.close()
+    (h0, ha, hv), (f0, fa, fv) = grads["fp64"], grads["double_float"]
+    hot = np.abs(h0).max(1) > 0
     N = d.n_bins
     Np = N * (N + 1) // 2
     substeps = int(nh.sum())
-    ms = float(np.median(ts))
     # per substep 9 right-hand-side-like FP64 passes (3 forward recomputes,
     # 3 transposed right-hand sides, 3 derivative gathers), each about the
     # forward's 2 x 13 flops per pair plus the fragment spread
     flops = 9 * (2 * 13 * Np + N * (N + 1)) * substeps
+    m64 = ms["fp64"]
     return {"workload": "adjoint_64x32_N80", "n_cells": d.n_cells, "n_bins": N, "t_span_yr": 2000.0,
-            "substeps": substeps, "forward_ms": st["elapsed_ms"], "adjoint_ms": ms,
-            "adjoint_substeps_per_s": substeps / (ms / 1e3),
-            "fp64_tflops_est": flops / (ms / 1e3) / 1e12,
-            "fp64_frac_est": flops / (ms / 1e3) / 1e12 / FP64_NOMINAL_TFLOPS,
+            "substeps": substeps, "forward_ms": st["elapsed_ms"], "adjoint_ms": m64,
+            "adjoint_substeps_per_s": substeps / (m64 / 1e3),
+            "fp64_tflops_est": flops / (m64 / 1e3) / 1e12,
+            "fp64_frac_est": flops / (m64 / 1e3) / 1e12 / FP64_NOMINAL_TFLOPS,
+            "double_float": {
+                "adjoint_ms": ms["double_float"], "speedup_over_fp64": m64 / ms["double_float"],
+                "grad_rho0_diff_over_cell_max": float((np.abs(f0[hot] - h0[hot]) /
+                                                       np.abs(h0[hot]).max(1, keepdims=True)).max()),
+                "grad_alpha_diff_over_max": float(np.abs(fa - ha).max() / np.abs(ha).max()),
+                "grad_vfrag_rel_diff": float(abs(fv[0] - hv[0]) / abs(hv[0])),
+                "note": "per-pair work in FP32 pairs (cudisc_coag_set_adjoint_precision), stage vectors FP64"},
             "note": "FP64 pipe fraction against the nominal 1.25 TFLOP/s, flops estimated as 9 passes of "
                     "the forward's per-pair work per substep"}
 

@@ -69,6 +69,14 @@ typedef enum {
                                arithmetic, FP64 state and mass budget */
 } cudisc_precision;
 
+/* Arithmetic of the adjoint's per-pair work (cudisc_coag_set_adjoint_precision). */
+typedef enum {
+    CUDISC_ADJOINT_FP64 = 0,          /* FP64 (the default) */
+    CUDISC_ADJOINT_DOUBLE_FLOAT = 1   /* pairs of FP32 numbers (h + l, ~48
+                                         significant bits, FP32 exponent range)
+                                         on the FP32 pipes */
+} cudisc_adjoint_precision;
+
 typedef enum {
     CUDISC_KERNEL_PHYSICAL = 0,  /* K = pi (a_i + a_j)^2 dv (Eq. kernel) */
     CUDISC_KERNEL_CONSTANT = 1,  /* K = kernel_const (closed-form tests) */
@@ -577,7 +585,8 @@ cudisc_status cudisc_coag_mixed_rings(const cudisc_coag_ctx *ctx, int *tile_stag
  * substeps, and each 16-substep segment is recomputed before its reverse
  * sweep.  Arithmetic is FP64 for contexts of either precision (FP32 loses
  * the gradient with respect to large grains, a small difference of
- * sweep-up sums); K and K p_frag are the context's current tables
+ * sweep-up sums), or double-float for the per-pair work after
+ * cudisc_coag_set_adjoint_precision; K and K p_frag are the context's current tables
  * (cudisc_coag_build_kernel), so a CUDISC_MIXED_TF32 context differentiates
  * its own map with FP32 kernel tables.  The context's
  * adjoint tables are built on the first call and its checkpoint storage
@@ -592,6 +601,20 @@ cudisc_status cudisc_coag_vjp(cudisc_coag_ctx *ctx, const double *rho0, double t
                               const double *hs, const long long *n_h, long long stride,
                               const double *grad_rhoT, double *grad_rho0, double *grad_alpha,
                               double *grad_vfrag);
+
+/* Arithmetic of the per-pair work of later cudisc_coag_vjp calls on ctx
+ * (the paper has no adjoint; see cudisc_coag_vjp): CUDISC_ADJOINT_FP64 (the
+ * default) or CUDISC_ADJOINT_DOUBLE_FLOAT, in which the forward recompute's
+ * right-hand sides and the transposed right-hand sides run in double-float
+ * (each value an unevaluated sum of two FP32 numbers; error-free FP32 sums
+ * and products), while the stage vectors, checkpoints and parameter-gradient
+ * sums stay FP64.  B300 executes FP64 at a small fraction of its FP32 rate,
+ * and the FP64 adjoint is bound by its FP64 pipe.  The FP32 exponent range
+ * applies to the per-pair terms: products below ~1e-38 of the cell's dust
+ * mass scale flush to zero.  The adjoint tables are rebuilt for the new type
+ * at the next cudisc_coag_vjp.  EINVAL for another value or a NULL ctx.
+ * Host only; allocates nothing. */
+cudisc_status cudisc_coag_set_adjoint_precision(cudisc_coag_ctx *ctx, int precision);
 
 void cudisc_coag_destroy(cudisc_coag_ctx *ctx);
 

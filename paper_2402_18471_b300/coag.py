@@ -129,6 +129,7 @@ def lib():
         L.cudisc_dust_destroy.argtypes = [v]
         L.cudisc_dust_destroy.restype = None
         L.cudisc_coag_set_v_frag.argtypes = [v, d]
+        L.cudisc_coag_set_adjoint_precision.argtypes = [v, C.c_int]
         L.cudisc_coag_vjp.argtypes = [v, v, d, v, v, C.c_longlong, v, v, v, v]
         L.cudisc_coag_destroy.argtypes = [v]
         L.cudisc_coag_destroy.restype = None
@@ -138,7 +139,7 @@ def lib():
         for fn in ("cudisc_coag_init", "cudisc_coag_build_kernel", "cudisc_coag_build_kernel_async", "cudisc_coag_get_kernel",
                    "cudisc_coag_rhs", "cudisc_coag_step", "cudisc_coag_set_records",
                    "cudisc_coag_replay", "cudisc_coag_step_static_scratch", "cudisc_coag_step_host",
-                   "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_vjp",
+                   "cudisc_coag_get_timings", "cudisc_coag_set_v_frag", "cudisc_coag_set_adjoint_precision", "cudisc_coag_vjp",
                    "cudisc_coag_mixed_cluster", "cudisc_coag_scratch_bytes", "cudisc_coag_mixed_pair", "cudisc_coag_mixed_rings", "cudisc_coag_set_fault_injection", "cudisc_partition", "cudisc_dust_init", "cudisc_dust_update_gas",
                    "cudisc_dust_step", "cudisc_dust_geometry", "cudisc_coag_step_async", "cudisc_coag_step_wait",
                    "cudisc_coag_init_batched", "cudisc_coag_batch_ctx", "cudisc_coag_batch_build_kernel",
@@ -418,6 +419,14 @@ def cudisc_coag_set_v_frag(ctx, v_frag: float):
     _check(lib().cudisc_coag_set_v_frag(ctx, float(v_frag)), ctx)
 
 
+ADJOINT_PRECISIONS = {"fp64": 0, "double_float": 1}   # cudisc_adjoint_precision
+
+
+def cudisc_coag_set_adjoint_precision(ctx, precision):
+    p = ADJOINT_PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(lib().cudisc_coag_set_adjoint_precision(ctx, p), ctx)
+
+
 def cudisc_coag_vjp(ctx, rho0_ptr, t_span, hs_ptr, n_ptr, stride, grad_rhoT_ptr, grad_rho0_ptr,
                     grad_alpha_ptr, grad_vfrag_ptr):
     _check(lib().cudisc_coag_vjp(ctx, rho0_ptr, float(t_span), hs_ptr, n_ptr, int(stride),
@@ -676,6 +685,11 @@ class Coag:
 
     def set_v_frag(self, v_frag: float):
         cudisc_coag_set_v_frag(self.ctx, float(v_frag))
+
+    def set_adjoint_precision(self, precision):
+        """Arithmetic of later vjp calls' per-pair work: "fp64" (default) or
+        "double_float" (FP32 pairs on the FP32 pipes)."""
+        cudisc_coag_set_adjoint_precision(self.ctx, precision)
 
     def vjp(self, rho0, grad_rhoT, hs=None, n_h=None, t_span=0.0):
         """Gradients of sum(grad_rhoT * rho(T)) with respect to rho0, the

@@ -636,6 +636,15 @@ cudisc_status cudisc_coag_build_kernel_async(cudisc_coag_ctx *c)
     return CUDISC_OK;
 }
 
+cudisc_status cudisc_coag_set_adjoint_precision(cudisc_coag_ctx *c, int precision)
+{
+    if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");
+    if (precision != CUDISC_ADJOINT_FP64 && precision != CUDISC_ADJOINT_DOUBLE_FLOAT)
+        return fail(c, CUDISC_EINVAL, "adjoint precision must be CUDISC_ADJOINT_FP64 or CUDISC_ADJOINT_DOUBLE_FLOAT");
+    c->adj_prec = precision;
+    return CUDISC_OK;
+}
+
 cudisc_status cudisc_coag_set_v_frag(cudisc_coag_ctx *c, double v_frag)
 {
     if (!c) return fail(nullptr, CUDISC_EINVAL, "ctx is NULL");

@@ -134,6 +134,7 @@ struct cudisc_coag_ctx {
     cudaEvent_t evb[3] = {nullptr, nullptr, nullptr};   // prep | kbuild | end
     double t_prep = 0.0, t_kbuild = 0.0, t_step = 0.0, t_vjp = 0.0;   // ms, last call
     cdc::VjpState *vjp = nullptr;      // built on the first cudisc_coag_vjp
+    int adj_prec = CUDISC_ADJOINT_FP64;   // arithmetic of cudisc_coag_vjp's per-pair work
 
     cdc::DevTables tables() const;
 };

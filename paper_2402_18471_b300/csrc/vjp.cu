@@ -33,8 +33,12 @@
 // h S), as in the mixed-precision integrator, so that products of small bin
 // densities stay well inside the floating-point range.  The adjoint runs in
 // FP64 for contexts of either precision (T = double; a mixed context supplies
-// its FP32 kernel tables, widened).  FP32 was measured and rejected for both
-// halves:
+// its FP32 kernel tables, widened), or, on request, in double-float (T = df,
+// FP32 pairs of ~48 significant bits, see dfloat.cuh): the per-pair work of
+// the forward recompute and of the transposed right-hand sides then runs on
+// the FP32 pipes, while the N-vectors of the BS3 stages, the checkpoints and
+// the parameter-gradient sums stay FP64.  Plain FP32 was measured and
+// rejected for both halves:
 //   - an FP32 forward recompute puts ~1e-4 of the largest gradient component
 //     into a coagulation-fragmentation equilibrium, whose gradient is
 //     sensitive to trajectory errors;
@@ -42,12 +46,14 @@
 //     large grains, which is a small difference of sweep-up sums (relative
 //     error O(1) in some cells of a 64 x 32 x 80-bin disc).
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <vector>
 
 #include "coag_internal.h"
 #include "oc07.cuh"
+#include "dfloat.cuh"
 
 namespace cdc {
 
@@ -63,6 +69,8 @@ struct VjpState {
     void *Ntab = nullptr;                                                           // T
     unsigned short *pk = nullptr, *pl = nullptr;
     void *pa = nullptr, *pb = nullptr, *pmf = nullptr;                              // T
+    void *ent_ab = nullptr, *fent_m = nullptr;      // forward gather coefficients, T ([nnz][2], [fnnz])
+    int tprec = -1;                 // type of the tables: CUDISC_ADJOINT_FP64 or _DOUBLE_FLOAT
     int *pair_q = nullptr;
     void *kt = nullptr;             // [5][n_cells][Np] T: K, KF, dK/da, dKF/da, dKF/dvf
     double *ckpt = nullptr;         // [n_cells][seg_cap][N]
@@ -84,9 +92,9 @@ struct VjpArgs {
     int N, Np, n_cells, n_ent;
     const unsigned int *pij;
     const int *row, *ent_p, *frow, *fent_p;
-    const double2 *ent_ab;                    // forward gather (FP64)
-    const double *fent_m, *Ntab64;
-    const T *Ntab;                            // transposed fragment spread (type T)
+    const T *ent_ab;                          // forward gather coefficients [nnz][2] (type T)
+    const T *fent_m;
+    const T *Ntab;                            // fragment spread [l][k] (type T), both directions
     const unsigned short *pk, *pl;
     const T *pa, *pb, *pmf;
     const T *K, *KF, *dKa, *dKFa, *dKFv;      // [n_cells][Np]
@@ -104,53 +112,53 @@ template <typename T>
 __device__ __forceinline__ T warp_sum(T s)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    for (int o = 16; o > 0; o >>= 1) s += shfl_xor(s, o);
     return s;
 }
 
-// f = rhs(y) for one cell in FP64.  XK, XF: [Np] scratch; fl: [N] scratch.
+// f = rhs(y) for one cell, y and the per-pair arithmetic in type T, f FP64.
+// XK, XF: [Np] scratch; fT, fl: [N] scratch.
 template <typename T>
 __device__ void rhs_cell(const VjpArgs<T> &A, const T *__restrict__ Kc, const T *__restrict__ KFc,
-                         const double *y, double *f, double *XK, double *XF, double *fl)
+                         const T *y, double *f, T *XK, T *XF, T *fT, T *fl)
 {
     const int N = A.N, Np = A.Np;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     for (int p = tid; p < Np; p += blockDim.x) {
         const unsigned int ij = __ldg(A.pij + p);
-        const double x = y[ij >> 16] * y[ij & 0xffff];
-        XK[p] = x * (double)Kc[p];
-        XF[p] = x * (double)KFc[p];
+        const T x = y[ij >> 16] * y[ij & 0xffff];
+        XK[p] = x * Kc[p];
+        XF[p] = x * KFc[p];
     }
     __syncthreads();
     // per output bin k: gather its entries; rows N..2N-1 gather the fragment
     // mass per largest-fragment bin l
     for (int r = warp; r < 2 * N; r += nw) {
-        double s = 0.0;
+        T s = T(0);
         if (r < N) {
             const int e1 = __ldg(A.row + r + 1);
             for (int e = __ldg(A.row + r) + lane; e < e1; e += 32) {
                 const int p = __ldg(A.ent_p + e);
-                const double2 ab = __ldg(A.ent_ab + e);
-                s += XK[p] * ab.x + XF[p] * ab.y;
+                s += XK[p] * ldg(A.ent_ab + 2 * e) + XF[p] * ldg(A.ent_ab + 2 * e + 1);
             }
         } else {
             const int l = r - N;
             const int e1 = __ldg(A.frow + l + 1);
             for (int e = __ldg(A.frow + l) + lane; e < e1; e += 32)
-                s += XF[__ldg(A.fent_p + e)] * __ldg(A.fent_m + e);
+                s += XF[__ldg(A.fent_p + e)] * ldg(A.fent_m + e);
         }
         s = warp_sum(s);
         if (lane == 0) {
-            if (r < N) f[r] = s;
+            if (r < N) fT[r] = s;
             else fl[r - N] = s;
         }
     }
     __syncthreads();
     // spread the gathered fragment mass: f_k += sum_{l >= k} N_k(m^e_{l+1}) F_l
     for (int k = tid; k < N; k += blockDim.x) {
-        double s = f[k];
-        for (int l = k; l < N; l++) s += __ldg(A.Ntab64 + (size_t)l * N + k) * fl[l];
-        f[k] = s;
+        T s = fT[k];
+        for (int l = k; l < N; l++) s += ldg(A.Ntab + (size_t)l * N + k) * fl[l];
+        f[k] = (double)s;
     }
     __syncthreads();
 }
@@ -167,7 +175,7 @@ __device__ void rhs_vjp_cell(const VjpArgs<T> &A, const T *__restrict__ Kc, cons
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     for (int l = warp; l < N; l += nw) {
         T s = T(0);
-        for (int k = lane; k <= l; k += 32) s += __ldg(A.Ntab + (size_t)l * N + k) * v[k];
+        for (int k = lane; k <= l; k += 32) s += ldg(A.Ntab + (size_t)l * N + k) * v[k];
         s = warp_sum(s);
         if (lane == 0) Fv[l] = s;
     }
@@ -180,10 +188,10 @@ __device__ void rhs_vjp_cell(const VjpArgs<T> &A, const T *__restrict__ Kc, cons
         for (int e = 0; e < A.n_ent; e++) {
             const size_t o = (size_t)e * Np + p;
             const T vk = v[__ldg(A.pk + o)];
-            Ga += __ldg(A.pa + o) * vk;
-            Gb += __ldg(A.pb + o) * vk;
+            Ga += ldg(A.pa + o) * vk;
+            Gb += ldg(A.pb + o) * vk;
         }
-        Gb += __ldg(A.pmf + p) * Fv[__ldg(A.pl + p)];
+        Gb += ldg(A.pmf + p) * Fv[__ldg(A.pl + p)];
         const T xx = x[i] * x[j];
         gq[p] = Kc[p] * Ga + KFc[p] * Gb;
         tA += xx * (Ga * dKa[p] + Gb * dKFa[p]);
@@ -209,21 +217,27 @@ __global__ void __launch_bounds__(kVjpThreads) vjp_kernel(VjpArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *red = reinterpret_cast<double *>(smem_raw);          // 64 doubles
-    double *XK = red + 64;                                        // [Np]; gq (T) aliases it
-    double *XF = XK + A.Np;
-    double *v64 = XF + A.Np;
+    T *XK = reinterpret_cast<T *>(red + 64);                      // [Np]; gq aliases it
+    T *XF = XK + A.Np;
+    double *v64 = reinterpret_cast<double *>(XF + A.Np);
     const int N = A.N, Np = A.Np;
     double *y = v64, *k1 = v64 + N, *k2 = v64 + 2 * N, *k3 = v64 + 3 * N, *st = v64 + 4 * N;
-    double *fl = v64 + 5 * N, *lam = v64 + 6 * N, *bar = v64 + 7 * N;
+    double *lam = v64 + 6 * N, *bar = v64 + 7 * N;   // v64 + 5 N: unused
     T *vT = reinterpret_cast<T *>(v64 + kVecs64 * N);
     T *xs = vT, *v = vT + N, *out = vT + 2 * N, *Fv = vT + 3 * N;
-    T *gq = reinterpret_cast<T *>(XK);
+    T *gq = XK;
     const int c = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const size_t cp = (size_t)c * Np;
     const T *Kc = A.K + cp, *KFc = A.KF + cp, *dKa = A.dKa + cp, *dKFa = A.dKFa + cp,
             *dKFv = A.dKFv + cp;
     const double *r0 = A.rho0 + (size_t)c * N;
+    // f = rhs(yd): the input in type T (xs), out and Fv as the gather's scratch
+    auto rhs = [&](const double *yd, double *f) {
+        for (int k = tid; k < N; k += blockDim.x) xs[k] = (T)yd[k];
+        __syncthreads();
+        rhs_cell(A, Kc, KFc, xs, f, XK, XF, out, Fv);
+    };
 
     // scale: the cell's initial dust mass
     if (warp == 0) {
@@ -246,13 +260,13 @@ __global__ void __launch_bounds__(kVjpThreads) vjp_kernel(VjpArgs<T> A)
         const double h = hc[t] * S;
         if (t % kSeg == 0)
             for (int k = tid; k < N; k += blockDim.x) ck[(size_t)(t / kSeg) * N + k] = y[k];
-        rhs_cell(A, Kc, KFc, y, k1, XK, XF, fl);
+        rhs(y, k1);
         for (int k = tid; k < N; k += blockDim.x) st[k] = y[k] + (0.5 * h) * k1[k];
         __syncthreads();
-        rhs_cell(A, Kc, KFc, st, k2, XK, XF, fl);
+        rhs(st, k2);
         for (int k = tid; k < N; k += blockDim.x) st[k] = y[k] + (0.75 * h) * k2[k];
         __syncthreads();
-        rhs_cell(A, Kc, KFc, st, k3, XK, XF, fl);
+        rhs(st, k3);
         for (int k = tid; k < N; k += blockDim.x)
             y[k] += h * ((2.0 / 9.0) * k1[k] + (1.0 / 3.0) * k2[k] + (4.0 / 9.0) * k3[k]);
         __syncthreads();
@@ -269,19 +283,19 @@ __global__ void __launch_bounds__(kVjpThreads) vjp_kernel(VjpArgs<T> A)
         for (long long t = t0; t < t1; t++) {
             const double h = hc[t] * S;
             double *slot = sb + (size_t)(t - t0) * 3 * N;
-            rhs_cell(A, Kc, KFc, y, k1, XK, XF, fl);
+            rhs(y, k1);
             for (int k = tid; k < N; k += blockDim.x) {
                 slot[k] = y[k];
                 slot[N + k] = k1[k];
                 st[k] = y[k] + (0.5 * h) * k1[k];
             }
             __syncthreads();
-            rhs_cell(A, Kc, KFc, st, k2, XK, XF, fl);
+            rhs(st, k2);
             for (int k = tid; k < N; k += blockDim.x) slot[2 * N + k] = k2[k];
             if (t + 1 < t1) {
                 for (int k = tid; k < N; k += blockDim.x) st[k] = y[k] + (0.75 * h) * k2[k];
                 __syncthreads();
-                rhs_cell(A, Kc, KFc, st, k3, XK, XF, fl);
+                rhs(st, k3);
                 for (int k = tid; k < N; k += blockDim.x)
                     y[k] += h * ((2.0 / 9.0) * k1[k] + (1.0 / 3.0) * k2[k] + (4.0 / 9.0) * k3[k]);
             }
@@ -545,6 +559,11 @@ cudaError_t build_tables_t(cudisc_coag_ctx *c, VjpState *S)
 
     S->n_ent = n_ent;
     S->tsz = sizeof(T);
+    S->tprec = std::is_same<T, df>::value ? CUDISC_ADJOINT_DOUBLE_FLOAT : CUDISC_ADJOINT_FP64;
+    std::vector<double> ab2(2 * ent_ab.size());
+    for (size_t q = 0; q < ent_ab.size(); q++) { ab2[2 * q] = ent_ab[q].x; ab2[2 * q + 1] = ent_ab[q].y; }
+    if ((e = upload_as<T>(&S->ent_ab, ab2, st)) != cudaSuccess) return e;
+    if ((e = upload_as<T>(&S->fent_m, fent_m, st)) != cudaSuccess) return e;
     if ((e = upload_as<T>(&S->Ntab, Ntab, st)) != cudaSuccess) return e;
     if ((e = upload_as<T>(&S->pa, pa, st)) != cudaSuccess) return e;
     if ((e = upload_as<T>(&S->pb, pb, st)) != cudaSuccess) return e;
@@ -588,7 +607,7 @@ cudaError_t launch_t(cudisc_coag_ctx *c, VjpState *S, const double *rho0, const 
     A.N = N; A.Np = Np; A.n_cells = c->n_cells; A.n_ent = S->n_ent;
     A.pij = c->d_pair_ij;
     A.row = c->d_row; A.ent_p = c->d_ent_p; A.frow = c->d_frow; A.fent_p = c->d_fent_p;
-    A.ent_ab = c->d_ent_ab; A.fent_m = c->d_fent_m; A.Ntab64 = c->d_Ntab;
+    A.ent_ab = static_cast<const T *>(S->ent_ab); A.fent_m = static_cast<const T *>(S->fent_m);
     A.Ntab = static_cast<const T *>(S->Ntab);
     A.pk = S->pk; A.pl = S->pl;
     A.pa = static_cast<const T *>(S->pa); A.pb = static_cast<const T *>(S->pb);
@@ -610,10 +629,26 @@ cudaError_t launch_t(cudisc_coag_ctx *c, VjpState *S, const double *rho0, const 
     return cudaGetLastError();
 }
 
+// the tables built for one arithmetic type (kept: checkpoints and records)
+void free_tables(VjpState *S)
+{
+    void *ptrs[] = {S->Ntab, S->pk, S->pl, S->pa, S->pb, S->pmf, S->ent_ab, S->fent_m,
+                    S->pair_q, S->kt, S->segbuf, S->vf_part, S->cell_status};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    S->Ntab = S->pa = S->pb = S->pmf = S->ent_ab = S->fent_m = S->kt = nullptr;
+    S->pk = S->pl = nullptr;
+    S->pair_q = S->cell_status = nullptr;
+    S->segbuf = S->vf_part = nullptr;
+    S->tables = false;
+    S->tprec = -1;
+}
+
 } // namespace
 
 bool vjp_fits(const cudisc_coag_ctx *c)
 {
+    static_assert(sizeof(df) == sizeof(double), "both adjoint types share one shared-memory layout");
     return vjp_smem<double>(c->N, c->Np) <= 232448;
 }
 
@@ -622,8 +657,9 @@ cudaError_t vjp_prepare(cudisc_coag_ctx *c, long long max_steps)
     if (!c->vjp) c->vjp = new VjpState();
     VjpState *S = c->vjp;
     cudaError_t e = cudaSuccess;
+    if (S->tables && S->tprec != c->adj_prec) free_tables(S);
     if (!S->tables) {
-        e = build_tables_t<double>(c, S);
+        e = c->adj_prec == CUDISC_ADJOINT_DOUBLE_FLOAT ? build_tables_t<df>(c, S) : build_tables_t<double>(c, S);
         if (e != cudaSuccess) return e;
     }
     const long long need = std::max<long long>(1, (max_steps + kSeg - 1) / kSeg);
@@ -668,6 +704,8 @@ cudaError_t launch_vjp(cudisc_coag_ctx *c, const double *rho0, const double *hs,
                        const long long *n_h, long long stride, const double *w, double *g_rho0,
                        double *g_alpha, double *g_vf)
 {
+    if (c->vjp->tprec == CUDISC_ADJOINT_DOUBLE_FLOAT)
+        return launch_t<df>(c, c->vjp, rho0, hs, n_h, stride, w, g_rho0, g_alpha, g_vf);
     return launch_t<double>(c, c->vjp, rho0, hs, n_h, stride, w, g_rho0, g_alpha, g_vf);
 }
 
@@ -685,6 +723,8 @@ void vjp_free(cudisc_coag_ctx *c)
                     S->rec_n, S->rec_st, S->rho_tmp};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    if (S->ent_ab) cudaFree(S->ent_ab);
+    if (S->fent_m) cudaFree(S->fent_m);
     delete S;
     c->vjp = nullptr;
 }

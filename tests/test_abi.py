@@ -98,6 +98,7 @@ def test_null_context_is_an_error_not_a_crash():
     assert L.cudisc_coag_step(None, None, 1.0, None, None) == coag.EINVAL
     assert L.cudisc_coag_vjp(None, None, 1.0, None, None, 0, None, None, None, None) == coag.EINVAL
     assert L.cudisc_coag_set_v_frag(None, 1.0) == coag.EINVAL
+    assert L.cudisc_coag_set_adjoint_precision(None, 0) == coag.EINVAL
     t = coag.cudisc_timings()
     assert L.cudisc_coag_get_timings(None, C.byref(t)) == coag.EINVAL
     cl, gr = C.c_int(), C.c_int()

@@ -293,3 +293,57 @@ def test_adjoint_workload_sampled(coag_mod, oracle_mod):
     ea = (np.abs(ha[cells] - want[1]) / np.abs(want[1]).max()).max()
     assert e0 <= 1e-3, e0
     assert ea <= 2e-3, ea
+
+
+def df_vs_fp64(coag_mod, d, precision, w, hs, n_h):
+    """The same context's adjoint in FP64 and then in double-float."""
+    g = coag_mod.Coag(d, precision)
+    args = (g.state(d.rho0), torch.as_tensor(w, device="cuda"), torch.as_tensor(hs, device="cuda"),
+            torch.as_tensor(n_h, device="cuda"))
+    out = []
+    for p in ("fp64", "double_float", "fp64"):
+        g.set_adjoint_precision(p)
+        g0, ga, gv = g.vjp(*args)
+        out.append((g0.cpu().numpy(), ga.cpu().numpy(), float(gv.cpu()[0])))
+    g.close()
+    return out
+
+
+# Double-float adjoint (cudisc_coag_set_adjoint_precision): each per-pair
+# term carries ~2^-46 of its size instead of FP64's 2^-53, i.e. ~2e2 times the
+# FP64 adjoint's rounding; the sums whose cancellation the tolerances above
+# allow for scale it the same way.  Against the FP64 GPU adjoint of the same
+# map: 1e-7 of the cell's largest component, 1e-6 for the scalar gradients.
+@pytest.mark.parametrize("case", list(CASES))
+def test_double_float_adjoint_matches_fp64(coag_mod, oracle_mod, case):
+    d = CASES[case]()
+    _, hs, n_h = oracle_log(oracle_mod, d)
+    w = weights(d)
+    first, df, again = df_vs_fp64(coag_mod, d, "fp64", w, hs, n_h)
+    # switching back rebuilds the FP64 tables: bitwise the first result
+    assert all(np.array_equal(a, b) for a, b in zip(first[:2], again[:2])) and first[2] == again[2]
+    check(df, first, 1e-7, f"{case}/double_float", 1e-6)
+
+
+def test_double_float_adjoint_on_the_adjoint_workload(coag_mod):
+    """64 R x 32 Z x 80 bins over 2000 yr with the mixed forward's records:
+    the double-float adjoint of the mixed context against its FP64 adjoint
+    on every cell."""
+    d = synth.adjoint_64x32()
+    w = synth.adjoint_loss_weights(d)
+    g = coag_mod.Coag(d, "mixed")
+    rec = g.set_records(4000)
+    assert g.step(g.state(d.rho0), d.t_span)["status"] == 0
+    g.set_records(0)
+    res = []
+    for p in ("fp64", "double_float"):
+        g.set_adjoint_precision(p)
+        g0, ga, gv = g.vjp(g.state(d.rho0), torch.as_tensor(w, device="cuda"), rec["dt"], rec["n"])
+        res.append((g0.cpu().numpy(), ga.cpu().numpy(), float(gv.cpu()[0])))
+    (h0, ha, hv), (g0, ga, gv) = res
+    assert np.isfinite(g0).all() and np.isfinite(ga).all() and np.isfinite(gv)
+    hot = np.flatnonzero(w.sum(1) > 0)
+    scale = np.abs(h0[hot]).max(1, keepdims=True)
+    assert (np.abs(g0[hot] - h0[hot]) / scale).max() <= 1e-7
+    assert np.abs(ga - ha).max() <= 1e-6 * np.abs(ha).max()
+    assert abs(gv - hv) <= 1e-6 * abs(hv)
