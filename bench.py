@@ -29,6 +29,13 @@ import time
 
 import numpy as np
 
+# The 32-disc batch runs one persistent kernel per disc on its own stream.
+# CUDA maps streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware queues (8 by
+# default), and discs whose streams share a queue then run one after another
+# (measured: 9.9 s per batch step instead of 4.2 s); the setting must precede
+# CUDA's initialisation.  The batch key replays one CUDA graph either way.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -353,17 +360,30 @@ def batch_measure(precision, steps, warmup, t_span_yr=None):
     init = [torch.as_tensor(np.ascontiguousarray(d.rho0), device="cuda") for d in discs]
     ys = [x.clone() for x in init]
     t_span = discs[0].t_span
-    ms, acc, mass = 0.0, 0, 0.0
-    for s in range(warmup + steps):
+    # the first warm-up is a synchronous batch step (it loads the kernels and
+    # sets their attributes); then the whole batch step, the discs' state
+    # copy-in and their 32 integrations forked from one stream, is captured
+    # as one CUDA graph and replayed
+    b.step(ys, t_span)
+    cap = torch.cuda.Stream()
+    cap.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap):
         for y, x in zip(ys, init):
             y.copy_(x)
+        b.step_async(ys, t_span)
+    ms, acc, mass = 0.0, 0, 0.0
+    w_left = max(warmup - 1, 0)            # warm-up replays after the synchronous one
+    for s in range(w_left + steps):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        stats = b.step(ys, t_span)
-        e1.record()
+        with torch.cuda.stream(cap):
+            e0.record()
+            graph.replay()
+            e1.record()
         torch.cuda.synchronize()
-        if s >= warmup:
+        stats = b.step_wait()
+        if s >= w_left:
             ms += e0.elapsed_time(e1)
             acc += sum(st["accepted"] for st in stats)
             mass = max([mass] + [st["mass_err_max"] for st in stats])
@@ -383,7 +403,7 @@ def batch_measure(precision, steps, warmup, t_span_yr=None):
     b.close()
     cells = sum(d.n_cells for d in discs)
     return {"value": acc / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
-            "n_discs": len(discs), "n_cells": cells,
+            "n_discs": len(discs), "n_cells": cells, "graph": "one CUDA graph per batch step (copy-in and all discs' integrations)",
             "n_bins": [min(d.n_bins for d in discs), max(d.n_bins for d in discs)],
             "t_span_yr": t_span / synth.CONST["yr"], "accepted_per_step": acc // steps,
             "mass_err_max_per_disc": mass,

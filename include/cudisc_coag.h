@@ -429,9 +429,27 @@ cudisc_status cudisc_coag_batch_build_kernel(cudisc_coag_batch *batch);
  * be NULL) per disc.  The discs' work waits for what is already queued on
  * stream (NULL: legacy default stream) and the call returns when all discs
  * are done.  Returns the worst status over the discs (their messages: the
- * discs' contexts). */
+ * discs' contexts).  The discs' persistent kernels run side by side only if
+ * their streams have hardware queues of their own: CUDA maps streams onto
+ * CUDA_DEVICE_MAX_CONNECTIONS queues (8 by default, set in the environment
+ * before CUDA initialises), and discs sharing a queue run one after another
+ * (a 32-disc batch took 9.9 s per step instead of 4.2 s).  A CUDA graph of
+ * cudisc_coag_batch_step_async runs them side by side either way. */
 cudisc_status cudisc_coag_batch_step(cudisc_coag_batch *batch, double *const *rho, double t_span,
                                      double *const *dt_cell, void *stream, cudisc_step_stats *stats);
+/* The same split in two, as cudisc_coag_step_async / _step_wait for one
+ * disc: _async issues every disc's integration (no kernel rebuild) on the
+ * disc's stream, forked from stream by an event and joined back to it, and
+ * returns without synchronising or allocating, so that the whole batch is
+ * one stretch of stream's work (a single CUDA graph when stream is being
+ * captured; issue one cudisc_coag_batch_step first, outside the capture, so
+ * that each disc's kernel attributes are set); _wait synchronises each disc
+ * and writes stats (host [n_discs], may be NULL) for the last issue.  EINVAL
+ * for NULL arguments or a bad t_span; a disc's launch error stops the issue
+ * at that disc. */
+cudisc_status cudisc_coag_batch_step_async(cudisc_coag_batch *batch, double *const *rho, double t_span,
+                                           double *const *dt_cell, void *stream);
+cudisc_status cudisc_coag_batch_step_wait(cudisc_coag_batch *batch, cudisc_step_stats *stats);
 void cudisc_coag_batch_destroy(cudisc_coag_batch *batch);
 
 /* Shards for several GPUs.  During a coagulation call every cell evolves on

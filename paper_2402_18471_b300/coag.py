@@ -130,6 +130,8 @@ def lib():
         L.cudisc_dust_destroy.restype = None
         L.cudisc_coag_set_v_frag.argtypes = [v, d]
         L.cudisc_coag_set_adjoint_precision.argtypes = [v, C.c_int]
+        L.cudisc_coag_batch_step_async.argtypes = [v, C.POINTER(v), d, C.POINTER(v), v]
+        L.cudisc_coag_batch_step_wait.argtypes = [v, C.POINTER(cudisc_step_stats)]
         L.cudisc_coag_vjp.argtypes = [v, v, d, v, v, C.c_longlong, v, v, v, v]
         L.cudisc_coag_destroy.argtypes = [v]
         L.cudisc_coag_destroy.restype = None
@@ -144,7 +146,7 @@ def lib():
                    "cudisc_dust_step", "cudisc_dust_geometry", "cudisc_coag_step_async", "cudisc_coag_step_wait",
                    "cudisc_coag_init_batched", "cudisc_coag_batch_ctx", "cudisc_coag_batch_build_kernel",
                    "cudisc_dust_source_update", "cudisc_dust_cfl_dt", "cudisc_hse_rho_gas", "cudisc_coag_batch_step", "cudisc_coag_step_spans", "cudisc_coag_subcycle",
-                   "cudisc_coag_subcycle_pending"):
+                   "cudisc_coag_subcycle_pending", "cudisc_coag_batch_step_async", "cudisc_coag_batch_step_wait"):
             getattr(L, fn).restype = C.c_int
         _lib = L
     return _lib
@@ -388,6 +390,21 @@ def cudisc_coag_batch_step(batch, rho_ptrs, t_span, dt_ptrs, stream_ptr, check=T
     dt = (C.c_void_p * n)(*dt_ptrs) if dt_ptrs is not None else None
     stats = (cudisc_step_stats * n)()
     st = lib().cudisc_coag_batch_step(batch, rho, float(t_span), dt, stream_ptr, stats)
+    if check:
+        _check(st)
+    return st, [x.as_dict() for x in stats]
+
+
+def cudisc_coag_batch_step_async(batch, rho_ptrs, t_span, dt_ptrs, stream_ptr):
+    n = len(rho_ptrs)
+    rho = (C.c_void_p * n)(*rho_ptrs)
+    dt = (C.c_void_p * n)(*dt_ptrs) if dt_ptrs is not None else None
+    _check(lib().cudisc_coag_batch_step_async(batch, rho, float(t_span), dt, stream_ptr))
+
+
+def cudisc_coag_batch_step_wait(batch, n, check=True):
+    stats = (cudisc_step_stats * n)()
+    st = lib().cudisc_coag_batch_step_wait(batch, stats)
     if check:
         _check(st)
     return st, [x.as_dict() for x in stats]
@@ -872,6 +889,22 @@ class Batch:
         st, stats = cudisc_coag_batch_step(self.handle, [r.data_ptr() for r in rhos], t_span,
                                            [d.data_ptr() if d is not None else None for d in dts]
                                            if dts is not None else None, stream, check=check)
+        for s in stats:
+            s["status"] = s["worst_status"]
+        return stats
+
+    def step_async(self, rhos, t_span, dts=None):
+        """Issue every disc's integration, forked from and joined back to
+        torch's current stream, without synchronising (graph-capturable once
+        a synchronous step() has run)."""
+        stream = self.torch.cuda.current_stream().cuda_stream
+        cudisc_coag_batch_step_async(self.handle, [r.data_ptr() for r in rhos], t_span,
+                                     [d.data_ptr() if d is not None else None for d in dts]
+                                     if dts is not None else None, stream)
+
+    def step_wait(self, check=True):
+        """Per-disc stats of the last issued batch step."""
+        st, stats = cudisc_coag_batch_step_wait(self.handle, len(self._views), check=check)
         for s in stats:
             s["status"] = s["worst_status"]
         return stats

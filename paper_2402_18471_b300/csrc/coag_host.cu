@@ -1172,6 +1172,42 @@ cudisc_status cudisc_coag_batch_step(cudisc_coag_batch *b, double *const *rho, d
     return worst;
 }
 
+cudisc_status cudisc_coag_batch_step_async(cudisc_coag_batch *b, double *const *rho, double t_span,
+                                           double *const *dt_cell, void *stream)
+{
+    if (!b) return fail(nullptr, CUDISC_EINVAL, "batch is NULL");
+    if (!rho) return fail(nullptr, CUDISC_EINVAL, "rho is NULL");
+    const int n = (int)b->ctx.size();
+    for (int i = 0; i < n; i++)
+        if (!rho[i]) return fail(nullptr, CUDISC_EINVAL, "rho[" + std::to_string(i) + "] is NULL");
+    if (!(t_span > 0.0) || !std::isfinite(t_span)) return fail(nullptr, CUDISC_EINVAL, "t_span must be positive and finite");
+    cudaStream_t s0 = (cudaStream_t)stream;
+    cudaError_t e = cudaEventRecord(b->ready, s0);
+    if (e != cudaSuccess) return fail(nullptr, CUDISC_ECUDA, cudaGetErrorString(e));
+    // fork every disc's stream from s0 and join it back: the whole batch is
+    // one span of s0's work (and one graph when s0 is being captured)
+    for (int i = 0; i < n; i++) {
+        cudisc_coag_ctx *c = b->ctx[i];
+        CUDA_TRY(c, cudaStreamWaitEvent(b->stream[i], b->ready, 0));
+        const cudisc_status st = issue_step(c, rho[i], t_span, dt_cell ? dt_cell[i] : nullptr, false);
+        if (st != CUDISC_OK) return st;
+        CUDA_TRY(c, cudaEventRecord(b->done[i], b->stream[i]));
+        CUDA_TRY(c, cudaStreamWaitEvent(s0, b->done[i], 0));
+    }
+    return CUDISC_OK;
+}
+
+cudisc_status cudisc_coag_batch_step_wait(cudisc_coag_batch *b, cudisc_step_stats *stats)
+{
+    if (!b) return fail(nullptr, CUDISC_EINVAL, "batch is NULL");
+    cudisc_status worst = CUDISC_OK;
+    for (size_t i = 0; i < b->ctx.size(); i++) {
+        const cudisc_status st = finish_step(b->ctx[i], stats ? &stats[i] : nullptr);
+        if (st != CUDISC_OK && (worst == CUDISC_OK || st > worst)) worst = st;
+    }
+    return worst;
+}
+
 void cudisc_coag_batch_destroy(cudisc_coag_batch *b) { free_batch(b); }
 
 // ---- shards for several GPUs ---------------------------------------------

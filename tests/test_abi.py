@@ -110,6 +110,8 @@ def test_null_context_is_an_error_not_a_crash():
     assert L.cudisc_coag_batch_ctx(None, 0, C.byref(h)) == coag.EINVAL
     assert L.cudisc_coag_batch_build_kernel(None) == coag.EINVAL
     assert L.cudisc_coag_batch_step(None, None, 1.0, None, None, None) == coag.EINVAL
+    assert L.cudisc_coag_batch_step_async(None, None, 1.0, None, None) == coag.EINVAL
+    assert L.cudisc_coag_batch_step_wait(None, None) == coag.EINVAL
     L.cudisc_coag_batch_destroy(None)
     L.cudisc_coag_destroy(None)
     assert L.cudisc_coag_build_kernel_async(None) == coag.EINVAL

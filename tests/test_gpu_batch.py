@@ -76,6 +76,38 @@ def test_batch_shares_the_sms(coag_mod):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_batch_step_in_one_cuda_graph(coag_mod, precision):
+    """All discs of a batch captured as one graph (each disc forked from the
+    capturing stream and joined back), replayed twice: bitwise the
+    synchronous batch step, the same accepted counts."""
+    discs = small_batch()
+    b = coag_mod.Batch(discs, precision)
+    init = [b.disc(i).state(d.rho0) for i, d in enumerate(discs)]
+    refs = [x.clone() for x in init]
+    stats = b.step(refs, discs[0].t_span)
+    assert all(st["worst_status"] == 0 for st in stats)
+    ys = [x.clone() for x in init]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        for y, x in zip(ys, init):
+            y.copy_(x)
+        b.step_async(ys, discs[0].t_span)
+    for _ in range(2):
+        for y in ys:
+            y.zero_()
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        st2 = b.step_wait()
+        for i in range(len(discs)):
+            assert st2[i]["worst_status"] == 0 and st2[i]["accepted"] == stats[i]["accepted"]
+            assert torch.equal(ys[i], refs[i])
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_async_step_in_a_cuda_graph(coag_mod, precision):
     d = synth.make_disc(8, 16, 40, 1e-5, 1.0, 5.0, 100.0, 300.0, alpha=1e-3, v_frag=100.0, seed=35)
     s = torch.cuda.Stream()
