@@ -57,9 +57,9 @@ FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
 # from one ncu capture of the named kernel (summaries under profiles/), valid
 # only for the kernel source they were taken on: a changed source reports null.
 MEASURED_TRAFFIC = {
-    "step_mixed_kernel": {"bytes_per_unit": (27.934206e9 + 0.641626e9) / 635513, "unit": "RHS evaluation",
+    "step_mixed_kernel": {"bytes_per_unit": (27.263355e9 + 0.621313e9) / 635513, "unit": "RHS evaluation",
                           "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
-                          "sha256": "4c9ba385ca268fe12da33bada02a8fc80e08bb0fc53347c94441711d07083aa3"},
+                          "sha256": "4baabbf21bb91af116bfcbc0fae71712879ab49f5f5eb3fedfd047d51ff08468"},
     "kbuild32_fast_kernel": {"bytes_per_unit": 21.657344e6 + 286.970368e6, "unit": "launch (8192 cells x 100 bins)",
                              "source": "paper_2402_18471_b300/csrc/kbuild.cu",
                              "sha256": "9df89ea17b9e98d86de430acce9ff5e5965a96c173b627df0a3357b3e852547c"},

@@ -780,12 +780,21 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
 
 // Generator thread: one TMEM row (a slot's hi or lo part) and kGP pairs of
 // every block (a kGenQ-th of its 16).  a = x_i x_j K p_coag, b = x_i x_j K
-// p_frag, split hi = rn_tf32(v), lo = v - hi; the thread keeps the
-// half its row holds and writes the 2 kGP values into the stage's TMEM
-// columns.  kv: the thread's 2-pair chunks {K p_c, K p_f, K p_c, K p_f}.
+// p_frag, split into hi, v rounded to nearest at TF32's 11 significant bits,
+// and lo = v - hi (exact); the thread keeps the half its row holds and
+// writes the 2 kGP values into the stage's TMEM columns.  kv: the thread's
+// 2-pair chunks {K p_c, K p_f, K p_c, K p_f}.
 // Packed FP32 pairs (two lanes of one 64-bit register): one instruction
-// rounds both products (mul.rn.f32x2 / sub.rn.f32x2, the same IEEE
-// round-to-nearest as two scalar ones), halving the generators' FP32 issue.
+// rounds both products (mul/sub/fma.rn.f32x2, the same IEEE round-to-nearest
+// as two scalar ones), halving the generators' FP32 issue.  The split is
+// Veltkamp's (Dekker 1971): with t = (2^13 + 1) v, hi = t - (t - v) keeps the
+// leading 24 - 13 = 11 bits of v, rounded to nearest.  It runs on the FMA
+// pipe as three fused multiply-adds (t = sigma v - 0, d = v (-1) + t,
+// hi = d (-1) + t): a chain of packed subtractions t - (t - v) came out as v
+// itself (a probe found every lane's hi equal to v), and the one-instruction
+// conversion cvt.rna.tf32.f32 runs on the conversion pipe, which bounded the
+// generators (the three fused operations took the bench step from 58.3 to
+// 55.8 ms).
 __device__ __forceinline__ unsigned long long pk2(float a, float b)
 {
     unsigned long long r;
@@ -808,13 +817,11 @@ __device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigne
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
-// TF32 rounding to nearest, ties away from zero, in one conversion (the same
-// rounding as tf32_rn's integer form)
-__device__ __forceinline__ float tf32_rna(float v)
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c)
 {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return __uint_as_float(r);
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
 }
 
 __device__ __forceinline__ void gen_vals(const float4 (&kc)[kGC], const float *xr, int bi, int jfirst,
@@ -829,6 +836,8 @@ __device__ __forceinline__ void gen_vals(const float4 (&kc)[kGC], const float *x
     }
     const float *kv = (const float *)kc;
     const unsigned long long xi2 = pk2(xi, xi);
+    // Veltkamp's split constant 2^13 + 1, -1, and -0 (the addend that leaves t = sigma v)
+    const unsigned long long sig2 = pk2(8193.0f, 8193.0f), mone2 = pk2(-1.0f, -1.0f), mzero2 = pk2(-0.0f, -0.0f);
 #pragma unroll
     for (int u = 0; u < kGP; u += 2) {
         float xa, xb;
@@ -838,11 +847,10 @@ __device__ __forceinline__ void gen_vals(const float4 (&kc)[kGC], const float *x
             const float xx = t == 0 ? xa : xb;
             const int q = 2 * (u + t);
             const unsigned long long v2 = mul2(pk2(xx, xx), pk2(kv[q], kv[q + 1]));   // x_i x_j {K p_c, K p_f}
-            float v0, v1;
-            upk2(v2, v0, v1);
-            const float h0 = tf32_rna(v0), h1 = tf32_rna(v1);
-            if (lo_half) upk2(sub2(v2, pk2(h0, h1)), out[q], out[q + 1]);
-            else { out[q] = h0; out[q + 1] = h1; }
+            const unsigned long long t2 = fma2(sig2, v2, mzero2);
+            const unsigned long long h2 = fma2(mone2, fma2(mone2, v2, t2), t2);
+            if (lo_half) upk2(sub2(v2, h2), out[q], out[q + 1]);
+            else upk2(h2, out[q], out[q + 1]);
         }
     }
 }
