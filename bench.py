@@ -59,7 +59,7 @@ FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
 MEASURED_TRAFFIC = {
     "step_mixed_kernel": {"bytes_per_unit": (27.263355e9 + 0.621313e9) / 635513, "unit": "RHS evaluation",
                           "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
-                          "sha256": "4baabbf21bb91af116bfcbc0fae71712879ab49f5f5eb3fedfd047d51ff08468"},
+                          "sha256": "872174406af4543b2dfcd87328e6ec1fa2d68f971876a47d23c2f016df376d37"},
     "kbuild32_fast_kernel": {"bytes_per_unit": 21.657344e6 + 286.970368e6, "unit": "launch (8192 cells x 100 bins)",
                              "source": "paper_2402_18471_b300/csrc/kbuild.cu",
                              "sha256": "9df89ea17b9e98d86de430acce9ff5e5965a96c173b627df0a3357b3e852547c"},

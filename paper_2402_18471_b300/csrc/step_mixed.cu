@@ -377,20 +377,13 @@ __device__ __forceinline__ double warp_sum(double v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-// TF32 split: hi = rn_tf32(v), an exact TF32 value, and lo = v - hi, exact in
-// FP32 (|lo| <= 2^-11 |v|).  The tensor core reads lo at TF32 precision (its
-// 13 low mantissa bits take no part), an error of at most 2^-10 |lo|, so the
-// hi + lo it multiplies matches v to 2^-21 relative.  (Rounding lo as well
-// would halve that bound for two more integer operations per element on the
-// generators, which bound the pass.)
-// Rounding to the 10-bit TF32 mantissa, ties away from zero, is integer
-// arithmetic on the bits of a finite float: add half a TF32 ulp (bit 12) to
-// the magnitude bits and clear the 13 dropped bits (a carry into the
-// exponent is the correct rounding up to the next binade).
-__device__ __forceinline__ float tf32_rn(float v)
-{
-    return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
-}
+// TF32 split: hi = v rounded to nearest at 11 significant bits, an exact
+// TF32 value, and lo = v - hi, exact in FP32 (|lo| <= 2^-11 |v|).  The tensor
+// core reads lo at TF32 precision (its 13 low mantissa bits take no part), an
+// error of at most 2^-10 |lo|, so the hi + lo it multiplies matches v to
+// 2^-21 relative.  (Rounding lo as well would halve that bound for more
+// arithmetic per element on the generators.)  The generators form hi by
+// Veltkamp's split (gen_vals).
 
 // ---- per-slot logic (one warp per slot, lanes over bins) ------------------
 
@@ -1185,8 +1178,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
         // c_full themselves) ----
         if (lane == 0 && pairm && !leader) {
             const uint32_t pr_remote = mapa(su32(pr_full), (uint32_t)(crank ^ 1));
-            int ms = 0, mc = 0;
-            uint32_t mu = 0, mv = 0;
+            int ms = 0;
+            uint32_t mu = 0;
             for (int r = 0;; r++) {
                 if (r > 0) {
                     if (!twait(go, (r - 1) & 1, &s_err, ERR_WAIT_MMA)) break;
@@ -1194,10 +1187,9 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                 }
                 bool ok = true;
                 for (int st = st_lo; st < st_hi; st++) {
-                    const int sb = ms, sc = mc;
-                    const uint32_t ub = mu, uc = mv;
+                    const int sb = ms;
+                    const uint32_t ub = mu;
                     if (++ms == SB) { ms = 0; mu++; }
-                    if (++mc == kAStages) { mc = 0; mv++; }
                     if (!twait(&bt_full[sb], ub & 1, &s_err, ERR_WAIT_MMA)) { ok = false; break; }
                     mbar_arrive_remote(pr_remote + 8u * (uint32_t)sb);   // release, cluster scope
                 }
