@@ -558,12 +558,13 @@ __device__ void slot_finish(const MixedArgs &a, Slot &sl, int slot)
 // 2^-24), so the budget leaves at most that fraction of s, itself the
 // contraction's rounding (~1e-7 of sum |dx|): ~1e-12 of the increment per
 // step at worst.  yh, the new leading part, is the next stage input.
+template <int MB>
 __device__ void commit_increment(SlotBufs B, int N, const float *dx)
 {
     const int lane = threadIdx.x & 31;
     float sh = 0.f, sl = 0.f, sa = 0.f;
 #pragma unroll
-    for (int m = 0; m < kLaneBins; m++) {          // dx is 0 beyond N
+    for (int m = 0; m < MB; m++) {                 // dx is 0 beyond N
         float e;
         two_sum(sh, dx[m], sh, e);
         sl = __fadd_rn(sl, e);
@@ -579,7 +580,7 @@ __device__ void commit_increment(SlotBufs B, int N, const float *dx)
     }
     const float q = sa > 0.f ? __fdiv_rn(__fadd_rn(sh, sl), sa) : 0.f;
 #pragma unroll
-    for (int m = 0; m < kLaneBins; m++) {
+    for (int m = 0; m < MB; m++) {
         const int k = lane + 32 * m;
         if (k < N) {
             float h = B.yh[k], l = B.yl[k];
@@ -610,10 +611,11 @@ __device__ bool begin_step(const MixedArgs &a, Slot &sl, float *xrow, SlotBufs B
 // Process one right-hand side result, D = sum of the TMEM accumulators for
 // this slot (kx = Sx D in scaled units).  Returns true when the slot
 // finished its cell.
+// MB: bins per lane, ceil(N / 32) (4 up to 128 bins, else kLaneBins).
+template <int MB>
 __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const float *Drow, int slot)
 {
     const int N = a.t.N, lane = threadIdx.x & 31;
-    constexpr int MB = kLaneBins;
     SlotBufs B = slot_bufs(a, slot);
     const float sx = sl.sxf;
     float kv[MB];
@@ -671,7 +673,7 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
                 const int k = lane + 32 * m;
                 dx[m] = (k < N) ? b1 * B.k1[k] + b2 * B.k2[k] + b3 * B.k3[k] : 0.f;
             }
-            commit_increment(B, N, dx);
+            commit_increment<MB>(B, N, dx);
             sl.nrep++;
             sl.nacc = sl.nrep;
             if (sl.nrep >= nh) return true;
@@ -742,7 +744,7 @@ __device__ bool slot_advance(const MixedArgs &a, Slot &sl, float *xrow, const fl
         const bool finite = __all_sync(0xffffffffu, fin);
         const bool nonneg = __all_sync(0xffffffffu, pos);
         if (finite && E <= 1.f && nonneg) {
-            commit_increment(B, N, dx);
+            commit_increment<MB>(B, N, dx);
             sl.t = sl.last ? sl.tend : sl.t + sl.hs;
 #pragma unroll
             for (int m = 0; m < MB; m++) {
@@ -949,7 +951,7 @@ __device__ __forceinline__ bool gen_pass(GenCtx &G, long long g0, int st_lo, int
 // exchanges; larger P shortens a pass, which bounds the time of the costliest
 // cells once there are fewer cells than slots to keep busy.
 
-template <bool Pair>
+template <bool Pair, int MB>
 __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
 {
     uint8_t *sm = smem_base();
@@ -1382,24 +1384,24 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                     // the members' partial rows added in member order (not
                     // starting with this CTA's own), so that a cell's result
                     // does not depend on which member keeps its slot
-                    float v[kLaneBins];
+                    float v[MB];
 #pragma unroll
-                    for (int m = 0; m < kLaneBins; m++) v[m] = 0.f;
+                    for (int m = 0; m < MB; m++) v[m] = 0.f;
                     for (int o = 0; o < P; o++) {
                         const float *dp = o == rank ? Drow : dpeer + ((size_t)(o < rank ? o : o - 1) * SL + sl) * NBP;
 #pragma unroll
-                        for (int m = 0; m < kLaneBins; m++)
+                        for (int m = 0; m < MB; m++)
                             if (lane + 32 * m < N) v[m] = o == 0 ? dp[lane + 32 * m] : v[m] + dp[lane + 32 * m];
                     }
 #pragma unroll
-                    for (int m = 0; m < kLaneBins; m++)
+                    for (int m = 0; m < MB; m++)
                         if (lane + 32 * m < N) Drow[lane + 32 * m] = v[m];
                 }
                 __syncwarp();
                 if (slr.cell >= 0) {
                     Slot loc = slr;
                     __syncwarp();
-                    bool fin = slot_advance(a, loc, xrows + (size_t)sidx * XS, Drow, sidx);
+                    bool fin = slot_advance<MB>(a, loc, xrows + (size_t)sidx * XS, Drow, sidx);
                     __syncwarp();
                     if (fin) {
                         slot_finish(a, loc, sidx);
@@ -1499,6 +1501,16 @@ int sm_count();
 // Clusters of P CTAs that can run at once (the launch's groups must all be
 // resident together: a group that started late would find its initial cells
 // untouched).  Asked of the runtime once per device, P and shared-memory size.
+// The kernel instance of a launch: CTA pairs or single CTAs, and the bins per
+// lane of the per-slot logic (4 up to 128 bins; CTA pairs need <= 128).  The
+// instances share their static shared memory and launch shape.
+using MixedKernel = void (*)(MixedArgs);
+MixedKernel mixed_kernel(bool pair, int N)
+{
+    if (pair) return step_mixed_kernel<true, 4>;
+    return N <= 128 ? step_mixed_kernel<false, 4> : step_mixed_kernel<false, kLaneBins>;
+}
+
 int max_clusters(int P, size_t smem, int n_sm, bool pair = false)   // P: the cluster size
 {
     if (P == 1) return n_sm;
@@ -1512,7 +1524,7 @@ int max_clusters(int P, size_t smem, int n_sm, bool pair = false)   // P: the cl
     for (int i = 0; i < n_cache; i++)
         if (cache[i].dev == dev && cache[i].P == (pair ? -P : P) && cache[i].smem == smem) return cache[i].n;
     int n = 0;
-    auto kern = pair ? step_mixed_kernel<true> : step_mixed_kernel<false>;
+    auto kern = mixed_kernel(pair, pair ? 128 : kMaxMixedBins);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
         cudaLaunchConfig_t lc = {};
@@ -1552,7 +1564,7 @@ size_t static_smem_bytes(bool pair)
     size_t &v = cached[pair ? 1 : 0];
     if (v == 0) {
         cudaFuncAttributes fa;
-        const cudaError_t e = cudaFuncGetAttributes(&fa, pair ? step_mixed_kernel<true> : step_mixed_kernel<false>);
+        const cudaError_t e = cudaFuncGetAttributes(&fa, mixed_kernel(pair, pair ? 128 : kMaxMixedBins));
         v = (e == cudaSuccess && fa.sharedSizeBytes > 0 && fa.sharedSizeBytes <= 8192) ? fa.sharedSizeBytes : 2048;
         if (e != cudaSuccess) cudaGetLastError();
     }
@@ -1708,8 +1720,7 @@ cudaError_t launch_kernel(const Config &cf, const MixedArgs &a, cudaStream_t str
         lc.attrs = at;
         lc.numAttrs = 1;
     }
-    return cf.pair ? cudaLaunchKernelEx(&lc, step_mixed_kernel<true>, a)
-                   : cudaLaunchKernelEx(&lc, step_mixed_kernel<false>, a);
+    return cudaLaunchKernelEx(&lc, mixed_kernel(cf.pair != 0, a.t.N), a);
 }
 
 // L2 prefetch of the K tables pays when the slot groups' tables (8 KB per
@@ -1740,7 +1751,7 @@ cudaError_t launch_mixed(const cudisc_coag_ctx *c, int mode, double *rho, double
     if (need > c->work_bytes) return cudaErrorInvalidValue;
     if (cf.P != c->mix_P || cf.groups != c->mix_G || cf.C != c->mix_C || cf.pair != c->mix_pair)
         return cudaErrorInvalidValue;   // layout of the K tables
-    cudaError_t e = cudaFuncSetAttribute(cf.pair ? step_mixed_kernel<true> : step_mixed_kernel<false>,
+    cudaError_t e = cudaFuncSetAttribute(mixed_kernel(cf.pair != 0, c->N),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(c->d_counter + 1, 0, 2 * sizeof(int), c->stream);
@@ -1832,7 +1843,7 @@ cudaError_t launch_step_mixed_static(cudisc_coag_ctx *c, double *rho, double t_s
         if (e != cudaSuccess) return e;
         c->static_scratch = ptr;
     }
-    cudaError_t e = cudaFuncSetAttribute(cf.pair ? step_mixed_kernel<true> : step_mixed_kernel<false>,
+    cudaError_t e = cudaFuncSetAttribute(mixed_kernel(cf.pair != 0, c->N),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(c->d_counter + 1, 0, 2 * sizeof(int), c->stream);
