@@ -200,8 +200,10 @@ typedef struct {
 
 /* Create a context: validates params (EINVAL on any inconsistency, naming the
  * field), builds the mapping tensors of Eqs. (Cijk), (Rijk), (fragrem) and
- * (Nijk) on the host in FP64, uploads them, allocates the workspace, and
- * builds K and p_frag from the gas arrays (as cudisc_coag_build_kernel).
+ * (Nijk) on the host in FP64, uploads them, allocates the workspace (and a
+ * pinned host block of ~40 bytes per cell, into which each step's per-cell
+ * results are read back), and builds K and p_frag from the gas arrays (as
+ * cudisc_coag_build_kernel).
  * The device pointers in params must stay valid for the context's life. */
 cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx **out);
 
@@ -519,13 +521,16 @@ cudisc_status cudisc_coag_step_static_scratch(cudisc_coag_ctx *ctx, double *rho,
  * the gas arrays when rebuild != 0 (as cudisc_coag_build_kernel), integrates
  * every cell over t_span with fresh initial step sizes (dt_cell NULL), and
  * copies the result to rho_out (host [n_cells][N]; may be rho_in).  All on
- * the context's stream, which is synchronised before the call returns.
+ * the context's stream, which is synchronised before the call returns,
+ * except the copy-in when rebuild != 0: it runs on a second stream of the
+ * context beside the table build (which reads the gas arrays only), forked
+ * after the stream's earlier work and joined before the integration.
  *   - Pinned host memory (cudaHostAlloc / cudaHostRegister) makes both
  *     copies DMA transfers; pageable memory works, through the driver's
  *     staging buffers.
- *   - The device state array (n_cells x N doubles) is allocated at the first
- *     call on a context and freed by cudisc_coag_destroy; later calls
- *     allocate nothing.
+ *   - The device state array (n_cells x N doubles), the second stream and
+ *     its two events are created at the first call on a context and freed
+ *     by cudisc_coag_destroy; later calls allocate nothing.
  *   - stats as cudisc_coag_step (elapsed_ms: the integration alone).
  *   - CUDISC_EINVAL for a NULL context or host pointer; per-cell failures as
  *     cudisc_coag_step (rho_out then holds the states reached). */

@@ -17,6 +17,9 @@ using cdc::CellOut;
 namespace {
 
 thread_local std::string g_thread_err;
+// byte offset of the per-cell results in a context's pinned read-back block
+// (the status word comes first)
+constexpr size_t kStatsOff = 64;
 
 } // namespace
 
@@ -470,6 +473,10 @@ static void free_ctx(cudisc_coag_ctx *c)
     if (c->ev1) cudaEventDestroy(c->ev1);
     for (cudaEvent_t &ev : c->evb)
         if (ev) cudaEventDestroy(ev);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_copied) cudaEventDestroy(c->ev_copied);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->h_stats) cudaFreeHost(c->h_stats);
     cdc::vjp_free(c);
     delete c;
 }
@@ -557,6 +564,7 @@ cudisc_status cudisc_coag_init(const cudisc_coag_params *params, cudisc_coag_ctx
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
     for (cudaEvent_t &ev : c->evb)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_stats, kStatsOff + (size_t)c->n_cells * sizeof(cdc::CellOut));
     if (e != cudaSuccess) {
         cuda_fail(c, e, "cudisc_coag_init: workspace allocation");
         st = (e == cudaErrorMemoryAllocation) ? CUDISC_ENOMEM : CUDISC_ECUDA;
@@ -686,19 +694,24 @@ cudisc_status cudisc_coag_set_records(cudisc_coag_ctx *c, double *dt_log, long l
 
 static cudisc_status finish_step(cudisc_coag_ctx *c, cudisc_step_stats *stats)
 {
+    // the status word and the per-cell results, read into pinned memory
+    // behind the integration, then one synchronisation
+    int *h_err = (int *)c->h_stats;
+    const CellOut *h = (const CellOut *)((char *)c->h_stats + kStatsOff);
+    CUDA_TRY(c, cudaMemcpyAsync(h_err, c->d_counter + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync((void *)h, c->d_out, (size_t)c->n_cells * sizeof(CellOut), cudaMemcpyDeviceToHost,
+                                c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    int dev_err = 0;
-    CUDA_TRY(c, cudaMemcpy(&dev_err, c->d_counter + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    const int dev_err = *h_err;
     if (dev_err != 0) {
         char buf[128];
         std::snprintf(buf, sizeof(buf), "a bounded device wait ran out (code %d); results are invalid", dev_err);
         return fail(c, CUDISC_ECUDA, buf);
     }
-    std::vector<CellOut> h(c->n_cells);
-    CUDA_TRY(c, cudaMemcpy(h.data(), c->d_out, h.size() * sizeof(CellOut), cudaMemcpyDeviceToHost));
     cudisc_step_stats s;
     std::memset(&s, 0, sizeof(s));
-    for (const CellOut &o : h) {
+    for (int i = 0; i < c->n_cells; i++) {
+        const CellOut &o = h[i];
         s.accepted += o.n_acc;
         s.rejected += o.n_rej;
         if (o.n_acc > s.max_accepted) s.max_accepted = o.n_acc;
@@ -758,11 +771,25 @@ cudisc_status cudisc_coag_step_host(cudisc_coag_ctx *c, const double *rho_in, do
     if (!rho_in || !rho_out) return fail(c, CUDISC_EINVAL, "rho_in and rho_out must be host arrays");
     if (!(t_span > 0.0) || !std::isfinite(t_span)) return fail(c, CUDISC_EINVAL, "t_span must be positive and finite");
     const size_t bytes = (size_t)c->n_cells * c->N * sizeof(double);
-    if (!c->d_host_state) CUDA_TRY(c, cudaMalloc(&c->d_host_state, bytes));
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_host_state, rho_in, bytes, cudaMemcpyHostToDevice, c->stream));
+    if (!c->d_host_state) {
+        CUDA_TRY(c, cudaMalloc(&c->d_host_state, bytes));
+        CUDA_TRY(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming));
+    }
     if (rebuild) {
+        // the kernel tables depend on the gas arrays only: the state's copy
+        // runs on a second stream beside their build, forked after the
+        // stream's earlier work and joined before the integration
+        CUDA_TRY(c, cudaEventRecord(c->ev_fork, c->stream));
+        CUDA_TRY(c, cudaStreamWaitEvent(c->copy_stream, c->ev_fork, 0));
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_host_state, rho_in, bytes, cudaMemcpyHostToDevice, c->copy_stream));
+        CUDA_TRY(c, cudaEventRecord(c->ev_copied, c->copy_stream));
         const cudisc_status sb = cudisc_coag_build_kernel_async(c);
+        CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_copied, 0));
         if (sb != CUDISC_OK) return sb;
+    } else {
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_host_state, rho_in, bytes, cudaMemcpyHostToDevice, c->stream));
     }
     cudisc_status st = issue_step(c, c->d_host_state, t_span, nullptr, true);
     if (st != CUDISC_OK) return st;

@@ -116,6 +116,9 @@ struct cudisc_coag_ctx {
     bool timed = false;                // the last integration issued recorded ev0/ev1
     void *static_scratch = nullptr;    // device address of the fixed scratch array (first static call)
     double *d_host_state = nullptr;    // [n_cells][N] device state of cudisc_coag_step_host (first call)
+    cudaStream_t copy_stream = nullptr;   // cudisc_coag_step_host: the state's copy-in beside the kernel build
+    cudaEvent_t ev_fork = nullptr, ev_copied = nullptr;
+    void *h_stats = nullptr;           // pinned: the status word, then [n_cells] CellOut (finish_step's reads)
     long long inject_wait_cycles = 0;  // test hook: wait limit of the mixed kernel (0: the default)
     int inject_withhold = 0;           // test hook: the mixed kernel's producer issues no copies
     // integration workspace

@@ -170,6 +170,15 @@ def test_step_host_equals_device_step(coag_mod, precision):
     pageable = np.ascontiguousarray(d.rho0).copy()
     st = g.step_host(pageable, pageable, d.t_span, rebuild=False)
     assert st["accepted"] == ref["accepted"] and np.array_equal(pageable, want)
+    # the copy-in on the context's second stream, beside the rebuild: from
+    # pageable memory in place, then twice in a row from pinned memory
+    pageable = np.ascontiguousarray(d.rho0).copy()
+    st = g.step_host(pageable, pageable, d.t_span, rebuild=True)
+    assert st["accepted"] == ref["accepted"] and np.array_equal(pageable, want)
+    for _ in range(2):
+        out.zero_()
+        st = g.step_host(pinned, out, d.t_span)
+        assert st["accepted"] == ref["accepted"] and np.array_equal(out.numpy(), want)
     g.close()
 
 
