@@ -57,9 +57,9 @@ FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
 # from one ncu capture of the named kernel (summaries under profiles/), valid
 # only for the kernel source they were taken on: a changed source reports null.
 MEASURED_TRAFFIC = {
-    "step_mixed_kernel": {"bytes_per_unit": (27.295945e9 + 0.559559e9) / 635513, "unit": "RHS evaluation",
+    "step_mixed_kernel": {"bytes_per_unit": (27.224462e9 + 0.563830e9) / 635513, "unit": "RHS evaluation",
                           "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
-                          "sha256": "3376ab5b2b0cf79a4ac390174af1835f7695643c95e8b1411597fc5df70d22ba"},
+                          "sha256": "c9c6c1a72de4b5b10f079e07957dcdefda24fad82daf81f171af0893f084e08e"},
     "kbuild32_fast_kernel": {"bytes_per_unit": 21.657344e6 + 286.970368e6, "unit": "launch (8192 cells x 100 bins)",
                              "source": "paper_2402_18471_b300/csrc/kbuild.cu",
                              "sha256": "9df89ea17b9e98d86de430acce9ff5e5965a96c173b627df0a3357b3e852547c"},

@@ -265,6 +265,10 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes
 {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -1410,11 +1414,27 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                         int w = 0;
                         if (lane == 0) w = ngrp * C + atomicAdd(a.queue, 1);
                         w = __shfl_sync(0xffffffffu, w, 0);
+                        // the queue's next two cells (loaded here, used after
+                        // this refill, so that their latency overlaps it)
+                        int cn[2];
+#pragma unroll
+                        for (int d = 0; d < 2; d++)
+                            cn[d] = w + 1 + d < n_work ? (a.wl.cells ? a.wl.cells[w + 1 + d] : w + 1 + d) : -1;
                         __syncwarp();
                         if (lane == 0) slr = loc;
                         __syncwarp();
                         slot_load(a, slr, xrows + (size_t)sidx * XS, sidx,
                                   w < n_work ? (a.wl.cells ? a.wl.cells[w] : w) : -1);
+                        // their K tables and states into L2 ahead of their
+                        // refills (whichever slots take them), so that those
+                        // wait on L2 rather than DRAM
+#pragma unroll
+                        for (int d = 0; d < 2; d++)
+                            if (cn[d] >= 0) {
+                                const uint32_t n_ch = (uint32_t)a.t.n_blk * 8u;
+                                if (lane == 0) bulk_prefetch_l2(a.K32 + (size_t)cn[d] * n_ch, n_ch * 16u);
+                                if (lane * 16 < N) prefetch_l2(a.rho + (size_t)cn[d] * N + lane * 16);
+                            }
                     } else if (lane == 0) {
                         slr = loc;
                     }
