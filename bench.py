@@ -57,9 +57,9 @@ FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
 # from one ncu capture of the named kernel (summaries under profiles/), valid
 # only for the kernel source they were taken on: a changed source reports null.
 MEASURED_TRAFFIC = {
-    "step_mixed_kernel": {"bytes_per_unit": (27.224462e9 + 0.563830e9) / 635513, "unit": "RHS evaluation",
+    "step_mixed_kernel": {"bytes_per_unit": (27.926282e9 + 0.517050e9) / 635513, "unit": "RHS evaluation",
                           "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
-                          "sha256": "c9c6c1a72de4b5b10f079e07957dcdefda24fad82daf81f171af0893f084e08e"},
+                          "sha256": "f4741f654f1acae6515de687894c884c3b8f4ce3b5bf81330fc229a8094780e2"},
     "kbuild32_fast_kernel": {"bytes_per_unit": 21.657344e6 + 286.970368e6, "unit": "launch (8192 cells x 100 bins)",
                              "source": "paper_2402_18471_b300/csrc/kbuild.cu",
                              "sha256": "9df89ea17b9e98d86de430acce9ff5e5965a96c173b627df0a3357b3e852547c"},

@@ -117,6 +117,8 @@ struct __align__(16) Slot {
     long long nacc, nrej, nrep;
     float sxf, atolx, hsf;             // Sx, atol / Sx and hs in FP32 for the per-bin work
     int cell, phase, last, status;
+    int kcell;                         // the cell whose K table this CTA last copied into its block
+                                       // range of the group's buffer for this slot (-1: none)
 };
 
 // ---- PTX wrappers ----------------------------------------------------------
@@ -451,32 +453,40 @@ __device__ __forceinline__ void pair_add(float &h, float &l, float x)
     two_sum(s, __fadd_rn(e, l), h, l);
 }
 
-// Copy cell c's K table into the slot's column of its group's buffer
-// ([block][chunk][slot] x 16 B, one bulk copy per block for the producer),
-// then make the generic-proxy stores visible to those copies.
-__device__ void slot_copy_k(const MixedArgs &a, int slot, int c)
+// Copy 2-pair chunks c_lo .. c_hi - 1 of cell c's K table into slot s's
+// column of group grp's buffer ([block][chunk][slot] x 16 B, read by the
+// producer's bulk copies, one per block).  The caller's threads t = 0 ..
+// nthr - 1 take every nthr-th chunk, D loads in flight each.  Each CTA of a
+// slot group copies the block range it streams, so that only its own
+// producer reads what it wrote: the caller orders the stores before those
+// copies with fence_proxy_global and a barrier.
+static_assert(kSlots == 64, "the per-pass K-copy mask reads slots lane and lane + 32");
+template <int D>
+__device__ void copy_k_range(const MixedArgs &a, int grp, int s, int c, int c_lo, int c_hi, int t, int nthr)
 {
-    const int lane = threadIdx.x & 31;
-    const int n_ch = a.t.n_blk * 8;                  // 2-pair chunks of a table
+    const int n_ch = a.t.n_blk * 8;
     const float4 *src = a.K32 + (size_t)c * n_ch;
-    float4 *dst = a.Kslot + (size_t)group_of_block(a) * n_ch * kSlots + slot;
-    // sixteen loads in flight per lane, then their stores
-    int i0 = lane;
-    for (; i0 + 15 * 32 < n_ch; i0 += 16 * 32) {
-        float4 v[16];
+    float4 *dst = a.Kslot + (size_t)grp * n_ch * kSlots + s;
+    for (int i0 = c_lo + t; i0 < c_hi; i0 += D * nthr) {
+        float4 v[D];
 #pragma unroll
-        for (int j = 0; j < 16; j++) v[j] = __ldg(src + i0 + 32 * j);
+        for (int j = 0; j < D; j++) {
+            const int i = i0 + j * nthr;
+            v[j] = i < c_hi ? __ldg(src + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
-        for (int j = 0; j < 16; j++) dst[(size_t)(i0 + 32 * j) * kSlots] = v[j];
+        for (int j = 0; j < D; j++) {
+            const int i = i0 + j * nthr;
+            if (i < c_hi) dst[(size_t)i * kSlots] = v[j];
+        }
     }
-    for (int i = i0; i < n_ch; i += 32) dst[(size_t)i * kSlots] = __ldg(src + i);
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    __syncwarp();
 }
+__device__ __forceinline__ void fence_proxy_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
-// Load cell c into slot: state, scales, phase 0 (or mark the slot empty).
+// Load cell c into slot: state, scales, phase 0 (or mark the slot empty);
+// its K table is copied by every CTA of the group afterwards (kcell = -1).
 // owner = false: only the stage-input row and the cell id (a slot whose
-// integrator state, and K-table copy, another CTA of the cluster keeps).
+// integrator state another CTA of the cluster keeps).
 __device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, int c, bool owner = true)
 {
     const int N = a.t.N, lane = threadIdx.x & 31;
@@ -485,7 +495,6 @@ __device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, i
         if (lane == 0) sl.cell = -1;
         return;
     }
-    if (owner) slot_copy_k(a, slot, c);
     SlotBufs B = slot_bufs(a, slot);
     const double *rc = a.rho + (size_t)c * N;
     double s = 0.0, sa = 0.0;
@@ -525,6 +534,7 @@ __device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, i
         sl.nacc = sl.nrej = sl.nrep = 0;
         sl.last = 0;
         sl.status = CUDISC_OK;
+        sl.kcell = -1;
     }
 }
 
@@ -1068,9 +1078,9 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
     }
     // initial slot fill: group x takes cells x, x + G, .., x + (C - 1) G (C =
     // the cells per group, at most NS): every group a spread of radii.  Every
-    // CTA of the cluster sets up the stage inputs of all 64 slots; the state
-    // of each slot, and the copy of its cell's K table into the group's
-    // buffer, is done by the one that keeps it.
+    // CTA of the cluster sets up the stage inputs of all 64 slots and copies
+    // its block range of their K tables into the group's buffer; the state
+    // of each slot is set up by the one that keeps it.
     const int C = a.kC;
     const int n_work = a.wl.count ? *a.wl.count : a.t.n_cells;   // work item w is cell wl.cells[w] (or w)
     if (warp >= 2) {
@@ -1078,7 +1088,11 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             const int w = grp + s * ngrp;
             const int c = (s < C && w < n_work) ? (a.wl.cells ? a.wl.cells[w] : w) : -1;
             slot_load(a, slots[s], xrows + (size_t)s * XS, s, c, s >= own0 && s < own0 + SL);
+            if (c >= 0) copy_k_range<16>(a, grp, s, c, 8 * b_lo, 8 * b_hi, lane, 32);
+            __syncwarp();
+            if (lane == 0) slots[s].kcell = c;
         }
+        fence_proxy_global();
     }
     tc_fence_before();
     __syncthreads();
@@ -1423,8 +1437,17 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
                         __syncwarp();
                         if (lane == 0) slr = loc;
                         __syncwarp();
-                        slot_load(a, slr, xrows + (size_t)sidx * XS, sidx,
-                                  w < n_work ? (a.wl.cells ? a.wl.cells[w] : w) : -1);
+                        const int cnew = w < n_work ? (a.wl.cells ? a.wl.cells[w] : w) : -1;
+                        slot_load(a, slr, xrows + (size_t)sidx * XS, sidx, cnew);
+                        if (!xchg && cnew >= 0) {
+                            // a lone CTA copies the whole table here, beside the
+                            // other warps' slot work (with a cluster, each member
+                            // copies its own range after the exchange, below)
+                            copy_k_range<16>(a, grp, sidx, cnew, 0, 8 * n_blk, lane, 32);
+                            fence_proxy_global();
+                            __syncwarp();
+                            if (lane == 0) slr.kcell = cnew;
+                        }
                         // their K tables and states into L2 ahead of their
                         // refills (whichever slots take them), so that those
                         // wait on L2 rather than DRAM
@@ -1471,6 +1494,30 @@ __global__ void __launch_bounds__(kThreads, 1) step_mixed_kernel(MixedArgs a)
             // ordered before the bulk copies of the next pass overwrite it
             fence_async_smem();
             if (!gen_sync(gbar, gphase, &s_err)) break;
+            {
+                // the slots that took a new cell this pass (refilled here or
+                // by another member): this CTA copies its block range of their
+                // K tables, all generator threads together, before its
+                // producer's next copies read them.  The mask is the same in
+                // every warp (all read the slots after the barrier).
+                const int ca = slots[lane].cell, cb = slots[lane + 32].cell;
+                const unsigned ma = __ballot_sync(0xffffffffu, ca >= 0 && ca != slots[lane].kcell);
+                const unsigned mb = __ballot_sync(0xffffffffu, cb >= 0 && cb != slots[lane + 32].kcell);
+                const unsigned long long mk = (unsigned long long)ma | ((unsigned long long)mb << 32);
+                if (mk) {
+                    for (unsigned long long mm = mk; mm; mm &= mm - 1) {
+                        const int s2 = __ffsll((long long)mm) - 1;
+                        copy_k_range<4>(a, grp, s2, slots[s2].cell, 8 * b_lo, 8 * b_hi, gt, 32 * kGenWarps);
+                    }
+                    fence_proxy_global();
+                    if (!gen_sync(gbar, gphase, &s_err)) break;
+                    if (gt == 0)
+                        for (unsigned long long mm = mk; mm; mm &= mm - 1) {
+                            const int s2 = __ffsll((long long)mm) - 1;
+                            slots[s2].kcell = slots[s2].cell;
+                        }
+                }
+            }
             if (gt == 0) {
                 int any = 0;
                 for (int s2 = 0; s2 < NS; s2++) any |= (slots[s2].cell >= 0);
