@@ -975,6 +975,7 @@ cudisc_status cudisc_coag_replay(cudisc_coag_ctx *c, double *rho, const double *
     else
         CUDA_TRY(c, cdc::launch_step_mixed(c, rho, 1.0, nullptr, hs, n_h, stride));
     CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
+    c->timed = true;
     return finish_step(c, nullptr);
 }
 
