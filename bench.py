@@ -59,7 +59,7 @@ FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (vector and tensor), nominal
 MEASURED_TRAFFIC = {
     "step_mixed_kernel": {"bytes_per_unit": (27.926282e9 + 0.517050e9) / 635513, "unit": "RHS evaluation",
                           "source": "paper_2402_18471_b300/csrc/step_mixed.cu",
-                          "sha256": "f4741f654f1acae6515de687894c884c3b8f4ce3b5bf81330fc229a8094780e2"},
+                          "sha256": "de7dced6ef4bbb0a6a2585b34495dd75725791a5bdfce8827e2c36533cc412a4"},
     "kbuild32_fast_kernel": {"bytes_per_unit": 21.657344e6 + 286.970368e6, "unit": "launch (8192 cells x 100 bins)",
                              "source": "paper_2402_18471_b300/csrc/kbuild.cu",
                              "sha256": "9df89ea17b9e98d86de430acce9ff5e5965a96c173b627df0a3357b3e852547c"},

@@ -483,8 +483,10 @@ __device__ void copy_k_range(const MixedArgs &a, int grp, int s, int c, int c_lo
 }
 __device__ __forceinline__ void fence_proxy_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
-// Load cell c into slot: state, scales, phase 0 (or mark the slot empty);
-// its K table is copied by every CTA of the group afterwards (kcell = -1).
+// Load cell c into slot: state, scales, phase 0 (or mark the slot empty).
+// Its K table is copied afterwards (kcell = -1 until then): by the refilling
+// warp in a lone CTA, else by every member, its own block range, after the
+// stage-input exchange.
 // owner = false: only the stage-input row and the cell id (a slot whose
 // integrator state another CTA of the cluster keeps).
 __device__ void slot_load(const MixedArgs &a, Slot &sl, float *xrow, int slot, int c, bool owner = true)
@@ -959,7 +961,8 @@ __device__ __forceinline__ bool gen_pass(GenCtx &G, long long g0, int st_lo, int
 // P); CTA r keeps the integrator state of slots SL r .. SL r + SL - 1 (SL =
 // 64 / P).  After its MMAs a CTA sends the partial sums of the other CTAs'
 // slots into their shared memory; after the per-slot logic it sends its own
-// slots' new stage inputs and cells to all of them.  Each exchange ends in
+// slots' new stage inputs and cells to all of them, and each member then
+// copies its block range of the new cells' K tables.  Each exchange ends in
 // one remote mbarrier arrival per sending warp and receiving CTA
 // (release/acquire at cluster scope).  Smaller P loses less to the
 // exchanges; larger P shortens a pass, which bounds the time of the costliest
